@@ -1,0 +1,210 @@
+"""CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The
+product (the CUDA library and its binding) never calls it and shares no code
+with it; the two only share the seeded input generator.
+
+What it computes (Napoli, Pappalardo, Tramontana, CISIS 2013):
+  * fan-in / fan-out per method (Sec. II.A);
+  * per class: LCOM as Chidamber-Kemerer pair counts (P = pairs sharing no
+    owned attribute, Q = pairs sharing one, LCOM_CK = max(P - Q, 0)), LCOM as
+    the Henderson-Sellers fraction 1 - S/(n a) kept as the exact pair
+    (n a - S, n a), and CBO, the number of other classes used (Sec. II.B);
+  * the effect of every candidate Move Method m -> D on the affected classes,
+    the improved/worsened tallies and the kept flag (Sec. III.A rules), by
+    two independent routes: O0 recomputes the affected classes from the
+    definitions after changing cls(m) (the re-evaluation of Sec. IV.C), O1
+    applies the incremental update formulas;
+  * the sorted suggestion list (top-k) and an order-independent digest.
+
+``brute.py`` is a third, pure-Python route (whole-system recompute with
+Python sets) for tiny systems; ``tables.py`` holds the paper's value-count
+model (Sec. III.B) that Table I's ``#values`` column pins.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+RECORD_DTYPE = np.dtype([("s", "<i4"), ("t", "<u2"), ("dcbo_src", "<i2"), ("dcbo_dst", "<i2"),
+                         ("n_improved", "<u2"), ("n_worsened", "<u2"), ("flags", "<u2")])
+KEPT_DTYPE = np.dtype([("m", "<i4"), ("d", "<i4"), ("n_improved", "<i4"), ("d_ck_sum", "<i4"),
+                       ("d_cbo_sum", "<i4"), ("pad", "<i4")])
+CLASS_FIELDS = ("n", "a", "P", "Q", "S", "ck", "hs_num", "hs_den", "cbo")
+CLASS_DTYPE = np.dtype([(f, "<i8") for f in CLASS_FIELDS])
+
+LCOM_CK, LCOM_HS, CBO = 1, 2, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` to ``liboracle.so`` (gcc -O2, pthreads)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread",
+                               "-o", _LIB, _SRC])
+    return _LIB
+
+
+class _Input(ctypes.Structure):
+    _fields_ = [("n_classes", ctypes.c_int32), ("n_methods", ctypes.c_int32),
+                ("n_attrs", ctypes.c_int32), ("cbo_attrs", ctypes.c_int32),
+                ("method_class", ctypes.c_void_p), ("attr_class", ctypes.c_void_p),
+                ("acc_rowptr", ctypes.c_void_p), ("call_rowptr", ctypes.c_void_p),
+                ("acc_idx", ctypes.c_void_p), ("call_idx", ctypes.c_void_p)]
+
+
+class _Crit(ctypes.Structure):
+    _fields_ = [("metric_mask", ctypes.c_uint32), ("min_improved", ctypes.c_int32)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("digest", ctypes.c_uint64), ("n_cand", ctypes.c_int64), ("n_kept", ctypes.c_int64),
+                ("n_methods_with_kept", ctypes.c_int64), ("kept", ctypes.c_void_p),
+                ("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.or_build.argtypes = [ctypes.POINTER(_Input), ctypes.c_int]
+        _lib.or_build.restype = ctypes.c_void_p
+        _lib.or_free.argtypes = [ctypes.c_void_p]
+        _lib.or_class_metrics.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        _lib.or_method_metrics.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 4
+        _lib.or_multigraph.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 3
+        _lib.or_multigraph.restype = ctypes.c_int64
+        _lib.or_evaluate.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Crit), ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.POINTER(_Result)]
+        _lib.or_evaluate.restype = ctypes.c_int
+        _lib.or_evaluate_one.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Crit), ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int64)]
+        _lib.or_evaluate_one.restype = ctypes.c_int
+        _lib.or_free_kept.argtypes = [ctypes.c_void_p]
+        _lib.or_record_hash.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+        _lib.or_record_hash.restype = ctypes.c_uint64
+    return _lib
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+class EvalResult:
+    def __init__(self, digest, n_cand, kept, n_methods_with_kept, records=None):
+        self.digest = digest
+        self.n_cand = n_cand
+        self.kept = kept                      # KEPT_DTYPE array, sorted by the suggestion key
+        self.n_kept = len(kept)
+        self.n_methods_with_kept = n_methods_with_kept
+        self.records = records                # RECORD_DTYPE array or None
+
+
+class Oracle:
+    """The oracle's view of one system (metrics by definition at build time)."""
+
+    def __init__(self, system, cbo_attrs: bool = True, threads: int | None = None):
+        lib = _load()
+        self.sys = system
+        self.threads = threads or default_threads()
+        self._keep = [np.ascontiguousarray(a) for a in (system.method_class, system.attr_class,
+                                                       system.acc_rowptr, system.call_rowptr,
+                                                       system.acc_idx, system.call_idx)]
+        mc, ac, ar, cr, ai, ci = self._keep
+        inp = _Input(system.n_classes, system.n_methods, system.n_attrs, int(bool(cbo_attrs)),
+                     mc.ctypes.data, ac.ctypes.data, ar.ctypes.data, cr.ctypes.data,
+                     ai.ctypes.data if ai.size else None, ci.ctypes.data if ci.size else None)
+        self._inp = inp
+        self._h = lib.or_build(ctypes.byref(inp), self.threads)
+        if not self._h:
+            raise ValueError("oracle: invalid system or out of memory")
+        self.n_classes = system.n_classes
+        self.n_methods = system.n_methods
+
+    def close(self):
+        if self._h:
+            _load().or_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def class_metrics(self) -> np.ndarray:
+        out = np.zeros(self.n_classes, dtype=CLASS_DTYPE)
+        _load().or_class_metrics(self._h, out.ctypes.data)
+        return out
+
+    def method_metrics(self) -> dict:
+        M = self.n_methods
+        arrs = {k: np.zeros(M, dtype=np.int32) for k in ("fan_in", "fan_out", "own", "q")}
+        _load().or_method_metrics(self._h, arrs["fan_in"].ctypes.data, arrs["fan_out"].ctypes.data,
+                                  arrs["own"].ctypes.data, arrs["q"].ctypes.data)
+        return arrs
+
+    def multigraph(self):
+        lib = _load()
+        u = lib.or_multigraph(self._h, None, None, None)
+        rowptr = np.zeros(self.n_classes + 1, dtype=np.int64)
+        dst = np.zeros(max(u, 1), dtype=np.int32)
+        cnt = np.zeros(max(u, 1), dtype=np.int32)
+        lib.or_multigraph(self._h, rowptr.ctypes.data, dst.ctypes.data, cnt.ctypes.data)
+        return rowptr, dst[:u], cnt[:u]
+
+    def evaluate(self, mask: int = 7, min_improved: int = 2, cand_rowptr=None, cand_dst=None,
+                 rows: tuple[int, int] | None = None, method: int = 1, records: bool = False,
+                 threads: int | None = None) -> EvalResult:
+        """Evaluate candidate rows (all D != cls(m) when cand_rowptr is None).
+        method 0 = recompute (O0), 1 = incremental (O1)."""
+        lib = _load()
+        r0, r1 = rows if rows is not None else (0, self.n_methods)
+        if cand_rowptr is not None:
+            cand_rowptr = np.ascontiguousarray(cand_rowptr, dtype=np.int64)
+            cand_dst = np.ascontiguousarray(cand_dst, dtype=np.int32)
+            n = int(cand_rowptr[r1] - cand_rowptr[r0])
+        else:
+            n = (r1 - r0) * (self.n_classes - 1)
+        rec = np.zeros(n, dtype=RECORD_DTYPE) if records else None
+        res = _Result()
+        crit = _Crit(mask, min_improved)
+        st = lib.or_evaluate(self._h, ctypes.byref(crit),
+                             cand_rowptr.ctypes.data if cand_rowptr is not None else None,
+                             cand_dst.ctypes.data if cand_dst is not None and cand_dst.size else None,
+                             r0, r1, method, threads or self.threads,
+                             rec.ctypes.data if rec is not None and n else None, ctypes.byref(res))
+        kept = np.zeros(res.n_kept, dtype=KEPT_DTYPE)
+        if res.n_kept:
+            ctypes.memmove(kept.ctypes.data, res.kept, res.n_kept * KEPT_DTYPE.itemsize)
+        lib.or_free_kept(res.kept)
+        if st != 0:
+            raise ValueError("oracle: invalid candidate (out of range or equal to the source class)")
+        return EvalResult(int(res.digest), int(res.n_cand), kept, int(res.n_methods_with_kept), rec)
+
+    def evaluate_one(self, m: int, d: int, mask: int = 7, min_improved: int = 2, method: int = 1):
+        rec = np.zeros(1, dtype=RECORD_DTYPE)
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        crit = _Crit(mask, min_improved)
+        rc = _load().or_evaluate_one(self._h, ctypes.byref(crit), m, d, method, rec.ctypes.data,
+                                     ctypes.byref(a), ctypes.byref(b))
+        if rc:
+            raise ValueError("oracle: invalid candidate")
+        return rec[0], int(a.value), int(b.value)
+
+
+def record_hash(m: int, d: int, rec) -> int:
+    arr = np.array([rec], dtype=RECORD_DTYPE) if not isinstance(rec, np.ndarray) else rec.reshape(1)
+    return int(_load().or_record_hash(m, d, arr.ctypes.data))

@@ -1,0 +1,327 @@
+"""Pins of the CPU oracle against things other than itself: the paper's printed
+numbers (Table I), hand-worked values, closed forms of the Sec. II definitions,
+a pure-Python whole-system brute force, and invariants of the move semantics."""
+from __future__ import annotations
+
+import csv
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import brute
+from oracle.tables import count_values, lcom_values
+from paper_1308_4011_b300 import synth
+
+from sysutil import GOLDEN, hand_example, make_system, moved, permute, tiny_random
+
+REC_FIELDS = ("s", "t", "dcbo_src", "dcbo_dst", "n_improved", "n_worsened", "flags")
+
+
+# ---------------------------------------------------------------- Table I
+
+def test_table1_value_counts():
+    """#values = 2m + m(m-1)/2 + 2c(m+1) (Sec. III.B) reproduces Table I's
+    printed column to its 0.1M precision: rounded for 12 rows, truncated for
+    JUnit (1.277M printed as 1.2M)."""
+    rows = [r for r in csv.DictReader(l for l in open(os.path.join(GOLDEN, "table1_values.csv"))
+                                      if not l.startswith("#"))]
+    assert len(rows) == 13
+    rounded = 0
+    for r in rows:
+        v = count_values(int(r["classes"]), int(r["methods"])) / 1e6
+        printed = float(r["values_millions"])
+        ok_round = abs(round(v, 1) - printed) < 1e-9
+        ok_trunc = abs(int(v * 10) / 10 - printed) < 1e-9
+        assert ok_round or ok_trunc, (r["system"], v, printed)
+        rounded += ok_round
+    assert rounded == 12
+    # the paper's worked example: JUnit, 1,200 methods and 231 classes -> "1.2 millions"
+    assert 1.2e6 <= count_values(231, 1200) < 1.3e6
+    assert lcom_values(231, 1200) == 231 * 1201
+
+
+# ---------------------------------------------------------------- hand-worked
+
+def _rec_tuple(r):
+    return tuple(int(r[f]) for f in REC_FIELDS)
+
+
+def test_hand_example_metrics():
+    s, g = hand_example()
+    o = oracle.Oracle(s, cbo_attrs=True, threads=1)
+    cm = o.class_metrics()
+    for f, vals in g["class_metrics_cbo_attrs"].items():
+        assert list(cm[f]) == vals, f
+    mm = o.method_metrics()
+    for f, vals in g["method_metrics"].items():
+        assert list(mm[f]) == vals, f
+    o2 = oracle.Oracle(s, cbo_attrs=False, threads=1)
+    assert list(o2.class_metrics()["cbo"]) == g["cbo_calls_only"]
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_hand_example_moves(method):
+    s, g = hand_example()
+    for mv in g["moves"]:
+        o = oracle.Oracle(s, cbo_attrs=bool(mv["cbo_attrs"]), threads=1)
+        rec, dck, dcb = o.evaluate_one(mv["m"], mv["d"], mask=mv["mask"], min_improved=mv["min_improved"],
+                                       method=method)
+        exp = mv["record"]
+        assert _rec_tuple(rec) == tuple(exp[f] for f in REC_FIELDS), mv
+        assert (dck, dcb) == (mv["d_ck_sum"], mv["d_cbo_sum"]), mv
+
+
+def test_hand_example_brute():
+    s, g = hand_example()
+    for mv in g["moves"]:
+        ev = brute.evaluate(s, mask=mv["mask"], min_improved=mv["min_improved"],
+                            cbo_attrs=bool(mv["cbo_attrs"]), candidates=[(mv["m"], mv["d"])])
+        r = ev[(mv["m"], mv["d"])]
+        assert tuple(r[f] for f in REC_FIELDS) == tuple(mv["record"][f] for f in REC_FIELDS)
+
+
+# ---------------------------------------------------------------- closed forms
+
+def _one_class(acc_rows, n_attrs, extra_classes=0):
+    n = len(acc_rows)
+    return make_system([0] * n, [0] * n_attrs, acc_rows, [[] for _ in range(n)], 1 + extra_classes)
+
+
+@pytest.mark.parametrize("n", [2, 3, 7, 33, 70])
+def test_lcom_all_share_one_attribute(n):
+    """Every method uses one common attribute: Q = n(n-1)/2, P = 0, LCOM = 0."""
+    rng = np.random.default_rng(n)
+    rows = [[0] + [int(v) for v in rng.choice(np.arange(1, 9), size=rng.integers(0, 3), replace=False)]
+            for _ in range(n)]
+    cm = oracle.Oracle(_one_class(rows, 9), threads=1).class_metrics()
+    assert (cm["P"][0], cm["Q"][0], cm["ck"][0]) == (0, n * (n - 1) // 2, 0)
+
+
+@pytest.mark.parametrize("n", [2, 5, 40])
+def test_lcom_disjoint_attributes(n):
+    """n methods on disjoint single attributes: P = n(n-1)/2, Q = 0."""
+    cm = oracle.Oracle(_one_class([[i] for i in range(n)], n), threads=1).class_metrics()
+    assert (cm["P"][0], cm["Q"][0], cm["ck"][0]) == (n * (n - 1) // 2, 0, n * (n - 1) // 2)
+
+
+def test_lcom_single_and_empty_class():
+    s = make_system([0], [0, 1], [[0, 1]], [[]], n_classes=2)
+    cm = oracle.Oracle(s, threads=1).class_metrics()
+    assert (cm["P"][0], cm["Q"][0], cm["ck"][0]) == (0, 0, 0)
+    # class 1 has no method and no attribute
+    assert (cm["n"][1], cm["ck"][1], cm["hs_num"][1], cm["hs_den"][1], cm["cbo"][1]) == (0, 0, 0, 1, 0)
+
+
+@pytest.mark.parametrize("n,a", [(1, 1), (3, 4), (10, 2)])
+def test_lcom_hs_closed_forms(n, a):
+    """All methods use all a attributes: LCOM_HS = 0/(n a); each uses exactly
+    one: (n a - n)/(n a)."""
+    cm = oracle.Oracle(_one_class([list(range(a)) for _ in range(n)], a), threads=1).class_metrics()
+    assert (cm["hs_num"][0], cm["hs_den"][0]) == (0, n * a)
+    cm = oracle.Oracle(_one_class([[i % a] for i in range(n)], a), threads=1).class_metrics()
+    assert (cm["hs_num"][0], cm["hs_den"][0]) == (n * a - n, n * a)
+
+
+def test_lcom_ignores_foreign_attributes():
+    """Sharing counts only attributes owned by the class."""
+    s = make_system([0, 0, 1], [0, 1, 1], [[1], [1], [2]], [[], [], []], n_classes=2)
+    cm = oracle.Oracle(s, threads=1).class_metrics()
+    assert (cm["P"][0], cm["Q"][0], cm["S"][0]) == (1, 0, 0)
+
+
+@pytest.mark.parametrize("k", [0, 1, 5, 12])
+def test_cbo_star(k):
+    """Class 0 calls one method in each of k other classes: CBO = k; the
+    called classes use nothing: CBO = 0."""
+    mc = [0] + list(range(1, k + 1))
+    s = make_system(mc, [], [[] for _ in mc], [list(range(1, k + 1))] + [[] for _ in range(k)], n_classes=k + 1)
+    cm = oracle.Oracle(s, threads=1).class_metrics()
+    assert cm["cbo"][0] == k
+    assert all(cm["cbo"][1:] == 0)
+
+
+def test_cbo_attribute_uses():
+    """Accessing another class's attribute couples only when attribute uses count."""
+    s = make_system([0, 1], [1], [[0], []], [[], []], n_classes=2)
+    assert oracle.Oracle(s, cbo_attrs=True, threads=1).class_metrics()["cbo"][0] == 1
+    assert oracle.Oracle(s, cbo_attrs=False, threads=1).class_metrics()["cbo"][0] == 0
+
+
+def test_cbo_equals_distinct_target_classes_on_tiny():
+    """CBO(C) = |{cls(t)} U {own(a)}| - own class, computed with numpy sets."""
+    s = synth.named("tiny")
+    cm = oracle.Oracle(s).class_metrics()
+    for Y in range(0, s.n_classes, 7):
+        members = np.nonzero(s.method_class == Y)[0]
+        used = set()
+        for x in members:
+            used |= set(s.method_class[s.calls(x)].tolist()) | set(s.attr_class[s.acc(x)].tolist())
+        used.discard(Y)
+        assert cm["cbo"][Y] == len(used)
+
+
+def test_fan_sums_and_pair_identity():
+    s = synth.named("tiny")
+    o = oracle.Oracle(s)
+    mm, cm = o.method_metrics(), o.class_metrics()
+    assert mm["fan_in"].sum() == mm["fan_out"].sum() == s.n_call
+    assert np.array_equal(mm["fan_in"], np.bincount(s.call_idx, minlength=s.n_methods))
+    assert np.all(cm["P"] + cm["Q"] == cm["n"] * (cm["n"] - 1) // 2)
+    # q_x sums to twice the sharing pairs, own_x sums to S
+    q_by_class = np.bincount(s.method_class, weights=mm["q"], minlength=s.n_classes)
+    assert np.array_equal(q_by_class.astype(np.int64), 2 * cm["Q"])
+    own_by_class = np.bincount(s.method_class, weights=mm["own"], minlength=s.n_classes)
+    assert np.array_equal(own_by_class.astype(np.int64), cm["S"])
+
+
+# ---------------------------------------------------------------- brute force
+
+@pytest.mark.parametrize("seed", range(12))
+def test_oracle_matches_brute_force(seed):
+    """O0 and O1 equal the pure-Python whole-system recompute on every
+    candidate of random tiny systems, for several criteria."""
+    s = tiny_random(seed)
+    for cbo_attrs in (True, False):
+        base = brute.class_metrics(s, [int(v) for v in s.method_class], cbo_attrs)
+        o = oracle.Oracle(s, cbo_attrs=cbo_attrs, threads=2)
+        cm = o.class_metrics()
+        for f in oracle.CLASS_FIELDS:
+            assert [int(v) for v in cm[f]] == [b[f] for b in base], f
+        for mask, mi in ((7, 2), (1, 1), (3, 2), (4, 1), (6, 1)):
+            ev = brute.evaluate(s, mask=mask, min_improved=mi, cbo_attrs=cbo_attrs)
+            exp = [tuple(ev[(m, D)][f] for f in REC_FIELDS)
+                   for m in range(s.n_methods) for D in range(s.n_classes) if D != s.method_class[m]]
+            for method in (0, 1):
+                r = o.evaluate(mask=mask, min_improved=mi, method=method, records=True)
+                got = [tuple(int(x) for x in rec) for rec in r.records]
+                assert got == exp, (seed, cbo_attrs, mask, mi, method)
+                assert r.digest == brute.digest(ev)
+                sug = [tuple(int(k[f]) for f in ("m", "d", "n_improved", "d_ck_sum", "d_cbo_sum")) for k in r.kept]
+                assert sug == brute.suggestions(ev)
+
+
+def test_brute_force_exercises_kept_moves():
+    """The random tiny systems above do produce kept moves (the filter is not vacuous)."""
+    kept = 0
+    for seed in range(12):
+        ev = brute.evaluate(tiny_random(seed), mask=3, min_improved=2)
+        kept += sum(1 for r in ev.values() if r["flags"] & 0x8000)
+    assert kept > 10
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_only_source_target_and_caller_classes_change(seed):
+    """Whole-system recompute: a move changes only the source, the target and
+    the classes of the moved method's callers."""
+    s = tiny_random(seed)
+    ev = brute.evaluate(s)
+    for (m, D), r in ev.items():
+        callers = {int(s.method_class[y]) for y in range(s.n_methods) if m in s.calls(y)}
+        assert set(r["changed"]) <= {int(s.method_class[m]), D} | callers
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("seed", range(5))
+def test_incremental_delta_equals_recompute_after_move(seed):
+    """Metrics of the moved system, computed from scratch, equal the base
+    metrics updated by the record (t, s, dCBO) of that move."""
+    s = synth.named("tiny") if seed == 0 else tiny_random(seed + 20)
+    o = oracle.Oracle(s, threads=2)
+    cm = o.class_metrics()
+    mm = o.method_metrics()
+    rng = np.random.default_rng(seed)
+    for _ in range(25 if seed == 0 else 10):
+        m = int(rng.integers(s.n_methods))
+        C = int(s.method_class[m])
+        D = int(rng.integers(s.n_classes - 1))
+        D += D >= C
+        rec, dck, dcb = o.evaluate_one(m, D, method=0)
+        cm2 = oracle.Oracle(moved(s, m, D), threads=2).class_metrics()
+        nC, nD = cm["n"][C], cm["n"][D]
+        assert cm2["n"][C] == nC - 1 and cm2["n"][D] == nD + 1
+        assert cm2["S"][C] == cm["S"][C] - mm["own"][m]
+        assert cm2["Q"][C] == cm["Q"][C] - mm["q"][m]
+        assert cm2["P"][C] == cm["P"][C] - (nC - 1 - mm["q"][m])
+        assert cm2["S"][D] == cm["S"][D] + rec["t"]
+        assert cm2["Q"][D] == cm["Q"][D] + rec["s"]
+        assert cm2["P"][D] == cm["P"][D] + (nD - rec["s"])
+        assert cm2["cbo"][C] == cm["cbo"][C] + rec["dcbo_src"]
+        assert cm2["cbo"][D] == cm["cbo"][D] + rec["dcbo_dst"]
+        assert dck == (cm2["ck"][C] - cm["ck"][C]) + (cm2["ck"][D] - cm["ck"][D])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_move_then_move_back_mirrors(seed):
+    """Moving m back from D to C undoes every change: the back move's deltas
+    are the forward move's, negated and with source/target swapped."""
+    s = tiny_random(seed + 40)
+    o = oracle.Oracle(s, threads=1)
+    rng = np.random.default_rng(seed)
+    for _ in range(10):
+        m = int(rng.integers(s.n_methods))
+        C = int(s.method_class[m])
+        D = int(rng.integers(s.n_classes - 1))
+        D += D >= C
+        fwd, dck, dcb = o.evaluate_one(m, D, mask=7, min_improved=1, method=1)
+        o2 = oracle.Oracle(moved(s, m, D), threads=1)
+        back, dck2, dcb2 = o2.evaluate_one(m, C, mask=7, min_improved=1, method=1)
+        assert back["dcbo_src"] == -fwd["dcbo_dst"] and back["dcbo_dst"] == -fwd["dcbo_src"]
+        assert (dck2, dcb2) == (-dck, -dcb)
+        flip = {0: 0, 1: 2, 2: 1}
+        for k in range(3):  # sign fields: source of the back move = target of the forward move
+            f_src = (int(fwd["flags"]) >> (2 * k)) & 3
+            f_dst = (int(fwd["flags"]) >> (6 + 2 * k)) & 3
+            b_src = (int(back["flags"]) >> (2 * k)) & 3
+            b_dst = (int(back["flags"]) >> (6 + 2 * k)) & 3
+            assert b_src == flip[f_dst] and b_dst == flip[f_src]
+        assert np.array_equal(oracle.Oracle(moved(moved(s, m, D), m, C), threads=1).class_metrics(),
+                              o.class_metrics())
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_relabelling_invariance(seed):
+    s = tiny_random(seed + 60) if seed else synth.named("tiny")
+    p, pc, pm, pa = permute(s, seed)
+    o, op = oracle.Oracle(s), oracle.Oracle(p)
+    cm, cmp_ = o.class_metrics(), op.class_metrics()
+    assert np.array_equal(cmp_[pc], cm)
+    mm, mmp = o.method_metrics(), op.method_metrics()
+    for f in mm:
+        assert np.array_equal(mmp[f][pm], mm[f])
+    k = o.evaluate(mask=3, min_improved=2).kept
+    kp = op.evaluate(mask=3, min_improved=2).kept
+    a = sorted((int(pm[r["m"]]), int(pc[r["d"]]), int(r["n_improved"]), int(r["d_ck_sum"]), int(r["d_cbo_sum"]))
+               for r in k)
+    b = sorted((int(r["m"]), int(r["d"]), int(r["n_improved"]), int(r["d_ck_sum"]), int(r["d_cbo_sum"])) for r in kp)
+    assert a == b
+
+
+@pytest.mark.slow
+def test_o0_equals_o1_on_tiny_workload():
+    """Recompute (O0) and incremental (O1) agree on all 398,000 candidates of
+    the tiny workload (200 classes, 2,000 methods), in two criteria."""
+    s = synth.named("tiny")
+    o = oracle.Oracle(s)
+    for mask, mi in ((7, 2), (3, 2)):
+        r0 = o.evaluate(mask=mask, min_improved=mi, method=0)
+        r1 = o.evaluate(mask=mask, min_improved=mi, method=1)
+        assert r0.n_cand == r1.n_cand == 2000 * 199
+        assert r0.digest == r1.digest
+        assert np.array_equal(r0.kept, r1.kept)
+
+
+def test_o0_equals_o1_sampled_medium_restricted():
+    """O0 and O1 agree on sampled restricted candidates of a mid-size system."""
+    s = synth.generate(1500, 15000, 7500, max_class=400, seed=5, lambda_acc=4, lambda_call=6, p_loc=0.75)
+    rowptr, dst = synth.candidates(s, 8, seed=5)
+    o = oracle.Oracle(s)
+    rng = np.random.default_rng(1)
+    rows = rng.choice(s.n_methods, size=12, replace=False)
+    for m in rows:
+        for D in dst[rowptr[m]:rowptr[m + 1]]:
+            a = o.evaluate_one(int(m), int(D), method=0, mask=7, min_improved=1)
+            b = o.evaluate_one(int(m), int(D), method=1, mask=7, min_improved=1)
+            assert _rec_tuple(a[0]) == _rec_tuple(b[0]) and a[1:] == b[1:]
