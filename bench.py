@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the Move Method metric engine on one B300 (or N replicas).
+
+One step = the whole hot path over one system, through the C ABI:
+  load_system (CSR already in HBM) -> compute_metrics (bitsets, LCOM pair
+  counts, coupling multigraph + CBO, fan-in/out, per-method move data) ->
+  evaluate_moves (full cross product, dense 16-byte records in HBM) ->
+  suggest_moves (fused evaluation + Pareto filter + top-k, read back) -> free.
+
+Workload: the medium synthetic system (5,000 classes, 60,000 methods,
+30,000 attributes, seed 1), 299,940,000 candidate moves per step.
+metric = candidate moves evaluated per second (every record bit-exact with the
+CPU oracle; checked by tests/test_gpu_parity.py and, here, by a digest check
+before timing).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): every rank runs an independent replica of the workload on its
+own GPU (weak scaling, no data-path collective); value = all candidates / max
+rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "candidate moves evaluated/sec (bit-exact vs oracle)"
+UNIT = "candidates/s"
+WORKLOAD = "medium synthetic system: 5,000 classes, 60,000 methods, 30,000 attributes, seed 1; full cross product"
+TOPK = 100
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (clocks + throttle reasons)."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r["power"] > 200.0] or rows
+        reasons = sorted({name for r in rows for name, key in (("hw_slowdown", "hw"),
+                                                                ("hw_thermal_slowdown", "hwt"),
+                                                                ("sw_thermal_slowdown", "swt"),
+                                                                ("sw_power_cap", "swp"))
+                          if r[key].lower() == "active"})
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["smax"] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1308_4011_b300 import mmref, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    seed_offset = 1000 * rank  # independent replica per rank (weak scaling)
+    params = dict(synth.MEDIUM)
+    params["seed"] = params["seed"] + seed_offset
+    system = synth.generate(**params, name="medium")
+    c, M = system.n_classes, system.n_methods
+    n_cand = M * (c - 1)
+    mask, min_imp = mmref.DEFAULT_MASK, mmref.DEFAULT_MIN_IMPROVED
+    stream = torch.cuda.current_stream(dev)
+
+    # inputs resident in HBM
+    dev_arrs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
+                (system.method_class, system.attr_class, system.acc_rowptr, system.acc_idx,
+                 system.call_rowptr, system.call_idx)]
+    records = torch.empty(n_cand * 16, dtype=torch.uint8, device=dev)
+    cls_out = torch.empty(c * 64, dtype=torch.uint8, device=dev)
+    meth_out = torch.empty(M * 16, dtype=torch.uint8, device=dev)
+    topk = np.zeros(TOPK, dtype=mmref.MOVE_DTYPE)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step(timing=None):
+        s = mmref.load_system(c, *dev_arrs, stream=stream)
+        mmref.compute_metrics(s, cls_out, meth_out)
+        if timing is not None:
+            timing[0].record(stream)
+        mmref.evaluate_moves(s, mask, min_imp, records=records)
+        if timing is not None:
+            timing[1].record(stream)
+        out = mmref.suggest_moves(s, TOPK, mask, min_imp, out=topk)
+        s.free()
+        return out
+
+    # correctness gate before timing: digest of every record vs the oracle on rank 0
+    verified = None
+    if rank == 0 and not args.no_verify:
+        import oracle
+        s = mmref.load_system(c, *dev_arrs, stream=stream)
+        mmref.compute_metrics(s, None, None)
+        dig = torch.zeros(1, dtype=torch.int64, device=dev)
+        mmref.evaluate_moves(s, mask, min_imp, digest=dig)
+        top_g, nk_g, _ = mmref.suggest_moves(s, TOPK, mask, min_imp)
+        s.free()
+        o = oracle.Oracle(system)
+        ref = o.evaluate(mask=mask, min_improved=min_imp, method=1)
+        ok_dig = int(dig.cpu().numpy().view(np.uint64)[0]) == ref.digest
+        ok_top = nk_g == ref.n_kept and [tuple(int(x[f]) for f in ("m", "d")) for x in top_g] == \
+            [(int(k["m"]), int(k["d"])) for k in ref.kept[:TOPK]]
+        verified = bool(ok_dig and ok_top)
+        if not verified:
+            print(json.dumps({"error": "GPU result differs from the oracle", "digest_ok": ok_dig,
+                              "topk_ok": ok_top}), file=sys.stderr)
+            sys.exit(3)
+        o.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    step_ms, eval_ms = [], []
+    launches0 = mmref.launch_count()
+    with ClockSampler(local_rank) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t_wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1)  # L2 flush between steps, outside the timed events
+            ev[2].record(stream)
+            step(timing=ev)
+            ev[3].record(stream)
+            torch.cuda.synchronize(dev)
+            step_ms.append(ev[2].elapsed_time(ev[3]))
+            eval_ms.append(ev[0].elapsed_time(ev[1]))
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        t_wall = time.perf_counter() - t_wall0
+    launches = mmref.launch_count() - launches0
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = n_cand * world * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies included
+    e2e = run_e2e(args, system, dev, stream, mask, min_imp)
+
+    peak, peak_kind = _peaks()
+    eval_s = statistics.median(eval_ms) / 1e3
+    alg_bytes = 16 * n_cand
+    achieved = alg_bytes / eval_s / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "eval_dense<records>", "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(eval_s * 1e3, 4)}
+    cpu = cpu_baseline(system, mask, min_imp) if (rank == 0 and not args.no_cpu_baseline) else None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32/int64", "data": "synthetic (seeded generator; no datasets)",
+            "config": {"workload": WORKLOAD, "n_classes": c, "n_methods": M, "n_attrs": system.n_attrs,
+                       "candidates_per_step": n_cand, "criteria": {"metric_mask": mask, "min_improved": min_imp},
+                       "topk": TOPK, "parallelism": f"replicas x{world}",
+                       "l2": "512 MB L2 flush between steps (outside events); each step also writes 4.8 GB"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // max(args.steps, 1) * args.steps,
+            "gpu_launches_per_step": launches / max(args.steps, 1), "clocks": clk.summary(),
+            "eval_ms_median": statistics.median(eval_ms), "step_ms": [round(x, 3) for x in step_ms],
+            "wall_s_timed_region": round(t_wall, 3), "verified_vs_oracle": verified}
+    return line
+
+
+def run_e2e(args, system, dev, stream, mask, min_imp):
+    import torch
+    from paper_1308_4011_b300 import mmref
+
+    c, M = system.n_classes, system.n_methods
+    n_cand = M * (c - 1)
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+              (system.method_class, system.attr_class, system.acc_rowptr, system.acc_idx,
+               system.call_rowptr, system.call_idx)]
+    cls_h = torch.empty(c * 64, dtype=torch.uint8).pin_memory()
+    meth_h = torch.empty(M * 16, dtype=torch.uint8).pin_memory()
+    top_h = torch.empty(TOPK * 24, dtype=torch.uint8).pin_memory()
+    records = torch.empty(n_cand * 16, dtype=torch.uint8, device=dev)
+    h2d = sum(int(p.numel() * p.element_size()) for p in pinned)
+    d2h = c * 64 + M * 16 + TOPK * 24 + 16
+
+    def step():
+        s = mmref.load_system(c, *pinned, stream=stream)
+        mmref.compute_metrics(s, cls_h, meth_h)
+        mmref.evaluate_moves(s, mask, min_imp, records=records)
+        mmref.suggest_moves(s, TOPK, mask, min_imp, out=top_h)
+        s.free()
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    del records
+    return {"value": n_cand * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": dt * 1e3 / args.steps,
+            "note": "host CSR (pinned) -> device, metrics + top-k back to host; records stay in HBM"}
+
+
+def cpu_baseline(system, mask, min_imp, rows=None):
+    """The CPU oracle as it stands (metrics by definition + incremental move
+    evaluation, all host threads) on a bounded sample of the same workload."""
+    import oracle
+    M = system.n_methods
+    rows = rows or M
+    t0 = time.perf_counter()
+    o = oracle.Oracle(system)
+    r = o.evaluate(mask=mask, min_improved=min_imp, method=1, rows=(0, rows))
+    dt = time.perf_counter() - t0
+    o.close()
+    return {"value": r.n_cand / dt, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+            "sample": f"metrics of all classes + candidate rows 0..{rows} of {M} ({r.n_cand} candidates)",
+            "seconds": round(dt, 3)}
+
+
+def run_reference(args, rank, world):
+    """The oracle timed as the reference arm on the host cores (rank 0 only)."""
+    if rank != 0:
+        return None
+    from paper_1308_4011_b300 import synth
+    system = synth.generate(**synth.MEDIUM, name="medium")
+    from paper_1308_4011_b300 import mmref  # noqa: F401  (criteria constants only)
+    mask, min_imp = 3, 2
+    rows = 15000  # a quarter of the methods per step keeps (W + K) steps within a few minutes
+    for _ in range(args.warmup):
+        cpu_baseline(system, mask, min_imp, rows)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = cpu_baseline(system, mask, min_imp, rows)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    value = len(vals) / sum(1.0 / v for v in vals)
+    n_cand_step = rows * (system.n_classes - 1)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64",
+            "data": "synthetic (seeded generator; no datasets)",
+            "config": {"workload": WORKLOAD, "n_classes": system.n_classes, "n_methods": system.n_methods,
+                       "candidates_per_step": n_cand_step, "criteria": {"metric_mask": mask, "min_improved": min_imp},
+                       "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": __import__("oracle").default_threads(),
+                             "kind": "oracle",
+                             "sample": f"metrics of all classes + candidate rows 0..{rows} of {system.n_methods}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-verify", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local_rank = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

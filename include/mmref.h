@@ -1,0 +1,266 @@
+/*
+ * mmref -- Move Method metric engine for NVIDIA B300 (sm_103a).
+ *
+ * C ABI of the library.  It computes, for every class of an object-oriented
+ * system, the modularity metrics of Napoli, Pappalardo and Tramontana, "Using
+ * Modularity Metrics to assist Move Method Refactoring of Large Systems"
+ * (CISIS 2013), and evaluates every candidate Move Method refactoring:
+ *
+ *   fan-in / fan-out ..... Sec. II.A: methods calling m / methods m calls
+ *   CBO .................. Sec. II.B: number of other classes a class uses
+ *                          (calls into them; optionally attribute accesses)
+ *   LCOM (CK) ............ Sec. II.B: method pairs sharing no attribute minus
+ *                          pairs sharing one, reported as max(P - Q, 0); only
+ *                          attributes owned by the class count
+ *   LCOM (HS) ............ Sec. II.B: 1 - mean over methods of the fraction of
+ *                          the class's attributes each uses; exact fraction
+ *                          (n*a - S) / (n*a), or 0/1 when n*a == 0
+ *   move evaluation ...... Sec. III.A (the three rules) and Sec. IV.C (metrics
+ *                          re-evaluated for the source and destination classes
+ *                          of each candidate move), done incrementally
+ *   suggestions .......... Sec. III.A / Sec. IV.A: keep the moves that improve
+ *                          several classes and worsen none, for one selected
+ *                          characteristic or the intersection of several
+ *
+ * Ids are int32: classes [0, n_classes), methods [0, n_methods), attributes
+ * [0, n_attrs) (Sec. IV.C: "classes, methods and attributes have been
+ * represented by a numerical id").  Everything is integer; no floating point
+ * is used anywhere on the path.
+ *
+ * Conventions for every call:
+ *   - Inputs are borrowed: the library copies what it keeps and never frees
+ *     caller memory.  Outputs are caller-owned buffers.
+ *   - A pointer's kind (host or device memory) is given explicitly.  Device
+ *     pointers must be valid on the current CUDA device.
+ *   - Work is ordered on the system's CUDA stream.  A call that writes host
+ *     memory synchronises that stream before it returns; a call that only
+ *     writes device memory may return before the work is done.
+ *   - On error the call returns a non-zero mm_status, leaves the outputs and
+ *     the system unchanged, and sets a thread-local message (mm_last_error).
+ *   - A handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef MMREF_H
+#define MMREF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MMREF_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define MMREF_API __attribute__((visibility("default")))
+#else
+#define MMREF_API
+#endif
+
+typedef enum {
+  MM_OK = 0,
+  MM_EINVAL = 1,     /* malformed input (ids out of range, unsorted rows, ...) */
+  MM_ENOMEM = 2,     /* device or host allocation failed */
+  MM_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+  MM_ENOTFOUND = 4,  /* edit removes an edge that does not exist */
+  MM_EEXIST = 5,     /* edit adds an edge that already exists */
+  MM_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  MM_EBUDGET = 7     /* admission refused: memory budget exceeded */
+} mm_status;
+
+enum { MM_PTR_HOST = 0, MM_PTR_DEVICE = 1 };
+
+/* metric selection bits (Sec. IV.A: the developer selects the characteristic
+ * to improve, or asks for all of them) */
+enum { MM_LCOM_CK = 1, MM_LCOM_HS = 2, MM_CBO = 4 };
+
+typedef struct mm_system mm_system; /* opaque; owns all device memory it allocates */
+
+/*
+ * A system in CSR form: the paper's "cls" array (owner class of each method
+ * and attribute) and "dpnd" array (per method, the invoked methods and the
+ * accessed attributes), Sec. IV.C.
+ *   method_class[n_methods]   owner class of each method
+ *   attr_class[n_attrs]       owner class of each attribute
+ *   acc_rowptr[n_methods+1]   int64, acc_rowptr[0] = 0, non-decreasing,
+ *                             acc_rowptr[n_methods] = n_acc
+ *   acc_idx[n_acc]            accessed attribute ids, strictly increasing
+ *                             within each method's row
+ *   call_rowptr/call_idx      called method ids, same rules, and no method
+ *                             calls itself
+ *   cbo_attrs                 1: an access to another class's attribute is a
+ *                             use for CBO (default); 0: only calls count
+ */
+typedef struct {
+  int32_t n_classes, n_methods, n_attrs;
+  int32_t ptr_kind; /* MM_PTR_HOST or MM_PTR_DEVICE, for all six arrays */
+  int64_t n_acc, n_call;
+  const int32_t *method_class;
+  const int32_t *attr_class;
+  const int64_t *acc_rowptr;
+  const int32_t *acc_idx;
+  const int64_t *call_rowptr;
+  const int32_t *call_idx;
+  int32_t cbo_attrs;
+  int32_t reserved;
+} mm_system_desc;
+
+/* Per-class metrics (64 bytes).  P = pairs of methods sharing no attribute of
+ * the class, Q = pairs sharing at least one (P + Q = n(n-1)/2), S = sum over
+ * methods of the number of the class's attributes they access. */
+typedef struct {
+  int32_t n_methods, n_attrs;
+  int64_t P, Q, S;
+  int64_t lcom_ck;          /* max(P - Q, 0) */
+  int64_t hs_num, hs_den;   /* LCOM_HS = hs_num / hs_den */
+  int32_t cbo, reserved;
+} mm_class_metrics;
+
+/* Per-method metrics.  own = accesses to the own class's attributes,
+ * q = methods of the own class sharing an attribute of the class with it. */
+typedef struct {
+  int32_t fan_in, fan_out, own, q;
+} mm_method_metrics;
+
+/*
+ * Evaluation record of one candidate move (method m from class C to class D),
+ * 16 bytes:
+ *   s           methods of D sharing an attribute of D with m
+ *   t           m's accesses to attributes of D (saturates at 65535)
+ *   dcbo_src    CBO(C) after - before (saturates to int16)
+ *   dcbo_dst    CBO(D) after - before (saturates to int16)
+ *   n_improved  affected classes with no selected metric higher and one lower
+ *   n_worsened  affected classes with a selected metric higher
+ *               (affected = C, D and the classes of m's callers; both
+ *               counts saturate at 65535)
+ *   flags       2-bit signs, 0 = unchanged, 1 = lower, 2 = higher:
+ *               bits 0-1 LCOM_CK(C), 2-3 LCOM_HS(C), 4-5 CBO(C),
+ *               bits 6-7 LCOM_CK(D), 8-9 LCOM_HS(D), 10-11 CBO(D);
+ *               bit 15 = kept (n_worsened == 0 and n_improved >= min_improved)
+ */
+typedef struct {
+  int32_t s;
+  uint16_t t;
+  int16_t dcbo_src, dcbo_dst;
+  uint16_t n_improved, n_worsened, flags;
+} mm_move_eval;
+
+/* Suggestion criteria (Sec. III.A, Sec. IV.A).  A move is kept when no
+ * affected class gets worse in a selected metric and at least min_improved
+ * classes get better. */
+typedef struct {
+  uint32_t metric_mask; /* MM_LCOM_CK | MM_LCOM_HS | MM_CBO subset, non-empty */
+  int32_t min_improved; /* >= 1 */
+} mm_criteria;
+
+/* One suggested move.  Suggestions are ordered by n_improved (descending),
+ * then d_lcom_ck_sum = dLCOM_CK(C) + dLCOM_CK(D) (ascending), then
+ * d_cbo_sum = dCBO(C) + dCBO(D) (ascending, not saturated), then m, then d
+ * (ascending). */
+typedef struct {
+  int32_t m, d;
+  int32_t n_improved;
+  int32_t d_lcom_ck_sum;
+  int32_t d_cbo_sum;
+  int32_t reserved;
+} mm_move;
+
+/*
+ * Candidate moves.  rowptr == NULL: the full cross product, every method to
+ * every class other than its own, n_methods * (n_classes - 1) candidates; the
+ * candidate of (m, D) has index m*(n_classes-1) + D - (D > cls(m)).
+ * Otherwise a CSR over methods: rowptr[n_methods+1] (int64, rowptr[0] = 0,
+ * non-decreasing, rowptr[n_methods] = n_cand) and dst[n_cand] destination
+ * classes, each in range and different from the method's class; index i is
+ * the position in dst.
+ */
+typedef struct {
+  const int64_t *rowptr;
+  const int32_t *dst;
+  int64_t n_cand;
+  int32_t ptr_kind;
+  int32_t reserved;
+} mm_candidates;
+
+typedef struct {
+  int32_t n_classes, n_methods, n_attrs, cbo_attrs;
+  int64_t n_acc, n_call;
+  int64_t n_class_edges;   /* distinct (C, E) class uses, E != C, after compute */
+  int64_t device_bytes;    /* device memory held by the system */
+} mm_system_info;
+
+/*
+ * Load a system (Sec. IV.C: the cls/dpnd arrays are copied to the GPU).
+ * Copies the desc's arrays to device memory on `cuda_stream` (a cudaStream_t,
+ * NULL = default stream) and validates them on the device.  The stream is
+ * kept for every later call on the handle.  Errors: MM_EINVAL for any rule of
+ * mm_system_desc broken (the message names the first rule found), MM_ENOMEM,
+ * MM_ECUDA.  Synchronises the stream (validation result).
+ */
+MMREF_API mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_system **out);
+
+/* Use another stream for the later calls on this handle. */
+MMREF_API mm_status mm_set_stream(mm_system *sys, void *cuda_stream);
+
+/*
+ * Compute every class and method metric (Sec. II.A, II.B) and the per-method
+ * data that move evaluation needs.  Builds, on the device: the class->method
+ * and class->attribute lists, the callers of each method, per-class attribute
+ * bitsets, the LCOM method-pair counts, the class-use multigraph (segmented
+ * sort + unique) with CBO and class adjacency bitsets, and fan-in/out.
+ * out_c[n_classes] and out_m[n_methods] are optional (NULL = keep on device);
+ * out_kind says where they live.
+ */
+MMREF_API mm_status mm_compute_metrics(mm_system *sys, mm_class_metrics *out_c, mm_method_metrics *out_m,
+                             int32_t out_kind);
+
+/*
+ * Evaluate candidate moves incrementally (Sec. III.A, Sec. IV.C) against the
+ * metrics of the last mm_compute_metrics.  cands == NULL means the full cross
+ * product.  records[n_cand] (nullable) receives one mm_move_eval per
+ * candidate in candidate order.  digest (nullable, one uint64) receives the
+ * sum modulo 2^64, over all candidates, of
+ *   h = sm(key ^ sm(lo ^ sm(hi))),  key = (uint64)m << 32 | D,
+ * where lo/hi are the record's first/last 8 bytes (little endian) and sm is
+ * the SplitMix64 output function (Steele, Lea, Flood 2014).  records and
+ * digest live in out_kind memory.  Errors: MM_EINVAL (no metrics computed,
+ * bad criteria, a candidate out of range or equal to the method's class),
+ * MM_ENOMEM, MM_ECUDA.
+ */
+MMREF_API mm_status mm_evaluate_moves(mm_system *sys, const mm_criteria *crit, const mm_candidates *cands,
+                            mm_move_eval *records, uint64_t *digest, int32_t out_kind);
+
+/*
+ * Suggest moves (Sec. III.A, IV.A): evaluate the candidates, keep those that
+ * pass the criteria (warp-ballot compaction), sort the kept moves in the
+ * order given at mm_move and write the first min(k, n_kept) to out_topk
+ * (out_kind memory; may be NULL when k == 0).  *n_kept and
+ * *n_methods_with_kept (host, nullable) receive the number of kept moves and
+ * of distinct methods among them.  Synchronises the stream.
+ */
+MMREF_API mm_status mm_suggest_moves(mm_system *sys, const mm_criteria *crit, const mm_candidates *cands,
+                           int32_t k, mm_move *out_topk, int32_t out_kind, int64_t *n_kept,
+                           int64_t *n_methods_with_kept);
+
+/* Sizes and device memory of a loaded system (host struct). */
+MMREF_API mm_status mm_system_info_get(mm_system *sys, mm_system_info *info);
+
+/* Free the system and all device memory it owns (stream-ordered). */
+MMREF_API void mm_free_system(mm_system *sys);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+MMREF_API const char *mm_last_error(void);
+
+MMREF_API const char *mm_status_string(mm_status st);
+
+MMREF_API int32_t mm_abi_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads, all systems); for accounting in benchmarks. */
+MMREF_API int64_t mm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMREF_H */

@@ -1,0 +1,352 @@
+// C ABI entry points (include/mmref.h): argument checks, allocation of a
+// system's device memory, stream handling and error reporting.  Every step of
+// the path itself runs in the kernels of mm_system.cu, mm_metrics.cu and
+// mm_moves.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "mm_internal.cuh"
+
+static thread_local std::string g_last_error;
+
+void mm_set_error(const std::string &msg) { g_last_error = msg; }
+
+#include <atomic>
+static std::atomic<long long> g_launches{0};
+void mm_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+template <class F>
+mm_status guarded(F &&f) {
+  try {
+    f();
+    g_last_error.clear();
+    return MM_OK;
+  } catch (const MmError &e) {
+    g_last_error = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return MM_ENOMEM;
+  } catch (...) {
+    g_last_error = "unexpected exception";
+    return MM_ECUDA;
+  }
+}
+
+void use_device(mm_system *s) {
+  int cur = -1;
+  MM_CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != s->device) MM_CUDA_TRY(cudaSetDevice(s->device));
+}
+
+void keep_pool_memory(int device) {
+  static bool done[64] = {false};
+  if (device < 0 || device >= 64 || done[device]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[device] = true;
+}
+
+template <class T>
+void upload(T *dst, const T *src, int64_t n, int32_t kind, cudaStream_t st) {
+  if (n <= 0) return;
+  MM_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(T) * (size_t)n,
+                              kind == MM_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+}
+
+void allocate_compute_buffers(mm_system *s) {
+  DevArena &a = s->arena;
+  const int64_t c = s->c, M = s->M, nu = s->n_call + s->n_acc;
+  s->bits_off = a.get<int64_t>(c + 1);
+  s->tile_off = a.get<int64_t>(c + 1);
+  s->bits = a.get<uint32_t>(s->summary.bits_words);
+  s->cls_P = a.get<int64_t>(c);
+  s->cls_Q = a.get<int64_t>(c);
+  s->cls_S = a.get<int64_t>(c);
+  s->cls_cbo = a.get<int32_t>(c);
+  s->own = a.get<int32_t>(M);
+  s->q = a.get<int32_t>(M);
+  s->mg_rowptr = a.get<int64_t>(c + 1);
+  s->mg_dst = a.get<int32_t>(nu);
+  s->mg_cnt = a.get<int32_t>(nu);
+  s->mg_count = a.get<int64_t>(2);
+  s->adj_words = (c + 31) / 32;
+  s->out_adj = a.get<uint32_t>(s->adj_words * c);
+  s->in_adj = a.get<uint32_t>(s->adj_words * c);
+  s->hdr = a.get<MoveHdr>(M);
+  s->l_list = a.get<int4>(nu);
+  s->l_s = a.get<int32_t>(nu);
+  s->l_x = a.get<int32_t>(nu);
+  s->r_list = a.get<int4>(s->n_call);
+}
+
+std::string describe(uint32_t err) {
+  if (err & VE_METHOD_CLASS) return "method_class: class id out of range";
+  if (err & VE_ATTR_CLASS) return "attr_class: class id out of range";
+  if (err & VE_ACC_ROWPTR) return "acc_rowptr: must start at 0, be non-decreasing and end at n_acc";
+  if (err & VE_ACC_IDX_RANGE) return "acc_idx: attribute id out of range";
+  if (err & VE_ACC_IDX_ORDER) return "acc_idx: each row must be strictly increasing (sorted, no duplicates)";
+  if (err & VE_CALL_ROWPTR) return "call_rowptr: must start at 0, be non-decreasing and end at n_call";
+  if (err & VE_CALL_IDX_RANGE) return "call_idx: method id out of range";
+  if (err & VE_CALL_IDX_ORDER) return "call_idx: each row must be strictly increasing (sorted, no duplicates)";
+  if (err & VE_SELF_CALL) return "call_idx: a method calls itself";
+  return "invalid system";
+}
+
+__global__ void export_class_kernel(const int32_t *cls_n, const int32_t *cls_a, const int64_t *P, const int64_t *Q,
+                                    const int64_t *S, const int32_t *cbo, int32_t c, mm_class_metrics *out) {
+  int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= c) return;
+  mm_class_metrics r;
+  r.n_methods = cls_n[C];
+  r.n_attrs = cls_a[C];
+  r.P = P[C];
+  r.Q = Q[C];
+  r.S = S[C];
+  r.lcom_ck = r.P > r.Q ? r.P - r.Q : 0;
+  int64_t na = (int64_t)r.n_methods * r.n_attrs;
+  r.hs_num = na == 0 ? 0 : na - r.S;
+  r.hs_den = na == 0 ? 1 : na;
+  r.cbo = cbo[C];
+  r.reserved = 0;
+  out[C] = r;
+}
+
+__global__ void export_method_kernel(const int32_t *fan_in, const int64_t *call_rowptr, const int32_t *own,
+                                     const int32_t *q, int32_t M, mm_method_metrics *out) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  mm_method_metrics r;
+  r.fan_in = fan_in[x];
+  r.fan_out = (int32_t)(call_rowptr[x + 1] - call_rowptr[x]);
+  r.own = own[x];
+  r.q = q[x];
+  out[x] = r;
+}
+
+}  // namespace
+
+void export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *out_m, int32_t kind) {
+  cudaStream_t st = s->stream;
+  if (out_c && s->c > 0) {
+    mm_class_metrics *d = kind == MM_PTR_DEVICE
+                              ? out_c
+                              : static_cast<mm_class_metrics *>(s->stage_ws.need(sizeof(mm_class_metrics) * s->c, st));
+    export_class_kernel<<<(unsigned)ceil_div(s->c, 256), 256, 0, st>>>(s->cls_n, s->cls_a, s->cls_P, s->cls_Q,
+                                                                      s->cls_S, s->cls_cbo, s->c, d);
+    MM_LAUNCH_CHECK();
+    if (kind == MM_PTR_HOST)
+      MM_CUDA_TRY(cudaMemcpyAsync(out_c, d, sizeof(mm_class_metrics) * s->c, cudaMemcpyDeviceToHost, st));
+    if (kind == MM_PTR_HOST) MM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  if (out_m && s->M > 0) {
+    mm_method_metrics *d =
+        kind == MM_PTR_DEVICE ? out_m
+                              : static_cast<mm_method_metrics *>(s->stage_ws.need(sizeof(mm_method_metrics) * s->M, st));
+    export_method_kernel<<<(unsigned)ceil_div(s->M, 256), 256, 0, st>>>(s->fan_in, s->call_rowptr, s->own, s->q,
+                                                                       s->M, d);
+    MM_LAUNCH_CHECK();
+    if (kind == MM_PTR_HOST) {
+      MM_CUDA_TRY(cudaMemcpyAsync(out_m, d, sizeof(mm_method_metrics) * s->M, cudaMemcpyDeviceToHost, st));
+      MM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+  }
+}
+
+extern "C" {
+
+mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_system **out) {
+  if (out) *out = nullptr;
+  mm_system *s = nullptr;
+  mm_status st = guarded([&] {
+    if (!desc || !out) throw MmError{MM_EINVAL, "load_system: desc and out must be non-NULL"};
+    if (desc->n_classes < 1) throw MmError{MM_EINVAL, "load_system: n_classes must be >= 1"};
+    if (desc->n_methods < 0 || desc->n_attrs < 0 || desc->n_acc < 0 || desc->n_call < 0)
+      throw MmError{MM_EINVAL, "load_system: negative size"};
+    if (desc->ptr_kind != MM_PTR_HOST && desc->ptr_kind != MM_PTR_DEVICE)
+      throw MmError{MM_EINVAL, "load_system: bad ptr_kind"};
+    if (desc->n_methods == 0 && (desc->n_acc != 0 || desc->n_call != 0))
+      throw MmError{MM_EINVAL, "load_system: accesses or calls without methods"};
+    if (desc->n_call + desc->n_acc >= (int64_t)0x7fffffff)
+      throw MmError{MM_EINVAL, "load_system: more than 2^31-1 calls plus accesses"};
+    if (desc->n_methods > 0 && (!desc->method_class || !desc->acc_rowptr || !desc->call_rowptr))
+      throw MmError{MM_EINVAL, "load_system: NULL method array"};
+    if (desc->n_attrs > 0 && !desc->attr_class) throw MmError{MM_EINVAL, "load_system: NULL attr_class"};
+    if ((desc->n_acc > 0 && !desc->acc_idx) || (desc->n_call > 0 && !desc->call_idx))
+      throw MmError{MM_EINVAL, "load_system: NULL index array"};
+    s = new mm_system();
+    MM_CUDA_TRY(cudaGetDevice(&s->device));
+    keep_pool_memory(s->device);
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    s->arena.stream = s->stream;
+    s->c = desc->n_classes;
+    s->M = desc->n_methods;
+    s->A = desc->n_attrs;
+    s->n_acc = desc->n_acc;
+    s->n_call = desc->n_call;
+    s->cbo_attrs = desc->cbo_attrs ? 1 : 0;
+    DevArena &a = s->arena;
+    const int64_t c = s->c, M = s->M, A = s->A;
+    s->method_class = a.get<int32_t>(M);
+    s->attr_class = a.get<int32_t>(A);
+    s->acc_rowptr = a.get<int64_t>(M + 1);
+    s->acc_idx = a.get<int32_t>(s->n_acc);
+    s->call_rowptr = a.get<int64_t>(M + 1);
+    s->call_idx = a.get<int32_t>(s->n_call);
+    s->cls_n = a.get<int32_t>(c);
+    s->cls_a = a.get<int32_t>(c);
+    s->cm_rowptr = a.get<int64_t>(c + 1);
+    s->cm_list = a.get<int32_t>(M);
+    s->method_local = a.get<int32_t>(M);
+    s->ca_rowptr = a.get<int64_t>(c + 1);
+    s->attr_local = a.get<int32_t>(A);
+    s->caller_rowptr = a.get<int64_t>(M + 1);
+    s->caller_idx = a.get<int32_t>(s->n_call);
+    s->fan_in = a.get<int32_t>(M);
+    s->d_err = a.get<uint32_t>(4);
+    s->d_u64 = a.get<unsigned long long>(32);
+    cudaStream_t stv = s->stream;
+    upload(s->method_class, desc->method_class, M, desc->ptr_kind, stv);
+    upload(s->attr_class, desc->attr_class, A, desc->ptr_kind, stv);
+    if (M >= 0 && desc->acc_rowptr) upload(s->acc_rowptr, desc->acc_rowptr, M + 1, desc->ptr_kind, stv);
+    upload(s->acc_idx, desc->acc_idx, s->n_acc, desc->ptr_kind, stv);
+    if (desc->call_rowptr) upload(s->call_rowptr, desc->call_rowptr, M + 1, desc->ptr_kind, stv);
+    upload(s->call_idx, desc->call_idx, s->n_call, desc->ptr_kind, stv);
+    if (M == 0) {
+      MM_CUDA_TRY(cudaMemsetAsync(s->acc_rowptr, 0, sizeof(int64_t), stv));
+      MM_CUDA_TRY(cudaMemsetAsync(s->call_rowptr, 0, sizeof(int64_t), stv));
+    }
+    load_validate_and_summarise(s);
+    if (s->summary.err) throw MmError{MM_EINVAL, "load_system: " + describe(s->summary.err)};
+    allocate_compute_buffers(s);
+    *out = s;
+  });
+  if (st != MM_OK && s) {
+    s->arena.release();
+    s->sort_ws.release(s->stream);
+    s->eval_ws.release(s->stream);
+    s->stage_ws.release(s->stream);
+    cudaStreamSynchronize(s->stream);
+    delete s;
+    if (out) *out = nullptr;
+  }
+  return st;
+}
+
+mm_status mm_set_stream(mm_system *s, void *cuda_stream) {
+  return guarded([&] {
+    if (!s) throw MmError{MM_EINVAL, "set_stream: NULL system"};
+    use_device(s);
+    // order the new stream after everything queued on the old one
+    cudaStream_t ns = static_cast<cudaStream_t>(cuda_stream);
+    if (ns != s->stream) {
+      cudaEvent_t ev;
+      MM_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      MM_CUDA_TRY(cudaEventRecord(ev, s->stream));
+      MM_CUDA_TRY(cudaStreamWaitEvent(ns, ev, 0));
+      MM_CUDA_TRY(cudaEventDestroy(ev));
+    }
+    s->stream = ns;
+    s->arena.stream = ns;
+  });
+}
+
+mm_status mm_compute_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *out_m, int32_t out_kind) {
+  return guarded([&] {
+    if (!s) throw MmError{MM_EINVAL, "compute_metrics: NULL system"};
+    if ((out_c || out_m) && out_kind != MM_PTR_HOST && out_kind != MM_PTR_DEVICE)
+      throw MmError{MM_EINVAL, "compute_metrics: bad out_kind"};
+    use_device(s);
+    build_structures(s);
+    build_metrics(s);
+    build_move_precompute(s);
+    s->metrics_ready = true;
+    export_metrics(s, out_c, out_m, out_kind);
+  });
+}
+
+mm_status mm_evaluate_moves(mm_system *s, const mm_criteria *crit, const mm_candidates *cands,
+                            mm_move_eval *records, uint64_t *digest, int32_t out_kind) {
+  return guarded([&] {
+    if (!s || !crit) throw MmError{MM_EINVAL, "evaluate_moves: NULL system or criteria"};
+    if (!s->metrics_ready) throw MmError{MM_EINVAL, "evaluate_moves: call mm_compute_metrics first"};
+    use_device(s);
+    evaluate_moves(s, *crit, cands, records, digest, out_kind);
+  });
+}
+
+mm_status mm_suggest_moves(mm_system *s, const mm_criteria *crit, const mm_candidates *cands, int32_t k,
+                           mm_move *out_topk, int32_t out_kind, int64_t *n_kept, int64_t *n_methods_with_kept) {
+  return guarded([&] {
+    if (!s || !crit) throw MmError{MM_EINVAL, "suggest_moves: NULL system or criteria"};
+    if (!s->metrics_ready) throw MmError{MM_EINVAL, "suggest_moves: call mm_compute_metrics first"};
+    use_device(s);
+    suggest_moves(s, *crit, cands, k, out_topk, out_kind, n_kept, n_methods_with_kept);
+  });
+}
+
+mm_status mm_system_info_get(mm_system *s, mm_system_info *info) {
+  return guarded([&] {
+    if (!s || !info) throw MmError{MM_EINVAL, "system_info: NULL argument"};
+    use_device(s);
+    info->n_classes = s->c;
+    info->n_methods = s->M;
+    info->n_attrs = s->A;
+    info->cbo_attrs = s->cbo_attrs;
+    info->n_acc = s->n_acc;
+    info->n_call = s->n_call;
+    info->n_class_edges = -1;
+    if (s->metrics_ready) {
+      int64_t v = 0;
+      MM_CUDA_TRY(cudaMemcpyAsync(&v, s->mg_count, sizeof(int64_t), cudaMemcpyDeviceToHost, s->stream));
+      MM_CUDA_TRY(cudaStreamSynchronize(s->stream));
+      info->n_class_edges = v;
+    }
+    info->device_bytes = s->arena.bytes + (int64_t)(s->sort_ws.cap + s->eval_ws.cap + s->stage_ws.cap);
+  });
+}
+
+void mm_free_system(mm_system *s) {
+  if (!s) return;
+  int cur = -1;
+  const int dev = s->device;
+  cudaGetDevice(&cur);
+  if (cur != dev) cudaSetDevice(dev);
+  s->arena.release();
+  s->sort_ws.release(s->stream);
+  s->eval_ws.release(s->stream);
+  s->stage_ws.release(s->stream);
+  delete s;
+  if (cur >= 0 && cur != dev) cudaSetDevice(cur);
+}
+
+const char *mm_last_error(void) { return g_last_error.c_str(); }
+
+const char *mm_status_string(mm_status st) {
+  switch (st) {
+    case MM_OK: return "ok";
+    case MM_EINVAL: return "invalid argument";
+    case MM_ENOMEM: return "out of memory";
+    case MM_ECUDA: return "CUDA error";
+    case MM_ENOTFOUND: return "not found";
+    case MM_EEXIST: return "already exists";
+    case MM_ETIMEOUT: return "device wait timed out";
+    case MM_EBUDGET: return "memory budget exceeded";
+  }
+  return "unknown status";
+}
+
+int32_t mm_abi_version(void) { return MMREF_ABI_VERSION; }
+
+int64_t mm_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Internal declarations of the mmref CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "mmref.h"
+
+// ---------------------------------------------------------------- errors
+
+void mm_set_error(const std::string &msg);
+
+struct MmError {
+  mm_status st;
+  std::string msg;
+};
+
+#define MM_CUDA_TRY(expr)                                                                    \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      throw MmError{e_ == cudaErrorMemoryAllocation ? MM_ENOMEM : MM_ECUDA,                  \
+                    std::string(#expr) + ": " + cudaGetErrorString(e_)};                     \
+  } while (0)
+
+// Every kernel launch site is followed by MM_LAUNCH_CHECK(), which also counts
+// the launch (mm_launch_count in the C ABI).
+void mm_count_launch();
+#define MM_LAUNCH_CHECK()      \
+  do {                         \
+    mm_count_launch();         \
+    MM_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
+
+static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static inline int bits_for(uint64_t max_value) {  // bits needed to hold [0, max_value]
+  int b = 0;
+  while (b < 64 && (max_value >> b) != 0) ++b;
+  return b;
+}
+
+// ---------------------------------------------------------------- device memory
+
+// Stream-ordered allocations owned by a system (freed with the system).
+struct DevArena {
+  cudaStream_t stream = nullptr;
+  std::vector<void *> ptrs;
+  int64_t bytes = 0;
+  void *alloc(size_t n);
+  void release();
+  template <class T>
+  T *get(int64_t count) {
+    return static_cast<T *>(alloc(sizeof(T) * (size_t)(count > 0 ? count : 1)));
+  }
+};
+
+// A grow-only scratch buffer.
+struct Scratch {
+  void *ptr = nullptr;
+  size_t cap = 0;
+  void *need(size_t n, cudaStream_t st);
+  void release(cudaStream_t st);
+};
+
+// Error word written by validation kernels (bit flags).
+enum : uint32_t {
+  VE_METHOD_CLASS = 1u << 0,
+  VE_ATTR_CLASS = 1u << 1,
+  VE_ACC_ROWPTR = 1u << 2,
+  VE_ACC_IDX_RANGE = 1u << 3,
+  VE_ACC_IDX_ORDER = 1u << 4,
+  VE_CALL_ROWPTR = 1u << 5,
+  VE_CALL_IDX_RANGE = 1u << 6,
+  VE_CALL_IDX_ORDER = 1u << 7,
+  VE_SELF_CALL = 1u << 8,
+  VE_CAND_ROWPTR = 1u << 9,
+  VE_CAND_RANGE = 1u << 10,
+  VE_CAND_SELF = 1u << 11
+};
+
+// Summary of a loaded system computed on the device at load time.
+struct LoadSummary {
+  uint32_t err;
+  int32_t max_class_methods;
+  int64_t bits_words;   // sum over classes of n_C * ceil(a_C / 32)
+  int64_t lcom_tiles;   // sum over classes of T_C (T_C + 1) / 2, T_C = ceil(n_C / 32)
+};
+
+// Per-method header for move evaluation (3 x int4 = 48 bytes):
+//   w0 = {C, l_off, l_len, r_off}
+//   w1 = {r_len, out_self, in_self, l_all}
+//   w2 = {src_signs (2-bit CK | 2-bit HS << 2), dck_src, 0, 0}
+// l list entries: int4 {E, out, cnt(C,E), t} plus s in a parallel int32 array.
+// r list entries: int4 {X, in, cnt(X,C), 0}.
+struct MoveHdr {
+  int4 w0, w1, w2;
+};
+
+struct mm_system {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int32_t c = 0, M = 0, A = 0, cbo_attrs = 1;
+  int64_t n_acc = 0, n_call = 0;
+  LoadSummary summary{};
+  bool metrics_ready = false;
+  int64_t n_class_edges = -1;
+
+  DevArena arena;      // everything sized at load time
+  Scratch sort_ws;     // radix-sort / scan scratch
+  Scratch eval_ws;     // evaluate/suggest scratch (kept lists, staging)
+  Scratch stage_ws;    // host-output staging
+
+  // inputs
+  int32_t *method_class, *attr_class, *acc_idx, *call_idx;
+  int64_t *acc_rowptr, *call_rowptr;
+
+  // class structures
+  int32_t *cls_n, *cls_a;          // methods / attributes per class
+  int64_t *cm_rowptr;              // class -> methods (ascending ids)
+  int32_t *cm_list;
+  int32_t *method_local;           // rank of a method inside its class
+  int64_t *ca_rowptr;              // class -> attributes (offsets only)
+  int32_t *attr_local;             // rank of an attribute inside its class
+  int64_t *caller_rowptr;          // callers of each method (transpose of calls)
+  int32_t *caller_idx;
+  int32_t *fan_in;
+
+  // attribute bitsets: class C, method rank i -> bits[bits_off[C] + i * W_C]
+  int64_t *bits_off;
+  uint32_t *bits;
+  int64_t *tile_off;               // LCOM pair-tile offsets per class
+
+  // metrics
+  int64_t *cls_P, *cls_Q, *cls_S;
+  int32_t *cls_cbo;
+  int32_t *own, *q;
+
+  // class-use multigraph (E != Y) and adjacency bitsets (row-major, adj_words per row)
+  int64_t *mg_rowptr;
+  int32_t *mg_dst, *mg_cnt;
+  int64_t *mg_count;               // device scalar: number of distinct (Y, E)
+  uint32_t *out_adj, *in_adj;
+  int64_t adj_words;
+
+  // move precompute
+  MoveHdr *hdr;
+  int4 *l_list;
+  int32_t *l_s;
+  int4 *r_list;
+  int32_t *l_x;                    // method of each L entry (capacity n_acc + n_call)
+
+  // device scalars
+  uint32_t *d_err;
+  unsigned long long *d_u64;       // [0] digest, [1] kept count, [2] methods with kept
+};
+
+// ---------------------------------------------------------------- primitives (mm_prims.cu)
+
+// Exclusive scan of n int64 values (in and out may alias); writes the total to
+// *total_dev when non-null.  Uses sys->sort_ws-independent scratch `ws`.
+void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, Scratch &ws,
+                        cudaStream_t st);
+void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch &ws, cudaStream_t st);
+
+// Stable LSD radix sort of n keys (and optional uint32 values) on bits [0, nbits).
+// The result is left in keys/vals; alt buffers are scratch of the same size.
+void radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                    int nbits, Scratch &ws, cudaStream_t st);
+void radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                    int nbits, Scratch &ws, cudaStream_t st);
+
+// ---------------------------------------------------------------- pipeline stages
+
+void load_validate_and_summarise(mm_system *s);     // mm_system.cu
+void build_structures(mm_system *s);                // mm_system.cu
+void build_metrics(mm_system *s);                   // mm_metrics.cu
+void build_move_precompute(mm_system *s);           // mm_moves.cu
+void export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *out_m, int32_t kind);
+void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *cands,
+                    mm_move_eval *records, uint64_t *digest, int32_t kind);
+void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *cands, int32_t k,
+                   mm_move *out, int32_t kind, int64_t *n_kept, int64_t *n_mk);

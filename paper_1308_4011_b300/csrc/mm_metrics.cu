@@ -1,0 +1,269 @@
+// Class metrics (Sec. II.B) on the device:
+//   * per-class attribute bitsets: row i of class C holds the attributes of C
+//     that its i-th method accesses (only attributes owned by C count);
+//   * LCOM method-pair kernel: for every unordered pair of methods of a class,
+//     "share" = any bit of (row_i AND row_j); Q = sharing pairs, P = n(n-1)/2 - Q,
+//     q_x = partners sharing with x; pairs are tiled 32 x 32 per warp, so a
+//     2,000-method class is spread over 2,016 warps and a singleton costs one;
+//   * coupling: every use edge (class of x, class it uses) as a 64-bit key,
+//     segmented by source class with the radix sort, run-length encoded into
+//     the class-use multigraph cnt[Y][E]; CBO(Y) = number of E != Y with
+//     cnt > 0; out/in adjacency bitsets for the move evaluation's probes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "mm_internal.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned grid_for(int64_t n, int tpb = TPB) {
+  int64_t g = ceil_div(n, tpb);
+  if (g < 1) g = 1;
+  if (g > 0x7fffffffLL) g = 0x7fffffffLL;
+  return (unsigned)g;
+}
+
+inline unsigned grid_persistent() { return 148 * 8; }
+
+__global__ void class_sizes_to_words(const int32_t *cls_n, const int32_t *cls_a, int32_t c, int64_t *words,
+                                     int64_t *tiles) {
+  int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= c) return;
+  int64_t n = cls_n[C], a = cls_a[C];
+  int64_t T = (n + 31) / 32;
+  words[C] = n * ((a + 31) / 32);
+  tiles[C] = T * (T + 1) / 2;
+}
+
+// One thread per method: set the bits of its accesses to its own class's
+// attributes (local attribute ranks); own_x = their number, S_C += own_x.
+__global__ void build_bitsets(const int32_t *method_class, const int32_t *method_local, const int64_t *acc_rowptr,
+                              const int32_t *acc_idx, const int32_t *attr_class, const int32_t *attr_local,
+                              const int32_t *cls_a, const int64_t *bits_off, uint32_t *bits, int32_t M,
+                              int32_t *own, int64_t *cls_S) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  int32_t C = method_class[x];
+  int64_t W = ((int64_t)cls_a[C] + 31) / 32;
+  uint32_t *row = bits + bits_off[C] + (int64_t)method_local[x] * W;
+  int32_t cnt = 0;
+  for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
+    int32_t al = acc_idx[e];
+    if (attr_class[al] == C) {
+      int32_t l = attr_local[al];
+      row[l >> 5] |= 1u << (l & 31);
+      ++cnt;
+    }
+  }
+  own[x] = cnt;
+  if (cnt) atomicAdd(reinterpret_cast<unsigned long long *>(&cls_S[C]), (unsigned long long)cnt);
+}
+
+__device__ __forceinline__ int32_t upper_class(const int64_t *off, int32_t c, int64_t t) {
+  // largest C with off[C] <= t (off has c+1 non-decreasing entries)
+  int32_t lo = 0, hi = c;
+  while (lo < hi) {
+    int32_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// LCOM pair kernel: one warp per 32 x 32 tile (rows ti, columns tj >= ti) of
+// the method-pair triangle of one class.  Lane l owns row i = 32 ti + l and
+// builds share_mask (bit jj: rows i and 32 tj + jj share an owned attribute).
+// Row sums give q_i; for off-diagonal tiles a ballot per column gives q_j.
+__global__ void __launch_bounds__(256) lcom_pairs(const int64_t *tile_off, const int32_t *cls_n,
+                                                  const int32_t *cls_a, const int64_t *bits_off,
+                                                  const uint32_t *__restrict__ bits, const int64_t *cm_rowptr,
+                                                  const int32_t *cm_list, int32_t c, int64_t total_tiles,
+                                                  int32_t *q, int64_t *cls_Q) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total_tiles; t += nwarps) {
+    int32_t C = upper_class(tile_off, c, t);
+    int64_t local = t - tile_off[C];
+    int32_t n = cls_n[C];
+    int32_t T = (n + 31) >> 5;
+    int32_t ti = 0;
+    while (local >= T - ti) { local -= T - ti; ++ti; }
+    int32_t tj = ti + (int32_t)local;
+    int64_t W = ((int64_t)cls_a[C] + 31) >> 5;
+    if (W == 0) continue;  // no attribute: no pair shares
+    const uint32_t *base = bits + bits_off[C];
+    int32_t i = ti * 32 + lane;
+    bool vi = i < n;
+    int32_t j0 = tj * 32;
+    int32_t jn = min(32, n - j0);
+    uint32_t share = 0;
+    for (int64_t w0 = 0; w0 < W; w0 += 8) {
+      uint32_t ri[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) ri[k] = (vi && w0 + k < W) ? base[(int64_t)i * W + w0 + k] : 0u;
+      for (int jj = 0; jj < jn; ++jj) {
+        const uint32_t *rj = base + (int64_t)(j0 + jj) * W + w0;
+        uint32_t acc = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (w0 + k < W) acc |= ri[k] & __ldg(rj + k);
+        if (acc) share |= 1u << jj;
+      }
+    }
+    if (ti == tj) share &= ~(1u << lane);
+    if (!vi) share = 0;
+    int32_t rc = __popc(share);
+    int32_t pairs = rc;
+    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_down_sync(0xffffffffu, pairs, o);
+    const int32_t *members = cm_list + cm_rowptr[C];
+    if (vi && rc) atomicAdd(&q[members[i]], rc);
+    if (ti != tj) {
+      int32_t colcnt = 0;
+      for (int jj = 0; jj < 32; ++jj) {
+        int32_t cc = __popc(__ballot_sync(0xffffffffu, (share >> jj) & 1u));
+        if (lane == jj) colcnt = cc;
+      }
+      if (lane < jn && colcnt) atomicAdd(&q[members[j0 + lane]], colcnt);
+    } else {
+      pairs >>= 1;  // each pair of the diagonal tile was seen from both rows
+    }
+    if (lane == 0 && pairs) atomicAdd(reinterpret_cast<unsigned long long *>(&cls_Q[C]), (unsigned long long)pairs);
+  }
+}
+
+// ---------------------------------------------------------------- coupling
+
+// keys of every use edge of x: (Y, E) -> Y * c + E, intra-class edges -> sentinel c*c
+__global__ void coupling_keys(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
+                              const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
+                              int32_t M, int32_t c, int32_t cbo_attrs, uint64_t *keys) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  const uint64_t sent = (uint64_t)c * (uint64_t)c;
+  int32_t Y = method_class[x];
+  int64_t pos = call_rowptr[x] + (cbo_attrs ? acc_rowptr[x] : 0);
+  for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e) {
+    int32_t E = method_class[call_idx[e]];
+    keys[pos++] = E != Y ? (uint64_t)Y * c + E : sent;
+  }
+  if (cbo_attrs)
+    for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
+      int32_t E = attr_class[acc_idx[e]];
+      keys[pos++] = E != Y ? (uint64_t)Y * c + E : sent;
+    }
+}
+
+__global__ void run_heads(const uint64_t *keys, int64_t n, uint64_t sent, int64_t *head, int64_t *n_valid) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t k = keys[i];
+  bool valid = k != sent;
+  head[i] = (valid && (i == 0 || keys[i - 1] != k)) ? 1 : 0;
+  if (valid && (i + 1 == n || keys[i + 1] == sent)) *n_valid = i + 1;
+}
+
+__global__ void run_starts(const uint64_t *keys, const int64_t *head_scan, int64_t n, uint64_t sent,
+                           int64_t *start) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t k = keys[i];
+  if (k != sent && (i == 0 || keys[i - 1] != k)) start[head_scan[i]] = i;
+}
+
+__global__ void multigraph_fill(const uint64_t *keys, const int64_t *start, const int64_t *n_unique,
+                                const int64_t *n_valid, int32_t c, int64_t cap, int32_t *mg_dst, int32_t *mg_cnt,
+                                int32_t *row_count, uint32_t *out_adj, uint32_t *in_adj, int64_t aw) {
+  const int64_t nu = *n_unique, nv = *n_valid;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu && u < cap;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s0 = start[u];
+    int64_t s1 = (u + 1 < nu) ? start[u + 1] : nv;
+    uint64_t k = keys[s0];
+    int32_t Y = (int32_t)(k / (uint64_t)c), E = (int32_t)(k % (uint64_t)c);
+    mg_dst[u] = E;
+    mg_cnt[u] = (int32_t)(s1 - s0);
+    atomicAdd(&row_count[Y], 1);
+    atomicOr(&out_adj[(int64_t)Y * aw + (E >> 5)], 1u << (E & 31));
+    atomicOr(&in_adj[(int64_t)E * aw + (Y >> 5)], 1u << (Y & 31));
+  }
+}
+
+__global__ void finalize_classes(const int32_t *cls_n, const int64_t *cls_Q, int32_t c, int64_t *cls_P) {
+  int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= c) return;
+  int64_t n = cls_n[C];
+  cls_P[C] = n * (n - 1) / 2 - cls_Q[C];
+}
+
+}  // namespace
+
+void build_metrics(mm_system *s) {
+  cudaStream_t st = s->stream;
+  const int32_t c = s->c, M = s->M;
+
+  // bitset and tile offsets
+  int64_t *tmp = static_cast<int64_t *>(s->eval_ws.need(sizeof(int64_t) * 2 * ((size_t)c + 1), st));
+  int64_t *words = tmp, *tiles = tmp + c + 1;
+  class_sizes_to_words<<<grid_for(c), TPB, 0, st>>>(s->cls_n, s->cls_a, c, words, tiles);
+  MM_LAUNCH_CHECK();
+  scan_exclusive_i64(words, s->bits_off, c, s->bits_off + c, s->sort_ws, st);
+  scan_exclusive_i64(tiles, s->tile_off, c, s->tile_off + c, s->sort_ws, st);
+
+  // bitsets, own, S
+  if (s->summary.bits_words > 0)
+    MM_CUDA_TRY(cudaMemsetAsync(s->bits, 0, sizeof(uint32_t) * (size_t)s->summary.bits_words, st));
+  MM_CUDA_TRY(cudaMemsetAsync(s->cls_S, 0, sizeof(int64_t) * (size_t)c, st));
+  MM_CUDA_TRY(cudaMemsetAsync(s->cls_Q, 0, sizeof(int64_t) * (size_t)c, st));
+  MM_CUDA_TRY(cudaMemsetAsync(s->q, 0, sizeof(int32_t) * (size_t)std::max(M, 1), st));
+  if (M > 0) {
+    build_bitsets<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->method_local, s->acc_rowptr, s->acc_idx,
+                                               s->attr_class, s->attr_local, s->cls_a, s->bits_off, s->bits, M,
+                                               s->own, s->cls_S);
+    MM_LAUNCH_CHECK();
+  }
+  // LCOM pair tiles
+  if (s->summary.lcom_tiles > 0) {
+    int64_t want = ceil_div(s->summary.lcom_tiles, 8);
+    unsigned g = (unsigned)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)grid_persistent() * 4);
+    lcom_pairs<<<g, 256, 0, st>>>(s->tile_off, s->cls_n, s->cls_a, s->bits_off, s->bits, s->cm_rowptr, s->cm_list,
+                                  c, s->summary.lcom_tiles, s->q, s->cls_Q);
+    MM_LAUNCH_CHECK();
+  }
+  finalize_classes<<<grid_for(c), TPB, 0, st>>>(s->cls_n, s->cls_Q, c, s->cls_P);
+  MM_LAUNCH_CHECK();
+
+  // coupling: keys -> sort -> runs -> multigraph, CBO, adjacency bitsets
+  const int64_t nk = s->n_call + (s->cbo_attrs ? s->n_acc : 0);
+  const uint64_t sent = (uint64_t)c * (uint64_t)c;
+  MM_CUDA_TRY(cudaMemsetAsync(s->out_adj, 0, sizeof(uint32_t) * (size_t)(s->adj_words * c), st));
+  MM_CUDA_TRY(cudaMemsetAsync(s->in_adj, 0, sizeof(uint32_t) * (size_t)(s->adj_words * c), st));
+  int32_t *row_count = s->cls_cbo;
+  MM_CUDA_TRY(cudaMemsetAsync(row_count, 0, sizeof(int32_t) * (size_t)c, st));
+  MM_CUDA_TRY(cudaMemsetAsync(s->mg_count, 0, sizeof(int64_t) * 2, st));
+  if (nk > 0) {
+    size_t bytes = sizeof(uint64_t) * 2 * (size_t)nk + sizeof(int64_t) * 2 * (size_t)nk;
+    char *b = static_cast<char *>(s->eval_ws.need(bytes, st));
+    uint64_t *keys = reinterpret_cast<uint64_t *>(b);
+    uint64_t *keys_alt = keys + nk;
+    int64_t *head = reinterpret_cast<int64_t *>(keys_alt + nk);
+    int64_t *start = head + nk;
+    coupling_keys<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
+                                               s->acc_idx, s->attr_class, M, c, s->cbo_attrs, keys);
+    MM_LAUNCH_CHECK();
+    radix_sort_u64(keys, keys_alt, nullptr, nullptr, nk, bits_for(sent), s->sort_ws, st);
+    int64_t *n_valid = s->mg_count + 1;
+    run_heads<<<grid_for(nk), TPB, 0, st>>>(keys, nk, sent, head, n_valid);
+    MM_LAUNCH_CHECK();
+    scan_exclusive_i64(head, head, nk, s->mg_count, s->sort_ws, st);
+    run_starts<<<grid_for(nk), TPB, 0, st>>>(keys, head, nk, sent, start);
+    MM_LAUNCH_CHECK();
+    multigraph_fill<<<grid_for(nk), TPB, 0, st>>>(keys, start, s->mg_count, n_valid, c, nk, s->mg_dst, s->mg_cnt,
+                                                  row_count, s->out_adj, s->in_adj, s->adj_words);
+    MM_LAUNCH_CHECK();
+  }
+  // mg_rowptr = exclusive scan of the row counts (CBO); last entry = distinct pairs
+  scan_exclusive_i32to64(row_count, s->mg_rowptr, c, s->sort_ws, st);
+  MM_CUDA_TRY(cudaMemcpyAsync(s->mg_rowptr + c, s->mg_count, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+}

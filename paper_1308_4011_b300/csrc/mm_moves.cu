@@ -1,0 +1,876 @@
+// Move Method evaluation (Sec. III.A rules, Sec. IV.C re-evaluation), done
+// incrementally instead of recomputing the classes for every candidate.
+//
+// For a method m of class C moved to class D != C:
+//   source C:  n' = n - 1, S' = S - own_m, Q' = Q - q_m, P' = P - (n - 1 - q_m)
+//   target D:  n' = n + 1, S' = S + t,     Q' = Q + s,   P' = P + (n - s)
+//              t = m's accesses to D's attributes, s = methods of D sharing one
+//   CBO, through the class-use multigraph cnt[Y][E] (E != Y):
+//     row C loses m's use edges and gains C->D for m's callers inside C,
+//     row D gains m's use edges and loses D->C for m's callers inside D,
+//     row X (any other class calling m) moves its edges from X->C to X->D.
+//   Only C, D and the classes of m's callers can change.
+//
+// Everything that does not depend on D is prepared once per method (header,
+// list L of the classes m uses with out_m[E], cnt[C][E], t and s, list R of
+// the classes calling m with in_m[X] and cnt[X][C]).  The dense kernel gives
+// each thread one destination D and walks a range of methods; the 32 lanes of
+// a warp hold 32 consecutive D, so every adjacency probe of a warp is one
+// 32-bit word, and the 16-byte records of a warp form one contiguous 512-byte
+// store.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "mm_internal.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned grid_for(int64_t n, int tpb = TPB) {
+  int64_t g = ceil_div(n, tpb);
+  if (g < 1) g = 1;
+  if (g > 0x7fffffffLL) g = 0x7fffffffLL;
+  return (unsigned)g;
+}
+
+__device__ __forceinline__ int32_t mg_lookup(const int64_t *rowptr, const int32_t *dst, const int32_t *cnt,
+                                             int32_t Y, int32_t E) {
+  int64_t lo = rowptr[Y], hi = rowptr[Y + 1];
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (dst[mid] < E) lo = mid + 1; else hi = mid;
+  }
+  return (lo < rowptr[Y + 1] && dst[lo] == E) ? cnt[lo] : 0;
+}
+
+// ---------------------------------------------------------------- precompute
+
+// use keys of m: ((m * c + E) << 1) | kind, kind 0 = call into E, 1 = access of an attribute of E
+__global__ void method_use_keys(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
+                                const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
+                                int32_t M, int32_t c, uint64_t *keys) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  int64_t pos = call_rowptr[x] + acc_rowptr[x];
+  uint64_t base = (uint64_t)x * (uint64_t)c;
+  for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e)
+    keys[pos++] = ((base + (uint64_t)method_class[call_idx[e]]) << 1);
+  for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e)
+    keys[pos++] = ((base + (uint64_t)attr_class[acc_idx[e]]) << 1) | 1u;
+}
+
+// caller-class keys of m: m * c + class(caller)
+__global__ void caller_class_keys(const int64_t *caller_rowptr, const int32_t *caller_idx,
+                                  const int32_t *method_class, int32_t M, int32_t c, uint64_t *keys) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  uint64_t base = (uint64_t)x * (uint64_t)c;
+  for (int64_t e = caller_rowptr[x]; e < caller_rowptr[x + 1]; ++e)
+    keys[e] = base + (uint64_t)method_class[caller_idx[e]];
+}
+
+__global__ void heads_shifted(const uint64_t *keys, int64_t n, int shift, int64_t *head) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  head[i] = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) ? 1 : 0;
+}
+
+__global__ void starts_shifted(const uint64_t *keys, const int64_t *head_scan, int64_t n, int shift,
+                               int64_t *start) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) start[head_scan[i]] = i;
+}
+
+// One thread per run (m, E) of m's use keys: split into the own-class run
+// (out_self) and list-L entries; L entries are placed by a second scan.
+__global__ void use_runs_classify(const uint64_t *keys, const int64_t *start, const int64_t *n_runs, int64_t n,
+                                  const int32_t *method_class, int32_t c, int32_t cbo_attrs, int32_t *out_self,
+                                  int64_t *lflag, int64_t cap) {
+  const int64_t nr = *n_runs;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < cap; u += (int64_t)gridDim.x * blockDim.x) {
+    if (u >= nr) { lflag[u] = 0; continue; }
+    int64_t s0 = start[u], s1 = (u + 1 < nr) ? start[u + 1] : n;
+    uint64_t me = keys[s0] >> 1;
+    int32_t x = (int32_t)(me / (uint64_t)c), E = (int32_t)(me % (uint64_t)c);
+    int32_t C = method_class[x];
+    if (E == C) {
+      int32_t calls = 0, accs = 0;
+      for (int64_t i = s0; i < s1; ++i) (keys[i] & 1u) ? ++accs : ++calls;
+      out_self[x] = calls + (cbo_attrs ? accs : 0);
+      lflag[u] = 0;
+    } else {
+      lflag[u] = 1;
+    }
+  }
+}
+
+__global__ void use_runs_fill(const uint64_t *keys, const int64_t *start, const int64_t *n_runs, int64_t n,
+                              const int64_t *lpos, const int32_t *method_class, int32_t c, int32_t cbo_attrs,
+                              const int64_t *mg_rowptr, const int32_t *mg_dst, const int32_t *mg_cnt, int4 *l_list,
+                              int32_t *l_x, int32_t *l_off, int32_t *l_len, int64_t cap) {
+  const int64_t nr = *n_runs;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nr && u < cap;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s0 = start[u], s1 = (u + 1 < nr) ? start[u + 1] : n;
+    uint64_t me = keys[s0] >> 1;
+    int32_t x = (int32_t)(me / (uint64_t)c), E = (int32_t)(me % (uint64_t)c);
+    int32_t C = method_class[x];
+    if (E == C) continue;
+    int32_t calls = 0, accs = 0;
+    for (int64_t i = s0; i < s1; ++i) (keys[i] & 1u) ? ++accs : ++calls;
+    int32_t out = calls + (cbo_attrs ? accs : 0);
+    int32_t cnt = out > 0 ? mg_lookup(mg_rowptr, mg_dst, mg_cnt, C, E) : 0;
+    int64_t l = lpos[u];
+    l_list[l] = make_int4(E, out, cnt, accs);
+    l_x[l] = x;
+    atomicMin(&l_off[x], (int32_t)l);
+    atomicAdd(&l_len[x], 1);
+  }
+}
+
+// s for list-L entries with t > 0: one warp per entry, lanes over the methods of D
+__global__ void l_entries_s(const int4 *l_list, const int32_t *l_x, const int64_t *n_l, const int64_t *acc_rowptr,
+                            const int32_t *acc_idx, const int32_t *attr_class, const int32_t *attr_local,
+                            const int32_t *cls_n, const int32_t *cls_a, const int64_t *bits_off,
+                            const uint32_t *bits, int32_t *l_s) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t nl = *n_l;
+  for (int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < nl; l += nwarps) {
+    int4 v = l_list[l];
+    if (v.w == 0) {
+      if (lane == 0) l_s[l] = 0;
+      continue;
+    }
+    int32_t D = v.x, x = l_x[l];
+    int32_t nD = cls_n[D];
+    int64_t W = ((int64_t)cls_a[D] + 31) >> 5;
+    const uint32_t *base = bits + bits_off[D];
+    int32_t s = 0;
+    for (int32_t j0 = 0; j0 < nD; j0 += 32) {
+      int32_t j = j0 + lane;
+      bool sh = false;
+      if (j < nD) {
+        const uint32_t *row = base + (int64_t)j * W;
+        for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1] && !sh; ++e) {
+          int32_t al = acc_idx[e];
+          if (attr_class[al] == D) {
+            int32_t b = attr_local[al];
+            sh = (row[b >> 5] >> (b & 31)) & 1u;
+          }
+        }
+      }
+      s += __popc(__ballot_sync(0xffffffffu, sh));
+    }
+    if (lane == 0) l_s[l] = s;
+  }
+}
+
+__global__ void caller_runs_fill(const uint64_t *keys, const int64_t *start, const int64_t *n_runs, int64_t n,
+                                 const int64_t *rpos, const int32_t *method_class, int32_t c,
+                                 const int64_t *mg_rowptr, const int32_t *mg_dst, const int32_t *mg_cnt,
+                                 int4 *r_list, int32_t *in_self, int32_t *r_off, int32_t *r_len, int64_t cap) {
+  const int64_t nr = *n_runs;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nr && u < cap;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s0 = start[u], s1 = (u + 1 < nr) ? start[u + 1] : n;
+    uint64_t k = keys[s0];
+    int32_t x = (int32_t)(k / (uint64_t)c), X = (int32_t)(k % (uint64_t)c);
+    int32_t C = method_class[x];
+    int32_t in = (int32_t)(s1 - s0);
+    if (X == C) {
+      in_self[x] = in;
+    } else {
+      int64_t r = rpos[u];
+      r_list[r] = make_int4(X, in, mg_lookup(mg_rowptr, mg_dst, mg_cnt, X, C), 0);
+      atomicMin(&r_off[x], (int32_t)r);
+      atomicAdd(&r_len[x], 1);
+    }
+  }
+}
+
+__global__ void caller_runs_flag(const uint64_t *keys, const int64_t *start, const int64_t *n_runs,
+                                 const int32_t *method_class, int32_t c, int64_t *rflag, int64_t cap) {
+  const int64_t nr = *n_runs;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < cap; u += (int64_t)gridDim.x * blockDim.x) {
+    if (u >= nr) { rflag[u] = 0; continue; }
+    uint64_t k = keys[start[u]];
+    int32_t x = (int32_t)(k / (uint64_t)c), X = (int32_t)(k % (uint64_t)c);
+    rflag[u] = X != method_class[x] ? 1 : 0;
+  }
+}
+
+__device__ __forceinline__ int sgn64(int64_t v) { return (v > 0) - (v < 0); }
+__device__ __forceinline__ uint32_t enc_sign(int s) { return s < 0 ? 1u : (s > 0 ? 2u : 0u); }
+
+__global__ void build_headers(const int32_t *method_class, const int32_t *cls_n, const int32_t *cls_a,
+                              const int64_t *cls_P, const int64_t *cls_Q, const int64_t *cls_S, const int32_t *own,
+                              const int32_t *q, const int32_t *l_off, const int32_t *l_len, const int32_t *r_off,
+                              const int32_t *r_len, const int32_t *out_self, const int32_t *in_self,
+                              const int4 *l_list, int32_t M, MoveHdr *hdr) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  int32_t C = method_class[x];
+  int32_t ll = l_len[x], lo = ll ? l_off[x] : 0;
+  int32_t rl = r_len[x], ro = rl ? r_off[x] : 0;
+  int32_t l_all = 0;
+  for (int32_t e = 0; e < ll; ++e) {
+    int4 v = l_list[lo + e];
+    if (v.y > 0 && v.z == v.y) ++l_all;  // C stops using E after the move
+  }
+  // source class after the move (independent of the destination)
+  int64_t n = cls_n[C], a = cls_a[C], S = cls_S[C];
+  int64_t diff = cls_P[C] - cls_Q[C];
+  int64_t ck = diff > 0 ? diff : 0;
+  int64_t diff2 = diff - (n - 1) + 2 * (int64_t)q[x];
+  int64_t ck2 = diff2 > 0 ? diff2 : 0;
+  int sck = sgn64(ck2 - ck);
+  int shs;
+  if (a == 0) shs = 0;
+  else if (n == 1) shs = own[x] < a ? -1 : 0;    // after: empty class, LCOM_HS = 0
+  else shs = sgn64((int64_t)own[x] * n - S);     // sign(S n' - S' n) with n' = n-1, S' = S - own
+  MoveHdr h;
+  h.w0 = make_int4(C, lo, ll, ro);
+  h.w1 = make_int4(rl, out_self[x], in_self[x], l_all);
+  h.w2 = make_int4((int)(enc_sign(sck) | (enc_sign(shs) << 2)), (int)(ck2 - ck), 0, 0);
+  hdr[x] = h;
+}
+
+}  // namespace
+
+void build_move_precompute(mm_system *s) {
+  cudaStream_t st = s->stream;
+  const int32_t c = s->c, M = s->M;
+  if (M == 0) return;
+  const int64_t nu = s->n_call + s->n_acc;
+  const int64_t nmax = std::max<int64_t>(std::max<int64_t>(nu, s->n_call), 1);
+  // scratch: keys, keys_alt (u64), head, start, flag/pos (i64), per-method temps
+  size_t bytes = sizeof(uint64_t) * 2 * (size_t)nmax + sizeof(int64_t) * 3 * (size_t)nmax +
+                 sizeof(int32_t) * 8 * (size_t)M + sizeof(int64_t) * 4 + 1024;
+  char *b = static_cast<char *>(s->eval_ws.need(bytes, st));
+  uint64_t *keys = reinterpret_cast<uint64_t *>(b);
+  uint64_t *keys_alt = keys + nmax;
+  int64_t *head = reinterpret_cast<int64_t *>(keys_alt + nmax);
+  int64_t *start = head + nmax;
+  int64_t *flag = start + nmax;
+  int32_t *out_self = reinterpret_cast<int32_t *>(flag + nmax);
+  int32_t *in_self = out_self + M;
+  int32_t *l_off = in_self + M;
+  int32_t *l_len = l_off + M;
+  int32_t *r_off = l_len + M;
+  int32_t *r_len = r_off + M;
+  int64_t *counters = reinterpret_cast<int64_t *>(r_len + 2 * (size_t)M);  // n_runs, n_l, n_rruns, n_r
+  counters = reinterpret_cast<int64_t *>((reinterpret_cast<uintptr_t>(counters) + 15) & ~uintptr_t(15));
+
+  MM_CUDA_TRY(cudaMemsetAsync(out_self, 0, sizeof(int32_t) * 2 * (size_t)M, st));
+  MM_CUDA_TRY(cudaMemsetAsync(l_off, 0x7f, sizeof(int32_t) * (size_t)M, st));
+  MM_CUDA_TRY(cudaMemsetAsync(l_len, 0, sizeof(int32_t) * (size_t)M, st));
+  MM_CUDA_TRY(cudaMemsetAsync(r_off, 0x7f, sizeof(int32_t) * (size_t)M, st));
+  MM_CUDA_TRY(cudaMemsetAsync(r_len, 0, sizeof(int32_t) * (size_t)M, st));
+  MM_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int64_t) * 4, st));
+
+  // list L: runs of (m, E) over m's use keys
+  if (nu > 0) {
+    method_use_keys<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
+                                                 s->acc_idx, s->attr_class, M, c, keys);
+    MM_LAUNCH_CHECK();
+    uint64_t maxkey = (((uint64_t)M * (uint64_t)c - 1) << 1) | 1u;
+    radix_sort_u64(keys, keys_alt, nullptr, nullptr, nu, bits_for(maxkey), s->sort_ws, st);
+    heads_shifted<<<grid_for(nu), TPB, 0, st>>>(keys, nu, 1, head);
+    MM_LAUNCH_CHECK();
+    scan_exclusive_i64(head, head, nu, &counters[0], s->sort_ws, st);
+    starts_shifted<<<grid_for(nu), TPB, 0, st>>>(keys, head, nu, 1, start);
+    MM_LAUNCH_CHECK();
+    use_runs_classify<<<grid_for(nu), TPB, 0, st>>>(keys, start, &counters[0], nu, s->method_class, c, s->cbo_attrs,
+                                                    out_self, flag, nu);
+    MM_LAUNCH_CHECK();
+    scan_exclusive_i64(flag, flag, nu, &counters[1], s->sort_ws, st);
+    use_runs_fill<<<grid_for(nu), TPB, 0, st>>>(keys, start, &counters[0], nu, flag, s->method_class, c,
+                                                s->cbo_attrs, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list,
+                                                s->l_x, l_off, l_len, nu);
+    MM_LAUNCH_CHECK();
+    l_entries_s<<<(unsigned)std::min<int64_t>(ceil_div(nu * 32, TPB), 148 * 32), TPB, 0, st>>>(s->l_list, s->l_x,
+                                                   &counters[1], s->acc_rowptr, s->acc_idx, s->attr_class,
+                                                   s->attr_local, s->cls_n, s->cls_a, s->bits_off, s->bits,
+                                                   s->l_s);
+    MM_LAUNCH_CHECK();
+  }
+  // list R: runs of (m, X) over the classes of m's callers
+  if (s->n_call > 0) {
+    const int64_t nc = s->n_call;
+    caller_class_keys<<<grid_for(M), TPB, 0, st>>>(s->caller_rowptr, s->caller_idx, s->method_class, M, c, keys);
+    MM_LAUNCH_CHECK();
+    radix_sort_u64(keys, keys_alt, nullptr, nullptr, nc, bits_for((uint64_t)M * (uint64_t)c - 1), s->sort_ws, st);
+    heads_shifted<<<grid_for(nc), TPB, 0, st>>>(keys, nc, 0, head);
+    MM_LAUNCH_CHECK();
+    scan_exclusive_i64(head, head, nc, &counters[2], s->sort_ws, st);
+    starts_shifted<<<grid_for(nc), TPB, 0, st>>>(keys, head, nc, 0, start);
+    MM_LAUNCH_CHECK();
+    caller_runs_flag<<<grid_for(nc), TPB, 0, st>>>(keys, start, &counters[2], s->method_class, c, flag, nc);
+    MM_LAUNCH_CHECK();
+    scan_exclusive_i64(flag, flag, nc, &counters[3], s->sort_ws, st);
+    caller_runs_fill<<<grid_for(nc), TPB, 0, st>>>(keys, start, &counters[2], nc, flag, s->method_class, c,
+                                                   s->mg_rowptr, s->mg_dst, s->mg_cnt, s->r_list, in_self, r_off,
+                                                   r_len, nc);
+    MM_LAUNCH_CHECK();
+  }
+  build_headers<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S,
+                                             s->own, s->q, l_off, l_len, r_off, r_len, out_self, in_self,
+                                             s->l_list, M, s->hdr);
+  MM_LAUNCH_CHECK();
+}
+
+// ======================================================================
+// evaluation
+
+namespace {
+
+struct DState {
+  int32_t D, nD, aD;
+  int64_t diffD, SD, ckD;
+};
+
+__device__ __forceinline__ DState load_dstate(int32_t D, const int32_t *cls_n, const int32_t *cls_a,
+                                              const int64_t *cls_P, const int64_t *cls_Q, const int64_t *cls_S) {
+  DState d;
+  d.D = D;
+  d.nD = cls_n[D];
+  d.aD = cls_a[D];
+  d.diffD = cls_P[D] - cls_Q[D];
+  d.SD = cls_S[D];
+  d.ckD = d.diffD > 0 ? d.diffD : 0;
+  return d;
+}
+
+struct EvalCtx {
+  const MoveHdr *hdr;
+  const int4 *l_list;
+  const int32_t *l_s;
+  const int4 *r_list;
+  const uint32_t *in_adj, *out_adj;
+  int64_t aw;
+  uint32_t mask;
+  int32_t min_improved;
+};
+
+__device__ __forceinline__ int dec_sign(uint32_t e) { return e == 1u ? -1 : (e == 2u ? 1 : 0); }
+__device__ __forceinline__ uint32_t sat_u16(int32_t v) { return v < 0 ? 0u : (v > 65535 ? 65535u : (uint32_t)v); }
+__device__ __forceinline__ uint32_t sat_i16(int32_t v) {
+  int32_t w = v < -32768 ? -32768 : (v > 32767 ? 32767 : v);
+  return (uint32_t)(uint16_t)(int16_t)w;
+}
+
+// Evaluate move (m -> D) given m's header h (C = h.w0.x != D).
+__device__ __forceinline__ uint4 eval_move(const EvalCtx &cx, const MoveHdr &h, const DState &ds, int32_t &dck_sum,
+                                           int32_t &dcbo_sum) {
+  const int32_t D = ds.D;
+  const int32_t C = h.w0.x;
+  const uint32_t dword = (uint32_t)D >> 5, dbit = (uint32_t)D & 31u;
+  // list L: classes m uses (E != C)
+  int32_t t = 0, sh = 0, outD = 0, cntCD = 0, gain = 0;
+  const int4 *L = cx.l_list + h.w0.y;
+  for (int32_t e = 0; e < h.w0.z; ++e) {
+    int4 v = __ldg(L + e);
+    if (v.x == D) {
+      outD = v.y;
+      cntCD = v.z;
+      t = v.w;
+      sh = t > 0 ? __ldg(cx.l_s + h.w0.y + e) : 0;
+    } else if (v.y > 0) {
+      gain += 1 - (int)((__ldg(cx.in_adj + (int64_t)v.x * cx.aw + dword) >> dbit) & 1u);
+    }
+  }
+  // list R: other classes calling m
+  int32_t inD = 0, cntDC = 0, impX = 0, worX = 0;
+  const int4 *R = cx.r_list + h.w0.w;
+  for (int32_t e = 0; e < h.w1.x; ++e) {
+    int4 v = __ldg(R + e);
+    if (v.x == D) {
+      inD = v.y;
+      cntDC = v.z;
+    } else {
+      int loss = v.z == v.y;
+      int g = 1 - (int)((__ldg(cx.out_adj + (int64_t)v.x * cx.aw + dword) >> dbit) & 1u);
+      int dx = g - loss;
+      impX += dx < 0;
+      worX += dx > 0;
+    }
+  }
+  const int32_t out_self = h.w1.y, in_self = h.w1.z, l_all = h.w1.w;
+  // row D, column C
+  int bDC, aDC;
+  if (inD > 0) {
+    bDC = 1;
+    aDC = (cntDC + out_self - inD) > 0;
+  } else {
+    bDC = (int)((__ldg(cx.in_adj + (int64_t)C * cx.aw + dword) >> dbit) & 1u);
+    aDC = bDC | (out_self > 0);
+  }
+  const int32_t dD = gain + aDC - bDC;
+  // row C, column D
+  int bCD, aCD, corr = 0;
+  if (outD > 0) {
+    bCD = 1;
+    aCD = (cntCD - outD + in_self) > 0;
+    corr = cntCD == outD;
+  } else {
+    bCD = (int)((__ldg(cx.out_adj + (int64_t)C * cx.aw + dword) >> dbit) & 1u);
+    aCD = bCD | (in_self > 0);
+  }
+  const int32_t dC = -l_all + corr + aCD - bCD;
+  // target LCOM
+  int64_t diff2 = ds.diffD + ds.nD - 2 * (int64_t)sh;
+  int64_t ck2 = diff2 > 0 ? diff2 : 0;
+  int sckD = sgn64(ck2 - ds.ckD);
+  int shsD;
+  if (ds.aD == 0) shsD = 0;
+  else if (ds.nD == 0) shsD = t < ds.aD ? 1 : 0;
+  else shsD = sgn64(ds.SD - (int64_t)t * ds.nD);  // sign(S n' - S' n) with n' = n+1, S' = S + t
+  const int sckC = dec_sign((uint32_t)h.w2.x & 3u), shsC = dec_sign(((uint32_t)h.w2.x >> 2) & 3u);
+  const int scbC = (dC > 0) - (dC < 0), scbD = (dD > 0) - (dD < 0);
+  const uint32_t mk = cx.mask;
+  int upC = ((mk & 1u) && sckC > 0) | ((mk & 2u) && shsC > 0) | ((mk & 4u) && scbC > 0);
+  int dnC = ((mk & 1u) && sckC < 0) | ((mk & 2u) && shsC < 0) | ((mk & 4u) && scbC < 0);
+  int upD = ((mk & 1u) && sckD > 0) | ((mk & 2u) && shsD > 0) | ((mk & 4u) && scbD > 0);
+  int dnD = ((mk & 1u) && sckD < 0) | ((mk & 2u) && shsD < 0) | ((mk & 4u) && scbD < 0);
+  int32_t imp = (!upC && dnC) + (!upD && dnD);
+  int32_t wor = upC + upD;
+  if (mk & 4u) {
+    imp += impX;
+    wor += worX;
+  }
+  uint32_t flags = enc_sign(sckC) | (enc_sign(shsC) << 2) | (enc_sign(scbC) << 4) | (enc_sign(sckD) << 6) |
+                   (enc_sign(shsD) << 8) | (enc_sign(scbD) << 10);
+  if (wor == 0 && imp >= cx.min_improved) flags |= 0x8000u;
+  dck_sum = h.w2.y + (int32_t)(ck2 - ds.ckD);
+  dcbo_sum = dC + dD;
+  uint4 r;
+  r.x = (uint32_t)sh;
+  r.y = sat_u16(t) | (sat_i16(dC) << 16);
+  r.z = sat_i16(dD) | (sat_u16(imp) << 16);
+  r.w = sat_u16(wor) | (flags << 16);
+  return r;
+}
+
+__device__ __forceinline__ uint64_t smix(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t record_hash(int32_t m, int32_t D, uint4 r) {
+  uint64_t lo = (uint64_t)r.x | ((uint64_t)r.y << 32);
+  uint64_t hi = (uint64_t)r.z | ((uint64_t)r.w << 32);
+  uint64_t key = ((uint64_t)(uint32_t)m << 32) | (uint32_t)D;
+  return smix(key ^ smix(lo ^ smix(hi)));
+}
+
+struct OutCtx {
+  uint4 *records;                 // nullable
+  unsigned long long *digest;     // nullable (device accumulator)
+  mm_move *kept;                  // nullable
+  unsigned long long *kept_count;
+  int64_t kept_cap;
+  uint8_t *kept_mark;             // per method
+};
+
+__device__ __forceinline__ void emit_kept(const OutCtx &oc, bool kept, int32_t m, int32_t D, uint32_t nimp,
+                                          int32_t dck, int32_t dcbo, uint32_t lane) {
+  uint32_t bal = __ballot_sync(0xffffffffu, kept);
+  if (bal == 0) return;
+  unsigned long long base = 0;
+  int leader = __ffs(bal) - 1;
+  if ((int)lane == leader) base = atomicAdd(oc.kept_count, (unsigned long long)__popc(bal));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (kept) {
+    unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
+    if ((int64_t)pos < oc.kept_cap) {
+      mm_move mv;
+      mv.m = m;
+      mv.d = D;
+      mv.n_improved = (int32_t)nimp;
+      mv.d_lcom_ck_sum = dck;
+      mv.d_cbo_sum = dcbo;
+      mv.reserved = 0;
+      oc.kept[pos] = mv;
+    }
+    oc.kept_mark[m] = 1;
+  }
+}
+
+// Dense cross product: thread = destination D, loop over a chunk of methods.
+template <bool REC, bool DIG, bool KEEP>
+__global__ void __launch_bounds__(256) eval_dense(EvalCtx cx, OutCtx oc, const int32_t *cls_n, const int32_t *cls_a,
+                                                  const int64_t *cls_P, const int64_t *cls_Q, const int64_t *cls_S,
+                                                  int32_t c, int32_t M, int32_t mchunk) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int32_t D = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  const bool vD = D < c;
+  DState ds = load_dstate(vD ? D : 0, cls_n, cls_a, cls_P, cls_Q, cls_S);
+  ds.D = D;
+  const int32_t m0 = blockIdx.y * mchunk;
+  const int32_t m1 = min(M, m0 + mchunk);
+  uint64_t dig = 0;
+  const int64_t row = (int64_t)c - 1;
+  for (int32_t m = m0; m < m1; ++m) {
+    MoveHdr h;
+    h.w0 = __ldg(&cx.hdr[m].w0);
+    h.w1 = __ldg(&cx.hdr[m].w1);
+    h.w2 = __ldg(&cx.hdr[m].w2);
+    const int32_t C = h.w0.x;
+    const bool act = vD && D != C;
+    int32_t dck = 0, dcbo = 0;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (act) r = eval_move(cx, h, ds, dck, dcbo);
+    if (REC && act) __stcs(oc.records + (int64_t)m * row + D - (D > C ? 1 : 0), r);
+    if (DIG && act) dig += record_hash(m, D, r);
+    if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
+  }
+  if (DIG) {
+    for (int o = 16; o > 0; o >>= 1) dig += __shfl_down_sync(0xffffffffu, dig, o);
+    if (lane == 0 && dig) atomicAdd(oc.digest, (unsigned long long)dig);
+  }
+}
+
+// Explicit candidate lists (CSR over methods): one warp per method row.
+template <bool REC, bool DIG, bool KEEP>
+__global__ void __launch_bounds__(256) eval_csr(EvalCtx cx, OutCtx oc, const int64_t *cand_rowptr,
+                                                const int32_t *cand_dst, const int32_t *cls_n,
+                                                const int32_t *cls_a, const int64_t *cls_P, const int64_t *cls_Q,
+                                                const int64_t *cls_S, int32_t M) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  uint64_t dig = 0;
+  for (int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; m < M; m += nwarps) {
+    MoveHdr h;
+    h.w0 = __ldg(&cx.hdr[m].w0);
+    h.w1 = __ldg(&cx.hdr[m].w1);
+    h.w2 = __ldg(&cx.hdr[m].w2);
+    const int64_t b0 = cand_rowptr[m], b1 = cand_rowptr[m + 1];
+    for (int64_t i0 = b0; i0 < b1; i0 += 32) {
+      const int64_t i = i0 + lane;
+      const bool act = i < b1;
+      int32_t D = act ? __ldg(cand_dst + i) : 0;
+      int32_t dck = 0, dcbo = 0;
+      uint4 r = make_uint4(0, 0, 0, 0);
+      if (act) {
+        DState ds = load_dstate(D, cls_n, cls_a, cls_P, cls_Q, cls_S);
+        r = eval_move(cx, h, ds, dck, dcbo);
+      }
+      if (REC && act) __stcs(oc.records + i, r);
+      if (DIG && act) dig += record_hash((int32_t)m, D, r);
+      if (KEEP) emit_kept(oc, act && (r.w >> 31), (int32_t)m, D, r.z >> 16, dck, dcbo, lane);
+    }
+  }
+  if (DIG) {
+    for (int o = 16; o > 0; o >>= 1) dig += __shfl_down_sync(0xffffffffu, dig, o);
+    if (lane == 0 && dig) atomicAdd(oc.digest, (unsigned long long)dig);
+  }
+}
+
+__global__ void validate_candidates(const int64_t *rowptr, const int32_t *dst, const int32_t *method_class,
+                                    int32_t M, int32_t c, int64_t n_cand, uint32_t *err) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  uint32_t e = 0;
+  if (x == 0 && (rowptr[0] != 0 || rowptr[M] != n_cand)) e |= VE_CAND_ROWPTR;
+  int64_t a = rowptr[x], b = rowptr[x + 1];
+  if (a < 0 || b < a || b > n_cand) {
+    e |= VE_CAND_ROWPTR;
+  } else {
+    int32_t C = method_class[x];
+    for (int64_t i = a; i < b; ++i) {
+      int32_t D = dst[i];
+      if (D < 0 || D >= c) e |= VE_CAND_RANGE;
+      else if (D == C) e |= VE_CAND_SELF;
+    }
+  }
+  if (e) atomicOr(err, e);
+}
+
+template <bool REC, bool DIG, bool KEEP>
+void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_t *rowptr, const int32_t *dst) {
+  cudaStream_t st = s->stream;
+  if (!rowptr) {
+    const int32_t c = s->c, M = s->M;
+    unsigned gx = (unsigned)ceil_div(c, 256);
+    // enough blocks for ~16 per SM, each walking a chunk of methods
+    int64_t want_y = std::max<int64_t>(1, (148 * 16 + gx - 1) / gx);
+    int32_t mchunk = (int32_t)std::max<int64_t>(1, ceil_div(M, want_y));
+    unsigned gy = (unsigned)ceil_div(M, mchunk);
+    eval_dense<REC, DIG, KEEP><<<dim3(gx, gy), 256, 0, st>>>(cx, oc, s->cls_n, s->cls_a, s->cls_P, s->cls_Q,
+                                                             s->cls_S, c, M, mchunk);
+  } else {
+    unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)s->M * 32, 256), 148 * 64);
+    eval_csr<REC, DIG, KEEP><<<g, 256, 0, st>>>(cx, oc, rowptr, dst, s->cls_n, s->cls_a, s->cls_P, s->cls_Q,
+                                                s->cls_S, s->M);
+  }
+  MM_LAUNCH_CHECK();
+}
+
+void dispatch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_t *rowptr, const int32_t *dst) {
+  const bool rec = oc.records != nullptr, dig = oc.digest != nullptr, keep = oc.kept_count != nullptr;
+  if (rec && dig) launch_eval<true, true, false>(s, cx, oc, rowptr, dst);
+  else if (rec) launch_eval<true, false, false>(s, cx, oc, rowptr, dst);
+  else if (dig) launch_eval<false, true, false>(s, cx, oc, rowptr, dst);
+  else if (keep) launch_eval<false, false, true>(s, cx, oc, rowptr, dst);
+  else launch_eval<false, false, false>(s, cx, oc, rowptr, dst);
+}
+
+// ---------------------------------------------------------------- top-k
+
+__device__ __forceinline__ bool move_before(const mm_move &a, const mm_move &b) {
+  if (a.n_improved != b.n_improved) return a.n_improved > b.n_improved;
+  if (a.d_lcom_ck_sum != b.d_lcom_ck_sum) return a.d_lcom_ck_sum < b.d_lcom_ck_sum;
+  if (a.d_cbo_sum != b.d_cbo_sum) return a.d_cbo_sum < b.d_cbo_sum;
+  if (a.m != b.m) return a.m < b.m;
+  return a.d < b.d;
+}
+
+constexpr int BITONIC_MAX = 2048;
+
+// single-block bitonic sort of up to 2048 kept moves in shared memory
+__global__ void __launch_bounds__(1024) bitonic_sort_moves(mm_move *v, int32_t n) {
+  __shared__ mm_move sm[BITONIC_MAX];
+  int32_t np = 1;
+  while (np < n) np <<= 1;
+  for (int32_t i = threadIdx.x; i < np; i += blockDim.x) {
+    if (i < n) sm[i] = v[i];
+    else {
+      mm_move z;
+      z.m = 0x7fffffff; z.d = 0x7fffffff; z.n_improved = -1; z.d_lcom_ck_sum = 0x7fffffff;
+      z.d_cbo_sum = 0x7fffffff; z.reserved = 0;
+      sm[i] = z;
+    }
+  }
+  __syncthreads();
+  for (int32_t k = 2; k <= np; k <<= 1) {
+    for (int32_t j = k >> 1; j > 0; j >>= 1) {
+      for (int32_t i = threadIdx.x; i < np; i += blockDim.x) {
+        int32_t ixj = i ^ j;
+        if (ixj > i) {
+          bool asc = (i & k) == 0;
+          mm_move a = sm[i], b = sm[ixj];
+          bool swap = asc ? move_before(b, a) : move_before(a, b);
+          if (swap) { sm[i] = b; sm[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) v[i] = sm[i];
+}
+
+// field-wise LSD radix sort of kept moves through a permutation
+__global__ void gather_field(const mm_move *v, const uint32_t *perm, int64_t n, int field, int64_t bias,
+                             uint32_t *key) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const mm_move &a = v[perm[i]];
+  int64_t f;
+  switch (field) {
+    case 0: f = a.d; break;
+    case 1: f = a.m; break;
+    case 2: f = (int64_t)a.d_cbo_sum + bias; break;
+    case 3: f = (int64_t)a.d_lcom_ck_sum + bias; break;
+    default: f = 65535 - (int64_t)a.n_improved; break;
+  }
+  key[i] = (uint32_t)f;
+}
+
+__global__ void iota_perm(uint32_t *p, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = (uint32_t)i;
+}
+
+__global__ void permute_moves(const mm_move *in, const uint32_t *perm, int64_t n, mm_move *out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[perm[i]];
+}
+
+__global__ void count_marks(const uint8_t *mark, int64_t n, unsigned long long *out) {
+  unsigned long long c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    c += mark[i];
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+}  // namespace
+
+static void check_criteria(const mm_criteria &crit) {
+  if ((crit.metric_mask & 7u) == 0 || (crit.metric_mask & ~7u) != 0)
+    throw MmError{MM_EINVAL, "criteria: metric_mask must be a non-empty subset of LCOM_CK|LCOM_HS|CBO"};
+  if (crit.min_improved < 1) throw MmError{MM_EINVAL, "criteria: min_improved must be >= 1"};
+}
+
+// Upload (if host) and validate an explicit candidate list; returns device pointers.
+static void prepare_candidates(mm_system *s, const mm_candidates *cands, const int64_t **rowptr,
+                               const int32_t **dst, int64_t *n_cand, Scratch &ws) {
+  *rowptr = nullptr;
+  *dst = nullptr;
+  if (!cands || !cands->rowptr) {
+    *n_cand = (int64_t)s->M * (int64_t)(s->c - 1);
+    if (s->c < 1) *n_cand = 0;
+    return;
+  }
+  if (cands->n_cand < 0) throw MmError{MM_EINVAL, "candidates: n_cand < 0"};
+  if (cands->n_cand > 0 && !cands->dst) throw MmError{MM_EINVAL, "candidates: dst is NULL"};
+  *n_cand = cands->n_cand;
+  cudaStream_t st = s->stream;
+  if (cands->ptr_kind == MM_PTR_HOST) {
+    size_t rb = sizeof(int64_t) * ((size_t)s->M + 1), db = sizeof(int32_t) * (size_t)cands->n_cand;
+    char *b = static_cast<char *>(ws.need(rb + db + 256, st));
+    MM_CUDA_TRY(cudaMemcpyAsync(b, cands->rowptr, rb, cudaMemcpyHostToDevice, st));
+    if (db) MM_CUDA_TRY(cudaMemcpyAsync(b + ((rb + 255) & ~size_t(255)), cands->dst, db, cudaMemcpyHostToDevice, st));
+    *rowptr = reinterpret_cast<const int64_t *>(b);
+    *dst = reinterpret_cast<const int32_t *>(b + ((rb + 255) & ~size_t(255)));
+  } else if (cands->ptr_kind == MM_PTR_DEVICE) {
+    *rowptr = cands->rowptr;
+    *dst = cands->dst;
+  } else {
+    throw MmError{MM_EINVAL, "candidates: bad ptr_kind"};
+  }
+  MM_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(uint32_t), st));
+  if (s->M > 0) {
+    validate_candidates<<<grid_for(s->M), TPB, 0, st>>>(*rowptr, *dst, s->method_class, s->M, s->c, *n_cand,
+                                                        s->d_err);
+    MM_LAUNCH_CHECK();
+  }
+  uint32_t err = 0;
+  MM_CUDA_TRY(cudaMemcpyAsync(&err, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  MM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (err & VE_CAND_ROWPTR) throw MmError{MM_EINVAL, "candidates: rowptr must start at 0, be non-decreasing and end at n_cand"};
+  if (err & VE_CAND_RANGE) throw MmError{MM_EINVAL, "candidates: destination class out of range"};
+  if (err & VE_CAND_SELF) throw MmError{MM_EINVAL, "candidates: destination equals the method's own class"};
+}
+
+static EvalCtx make_ctx(mm_system *s, const mm_criteria &crit) {
+  EvalCtx cx;
+  cx.hdr = s->hdr;
+  cx.l_list = s->l_list;
+  cx.l_s = s->l_s;
+  cx.r_list = s->r_list;
+  cx.in_adj = s->in_adj;
+  cx.out_adj = s->out_adj;
+  cx.aw = s->adj_words;
+  cx.mask = crit.metric_mask;
+  cx.min_improved = crit.min_improved;
+  return cx;
+}
+
+void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *cands, mm_move_eval *records,
+                    uint64_t *digest, int32_t kind) {
+  check_criteria(crit);
+  if (kind != MM_PTR_HOST && kind != MM_PTR_DEVICE) throw MmError{MM_EINVAL, "evaluate: bad out_kind"};
+  cudaStream_t st = s->stream;
+  const int64_t *rowptr;
+  const int32_t *dst;
+  int64_t n_cand;
+  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, s->stage_ws);
+  if (n_cand == 0 || s->M == 0) {
+    if (digest) {
+      if (kind == MM_PTR_HOST) *digest = 0;
+      else MM_CUDA_TRY(cudaMemsetAsync(digest, 0, sizeof(uint64_t), st));
+    }
+    return;
+  }
+  EvalCtx cx = make_ctx(s, crit);
+  OutCtx oc{};
+  uint4 *rec_dev = nullptr;
+  if (records) {
+    if (kind == MM_PTR_DEVICE) rec_dev = reinterpret_cast<uint4 *>(records);
+    else rec_dev = static_cast<uint4 *>(s->eval_ws.need(sizeof(uint4) * (size_t)n_cand, st));
+  }
+  oc.records = rec_dev;
+  if (digest) {
+    oc.digest = s->d_u64;
+    MM_CUDA_TRY(cudaMemsetAsync(s->d_u64, 0, sizeof(unsigned long long), st));
+  }
+  dispatch_eval(s, cx, oc, rowptr, dst);
+  if (records && kind == MM_PTR_HOST)
+    MM_CUDA_TRY(cudaMemcpyAsync(records, rec_dev, sizeof(uint4) * (size_t)n_cand, cudaMemcpyDeviceToHost, st));
+  if (digest) {
+    MM_CUDA_TRY(cudaMemcpyAsync(digest, s->d_u64, sizeof(uint64_t),
+                                kind == MM_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  }
+  if (kind == MM_PTR_HOST) MM_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *cands, int32_t k, mm_move *out,
+                   int32_t kind, int64_t *n_kept, int64_t *n_mk) {
+  check_criteria(crit);
+  if (k < 0) throw MmError{MM_EINVAL, "suggest: k < 0"};
+  if (k > 0 && !out) throw MmError{MM_EINVAL, "suggest: out_topk is NULL"};
+  if (kind != MM_PTR_HOST && kind != MM_PTR_DEVICE) throw MmError{MM_EINVAL, "suggest: bad out_kind"};
+  cudaStream_t st = s->stream;
+  const int64_t *rowptr;
+  const int32_t *dst;
+  int64_t n_cand;
+  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, s->stage_ws);
+  int64_t K = 0, nm = 0;
+  mm_move *kept = nullptr;
+  if (n_cand > 0 && s->M > 0) {
+    EvalCtx cx = make_ctx(s, crit);
+    int64_t cap = std::max<int64_t>(4096, (int64_t)(s->eval_ws.cap / sizeof(mm_move)) / 2);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      size_t bytes = sizeof(mm_move) * 2 * (size_t)cap + (size_t)s->M + 256;
+      char *b = static_cast<char *>(s->eval_ws.need(bytes, st));
+      kept = reinterpret_cast<mm_move *>(b);
+      uint8_t *mark = reinterpret_cast<uint8_t *>(b + sizeof(mm_move) * 2 * (size_t)cap);
+      MM_CUDA_TRY(cudaMemsetAsync(mark, 0, (size_t)s->M, st));
+      MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 1, 0, 2 * sizeof(unsigned long long), st));
+      OutCtx oc{};
+      oc.kept = kept;
+      oc.kept_count = s->d_u64 + 1;
+      oc.kept_cap = cap;
+      oc.kept_mark = mark;
+      dispatch_eval(s, cx, oc, rowptr, dst);
+      count_marks<<<148 * 4, 256, 0, st>>>(mark, s->M, s->d_u64 + 2);
+      MM_LAUNCH_CHECK();
+      unsigned long long hc[2];
+      MM_CUDA_TRY(cudaMemcpyAsync(hc, s->d_u64 + 1, sizeof(hc), cudaMemcpyDeviceToHost, st));
+      MM_CUDA_TRY(cudaStreamSynchronize(st));
+      K = (int64_t)hc[0];
+      nm = (int64_t)hc[1];
+      if (K <= cap) break;
+      cap = K + K / 8 + 1024;  // grow and evaluate again
+    }
+    if (K > 1 && K <= BITONIC_MAX) {
+      bitonic_sort_moves<<<1, 1024, 0, st>>>(kept, (int32_t)K);
+      MM_LAUNCH_CHECK();
+    } else if (K > BITONIC_MAX) {
+      // permutation sort, least significant field first (d, m, dCBO, dLCOM, n_improved desc)
+      size_t pb = sizeof(uint32_t) * 4 * (size_t)K;
+      uint32_t *pw = static_cast<uint32_t *>(s->stage_ws.need(pb + sizeof(mm_move) * (size_t)K + 256, st));
+      uint32_t *key = pw, *key_alt = pw + K, *perm = pw + 2 * K, *perm_alt = pw + 3 * K;
+      mm_move *sorted = reinterpret_cast<mm_move *>(pw + 4 * K);
+      iota_perm<<<grid_for(K), TPB, 0, st>>>(perm, K);
+      MM_LAUNCH_CHECK();
+      const int64_t bias_cbo = 2 * (int64_t)s->c + 4;
+      const int64_t bias_ck = 4 * (int64_t)std::max(s->summary.max_class_methods, 1) + 4;
+      const int fbits[5] = {bits_for((uint64_t)std::max(s->c - 1, 0)), bits_for((uint64_t)std::max(s->M - 1, 0)),
+                            bits_for((uint64_t)(2 * bias_cbo)), bits_for((uint64_t)(2 * bias_ck)), 16};
+      const int64_t bias[5] = {0, 0, bias_cbo, bias_ck, 0};
+      for (int f = 0; f < 5; ++f) {
+        gather_field<<<grid_for(K), TPB, 0, st>>>(kept, perm, K, f, bias[f], key);
+        MM_LAUNCH_CHECK();
+        radix_sort_u32(key, key_alt, perm, perm_alt, K, fbits[f], s->sort_ws, st);
+      }
+      permute_moves<<<grid_for(K), TPB, 0, st>>>(kept, perm, K, sorted);
+      MM_LAUNCH_CHECK();
+      MM_CUDA_TRY(cudaMemcpyAsync(kept, sorted, sizeof(mm_move) * (size_t)K, cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  int64_t nout = std::min<int64_t>(k, K);
+  if (nout > 0)
+    MM_CUDA_TRY(cudaMemcpyAsync(out, kept, sizeof(mm_move) * (size_t)nout,
+                                kind == MM_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  MM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (n_kept) *n_kept = K;
+  if (n_mk) *n_mk = nm;
+}

@@ -1,0 +1,251 @@
+// Device-wide primitives: exclusive scan and a stable LSD radix sort.
+//
+// The sort is the "segmented sort" the coupling metric needs (class-use keys
+// (Y, E) sorted by source class, Sec. II.B CBO) and it also builds the
+// class -> method lists, the callers of each method and the per-method use
+// lists.  Keys are sorted 8 bits per pass; within a 4096-key tile every warp
+// ranks its keys with __match_any_sync so equal digits keep their input order,
+// which makes every pass, and hence the sort, stable and deterministic.
+#include <cuda_runtime.h>
+
+#include "mm_internal.cuh"
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <class T>
+__device__ T block_exclusive_sum(T v, T *total) {
+  __shared__ T warp_sums[SCAN_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < SCAN_THREADS / 32 ? warp_sums[lane] : T(0);
+    T wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < SCAN_THREADS / 32) warp_sums[lane] = wi - w;
+    if (lane == SCAN_THREADS / 32 - 1) *total = wi;
+  }
+  __syncthreads();
+  T r = incl - v + warp_sums[warp];
+  __syncthreads();
+  return r;
+}
+
+template <class Tin, class Tout>
+__global__ void scan_reduce_kernel(const Tin *in, Tout *partial, int64_t n) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  Tout s = 0;
+  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+    int64_t k = base + i;
+    if (k < n) s += (Tout)in[k];
+  }
+  __shared__ Tout tot;
+  Tout dummy = block_exclusive_sum<Tout>(s, &tot);
+  (void)dummy;
+  __syncthreads();
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+template <class T>
+__global__ void scan_partials_kernel(T *partial, int64_t nb, T *total_out) {
+  __shared__ T carry_s;
+  __shared__ T tot;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += SCAN_THREADS) {
+    int64_t k = base + threadIdx.x;
+    T v = k < nb ? partial[k] : T(0);
+    T ex = block_exclusive_sum<T>(v, &tot);
+    T carry = carry_s;
+    if (k < nb) partial[k] = ex + carry;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = carry + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total_out) *total_out = carry_s;
+}
+
+template <class Tin, class Tout>
+__global__ void scan_tiles_kernel(const Tin *in, Tout *out, int64_t n, const Tout *partial) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  Tout v[SCAN_ITEMS];
+  Tout s = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    int64_t k = base + i;
+    v[i] = k < n ? (Tout)in[k] : Tout(0);
+    s += v[i];
+  }
+  __shared__ Tout tot;
+  Tout ex = block_exclusive_sum<Tout>(s, &tot) + partial[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    int64_t k = base + i;
+    if (k < n) out[k] = ex;
+    ex += v[i];
+  }
+}
+
+template <class Tin, class Tout>
+void scan_exclusive(const Tin *in, Tout *out, int64_t n, Tout *total_dev, Scratch &ws, cudaStream_t st) {
+  if (n <= 0) {
+    if (total_dev) MM_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(Tout), st));
+    return;
+  }
+  int64_t nb = ceil_div(n, SCAN_TILE);
+  Tout *partial = static_cast<Tout *>(ws.need(sizeof(Tout) * (size_t)nb, st));
+  scan_reduce_kernel<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, partial, n);
+  MM_LAUNCH_CHECK();
+  scan_partials_kernel<Tout><<<1, SCAN_THREADS, 0, st>>>(partial, nb, total_dev);
+  MM_LAUNCH_CHECK();
+  scan_tiles_kernel<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, partial);
+  MM_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------- radix sort
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096 keys
+constexpr int RS_RADIX = 256;
+
+template <class K>
+__global__ void radix_upsweep(const K *keys, int64_t n, int shift, uint32_t *hist, int64_t ntiles) {
+  __shared__ uint32_t cnt[RS_RADIX];
+  for (int i = threadIdx.x; i < RS_RADIX; i += RS_THREADS) cnt[i] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
+    int64_t k = base + i;
+    if (k < n) atomicAdd(&cnt[(uint32_t)(keys[k] >> shift) & 0xffu], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) hist[(int64_t)d * ntiles + blockIdx.x] = cnt[d];
+}
+
+template <class K, bool VALS>
+__global__ void __launch_bounds__(RS_THREADS) radix_downsweep(const K *keys_in, const uint32_t *vals_in,
+                                                               K *keys_out, uint32_t *vals_out, int64_t n,
+                                                               int shift, const uint32_t *offsets,
+                                                               int64_t ntiles) {
+  __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < RS_WARPS * RS_RADIX; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (RS_ITEMS * 32);
+  const uint32_t lt = (1u << lane) - 1u;
+  K key[RS_ITEMS];
+  uint32_t val[RS_ITEMS];
+  uint32_t rank[RS_ITEMS];
+  uint32_t dig[RS_ITEMS];
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    int64_t idx = wbase + r * 32 + lane;
+    bool valid = idx < n;
+    key[r] = valid ? keys_in[idx] : K(0);
+    if (VALS) val[r] = valid ? vals_in[idx] : 0u;
+    uint32_t d = (uint32_t)(key[r] >> shift) & 0xffu;
+    dig[r] = valid ? d : 0xffffffffu;
+    uint32_t tag = valid ? d : (0x1000u + lane);  // invalid lanes never match
+    uint32_t peers = __match_any_sync(0xffffffffu, tag);
+    uint32_t before = 0;
+    if (valid) before = wcnt[warp][d];
+    rank[r] = before + __popc(peers & lt);
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) {
+    uint32_t run = offsets[(int64_t)d * ntiles + blockIdx.x];
+    for (int w = 0; w < RS_WARPS; ++w) {
+      uint32_t t = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    if (dig[r] != 0xffffffffu) {
+      uint32_t pos = wcnt[warp][dig[r]] + rank[r];
+      keys_out[pos] = key[r];
+      if (VALS) vals_out[pos] = val[r];
+    }
+  }
+}
+
+template <class K>
+void radix_sort(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int nbits, Scratch &ws,
+                cudaStream_t st) {
+  if (n <= 1 || nbits <= 0) return;
+  if (n >= (int64_t)0xffffffffLL) throw MmError{MM_EINVAL, "radix sort: more than 2^32-1 keys"};
+  int64_t ntiles = ceil_div(n, RS_TILE);
+  int64_t nh = ntiles * RS_RADIX;
+  // scratch: hist (uint32 nh) + scan partials
+  size_t hist_bytes = sizeof(uint32_t) * (size_t)nh;
+  size_t part_bytes = sizeof(uint32_t) * (size_t)ceil_div(nh, SCAN_TILE);
+  char *base = static_cast<char *>(ws.need(hist_bytes + part_bytes + 256, st));
+  uint32_t *hist = reinterpret_cast<uint32_t *>(base);
+  Scratch part_ws;  // view into the same allocation for the scan partials
+  part_ws.ptr = base + ((hist_bytes + 255) / 256) * 256;
+  part_ws.cap = part_bytes + 256 - ((hist_bytes + 255) / 256 * 256 - hist_bytes);
+  int passes = (nbits + 7) / 8;
+  K *kin = keys, *kout = keys_alt;
+  uint32_t *vin = vals, *vout = vals_alt;
+  for (int p = 0; p < passes; ++p) {
+    int shift = 8 * p;
+    radix_upsweep<K><<<(unsigned)ntiles, RS_THREADS, 0, st>>>(kin, n, shift, hist, ntiles);
+    MM_LAUNCH_CHECK();
+    scan_exclusive<uint32_t, uint32_t>(hist, hist, nh, nullptr, part_ws, st);
+    if (vals)
+      radix_downsweep<K, true><<<(unsigned)ntiles, RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, shift, hist,
+                                                                      ntiles);
+    else
+      radix_downsweep<K, false><<<(unsigned)ntiles, RS_THREADS, 0, st>>>(kin, nullptr, kout, nullptr, n, shift,
+                                                                       hist, ntiles);
+    MM_LAUNCH_CHECK();
+    K *tk = kin; kin = kout; kout = tk;
+    uint32_t *tv = vin; vin = vout; vout = tv;
+  }
+  if (kin != keys) {
+    MM_CUDA_TRY(cudaMemcpyAsync(keys, kin, sizeof(K) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (vals) MM_CUDA_TRY(cudaMemcpyAsync(vals, vin, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+  }
+}
+
+}  // namespace
+
+void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, Scratch &ws,
+                        cudaStream_t st) {
+  scan_exclusive<int64_t, int64_t>(in, out, n, total_dev, ws, st);
+}
+
+void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch &ws, cudaStream_t st) {
+  scan_exclusive<int32_t, int64_t>(in, out, n, nullptr, ws, st);
+}
+
+void radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int nbits,
+                    Scratch &ws, cudaStream_t st) {
+  radix_sort<uint32_t>(keys, keys_alt, vals, vals_alt, n, nbits, ws, st);
+}
+
+void radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int nbits,
+                    Scratch &ws, cudaStream_t st) {
+  radix_sort<uint64_t>(keys, keys_alt, vals, vals_alt, n, nbits, ws, st);
+}

@@ -1,0 +1,261 @@
+// Loading a system: upload of the CSR arrays (the paper's cls / dpnd arrays,
+// Sec. IV.C), validation on the device, and the class structures every metric
+// needs: class -> methods, class -> attributes, and the callers of each method
+// (the transpose used for fan-in, Sec. II.A).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "mm_internal.cuh"
+
+// ---------------------------------------------------------------- memory helpers
+
+void *DevArena::alloc(size_t n) {
+  void *p = nullptr;
+  n = (n + 255) & ~size_t(255);
+  MM_CUDA_TRY(cudaMallocAsync(&p, n, stream));
+  ptrs.push_back(p);
+  bytes += (int64_t)n;
+  return p;
+}
+
+void DevArena::release() {
+  for (void *p : ptrs) cudaFreeAsync(p, stream);
+  ptrs.clear();
+  bytes = 0;
+}
+
+void *Scratch::need(size_t n, cudaStream_t st) {
+  if (n <= cap && ptr) return ptr;
+  size_t want = std::max(n, cap + cap / 2);
+  if (ptr) MM_CUDA_TRY(cudaFreeAsync(ptr, st));
+  ptr = nullptr;
+  cap = 0;
+  want = (want + 255) & ~size_t(255);
+  MM_CUDA_TRY(cudaMallocAsync(&ptr, want, st));
+  cap = want;
+  return ptr;
+}
+
+void Scratch::release(cudaStream_t st) {
+  if (ptr) cudaFreeAsync(ptr, st);
+  ptr = nullptr;
+  cap = 0;
+}
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned grid_for(int64_t n, int tpb = TPB) {
+  int64_t g = ceil_div(n, tpb);
+  if (g < 1) g = 1;
+  if (g > 0x7fffffffLL) g = 0x7fffffffLL;
+  return (unsigned)g;
+}
+
+// ---------------------------------------------------------------- validation
+
+__global__ void validate_methods(const int32_t *method_class, const int64_t *acc_rowptr, const int32_t *acc_idx,
+                                 const int64_t *call_rowptr, const int32_t *call_idx, int32_t c, int32_t M,
+                                 int32_t A, int64_t n_acc, int64_t n_call, uint32_t *err) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  uint32_t e = 0;
+  int32_t C = method_class[x];
+  if (C < 0 || C >= c) e |= VE_METHOD_CLASS;
+  if (x == 0) {
+    if (acc_rowptr[0] != 0 || acc_rowptr[M] != n_acc) e |= VE_ACC_ROWPTR;
+    if (call_rowptr[0] != 0 || call_rowptr[M] != n_call) e |= VE_CALL_ROWPTR;
+  }
+  int64_t a0 = acc_rowptr[x], a1 = acc_rowptr[x + 1];
+  if (a0 < 0 || a1 < a0 || a1 > n_acc) {
+    e |= VE_ACC_ROWPTR;
+  } else {
+    int32_t prev = -1;
+    for (int64_t k = a0; k < a1; ++k) {
+      int32_t v = acc_idx[k];
+      if (v < 0 || v >= A) e |= VE_ACC_IDX_RANGE;
+      if (v <= prev) e |= VE_ACC_IDX_ORDER;
+      prev = v;
+    }
+  }
+  int64_t c0 = call_rowptr[x], c1 = call_rowptr[x + 1];
+  if (c0 < 0 || c1 < c0 || c1 > n_call) {
+    e |= VE_CALL_ROWPTR;
+  } else {
+    int32_t prev = -1;
+    for (int64_t k = c0; k < c1; ++k) {
+      int32_t v = call_idx[k];
+      if (v < 0 || v >= M) e |= VE_CALL_IDX_RANGE;
+      if (v <= prev) e |= VE_CALL_IDX_ORDER;
+      if (v == x) e |= VE_SELF_CALL;
+      prev = v;
+    }
+  }
+  if (e) atomicOr(err, e);
+}
+
+__global__ void validate_attrs(const int32_t *attr_class, int32_t c, int32_t A, uint32_t *err) {
+  int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= A) return;
+  int32_t C = attr_class[a];
+  if (C < 0 || C >= c) atomicOr(err, (uint32_t)VE_ATTR_CLASS);
+}
+
+__global__ void class_histograms(const int32_t *method_class, const int32_t *attr_class, int32_t c, int32_t M,
+                                 int32_t A, int32_t *cls_n, int32_t *cls_a) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) {
+    int32_t C = method_class[i];
+    if (C >= 0 && C < c) atomicAdd(&cls_n[C], 1);
+  }
+  if (i < A) {
+    int32_t C = attr_class[i];
+    if (C >= 0 && C < c) atomicAdd(&cls_a[C], 1);
+  }
+}
+
+__global__ void summarise_classes(const int32_t *cls_n, const int32_t *cls_a, int32_t c, LoadSummary *sum) {
+  int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t words = 0, tiles = 0;
+  int32_t nmax = 0;
+  if (C < c) {
+    int64_t n = cls_n[C], a = cls_a[C];
+    int64_t W = (a + 31) / 32;
+    int64_t T = (n + 31) / 32;
+    words = n * W;
+    tiles = T * (T + 1) / 2;
+    nmax = (int32_t)n;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    words += __shfl_down_sync(0xffffffffu, words, o);
+    tiles += __shfl_down_sync(0xffffffffu, tiles, o);
+    nmax = max(nmax, __shfl_down_sync(0xffffffffu, nmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (words) atomicAdd((unsigned long long *)&sum->bits_words, (unsigned long long)words);
+    if (tiles) atomicAdd((unsigned long long *)&sum->lcom_tiles, (unsigned long long)tiles);
+    atomicMax(&sum->max_class_methods, nmax);
+  }
+}
+
+// ---------------------------------------------------------------- structures
+
+__global__ void iota_u32(uint32_t *v, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (uint32_t)i;
+}
+
+__global__ void copy_i32_to_u32(const int32_t *in, uint32_t *out, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (uint32_t)in[i];
+}
+
+// rank of each item inside its class after the stable sort by class
+__global__ void local_ranks(const uint32_t *sorted_cls, const uint32_t *sorted_item, const int64_t *rowptr,
+                            int64_t n, int32_t *local, int32_t *list) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t C = sorted_cls[i], it = sorted_item[i];
+  local[it] = (int32_t)(i - rowptr[C]);
+  if (list) list[i] = (int32_t)it;
+}
+
+__global__ void expand_callers(const int64_t *call_rowptr, int32_t M, uint32_t *caller_of_edge) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e) caller_of_edge[e] = (uint32_t)x;
+}
+
+__global__ void fan_in_hist(const int32_t *call_idx, int64_t n_call, int32_t *fan_in) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n_call) atomicAdd(&fan_in[call_idx[e]], 1);
+}
+
+}  // namespace
+
+void load_validate_and_summarise(mm_system *s) {
+  cudaStream_t st = s->stream;
+  MM_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(uint32_t), st));
+  if (s->M > 0)
+    validate_methods<<<grid_for(s->M), TPB, 0, st>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->call_rowptr,
+                                                     s->call_idx, s->c, s->M, s->A, s->n_acc, s->n_call, s->d_err);
+  MM_LAUNCH_CHECK();
+  if (s->A > 0) validate_attrs<<<grid_for(s->A), TPB, 0, st>>>(s->attr_class, s->c, s->A, s->d_err);
+  MM_LAUNCH_CHECK();
+  MM_CUDA_TRY(cudaMemsetAsync(s->cls_n, 0, sizeof(int32_t) * (size_t)s->c, st));
+  MM_CUDA_TRY(cudaMemsetAsync(s->cls_a, 0, sizeof(int32_t) * (size_t)s->c, st));
+  int64_t nmax = std::max<int64_t>(s->M, s->A);
+  class_histograms<<<grid_for(nmax), TPB, 0, st>>>(s->method_class, s->attr_class, s->c, s->M, s->A, s->cls_n,
+                                                   s->cls_a);
+  MM_LAUNCH_CHECK();
+  LoadSummary *dsum = reinterpret_cast<LoadSummary *>(s->d_u64 + 4);
+  MM_CUDA_TRY(cudaMemsetAsync(dsum, 0, sizeof(LoadSummary), st));
+  summarise_classes<<<grid_for(s->c), TPB, 0, st>>>(s->cls_n, s->cls_a, s->c, dsum);
+  MM_LAUNCH_CHECK();
+  LoadSummary h{};
+  MM_CUDA_TRY(cudaMemcpyAsync(&h, dsum, sizeof(LoadSummary), cudaMemcpyDeviceToHost, st));
+  uint32_t err = 0;
+  MM_CUDA_TRY(cudaMemcpyAsync(&err, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  MM_CUDA_TRY(cudaStreamSynchronize(st));
+  h.err = err;
+  s->summary = h;
+}
+
+namespace {
+__global__ void set_i64(int64_t *p, int64_t v) { *p = v; }
+}  // namespace
+
+void build_structures(mm_system *s) {
+  cudaStream_t st = s->stream;
+  const int64_t c = s->c, M = s->M, A = s->A, E = s->n_call;
+  int64_t n = std::max<int64_t>(std::max<int64_t>(M, A), E);
+  n = std::max<int64_t>(n, 1);
+  uint32_t *buf = static_cast<uint32_t *>(s->eval_ws.need(sizeof(uint32_t) * 4 * (size_t)n, st));
+  uint32_t *k = buf, *ka = buf + n, *v = buf + 2 * n, *va = buf + 3 * n;
+  const int cbits = bits_for((uint64_t)(c > 0 ? c - 1 : 0));
+  const int mbits = bits_for((uint64_t)(M > 0 ? M - 1 : 0));
+
+  // class -> methods: stable sort of method ids by owner class
+  scan_exclusive_i32to64(s->cls_n, s->cm_rowptr, c, s->sort_ws, st);
+  set_i64<<<1, 1, 0, st>>>(s->cm_rowptr + c, M);
+  MM_LAUNCH_CHECK();
+  if (M > 0) {
+    copy_i32_to_u32<<<grid_for(M), TPB, 0, st>>>(s->method_class, k, M);
+    iota_u32<<<grid_for(M), TPB, 0, st>>>(v, M);
+    MM_LAUNCH_CHECK();
+    radix_sort_u32(k, ka, v, va, M, cbits, s->sort_ws, st);
+    local_ranks<<<grid_for(M), TPB, 0, st>>>(k, v, s->cm_rowptr, M, s->method_local, s->cm_list);
+    MM_LAUNCH_CHECK();
+  }
+  // class -> attributes
+  scan_exclusive_i32to64(s->cls_a, s->ca_rowptr, c, s->sort_ws, st);
+  set_i64<<<1, 1, 0, st>>>(s->ca_rowptr + c, A);
+  MM_LAUNCH_CHECK();
+  if (A > 0) {
+    copy_i32_to_u32<<<grid_for(A), TPB, 0, st>>>(s->attr_class, k, A);
+    iota_u32<<<grid_for(A), TPB, 0, st>>>(v, A);
+    MM_LAUNCH_CHECK();
+    radix_sort_u32(k, ka, v, va, A, cbits, s->sort_ws, st);
+    local_ranks<<<grid_for(A), TPB, 0, st>>>(k, v, s->ca_rowptr, A, s->attr_local, nullptr);
+    MM_LAUNCH_CHECK();
+  }
+  // callers of each method: stable sort of (callee, caller) edges by callee;
+  // callers come out ascending because edges are listed by caller
+  MM_CUDA_TRY(cudaMemsetAsync(s->fan_in, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(M, 1), st));
+  if (E > 0) {
+    fan_in_hist<<<grid_for(E), TPB, 0, st>>>(s->call_idx, E, s->fan_in);
+    MM_LAUNCH_CHECK();
+  }
+  scan_exclusive_i32to64(s->fan_in, s->caller_rowptr, M, s->sort_ws, st);
+  set_i64<<<1, 1, 0, st>>>(s->caller_rowptr + M, E);
+  MM_LAUNCH_CHECK();
+  if (E > 0) {
+    copy_i32_to_u32<<<grid_for(E), TPB, 0, st>>>(s->call_idx, k, E);
+    expand_callers<<<grid_for(M), TPB, 0, st>>>(s->call_rowptr, s->M, v);
+    MM_LAUNCH_CHECK();
+    radix_sort_u32(k, ka, v, va, E, mbits, s->sort_ws, st);
+    MM_CUDA_TRY(cudaMemcpyAsync(s->caller_idx, v, sizeof(uint32_t) * (size_t)E, cudaMemcpyDeviceToDevice, st));
+  }
+}

@@ -1,0 +1,259 @@
+"""Python binding of the mmref C ABI (``include/mmref.h``): argument
+marshalling only.  Every step of the path runs in the CUDA library
+``libmmref.so``; there is no CPU fallback -- importing this module without the
+built library raises.
+
+Device memory and streams come from PyTorch: device inputs/outputs are CUDA
+tensors (passed by ``data_ptr()``), the stream is
+``torch.cuda.current_stream().cuda_stream`` unless one is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmmref.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"mmref: {LIB_PATH} is missing; build it with `python -m paper_1308_4011_b300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ENOTFOUND, MM_EEXIST, MM_ETIMEOUT, MM_EBUDGET = range(8)
+PTR_HOST, PTR_DEVICE = 0, 1
+LCOM_CK, LCOM_HS, CBO = 1, 2, 4
+# default criteria: LCOM only (both forms), improve source and target (Table I's mode)
+DEFAULT_MASK = LCOM_CK | LCOM_HS
+DEFAULT_MIN_IMPROVED = 2
+
+EXPORTED = ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluate_moves", "mm_suggest_moves",
+            "mm_system_info_get", "mm_free_system", "mm_last_error", "mm_status_string", "mm_abi_version",
+            "mm_launch_count")
+
+CLASS_METRICS_DTYPE = np.dtype([("n_methods", "<i4"), ("n_attrs", "<i4"), ("P", "<i8"), ("Q", "<i8"),
+                                ("S", "<i8"), ("lcom_ck", "<i8"), ("hs_num", "<i8"), ("hs_den", "<i8"),
+                                ("cbo", "<i4"), ("reserved", "<i4")])
+METHOD_METRICS_DTYPE = np.dtype([("fan_in", "<i4"), ("fan_out", "<i4"), ("own", "<i4"), ("q", "<i4")])
+MOVE_EVAL_DTYPE = np.dtype([("s", "<i4"), ("t", "<u2"), ("dcbo_src", "<i2"), ("dcbo_dst", "<i2"),
+                            ("n_improved", "<u2"), ("n_worsened", "<u2"), ("flags", "<u2")])
+MOVE_DTYPE = np.dtype([("m", "<i4"), ("d", "<i4"), ("n_improved", "<i4"), ("d_lcom_ck_sum", "<i4"),
+                       ("d_cbo_sum", "<i4"), ("reserved", "<i4")])
+assert CLASS_METRICS_DTYPE.itemsize == 64 and MOVE_EVAL_DTYPE.itemsize == 16 and MOVE_DTYPE.itemsize == 24
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("n_classes", ctypes.c_int32), ("n_methods", ctypes.c_int32), ("n_attrs", ctypes.c_int32),
+                ("ptr_kind", ctypes.c_int32), ("n_acc", ctypes.c_int64), ("n_call", ctypes.c_int64),
+                ("method_class", ctypes.c_void_p), ("attr_class", ctypes.c_void_p),
+                ("acc_rowptr", ctypes.c_void_p), ("acc_idx", ctypes.c_void_p),
+                ("call_rowptr", ctypes.c_void_p), ("call_idx", ctypes.c_void_p),
+                ("cbo_attrs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _Crit(ctypes.Structure):
+    _fields_ = [("metric_mask", ctypes.c_uint32), ("min_improved", ctypes.c_int32)]
+
+
+class _Cands(ctypes.Structure):
+    _fields_ = [("rowptr", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("n_cand", ctypes.c_int64),
+                ("ptr_kind", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_classes", ctypes.c_int32), ("n_methods", ctypes.c_int32), ("n_attrs", ctypes.c_int32),
+                ("cbo_attrs", ctypes.c_int32), ("n_acc", ctypes.c_int64), ("n_call", ctypes.c_int64),
+                ("n_class_edges", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_lib.mm_load_system.argtypes = [ctypes.POINTER(_Desc), _vp, ctypes.POINTER(_vp)]
+_lib.mm_set_stream.argtypes = [_vp, _vp]
+_lib.mm_compute_metrics.argtypes = [_vp, _vp, _vp, ctypes.c_int32]
+_lib.mm_evaluate_moves.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.POINTER(_Cands), _vp, _vp, ctypes.c_int32]
+_lib.mm_suggest_moves.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.POINTER(_Cands), ctypes.c_int32, _vp,
+                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+_lib.mm_system_info_get.argtypes = [_vp, ctypes.POINTER(_Info)]
+_lib.mm_free_system.argtypes = [_vp]
+_lib.mm_free_system.restype = None
+_lib.mm_last_error.restype = ctypes.c_char_p
+_lib.mm_status_string.argtypes = [ctypes.c_int]
+_lib.mm_status_string.restype = ctypes.c_char_p
+_lib.mm_abi_version.restype = ctypes.c_int32
+_lib.mm_launch_count.restype = ctypes.c_int64
+for _n in ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluate_moves", "mm_suggest_moves",
+           "mm_system_info_get"):
+    getattr(_lib, _n).restype = ctypes.c_int
+
+
+class MMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.mm_status_string(status).decode()}: {msg}")
+        self.status = status
+
+
+def _check(st: int):
+    if st != MM_OK:
+        raise MMError(st, _lib.mm_last_error().decode())
+
+
+def abi_version() -> int:
+    return int(_lib.mm_abi_version())
+
+
+def launch_count() -> int:
+    """Kernels launched by libmmref.so in this process so far."""
+    return int(_lib.mm_launch_count())
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None for None / empty)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr() if a.numel() else None
+    return a.ctypes.data if a.size else None
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _kind(x) -> int:
+    if hasattr(x, "is_cuda"):
+        return PTR_DEVICE if x.is_cuda else PTR_HOST
+    return PTR_HOST
+
+
+class System:
+    """A loaded system (owns device memory until ``free()``)."""
+
+    def __init__(self, handle, n_classes, n_methods, n_attrs, keepalive):
+        self._h = ctypes.c_void_p(handle)
+        self.n_classes, self.n_methods, self.n_attrs = n_classes, n_methods, n_attrs
+        self._keep = keepalive
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            _lib.mm_free_system(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        inf = _Info()
+        _check(_lib.mm_system_info_get(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in _Info._fields_}
+
+    def set_stream(self, stream):
+        _check(_lib.mm_set_stream(self._h, _stream_handle(stream)))
+
+    @property
+    def n_candidates_full(self) -> int:
+        return self.n_methods * (self.n_classes - 1)
+
+
+def load_system(n_classes, method_class, attr_class, acc_rowptr, acc_idx, call_rowptr, call_idx, *,
+                cbo_attrs: bool = True, stream=None) -> System:
+    """mm_load_system.  Arrays are either all numpy (host) or all CUDA tensors."""
+    arrs = (method_class, attr_class, acc_rowptr, acc_idx, call_rowptr, call_idx)
+    kinds = {_kind(a) for a in arrs}
+    if len(kinds) != 1:
+        raise ValueError("load_system: all arrays must be host (numpy) or all device (CUDA tensors)")
+    kind = kinds.pop()
+    if kind == PTR_HOST:
+        arrs = tuple(np.ascontiguousarray(a, dtype=dt) for a, dt in
+                     zip(arrs, (np.int32, np.int32, np.int64, np.int32, np.int64, np.int32)))
+    n_methods = int(arrs[0].shape[0])
+    d = _Desc(int(n_classes), n_methods, int(arrs[1].shape[0]), kind, int(arrs[3].shape[0]), int(arrs[5].shape[0]),
+              _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), _ptr(arrs[3]), _ptr(arrs[4]), _ptr(arrs[5]),
+              1 if cbo_attrs else 0, 0)
+    h = ctypes.c_void_p()
+    _check(_lib.mm_load_system(ctypes.byref(d), _stream_handle(stream), ctypes.byref(h)))
+    return System(h.value, int(n_classes), n_methods, int(arrs[1].shape[0]), arrs)
+
+
+def load_synth(system, *, cbo_attrs: bool = True, device: bool = False, stream=None) -> System:
+    """Load a ``synth.System``; with device=True the arrays are first moved to
+    CUDA tensors (the inputs-resident-in-HBM form)."""
+    arrs = (system.method_class, system.attr_class, system.acc_rowptr, system.acc_idx, system.call_rowptr,
+            system.call_idx)
+    if device:
+        import torch
+        arrs = tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs)
+    return load_system(system.n_classes, *arrs, cbo_attrs=cbo_attrs, stream=stream)
+
+
+def compute_metrics(sys: System, out_class=None, out_method=None):
+    """mm_compute_metrics.  out_* are optional buffers: numpy arrays of
+    CLASS_METRICS_DTYPE / METHOD_METRICS_DTYPE, or CUDA uint8 tensors of
+    64*n_classes / 16*n_methods bytes.  Pass the string "host" to get new
+    numpy arrays back."""
+    if isinstance(out_class, str):
+        out_class = np.zeros(sys.n_classes, dtype=CLASS_METRICS_DTYPE)
+    if isinstance(out_method, str):
+        out_method = np.zeros(sys.n_methods, dtype=METHOD_METRICS_DTYPE)
+    outs = [o for o in (out_class, out_method) if o is not None]
+    kind = _kind(outs[0]) if outs else PTR_HOST
+    if any(_kind(o) != kind for o in outs):
+        raise ValueError("compute_metrics: outputs must be both host or both device")
+    _check(_lib.mm_compute_metrics(sys.handle, _ptr(out_class), _ptr(out_method), kind))
+    return out_class, out_method
+
+
+def _cands(cand_rowptr, cand_dst):
+    if cand_rowptr is None:
+        return None, None
+    kind = _kind(cand_rowptr)
+    if kind == PTR_HOST:
+        cand_rowptr = np.ascontiguousarray(cand_rowptr, dtype=np.int64)
+        cand_dst = np.ascontiguousarray(cand_dst, dtype=np.int32)
+    n = int(cand_dst.shape[0])
+    c = _Cands(_ptr(cand_rowptr), _ptr(cand_dst), n, kind, 0)
+    return c, (cand_rowptr, cand_dst)
+
+
+def evaluate_moves(sys: System, mask: int = DEFAULT_MASK, min_improved: int = DEFAULT_MIN_IMPROVED,
+                   cand_rowptr=None, cand_dst=None, records=None, digest=None):
+    """mm_evaluate_moves.  records: a numpy array of MOVE_EVAL_DTYPE or a CUDA
+    uint8 tensor of 16*n_cand bytes (or None).  digest: a 1-element numpy
+    uint64 array or CUDA int64 tensor (or None).  Both in the same memory."""
+    crit = _Crit(mask, min_improved)
+    cd, keep = _cands(cand_rowptr, cand_dst)
+    outs = [o for o in (records, digest) if o is not None]
+    kind = _kind(outs[0]) if outs else PTR_DEVICE
+    if any(_kind(o) != kind for o in outs):
+        raise ValueError("evaluate_moves: records and digest must be in the same memory")
+    _check(_lib.mm_evaluate_moves(sys.handle, ctypes.byref(crit), ctypes.byref(cd) if cd else None,
+                                  _ptr(records), _ptr(digest), kind))
+    del keep
+    return records, digest
+
+
+def suggest_moves(sys: System, k: int, mask: int = DEFAULT_MASK, min_improved: int = DEFAULT_MIN_IMPROVED,
+                  cand_rowptr=None, cand_dst=None, out=None):
+    """mm_suggest_moves.  Returns (top-k moves as a MOVE_DTYPE numpy array, or
+    the given out buffer), n_kept, n_methods_with_kept."""
+    crit = _Crit(mask, min_improved)
+    cd, keep = _cands(cand_rowptr, cand_dst)
+    if out is None:
+        out = np.zeros(max(k, 0), dtype=MOVE_DTYPE)
+    nk, nm = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.mm_suggest_moves(sys.handle, ctypes.byref(crit), ctypes.byref(cd) if cd else None, int(k),
+                                 _ptr(out), _kind(out), ctypes.byref(nk), ctypes.byref(nm)))
+    del keep
+    n = min(int(k), int(nk.value))
+    return (out[:n] if _kind(out) == PTR_HOST else out), int(nk.value), int(nm.value)

@@ -1,0 +1,408 @@
+"""GPU parity: every output of the CUDA path, through the C ABI, equals the
+CPU oracle bit for bit (all outputs are integers).  The oracle itself is pinned
+by tests/test_oracle_pins.py."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import brute
+from paper_1308_4011_b300 import synth
+
+from sysutil import make_system, moved, permute, tiny_random
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU machines deselect with -m "not gpu"
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1308_4011_b300 import mmref  # noqa: E402  (loads libmmref.so; no fallback)
+
+CLASS_MAP = {"n_methods": "n", "n_attrs": "a", "P": "P", "Q": "Q", "S": "S", "lcom_ck": "ck",
+             "hs_num": "hs_num", "hs_den": "hs_den", "cbo": "cbo"}
+CRITERIA = [(7, 2), (3, 2), (1, 1), (4, 1), (6, 1), (2, 2)]
+
+
+def gpu_load(sys_, cbo_attrs=True, device=False):
+    s = mmref.load_synth(sys_, cbo_attrs=cbo_attrs, device=device)
+    cm, mm_ = mmref.compute_metrics(s, "host", "host")
+    return s, cm, mm_
+
+
+def check_metrics(sys_, o, cm, mm_):
+    ocm, omm = o.class_metrics(), o.method_metrics()
+    for g, f in CLASS_MAP.items():
+        assert np.array_equal(cm[g].astype(np.int64), ocm[f]), g
+    for f in ("fan_in", "fan_out", "own", "q"):
+        assert np.array_equal(mm_[f], omm[f]), f
+
+
+def gpu_records(s, mask, mi, rowptr=None, dst=None):
+    n = s.n_candidates_full if rowptr is None else len(dst)
+    rec = torch.empty(max(n, 1) * 16, dtype=torch.uint8, device="cuda")
+    dig = torch.zeros(1, dtype=torch.int64, device="cuda")
+    mmref.evaluate_moves(s, mask, mi, rowptr, dst, records=rec, digest=dig)
+    torch.cuda.synchronize()
+    r = rec[: n * 16].cpu().numpy().view(mmref.MOVE_EVAL_DTYPE)
+    return r, int(dig.cpu().numpy().view(np.uint64)[0])
+
+
+def gpu_digest(s, mask, mi, rowptr=None, dst=None):
+    dig = np.zeros(1, dtype=np.uint64)
+    mmref.evaluate_moves(s, mask, mi, rowptr, dst, digest=dig)
+    return int(dig[0])
+
+
+def kept_tuples(arr, names=("m", "d", "n_improved", "d_lcom_ck_sum", "d_cbo_sum")):
+    return [tuple(int(x[f]) for f in names) for x in arr]
+
+
+def oracle_kept(res):
+    return [tuple(int(x[f]) for f in ("m", "d", "n_improved", "d_ck_sum", "d_cbo_sum")) for x in res.kept]
+
+
+def same_records(gpu, orc):
+    return np.array_equal(np.ascontiguousarray(gpu).view(np.uint8), np.ascontiguousarray(orc).view(np.uint8))
+
+
+# ---------------------------------------------------------------- tiny workload
+
+@pytest.fixture(scope="module")
+def tiny():
+    s = synth.named("tiny")
+    return s, oracle.Oracle(s), oracle.Oracle(s, cbo_attrs=False)
+
+
+@pytest.mark.parametrize("cbo_attrs", [True, False])
+def test_tiny_metrics(tiny, cbo_attrs):
+    s, o1, o2 = tiny
+    g, cm, mm_ = gpu_load(s, cbo_attrs=cbo_attrs)
+    check_metrics(s, o1 if cbo_attrs else o2, cm, mm_)
+    assert g.info()["n_class_edges"] == len(o1.multigraph()[1] if cbo_attrs else o2.multigraph()[1])
+
+
+@pytest.mark.parametrize("mask,mi", CRITERIA)
+def test_tiny_every_record(tiny, mask, mi):
+    """All 398,000 candidates of the tiny workload, record by record."""
+    s, o, _ = tiny
+    g, _, _ = gpu_load(s)
+    rec, dig = gpu_records(g, mask, mi)
+    ref = o.evaluate(mask=mask, min_improved=mi, method=1, records=True)
+    assert rec.shape[0] == ref.n_cand == 2000 * 199
+    assert same_records(rec, ref.records)
+    assert dig == ref.digest
+    assert gpu_digest(g, mask, mi) == ref.digest
+
+
+def test_tiny_records_vs_recompute(tiny):
+    """Against O0, the recompute-after-move oracle, on every candidate."""
+    s, o, _ = tiny
+    g, _, _ = gpu_load(s)
+    rec, dig = gpu_records(g, 7, 2)
+    ref = o.evaluate(mask=7, min_improved=2, method=0, records=True)
+    assert same_records(rec, ref.records) and dig == ref.digest
+
+
+@pytest.mark.parametrize("mask,mi", CRITERIA)
+def test_tiny_suggestions(tiny, mask, mi):
+    s, o, _ = tiny
+    g, _, _ = gpu_load(s)
+    ref = o.evaluate(mask=mask, min_improved=mi, method=1)
+    top, nk, nm = mmref.suggest_moves(g, k=ref.n_kept + 5, mask=mask, min_improved=mi)
+    assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+    assert kept_tuples(top) == oracle_kept(ref)
+    top10, nk2, _ = mmref.suggest_moves(g, k=10, mask=mask, min_improved=mi)
+    assert nk2 == nk and kept_tuples(top10) == oracle_kept(ref)[:10]
+
+
+def test_tiny_device_inputs_and_outputs(tiny):
+    s, o, _ = tiny
+    g = mmref.load_synth(s, device=True)
+    cm = torch.empty(s.n_classes * 64, dtype=torch.uint8, device="cuda")
+    mm_ = torch.empty(s.n_methods * 16, dtype=torch.uint8, device="cuda")
+    mmref.compute_metrics(g, cm, mm_)
+    check_metrics(s, o, cm.cpu().numpy().view(mmref.CLASS_METRICS_DTYPE),
+                  mm_.cpu().numpy().view(mmref.METHOD_METRICS_DTYPE))
+    out = torch.empty(50 * 24, dtype=torch.uint8, device="cuda")
+    _, nk, _ = mmref.suggest_moves(g, k=50, out=out)
+    ref = o.evaluate(mask=3, min_improved=2)
+    n = min(50, nk)
+    assert kept_tuples(out.cpu().numpy().view(mmref.MOVE_DTYPE)[:n]) == oracle_kept(ref)[:n]
+
+
+def test_tiny_restricted_equals_dense(tiny):
+    """The CSR kernel on the full cross product written as a list equals the dense kernel."""
+    s, o, _ = tiny
+    g, _, _ = gpu_load(s)
+    c = s.n_classes
+    rowptr = np.arange(s.n_methods + 1, dtype=np.int64) * (c - 1)
+    dst = np.concatenate([np.delete(np.arange(c, dtype=np.int32), s.method_class[m]) for m in range(s.n_methods)])
+    a, da = gpu_records(g, 7, 1)
+    b, db = gpu_records(g, 7, 1, rowptr, dst)
+    assert same_records(a, b) and da == db
+    # device-resident candidate list too
+    b2, db2 = gpu_records(g, 7, 1, torch.from_numpy(rowptr).cuda(), torch.from_numpy(dst).cuda())
+    assert same_records(a, b2) and da == db2
+
+
+# ---------------------------------------------------------------- tiny random systems, brute-force pinned
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_tiny_vs_brute_force(seed):
+    s = tiny_random(seed)
+    for cbo_attrs in (True, False):
+        g, cm, mm_ = gpu_load(s, cbo_attrs=cbo_attrs)
+        o = oracle.Oracle(s, cbo_attrs=cbo_attrs, threads=1)
+        check_metrics(s, o, cm, mm_)
+        for mask, mi in ((7, 2), (3, 2), (7, 1)):
+            ev = brute.evaluate(s, mask=mask, min_improved=mi, cbo_attrs=cbo_attrs)
+            rec, dig = gpu_records(g, mask, mi)
+            assert dig == brute.digest(ev)
+            exp = [tuple(ev[(m, D)][f] for f in mmref.MOVE_EVAL_DTYPE.names)
+                   for m in range(s.n_methods) for D in range(s.n_classes) if D != s.method_class[m]]
+            assert [tuple(int(v) for v in r) for r in rec] == exp
+            top, nk, _ = mmref.suggest_moves(g, k=1000, mask=mask, min_improved=mi)
+            assert kept_tuples(top) == brute.suggestions(ev)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def _eval_all_ways(sys_, cbo_attrs=True):
+    g, cm, mm_ = gpu_load(sys_, cbo_attrs=cbo_attrs)
+    o = oracle.Oracle(sys_, cbo_attrs=cbo_attrs, threads=1)
+    check_metrics(sys_, o, cm, mm_)
+    for mask, mi in ((7, 2), (7, 1), (3, 1)):
+        ref = o.evaluate(mask=mask, min_improved=mi, method=0, records=True)
+        if g.n_candidates_full:
+            rec, dig = gpu_records(g, mask, mi)
+            assert same_records(rec, ref.records) and dig == ref.digest
+        top, nk, nm = mmref.suggest_moves(g, k=100000, mask=mask, min_improved=mi)
+        assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+        assert kept_tuples(top) == oracle_kept(ref)
+
+
+def test_single_class_has_no_candidates():
+    s = make_system([0, 0, 0], [0, 0], [[0], [0, 1], []], [[1], [2], []], n_classes=1)
+    g, cm, _ = gpu_load(s)
+    assert g.n_candidates_full == 0
+    assert (cm["P"][0], cm["Q"][0]) == (2, 1)
+    _, dig = np.zeros(0), gpu_digest(g, 7, 2)
+    assert dig == 0
+    top, nk, nm = mmref.suggest_moves(g, k=5)
+    assert (len(top), nk, nm) == (0, 0, 0)
+
+
+def test_empty_classes_and_no_attributes():
+    """Classes without methods (moves into an empty class), no attributes at all."""
+    s = make_system([0, 0, 2, 2, 2], [], [[], [], [], [], []], [[1, 2], [], [0], [], [1]], n_classes=4)
+    _eval_all_ways(s)
+
+
+def test_emptying_a_class_and_methods_without_accesses():
+    s = make_system([0, 1, 1, 2, 3, 3, 3], [1, 1, 3, 0], [[0, 1], [], [1], [2, 3], [2], [], [0]],
+                    [[1], [0], [], [4, 5], [], [6], [3]], n_classes=5)
+    _eval_all_ways(s)
+    _eval_all_ways(s, cbo_attrs=False)
+
+
+@pytest.mark.parametrize("c", [31, 33, 257, 300])
+def test_ragged_class_counts(c):
+    """Class counts off the 32-lane and 256-thread grids (ragged D tiles)."""
+    s = synth.generate(c, 6 * c, 3 * c, max_class=40, seed=c, lambda_acc=3, lambda_call=3, p_loc=0.6)
+    g, cm, mm_ = gpu_load(s)
+    o = oracle.Oracle(s)
+    check_metrics(s, o, cm, mm_)
+    rec, dig = gpu_records(g, 7, 1)
+    ref = o.evaluate(mask=7, min_improved=1, method=1, records=True)
+    assert same_records(rec, ref.records) and dig == ref.digest
+
+
+def test_large_class_multi_tile_lcom():
+    """A class of 300 methods and 100 attributes (10 x 10 pair tiles, 4 words per row)."""
+    rng = np.random.default_rng(7)
+    n, a = 300, 100
+    acc = [sorted(rng.choice(a, size=rng.integers(0, 6), replace=False).tolist()) for _ in range(n)]
+    s = make_system([0] * n + [1] * 5, [0] * a + [1] * 3, acc + [[a], [a + 1], [], [a, a + 2], [0]],
+                    [[] for _ in range(n + 5)], n_classes=2)
+    g, cm, mm_ = gpu_load(s)
+    check_metrics(s, oracle.Oracle(s), cm, mm_)
+
+
+def test_relabelled_system_gives_permuted_results():
+    s = tiny_random(5)
+    p, pc, pm, pa = permute(s, 3)
+    _, cm, mm_ = gpu_load(s)
+    _, cmp_, mmp = gpu_load(p)
+    assert np.array_equal(cmp_[pc], cm)
+    assert np.array_equal(mmp[pm], mm_)
+
+
+def test_move_then_move_back_on_gpu():
+    s = synth.named("tiny")
+    g, cm, _ = gpu_load(s)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        m = int(rng.integers(s.n_methods))
+        C = int(s.method_class[m])
+        D = int(rng.integers(s.n_classes - 1))
+        D += D >= C
+        rp = np.zeros(s.n_methods + 1, dtype=np.int64)
+        rp[m + 1:] = 1
+        fwd, _ = gpu_records(g, 7, 1, rp, np.array([D], dtype=np.int32))
+        g2, cm2, _ = gpu_load(moved(s, m, D))
+        assert cm2["cbo"][C] == cm["cbo"][C] + fwd["dcbo_src"][0]
+        assert cm2["cbo"][D] == cm["cbo"][D] + fwd["dcbo_dst"][0]
+        assert cm2["Q"][D] == cm["Q"][D] + fwd["s"][0]
+        assert cm2["S"][D] == cm["S"][D] + fwd["t"][0]
+        rp2 = rp.copy()
+        back, _ = gpu_records(g2, 7, 1, rp2, np.array([C], dtype=np.int32))
+        assert back["dcbo_src"][0] == -fwd["dcbo_dst"][0] and back["dcbo_dst"][0] == -fwd["dcbo_src"][0]
+
+
+# ---------------------------------------------------------------- invalid input
+
+def _bad(**kw):
+    s = synth.generate(10, 40, 20, max_class=10, seed=1)
+    arrs = dict(method_class=s.method_class.copy(), attr_class=s.attr_class.copy(),
+                acc_rowptr=s.acc_rowptr.copy(), acc_idx=s.acc_idx.copy(), call_rowptr=s.call_rowptr.copy(),
+                call_idx=s.call_idx.copy())
+    for k, f in kw.items():
+        f(arrs[k])
+    return arrs
+
+
+@pytest.mark.parametrize("name,edit,msg", [
+    ("method_class", lambda a: a.__setitem__(3, 10), "method_class"),
+    ("attr_class", lambda a: a.__setitem__(0, -1), "attr_class"),
+    ("acc_idx", lambda a: a.__setitem__(0, 999), "acc_idx"),
+    ("call_idx", lambda a: a.__setitem__(0, 4000), "call_idx"),
+    ("acc_rowptr", lambda a: a.__setitem__(-1, a[-1] - 1), "acc_rowptr"),
+])
+def test_invalid_systems_rejected(name, edit, msg):
+    arrs = _bad(**{name: edit})
+    with pytest.raises(mmref.MMError) as e:
+        mmref.load_system(10, **arrs)
+    assert e.value.status == mmref.MM_EINVAL and msg in str(e.value)
+
+
+def test_unsorted_and_self_calls_rejected():
+    s = synth.generate(10, 40, 20, max_class=10, seed=1)
+    x = int(np.argmax(np.diff(s.call_rowptr) >= 2))
+    ci = s.call_idx.copy()
+    a, b = s.call_rowptr[x], s.call_rowptr[x] + 1
+    ci[a], ci[b] = ci[b], ci[a]
+    with pytest.raises(mmref.MMError, match="strictly increasing"):
+        mmref.load_system(10, s.method_class, s.attr_class, s.acc_rowptr, s.acc_idx, s.call_rowptr, ci)
+    ci = s.call_idx.copy()
+    ci[s.call_rowptr[x]] = x
+    ci[s.call_rowptr[x]:s.call_rowptr[x + 1]].sort()
+    with pytest.raises(mmref.MMError):
+        mmref.load_system(10, s.method_class, s.attr_class, s.acc_rowptr, s.acc_idx, s.call_rowptr, ci)
+
+
+def test_invalid_candidates_and_criteria_rejected():
+    s = synth.generate(10, 40, 20, max_class=10, seed=1)
+    g, _, _ = gpu_load(s)
+    rp = np.zeros(41, dtype=np.int64)
+    rp[1:] = 1
+    with pytest.raises(mmref.MMError, match="own class"):
+        mmref.evaluate_moves(g, 7, 2, rp, np.array([s.method_class[0]], dtype=np.int32), digest=np.zeros(1, np.uint64))
+    with pytest.raises(mmref.MMError, match="out of range"):
+        mmref.evaluate_moves(g, 7, 2, rp, np.array([10], dtype=np.int32), digest=np.zeros(1, np.uint64))
+    with pytest.raises(mmref.MMError, match="metric_mask"):
+        mmref.suggest_moves(g, 5, mask=0)
+    with pytest.raises(mmref.MMError, match="min_improved"):
+        mmref.suggest_moves(g, 5, mask=7, min_improved=0)
+    # the system is still usable after the errors
+    assert gpu_digest(g, 7, 2) == oracle.Oracle(s).evaluate(mask=7, min_improved=2).digest
+
+
+# ---------------------------------------------------------------- full-size workloads
+
+@pytest.fixture(scope="module")
+def medium():
+    s = synth.named("medium")
+    return s, oracle.Oracle(s)
+
+
+def test_medium_metrics(medium):
+    s, o = medium
+    _, cm, mm_ = gpu_load(s, device=True)
+    check_metrics(s, o, cm, mm_)
+
+
+def test_medium_full_cross_product(medium):
+    """299,940,000 candidates: the digest of every record equals the oracle's,
+    dense records on the device, in the launch configuration the benchmark uses;
+    sampled records equal the recompute oracle one by one."""
+    s, o = medium
+    g, _, _ = gpu_load(s, device=True)
+    n = g.n_candidates_full
+    assert n == 60000 * 4999
+    rec = torch.empty(n * 16, dtype=torch.uint8, device="cuda")
+    dig = torch.zeros(1, dtype=torch.int64, device="cuda")
+    mmref.evaluate_moves(g, 3, 2, records=rec, digest=dig)
+    ref = o.evaluate(mask=3, min_improved=2, method=1)
+    assert int(dig.cpu().numpy().view(np.uint64)[0]) == ref.digest
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(n, size=400, replace=False))
+    recs = rec.view(-1, 16)[torch.from_numpy(idx).cuda()].cpu().numpy().reshape(-1).view(mmref.MOVE_EVAL_DTYPE)
+    c = s.n_classes
+    for i, r in zip(idx, recs):
+        m, j = divmod(int(i), c - 1)
+        D = j + (j >= s.method_class[m])
+        exp, _, _ = o.evaluate_one(m, D, mask=3, min_improved=2, method=0)
+        assert same_records(np.array([r]), np.array([exp])), (m, D)
+    del rec
+    top, nk, nm = mmref.suggest_moves(g, k=ref.n_kept, mask=3, min_improved=2)
+    assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+    assert kept_tuples(top) == oracle_kept(ref)
+
+
+def test_medium_host_buffers_path(medium):
+    """The end-to-end form: host CSR in, host results out."""
+    s, o = medium
+    g = mmref.load_synth(s)
+    cm, _ = mmref.compute_metrics(g, "host", None)
+    assert np.array_equal(cm["cbo"].astype(np.int64), o.class_metrics()["cbo"])
+    dig = np.zeros(1, dtype=np.uint64)
+    mmref.evaluate_moves(g, 7, 2, digest=dig)
+    assert int(dig[0]) == o.evaluate(mask=7, min_improved=2).digest
+
+
+@pytest.fixture(scope="module")
+def large():
+    s = synth.named("large")
+    rp, dst = synth.candidates(s, synth.LARGE_EXTRA_CANDIDATES, seed=2)
+    return s, rp, dst, oracle.Oracle(s)
+
+
+def test_large_metrics(large):
+    s, _, _, o = large
+    _, cm, mm_ = gpu_load(s, device=True)
+    check_metrics(s, o, cm, mm_)
+
+
+def test_large_restricted_candidates(large):
+    s, rp, dst, o = large
+    g, _, _ = gpu_load(s, device=True)
+    rpd, dd = torch.from_numpy(rp).cuda(), torch.from_numpy(dst).cuda()
+    n = len(dst)
+    rec = torch.empty(n * 16, dtype=torch.uint8, device="cuda")
+    dig = torch.zeros(1, dtype=torch.int64, device="cuda")
+    mmref.evaluate_moves(g, 7, 1, rpd, dd, records=rec, digest=dig)
+    ref = o.evaluate(mask=7, min_improved=1, cand_rowptr=rp, cand_dst=dst, method=1)
+    assert int(dig.cpu().numpy().view(np.uint64)[0]) == ref.digest
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(n, size=300, replace=False))
+    recs = rec.view(-1, 16)[torch.from_numpy(idx).cuda()].cpu().numpy().reshape(-1).view(mmref.MOVE_EVAL_DTYPE)
+    rows = np.searchsorted(rp, idx, side="right") - 1
+    for i, m, r in zip(idx, rows, recs):
+        exp, _, _ = o.evaluate_one(int(m), int(dst[i]), mask=7, min_improved=1, method=0)
+        assert same_records(np.array([r]), np.array([exp])), (m, dst[i])
+    top, nk, nm = mmref.suggest_moves(g, k=min(ref.n_kept, 5000), mask=7, min_improved=1, cand_rowptr=rpd,
+                                      cand_dst=dd)
+    assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+    assert kept_tuples(top) == oracle_kept(ref)[:5000]
