@@ -124,6 +124,8 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     seed_offset = 1000 * rank  # independent replica per rank (weak scaling)
     params = dict(synth.MEDIUM)
+    if args.case == "small":  # profiling case: medium degrees and locality, 1,000 classes x 12,000 methods
+        params.update(n_classes=1000, n_methods=12000, n_attrs=6000, max_class=80)
     params["seed"] = params["seed"] + seed_offset
     system = synth.generate(**params, name="medium")
     c, M = system.n_classes, system.n_methods
@@ -223,10 +225,11 @@ def run_ours(args, rank, world, local_rank):
             "kernel": "eval_dense<records>", "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
             "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(eval_s * 1e3, 4)}
     cpu = cpu_baseline(system, mask, min_imp) if (rank == 0 and not args.no_cpu_baseline) else None
+    workload = WORKLOAD if args.case == "medium" else "PROFILING CASE (not the bench workload): " + WORKLOAD
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32/int64", "data": "synthetic (seeded generator; no datasets)",
-            "config": {"workload": WORKLOAD, "n_classes": c, "n_methods": M, "n_attrs": system.n_attrs,
+            "config": {"workload": workload, "n_classes": c, "n_methods": M, "n_attrs": system.n_attrs,
                        "candidates_per_step": n_cand, "criteria": {"metric_mask": mask, "min_improved": min_imp},
                        "topk": TOPK, "parallelism": f"replicas x{world}",
                        "l2": "512 MB L2 flush between steps (outside events); each step also writes 4.8 GB"},
@@ -329,6 +332,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["medium", "small"], default="medium",
+                    help="small = profiling case (1,000 classes, 12,000 methods, 192 MB of records); "
+                         "not a bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

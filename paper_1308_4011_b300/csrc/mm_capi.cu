@@ -79,7 +79,7 @@ void allocate_compute_buffers(mm_system *s) {
   s->mg_dst = a.get<int32_t>(nu);
   s->mg_cnt = a.get<int32_t>(nu);
   s->mg_count = a.get<int64_t>(2);
-  s->adj_words = (c + 31) / 32;
+  s->adj_words = ((c + 127) / 128) * 4;  // rows padded to 16 bytes for vector loads
   s->out_adj = a.get<uint32_t>(s->adj_words * c);
   s->in_adj = a.get<uint32_t>(s->adj_words * c);
   s->hdr = a.get<MoveHdr>(M);
@@ -235,6 +235,7 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     s->sort_ws.release(s->stream);
     s->eval_ws.release(s->stream);
     s->stage_ws.release(s->stream);
+    s->kept_ws.release(s->stream);
     cudaStreamSynchronize(s->stream);
     delete s;
     if (out) *out = nullptr;
@@ -266,6 +267,7 @@ mm_status mm_compute_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_me
     if ((out_c || out_m) && out_kind != MM_PTR_HOST && out_kind != MM_PTR_DEVICE)
       throw MmError{MM_EINVAL, "compute_metrics: bad out_kind"};
     use_device(s);
+    s->kept_valid = false;
     build_structures(s);
     build_metrics(s);
     build_move_precompute(s);
@@ -311,7 +313,8 @@ mm_status mm_system_info_get(mm_system *s, mm_system_info *info) {
       MM_CUDA_TRY(cudaStreamSynchronize(s->stream));
       info->n_class_edges = v;
     }
-    info->device_bytes = s->arena.bytes + (int64_t)(s->sort_ws.cap + s->eval_ws.cap + s->stage_ws.cap);
+    info->device_bytes =
+        s->arena.bytes + (int64_t)(s->sort_ws.cap + s->eval_ws.cap + s->stage_ws.cap + s->kept_ws.cap);
   });
 }
 
@@ -325,6 +328,7 @@ void mm_free_system(mm_system *s) {
   s->sort_ws.release(s->stream);
   s->eval_ws.release(s->stream);
   s->stage_ws.release(s->stream);
+  s->kept_ws.release(s->stream);
   delete s;
   if (cur >= 0 && cur != dev) cudaSetDevice(cur);
 }

@@ -113,6 +113,11 @@ struct mm_system {
   Scratch sort_ws;     // radix-sort / scan scratch
   Scratch eval_ws;     // evaluate/suggest scratch (kept lists, staging)
   Scratch stage_ws;    // host-output staging
+  Scratch kept_ws;     // kept moves + per-method marks of the last evaluation
+  bool kept_valid = false;   // kept_ws holds the full cross product's kept moves for:
+  uint32_t kept_mask = 0;    //   this metric mask
+  int32_t kept_min = 0;      //   and this min_improved
+  int64_t kept_cap = 0;
 
   // inputs
   int32_t *method_class, *attr_class, *acc_idx, *call_idx;

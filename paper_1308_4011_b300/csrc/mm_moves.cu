@@ -331,6 +331,8 @@ namespace {
 struct DState {
   int32_t D, nD, aD;
   int64_t diffD, SD, ckD;
+  // target-side LCOM outcome when m shares nothing with D (t = s = 0), the common case
+  int32_t sck0, shs0, dck0;
 };
 
 __device__ __forceinline__ DState load_dstate(int32_t D, const int32_t *cls_n, const int32_t *cls_a,
@@ -342,6 +344,11 @@ __device__ __forceinline__ DState load_dstate(int32_t D, const int32_t *cls_n, c
   d.diffD = cls_P[D] - cls_Q[D];
   d.SD = cls_S[D];
   d.ckD = d.diffD > 0 ? d.diffD : 0;
+  int64_t diff2 = d.diffD + d.nD;
+  int64_t ck2 = diff2 > 0 ? diff2 : 0;
+  d.sck0 = sgn64(ck2 - d.ckD);
+  d.dck0 = (int32_t)(ck2 - d.ckD);
+  d.shs0 = d.aD == 0 ? 0 : (d.nD == 0 ? 1 : (d.SD > 0 ? 1 : 0));
   return d;
 }
 
@@ -363,96 +370,118 @@ __device__ __forceinline__ uint32_t sat_i16(int32_t v) {
   return (uint32_t)(uint16_t)(int16_t)w;
 }
 
-// Evaluate move (m -> D) given m's header h (C = h.w0.x != D).
+// Everything gathered for one candidate (m -> D) from m's lists and the adjacency bitsets.
+struct Gathered {
+  int32_t gain;          // classes E used by m (E != C, D) that D does not use yet
+  int32_t impX, worX;    // caller classes X != C, D whose CBO drops / rises
+  int32_t t, sh;         // m's accesses to D's attributes, methods of D sharing one
+  int32_t outD, cntCD;   // m's use edges into D, C's use edges into D (when outD > 0)
+  int32_t inD, cntDC;    // m's callers in D, D's use edges into C (when inD > 0)
+  int32_t bDC, bCD;      // D uses C / C uses D, before the move (bit probes)
+};
+
+// Record of one candidate from the gathered data (shared by every kernel).
+__device__ __forceinline__ uint4 finish_move(const MoveHdr &h, const DState &ds, const Gathered &g, uint32_t mk,
+                                             int32_t min_improved, int32_t &dck_sum, int32_t &dcbo_sum) {
+  const int32_t out_self = h.w1.y, in_self = h.w1.z, l_all = h.w1.w;
+  // row D, column C
+  int bDC = g.bDC, aDC;
+  if (g.inD > 0) {
+    bDC = 1;
+    aDC = (g.cntDC + out_self - g.inD) > 0;
+  } else {
+    aDC = bDC | (out_self > 0);
+  }
+  const int32_t dD = g.gain + aDC - bDC;
+  // row C, column D
+  int bCD = g.bCD, aCD, corr = 0;
+  if (g.outD > 0) {
+    bCD = 1;
+    aCD = (g.cntCD - g.outD + in_self) > 0;
+    corr = g.cntCD == g.outD;
+  } else {
+    aCD = bCD | (in_self > 0);
+  }
+  const int32_t dC = -l_all + corr + aCD - bCD;
+  // target LCOM
+  int sckD, shsD;
+  int32_t dckD;
+  if (g.t == 0 && g.sh == 0) {
+    sckD = ds.sck0;
+    shsD = ds.shs0;
+    dckD = ds.dck0;
+  } else {
+    int64_t diff2 = ds.diffD + ds.nD - 2 * (int64_t)g.sh;
+    int64_t ck2 = diff2 > 0 ? diff2 : 0;
+    sckD = sgn64(ck2 - ds.ckD);
+    dckD = (int32_t)(ck2 - ds.ckD);
+    if (ds.aD == 0) shsD = 0;
+    else if (ds.nD == 0) shsD = g.t < ds.aD ? 1 : 0;
+    else shsD = sgn64(ds.SD - (int64_t)g.t * ds.nD);  // sign(S n' - S' n) with n' = n+1, S' = S + t
+  }
+  const int sckC = dec_sign((uint32_t)h.w2.x & 3u), shsC = dec_sign(((uint32_t)h.w2.x >> 2) & 3u);
+  const int scbC = (dC > 0) - (dC < 0), scbD = (dD > 0) - (dD < 0);
+  const int upC = ((mk & 1u) && sckC > 0) | ((mk & 2u) && shsC > 0) | ((mk & 4u) && scbC > 0);
+  const int dnC = ((mk & 1u) && sckC < 0) | ((mk & 2u) && shsC < 0) | ((mk & 4u) && scbC < 0);
+  const int upD = ((mk & 1u) && sckD > 0) | ((mk & 2u) && shsD > 0) | ((mk & 4u) && scbD > 0);
+  const int dnD = ((mk & 1u) && sckD < 0) | ((mk & 2u) && shsD < 0) | ((mk & 4u) && scbD < 0);
+  int32_t imp = (!upC && dnC) + (!upD && dnD);
+  int32_t wor = upC + upD;
+  if (mk & 4u) {
+    imp += g.impX;
+    wor += g.worX;
+  }
+  uint32_t flags = ((uint32_t)h.w2.x & 15u) | (enc_sign(scbC) << 4) | (enc_sign(sckD) << 6) |
+                   (enc_sign(shsD) << 8) | (enc_sign(scbD) << 10);
+  if (wor == 0 && imp >= min_improved) flags |= 0x8000u;
+  dck_sum = h.w2.y + dckD;
+  dcbo_sum = dC + dD;
+  uint4 r;
+  r.x = (uint32_t)g.sh;
+  r.y = sat_u16(g.t) | (sat_i16(dC) << 16);
+  r.z = sat_i16(dD) | (sat_u16(imp) << 16);
+  r.w = sat_u16(wor) | (flags << 16);
+  return r;
+}
+
+// Gather for (m -> D) straight from global memory (explicit candidate lists,
+// and methods whose lists do not fit the shared-memory stage).
 __device__ __forceinline__ uint4 eval_move(const EvalCtx &cx, const MoveHdr &h, const DState &ds, int32_t &dck_sum,
                                            int32_t &dcbo_sum) {
   const int32_t D = ds.D;
   const int32_t C = h.w0.x;
   const uint32_t dword = (uint32_t)D >> 5, dbit = (uint32_t)D & 31u;
-  // list L: classes m uses (E != C)
-  int32_t t = 0, sh = 0, outD = 0, cntCD = 0, gain = 0;
+  Gathered g;
+  g.gain = 0; g.impX = 0; g.worX = 0; g.t = 0; g.sh = 0; g.outD = 0; g.cntCD = 0; g.inD = 0; g.cntDC = 0;
   const int4 *L = cx.l_list + h.w0.y;
   for (int32_t e = 0; e < h.w0.z; ++e) {
     int4 v = __ldg(L + e);
     if (v.x == D) {
-      outD = v.y;
-      cntCD = v.z;
-      t = v.w;
-      sh = t > 0 ? __ldg(cx.l_s + h.w0.y + e) : 0;
+      g.outD = v.y;
+      g.cntCD = v.z;
+      g.t = v.w;
+      g.sh = v.w > 0 ? __ldg(cx.l_s + h.w0.y + e) : 0;
     } else if (v.y > 0) {
-      gain += 1 - (int)((__ldg(cx.in_adj + (int64_t)v.x * cx.aw + dword) >> dbit) & 1u);
+      g.gain += 1 - (int)((__ldg(cx.in_adj + (int64_t)v.x * cx.aw + dword) >> dbit) & 1u);
     }
   }
-  // list R: other classes calling m
-  int32_t inD = 0, cntDC = 0, impX = 0, worX = 0;
   const int4 *R = cx.r_list + h.w0.w;
   for (int32_t e = 0; e < h.w1.x; ++e) {
     int4 v = __ldg(R + e);
     if (v.x == D) {
-      inD = v.y;
-      cntDC = v.z;
+      g.inD = v.y;
+      g.cntDC = v.z;
     } else {
       int loss = v.z == v.y;
-      int g = 1 - (int)((__ldg(cx.out_adj + (int64_t)v.x * cx.aw + dword) >> dbit) & 1u);
-      int dx = g - loss;
-      impX += dx < 0;
-      worX += dx > 0;
+      int gx = 1 - (int)((__ldg(cx.out_adj + (int64_t)v.x * cx.aw + dword) >> dbit) & 1u);
+      int dx = gx - loss;
+      g.impX += dx < 0;
+      g.worX += dx > 0;
     }
   }
-  const int32_t out_self = h.w1.y, in_self = h.w1.z, l_all = h.w1.w;
-  // row D, column C
-  int bDC, aDC;
-  if (inD > 0) {
-    bDC = 1;
-    aDC = (cntDC + out_self - inD) > 0;
-  } else {
-    bDC = (int)((__ldg(cx.in_adj + (int64_t)C * cx.aw + dword) >> dbit) & 1u);
-    aDC = bDC | (out_self > 0);
-  }
-  const int32_t dD = gain + aDC - bDC;
-  // row C, column D
-  int bCD, aCD, corr = 0;
-  if (outD > 0) {
-    bCD = 1;
-    aCD = (cntCD - outD + in_self) > 0;
-    corr = cntCD == outD;
-  } else {
-    bCD = (int)((__ldg(cx.out_adj + (int64_t)C * cx.aw + dword) >> dbit) & 1u);
-    aCD = bCD | (in_self > 0);
-  }
-  const int32_t dC = -l_all + corr + aCD - bCD;
-  // target LCOM
-  int64_t diff2 = ds.diffD + ds.nD - 2 * (int64_t)sh;
-  int64_t ck2 = diff2 > 0 ? diff2 : 0;
-  int sckD = sgn64(ck2 - ds.ckD);
-  int shsD;
-  if (ds.aD == 0) shsD = 0;
-  else if (ds.nD == 0) shsD = t < ds.aD ? 1 : 0;
-  else shsD = sgn64(ds.SD - (int64_t)t * ds.nD);  // sign(S n' - S' n) with n' = n+1, S' = S + t
-  const int sckC = dec_sign((uint32_t)h.w2.x & 3u), shsC = dec_sign(((uint32_t)h.w2.x >> 2) & 3u);
-  const int scbC = (dC > 0) - (dC < 0), scbD = (dD > 0) - (dD < 0);
-  const uint32_t mk = cx.mask;
-  int upC = ((mk & 1u) && sckC > 0) | ((mk & 2u) && shsC > 0) | ((mk & 4u) && scbC > 0);
-  int dnC = ((mk & 1u) && sckC < 0) | ((mk & 2u) && shsC < 0) | ((mk & 4u) && scbC < 0);
-  int upD = ((mk & 1u) && sckD > 0) | ((mk & 2u) && shsD > 0) | ((mk & 4u) && scbD > 0);
-  int dnD = ((mk & 1u) && sckD < 0) | ((mk & 2u) && shsD < 0) | ((mk & 4u) && scbD < 0);
-  int32_t imp = (!upC && dnC) + (!upD && dnD);
-  int32_t wor = upC + upD;
-  if (mk & 4u) {
-    imp += impX;
-    wor += worX;
-  }
-  uint32_t flags = enc_sign(sckC) | (enc_sign(shsC) << 2) | (enc_sign(scbC) << 4) | (enc_sign(sckD) << 6) |
-                   (enc_sign(shsD) << 8) | (enc_sign(scbD) << 10);
-  if (wor == 0 && imp >= cx.min_improved) flags |= 0x8000u;
-  dck_sum = h.w2.y + (int32_t)(ck2 - ds.ckD);
-  dcbo_sum = dC + dD;
-  uint4 r;
-  r.x = (uint32_t)sh;
-  r.y = sat_u16(t) | (sat_i16(dC) << 16);
-  r.z = sat_i16(dD) | (sat_u16(imp) << 16);
-  r.w = sat_u16(wor) | (flags << 16);
-  return r;
+  g.bDC = (int)((__ldg(cx.in_adj + (int64_t)C * cx.aw + dword) >> dbit) & 1u);
+  g.bCD = (int)((__ldg(cx.out_adj + (int64_t)C * cx.aw + dword) >> dbit) & 1u);
+  return finish_move(h, ds, g, cx.mask, cx.min_improved, dck_sum, dcbo_sum);
 }
 
 __device__ __forceinline__ uint64_t smix(uint64_t x) {
@@ -502,33 +531,324 @@ __device__ __forceinline__ void emit_kept(const OutCtx &oc, bool kept, int32_t m
   }
 }
 
-// Dense cross product: thread = destination D, loop over a chunk of methods.
+// Dense cross product.  A block owns DB_SPAN = 1024 consecutive destinations;
+// thread (warp w, lane l) evaluates D = D0 + 32 w + l + 256 q for q = 0..3, so
+// each warp-wide store writes 32 consecutive 16-byte records (512 bytes).
+// Methods are walked in batches.  For each batch the block first stages in
+// shared memory, cooperatively and with many loads in flight: the headers, the
+// list entries and, for every entry, the 32 adjacency words covering the
+// block's destinations, already turned into per-destination contributions:
+//   L entry E (m uses E):   bit D = 1 iff D does not use E yet (CBO(D) gains E),
+//                           0 where D == E or m has no use edge into E;
+//   R entry X (X calls m):  bit D = 1 iff CBO(X) drops (X stops using C and
+//                           already uses D) or rises (X keeps C, starts using D);
+//                           which of the two is the entry's uniform "shift".
+// The evaluation loops are then shift/and/add on shared-memory broadcasts.  A
+// destination that appears in m's own lists (D == E or D == X) takes the exact
+// general path; everything else uses destination constants precomputed once.
+constexpr int DQ = 4;
+constexpr int DB_THREADS = 256;
+constexpr int DB_WARPS = DB_THREADS / 32;
+constexpr int DB_SPAN = DB_THREADS * DQ;
+constexpr int DB_WORDS = DB_SPAN / 32;
+constexpr int DB_MB = 32;
+constexpr int DB_ECAP = 192;
+
+struct DenseStage {
+  MoveHdr hdr[DB_MB];
+  int32_t lb[DB_MB], rb[DB_MB], hb[DB_MB], hn[DB_MB];
+  int4 ent[DB_ECAP];              // L: {E, out, cnt(C,E), t}; R: {X, in, cnt(X,C), shift 0|16}
+  int32_t ents[DB_ECAP];          // s of L entries
+  uint4 word[DB_ECAP][DB_WARPS];  // [slot][w] = contribution words w, w+8, w+16, w+24
+  uint4 cw[DB_MB][2][DB_WARPS];   // adjacency words of row C: [0] = in_adj (D uses C), [1] = out_adj (C uses D)
+  int16_t hit[DB_ECAP];           // slots whose class lies in the block's span
+  int32_t k, overflow;
+};
+
+__device__ __forceinline__ uint32_t sel4(const uint4 &v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ int32_t clamp16(int32_t v) { return max(-32768, min(32767, v)); }
+__device__ __forceinline__ uint32_t enc_small(int32_t v) { return (uint32_t)(v < 0) | ((uint32_t)(v > 0) << 1); }
+
+// Rare paths of the dense kernel, kept out of line so they do not cost the
+// common path registers.
+__device__ __noinline__ uint4 dense_hit_path(const EvalCtx &cx, const DenseStage &st, int32_t j, const MoveHdr &h,
+                                             int32_t D, uint32_t gain, uint32_t iw, uint32_t bDC, uint32_t bCD,
+                                             const int32_t *cls_n, const int32_t *cls_a, const int64_t *cls_P,
+                                             const int64_t *cls_Q, const int64_t *cls_S, int32_t *dck, int32_t *dcbo) {
+  Gathered g;
+  g.gain = (int32_t)gain;
+  g.impX = (int32_t)(iw & 0xffffu);
+  g.worX = (int32_t)(iw >> 16);
+  g.t = 0; g.sh = 0; g.outD = 0; g.cntCD = 0; g.inD = 0; g.cntDC = 0;
+  const int32_t hb = st.hb[j], hn = st.hn[j];
+  for (int32_t i = 0; i < hn; ++i) {
+    const int32_t slot = st.hit[hb + i];
+    const int4 v = st.ent[slot];
+    if (v.x != D) continue;
+    if (slot < st.rb[j]) {
+      g.outD = v.y; g.cntCD = v.z; g.t = v.w; g.sh = st.ents[slot];
+    } else {
+      g.inD = v.y; g.cntDC = v.z;
+    }
+  }
+  g.bDC = (int32_t)bDC;
+  g.bCD = (int32_t)bCD;
+  DState ds = load_dstate(D, cls_n, cls_a, cls_P, cls_Q, cls_S);
+  int32_t a = 0, b = 0;
+  uint4 r = finish_move(h, ds, g, cx.mask, cx.min_improved, a, b);
+  *dck = a;
+  *dcbo = b;
+  return r;
+}
+
+__device__ __noinline__ uint4 dense_global_path(const EvalCtx &cx, const MoveHdr &h, int32_t D,
+                                                const int32_t *cls_n, const int32_t *cls_a, const int64_t *cls_P,
+                                                const int64_t *cls_Q, const int64_t *cls_S, int32_t *dck,
+                                                int32_t *dcbo) {
+  DState ds = load_dstate(D, cls_n, cls_a, cls_P, cls_Q, cls_S);
+  int32_t a = 0, b = 0;
+  uint4 r = eval_move(cx, h, ds, a, b);
+  *dck = a;
+  *dcbo = b;
+  return r;
+}
+
 template <bool REC, bool DIG, bool KEEP>
-__global__ void __launch_bounds__(256) eval_dense(EvalCtx cx, OutCtx oc, const int32_t *cls_n, const int32_t *cls_a,
-                                                  const int64_t *cls_P, const int64_t *cls_Q, const int64_t *cls_S,
-                                                  int32_t c, int32_t M, int32_t mchunk) {
+__global__ void __launch_bounds__(DB_THREADS) eval_dense(EvalCtx cx, OutCtx oc, const int32_t *cls_n,
+                                                         const int32_t *cls_a, const int64_t *cls_P,
+                                                         const int64_t *cls_Q, const int64_t *cls_S, int32_t c,
+                                                         int32_t M, int32_t mchunk) {
+  __shared__ __align__(16) DenseStage st;
   const uint32_t lane = threadIdx.x & 31u;
-  const int32_t D = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-  const bool vD = D < c;
-  DState ds = load_dstate(vD ? D : 0, cls_n, cls_a, cls_P, cls_Q, cls_S);
-  ds.D = D;
+  const int warp = (int)(threadIdx.x >> 5);
+  const int32_t D0 = (int32_t)blockIdx.x * DB_SPAN;
+  const int64_t dw0 = D0 >> 5;
+  const uint32_t mk = cx.mask;
+  const int32_t mk4 = (mk & 4u) ? 1 : 0;
+  // destination constants (target LCOM outcome when m shares nothing with D)
+  int32_t dconst[DQ], dck0[DQ];
+#pragma unroll
+  for (int q = 0; q < DQ; ++q) {
+    const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
+    DState ds = load_dstate(D < c ? D : 0, cls_n, cls_a, cls_P, cls_Q, cls_S);
+    const int32_t up = ((mk & 1u) && ds.sck0 > 0) | ((mk & 2u) && ds.shs0 > 0);
+    const int32_t dn = ((mk & 1u) && ds.sck0 < 0) | ((mk & 2u) && ds.shs0 < 0);
+    dconst[q] = up | (dn << 1) | (int32_t)((enc_sign(ds.sck0) << 6) | (enc_sign(ds.shs0) << 8));
+    dck0[q] = ds.dck0;
+  }
   const int32_t m0 = blockIdx.y * mchunk;
   const int32_t m1 = min(M, m0 + mchunk);
-  uint64_t dig = 0;
   const int64_t row = (int64_t)c - 1;
-  for (int32_t m = m0; m < m1; ++m) {
-    MoveHdr h;
-    h.w0 = __ldg(&cx.hdr[m].w0);
-    h.w1 = __ldg(&cx.hdr[m].w1);
-    h.w2 = __ldg(&cx.hdr[m].w2);
-    const int32_t C = h.w0.x;
-    const bool act = vD && D != C;
-    int32_t dck = 0, dcbo = 0;
-    uint4 r = make_uint4(0, 0, 0, 0);
-    if (act) r = eval_move(cx, h, ds, dck, dcbo);
-    if (REC && act) __stcs(oc.records + (int64_t)m * row + D - (D > C ? 1 : 0), r);
-    if (DIG && act) dig += record_hash(m, D, r);
-    if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
+  const int64_t seg_words = cx.aw - dw0;  // adjacency words left in a row from dw0 (may exceed 32)
+  uint64_t dig = 0;
+  for (int32_t mb = m0; mb < m1;) {
+    // ---- plan: warp 0 scans the list lengths of up to 32 methods
+    if (warp == 0) {
+      const int32_t m = mb + (int32_t)lane;
+      const bool ok = m < m1;
+      MoveHdr h;
+      h.w0 = make_int4(0, 0, 0, 0);
+      h.w1 = make_int4(0, 0, 0, 0);
+      h.w2 = make_int4(0, 0, 0, 0);
+      if (ok) {
+        h.w0 = __ldg(&cx.hdr[m].w0);
+        h.w1 = __ldg(&cx.hdr[m].w1);
+        h.w2 = __ldg(&cx.hdr[m].w2);
+      }
+      const int32_t len = ok ? h.w0.z + h.w1.x : 0;
+      int32_t incl = len;
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+      }
+      const uint32_t fit = __ballot_sync(0xffffffffu, ok && incl <= DB_ECAP);
+      int32_t k = __popc(fit);
+      int32_t overflow = 0;
+      if (k == 0) { k = 1; overflow = 1; }
+      if ((int32_t)lane < k) {
+        st.hdr[lane] = h;
+        st.lb[lane] = incl - len;
+        st.rb[lane] = incl - len + h.w0.z;
+      }
+      if (lane == 0) { st.k = k; st.overflow = overflow; }
+    }
+    __syncthreads();
+    const int32_t k = st.k;
+    const bool overflow = st.overflow != 0;
+    // ---- stage: warp w prepares methods w, w+8, ... (lanes over list entries)
+    if (!overflow) {
+      for (int32_t j = warp; j < k; j += DB_WARPS) {
+        const MoveHdr h = st.hdr[j];
+        const int32_t nl = h.w0.z, nr = h.w1.x, C = h.w0.x;
+        int32_t nh = 0;
+        const int32_t hb = st.lb[j];  // the method's hits are stored from its first slot on
+        for (int32_t e0 = 0; e0 < nl + nr; e0 += 32) {
+          const int32_t e = e0 + (int32_t)lane;
+          const bool ok = e < nl + nr;
+          const bool isL = e < nl;
+          int4 v = make_int4(-1, 0, 0, 0);
+          int32_t slot = 0;
+          if (ok) {
+            if (isL) {
+              v = __ldg(cx.l_list + h.w0.y + e);
+              slot = st.lb[j] + e;
+              st.ents[slot] = v.w > 0 ? __ldg(cx.l_s + h.w0.y + e) : 0;
+            } else {
+              v = __ldg(cx.r_list + h.w0.w + (e - nl));
+              slot = st.rb[j] + (e - nl);
+            }
+          }
+          if (ok) {
+            const uint4 *rowp = reinterpret_cast<const uint4 *>((isL ? cx.in_adj : cx.out_adj) +
+                                                                (int64_t)v.x * cx.aw + dw0);
+            // contribution = (adjacency ^ xr) & am:
+            //   L: D does not use E yet (only if m really uses E);  R: loss ? X uses D : X does not use D
+            uint32_t xr, am;
+            if (isL) {
+              xr = 0xffffffffu;
+              am = v.y > 0 ? 0xffffffffu : 0u;
+            } else {
+              const bool loss = v.z == v.y;  // X stops using C
+              xr = loss ? 0u : 0xffffffffu;
+              am = 0xffffffffu;
+              v.w = loss ? 0 : 16;           // drop -> improved counter, rise -> worsened counter
+            }
+            const int32_t relv = v.x - D0;
+            const int32_t hw = (relv >= 0 && relv < DB_SPAN) ? (relv >> 5) : -1;
+            const uint32_t hbit = 1u << (relv & 31);
+            uint32_t *dstw = reinterpret_cast<uint32_t *>(&st.word[slot][0]);
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4) {  // words g = 8 c4 + w, w = 0..7, stored at [w][c4]
+              uint4 a = make_uint4(0, 0, 0, 0), b = make_uint4(0, 0, 0, 0);
+              if (8 * c4 < seg_words) a = __ldg(rowp + 2 * c4);
+              if (8 * c4 + 4 < seg_words) b = __ldg(rowp + 2 * c4 + 1);
+              const uint32_t wv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+              for (int w = 0; w < DB_WARPS; ++w) {
+                uint32_t x = (wv[w] ^ xr) & am;
+                if (hw == 8 * c4 + w) x &= ~hbit;
+                dstw[4 * w + c4] = x;
+              }
+            }
+            st.ent[slot] = v;
+          }
+          const int32_t rel = v.x - D0;
+          const bool is_hit = ok && rel >= 0 && rel < DB_SPAN;
+          const uint32_t hm = __ballot_sync(0xffffffffu, is_hit);
+          if (is_hit) st.hit[hb + nh + __popc(hm & ((1u << lane) - 1u))] = (int16_t)slot;
+          nh += __popc(hm);
+        }
+        if (lane == 0) { st.hb[j] = hb; st.hn[j] = nh; }
+        if (lane < 2 * DB_WARPS) {
+          const int which = (int)lane / DB_WARPS, w = (int)lane % DB_WARPS;
+          const uint32_t *rowp = (which ? cx.out_adj : cx.in_adj) + (int64_t)C * cx.aw + dw0;
+          uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+          if (w < seg_words) a0 = __ldg(rowp + w);
+          if (w + 8 < seg_words) a1 = __ldg(rowp + w + 8);
+          if (w + 16 < seg_words) a2 = __ldg(rowp + w + 16);
+          if (w + 24 < seg_words) a3 = __ldg(rowp + w + 24);
+          st.cw[j][which][w] = make_uint4(a0, a1, a2, a3);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- evaluate the batch
+    for (int32_t j = 0; j < k; ++j) {
+      const int32_t m = mb + j;
+      const MoveHdr h = st.hdr[j];
+      const int32_t C = h.w0.x;
+      const int64_t rowbase = (int64_t)m * row;
+      if (overflow) {
+#pragma unroll
+        for (int q = 0; q < DQ; ++q) {
+          const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
+          const bool act = D < c && D != C;
+          int32_t dck = 0, dcbo = 0;
+          uint4 r = make_uint4(0, 0, 0, 0);
+          if (act) r = dense_global_path(cx, h, D, cls_n, cls_a, cls_P, cls_Q, cls_S, &dck, &dcbo);
+          if (REC && act) __stcs(oc.records + rowbase + D - (D > C ? 1 : 0), r);
+          if (DIG && act) dig += record_hash(m, D, r);
+          if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
+        }
+        continue;
+      }
+      uint32_t gain[DQ] = {0, 0, 0, 0}, iw[DQ] = {0, 0, 0, 0};
+      {
+        const int32_t lb = st.lb[j], nl = h.w0.z;
+        for (int32_t e = 0; e < nl; ++e) {
+          const uint4 wd = st.word[lb + e][warp];
+          gain[0] += (wd.x >> lane) & 1u;
+          gain[1] += (wd.y >> lane) & 1u;
+          gain[2] += (wd.z >> lane) & 1u;
+          gain[3] += (wd.w >> lane) & 1u;
+        }
+        const int32_t rb = st.rb[j], nr = h.w1.x;
+        for (int32_t e = 0; e < nr; ++e) {
+          const uint32_t sh = (uint32_t)st.ent[rb + e].w;
+          const uint4 wd = st.word[rb + e][warp];
+          iw[0] += ((wd.x >> lane) & 1u) << sh;
+          iw[1] += ((wd.y >> lane) & 1u) << sh;
+          iw[2] += ((wd.z >> lane) & 1u) << sh;
+          iw[3] += ((wd.w >> lane) & 1u) << sh;
+        }
+      }
+      // hits: destinations of this thread that appear in m's lists
+      uint32_t hitq = 0;
+      {
+        const int32_t hb = st.hb[j], hn = st.hn[j];
+        for (int32_t i = 0; i < hn; ++i) {
+          const int32_t X = st.ent[st.hit[hb + i]].x;
+          const int32_t rel = X - D0 - (int32_t)threadIdx.x;
+          if (rel >= 0 && (rel & (DB_THREADS - 1)) == 0) hitq |= 1u << (rel >> 8);
+        }
+      }
+      const uint4 cin = st.cw[j][0][warp], cout = st.cw[j][1][warp];
+      const int32_t os = h.w1.y > 0, is = h.w1.z > 0, l_all = h.w1.w;
+      const uint32_t sC = (uint32_t)h.w2.x & 15u;
+      const int sckC = dec_sign(sC & 3u), shsC = dec_sign(sC >> 2);
+      const int32_t upCl = ((mk & 1u) && sckC > 0) | ((mk & 2u) && shsC > 0);
+      const int32_t dnCl = ((mk & 1u) && sckC < 0) | ((mk & 2u) && shsC < 0);
+#pragma unroll
+      for (int q = 0; q < DQ; ++q) {
+        const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
+        const bool act = D < c && D != C;
+        int32_t dck, dcbo;
+        uint4 r;
+        if ((hitq >> q) & 1u) {
+          // exact general path: D appears in m's lists
+          dck = 0; dcbo = 0;
+          r = make_uint4(0, 0, 0, 0);
+          if (act)
+            r = dense_hit_path(cx, st, j, h, D, gain[q], iw[q], (sel4(cin, q) >> lane) & 1u,
+                               (sel4(cout, q) >> lane) & 1u, cls_n, cls_a, cls_P, cls_Q, cls_S, &dck, &dcbo);
+        } else {
+          const int32_t bDC = (int32_t)((sel4(cin, q) >> lane) & 1u);
+          const int32_t bCD = (int32_t)((sel4(cout, q) >> lane) & 1u);
+          const int32_t dD = (int32_t)gain[q] + (os & (bDC ^ 1));
+          const int32_t dC = (is & (bCD ^ 1)) - l_all;
+          const int32_t upC = upCl | (mk4 & (dC > 0)), dnC = dnCl | (mk4 & (dC < 0));
+          const int32_t upD = (dconst[q] & 1) | (mk4 & (dD > 0)), dnD = ((dconst[q] >> 1) & 1) | (mk4 & (dD < 0));
+          const int32_t imp = (dnC & (upC ^ 1)) + (dnD & (upD ^ 1)) + (mk4 ? (int32_t)(iw[q] & 0xffffu) : 0);
+          const int32_t wor = upC + upD + (mk4 ? (int32_t)(iw[q] >> 16) : 0);
+          uint32_t flags = sC | ((uint32_t)dconst[q] & 0x3c0u) | (enc_small(dC) << 4) | (enc_small(dD) << 10);
+          if (wor == 0 && imp >= cx.min_improved) flags |= 0x8000u;
+          r.x = 0u;
+          r.y = (uint32_t)(uint16_t)(int16_t)clamp16(dC) << 16;
+          r.z = (uint32_t)(uint16_t)(int16_t)clamp16(dD) | ((uint32_t)min(imp, 65535) << 16);
+          r.w = (uint32_t)min(wor, 65535) | (flags << 16);
+          dck = h.w2.y + dck0[q];
+          dcbo = dC + dD;
+        }
+        if (REC && act) __stcs(oc.records + rowbase + D - (D > C ? 1 : 0), r);
+        if (DIG && act) dig += record_hash(m, D, r);
+        if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
+      }
+    }
+    mb += k;
+    __syncthreads();
   }
   if (DIG) {
     for (int o = 16; o > 0; o >>= 1) dig += __shfl_down_sync(0xffffffffu, dig, o);
@@ -597,12 +917,12 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
   cudaStream_t st = s->stream;
   if (!rowptr) {
     const int32_t c = s->c, M = s->M;
-    unsigned gx = (unsigned)ceil_div(c, 256);
+    unsigned gx = (unsigned)ceil_div(c, DB_SPAN);
     // enough blocks for ~16 per SM, each walking a chunk of methods
     int64_t want_y = std::max<int64_t>(1, (148 * 16 + gx - 1) / gx);
     int32_t mchunk = (int32_t)std::max<int64_t>(1, ceil_div(M, want_y));
     unsigned gy = (unsigned)ceil_div(M, mchunk);
-    eval_dense<REC, DIG, KEEP><<<dim3(gx, gy), 256, 0, st>>>(cx, oc, s->cls_n, s->cls_a, s->cls_P, s->cls_Q,
+    eval_dense<REC, DIG, KEEP><<<dim3(gx, gy), DB_THREADS, 0, st>>>(cx, oc, s->cls_n, s->cls_a, s->cls_P, s->cls_Q,
                                                              s->cls_S, c, M, mchunk);
   } else {
     unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)s->M * 32, 256), 148 * 64);
@@ -613,12 +933,17 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
 }
 
 void dispatch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_t *rowptr, const int32_t *dst) {
-  const bool rec = oc.records != nullptr, dig = oc.digest != nullptr, keep = oc.kept_count != nullptr;
-  if (rec && dig) launch_eval<true, true, false>(s, cx, oc, rowptr, dst);
-  else if (rec) launch_eval<true, false, false>(s, cx, oc, rowptr, dst);
-  else if (dig) launch_eval<false, true, false>(s, cx, oc, rowptr, dst);
-  else if (keep) launch_eval<false, false, true>(s, cx, oc, rowptr, dst);
-  else launch_eval<false, false, false>(s, cx, oc, rowptr, dst);
+  const int sel = (oc.records ? 4 : 0) | (oc.digest ? 2 : 0) | (oc.kept_count ? 1 : 0);
+  switch (sel) {
+    case 0: launch_eval<false, false, false>(s, cx, oc, rowptr, dst); break;
+    case 1: launch_eval<false, false, true>(s, cx, oc, rowptr, dst); break;
+    case 2: launch_eval<false, true, false>(s, cx, oc, rowptr, dst); break;
+    case 3: launch_eval<false, true, true>(s, cx, oc, rowptr, dst); break;
+    case 4: launch_eval<true, false, false>(s, cx, oc, rowptr, dst); break;
+    case 5: launch_eval<true, false, true>(s, cx, oc, rowptr, dst); break;
+    case 6: launch_eval<true, true, false>(s, cx, oc, rowptr, dst); break;
+    default: launch_eval<true, true, true>(s, cx, oc, rowptr, dst); break;
+  }
 }
 
 // ---------------------------------------------------------------- top-k
@@ -763,6 +1088,30 @@ static EvalCtx make_ctx(mm_system *s, const mm_criteria &crit) {
   return cx;
 }
 
+// Kept-move buffer of the system: [cap] moves followed by one mark byte per method.
+static void kept_buffers(mm_system *s, int64_t cap, mm_move **kept, uint8_t **mark) {
+  size_t bytes = sizeof(mm_move) * (size_t)cap + (size_t)s->M + 256;
+  char *b = static_cast<char *>(s->kept_ws.need(bytes, s->stream));
+  *kept = reinterpret_cast<mm_move *>(b);
+  *mark = reinterpret_cast<uint8_t *>(b + sizeof(mm_move) * (size_t)cap);
+}
+
+static void attach_kept(mm_system *s, OutCtx &oc, int64_t cap) {
+  mm_move *kept;
+  uint8_t *mark;
+  kept_buffers(s, cap, &kept, &mark);
+  MM_CUDA_TRY(cudaMemsetAsync(mark, 0, (size_t)s->M, s->stream));
+  MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 1, 0, sizeof(unsigned long long), s->stream));
+  oc.kept = kept;
+  oc.kept_count = s->d_u64 + 1;
+  oc.kept_cap = cap;
+  oc.kept_mark = mark;
+}
+
+static int64_t kept_capacity(mm_system *s) {
+  return std::max<int64_t>(65536, s->kept_cap);
+}
+
 void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *cands, mm_move_eval *records,
                     uint64_t *digest, int32_t kind) {
   check_criteria(crit);
@@ -772,6 +1121,7 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
   const int32_t *dst;
   int64_t n_cand;
   prepare_candidates(s, cands, &rowptr, &dst, &n_cand, s->stage_ws);
+  s->kept_valid = false;
   if (n_cand == 0 || s->M == 0) {
     if (digest) {
       if (kind == MM_PTR_HOST) *digest = 0;
@@ -791,7 +1141,18 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
     oc.digest = s->d_u64;
     MM_CUDA_TRY(cudaMemsetAsync(s->d_u64, 0, sizeof(unsigned long long), st));
   }
+  // The full cross product also compacts its kept moves in the same pass, so a
+  // following mm_suggest_moves with the same criteria needs no second pass.
+  const bool fuse_kept = rowptr == nullptr;
+  const int64_t cap = kept_capacity(s);
+  if (fuse_kept) attach_kept(s, oc, cap);
   dispatch_eval(s, cx, oc, rowptr, dst);
+  if (fuse_kept) {
+    s->kept_valid = true;
+    s->kept_mask = crit.metric_mask;
+    s->kept_min = crit.min_improved;
+    s->kept_cap = cap;
+  }
   if (records && kind == MM_PTR_HOST)
     MM_CUDA_TRY(cudaMemcpyAsync(records, rec_dev, sizeof(uint4) * (size_t)n_cand, cudaMemcpyDeviceToHost, st));
   if (digest) {
@@ -816,20 +1177,19 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
   mm_move *kept = nullptr;
   if (n_cand > 0 && s->M > 0) {
     EvalCtx cx = make_ctx(s, crit);
-    int64_t cap = std::max<int64_t>(4096, (int64_t)(s->eval_ws.cap / sizeof(mm_move)) / 2);
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      size_t bytes = sizeof(mm_move) * 2 * (size_t)cap + (size_t)s->M + 256;
-      char *b = static_cast<char *>(s->eval_ws.need(bytes, st));
-      kept = reinterpret_cast<mm_move *>(b);
-      uint8_t *mark = reinterpret_cast<uint8_t *>(b + sizeof(mm_move) * 2 * (size_t)cap);
-      MM_CUDA_TRY(cudaMemsetAsync(mark, 0, (size_t)s->M, st));
-      MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 1, 0, 2 * sizeof(unsigned long long), st));
-      OutCtx oc{};
-      oc.kept = kept;
-      oc.kept_count = s->d_u64 + 1;
-      oc.kept_cap = cap;
-      oc.kept_mark = mark;
-      dispatch_eval(s, cx, oc, rowptr, dst);
+    const bool reuse = rowptr == nullptr && s->kept_valid && s->kept_mask == crit.metric_mask &&
+                       s->kept_min == crit.min_improved;
+    int64_t cap = reuse ? s->kept_cap : kept_capacity(s);
+    if (!reuse) s->kept_valid = false;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      uint8_t *mark;
+      kept_buffers(s, cap, &kept, &mark);
+      if (!(reuse && attempt == 0)) {
+        OutCtx oc{};
+        attach_kept(s, oc, cap);
+        dispatch_eval(s, cx, oc, rowptr, dst);
+      }
+      MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 2, 0, sizeof(unsigned long long), st));
       count_marks<<<148 * 4, 256, 0, st>>>(mark, s->M, s->d_u64 + 2);
       MM_LAUNCH_CHECK();
       unsigned long long hc[2];
@@ -839,6 +1199,13 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
       nm = (int64_t)hc[1];
       if (K <= cap) break;
       cap = K + K / 8 + 1024;  // grow and evaluate again
+      s->kept_valid = false;
+    }
+    if (rowptr == nullptr) {  // the full cross product's kept moves stay cached for these criteria
+      s->kept_cap = std::max(s->kept_cap, cap);
+      s->kept_valid = true;
+      s->kept_mask = crit.metric_mask;
+      s->kept_min = crit.min_improved;
     }
     if (K > 1 && K <= BITONIC_MAX) {
       bitonic_sort_moves<<<1, 1024, 0, st>>>(kept, (int32_t)K);
