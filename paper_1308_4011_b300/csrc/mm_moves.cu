@@ -562,6 +562,9 @@ struct DenseStage {
   uint4 word[DB_ECAP][DB_WARPS];  // [slot][w] = contribution words w, w+8, w+16, w+24
   uint4 cw[DB_MB][2][DB_WARPS];   // adjacency words of row C: [0] = in_adj (D uses C), [1] = out_adj (C uses D)
   int16_t hit[DB_ECAP];           // slots whose class lies in the block's span
+  // source-side outcome of method j for b = [m's callers in C make C start using D]:
+  //   pc = improved + (worsened << 16) of class C, fc = sign bits 0-5, rc = record word 1 (dCBO(C) << 16)
+  int32_t pc[DB_MB][2], fc[DB_MB][2], rc[DB_MB][2];
   int32_t k, overflow;
 };
 
@@ -574,28 +577,35 @@ __device__ __forceinline__ uint32_t enc_small(int32_t v) { return (uint32_t)(v <
 
 // Rare paths of the dense kernel, kept out of line so they do not cost the
 // common path registers.
-__device__ __noinline__ uint4 dense_hit_path(const EvalCtx &cx, const DenseStage &st, int32_t j, const MoveHdr &h,
-                                             int32_t D, uint32_t gain, uint32_t iw, uint32_t bDC, uint32_t bCD,
-                                             const int32_t *cls_n, const int32_t *cls_a, const int64_t *cls_P,
-                                             const int64_t *cls_Q, const int64_t *cls_S, int32_t *dck, int32_t *dcbo) {
+__device__ __noinline__ uint4 dense_hit_path(const EvalCtx &cx, const DenseStage &st, int32_t j, int32_t D, int q,
+                                             uint32_t lane, int warp, const int32_t *cls_n, const int32_t *cls_a,
+                                             const int64_t *cls_P, const int64_t *cls_Q, const int64_t *cls_S,
+                                             int32_t *dck, int32_t *dcbo) {
+  const MoveHdr h = st.hdr[j];
   Gathered g;
-  g.gain = (int32_t)gain;
-  g.impX = (int32_t)(iw & 0xffffu);
-  g.worX = (int32_t)(iw >> 16);
+  g.gain = 0; g.impX = 0; g.worX = 0;
   g.t = 0; g.sh = 0; g.outD = 0; g.cntCD = 0; g.inD = 0; g.cntDC = 0;
+  const int32_t lb = st.lb[j], nl = h.w0.z, rb = st.rb[j], nr = h.w1.x;
+  for (int32_t e = 0; e < nl; ++e) g.gain += (int32_t)((sel4(st.word[lb + e][warp], q) >> lane) & 1u);
+  if (cx.mask & 4u)
+    for (int32_t e = 0; e < nr; ++e) {
+      const uint32_t bit = (sel4(st.word[rb + e][warp], q) >> lane) & 1u;
+      if (st.ent[rb + e].w == 0) g.impX += (int32_t)bit;
+      else g.worX += (int32_t)bit;
+    }
   const int32_t hb = st.hb[j], hn = st.hn[j];
   for (int32_t i = 0; i < hn; ++i) {
     const int32_t slot = st.hit[hb + i];
     const int4 v = st.ent[slot];
     if (v.x != D) continue;
-    if (slot < st.rb[j]) {
+    if (slot < rb) {
       g.outD = v.y; g.cntCD = v.z; g.t = v.w; g.sh = st.ents[slot];
     } else {
       g.inD = v.y; g.cntDC = v.z;
     }
   }
-  g.bDC = (int32_t)bDC;
-  g.bCD = (int32_t)bCD;
+  g.bDC = (int32_t)((sel4(st.cw[j][0][warp], q) >> lane) & 1u);
+  g.bCD = (int32_t)((sel4(st.cw[j][1][warp], q) >> lane) & 1u);
   DState ds = load_dstate(D, cls_n, cls_a, cls_P, cls_Q, cls_S);
   int32_t a = 0, b = 0;
   uint4 r = finish_move(h, ds, g, cx.mask, cx.min_improved, a, b);
@@ -628,15 +638,20 @@ __global__ void __launch_bounds__(DB_THREADS) eval_dense(EvalCtx cx, OutCtx oc, 
   const int64_t dw0 = D0 >> 5;
   const uint32_t mk = cx.mask;
   const int32_t mk4 = (mk & 4u) ? 1 : 0;
-  // destination constants (target LCOM outcome when m shares nothing with D)
-  int32_t dconst[DQ], dck0[DQ];
+  // destination constants: target outcome when m shares nothing with D, for
+  // p = [dCBO(D) > 0] (in that case dCBO(D) >= 0): pd = improved + (worsened << 16),
+  // fd = sign bits 6-11
+  int32_t pd0[DQ], pd1[DQ], fd0[DQ], dck0[DQ];
 #pragma unroll
   for (int q = 0; q < DQ; ++q) {
     const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
     DState ds = load_dstate(D < c ? D : 0, cls_n, cls_a, cls_P, cls_Q, cls_S);
     const int32_t up = ((mk & 1u) && ds.sck0 > 0) | ((mk & 2u) && ds.shs0 > 0);
     const int32_t dn = ((mk & 1u) && ds.sck0 < 0) | ((mk & 2u) && ds.shs0 < 0);
-    dconst[q] = up | (dn << 1) | (int32_t)((enc_sign(ds.sck0) << 6) | (enc_sign(ds.shs0) << 8));
+    const int32_t up1 = up | mk4;
+    pd0[q] = (dn & (up ^ 1)) + (up << 16);
+    pd1[q] = (dn & (up1 ^ 1)) + (up1 << 16);
+    fd0[q] = (int32_t)((enc_sign(ds.sck0) << 6) | (enc_sign(ds.shs0) << 8));
     dck0[q] = ds.dck0;
   }
   const int32_t m0 = blockIdx.y * mchunk;
@@ -672,6 +687,18 @@ __global__ void __launch_bounds__(DB_THREADS) eval_dense(EvalCtx cx, OutCtx oc, 
         st.hdr[lane] = h;
         st.lb[lane] = incl - len;
         st.rb[lane] = incl - len + h.w0.z;
+        const uint32_t sC = (uint32_t)h.w2.x & 15u;
+        const int sckC = dec_sign(sC & 3u), shsC = dec_sign(sC >> 2);
+        const int32_t upCl = ((mk & 1u) && sckC > 0) | ((mk & 2u) && shsC > 0);
+        const int32_t dnCl = ((mk & 1u) && sckC < 0) | ((mk & 2u) && shsC < 0);
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const int32_t dC = b - h.w1.w;  // -l_all, plus one when C starts using D
+          const int32_t upC = upCl | (mk4 & (dC > 0)), dnC = dnCl | (mk4 & (dC < 0));
+          st.pc[lane][b] = (dnC & (upC ^ 1)) + (upC << 16);
+          st.fc[lane][b] = (int32_t)(sC | (enc_small(dC) << 4));
+          st.rc[lane][b] = (int32_t)((uint32_t)(uint16_t)(int16_t)clamp16(dC) << 16);
+        }
       }
       if (lane == 0) { st.k = k; st.overflow = overflow; }
     }
@@ -685,9 +712,11 @@ __global__ void __launch_bounds__(DB_THREADS) eval_dense(EvalCtx cx, OutCtx oc, 
         const int32_t nl = h.w0.z, nr = h.w1.x, C = h.w0.x;
         int32_t nh = 0;
         const int32_t hb = st.lb[j];  // the method's hits are stored from its first slot on
-        for (int32_t e0 = 0; e0 < nl + nr; e0 += 32) {
-          const int32_t e = e0 + (int32_t)lane;
-          const bool ok = e < nl + nr;
+        const int32_t items = 4 * (nl + nr);
+        for (int32_t i0 = 0; i0 < items; i0 += 32) {
+          const int32_t it = i0 + (int32_t)lane;
+          const bool ok = it < items;
+          const int32_t e = it >> 2, c4 = it & 3;
           const bool isL = e < nl;
           int4 v = make_int4(-1, 0, 0, 0);
           int32_t slot = 0;
@@ -695,15 +724,11 @@ __global__ void __launch_bounds__(DB_THREADS) eval_dense(EvalCtx cx, OutCtx oc, 
             if (isL) {
               v = __ldg(cx.l_list + h.w0.y + e);
               slot = st.lb[j] + e;
-              st.ents[slot] = v.w > 0 ? __ldg(cx.l_s + h.w0.y + e) : 0;
+              if (c4 == 0) st.ents[slot] = v.w > 0 ? __ldg(cx.l_s + h.w0.y + e) : 0;
             } else {
               v = __ldg(cx.r_list + h.w0.w + (e - nl));
               slot = st.rb[j] + (e - nl);
             }
-          }
-          if (ok) {
-            const uint4 *rowp = reinterpret_cast<const uint4 *>((isL ? cx.in_adj : cx.out_adj) +
-                                                                (int64_t)v.x * cx.aw + dw0);
             // contribution = (adjacency ^ xr) & am:
             //   L: D does not use E yet (only if m really uses E);  R: loss ? X uses D : X does not use D
             uint32_t xr, am;
@@ -719,24 +744,23 @@ __global__ void __launch_bounds__(DB_THREADS) eval_dense(EvalCtx cx, OutCtx oc, 
             const int32_t relv = v.x - D0;
             const int32_t hw = (relv >= 0 && relv < DB_SPAN) ? (relv >> 5) : -1;
             const uint32_t hbit = 1u << (relv & 31);
+            const uint4 *rowp = reinterpret_cast<const uint4 *>((isL ? cx.in_adj : cx.out_adj) +
+                                                                (int64_t)v.x * cx.aw + dw0);
+            uint4 a = make_uint4(0, 0, 0, 0), b = make_uint4(0, 0, 0, 0);
+            if (8 * c4 < seg_words) a = __ldg(rowp + 2 * c4);
+            if (8 * c4 + 4 < seg_words) b = __ldg(rowp + 2 * c4 + 1);
+            const uint32_t wv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
             uint32_t *dstw = reinterpret_cast<uint32_t *>(&st.word[slot][0]);
 #pragma unroll
-            for (int c4 = 0; c4 < 4; ++c4) {  // words g = 8 c4 + w, w = 0..7, stored at [w][c4]
-              uint4 a = make_uint4(0, 0, 0, 0), b = make_uint4(0, 0, 0, 0);
-              if (8 * c4 < seg_words) a = __ldg(rowp + 2 * c4);
-              if (8 * c4 + 4 < seg_words) b = __ldg(rowp + 2 * c4 + 1);
-              const uint32_t wv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-              for (int w = 0; w < DB_WARPS; ++w) {
-                uint32_t x = (wv[w] ^ xr) & am;
-                if (hw == 8 * c4 + w) x &= ~hbit;
-                dstw[4 * w + c4] = x;
-              }
+            for (int w = 0; w < DB_WARPS; ++w) {  // word g = 8 c4 + w is stored at [w][c4]
+              uint32_t x = (wv[w] ^ xr) & am;
+              if (hw == 8 * c4 + w) x &= ~hbit;
+              dstw[4 * w + c4] = x;
             }
-            st.ent[slot] = v;
+            if (c4 == 0) st.ent[slot] = v;
           }
           const int32_t rel = v.x - D0;
-          const bool is_hit = ok && rel >= 0 && rel < DB_SPAN;
+          const bool is_hit = ok && c4 == 0 && rel >= 0 && rel < DB_SPAN;
           const uint32_t hm = __ballot_sync(0xffffffffu, is_hit);
           if (is_hit) st.hit[hb + nh + __popc(hm & ((1u << lane) - 1u))] = (int16_t)slot;
           nh += __popc(hm);
@@ -785,14 +809,16 @@ __global__ void __launch_bounds__(DB_THREADS) eval_dense(EvalCtx cx, OutCtx oc, 
           gain[2] += (wd.z >> lane) & 1u;
           gain[3] += (wd.w >> lane) & 1u;
         }
-        const int32_t rb = st.rb[j], nr = h.w1.x;
-        for (int32_t e = 0; e < nr; ++e) {
-          const uint32_t sh = (uint32_t)st.ent[rb + e].w;
-          const uint4 wd = st.word[rb + e][warp];
-          iw[0] += ((wd.x >> lane) & 1u) << sh;
-          iw[1] += ((wd.y >> lane) & 1u) << sh;
-          iw[2] += ((wd.z >> lane) & 1u) << sh;
-          iw[3] += ((wd.w >> lane) & 1u) << sh;
+        if (mk4) {  // caller classes only matter when CBO is selected
+          const int32_t rb = st.rb[j], nr = h.w1.x;
+          for (int32_t e = 0; e < nr; ++e) {
+            const uint32_t sh = (uint32_t)st.ent[rb + e].w;
+            const uint4 wd = st.word[rb + e][warp];
+            iw[0] += ((wd.x >> lane) & 1u) << sh;
+            iw[1] += ((wd.y >> lane) & 1u) << sh;
+            iw[2] += ((wd.z >> lane) & 1u) << sh;
+            iw[3] += ((wd.w >> lane) & 1u) << sh;
+          }
         }
       }
       // hits: destinations of this thread that appear in m's lists
@@ -806,42 +832,48 @@ __global__ void __launch_bounds__(DB_THREADS) eval_dense(EvalCtx cx, OutCtx oc, 
         }
       }
       const uint4 cin = st.cw[j][0][warp], cout = st.cw[j][1][warp];
-      const int32_t os = h.w1.y > 0, is = h.w1.z > 0, l_all = h.w1.w;
-      const uint32_t sC = (uint32_t)h.w2.x & 15u;
-      const int sckC = dec_sign(sC & 3u), shsC = dec_sign(sC >> 2);
-      const int32_t upCl = ((mk & 1u) && sckC > 0) | ((mk & 2u) && shsC > 0);
-      const int32_t dnCl = ((mk & 1u) && sckC < 0) | ((mk & 2u) && shsC < 0);
+      const uint32_t os = h.w1.y > 0 ? 1u : 0u, is = h.w1.z > 0 ? 1u : 0u;
+      const int32_t pc0 = st.pc[j][0], pc1 = st.pc[j][1], fc0 = st.fc[j][0], fc1 = st.fc[j][1];
+      const int32_t rc0 = st.rc[j][0], rc1 = st.rc[j][1];
 #pragma unroll
       for (int q = 0; q < DQ; ++q) {
         const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
-        const bool act = D < c && D != C;
-        int32_t dck, dcbo;
+        const bool act = D < c && D != C && !((hitq >> q) & 1u);
+        // common path: m shares nothing with D and D is in neither of m's lists
+        const uint32_t bDC = (sel4(cin, q) >> lane) & 1u, bCD = (sel4(cout, q) >> lane) & 1u;
+        const uint32_t b = is & (bCD ^ 1u);                          // C starts using D
+        const int32_t dD = (int32_t)(gain[q] + (os & (bDC ^ 1u)));   // >= 0 on this path
+        const bool p = dD != 0;
+        const int32_t P = (b ? pc1 : pc0) + (p ? pd1[q] : pd0[q]) + (int32_t)iw[q];
+        const bool kept = (P >> 16) == 0 && (P & 0xffff) >= cx.min_improved;
+        const uint32_t flags = (uint32_t)(b ? fc1 : fc0) | (uint32_t)fd0[q] | (p ? (2u << 10) : 0u) |
+                               (kept ? 0x8000u : 0u);
         uint4 r;
-        if ((hitq >> q) & 1u) {
-          // exact general path: D appears in m's lists
-          dck = 0; dcbo = 0;
-          r = make_uint4(0, 0, 0, 0);
-          if (act)
-            r = dense_hit_path(cx, st, j, h, D, gain[q], iw[q], (sel4(cin, q) >> lane) & 1u,
-                               (sel4(cout, q) >> lane) & 1u, cls_n, cls_a, cls_P, cls_Q, cls_S, &dck, &dcbo);
-        } else {
-          const int32_t bDC = (int32_t)((sel4(cin, q) >> lane) & 1u);
-          const int32_t bCD = (int32_t)((sel4(cout, q) >> lane) & 1u);
-          const int32_t dD = (int32_t)gain[q] + (os & (bDC ^ 1));
-          const int32_t dC = (is & (bCD ^ 1)) - l_all;
-          const int32_t upC = upCl | (mk4 & (dC > 0)), dnC = dnCl | (mk4 & (dC < 0));
-          const int32_t upD = (dconst[q] & 1) | (mk4 & (dD > 0)), dnD = ((dconst[q] >> 1) & 1) | (mk4 & (dD < 0));
-          const int32_t imp = (dnC & (upC ^ 1)) + (dnD & (upD ^ 1)) + (mk4 ? (int32_t)(iw[q] & 0xffffu) : 0);
-          const int32_t wor = upC + upD + (mk4 ? (int32_t)(iw[q] >> 16) : 0);
-          uint32_t flags = sC | ((uint32_t)dconst[q] & 0x3c0u) | (enc_small(dC) << 4) | (enc_small(dD) << 10);
-          if (wor == 0 && imp >= cx.min_improved) flags |= 0x8000u;
-          r.x = 0u;
-          r.y = (uint32_t)(uint16_t)(int16_t)clamp16(dC) << 16;
-          r.z = (uint32_t)(uint16_t)(int16_t)clamp16(dD) | ((uint32_t)min(imp, 65535) << 16);
-          r.w = (uint32_t)min(wor, 65535) | (flags << 16);
-          dck = h.w2.y + dck0[q];
-          dcbo = dC + dD;
+        r.x = 0u;
+        r.y = (uint32_t)(b ? rc1 : rc0);
+        r.z = (uint32_t)dD | ((uint32_t)P << 16);
+        r.w = ((uint32_t)P >> 16) | (flags << 16);
+        if (REC && act) __stcs(oc.records + rowbase + D - (D > C ? 1 : 0), r);
+        if (DIG && act) dig += record_hash(m, D, r);
+        if (KEEP) {
+          const bool kk = act && kept;
+          const int32_t dck = kk ? h.w2.y + dck0[q] : 0;
+          emit_kept(oc, kk, m, D, r.z >> 16, dck, (int32_t)b - h.w1.w + dD, lane);
         }
+      }
+      // exact general path for destinations that appear in m's lists (rare)
+      uint32_t pending = hitq;
+      while (__any_sync(0xffffffffu, pending != 0)) {
+        int q = -1;
+        if (pending) {
+          q = __ffs(pending) - 1;
+          pending &= pending - 1;
+        }
+        const int32_t D = D0 + (int32_t)threadIdx.x + (q < 0 ? 0 : q) * DB_THREADS;
+        const bool act = q >= 0 && D < c && D != C;
+        int32_t dck = 0, dcbo = 0;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        if (act) r = dense_hit_path(cx, st, j, D, q, lane, warp, cls_n, cls_a, cls_P, cls_Q, cls_S, &dck, &dcbo);
         if (REC && act) __stcs(oc.records + rowbase + D - (D > C ? 1 : 0), r);
         if (DIG && act) dig += record_hash(m, D, r);
         if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
