@@ -61,7 +61,7 @@ def _peaks():
 class ClockSampler:
     """nvidia-smi sampling during the timed region (clocks + throttle reasons)."""
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -69,15 +69,19 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.window = None  # (t0, t1) wall-clock seconds of the timed region
+
+    def mark(self, t0: float, t1: float):
+        self.window = (t0, t1)
 
     def __enter__(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
-            time.sleep(0.3)
+            time.sleep(1.0)  # let nvidia-smi finish starting before any timing
         except Exception:
             self.proc = None
         return self
@@ -94,18 +98,25 @@ class ClockSampler:
     def summary(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        import datetime
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
-                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append(dict(t=ts, sm=float(parts[2]), smax=float(parts[3]), power=float(parts[4]),
+                                 hw=parts[6], hwt=parts[7], swt=parts[8], swp=parts[9]))
             except ValueError:
                 continue
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        inside = rows
+        if self.window:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 - 0.05 <= r["t"] <= t1 + 0.05] or rows
+        rows = inside
         load = [r for r in rows if r["power"] > 200.0] or rows
         reasons = sorted({name for r in rows for name, key in (("hw_slowdown", "hw"),
                                                                 ("hw_thermal_slowdown", "hwt"),
@@ -113,7 +124,8 @@ class ClockSampler:
                                                                 ("sw_power_cap", "swp"))
                           if r[key].lower() == "active"})
         return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["smax"] for r in rows),
-                "samples": len(rows), "reasons": reasons}
+                "samples": len(rows), "reasons": reasons,
+                "power_w_median": statistics.median(r["power"] for r in rows)}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -178,20 +190,20 @@ def run_ours(args, rank, world, local_rank):
             sys.exit(3)
         o.close()
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize(dev)
-
     dist = None
     if world > 1:
         import torch.distributed as dist
     step_ms, eval_ms = [], []
-    launches0 = mmref.launch_count()
     with ClockSampler(local_rank) as clk:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        launches0 = mmref.launch_count()
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
         t_wall0 = time.perf_counter()
+        t_epoch0 = time.time()
         for _ in range(args.steps):
             flush.fill_(1)  # L2 flush between steps, outside the timed events
             ev[2].record(stream)
@@ -204,6 +216,8 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.barrier()
         t_wall = time.perf_counter() - t_wall0
+        clk.mark(t_epoch0, time.time())
+        time.sleep(0.25)  # one more sample after the region
     launches = mmref.launch_count() - launches0
     total_ms = sum(step_ms)
     if dist:
@@ -233,9 +247,11 @@ def run_ours(args, rank, world, local_rank):
                        "candidates_per_step": n_cand, "criteria": {"metric_mask": mask, "min_improved": min_imp},
                        "topk": TOPK, "parallelism": f"replicas x{world}",
                        "l2": "512 MB L2 flush between steps (outside events); each step also writes 4.8 GB"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // max(args.steps, 1) * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "gpu_launches_per_step": launches / max(args.steps, 1), "clocks": clk.summary(),
-            "eval_ms_median": statistics.median(eval_ms), "step_ms": [round(x, 3) for x in step_ms],
+            "eval_ms_median": statistics.median(eval_ms),
+            "step_ms_min_median_max": [round(min(step_ms), 3), round(statistics.median(step_ms), 3),
+                                       round(max(step_ms), 3)],
             "wall_s_timed_region": round(t_wall, 3), "verified_vs_oracle": verified}
     return line
 
@@ -327,7 +343,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-verify", action="store_true")
