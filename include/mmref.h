@@ -242,6 +242,34 @@ MMREF_API mm_status mm_suggest_moves(mm_system *sys, const mm_criteria *crit, co
                            int32_t k, mm_move *out_topk, int32_t out_kind, int64_t *n_kept,
                            int64_t *n_methods_with_kept);
 
+/*
+ * Allocation-free variant of mm_suggest_moves.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory at
+ * the time they ask for suggestions -- a serving process whose device memory
+ * is entirely reserved by its own fixed-budget allocator, or a latency-critical
+ * loop that must not trigger allocation (which can stall or fail under memory
+ * pressure).  It computes the same result as mm_suggest_moves (same criteria,
+ * same order) but calls no cudaMalloc, cudaFree or allocating routine: its
+ * working memory is a static device array of about 4.2 MB in the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Limits: the system has at most MM_NOALLOC_MAX_METHODS methods and the
+ * criteria keep at most MM_NOALLOC_MAX_KEPT moves; beyond either the call
+ * returns MM_EBUDGET with a message naming the limit, and mm_suggest_moves
+ * must be used instead.  Candidate lists must be NULL (full cross product) or
+ * in device memory.  out_topk is in out_kind memory.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls in the process share the one array and
+ * each call clears what it needs; calls that overlap on the GPU (from several
+ * threads or streams) race on it and must be serialised by the caller.
+ * Synchronises the system's stream.
+ */
+#define MM_NOALLOC_MAX_METHODS 1048576
+#define MM_NOALLOC_MAX_KEPT 65536
+MMREF_API mm_status mm_suggest_moves_noalloc(mm_system *sys, const mm_criteria *crit, const mm_candidates *cands,
+                                             int32_t k, mm_move *out_topk, int32_t out_kind, int64_t *n_kept,
+                                             int64_t *n_methods_with_kept);
+
 /* Sizes and device memory of a loaded system (host struct). */
 MMREF_API mm_status mm_system_info_get(mm_system *sys, mm_system_info *info);
 

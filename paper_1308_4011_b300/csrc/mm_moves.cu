@@ -550,7 +550,6 @@ constexpr int DQ = 4;
 constexpr int DB_THREADS = 256;
 constexpr int DB_WARPS = DB_THREADS / 32;
 constexpr int DB_SPAN = DB_THREADS * DQ;
-constexpr int DB_WORDS = DB_SPAN / 32;
 constexpr int DB_MB = 32;
 constexpr int DB_ECAP = 192;
 
@@ -1272,4 +1271,37 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
   MM_CUDA_TRY(cudaStreamSynchronize(st));
   if (n_kept) *n_kept = K;
   if (n_mk) *n_mk = nm;
+}
+
+// ---------------------------------------------------------------- helpers for the allocation-free entry point
+
+// Evaluate the candidates (full cross product or device-resident lists) and
+// compact the kept moves into caller-provided device buffers; allocates nothing.
+// *count and mark[M] must be zero on entry.
+void eval_kept_into(mm_system *s, const mm_criteria &crit, const mm_candidates *cands, mm_move *kept, int64_t cap,
+                    unsigned long long *count, uint8_t *mark) {
+  check_criteria(crit);
+  if (cands && cands->rowptr && cands->ptr_kind != MM_PTR_DEVICE)
+    throw MmError{MM_EINVAL, "candidate lists must be in device memory here"};
+  const int64_t *rowptr;
+  const int32_t *dst;
+  int64_t n_cand;
+  Scratch unused;
+  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, unused);
+  if (n_cand == 0 || s->M == 0) return;
+  EvalCtx cx = make_ctx(s, crit);
+  OutCtx oc{};
+  oc.kept = kept;
+  oc.kept_count = count;
+  oc.kept_cap = cap;
+  oc.kept_mark = mark;
+  dispatch_eval(s, cx, oc, rowptr, dst);
+}
+
+// Sort up to 2,048 kept moves in place (single-block bitonic sort).
+void sort_moves_small(mm_move *v, int32_t n, cudaStream_t st) {
+  if (n <= 1) return;
+  if (n > BITONIC_MAX) throw MmError{MM_EINVAL, "sort_moves_small: more than 2048 moves"};
+  bitonic_sort_moves<<<1, 1024, 0, st>>>(v, n);
+  MM_LAUNCH_CHECK();
 }

@@ -31,7 +31,7 @@ DEFAULT_MIN_IMPROVED = 2
 
 EXPORTED = ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluate_moves", "mm_suggest_moves",
             "mm_system_info_get", "mm_free_system", "mm_last_error", "mm_status_string", "mm_abi_version",
-            "mm_launch_count")
+            "mm_launch_count", "mm_suggest_moves_noalloc")
 
 CLASS_METRICS_DTYPE = np.dtype([("n_methods", "<i4"), ("n_attrs", "<i4"), ("P", "<i8"), ("Q", "<i8"),
                                 ("S", "<i8"), ("lcom_ck", "<i8"), ("hs_num", "<i8"), ("hs_den", "<i8"),
@@ -76,6 +76,11 @@ _lib.mm_evaluate_moves.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.POINTER(_C
 _lib.mm_suggest_moves.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.POINTER(_Cands), ctypes.c_int32, _vp,
                                   ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
 _lib.mm_system_info_get.argtypes = [_vp, ctypes.POINTER(_Info)]
+_lib.mm_suggest_moves_noalloc.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.POINTER(_Cands), ctypes.c_int32, _vp,
+                                          ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+_lib.mm_suggest_moves_noalloc.restype = ctypes.c_int
+NOALLOC_MAX_METHODS = 1048576
+NOALLOC_MAX_KEPT = 65536
 _lib.mm_free_system.argtypes = [_vp]
 _lib.mm_free_system.restype = None
 _lib.mm_last_error.restype = ctypes.c_char_p
@@ -254,6 +259,23 @@ def suggest_moves(sys: System, k: int, mask: int = DEFAULT_MASK, min_improved: i
     nk, nm = ctypes.c_int64(), ctypes.c_int64()
     _check(_lib.mm_suggest_moves(sys.handle, ctypes.byref(crit), ctypes.byref(cd) if cd else None, int(k),
                                  _ptr(out), _kind(out), ctypes.byref(nk), ctypes.byref(nm)))
+    del keep
+    n = min(int(k), int(nk.value))
+    return (out[:n] if _kind(out) == PTR_HOST else out), int(nk.value), int(nm.value)
+
+
+def suggest_moves_noalloc(sys: System, k: int, mask: int = DEFAULT_MASK, min_improved: int = DEFAULT_MIN_IMPROVED,
+                          cand_rowptr=None, cand_dst=None, out=None):
+    """mm_suggest_moves_noalloc: same result as suggest_moves, computed in the
+    library's fixed static device array without allocating device memory (for
+    callers that cannot allocate).  Candidate lists must be CUDA tensors."""
+    crit = _Crit(mask, min_improved)
+    cd, keep = _cands(cand_rowptr, cand_dst)
+    if out is None:
+        out = np.zeros(max(k, 0), dtype=MOVE_DTYPE)
+    nk, nm = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.mm_suggest_moves_noalloc(sys.handle, ctypes.byref(crit), ctypes.byref(cd) if cd else None, int(k),
+                                         _ptr(out), _kind(out), ctypes.byref(nk), ctypes.byref(nm)))
     del keep
     n = min(int(k), int(nk.value))
     return (out[:n] if _kind(out) == PTR_HOST else out), int(nk.value), int(nm.value)
