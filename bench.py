@@ -340,6 +340,80 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_batched(args, rank, world, local_rank):
+    """256 independent systems (class counts log-uniform in 100..20,000, 12
+    methods and 6 attributes per class, seeds 100..355): one persistent launch
+    under a CUDA graph vs the same systems one after another."""
+    import torch
+    from paper_1308_4011_b300 import mmref, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n_sys = args.batch_systems
+    params = [synth.batched_params(100 + i) for i in range(n_sys)]
+    loaded, shapes = [], []
+    t0 = time.perf_counter()
+    for p in params:
+        s = synth.generate(**p)
+        loaded.append(mmref.load_synth(s, device=True))
+        shapes.append((s.n_classes, s.n_methods))
+    gen_s = time.perf_counter() - t0
+    n_cand = sum(m * (c - 1) for c, m in shapes)
+    mask, mi = mmref.DEFAULT_MASK, mmref.DEFAULT_MIN_IMPROVED
+    stream = torch.cuda.current_stream(dev)
+    # kept-move capacity per system: the largest count of a first pass
+    b0 = mmref.Batch(loaded, mask=mask, min_improved=mi, kept_cap=1, stream=stream)
+    _, counts0 = b0.run(digest=False)
+    b0.free()
+    cap = int(max(int(counts0.max()), 1) * 1.1) + 64
+    b = mmref.Batch(loaded, mask=mask, min_improved=mi, kept_cap=cap, stream=stream)
+    tile = b.autotune()
+    # verification: per-system digests of the batch equal the single-system launches
+    dig, nk = b.run(digest=True)
+    d1 = torch.zeros(n_sys, dtype=torch.int64, device=dev)
+    for i, g in enumerate(loaded):
+        mmref.evaluate_moves(g, mask, mi, digest=d1[i:i + 1])
+    torch.cuda.synchronize(dev)
+    ok = bool(np.array_equal(d1.cpu().numpy().view(np.uint64), dig))
+    k = TOPK
+
+    def batched():  # metrics + evaluation + kept moves + sorted suggestions, then top-k of every system
+        _, counts = b.run(digest=False)
+        return [b.suggestions(i, k)[0] for i in range(n_sys)], counts
+
+    def sequential():  # the same systems one after another through the single-system calls
+        out = []
+        for g in loaded:
+            mmref.compute_metrics(g, None, None)
+            out.append(mmref.suggest_moves(g, k, mask, mi)[0])
+        return out
+
+    tops_b, counts = batched()
+    tops_s = sequential()
+    ok_top = all(np.array_equal(x, y) for x, y in zip(tops_b, tops_s))
+    times_b, times_s = [], []
+    reps = max(3, args.steps // 10)
+    for _ in range(reps):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter(); sequential(); torch.cuda.synchronize(dev); times_s.append(time.perf_counter() - t)
+    batched()  # warm after the sequential calls (sorting large kept lists may grow scratch)
+    for _ in range(reps):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter(); batched(); torch.cuda.synchronize(dev); times_b.append(time.perf_counter() - t)
+    tb, ts = statistics.median(times_b), statistics.median(times_s)
+    b.free()
+    for g in loaded:
+        g.free()
+    return {"metric": METRIC, "value": n_cand / tb, "unit": UNIT, "workload": "batched",
+            "config": {"workload": f"{n_sys} systems, classes log-uniform 100..20,000, 12 methods/class, "
+                                   f"seeds 100..{99 + n_sys}, full cross products (digest + kept moves)",
+                       "candidates": n_cand, "tile_methods": tile, "kept_cap_per_system": cap},
+            "batched_s": tb, "sequential_s": ts, "speedup_vs_sequential": ts / tb,
+            "sequential_value": n_cand / ts, "digests_equal_single_system": ok, "topk_equal_sequential": ok_top,
+            "generate_and_load_s": gen_s, "n_kept_total": int(counts.sum()),
+            "note": "timed: metrics + full evaluation + kept moves + top-100 per system, no digest"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,6 +422,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["medium", "batched"], default="medium",
+                    help="batched = the 256-system batch vs sequential launches (its own JSON line)")
+    ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--case", choices=["medium", "small"], default="medium",
                     help="small = profiling case (1,000 classes, 12,000 methods, 192 MB of records); "
                          "not a bench line")
@@ -359,6 +436,9 @@ def main():
         line = run_reference(args, rank, world)
         if line is not None:
             print(json.dumps(line), flush=True)
+        return
+    if args.workload == "batched":
+        print(json.dumps(run_batched(args, rank, world, local_rank)), flush=True)
         return
     if world > 1:
         import torch

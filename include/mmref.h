@@ -270,6 +270,38 @@ MMREF_API mm_status mm_suggest_moves_noalloc(mm_system *sys, const mm_criteria *
                                              int32_t k, mm_move *out_topk, int32_t out_kind, int64_t *n_kept,
                                              int64_t *n_methods_with_kept);
 
+/*
+ * Batched evaluation (no counterpart in the paper; the paper analyses one
+ * system at a time, Sec. V).  A batch holds many loaded systems of very
+ * uneven sizes.  mm_batch_run computes every system's metrics (as
+ * mm_compute_metrics) and evaluates every system's full cross product in one
+ * persistent work-stealing launch; the whole sequence is captured once in a
+ * CUDA graph and replayed on later runs.  Per system it yields the digest of
+ * all its records (as mm_evaluate_moves) and its kept moves for `crit`
+ * (as mm_suggest_moves), up to kept_cap moves per system.
+ * While a batch exists its systems must not be used by other calls
+ * concurrently; results of other calls on them stay valid.
+ */
+typedef struct mm_batch mm_batch;
+
+/* Create a batch over systems[0..n) (all loaded on the current device; their
+ * metrics need not be computed).  The stream orders every batch call. */
+MMREF_API mm_status mm_batch_create(mm_system *const *systems, int32_t n, const mm_criteria *crit,
+                                    int64_t kept_cap, void *cuda_stream, mm_batch **out);
+/* Methods per evaluation tile (default 256, or the autotuned value). */
+MMREF_API mm_status mm_batch_set_tile(mm_batch *b, int32_t methods_per_tile);
+/* Time a few tile sizes on this batch, keep the fastest (cached in the
+ * process per batch shape) and return it in *chosen. */
+MMREF_API mm_status mm_batch_autotune(mm_batch *b, int32_t *chosen);
+/* Run: digests[n] and n_kept[n] (host, nullable) receive each system's digest
+ * and kept-move count.  Synchronises the batch stream. */
+MMREF_API mm_status mm_batch_run(mm_batch *b, uint64_t *digests, int64_t *n_kept);
+/* Sorted suggestions of system i from the last run (order of mm_move);
+ * MM_EBUDGET if that system kept more than kept_cap moves. */
+MMREF_API mm_status mm_batch_suggestions(mm_batch *b, int32_t i, int32_t k, mm_move *out_topk, int32_t out_kind,
+                                         int64_t *n_kept);
+MMREF_API void mm_batch_free(mm_batch *b);
+
 /* Sizes and device memory of a loaded system (host struct). */
 MMREF_API mm_status mm_system_info_get(mm_system *sys, mm_system_info *info);
 

@@ -189,3 +189,26 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
                     mm_move_eval *records, uint64_t *digest, int32_t kind);
 void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *cands, int32_t k,
                    mm_move *out, int32_t kind, int64_t *n_kept, int64_t *n_mk);
+
+// ---------------------------------------------------------------- batched evaluation (mm_moves.cu)
+
+// One system of a batch and where its results go (all device pointers).
+struct BatchLaunchSpec {
+  mm_system *sys;
+  unsigned long long *digest;      // one per system
+  mm_move *kept;                   // kept_cap per system (nullable)
+  unsigned long long *kept_count;  // one per system
+  uint8_t *kept_mark;              // M bytes per system
+};
+int64_t batch_tiles(const mm_system *s, int32_t mchunk);
+size_t batch_item_bytes();
+void batch_fill_items(const BatchLaunchSpec *specs, int32_t n, const mm_criteria &crit, int32_t mchunk,
+                      int64_t kept_cap, void *items_host, int64_t *total_tiles);
+void batch_launch(const void *items_dev, int32_t n, int64_t total_tiles, int32_t mchunk, bool keep, bool digest,
+                  unsigned long long *next_tile, int grid, cudaStream_t st);
+void sort_moves_segments(mm_move *base, int64_t stride, const unsigned long long *counts, int32_t n,
+                         cudaStream_t st);
+constexpr int64_t kSegmentSortMax = 2048;
+int batch_persistent_grid();
+void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K);
+void check_criteria_public(const mm_criteria &crit);

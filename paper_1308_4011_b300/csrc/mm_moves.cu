@@ -625,15 +625,28 @@ __device__ __noinline__ uint4 dense_global_path(const EvalCtx &cx, const MoveHdr
   return r;
 }
 
+// Parameters of one system for the dense evaluation (also the unit of the
+// batched persistent kernel).
+struct DenseSys {
+  EvalCtx cx;
+  const int32_t *cls_n, *cls_a;
+  const int64_t *cls_P, *cls_Q, *cls_S;
+  int32_t c, M;
+};
+
+// One tile of the dense cross product: destinations [bx*DB_SPAN, +DB_SPAN) x
+// methods [m0, m1).  Called by every thread of a block; returns this thread's
+// digest partial.
 template <bool REC, bool DIG, bool KEEP>
-__global__ void __launch_bounds__(DB_THREADS) eval_dense(EvalCtx cx, OutCtx oc, const int32_t *cls_n,
-                                                         const int32_t *cls_a, const int64_t *cls_P,
-                                                         const int64_t *cls_Q, const int64_t *cls_S, int32_t c,
-                                                         int32_t M, int32_t mchunk) {
-  __shared__ __align__(16) DenseStage st;
+__device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx &oc, DenseStage &st, int32_t bx,
+                                               int32_t m0, int32_t m1) {
+  const EvalCtx &cx = sy.cx;
+  const int32_t *cls_n = sy.cls_n, *cls_a = sy.cls_a;
+  const int64_t *cls_P = sy.cls_P, *cls_Q = sy.cls_Q, *cls_S = sy.cls_S;
+  const int32_t c = sy.c;
   const uint32_t lane = threadIdx.x & 31u;
   const int warp = (int)(threadIdx.x >> 5);
-  const int32_t D0 = (int32_t)blockIdx.x * DB_SPAN;
+  const int32_t D0 = bx * DB_SPAN;
   const int64_t dw0 = D0 >> 5;
   const uint32_t mk = cx.mask;
   const int32_t mk4 = (mk & 4u) ? 1 : 0;
@@ -653,8 +666,6 @@ __global__ void __launch_bounds__(DB_THREADS) eval_dense(EvalCtx cx, OutCtx oc, 
     fd0[q] = (int32_t)((enc_sign(ds.sck0) << 6) | (enc_sign(ds.shs0) << 8));
     dck0[q] = ds.dck0;
   }
-  const int32_t m0 = blockIdx.y * mchunk;
-  const int32_t m1 = min(M, m0 + mchunk);
   const int64_t row = (int64_t)c - 1;
   const int64_t seg_words = cx.aw - dw0;  // adjacency words left in a row from dw0 (may exceed 32)
   uint64_t dig = 0;
@@ -881,9 +892,18 @@ __global__ void __launch_bounds__(DB_THREADS) eval_dense(EvalCtx cx, OutCtx oc, 
     mb += k;
     __syncthreads();
   }
+  return dig;
+}
+
+template <bool REC, bool DIG, bool KEEP>
+__global__ void __launch_bounds__(DB_THREADS) eval_dense(DenseSys sy, OutCtx oc, int32_t mchunk) {
+  __shared__ __align__(16) DenseStage st;
+  const int32_t m0 = blockIdx.y * mchunk;
+  const int32_t m1 = min(sy.M, m0 + mchunk);
+  uint64_t dig = dense_tile<REC, DIG, KEEP>(sy, oc, st, (int32_t)blockIdx.x, m0, m1);
   if (DIG) {
     for (int o = 16; o > 0; o >>= 1) dig += __shfl_down_sync(0xffffffffu, dig, o);
-    if (lane == 0 && dig) atomicAdd(oc.digest, (unsigned long long)dig);
+    if ((threadIdx.x & 31u) == 0 && dig) atomicAdd(oc.digest, (unsigned long long)dig);
   }
 }
 
@@ -953,8 +973,8 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
     int64_t want_y = std::max<int64_t>(1, (148 * 16 + gx - 1) / gx);
     int32_t mchunk = (int32_t)std::max<int64_t>(1, ceil_div(M, want_y));
     unsigned gy = (unsigned)ceil_div(M, mchunk);
-    eval_dense<REC, DIG, KEEP><<<dim3(gx, gy), DB_THREADS, 0, st>>>(cx, oc, s->cls_n, s->cls_a, s->cls_P, s->cls_Q,
-                                                             s->cls_S, c, M, mchunk);
+    DenseSys sy{cx, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, c, M};
+    eval_dense<REC, DIG, KEEP><<<dim3(gx, gy), DB_THREADS, 0, st>>>(sy, oc, mchunk);
   } else {
     unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)s->M * 32, 256), 148 * 64);
     eval_csr<REC, DIG, KEEP><<<g, 256, 0, st>>>(cx, oc, rowptr, dst, s->cls_n, s->cls_a, s->cls_P, s->cls_Q,
@@ -989,9 +1009,8 @@ __device__ __forceinline__ bool move_before(const mm_move &a, const mm_move &b) 
 
 constexpr int BITONIC_MAX = 2048;
 
-// single-block bitonic sort of up to 2048 kept moves in shared memory
-__global__ void __launch_bounds__(1024) bitonic_sort_moves(mm_move *v, int32_t n) {
-  __shared__ mm_move sm[BITONIC_MAX];
+// one block sorts up to 2048 kept moves in shared memory (bitonic network)
+__device__ __forceinline__ void bitonic_block(mm_move *v, int32_t n, mm_move *sm) {
   int32_t np = 1;
   while (np < n) np <<= 1;
   for (int32_t i = threadIdx.x; i < np; i += blockDim.x) {
@@ -1019,6 +1038,20 @@ __global__ void __launch_bounds__(1024) bitonic_sort_moves(mm_move *v, int32_t n
     }
   }
   for (int32_t i = threadIdx.x; i < n; i += blockDim.x) v[i] = sm[i];
+}
+
+__global__ void __launch_bounds__(1024) bitonic_sort_moves(mm_move *v, int32_t n) {
+  __shared__ mm_move sm[BITONIC_MAX];
+  bitonic_block(v, n, sm);
+}
+
+// block i sorts segment i (base + i*stride, counts[i] moves) when it fits in one block
+__global__ void __launch_bounds__(1024) bitonic_sort_segments(mm_move *base, int64_t stride,
+                                                              const unsigned long long *counts) {
+  __shared__ mm_move sm[BITONIC_MAX];
+  const unsigned long long K = counts[blockIdx.x];
+  if (K < 2 || K > (unsigned long long)BITONIC_MAX || (int64_t)K > stride) return;
+  bitonic_block(base + (int64_t)blockIdx.x * stride, (int32_t)K, sm);
 }
 
 // field-wise LSD radix sort of kept moves through a permutation
@@ -1193,6 +1226,38 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
   if (kind == MM_PTR_HOST) MM_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
+// Sort kept moves in the suggestion order: one-block bitonic sort up to 2,048,
+// else a stable LSD radix sort field by field (d, m, dCBO, dLCOM, n_improved desc)
+// through a permutation.
+void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K) {
+  cudaStream_t st = s->stream;
+  if (K > 1 && K <= BITONIC_MAX) {
+    bitonic_sort_moves<<<1, 1024, 0, st>>>(kept, (int32_t)K);
+    MM_LAUNCH_CHECK();
+  } else if (K > BITONIC_MAX) {
+    // permutation sort, least significant field first (d, m, dCBO, dLCOM, n_improved desc)
+    size_t pb = sizeof(uint32_t) * 4 * (size_t)K;
+    uint32_t *pw = static_cast<uint32_t *>(s->stage_ws.need(pb + sizeof(mm_move) * (size_t)K + 256, st));
+    uint32_t *key = pw, *key_alt = pw + K, *perm = pw + 2 * K, *perm_alt = pw + 3 * K;
+    mm_move *sorted = reinterpret_cast<mm_move *>(pw + 4 * K);
+    iota_perm<<<grid_for(K), TPB, 0, st>>>(perm, K);
+    MM_LAUNCH_CHECK();
+    const int64_t bias_cbo = 2 * (int64_t)s->c + 4;
+    const int64_t bias_ck = 4 * (int64_t)std::max(s->summary.max_class_methods, 1) + 4;
+    const int fbits[5] = {bits_for((uint64_t)std::max(s->c - 1, 0)), bits_for((uint64_t)std::max(s->M - 1, 0)),
+                          bits_for((uint64_t)(2 * bias_cbo)), bits_for((uint64_t)(2 * bias_ck)), 16};
+    const int64_t bias[5] = {0, 0, bias_cbo, bias_ck, 0};
+    for (int f = 0; f < 5; ++f) {
+      gather_field<<<grid_for(K), TPB, 0, st>>>(kept, perm, K, f, bias[f], key);
+      MM_LAUNCH_CHECK();
+      radix_sort_u32(key, key_alt, perm, perm_alt, K, fbits[f], s->sort_ws, st);
+    }
+    permute_moves<<<grid_for(K), TPB, 0, st>>>(kept, perm, K, sorted);
+    MM_LAUNCH_CHECK();
+    MM_CUDA_TRY(cudaMemcpyAsync(kept, sorted, sizeof(mm_move) * (size_t)K, cudaMemcpyDeviceToDevice, st));
+  }
+}
+
 void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *cands, int32_t k, mm_move *out,
                    int32_t kind, int64_t *n_kept, int64_t *n_mk) {
   check_criteria(crit);
@@ -1238,31 +1303,7 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
       s->kept_mask = crit.metric_mask;
       s->kept_min = crit.min_improved;
     }
-    if (K > 1 && K <= BITONIC_MAX) {
-      bitonic_sort_moves<<<1, 1024, 0, st>>>(kept, (int32_t)K);
-      MM_LAUNCH_CHECK();
-    } else if (K > BITONIC_MAX) {
-      // permutation sort, least significant field first (d, m, dCBO, dLCOM, n_improved desc)
-      size_t pb = sizeof(uint32_t) * 4 * (size_t)K;
-      uint32_t *pw = static_cast<uint32_t *>(s->stage_ws.need(pb + sizeof(mm_move) * (size_t)K + 256, st));
-      uint32_t *key = pw, *key_alt = pw + K, *perm = pw + 2 * K, *perm_alt = pw + 3 * K;
-      mm_move *sorted = reinterpret_cast<mm_move *>(pw + 4 * K);
-      iota_perm<<<grid_for(K), TPB, 0, st>>>(perm, K);
-      MM_LAUNCH_CHECK();
-      const int64_t bias_cbo = 2 * (int64_t)s->c + 4;
-      const int64_t bias_ck = 4 * (int64_t)std::max(s->summary.max_class_methods, 1) + 4;
-      const int fbits[5] = {bits_for((uint64_t)std::max(s->c - 1, 0)), bits_for((uint64_t)std::max(s->M - 1, 0)),
-                            bits_for((uint64_t)(2 * bias_cbo)), bits_for((uint64_t)(2 * bias_ck)), 16};
-      const int64_t bias[5] = {0, 0, bias_cbo, bias_ck, 0};
-      for (int f = 0; f < 5; ++f) {
-        gather_field<<<grid_for(K), TPB, 0, st>>>(kept, perm, K, f, bias[f], key);
-        MM_LAUNCH_CHECK();
-        radix_sort_u32(key, key_alt, perm, perm_alt, K, fbits[f], s->sort_ws, st);
-      }
-      permute_moves<<<grid_for(K), TPB, 0, st>>>(kept, perm, K, sorted);
-      MM_LAUNCH_CHECK();
-      MM_CUDA_TRY(cudaMemcpyAsync(kept, sorted, sizeof(mm_move) * (size_t)K, cudaMemcpyDeviceToDevice, st));
-    }
+    sort_kept_moves(s, kept, K);
   }
   int64_t nout = std::min<int64_t>(k, K);
   if (nout > 0)
@@ -1303,5 +1344,123 @@ void sort_moves_small(mm_move *v, int32_t n, cudaStream_t st) {
   if (n <= 1) return;
   if (n > BITONIC_MAX) throw MmError{MM_EINVAL, "sort_moves_small: more than 2048 moves"};
   bitonic_sort_moves<<<1, 1024, 0, st>>>(v, n);
+  MM_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------- batched persistent evaluation
+
+namespace {
+
+struct BatchItem {
+  DenseSys sy;
+  OutCtx oc;
+  int64_t tile0;  // first global tile index of this system
+  int32_t gx;     // destination blocks of this system
+  int32_t pad;
+};
+
+// One persistent launch over every system of a batch: blocks take
+// (system, destination block, method chunk) tiles from a global counter and run
+// the same dense_tile as the single-system kernel.
+template <bool DIG, bool KEEP>
+__global__ void __launch_bounds__(DB_THREADS, 3) eval_dense_batched(const BatchItem *items, int32_t n,
+                                                                    int64_t total_tiles, int32_t mchunk,
+                                                                    unsigned long long *next_tile) {
+  __shared__ __align__(16) DenseStage st;
+  __shared__ long long s_t;
+  __shared__ __align__(16) BatchItem s_it;  // the current tile's system, read by every thread
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long t = (long long)atomicAdd(next_tile, 1ull);
+      s_t = t;
+      if (t < total_tiles) {
+        int32_t lo = 0, hi = n - 1;  // last item with tile0 <= t
+        while (lo < hi) {
+          int32_t mid = (lo + hi + 1) >> 1;
+          if (items[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+        }
+        s_it = items[lo];
+      }
+    }
+    __syncthreads();
+    const int64_t t = s_t;
+    if (t >= total_tiles) break;
+    const BatchItem &it = s_it;
+    const int64_t local = t - it.tile0;
+    const int32_t bx = (int32_t)(local % it.gx);
+    const int32_t m0 = (int32_t)(local / it.gx) * mchunk;
+    const int32_t m1 = min(it.sy.M, m0 + mchunk);
+    uint64_t dig = dense_tile<false, DIG, KEEP>(it.sy, it.oc, st, bx, m0, m1);
+    if (DIG) {
+      for (int o = 16; o > 0; o >>= 1) dig += __shfl_down_sync(0xffffffffu, dig, o);
+      if ((threadIdx.x & 31u) == 0 && dig) atomicAdd(it.oc.digest, (unsigned long long)dig);
+    }
+    __syncthreads();  // every thread is done with s_it / s_t before the next tile overwrites them
+  }
+}
+
+}  // namespace
+
+// Host side of the batched evaluation (see mm_batch.cu).
+int64_t batch_tiles(const mm_system *s, int32_t mchunk) {
+  if (s->M == 0 || s->c < 2) return 0;
+  return ceil_div(s->c, DB_SPAN) * ceil_div(s->M, mchunk);
+}
+
+void batch_fill_items(const BatchLaunchSpec *specs, int32_t n, const mm_criteria &crit, int32_t mchunk,
+                      int64_t kept_cap, void *items_host, int64_t *total_tiles) {
+  BatchItem *items = static_cast<BatchItem *>(items_host);
+  int64_t t = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    mm_system *s = specs[i].sys;
+    EvalCtx cx = make_ctx(s, crit);
+    BatchItem &it = items[i];
+    it.sy = DenseSys{cx, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, s->c, s->M};
+    it.oc = OutCtx{};
+    it.oc.digest = specs[i].digest;
+    it.oc.kept = specs[i].kept;
+    it.oc.kept_count = specs[i].kept_count;
+    it.oc.kept_cap = kept_cap;
+    it.oc.kept_mark = specs[i].kept_mark;
+    it.tile0 = t;
+    it.gx = (int32_t)std::max<int64_t>(1, ceil_div(s->c, DB_SPAN));
+    it.pad = 0;
+    t += batch_tiles(s, mchunk);
+  }
+  *total_tiles = t;
+}
+
+size_t batch_item_bytes() { return sizeof(BatchItem); }
+
+void batch_launch(const void *items_dev, int32_t n, int64_t total_tiles, int32_t mchunk, bool keep, bool digest,
+                  unsigned long long *next_tile, int grid, cudaStream_t st) {
+  if (total_tiles == 0) return;
+  const BatchItem *items = static_cast<const BatchItem *>(items_dev);
+  if (keep && digest)
+    eval_dense_batched<true, true><<<grid, DB_THREADS, 0, st>>>(items, n, total_tiles, mchunk, next_tile);
+  else if (keep)
+    eval_dense_batched<false, true><<<grid, DB_THREADS, 0, st>>>(items, n, total_tiles, mchunk, next_tile);
+  else if (digest)
+    eval_dense_batched<true, false><<<grid, DB_THREADS, 0, st>>>(items, n, total_tiles, mchunk, next_tile);
+  else
+    eval_dense_batched<false, false><<<grid, DB_THREADS, 0, st>>>(items, n, total_tiles, mchunk, next_tile);
+  MM_LAUNCH_CHECK();
+}
+
+int batch_persistent_grid() {
+  int dev = 0, sms = 148, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_dense_batched<true, true>, DB_THREADS, 0);
+  return sms * std::max(per_sm, 1);
+}
+
+void check_criteria_public(const mm_criteria &crit) { check_criteria(crit); }
+
+// Sort every segment holding at most 2,048 moves (one block per segment).
+void sort_moves_segments(mm_move *base, int64_t stride, const unsigned long long *counts, int32_t n,
+                         cudaStream_t st) {
+  if (n <= 0) return;
+  bitonic_sort_segments<<<n, 1024, 0, st>>>(base, stride, counts);
   MM_LAUNCH_CHECK();
 }

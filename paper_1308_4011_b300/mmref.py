@@ -31,7 +31,8 @@ DEFAULT_MIN_IMPROVED = 2
 
 EXPORTED = ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluate_moves", "mm_suggest_moves",
             "mm_system_info_get", "mm_free_system", "mm_last_error", "mm_status_string", "mm_abi_version",
-            "mm_launch_count", "mm_suggest_moves_noalloc")
+            "mm_launch_count", "mm_suggest_moves_noalloc", "mm_batch_create", "mm_batch_set_tile",
+            "mm_batch_autotune", "mm_batch_run", "mm_batch_suggestions", "mm_batch_free")
 
 CLASS_METRICS_DTYPE = np.dtype([("n_methods", "<i4"), ("n_attrs", "<i4"), ("P", "<i8"), ("Q", "<i8"),
                                 ("S", "<i8"), ("lcom_ck", "<i8"), ("hs_num", "<i8"), ("hs_den", "<i8"),
@@ -79,6 +80,17 @@ _lib.mm_system_info_get.argtypes = [_vp, ctypes.POINTER(_Info)]
 _lib.mm_suggest_moves_noalloc.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.POINTER(_Cands), ctypes.c_int32, _vp,
                                           ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
 _lib.mm_suggest_moves_noalloc.restype = ctypes.c_int
+_lib.mm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_Crit), ctypes.c_int64, _vp,
+                                 ctypes.POINTER(_vp)]
+_lib.mm_batch_set_tile.argtypes = [_vp, ctypes.c_int32]
+_lib.mm_batch_autotune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+_lib.mm_batch_run.argtypes = [_vp, _vp, _vp]
+_lib.mm_batch_suggestions.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int64)]
+_lib.mm_batch_free.argtypes = [_vp]
+_lib.mm_batch_free.restype = None
+for _n in ("mm_batch_create", "mm_batch_set_tile", "mm_batch_autotune", "mm_batch_run", "mm_batch_suggestions"):
+    getattr(_lib, _n).restype = ctypes.c_int
 NOALLOC_MAX_METHODS = 1048576
 NOALLOC_MAX_KEPT = 65536
 _lib.mm_free_system.argtypes = [_vp]
@@ -279,3 +291,51 @@ def suggest_moves_noalloc(sys: System, k: int, mask: int = DEFAULT_MASK, min_imp
     del keep
     n = min(int(k), int(nk.value))
     return (out[:n] if _kind(out) == PTR_HOST else out), int(nk.value), int(nm.value)
+
+
+class Batch:
+    """Many systems evaluated by one persistent launch under a CUDA graph
+    (mm_batch_*).  The systems must stay alive while the batch exists."""
+
+    def __init__(self, systems, mask: int = DEFAULT_MASK, min_improved: int = DEFAULT_MIN_IMPROVED,
+                 kept_cap: int = 4096, stream=None):
+        self.systems = list(systems)
+        arr = (_vp * len(self.systems))(*[s.handle.value for s in self.systems])
+        crit = _Crit(mask, min_improved)
+        h = _vp()
+        _check(_lib.mm_batch_create(arr, len(self.systems), ctypes.byref(crit), int(kept_cap),
+                                    _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self.n = len(self.systems)
+
+    def set_tile(self, methods_per_tile: int):
+        _check(_lib.mm_batch_set_tile(self._h, int(methods_per_tile)))
+
+    def autotune(self) -> int:
+        c = ctypes.c_int32()
+        _check(_lib.mm_batch_autotune(self._h, ctypes.byref(c)))
+        return int(c.value)
+
+    def run(self, digest: bool = True):
+        """One replay of the batch graph; returns (digests or None, kept counts)."""
+        dig = np.zeros(self.n, dtype=np.uint64) if digest else None
+        nk = np.zeros(self.n, dtype=np.int64)
+        _check(_lib.mm_batch_run(self._h, dig.ctypes.data if digest else None, nk.ctypes.data))
+        return dig, nk
+
+    def suggestions(self, i: int, k: int):
+        out = np.zeros(max(k, 1), dtype=MOVE_DTYPE)
+        nk = ctypes.c_int64()
+        _check(_lib.mm_batch_suggestions(self._h, int(i), int(k), out.ctypes.data, PTR_HOST, ctypes.byref(nk)))
+        return out[: min(k, nk.value)], int(nk.value)
+
+    def free(self):
+        if self._h:
+            _lib.mm_batch_free(self._h)
+            self._h = _vp(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
