@@ -302,6 +302,49 @@ MMREF_API mm_status mm_batch_suggestions(mm_batch *b, int32_t i, int32_t k, mm_m
                                          int64_t *n_kept);
 MMREF_API void mm_batch_free(mm_batch *b);
 
+/*
+ * Edits (the system evolves while it is analysed; abstract, and Sec. IV.C's
+ * re-evaluation after a class representation changes).
+ *   MM_EDIT_ADD_ACCESS / MM_EDIT_REMOVE_ACCESS   target = attribute id
+ *   MM_EDIT_ADD_CALL / MM_EDIT_REMOVE_CALL       target = called method id
+ *   MM_EDIT_MOVE                                 target = destination class
+ */
+enum {
+  MM_EDIT_ADD_ACCESS = 1,
+  MM_EDIT_REMOVE_ACCESS = 2,
+  MM_EDIT_ADD_CALL = 3,
+  MM_EDIT_REMOVE_CALL = 4,
+  MM_EDIT_MOVE = 5
+};
+typedef struct {
+  int32_t kind, m, target, reserved;
+} mm_edit;
+
+/*
+ * Apply one edit to a system whose metrics have been computed.  The device
+ * CSR is patched in place, every class and method metric is brought up to
+ * date (as mm_compute_metrics would compute it on the edited system), and the
+ * cached kept moves of the full cross product (left by mm_evaluate_moves or
+ * mm_suggest_moves) are updated by evaluating only the candidates whose
+ * record can change: every candidate of a method in an affected class and
+ * every candidate into an affected class.  Affected classes: the method's
+ * class and the attribute's owner (access), the callee's class (call), or
+ * the source, destination, the classes the method uses and the classes of
+ * its callers (move).  Errors (system unchanged): MM_EINVAL (ids out of
+ * range, self-call, move to the own class), MM_EEXIST (adding an existing
+ * access or call), MM_ENOTFOUND (removing a missing one).  Does not
+ * synchronise the stream except on the first edit of a system (it copies the
+ * rows to a host mirror used to validate edits).
+ */
+MMREF_API mm_status mm_apply_edit(mm_system *sys, const mm_edit *edit);
+
+/* Copy the system's current arrays (after edits) to host buffers sized from
+ * mm_system_info_get (n_acc, n_call); any pointer may be NULL.  Synchronises
+ * the stream.  Used to re-admit a served system and to check it. */
+MMREF_API mm_status mm_export_system(mm_system *sys, int32_t *method_class, int32_t *attr_class,
+                                     int64_t *acc_rowptr, int32_t *acc_idx, int64_t *call_rowptr,
+                                     int32_t *call_idx);
+
 /* Sizes and device memory of a loaded system (host struct). */
 MMREF_API mm_status mm_system_info_get(mm_system *sys, mm_system_info *info);
 

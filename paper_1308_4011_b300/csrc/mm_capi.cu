@@ -329,8 +329,26 @@ void mm_free_system(mm_system *s) {
   s->eval_ws.release(s->stream);
   s->stage_ws.release(s->stream);
   s->kept_ws.release(s->stream);
+  s->edit_ws.release(s->stream);
   delete s;
   if (cur >= 0 && cur != dev) cudaSetDevice(cur);
+}
+
+mm_status mm_apply_edit(mm_system *s, const mm_edit *e) {
+  return guarded([&] {
+    if (!s || !e) throw MmError{MM_EINVAL, "apply_edit: NULL argument"};
+    use_device(s);
+    apply_edit(s, *e);
+  });
+}
+
+mm_status mm_export_system(mm_system *s, int32_t *method_class, int32_t *attr_class, int64_t *acc_rowptr,
+                           int32_t *acc_idx, int64_t *call_rowptr, int32_t *call_idx) {
+  return guarded([&] {
+    if (!s) throw MmError{MM_EINVAL, "export_system: NULL system"};
+    use_device(s);
+    export_system(s, method_class, attr_class, acc_rowptr, acc_idx, call_rowptr, call_idx);
+  });
 }
 
 const char *mm_last_error(void) { return g_last_error.c_str(); }

@@ -52,6 +52,7 @@ struct DevArena {
   int64_t bytes = 0;
   void *alloc(size_t n);
   void release();
+  void forget(void *p);  // free one allocation now (stream-ordered)
   template <class T>
   T *get(int64_t count) {
     return static_cast<T *>(alloc(sizeof(T) * (size_t)(count > 0 ? count : 1)));
@@ -100,8 +101,19 @@ struct MoveHdr {
   int4 w0, w1, w2;
 };
 
+// Host mirror of a system, built on its first edit: the rows (sorted) for edit
+// validation and ranks, owners, per-class sizes, and the load-time summary.
+struct EditMirror {
+  bool ready = false;
+  std::vector<std::vector<int32_t>> acc, calls, callers;
+  std::vector<int32_t> method_class, attr_class, cls_n, cls_a;
+  int64_t acc_cap = 0, call_cap = 0, nu_cap = 0, bits_cap = 0;
+};
+
 struct mm_system {
   cudaStream_t stream = nullptr;
+  EditMirror mirror;
+  int64_t edits = 0;
   int device = 0;
   int32_t c = 0, M = 0, A = 0, cbo_attrs = 1;
   int64_t n_acc = 0, n_call = 0;
@@ -114,6 +126,7 @@ struct mm_system {
   Scratch eval_ws;     // evaluate/suggest scratch (kept lists, staging)
   Scratch stage_ws;    // host-output staging
   Scratch kept_ws;     // kept moves + per-method marks of the last evaluation
+  Scratch edit_ws;     // edit patches and incremental re-evaluation
   bool kept_valid = false;   // kept_ws holds the full cross product's kept moves for:
   uint32_t kept_mask = 0;    //   this metric mask
   int32_t kept_min = 0;      //   and this min_improved
@@ -212,3 +225,11 @@ constexpr int64_t kSegmentSortMax = 2048;
 int batch_persistent_grid();
 void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K);
 void check_criteria_public(const mm_criteria &crit);
+
+// edit path (mm_edit.cu / mm_moves.cu)
+void eval_csr_kept_append(mm_system *s, const mm_criteria &crit, const int64_t *rowptr, const int32_t *dst,
+                          mm_move *kept, int64_t cap, unsigned long long *count, uint8_t *mark);
+bool kept_cache(mm_system *s, mm_move **kept, uint8_t **mark, int64_t *cap);
+void apply_edit(mm_system *s, const mm_edit &e);
+void export_system(mm_system *s, int32_t *method_class, int32_t *attr_class, int64_t *acc_rowptr,
+                   int32_t *acc_idx, int64_t *call_rowptr, int32_t *call_idx);

@@ -1464,3 +1464,24 @@ void sort_moves_segments(mm_move *base, int64_t stride, const unsigned long long
   bitonic_sort_segments<<<n, 1024, 0, st>>>(base, stride, counts);
   MM_LAUNCH_CHECK();
 }
+
+// Evaluate an internal (valid by construction) device candidate list and append
+// the kept moves to the system's kept buffer (count and marks already set).
+void eval_csr_kept_append(mm_system *s, const mm_criteria &crit, const int64_t *rowptr, const int32_t *dst,
+                          mm_move *kept, int64_t cap, unsigned long long *count, uint8_t *mark) {
+  EvalCtx cx = make_ctx(s, crit);
+  OutCtx oc{};
+  oc.kept = kept;
+  oc.kept_count = count;
+  oc.kept_cap = cap;
+  oc.kept_mark = mark;
+  dispatch_eval(s, cx, oc, rowptr, dst);
+}
+
+// The system's cached kept list (full cross product) for the edit path.
+bool kept_cache(mm_system *s, mm_move **kept, uint8_t **mark, int64_t *cap) {
+  if (!s->kept_valid) return false;
+  kept_buffers(s, s->kept_cap, kept, mark);
+  *cap = s->kept_cap;
+  return true;
+}

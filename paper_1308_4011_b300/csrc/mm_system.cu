@@ -19,6 +19,15 @@ void *DevArena::alloc(size_t n) {
   return p;
 }
 
+void DevArena::forget(void *p) {
+  for (size_t i = 0; i < ptrs.size(); ++i)
+    if (ptrs[i] == p) {
+      cudaFreeAsync(p, stream);
+      ptrs.erase(ptrs.begin() + (long)i);
+      return;
+    }
+}
+
 void DevArena::release() {
   for (void *p : ptrs) cudaFreeAsync(p, stream);
   ptrs.clear();

@@ -32,7 +32,8 @@ DEFAULT_MIN_IMPROVED = 2
 EXPORTED = ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluate_moves", "mm_suggest_moves",
             "mm_system_info_get", "mm_free_system", "mm_last_error", "mm_status_string", "mm_abi_version",
             "mm_launch_count", "mm_suggest_moves_noalloc", "mm_batch_create", "mm_batch_set_tile",
-            "mm_batch_autotune", "mm_batch_run", "mm_batch_suggestions", "mm_batch_free")
+            "mm_batch_autotune", "mm_batch_run", "mm_batch_suggestions", "mm_batch_free", "mm_apply_edit",
+            "mm_export_system")
 
 CLASS_METRICS_DTYPE = np.dtype([("n_methods", "<i4"), ("n_attrs", "<i4"), ("P", "<i8"), ("Q", "<i8"),
                                 ("S", "<i8"), ("lcom_ck", "<i8"), ("hs_num", "<i8"), ("hs_den", "<i8"),
@@ -91,6 +92,16 @@ _lib.mm_batch_free.argtypes = [_vp]
 _lib.mm_batch_free.restype = None
 for _n in ("mm_batch_create", "mm_batch_set_tile", "mm_batch_autotune", "mm_batch_run", "mm_batch_suggestions"):
     getattr(_lib, _n).restype = ctypes.c_int
+class _Edit(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("m", ctypes.c_int32), ("target", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib.mm_apply_edit.argtypes = [_vp, ctypes.POINTER(_Edit)]
+_lib.mm_apply_edit.restype = ctypes.c_int
+_lib.mm_export_system.argtypes = [_vp] + [_vp] * 6
+_lib.mm_export_system.restype = ctypes.c_int
+EDIT_ADD_ACCESS, EDIT_REMOVE_ACCESS, EDIT_ADD_CALL, EDIT_REMOVE_CALL, EDIT_MOVE = 1, 2, 3, 4, 5
 NOALLOC_MAX_METHODS = 1048576
 NOALLOC_MAX_KEPT = 65536
 _lib.mm_free_system.argtypes = [_vp]
@@ -339,3 +350,20 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+def apply_edit(sys: System, kind: int, m: int, target: int):
+    """mm_apply_edit: one edit (EDIT_* kind, method m, attribute / callee / class)."""
+    e = _Edit(int(kind), int(m), int(target), 0)
+    _check(_lib.mm_apply_edit(sys.handle, ctypes.byref(e)))
+
+
+def export_system(sys: System):
+    """mm_export_system: the system's current arrays as numpy arrays
+    (method_class, attr_class, acc_rowptr, acc_idx, call_rowptr, call_idx)."""
+    inf = sys.info()
+    M, A = sys.n_methods, sys.n_attrs
+    out = (np.zeros(M, np.int32), np.zeros(A, np.int32), np.zeros(M + 1, np.int64), np.zeros(inf["n_acc"], np.int32),
+           np.zeros(M + 1, np.int64), np.zeros(inf["n_call"], np.int32))
+    _check(_lib.mm_export_system(sys.handle, *[_ptr(a) for a in out]))
+    return out
