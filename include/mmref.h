@@ -345,6 +345,68 @@ MMREF_API mm_status mm_export_system(mm_system *sys, int32_t *method_class, int3
                                      int64_t *acc_rowptr, int32_t *acc_idx, int64_t *call_rowptr,
                                      int32_t *call_idx);
 
+/*
+ * Serving (no counterpart in the paper beyond "continuously gathered while the
+ * system evolves", abstract).  A server keeps many evolving systems, makes
+ * them resident on the device on demand under a memory budget (evicting idle
+ * systems least recently used first, their current arrays copied back to the
+ * host), and answers requests: each request is an intended edit of one
+ * system; it is resolved against that system's current state (an addition
+ * picks the first absent attribute or callee from a position given by the
+ * selector, a removal one of the existing entries or, if there is none, the
+ * matching addition, a move one of the other classes), applied with
+ * mm_apply_edit, and answered with the system's top-k suggestions for the
+ * server's criteria.  n_slots worker threads, each on its own CUDA stream,
+ * serve requests concurrently as they arrive (continuous batching: a request
+ * that arrives while others run starts as soon as a slot is free, and the
+ * kernels of different slots overlap on the device); requests of one system
+ * run one at a time in arrival order, so each result is the same whatever
+ * else is in flight.
+ */
+typedef struct mm_server mm_server;
+typedef struct {
+  int64_t budget_bytes;  /* device memory for resident systems */
+  int32_t n_slots;       /* concurrent requests (1..64) */
+  int32_t topk;          /* suggestions returned per request */
+  mm_criteria crit;
+} mm_server_config;
+typedef struct {
+  int32_t system, kind, m, reserved; /* kind: MM_EDIT_*; m: method of the edit */
+  uint64_t selector;                 /* picks the concrete target, see above */
+  double arrival_s;                  /* seconds from the start of mm_server_run, non-decreasing */
+} mm_request;
+typedef struct {
+  int32_t status, slot;              /* mm_status of the request, worker slot */
+  mm_edit edit;                      /* the resolved edit */
+  double arrival_s, start_s, done_s; /* latency = done_s - arrival_s */
+  int64_t n_kept, n_methods_with_kept;
+} mm_response;
+typedef struct {
+  int64_t served, failed, loads, evictions, resident_bytes, n_snapshots;
+  double wall_s;
+} mm_server_stats;
+typedef struct {
+  int64_t request;
+  int32_t system, n_classes, n_methods, n_attrs;
+  int64_t n_acc, n_call;
+} mm_snapshot_info;
+
+MMREF_API mm_status mm_server_create(const mm_server_config *cfg, mm_server **out);
+/* Register a system (host arrays, copied); *id is its index for requests. */
+MMREF_API mm_status mm_server_add_system(mm_server *sv, const mm_system_desc *desc, int32_t *id);
+/* Serve n requests (open loop: request i is released at arrival_s).  resp[n]
+ * receives one response per request; topk (nullable) n * cfg.topk moves.
+ * With snapshot_every > 0 the state of the edited system after requests
+ * 0, snapshot_every, 2*snapshot_every, ... is kept for mm_server_snapshot. */
+MMREF_API mm_status mm_server_run(mm_server *sv, const mm_request *req, int64_t n, mm_response *resp,
+                                  mm_move *topk, int64_t snapshot_every);
+MMREF_API mm_status mm_server_stats_get(mm_server *sv, mm_server_stats *out);
+/* Snapshot k: sizes in *info; arrays (nullable) sized from a first call. */
+MMREF_API mm_status mm_server_snapshot(mm_server *sv, int64_t k, mm_snapshot_info *info, int32_t *method_class,
+                                       int32_t *attr_class, int64_t *acc_rowptr, int32_t *acc_idx,
+                                       int64_t *call_rowptr, int32_t *call_idx);
+MMREF_API void mm_server_free(mm_server *sv);
+
 /* Sizes and device memory of a loaded system (host struct). */
 MMREF_API mm_status mm_system_info_get(mm_system *sys, mm_system_info *info);
 

@@ -402,3 +402,57 @@ void export_system(mm_system *s, int32_t *method_class, int32_t *attr_class, int
     MM_CUDA_TRY(cudaMemcpyAsync(call_idx, s->call_idx, 4 * s->n_call, cudaMemcpyDeviceToHost, st));
   MM_CUDA_TRY(cudaStreamSynchronize(st));
 }
+
+// ---------------------------------------------------------------- edit resolution for request streams
+
+void ensure_mirror(mm_system *s) {
+  if (!s->mirror.ready) build_mirror(s);
+}
+
+// Turn an intended edit (kind, method, random selector) into a concrete valid
+// edit against the system's current state: an addition picks the first
+// absent attribute / callee from a position given by the selector; a removal
+// picks one of the existing entries (or becomes the matching addition when
+// there is none); a move picks one of the other classes.
+mm_edit resolve_edit(mm_system *s, int32_t kind, int32_t m, uint64_t sel) {
+  ensure_mirror(s);
+  const EditMirror &mr = s->mirror;
+  if (m < 0 || m >= s->M) throw MmError{MM_EINVAL, "resolve_edit: method id out of range"};
+  mm_edit e{kind, m, 0, 0};
+  const auto &acc = mr.acc[m];
+  const auto &calls = mr.calls[m];
+  if (kind == MM_EDIT_REMOVE_ACCESS && acc.empty()) kind = MM_EDIT_ADD_ACCESS;
+  if (kind == MM_EDIT_REMOVE_CALL && calls.empty()) kind = MM_EDIT_ADD_CALL;
+  if (kind == MM_EDIT_ADD_ACCESS && (int64_t)acc.size() >= s->A) kind = MM_EDIT_MOVE;
+  if (kind == MM_EDIT_ADD_CALL && (int64_t)calls.size() >= (int64_t)s->M - 1) kind = MM_EDIT_MOVE;
+  if (kind == MM_EDIT_MOVE && s->c < 2) throw MmError{MM_EINVAL, "resolve_edit: no other class to move to"};
+  e.kind = kind;
+  switch (kind) {
+    case MM_EDIT_ADD_ACCESS: {
+      int32_t a = (int32_t)(sel % (uint64_t)s->A);
+      while (std::binary_search(acc.begin(), acc.end(), a)) a = (a + 1) % s->A;
+      e.target = a;
+      break;
+    }
+    case MM_EDIT_REMOVE_ACCESS:
+      e.target = acc[sel % acc.size()];
+      break;
+    case MM_EDIT_ADD_CALL: {
+      int32_t t = (int32_t)(sel % (uint64_t)s->M);
+      while (t == m || std::binary_search(calls.begin(), calls.end(), t)) t = (t + 1) % s->M;
+      e.target = t;
+      break;
+    }
+    case MM_EDIT_REMOVE_CALL:
+      e.target = calls[sel % calls.size()];
+      break;
+    case MM_EDIT_MOVE: {
+      int32_t d = (int32_t)(sel % (uint64_t)(s->c - 1));
+      e.target = d + (d >= mr.method_class[m] ? 1 : 0);
+      break;
+    }
+    default:
+      throw MmError{MM_EINVAL, "resolve_edit: unknown edit kind"};
+  }
+  return e;
+}

@@ -233,3 +233,5 @@ bool kept_cache(mm_system *s, mm_move **kept, uint8_t **mark, int64_t *cap);
 void apply_edit(mm_system *s, const mm_edit &e);
 void export_system(mm_system *s, int32_t *method_class, int32_t *attr_class, int64_t *acc_rowptr,
                    int32_t *acc_idx, int64_t *call_rowptr, int32_t *call_idx);
+void ensure_mirror(mm_system *s);
+mm_edit resolve_edit(mm_system *s, int32_t kind, int32_t m, uint64_t sel);

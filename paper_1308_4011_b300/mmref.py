@@ -33,7 +33,8 @@ EXPORTED = ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluat
             "mm_system_info_get", "mm_free_system", "mm_last_error", "mm_status_string", "mm_abi_version",
             "mm_launch_count", "mm_suggest_moves_noalloc", "mm_batch_create", "mm_batch_set_tile",
             "mm_batch_autotune", "mm_batch_run", "mm_batch_suggestions", "mm_batch_free", "mm_apply_edit",
-            "mm_export_system")
+            "mm_export_system", "mm_server_create", "mm_server_add_system", "mm_server_run", "mm_server_stats_get",
+            "mm_server_snapshot", "mm_server_free")
 
 CLASS_METRICS_DTYPE = np.dtype([("n_methods", "<i4"), ("n_attrs", "<i4"), ("P", "<i8"), ("Q", "<i8"),
                                 ("S", "<i8"), ("lcom_ck", "<i8"), ("hs_num", "<i8"), ("hs_den", "<i8"),
@@ -367,3 +368,114 @@ def export_system(sys: System):
            np.zeros(M + 1, np.int64), np.zeros(inf["n_call"], np.int32))
     _check(_lib.mm_export_system(sys.handle, *[_ptr(a) for a in out]))
     return out
+
+
+# ---------------------------------------------------------------- serving
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("n_slots", ctypes.c_int32), ("topk", ctypes.c_int32),
+                ("crit", _Crit)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("served", ctypes.c_int64), ("failed", ctypes.c_int64), ("loads", ctypes.c_int64),
+                ("evictions", ctypes.c_int64), ("resident_bytes", ctypes.c_int64), ("n_snapshots", ctypes.c_int64),
+                ("wall_s", ctypes.c_double)]
+
+
+class _SnapInfo(ctypes.Structure):
+    _fields_ = [("request", ctypes.c_int64), ("system", ctypes.c_int32), ("n_classes", ctypes.c_int32),
+                ("n_methods", ctypes.c_int32), ("n_attrs", ctypes.c_int32), ("n_acc", ctypes.c_int64),
+                ("n_call", ctypes.c_int64)]
+
+
+REQUEST_DTYPE = np.dtype([("system", "<i4"), ("kind", "<i4"), ("m", "<i4"), ("reserved", "<i4"),
+                          ("selector", "<u8"), ("arrival_s", "<f8")])
+RESPONSE_DTYPE = np.dtype([("status", "<i4"), ("slot", "<i4"), ("kind", "<i4"), ("m", "<i4"), ("target", "<i4"),
+                           ("reserved", "<i4"), ("arrival_s", "<f8"), ("start_s", "<f8"), ("done_s", "<f8"),
+                           ("n_kept", "<i8"), ("n_methods_with_kept", "<i8")])
+assert REQUEST_DTYPE.itemsize == 32 and RESPONSE_DTYPE.itemsize == 64
+
+_lib.mm_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(_vp)]
+_lib.mm_server_add_system.argtypes = [_vp, ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_int32)]
+_lib.mm_server_run.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp, ctypes.c_int64]
+_lib.mm_server_stats_get.argtypes = [_vp, ctypes.POINTER(_ServerStats)]
+_lib.mm_server_snapshot.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(_SnapInfo)] + [_vp] * 6
+_lib.mm_server_free.argtypes = [_vp]
+_lib.mm_server_free.restype = None
+for _n in ("mm_server_create", "mm_server_add_system", "mm_server_run", "mm_server_stats_get", "mm_server_snapshot"):
+    getattr(_lib, _n).restype = ctypes.c_int
+
+
+class Server:
+    """mm_server_*: resident evolving systems answering edit requests."""
+
+    def __init__(self, budget_bytes: int, n_slots: int = 8, topk: int = 10, mask: int = DEFAULT_MASK,
+                 min_improved: int = DEFAULT_MIN_IMPROVED):
+        cfg = _ServerConfig(int(budget_bytes), int(n_slots), int(topk), _Crit(mask, min_improved))
+        h = _vp()
+        _check(_lib.mm_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.topk = int(topk)
+
+    def add_system(self, system, cbo_attrs: bool = True) -> int:
+        arrs = [np.ascontiguousarray(a, dtype=dt) for a, dt in
+                zip((system.method_class, system.attr_class, system.acc_rowptr, system.acc_idx,
+                     system.call_rowptr, system.call_idx),
+                    (np.int32, np.int32, np.int64, np.int32, np.int64, np.int32))]
+        d = _Desc(system.n_classes, system.n_methods, system.n_attrs, PTR_HOST, arrs[3].size, arrs[5].size,
+                  *[_ptr(a) for a in arrs], 1 if cbo_attrs else 0, 0)
+        i = ctypes.c_int32()
+        _check(_lib.mm_server_add_system(self._h, ctypes.byref(d), ctypes.byref(i)))
+        return int(i.value)
+
+    def run(self, requests: np.ndarray, snapshot_every: int = 0):
+        req = np.ascontiguousarray(requests, dtype=REQUEST_DTYPE)
+        n = len(req)
+        resp = np.zeros(n, dtype=RESPONSE_DTYPE)
+        top = np.zeros(max(n * self.topk, 1), dtype=MOVE_DTYPE)
+        _check(_lib.mm_server_run(self._h, req.ctypes.data if n else None, n, resp.ctypes.data if n else None,
+                                  top.ctypes.data if self.topk else None, int(snapshot_every)))
+        return resp, top[: n * self.topk].reshape(n, self.topk)
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(_lib.mm_server_stats_get(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+
+    def snapshot(self, k: int):
+        """(request index, system id, the system's arrays after that request)."""
+        inf = _SnapInfo()
+        _check(_lib.mm_server_snapshot(self._h, int(k), ctypes.byref(inf), *([None] * 6)))
+        M, A = inf.n_methods, inf.n_attrs
+        out = (np.zeros(M, np.int32), np.zeros(A, np.int32), np.zeros(M + 1, np.int64),
+               np.zeros(max(inf.n_acc, 1), np.int32), np.zeros(M + 1, np.int64), np.zeros(max(inf.n_call, 1), np.int32))
+        _check(_lib.mm_server_snapshot(self._h, int(k), ctypes.byref(inf), *[a.ctypes.data for a in out]))
+        return int(inf.request), int(inf.system), inf.n_classes, (out[0], out[1], out[2], out[3][: inf.n_acc],
+                                                                  out[4], out[5][: inf.n_call])
+
+    def free(self):
+        if self._h:
+            _lib.mm_server_free(self._h)
+            self._h = _vp(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def make_requests(systems_methods, n: int, rate_per_s: float, seed: int) -> np.ndarray:
+    """A seeded open-loop request stream: Poisson arrivals at rate_per_s, a
+    uniform system, one of the five edit kinds with probability 1/5 each, a
+    uniform method of that system, a 64-bit selector."""
+    rng = np.random.default_rng(seed)
+    req = np.zeros(n, dtype=REQUEST_DTYPE)
+    req["system"] = rng.integers(0, len(systems_methods), size=n)
+    req["kind"] = rng.integers(1, 6, size=n)
+    ms = np.asarray(systems_methods, dtype=np.int64)
+    req["m"] = (rng.random(n) * ms[req["system"]]).astype(np.int64)
+    req["selector"] = rng.integers(0, 2 ** 63 - 1, size=n, dtype=np.int64).astype(np.uint64)
+    req["arrival_s"] = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n)) if rate_per_s > 0 else 0.0
+    return req
