@@ -414,6 +414,97 @@ def run_batched(args, rank, world, local_rank):
             "note": "timed: metrics + full evaluation + kept moves + top-100 per system, no digest"}
 
 
+def run_serving(args, rank, world, local_rank):
+    """64 resident systems (drawn as the batched mix, seeds 100..163) answering
+    a Poisson stream of edit requests (each kind 1/5, seed 7): a saturating
+    burst for capacity, then an open-loop run at half of it for latency, every
+    1,000th state checked; a 2 GB-budget stress run where admission binds."""
+    import torch
+    import oracle
+    from paper_1308_4011_b300 import mmref, synth
+
+    torch.cuda.set_device(local_rank)
+    n_req = args.requests
+    systems = [synth.generate(**synth.batched_params(100 + i)) for i in range(64)]
+    ms = [s.n_methods for s in systems]
+    topk = 10
+
+    def serve(budget, req, slots, snap=0):
+        sv = mmref.Server(budget, n_slots=slots, topk=topk)
+        for s in systems:
+            sv.add_system(s)
+        resp, top = sv.run(req, snap)
+        return sv, resp, top
+
+    # warm-up pass: every system admitted once (loads are not part of the request latency below)
+    warm = mmref.make_requests(ms, 64, rate_per_s=0.0, seed=99)
+    warm["system"] = np.arange(64)
+    warm["m"] = warm["m"] % np.asarray(ms)[warm["system"]]
+    # capacity: everything arrives at once
+    burst = mmref.make_requests(ms, n_req, rate_per_s=0.0, seed=7)
+    sv, resp_b, _ = serve(100 << 30, np.concatenate([warm, burst]), args.slots)
+    stats_b = sv.stats()
+    sv.free()
+    rb = resp_b[64:]
+    cap_rps = n_req / (rb["done_s"].max() - rb["arrival_s"].min())
+    # latency: open loop at half the capacity, with snapshots
+    rate = 0.5 * cap_rps
+    req = mmref.make_requests(ms, n_req, rate_per_s=rate, seed=7)
+    warm2 = warm.copy()
+    req["arrival_s"] += 2.0  # let the warm-up admissions finish first
+    sv, resp, top = serve(100 << 30, np.concatenate([warm2, req]), args.slots, snap=1000)
+    r = resp[64:]
+    lat = (r["done_s"] - r["arrival_s"]) * 1e3
+    stats = sv.stats()
+    ok_req = bool((resp["status"] == 0).all())
+    # every 1,000th state: the oracle where it finishes in seconds, else a fresh full GPU recompute
+    n_oracle = n_gpu = bad = 0
+    for k in range(stats["n_snapshots"]):
+        i, si, c, arrs = sv.snapshot(k)
+        if i < 64:
+            continue
+        s = synth.System(c, len(arrs[0]), len(arrs[1]), *arrs)
+        got_n = int(resp["n_kept"][i])
+        got_top = [(int(x["m"]), int(x["d"])) for x in top[i]]
+        if s.n_methods * (c - 1) <= 2e8:
+            ref = oracle.Oracle(s).evaluate(mask=mmref.DEFAULT_MASK, min_improved=mmref.DEFAULT_MIN_IMPROVED)
+            exp_n, exp_top = ref.n_kept, [(int(x["m"]), int(x["d"])) for x in ref.kept[:topk]]
+            n_oracle += 1
+        else:
+            g = mmref.load_synth(s, device=True)
+            mmref.compute_metrics(g, None, None)
+            t2, exp_n, _ = mmref.suggest_moves(g, topk)
+            exp_top = [(int(x["m"]), int(x["d"])) for x in t2]
+            g.free()
+            n_gpu += 1
+        if exp_n != got_n or exp_top != got_top[: len(exp_top)]:
+            bad += 1
+    sv.free()
+    # stress: a 2 GB budget makes admission evict and reload
+    n_stress = min(n_req, 20000)
+    req_s = mmref.make_requests(ms, n_stress, rate_per_s=0.0, seed=8)
+    sv, resp_s, _ = serve(2 << 30, req_s, args.slots)
+    stats_s = sv.stats()
+    sv.free()
+    rs = resp_s
+    return {"metric": "edit requests/s and latency (bit-exact vs oracle)", "workload": "serving",
+            "value": cap_rps, "unit": "requests/s",
+            "config": {"workload": "64 resident systems (classes log-uniform 100..20,000, seeds 100..163), "
+                                   f"{n_req} Poisson edit requests (each kind 1/5, seed 7), 100 GB budget",
+                       "slots": args.slots, "topk": topk},
+            "capacity_requests_per_s": cap_rps, "offered_rate_per_s": rate,
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "latency_ms_mean": float(lat.mean()), "achieved_rps_open_loop": n_req / (r["done_s"].max() - r["arrival_s"].min()),
+            "all_requests_ok": ok_req, "snapshots_checked_oracle": n_oracle, "snapshots_checked_gpu_recompute": n_gpu,
+            "snapshots_mismatched": bad, "stats": stats, "burst_stats": stats_b,
+            "stress_2GB": {"requests": n_stress, "ok": int((rs["status"] == 0).sum()),
+                           "refused_budget": int((rs["status"] == 7).sum()), "evictions": stats_s["evictions"],
+                           "loads": stats_s["loads"],
+                           "requests_per_s": n_stress / (rs["done_s"].max() - rs["arrival_s"].min()),
+                           "latency_ms_p50": float(np.percentile((rs["done_s"] - rs["arrival_s"]) * 1e3, 50)),
+                           "latency_ms_p99": float(np.percentile((rs["done_s"] - rs["arrival_s"]) * 1e3, 99))}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -422,8 +513,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["medium", "batched"], default="medium",
-                    help="batched = the 256-system batch vs sequential launches (its own JSON line)")
+    ap.add_argument("--workload", choices=["medium", "batched", "serving"], default="medium",
+                    help="batched = the 256-system batch vs sequential launches; serving = the edit-request "
+                         "loop (each prints its own JSON line)")
+    ap.add_argument("--requests", type=int, default=100000)
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--case", choices=["medium", "small"], default="medium",
                     help="small = profiling case (1,000 classes, 12,000 methods, 192 MB of records); "
@@ -439,6 +533,9 @@ def main():
         return
     if args.workload == "batched":
         print(json.dumps(run_batched(args, rank, world, local_rank)), flush=True)
+        return
+    if args.workload == "serving":
+        print(json.dumps(run_serving(args, rank, world, local_rank)), flush=True)
         return
     if world > 1:
         import torch
