@@ -209,8 +209,6 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     s->method_local = a.get<int32_t>(M);
     s->ca_rowptr = a.get<int64_t>(c + 1);
     s->attr_local = a.get<int32_t>(A);
-    s->caller_rowptr = a.get<int64_t>(M + 1);
-    s->caller_idx = a.get<int32_t>(s->n_call);
     s->fan_in = a.get<int32_t>(M);
     s->d_err = a.get<uint32_t>(4);
     s->d_u64 = a.get<unsigned long long>(32);

@@ -182,7 +182,6 @@ void ensure_capacity(mm_system *s, int64_t n_acc, int64_t n_call) {
   if (n_call > mr.call_cap) {
     int64_t cap = n_call + n_call / 4 + 1024;
     s->call_idx = regrow(s, s->call_idx, s->n_call, cap);
-    s->caller_idx = regrow(s, s->caller_idx, (int64_t)0, cap);
     s->r_list = regrow(s, s->r_list, (int64_t)0, cap);
     mr.call_cap = cap;
   }
@@ -314,6 +313,7 @@ void apply_edit(mm_system *s, const mm_edit &e) {
       move_counts<<<1, 1, 0, st>>>(s->cls_n, C, D);
       MM_LAUNCH_CHECK();
       mr.method_class[m] = D;
+      s->methods_by_class = false;  // the move breaks the grouping by class
       mr.cls_n[C]--;
       mr.cls_n[D]++;
       break;

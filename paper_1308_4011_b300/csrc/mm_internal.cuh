@@ -80,7 +80,11 @@ enum : uint32_t {
   VE_SELF_CALL = 1u << 8,
   VE_CAND_ROWPTR = 1u << 9,
   VE_CAND_RANGE = 1u << 10,
-  VE_CAND_SELF = 1u << 11
+  VE_CAND_SELF = 1u << 11,
+  VE_ERRORS = (1u << 16) - 1,
+  // not errors: layout facts found while validating
+  VI_METHODS_UNSORTED = 1u << 16,  // method_class is not non-decreasing
+  VI_ATTRS_UNSORTED = 1u << 17     // attr_class is not non-decreasing
 };
 
 // Summary of a loaded system computed on the device at load time.
@@ -119,6 +123,8 @@ struct mm_system {
   int64_t n_acc = 0, n_call = 0;
   LoadSummary summary{};
   bool metrics_ready = false;
+  bool methods_by_class = false;   // method ids contiguous by class: no sort needed
+  bool attrs_by_class = false;
   int64_t n_class_edges = -1;
 
   DevArena arena;      // everything sized at load time
@@ -143,8 +149,6 @@ struct mm_system {
   int32_t *method_local;           // rank of a method inside its class
   int64_t *ca_rowptr;              // class -> attributes (offsets only)
   int32_t *attr_local;             // rank of an attribute inside its class
-  int64_t *caller_rowptr;          // callers of each method (transpose of calls)
-  int32_t *caller_idx;
   int32_t *fan_in;
 
   // attribute bitsets: class C, method rank i -> bits[bits_off[C] + i * W_C]

@@ -61,14 +61,15 @@ __global__ void method_use_keys(const int32_t *method_class, const int64_t *call
     keys[pos++] = ((base + (uint64_t)attr_class[acc_idx[e]]) << 1) | 1u;
 }
 
-// caller-class keys of m: m * c + class(caller)
-__global__ void caller_class_keys(const int64_t *caller_rowptr, const int32_t *caller_idx,
+// caller-class keys, one per call edge y -> x: x * c + class(y) (sorted later,
+// so the callers of x come out grouped by class without a transpose)
+__global__ void caller_class_keys(const int64_t *call_rowptr, const int32_t *call_idx,
                                   const int32_t *method_class, int32_t M, int32_t c, uint64_t *keys) {
-  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= M) return;
-  uint64_t base = (uint64_t)x * (uint64_t)c;
-  for (int64_t e = caller_rowptr[x]; e < caller_rowptr[x + 1]; ++e)
-    keys[e] = base + (uint64_t)method_class[caller_idx[e]];
+  int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= M) return;
+  const uint64_t cy = (uint64_t)method_class[y];
+  for (int64_t e = call_rowptr[y]; e < call_rowptr[y + 1]; ++e)
+    keys[e] = (uint64_t)call_idx[e] * (uint64_t)c + cy;
 }
 
 __global__ void heads_shifted(const uint64_t *keys, int64_t n, int shift, int64_t *head) {
@@ -301,7 +302,7 @@ void build_move_precompute(mm_system *s) {
   // list R: runs of (m, X) over the classes of m's callers
   if (s->n_call > 0) {
     const int64_t nc = s->n_call;
-    caller_class_keys<<<grid_for(M), TPB, 0, st>>>(s->caller_rowptr, s->caller_idx, s->method_class, M, c, keys);
+    caller_class_keys<<<grid_for(M), TPB, 0, st>>>(s->call_rowptr, s->call_idx, s->method_class, M, c, keys);
     MM_LAUNCH_CHECK();
     radix_sort_u64(keys, keys_alt, nullptr, nullptr, nc, bits_for((uint64_t)M * (uint64_t)c - 1), s->sort_ws, st);
     heads_shifted<<<grid_for(nc), TPB, 0, st>>>(keys, nc, 0, head);

@@ -100,10 +100,76 @@ __global__ void scan_tiles_kernel(const Tin *in, Tout *out, int64_t n, const Tou
   }
 }
 
+// Small inputs: one block walks the array in 16K-element chunks with a carry
+// (one launch instead of three).
+constexpr int SCAN1_THREADS = 1024;
+constexpr int SCAN1_ITEMS = 16;
+constexpr int64_t SCAN1_MAX = 1 << 16;
+
+template <class T>
+__device__ T block1024_exclusive_sum(T v, T *total) {
+  __shared__ T warp_sums[SCAN1_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    T w = warp_sums[lane];
+    T wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    warp_sums[lane] = wi - w;
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  T r = incl - v + warp_sums[warp];
+  __syncthreads();
+  return r;
+}
+
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(const Tin *in, Tout *out, int64_t n,
+                                                                   Tout *total_out) {
+  __shared__ Tout tot;
+  Tout carry = 0;
+  for (int64_t base = 0; base < n; base += (int64_t)SCAN1_THREADS * SCAN1_ITEMS) {
+    const int64_t b = base + (int64_t)threadIdx.x * SCAN1_ITEMS;
+    Tout v[SCAN1_ITEMS];
+    Tout sum = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN1_ITEMS; ++i) {
+      v[i] = b + i < n ? (Tout)in[b + i] : Tout(0);
+      sum += v[i];
+    }
+    Tout ex = block1024_exclusive_sum<Tout>(sum, &tot) + carry;
+#pragma unroll
+    for (int i = 0; i < SCAN1_ITEMS; ++i) {
+      if (b + i < n) out[b + i] = ex;
+      ex += v[i];
+    }
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
 template <class Tin, class Tout>
 void scan_exclusive(const Tin *in, Tout *out, int64_t n, Tout *total_dev, Scratch &ws, cudaStream_t st) {
   if (n <= 0) {
     if (total_dev) MM_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(Tout), st));
+    return;
+  }
+  if (n <= SCAN1_MAX) {
+    scan_single_block<Tin, Tout><<<1, SCAN1_THREADS, 0, st>>>(in, out, n, total_dev);
+    MM_LAUNCH_CHECK();
     return;
   }
   int64_t nb = ceil_div(n, SCAN_TILE);

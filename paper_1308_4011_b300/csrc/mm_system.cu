@@ -73,6 +73,7 @@ __global__ void validate_methods(const int32_t *method_class, const int64_t *acc
   uint32_t e = 0;
   int32_t C = method_class[x];
   if (C < 0 || C >= c) e |= VE_METHOD_CLASS;
+  if (x + 1 < M && method_class[x + 1] < C) e |= VI_METHODS_UNSORTED;
   if (x == 0) {
     if (acc_rowptr[0] != 0 || acc_rowptr[M] != n_acc) e |= VE_ACC_ROWPTR;
     if (call_rowptr[0] != 0 || call_rowptr[M] != n_call) e |= VE_CALL_ROWPTR;
@@ -109,7 +110,10 @@ __global__ void validate_attrs(const int32_t *attr_class, int32_t c, int32_t A, 
   int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= A) return;
   int32_t C = attr_class[a];
-  if (C < 0 || C >= c) atomicOr(err, (uint32_t)VE_ATTR_CLASS);
+  uint32_t e = 0;
+  if (C < 0 || C >= c) e |= VE_ATTR_CLASS;
+  if (a + 1 < A && attr_class[a + 1] < C) e |= VI_ATTRS_UNSORTED;
+  if (e) atomicOr(err, e);
 }
 
 __global__ void class_histograms(const int32_t *method_class, const int32_t *attr_class, int32_t c, int32_t M,
@@ -171,10 +175,13 @@ __global__ void local_ranks(const uint32_t *sorted_cls, const uint32_t *sorted_i
   if (list) list[i] = (int32_t)it;
 }
 
-__global__ void expand_callers(const int64_t *call_rowptr, int32_t M, uint32_t *caller_of_edge) {
-  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= M) return;
-  for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e) caller_of_edge[e] = (uint32_t)x;
+// ids already grouped by class in ascending order: the rank is id - first id of the class
+__global__ void local_ranks_sorted(const int32_t *cls, const int64_t *rowptr, int64_t n, int32_t *local,
+                                   int32_t *list) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  local[i] = (int32_t)(i - rowptr[cls[i]]);
+  if (list) list[i] = (int32_t)i;
 }
 
 __global__ void fan_in_hist(const int32_t *call_idx, int64_t n_call, int32_t *fan_in) {
@@ -208,7 +215,9 @@ void load_validate_and_summarise(mm_system *s) {
   uint32_t err = 0;
   MM_CUDA_TRY(cudaMemcpyAsync(&err, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   MM_CUDA_TRY(cudaStreamSynchronize(st));
-  h.err = err;
+  h.err = err & VE_ERRORS;
+  s->methods_by_class = !(err & VI_METHODS_UNSORTED);
+  s->attrs_by_class = !(err & VI_ATTRS_UNSORTED);
   s->summary = h;
 }
 
@@ -224,13 +233,15 @@ void build_structures(mm_system *s) {
   uint32_t *buf = static_cast<uint32_t *>(s->eval_ws.need(sizeof(uint32_t) * 4 * (size_t)n, st));
   uint32_t *k = buf, *ka = buf + n, *v = buf + 2 * n, *va = buf + 3 * n;
   const int cbits = bits_for((uint64_t)(c > 0 ? c - 1 : 0));
-  const int mbits = bits_for((uint64_t)(M > 0 ? M - 1 : 0));
 
   // class -> methods: stable sort of method ids by owner class
   scan_exclusive_i32to64(s->cls_n, s->cm_rowptr, c, s->sort_ws, st);
   set_i64<<<1, 1, 0, st>>>(s->cm_rowptr + c, M);
   MM_LAUNCH_CHECK();
-  if (M > 0) {
+  if (M > 0 && s->methods_by_class) {
+    local_ranks_sorted<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->cm_rowptr, M, s->method_local, s->cm_list);
+    MM_LAUNCH_CHECK();
+  } else if (M > 0) {
     copy_i32_to_u32<<<grid_for(M), TPB, 0, st>>>(s->method_class, k, M);
     iota_u32<<<grid_for(M), TPB, 0, st>>>(v, M);
     MM_LAUNCH_CHECK();
@@ -242,7 +253,10 @@ void build_structures(mm_system *s) {
   scan_exclusive_i32to64(s->cls_a, s->ca_rowptr, c, s->sort_ws, st);
   set_i64<<<1, 1, 0, st>>>(s->ca_rowptr + c, A);
   MM_LAUNCH_CHECK();
-  if (A > 0) {
+  if (A > 0 && s->attrs_by_class) {
+    local_ranks_sorted<<<grid_for(A), TPB, 0, st>>>(s->attr_class, s->ca_rowptr, A, s->attr_local, nullptr);
+    MM_LAUNCH_CHECK();
+  } else if (A > 0) {
     copy_i32_to_u32<<<grid_for(A), TPB, 0, st>>>(s->attr_class, k, A);
     iota_u32<<<grid_for(A), TPB, 0, st>>>(v, A);
     MM_LAUNCH_CHECK();
@@ -250,21 +264,11 @@ void build_structures(mm_system *s) {
     local_ranks<<<grid_for(A), TPB, 0, st>>>(k, v, s->ca_rowptr, A, s->attr_local, nullptr);
     MM_LAUNCH_CHECK();
   }
-  // callers of each method: stable sort of (callee, caller) edges by callee;
-  // callers come out ascending because edges are listed by caller
+  // fan-in: number of callers of each method (the callers themselves are
+  // grouped by class later, from the call edges, by the move precompute's sort)
   MM_CUDA_TRY(cudaMemsetAsync(s->fan_in, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(M, 1), st));
   if (E > 0) {
     fan_in_hist<<<grid_for(E), TPB, 0, st>>>(s->call_idx, E, s->fan_in);
     MM_LAUNCH_CHECK();
-  }
-  scan_exclusive_i32to64(s->fan_in, s->caller_rowptr, M, s->sort_ws, st);
-  set_i64<<<1, 1, 0, st>>>(s->caller_rowptr + M, E);
-  MM_LAUNCH_CHECK();
-  if (E > 0) {
-    copy_i32_to_u32<<<grid_for(E), TPB, 0, st>>>(s->call_idx, k, E);
-    expand_callers<<<grid_for(M), TPB, 0, st>>>(s->call_rowptr, s->M, v);
-    MM_LAUNCH_CHECK();
-    radix_sort_u32(k, ka, v, va, E, mbits, s->sort_ws, st);
-    MM_CUDA_TRY(cudaMemcpyAsync(s->caller_idx, v, sizeof(uint32_t) * (size_t)E, cudaMemcpyDeviceToDevice, st));
   }
 }
