@@ -82,6 +82,10 @@ void allocate_compute_buffers(mm_system *s) {
   s->adj_words = ((c + 127) / 128) * 4;  // rows padded to 16 bytes for vector loads
   s->out_adj = a.get<uint32_t>(s->adj_words * c);
   s->in_adj = a.get<uint32_t>(s->adj_words * c);
+  s->sum_words = (s->adj_words + 31) / 32;
+  s->csum = a.get<uint2>(s->sum_words * (2 * c + 1));
+  s->cpk = a.get<uint32_t>(2 * nu);
+  s->dest_rec = a.get<int4>(2 * c);
   s->hdr = a.get<MoveHdr>(M);
   s->l_list = a.get<int4>(nu);
   s->l_s = a.get<int32_t>(nu);

@@ -192,6 +192,7 @@ void ensure_capacity(mm_system *s, int64_t n_acc, int64_t n_call) {
     s->l_list = regrow(s, s->l_list, (int64_t)0, cap);
     s->l_s = regrow(s, s->l_s, (int64_t)0, cap);
     s->l_x = regrow(s, s->l_x, (int64_t)0, cap);
+    s->cpk = regrow(s, s->cpk, (int64_t)0, 2 * cap);
     mr.nu_cap = cap;
   }
 }

@@ -167,6 +167,15 @@ struct mm_system {
   int64_t *mg_count;               // device scalar: number of distinct (Y, E)
   uint32_t *out_adj, *in_adj;
   int64_t adj_words;
+  // compressed two-level adjacency for the restricted evaluation (L2-resident).
+  // Rows 0..c-1 are the out-rows, rows c..2c-1 the in-rows, row 2c is all zero.
+  // Record k of a row = {bits, first}: bit j set iff full word 32 k + j of the
+  // row is non-zero; `first` = index in cpk of the first non-zero word it marks.
+  uint2 *csum;
+  uint32_t *cpk;                   // non-zero words, row by row (at most one per distinct pair and side)
+  int64_t sum_words;               // records per row = ceil(adj_words / 32)
+  // destination record per class: {P - Q, S, n, a} (32 bytes, one load per candidate)
+  int4 *dest_rec;
 
   // move precompute
   MoveHdr *hdr;

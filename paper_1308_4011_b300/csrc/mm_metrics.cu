@@ -174,7 +174,8 @@ __global__ void run_starts(const uint64_t *keys, const int64_t *head_scan, int64
 
 __global__ void multigraph_fill(const uint64_t *keys, const int64_t *start, const int64_t *n_unique,
                                 const int64_t *n_valid, int32_t c, int64_t cap, int32_t *mg_dst, int32_t *mg_cnt,
-                                int32_t *row_count, uint32_t *out_adj, uint32_t *in_adj, int64_t aw) {
+                                int32_t *row_count, uint32_t *out_adj, uint32_t *in_adj, int64_t aw,
+                                uint2 *csum, int64_t sw) {
   const int64_t nu = *n_unique, nv = *n_valid;
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu && u < cap;
        u += (int64_t)gridDim.x * blockDim.x) {
@@ -187,6 +188,9 @@ __global__ void multigraph_fill(const uint64_t *keys, const int64_t *start, cons
     atomicAdd(&row_count[Y], 1);
     atomicOr(&out_adj[(int64_t)Y * aw + (E >> 5)], 1u << (E & 31));
     atomicOr(&in_adj[(int64_t)E * aw + (Y >> 5)], 1u << (Y & 31));
+    // bit (w & 31) of record (w >> 5) marks full word w = E >> 5 (resp. Y >> 5) non-zero
+    atomicOr(&csum[(int64_t)Y * sw + (E >> 10)].x, 1u << ((E >> 5) & 31));
+    atomicOr(&csum[((int64_t)c + E) * sw + (Y >> 10)].x, 1u << ((Y >> 5) & 31));
   }
 }
 
@@ -195,6 +199,45 @@ __global__ void finalize_classes(const int32_t *cls_n, const int64_t *cls_Q, int
   if (C >= c) return;
   int64_t n = cls_n[C];
   cls_P[C] = n * (n - 1) / 2 - cls_Q[C];
+}
+
+__global__ void summary_popc(const uint2 *sum, int64_t n, int32_t *cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    cnt[i] = __popc(sum[i].x);
+}
+
+// record i gets the packed index of its first word; its marked full words are
+// copied there (rows below c from the out-bitsets, the next c from the in-bitsets)
+__global__ void summary_pack(uint2 *sum, const int64_t *first, const uint32_t *out_adj, const uint32_t *in_adj,
+                             int64_t c, int64_t aw, int64_t sw, int64_t n, uint32_t *packed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / sw, k = i % sw;
+    uint32_t bits = sum[i].x;
+    const uint32_t f = (uint32_t)first[i];
+    sum[i].y = f;
+    const uint32_t *row = r < c ? out_adj + r * aw : in_adj + (r - c) * aw;
+    uint32_t o = f;
+    while (bits) {
+      const int j = __ffs(bits) - 1;
+      bits &= bits - 1;
+      packed[o++] = row[k * 32 + j];
+    }
+  }
+}
+
+// destination record: {P - Q, S} as int64 in the first int4; {n, a, dck0, sck0 | shs0 << 8}
+// in the second, where the last three are D's LCOM outcome when m shares nothing with D
+__global__ void destination_records(const int32_t *cls_n, const int32_t *cls_a, const int64_t *P, const int64_t *Q,
+                                    const int64_t *S, int32_t c, int4 *rec) {
+  int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= c) return;
+  const int64_t d = P[C] - Q[C], sv = S[C];
+  const int32_t n = cls_n[C], a = cls_a[C];
+  const int64_t ck = d > 0 ? d : 0, d2 = d + n, ck2 = d2 > 0 ? d2 : 0;
+  const int32_t sck0 = (ck2 > ck) - (ck2 < ck);
+  const int32_t shs0 = a == 0 ? 0 : (n == 0 ? 1 : (sv > 0 ? 1 : 0));
+  rec[2 * C] = make_int4((int32_t)(uint32_t)d, (int32_t)(d >> 32), (int32_t)(uint32_t)sv, (int32_t)(sv >> 32));
+  rec[2 * C + 1] = make_int4(n, a, (int32_t)(ck2 - ck), (sck0 & 0xff) | ((shs0 & 0xff) << 8));
 }
 
 }  // namespace
@@ -239,6 +282,7 @@ void build_metrics(mm_system *s) {
   const uint64_t sent = (uint64_t)c * (uint64_t)c;
   MM_CUDA_TRY(cudaMemsetAsync(s->out_adj, 0, sizeof(uint32_t) * (size_t)(s->adj_words * c), st));
   MM_CUDA_TRY(cudaMemsetAsync(s->in_adj, 0, sizeof(uint32_t) * (size_t)(s->adj_words * c), st));
+  MM_CUDA_TRY(cudaMemsetAsync(s->csum, 0, sizeof(uint2) * (size_t)(s->sum_words * (2 * c + 1)), st));
   int32_t *row_count = s->cls_cbo;
   MM_CUDA_TRY(cudaMemsetAsync(row_count, 0, sizeof(int32_t) * (size_t)c, st));
   MM_CUDA_TRY(cudaMemsetAsync(s->mg_count, 0, sizeof(int64_t) * 2, st));
@@ -260,10 +304,28 @@ void build_metrics(mm_system *s) {
     run_starts<<<grid_for(nk), TPB, 0, st>>>(keys, head, nk, sent, start);
     MM_LAUNCH_CHECK();
     multigraph_fill<<<grid_for(nk), TPB, 0, st>>>(keys, start, s->mg_count, n_valid, c, nk, s->mg_dst, s->mg_cnt,
-                                                  row_count, s->out_adj, s->in_adj, s->adj_words);
+                                                  row_count, s->out_adj, s->in_adj, s->adj_words,
+                                                  s->csum, s->sum_words);
     MM_LAUNCH_CHECK();
   }
   // mg_rowptr = exclusive scan of the row counts (CBO); last entry = distinct pairs
   scan_exclusive_i32to64(row_count, s->mg_rowptr, c, s->sort_ws, st);
   MM_CUDA_TRY(cudaMemcpyAsync(s->mg_rowptr + c, s->mg_count, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  // compressed adjacency: record counts -> exclusive scan -> packed non-zero words
+  {
+    const int64_t ns = s->sum_words * (2 * (int64_t)c + 1);
+    char *b = static_cast<char *>(s->eval_ws.need((sizeof(int32_t) + sizeof(int64_t)) * (size_t)ns + 16, st));
+    int64_t *first = reinterpret_cast<int64_t *>(b);
+    int32_t *cnt = reinterpret_cast<int32_t *>(first + ns);
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(ns, TPB), 148 * 16);
+    summary_popc<<<g, TPB, 0, st>>>(s->csum, ns, cnt);
+    MM_LAUNCH_CHECK();
+    scan_exclusive_i32to64(cnt, first, ns, s->sort_ws, st);
+    summary_pack<<<g, TPB, 0, st>>>(s->csum, first, s->out_adj, s->in_adj, c, s->adj_words, s->sum_words, ns,
+                                    s->cpk);
+    MM_LAUNCH_CHECK();
+  }
+  destination_records<<<grid_for(c), TPB, 0, st>>>(s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, c,
+                                                   s->dest_rec);
+  MM_LAUNCH_CHECK();
 }

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "mm_internal.cuh"
 
@@ -577,7 +578,7 @@ __device__ __forceinline__ uint32_t enc_small(int32_t v) { return (uint32_t)(v <
 
 // Rare paths of the dense kernel, kept out of line so they do not cost the
 // common path registers.
-__device__ __noinline__ uint4 dense_hit_path(const EvalCtx &cx, const DenseStage &st, int32_t j, int32_t D, int q,
+__device__ __noinline__ uint4 dense_hit_path(const EvalCtx cx, const DenseStage &st, int32_t j, int32_t D, int q,
                                              uint32_t lane, int warp, const int32_t *cls_n, const int32_t *cls_a,
                                              const int64_t *cls_P, const int64_t *cls_Q, const int64_t *cls_S,
                                              int32_t *dck, int32_t *dcbo) {
@@ -614,7 +615,7 @@ __device__ __noinline__ uint4 dense_hit_path(const EvalCtx &cx, const DenseStage
   return r;
 }
 
-__device__ __noinline__ uint4 dense_global_path(const EvalCtx &cx, const MoveHdr &h, int32_t D,
+__device__ __noinline__ uint4 dense_global_path(const EvalCtx cx, const MoveHdr &h, int32_t D,
                                                 const int32_t *cls_n, const int32_t *cls_a, const int64_t *cls_P,
                                                 const int64_t *cls_Q, const int64_t *cls_S, int32_t *dck,
                                                 int32_t *dcbo) {
@@ -897,7 +898,7 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
 }
 
 template <bool REC, bool DIG, bool KEEP>
-__global__ void __launch_bounds__(DB_THREADS) eval_dense(DenseSys sy, OutCtx oc, int32_t mchunk) {
+__global__ void __launch_bounds__(DB_THREADS, 3) eval_dense(DenseSys sy, OutCtx oc, int32_t mchunk) {
   __shared__ __align__(16) DenseStage st;
   const int32_t m0 = blockIdx.y * mchunk;
   const int32_t m1 = min(sy.M, m0 + mchunk);
@@ -908,40 +909,329 @@ __global__ void __launch_bounds__(DB_THREADS) eval_dense(DenseSys sy, OutCtx oc,
   }
 }
 
-// Explicit candidate lists (CSR over methods): one warp per method row.
+// Restricted candidates (explicit destination lists, CSR over methods) on the
+// compressed adjacency.  A warp owns groups of 8 consecutive methods: one
+// coalesced pass loads their row bounds and headers, asynchronous copies bring
+// their L and R lists (stored in method order by the list build) into shared
+// memory.  For each method the warp lays out its probe rows -- the in-row of
+// each class m uses, the out-row of each class calling m, C's in-row and
+// out-row -- in pages of 32 with three masks per page, then walks the
+// candidates 32 at a time.  A lane probes every row at its destination D (one
+// 8-byte summary record, plus one packed word only when the record marks D's
+// word non-zero; a method's records are re-read from L1 by all its candidates,
+// the packed words come from L2), collects the answers of a page as a bit mask
+// and reduces it with the page masks:  gain = L rows without the bit, impX = R
+// rows of callers that drop C and already use D, worX = R rows of callers that
+// keep C and do not use D yet; a row whose class is D itself is masked out and
+// supplies the D-specific list fields instead.  Methods whose lists exceed the
+// stage take the general per-candidate path.
+constexpr int CG_M = 8;               // methods per group
+constexpr int CG_LCAP = 96;           // staged L entries per warp
+constexpr int CG_RCAP = 96;           // staged R entries per warp
+constexpr int CG_PMAX = 128;          // probe rows per method (4 pages of 32)
+constexpr int CG_WARPS = 8;
+constexpr int CG_PB = 4;              // probes per batch (rows are padded to whole batches)
+
+struct CsrGroup {
+  MoveHdr hdr[CG_M];
+  int64_t rp[CG_M + 2];               // candidate row bounds of the group
+  int32_t loff[CG_M], roff[CG_M];     // list offsets in the stage
+  int4 lent[CG_LCAP];
+  int4 rent[CG_RCAP];
+  int32_t lsh[CG_LCAP];
+  uint2 prow[CG_PMAX];                // probe rows of the current method: {record offset, class}
+  uint4 pmask[CG_PMAX / 32];          // per page: {L rows with a use edge, R rows dropping C, R rows keeping C}
+};
+constexpr int CG_WARP_BYTES = (int)((sizeof(CsrGroup) + 15) / 16 * 16);
+static_assert(CG_WARPS * CG_WARP_BYTES <= 48 * 1024, "stage fits the default shared-memory window");
+
+struct CsrSys {
+  EvalCtx cx;
+  const uint2 *csum;                  // summary records: out-rows, in-rows, zero row
+  const uint32_t *cpk;                // packed non-zero words
+  const int4 *dest_rec;
+  const int32_t *cls_n, *cls_a;
+  const int64_t *cls_P, *cls_Q, *cls_S;
+  uint32_t sw;                        // records per row
+  uint32_t c;
+  int32_t M;
+  int32_t staged;                     // 0: every method takes the general path
+};
+
+// Asynchronous global -> shared copies (completion awaited by cp_async_wait).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Predicated read-only load: no branch, so a batch of them is in flight together.
+__device__ __forceinline__ uint32_t ldg_if(const uint32_t *p, bool pred) {
+  uint32_t v = 0;
+  asm("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q ld.global.nc.u32 %0, [%1];\n}\n"
+      : "+r"(v)
+      : "l"(p), "r"((uint32_t)pred));
+  return v;
+}
+
+// destination constants: {P - Q, S} and {n, a, dck0, sck0 | shs0 << 8}
+__device__ __forceinline__ DState dstate_rec(const int4 *rec, int32_t D) {
+  const int4 a = __ldg(rec + 2 * (int64_t)D), b = __ldg(rec + 2 * (int64_t)D + 1);
+  DState d;
+  d.D = D;
+  d.nD = b.x;
+  d.aD = b.y;
+  d.dck0 = b.z;
+  d.sck0 = (int32_t)(int8_t)(b.w & 0xff);
+  d.shs0 = (int32_t)(int8_t)((b.w >> 8) & 0xff);
+  d.diffD = (int64_t)(((uint64_t)(uint32_t)a.y << 32) | (uint32_t)a.x);
+  d.SD = (int64_t)(((uint64_t)(uint32_t)a.w << 32) | (uint32_t)a.z);
+  d.ckD = d.diffD > 0 ? d.diffD : 0;
+  return d;
+}
+
+// Methods whose lists exceed the stage: the general per-candidate path.  Its
+// arguments are values: a reference to a kernel parameter would keep the whole
+// parameter block in local memory for the caller's lifetime.
 template <bool REC, bool DIG, bool KEEP>
-__global__ void __launch_bounds__(256) eval_csr(EvalCtx cx, OutCtx oc, const int64_t *cand_rowptr,
-                                                const int32_t *cand_dst, const int32_t *cls_n,
-                                                const int32_t *cls_a, const int64_t *cls_P, const int64_t *cls_Q,
-                                                const int64_t *cls_S, int32_t M) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+__device__ __noinline__ uint64_t csr_general_row(const EvalCtx cx, const OutCtx oc, const int32_t *cls_n,
+                                                 const int32_t *cls_a, const int64_t *cls_P, const int64_t *cls_Q,
+                                                 const int64_t *cls_S, const MoveHdr h, int32_t m,
+                                                 const int32_t *cand_dst, int64_t b0, int64_t b1, uint32_t lane) {
   uint64_t dig = 0;
-  for (int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; m < M; m += nwarps) {
-    MoveHdr h;
-    h.w0 = __ldg(&cx.hdr[m].w0);
-    h.w1 = __ldg(&cx.hdr[m].w1);
-    h.w2 = __ldg(&cx.hdr[m].w2);
-    const int64_t b0 = cand_rowptr[m], b1 = cand_rowptr[m + 1];
-    for (int64_t i0 = b0; i0 < b1; i0 += 32) {
-      const int64_t i = i0 + lane;
-      const bool act = i < b1;
-      int32_t D = act ? __ldg(cand_dst + i) : 0;
-      int32_t dck = 0, dcbo = 0;
-      uint4 r = make_uint4(0, 0, 0, 0);
-      if (act) {
-        DState ds = load_dstate(D, cls_n, cls_a, cls_P, cls_Q, cls_S);
-        r = eval_move(cx, h, ds, dck, dcbo);
+  for (int64_t i0 = b0; i0 < b1; i0 += 32) {
+    const int64_t i = i0 + lane;
+    const bool act = i < b1;
+    const int32_t D = act ? __ldg(cand_dst + i) : 0;
+    int32_t dck = 0, dcbo = 0;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (act) {
+      DState ds = load_dstate(D, cls_n, cls_a, cls_P, cls_Q, cls_S);
+      r = eval_move(cx, h, ds, dck, dcbo);
+    }
+    if (REC && act) __stcs(oc.records + i, r);
+    if (DIG && act) dig += record_hash(m, D, r);
+    if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
+  }
+  return dig;
+}
+
+// One candidate (m -> D): probe every row at D, reduce page by page.
+__device__ __forceinline__ uint4 csr_candidate(const CsrSys &sy, const CsrGroup &w, const MoveHdr &h, int32_t lo,
+                                               int32_t ro, int32_t D, int32_t &dck, int32_t &dcbo) {
+  const DState ds = dstate_rec(sy.dest_rec, D);
+  const int32_t nL = h.w0.z, nR = h.w1.x, nLR = nL + nR, nP = nLR + 2;
+  const uint32_t rw = (uint32_t)D >> 10, b = ((uint32_t)D >> 5) & 31u, below = (1u << b) - 1u;
+  const uint32_t dsh = (uint32_t)D & 31u;
+  Gathered g;
+  g.gain = 0; g.impX = 0; g.worX = 0; g.bDC = 0; g.bCD = 0;
+  g.t = 0; g.sh = 0; g.outD = 0; g.cntCD = 0; g.inD = 0; g.cntDC = 0;
+  int32_t ml = -1, mr = -1;  // rows of m's lists whose class is D
+  for (int32_t p0 = 0; p0 < nP; p0 += 32) {
+    const int32_t pend = min(nP - p0, 32);
+    uint32_t bits = 0, match = 0;
+    for (int32_t k0 = 0; k0 < pend; k0 += CG_PB) {
+      uint2 rec[CG_PB];
+#pragma unroll
+      for (int u = 0; u < CG_PB; ++u) {
+        const uint2 pw = w.prow[p0 + k0 + u];  // rows past nP are the zero row
+        match |= (uint32_t)((int32_t)pw.y == D) << (k0 + u);
+        rec[u] = __ldg(sy.csum + (pw.x + rw));
       }
-      if (REC && act) __stcs(oc.records + i, r);
-      if (DIG && act) dig += record_hash((int32_t)m, D, r);
-      if (KEEP) emit_kept(oc, act && (r.w >> 31), (int32_t)m, D, r.z >> 16, dck, dcbo, lane);
+      uint32_t word[CG_PB];
+#pragma unroll
+      for (int u = 0; u < CG_PB; ++u)
+        word[u] = ldg_if(sy.cpk + rec[u].y + __popc(rec[u].x & below), (rec[u].x >> b) & 1u);
+#pragma unroll
+      for (int u = 0; u < CG_PB; ++u) bits |= ((word[u] >> dsh) & 1u) << (k0 + u);
+    }
+    const uint4 pm = w.pmask[p0 >> 5];
+    const uint32_t valid = ~match;
+    const uint32_t lv = pm.x & valid;
+    g.gain += __popc(lv) - __popc(bits & lv);
+    g.impX += __popc(bits & pm.y & valid);
+    g.worX += __popc(~bits & pm.z & valid);
+    if (match) {
+      const int32_t e = p0 + __ffs(match) - 1;  // D appears at most once among m's L and once among its R
+      const uint32_t rest = match & (match - 1u);
+      if (e < nL) ml = e; else mr = e;
+      if (rest) mr = p0 + __ffs(rest) - 1;
+    }
+    const int32_t cin = nLR - p0;
+    if (cin >= 0 && cin < 32) g.bDC = (int32_t)((bits >> cin) & 1u);
+    if (cin + 1 >= 0 && cin + 1 < 32) g.bCD = (int32_t)((bits >> (cin + 1)) & 1u);
+  }
+  if (ml >= 0) {
+    const int4 v = w.lent[lo + ml];
+    g.outD = v.y;
+    g.cntCD = v.z;
+    g.t = v.w;
+    g.sh = w.lsh[lo + ml];
+  }
+  if (mr >= 0) {
+    const int4 v = w.rent[ro + mr - nL];
+    g.inD = v.y;
+    g.cntDC = v.z;
+  }
+  return finish_move(h, ds, g, sy.cx.mask, sy.cx.min_improved, dck, dcbo);
+}
+
+__device__ __forceinline__ int32_t warp_scan_incl(int32_t v, uint32_t lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if ((int)lane >= o) v += t;
+  }
+  return v;
+}
+
+template <bool REC, bool DIG, bool KEEP>
+__global__ void __launch_bounds__(CG_WARPS * 32, 3) eval_csr_grouped(CsrSys sy, OutCtx oc,
+                                                                     const int64_t *cand_rowptr,
+                                                                     const int32_t *cand_dst) {
+  extern __shared__ __align__(16) unsigned char cg_smem[];
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  CsrGroup &w = *reinterpret_cast<CsrGroup *>(cg_smem + (size_t)wid * CG_WARP_BYTES);
+  const uint32_t sw = sy.sw, zero_row = 2u * sy.c * sw;
+  const int64_t ngroups = ((int64_t)sy.M + CG_M - 1) / CG_M;
+  const int64_t nwarps = (int64_t)gridDim.x * CG_WARPS;
+  uint64_t dig = 0;
+  for (int64_t grp = (int64_t)blockIdx.x * CG_WARPS + wid; grp < ngroups; grp += nwarps) {
+    const int32_t ma = (int32_t)(grp * CG_M);
+    const int32_t nm = min(CG_M, sy.M - ma);
+    __syncwarp();  // the previous group's readers are done with the stage
+    MoveHdr h;
+    h.w0 = make_int4(0, 0, 0, 0);
+    h.w1 = make_int4(0, 0, 0, 0);
+    h.w2 = make_int4(0, 0, 0, 0);
+    if ((int32_t)lane < nm) {
+      h.w0 = __ldg(&sy.cx.hdr[ma + lane].w0);
+      h.w1 = __ldg(&sy.cx.hdr[ma + lane].w1);
+      h.w2 = __ldg(&sy.cx.hdr[ma + lane].w2);
+      w.hdr[lane] = h;
+      w.rp[lane + 1] = __ldg(cand_rowptr + ma + lane + 1);
+    }
+    if (lane == 0) w.rp[0] = __ldg(cand_rowptr + ma);
+    const int32_t nl = h.w0.z, nr = h.w1.x;
+    const bool big = !sy.staged || nl > CG_LCAP || nr > CG_RCAP || nl + nr + 2 > CG_PMAX;
+    const uint32_t bigm = __ballot_sync(0xffffffffu, big);
+    __syncwarp();
+    int32_t j = 0;
+    while (j < nm) {
+      if ((bigm >> j) & 1u) {  // lists too long for the stage
+        const MoveHdr hj = w.hdr[j];
+        dig += csr_general_row<REC, DIG, KEEP>(sy.cx, oc, sy.cls_n, sy.cls_a, sy.cls_P, sy.cls_Q, sy.cls_S, hj,
+                                               ma + j, cand_dst, w.rp[j], w.rp[j + 1], lane);
+        ++j;
+        continue;
+      }
+      // longest run j..k-1 without a big method whose lists fit together
+      const bool inrun = (int32_t)lane >= j && (int32_t)lane < nm;
+      const int32_t cl = warp_scan_incl(inrun ? nl : 0, lane);
+      const int32_t cr = warp_scan_incl(inrun ? nr : 0, lane);
+      const uint32_t after = bigm & ~((2u << j) - 1u);  // big methods after j
+      const int32_t fb = after ? __ffs(after) - 1 : 32;
+      const uint32_t fits =
+          __ballot_sync(0xffffffffu, inrun && (int32_t)lane < fb && cl <= CG_LCAP && cr <= CG_RCAP);
+      const int32_t k = j + __popc(fits);
+      const bool mine = (int32_t)lane >= j && (int32_t)lane < k;
+      const int32_t totL = __shfl_sync(0xffffffffu, cl, k - 1);
+      const int32_t totR = __shfl_sync(0xffffffffu, cr, k - 1);
+      const uint32_t hasl = __ballot_sync(0xffffffffu, mine && nl > 0);
+      const uint32_t hasr = __ballot_sync(0xffffffffu, mine && nr > 0);
+      const int32_t l0 = __shfl_sync(0xffffffffu, h.w0.y, hasl ? __ffs(hasl) - 1 : 0);
+      const int32_t r0 = __shfl_sync(0xffffffffu, h.w0.w, hasr ? __ffs(hasr) - 1 : 0);
+      if (mine) {
+        w.loff[lane] = cl - nl;
+        w.roff[lane] = cr - nr;
+      }
+      for (int32_t e = (int32_t)lane; e < totL; e += 32) {
+        cp_async16(&w.lent[e], sy.cx.l_list + l0 + e);
+        cp_async4(&w.lsh[e], sy.cx.l_s + l0 + e);
+      }
+      for (int32_t e = (int32_t)lane; e < totR; e += 32) cp_async16(&w.rent[e], sy.cx.r_list + r0 + e);
+      cp_async_wait();
+      __syncwarp();
+      for (int32_t jm = j; jm < k; ++jm) {
+        const int64_t b0 = w.rp[jm], b1 = w.rp[jm + 1];
+        if (b0 == b1) continue;
+        const MoveHdr hm = w.hdr[jm];
+        const int32_t lo = w.loff[jm], ro = w.roff[jm];
+        const int32_t nL = hm.w0.z, nR = hm.w1.x, nP = nL + nR + 2;
+        const int32_t C = hm.w0.x;
+        int32_t Dn = b0 + (int64_t)lane < b1 ? __ldg(cand_dst + b0 + lane) : C;
+        __syncwarp();  // the previous method's readers are done with the row table
+        // row table, page by page: lane describes row p0 + lane (rows past nP: the zero row)
+        for (int32_t p0 = 0; p0 < nP; p0 += 32) {
+          const int32_t kk = p0 + (int32_t)lane;
+          uint32_t off = zero_row, cls = 0xffffffffu;
+          bool isl = false, isrl = false, isrk = false;
+          if (kk < nL) {
+            const int4 v = w.lent[lo + kk];
+            cls = (uint32_t)v.x;
+            off = (sy.c + cls) * sw;
+            isl = v.y > 0;
+          } else if (kk < nL + nR) {
+            const int4 v = w.rent[ro + kk - nL];
+            cls = (uint32_t)v.x;
+            off = cls * sw;
+            isrl = v.z == v.y;
+            isrk = !isrl;
+          } else if (kk < nP) {
+            cls = (uint32_t)C;
+            off = (kk == nL + nR ? sy.c + cls : cls) * sw;
+          }
+          w.prow[kk] = make_uint2(off, cls);
+          const uint32_t lm = __ballot_sync(0xffffffffu, isl);
+          const uint32_t rl = __ballot_sync(0xffffffffu, isrl);
+          const uint32_t rk = __ballot_sync(0xffffffffu, isrk);
+          if (lane == 0) w.pmask[p0 >> 5] = make_uint4(lm, rl, rk, 0u);
+        }
+        __syncwarp();
+        for (int64_t i0 = b0; i0 < b1; i0 += 32) {
+          const int64_t i = i0 + lane;
+          const bool act = i < b1;
+          const int32_t D = Dn;
+          if (i0 + 32 + (int64_t)lane < b1) Dn = __ldg(cand_dst + i0 + 32 + lane);  // next chunk in flight
+          int32_t dck = 0, dcbo = 0;
+          uint4 r = make_uint4(0, 0, 0, 0);
+          if (act) r = csr_candidate(sy, w, hm, lo, ro, D, dck, dcbo);
+          if (REC && act) __stcs(oc.records + i, r);
+          if (DIG && act) dig += record_hash(ma + jm, D, r);
+          if (KEEP) emit_kept(oc, act && (r.w >> 31), ma + jm, D, r.z >> 16, dck, dcbo, lane);
+        }
+      }
+      __syncwarp();  // lists reused by the next run
+      j = k;
     }
   }
   if (DIG) {
     for (int o = 16; o > 0; o >>= 1) dig += __shfl_down_sync(0xffffffffu, dig, o);
     if (lane == 0 && dig) atomicAdd(oc.digest, (unsigned long long)dig);
   }
+}
+
+// Blocks of the grouped kernel resident on the device (occupancy query, cached
+// per instantiation).
+template <bool REC, bool DIG, bool KEEP>
+int64_t grouped_resident_grid() {
+  static std::atomic<int64_t> cached{0};
+  int64_t v = cached.load(std::memory_order_relaxed);
+  if (!v) {
+    int dev = 0, sms = 148, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, eval_csr_grouped<REC, DIG, KEEP>, CG_WARPS * 32,
+                                                      CG_WARPS * CG_WARP_BYTES) != cudaSuccess || per < 1)
+      per = 1;
+    v = (int64_t)sms * per;
+    cached.store(v, std::memory_order_relaxed);
+  }
+  return v;
 }
 
 __global__ void validate_candidates(const int64_t *rowptr, const int32_t *dst, const int32_t *method_class,
@@ -977,9 +1267,25 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
     DenseSys sy{cx, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, c, M};
     eval_dense<REC, DIG, KEEP><<<dim3(gx, gy), DB_THREADS, 0, st>>>(sy, oc, mchunk);
   } else {
-    unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)s->M * 32, 256), 148 * 64);
-    eval_csr<REC, DIG, KEEP><<<g, 256, 0, st>>>(cx, oc, rowptr, dst, s->cls_n, s->cls_a, s->cls_P, s->cls_Q,
-                                                s->cls_S, s->M);
+    CsrSys sy;
+    sy.cx = cx;
+    sy.csum = s->csum;
+    sy.cpk = s->cpk;
+    sy.dest_rec = s->dest_rec;
+    sy.cls_n = s->cls_n;
+    sy.cls_a = s->cls_a;
+    sy.cls_P = s->cls_P;
+    sy.cls_Q = s->cls_Q;
+    sy.cls_S = s->cls_S;
+    sy.sw = (uint32_t)s->sum_words;
+    sy.c = (uint32_t)s->c;
+    // record offsets are 32-bit: larger systems evaluate every method on the general path
+    sy.staged = s->sum_words * (2 * (int64_t)s->c + 1) < (int64_t)UINT32_MAX ? 1 : 0;
+    sy.M = s->M;
+    const int64_t groups = ceil_div((int64_t)s->M, CG_M);
+    const int64_t full = grouped_resident_grid<REC, DIG, KEEP>();
+    unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(groups, CG_WARPS), full));
+    eval_csr_grouped<REC, DIG, KEEP><<<g, CG_WARPS * 32, CG_WARPS * CG_WARP_BYTES, st>>>(sy, oc, rowptr, dst);
   }
   MM_LAUNCH_CHECK();
 }

@@ -52,7 +52,7 @@ struct Snapshot {
 int64_t estimate_footprint(const Served &v) {
   const int64_t nu = (int64_t)v.acc_idx.size() + (int64_t)v.call_idx.size();
   const int64_t aw = ((int64_t)v.c + 127) / 128 * 4;
-  const int64_t sized = 160 * (int64_t)v.M + 120 * nu + 64 * (int64_t)v.c + 8 * aw * v.c;
+  const int64_t sized = 160 * (int64_t)v.M + 128 * nu + 96 * (int64_t)v.c + 8 * aw * v.c + aw * v.c / 2;
   return sized / 10 * 9 + (2 << 20);
 }
 
