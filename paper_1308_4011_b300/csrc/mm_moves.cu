@@ -1020,25 +1020,29 @@ __device__ __noinline__ uint64_t csr_general_row(const EvalCtx cx, const OutCtx 
   return dig;
 }
 
-// One candidate (m -> D): probe every row at D, reduce page by page.
+// One candidate (m -> D): probe the rows at D, reduce page by page.  Rows are
+// m's L entries, C's in-row and out-row, then m's R entries; the R rows only
+// matter to the callers' CBO, so without CBO in the mask they are only
+// compared with D, not probed.
 __device__ __forceinline__ uint4 csr_candidate(const CsrSys &sy, const CsrGroup &w, const MoveHdr &h, int32_t lo,
                                                int32_t ro, int32_t D, int32_t &dck, int32_t &dcbo) {
   const DState ds = dstate_rec(sy.dest_rec, D);
-  const int32_t nL = h.w0.z, nR = h.w1.x, nLR = nL + nR, nP = nLR + 2;
+  const int32_t nL = h.w0.z, nR = h.w1.x;
+  const int32_t nprobe = (sy.cx.mask & 4u) ? nL + nR + 2 : nL + 2;
   const uint32_t rw = (uint32_t)D >> 10, b = ((uint32_t)D >> 5) & 31u, below = (1u << b) - 1u;
   const uint32_t dsh = (uint32_t)D & 31u;
   Gathered g;
   g.gain = 0; g.impX = 0; g.worX = 0; g.bDC = 0; g.bCD = 0;
   g.t = 0; g.sh = 0; g.outD = 0; g.cntCD = 0; g.inD = 0; g.cntDC = 0;
-  int32_t ml = -1, mr = -1;  // rows of m's lists whose class is D
-  for (int32_t p0 = 0; p0 < nP; p0 += 32) {
-    const int32_t pend = min(nP - p0, 32);
+  int32_t ml = -1, mr = -1;  // entries of m's lists whose class is D
+  for (int32_t p0 = 0; p0 < nprobe; p0 += 32) {
+    const int32_t pend = min(nprobe - p0, 32);
     uint32_t bits = 0, match = 0;
     for (int32_t k0 = 0; k0 < pend; k0 += CG_PB) {
       uint2 rec[CG_PB];
 #pragma unroll
       for (int u = 0; u < CG_PB; ++u) {
-        const uint2 pw = w.prow[p0 + k0 + u];  // rows past nP are the zero row
+        const uint2 pw = w.prow[p0 + k0 + u];  // rows past the probed ones are the zero row
         match |= (uint32_t)((int32_t)pw.y == D) << (k0 + u);
         rec[u] = __ldg(sy.csum + (pw.x + rw));
       }
@@ -1055,15 +1059,17 @@ __device__ __forceinline__ uint4 csr_candidate(const CsrSys &sy, const CsrGroup 
     g.gain += __popc(lv) - __popc(bits & lv);
     g.impX += __popc(bits & pm.y & valid);
     g.worX += __popc(~bits & pm.z & valid);
-    if (match) {
-      const int32_t e = p0 + __ffs(match) - 1;  // D appears at most once among m's L and once among its R
-      const uint32_t rest = match & (match - 1u);
-      if (e < nL) ml = e; else mr = e;
-      if (rest) mr = p0 + __ffs(rest) - 1;
+    for (uint32_t mm = match; mm; mm &= mm - 1u) {  // D appears at most once among L and once among R
+      const int32_t e = p0 + __ffs(mm) - 1;
+      if (e < nL) ml = e; else mr = e - nL - 2;
     }
-    const int32_t cin = nLR - p0;
+    const int32_t cin = nL - p0;
     if (cin >= 0 && cin < 32) g.bDC = (int32_t)((bits >> cin) & 1u);
     if (cin + 1 >= 0 && cin + 1 < 32) g.bCD = (int32_t)((bits >> (cin + 1)) & 1u);
+  }
+  if (!(sy.cx.mask & 4u)) {
+    for (int32_t e = 0; e < nR; ++e)
+      if (w.rent[ro + e].x == D) mr = e;
   }
   if (ml >= 0) {
     const int4 v = w.lent[lo + ml];
@@ -1073,7 +1079,7 @@ __device__ __forceinline__ uint4 csr_candidate(const CsrSys &sy, const CsrGroup 
     g.sh = w.lsh[lo + ml];
   }
   if (mr >= 0) {
-    const int4 v = w.rent[ro + mr - nL];
+    const int4 v = w.rent[ro + mr];
     g.inD = v.y;
     g.cntDC = v.z;
   }
@@ -1165,7 +1171,8 @@ __global__ void __launch_bounds__(CG_WARPS * 32, 3) eval_csr_grouped(CsrSys sy, 
         const int32_t C = hm.w0.x;
         int32_t Dn = b0 + (int64_t)lane < b1 ? __ldg(cand_dst + b0 + lane) : C;
         __syncwarp();  // the previous method's readers are done with the row table
-        // row table, page by page: lane describes row p0 + lane (rows past nP: the zero row)
+        // row table, page by page: lane describes row p0 + lane (rows past nP: the zero row).
+        // Order: L entries, C's in-row, C's out-row, R entries.
         for (int32_t p0 = 0; p0 < nP; p0 += 32) {
           const int32_t kk = p0 + (int32_t)lane;
           uint32_t off = zero_row, cls = 0xffffffffu;
@@ -1175,15 +1182,14 @@ __global__ void __launch_bounds__(CG_WARPS * 32, 3) eval_csr_grouped(CsrSys sy, 
             cls = (uint32_t)v.x;
             off = (sy.c + cls) * sw;
             isl = v.y > 0;
-          } else if (kk < nL + nR) {
-            const int4 v = w.rent[ro + kk - nL];
+          } else if (kk < nL + 2) {
+            off = (kk == nL ? sy.c + (uint32_t)C : (uint32_t)C) * sw;  // C is never a candidate: no class
+          } else if (kk < nP) {
+            const int4 v = w.rent[ro + kk - nL - 2];
             cls = (uint32_t)v.x;
             off = cls * sw;
             isrl = v.z == v.y;
             isrk = !isrl;
-          } else if (kk < nP) {
-            cls = (uint32_t)C;
-            off = (kk == nL + nR ? sy.c + cls : cls) * sw;
           }
           w.prow[kk] = make_uint2(off, cls);
           const uint32_t lm = __ballot_sync(0xffffffffu, isl);
