@@ -66,9 +66,8 @@ void upload(T *dst, const T *src, int64_t n, int32_t kind, cudaStream_t st) {
 void allocate_compute_buffers(mm_system *s) {
   DevArena &a = s->arena;
   const int64_t c = s->c, M = s->M, nu = s->n_call + s->n_acc;
-  s->bits_off = a.get<int64_t>(c + 1);
-  s->tile_off = a.get<int64_t>(c + 1);
-  s->bits = a.get<uint32_t>(s->summary.bits_words);
+  s->own_ptr = a.get<int64_t>((int64_t)s->A + 1);
+  s->own_list = a.get<int32_t>(std::max<int64_t>(s->n_acc, 1));
   s->cls_P = a.get<int64_t>(c);
   s->cls_Q = a.get<int64_t>(c);
   s->cls_S = a.get<int64_t>(c);
@@ -316,7 +315,8 @@ mm_status mm_system_info_get(mm_system *s, mm_system_info *info) {
       info->n_class_edges = v;
     }
     info->device_bytes =
-        s->arena.bytes + (int64_t)(s->sort_ws.cap + s->eval_ws.cap + s->stage_ws.cap + s->kept_ws.cap);
+        s->arena.bytes + (int64_t)(s->sort_ws.cap + s->eval_ws.cap + s->stage_ws.cap + s->kept_ws.cap +
+                                   s->edit_ws.cap + s->union_ws.cap);
   });
 }
 
@@ -332,6 +332,7 @@ void mm_free_system(mm_system *s) {
   s->stage_ws.release(s->stream);
   s->kept_ws.release(s->stream);
   s->edit_ws.release(s->stream);
+  s->union_ws.release(s->stream);
   delete s;
   if (cur >= 0 && cur != dev) cudaSetDevice(cur);
 }

@@ -159,7 +159,6 @@ void build_mirror(mm_system *s) {
   mr.acc_cap = s->n_acc;
   mr.call_cap = s->n_call;
   mr.nu_cap = s->n_acc + s->n_call;
-  mr.bits_cap = s->summary.bits_words;
   mr.ready = true;
 }
 
@@ -177,6 +176,7 @@ void ensure_capacity(mm_system *s, int64_t n_acc, int64_t n_call) {
   if (n_acc > mr.acc_cap) {
     int64_t cap = n_acc + n_acc / 4 + 1024;
     s->acc_idx = regrow(s, s->acc_idx, s->n_acc, cap);
+    s->own_list = regrow(s, s->own_list, (int64_t)0, cap);
     mr.acc_cap = cap;
   }
   if (n_call > mr.call_cap) {
@@ -211,11 +211,6 @@ void resummarise(mm_system *s) {
   s->summary.bits_words = words;
   s->summary.lcom_tiles = tiles;
   s->summary.max_class_methods = nmax;
-  if (words > mr.bits_cap) {
-    int64_t cap = words + words / 4 + 1024;
-    s->bits = regrow(s, s->bits, (int64_t)0, cap);
-    mr.bits_cap = cap;
-  }
 }
 
 // Insert (value at rank) into or remove (the element at rank) from row m of a device CSR.

@@ -111,7 +111,7 @@ struct EditMirror {
   bool ready = false;
   std::vector<std::vector<int32_t>> acc, calls, callers;
   std::vector<int32_t> method_class, attr_class, cls_n, cls_a;
-  int64_t acc_cap = 0, call_cap = 0, nu_cap = 0, bits_cap = 0;
+  int64_t acc_cap = 0, call_cap = 0, nu_cap = 0;
 };
 
 struct mm_system {
@@ -133,6 +133,7 @@ struct mm_system {
   Scratch stage_ws;    // host-output staging
   Scratch kept_ws;     // kept moves + per-method marks of the last evaluation
   Scratch edit_ws;     // edit patches and incremental re-evaluation
+  Scratch union_ws;    // per-warp bitmaps of accessor unions (largest classes only)
   bool kept_valid = false;   // kept_ws holds the full cross product's kept moves for:
   uint32_t kept_mask = 0;    //   this metric mask
   int32_t kept_min = 0;      //   and this min_improved
@@ -151,10 +152,10 @@ struct mm_system {
   int32_t *attr_local;             // rank of an attribute inside its class
   int32_t *fan_in;
 
-  // attribute bitsets: class C, method rank i -> bits[bits_off[C] + i * W_C]
-  int64_t *bits_off;
-  uint32_t *bits;
-  int64_t *tile_off;               // LCOM pair-tile offsets per class
+  // inverted index of own accesses: attribute alpha -> class-local ranks of the
+  // methods of own(alpha) that access it, at own_list[own_ptr[alpha] ..]
+  int64_t *own_ptr;                // n_attrs + 1
+  int32_t *own_list;               // <= n_acc entries
 
   // metrics
   int64_t *cls_P, *cls_Q, *cls_S;
@@ -208,6 +209,46 @@ void radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t
 
 void load_validate_and_summarise(mm_system *s);     // mm_system.cu
 void build_structures(mm_system *s);                // mm_system.cu
+// Per-warp bitmaps for accessor unions over the methods of one class: words
+// per warp (largest class), shared-memory bytes per block of 256 threads, or a
+// zeroed global slice per warp of `grid` blocks when the largest class is too
+// big for shared memory (then smem = 0 and gbm != nullptr).
+struct UnionBitmap {
+  int32_t words;
+  size_t smem;
+  uint32_t *gbm;
+  unsigned grid;
+};
+UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted);
+// Number of distinct methods of class K that access at least one of the
+// attributes of K in acc_row[0 .. len): the union of their accessor lists,
+// counted in a per-warp bitmap over K's method ranks (set, then read back and
+// cleared word by word, so the bitmap is all zero again on return).
+__device__ __forceinline__ int32_t accessor_union(const int32_t *acc_row, int64_t len, int32_t K, const int32_t *attr_class,
+                                  const int64_t *own_ptr, const int32_t *own_list, uint32_t *bm, uint32_t lane) {
+  int32_t cnt = 0;
+  for (int phase = 0; phase < 2; ++phase) {
+    for (int64_t e0 = 0; e0 < len; e0 += 32) {
+      const int32_t al = e0 + lane < len ? acc_row[e0 + lane] : -1;
+      uint32_t mine = __ballot_sync(0xffffffffu, al >= 0 && attr_class[al] == K);
+      while (mine) {
+        const int b = __ffs(mine) - 1;
+        mine &= mine - 1u;
+        const int32_t a = __shfl_sync(0xffffffffu, al, b);
+        const int64_t p1 = own_ptr[a + 1];
+        for (int64_t p = own_ptr[a] + lane; p < p1; p += 32) {
+          const int32_t j = own_list[p];
+          if (phase == 0) atomicOr(&bm[j >> 5], 1u << (j & 31));
+          else cnt += __popc(atomicExch(&bm[j >> 5], 0u));
+        }
+      }
+    }
+    __syncwarp();
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  return cnt;
+}
+
 void build_metrics(mm_system *s);                   // mm_metrics.cu
 void build_move_precompute(mm_system *s);           // mm_moves.cu
 void export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *out_m, int32_t kind);

@@ -1,14 +1,16 @@
 // Class metrics (Sec. II.B) on the device:
-//   * per-class attribute bitsets: row i of class C holds the attributes of C
-//     that its i-th method accesses (only attributes owned by C count);
-//   * LCOM method-pair kernel: for every unordered pair of methods of a class,
-//     "share" = any bit of (row_i AND row_j); Q = sharing pairs, P = n(n-1)/2 - Q,
-//     q_x = partners sharing with x; pairs are tiled 32 x 32 per warp, so a
-//     2,000-method class is spread over 2,016 warps and a singleton costs one;
+//   * inverted index of own accesses: attribute -> the methods of its class
+//     that access it (only attributes owned by the class count);
+//   * LCOM pair counts: the methods sharing an attribute with x are the union
+//     of the accessor lists of x's own attributes, so q_x = |union| - 1 and
+//     Q = sum q_x / 2, P = n(n-1)/2 - Q; the union is counted in a per-warp
+//     bitmap over the class's method ranks.  Work is the sum over accesses of
+//     the accessor-list length instead of n^2 word ANDs per class;
 //   * coupling: every use edge (class of x, class it uses) as a 64-bit key,
 //     segmented by source class with the radix sort, run-length encoded into
 //     the class-use multigraph cnt[Y][E]; CBO(Y) = number of E != Y with
-//     cnt > 0; out/in adjacency bitsets for the move evaluation's probes.
+//     cnt > 0; out/in adjacency bitsets and their compressed two-level form
+//     for the move evaluation's probes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,35 +28,21 @@ inline unsigned grid_for(int64_t n, int tpb = TPB) {
   return (unsigned)g;
 }
 
-inline unsigned grid_persistent() { return 148 * 8; }
+// ---------------------------------------------------------------- LCOM
 
-__global__ void class_sizes_to_words(const int32_t *cls_n, const int32_t *cls_a, int32_t c, int64_t *words,
-                                     int64_t *tiles) {
-  int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (C >= c) return;
-  int64_t n = cls_n[C], a = cls_a[C];
-  int64_t T = (n + 31) / 32;
-  words[C] = n * ((a + 31) / 32);
-  tiles[C] = T * (T + 1) / 2;
-}
-
-// One thread per method: set the bits of its accesses to its own class's
-// attributes (local attribute ranks); own_x = their number, S_C += own_x.
-__global__ void build_bitsets(const int32_t *method_class, const int32_t *method_local, const int64_t *acc_rowptr,
-                              const int32_t *acc_idx, const int32_t *attr_class, const int32_t *attr_local,
-                              const int32_t *cls_a, const int64_t *bits_off, uint32_t *bits, int32_t M,
-                              int32_t *own, int64_t *cls_S) {
+// Inverted index of own accesses.  One thread per method: count its accesses
+// to its own class's attributes per attribute; own_x = their number, S_C += own_x.
+__global__ void own_access_count(const int32_t *method_class, const int64_t *acc_rowptr, const int32_t *acc_idx,
+                                 const int32_t *attr_class, int32_t M, int64_t *acnt, int32_t *own,
+                                 int64_t *cls_S) {
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
-  int32_t C = method_class[x];
-  int64_t W = ((int64_t)cls_a[C] + 31) / 32;
-  uint32_t *row = bits + bits_off[C] + (int64_t)method_local[x] * W;
+  const int32_t C = method_class[x];
   int32_t cnt = 0;
   for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
-    int32_t al = acc_idx[e];
+    const int32_t al = acc_idx[e];
     if (attr_class[al] == C) {
-      int32_t l = attr_local[al];
-      row[l >> 5] |= 1u << (l & 31);
+      atomicAdd(reinterpret_cast<unsigned long long *>(&acnt[al]), 1ull);
       ++cnt;
     }
   }
@@ -62,75 +50,58 @@ __global__ void build_bitsets(const int32_t *method_class, const int32_t *method
   if (cnt) atomicAdd(reinterpret_cast<unsigned long long *>(&cls_S[C]), (unsigned long long)cnt);
 }
 
-__device__ __forceinline__ int32_t upper_class(const int64_t *off, int32_t c, int64_t t) {
-  // largest C with off[C] <= t (off has c+1 non-decreasing entries)
-  int32_t lo = 0, hi = c;
-  while (lo < hi) {
-    int32_t mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= t) lo = mid; else hi = mid - 1;
+// accessors of alpha (class-local method ranks) at own_list[own_ptr[alpha] ..], in any order
+__global__ void own_access_fill(const int32_t *method_class, const int32_t *method_local, const int64_t *acc_rowptr,
+                                const int32_t *acc_idx, const int32_t *attr_class, int32_t M,
+                                const int64_t *own_ptr, int32_t *cursor, int32_t *own_list) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  const int32_t C = method_class[x], r = method_local[x];
+  for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
+    const int32_t al = acc_idx[e];
+    if (attr_class[al] == C) own_list[own_ptr[al] + atomicAdd(&cursor[al], 1)] = r;
   }
-  return lo;
 }
 
-// LCOM pair kernel: one warp per 32 x 32 tile (rows ti, columns tj >= ti) of
-// the method-pair triangle of one class.  Lane l owns row i = 32 ti + l and
-// builds share_mask (bit jj: rows i and 32 tj + jj share an owned attribute).
-// Row sums give q_i; for off-diagonal tiles a ballot per column gives q_j.
-__global__ void __launch_bounds__(256) lcom_pairs(const int64_t *tile_off, const int32_t *cls_n,
-                                                  const int32_t *cls_a, const int64_t *bits_off,
-                                                  const uint32_t *__restrict__ bits, const int64_t *cm_rowptr,
-                                                  const int32_t *cm_list, int32_t c, int64_t total_tiles,
-                                                  int32_t *q, int64_t *cls_Q) {
-  const int lane = threadIdx.x & 31;
+// LCOM pair counts: q_x = methods of x's class sharing an own attribute with x
+// = |union of the accessors of x's own attributes| - 1 (x itself), and
+// sum_x q_x = 2 Q_C.  One warp per method; bitmap words per warp in shared
+// memory, or in a zeroed global slice when the largest class is too big.
+__global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, const int64_t *acc_rowptr,
+                                                  const int32_t *acc_idx, const int32_t *attr_class,
+                                                  const int64_t *own_ptr, const int32_t *own_list,
+                                                  const int32_t *own, int32_t M, int32_t words,
+                                                  uint32_t *gbm, int32_t *q, int64_t *cls_Q) {
+  extern __shared__ uint32_t lu_smem[];
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  uint32_t *bm = gbm ? gbm + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wid) * words : lu_smem + wid * words;
+  if (!gbm)
+    for (int32_t i = (int32_t)lane; i < words; i += 32) bm[i] = 0u;
+  __syncwarp();
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total_tiles; t += nwarps) {
-    int32_t C = upper_class(tile_off, c, t);
-    int64_t local = t - tile_off[C];
-    int32_t n = cls_n[C];
-    int32_t T = (n + 31) >> 5;
-    int32_t ti = 0;
-    while (local >= T - ti) { local -= T - ti; ++ti; }
-    int32_t tj = ti + (int32_t)local;
-    int64_t W = ((int64_t)cls_a[C] + 31) >> 5;
-    if (W == 0) continue;  // no attribute: no pair shares
-    const uint32_t *base = bits + bits_off[C];
-    int32_t i = ti * 32 + lane;
-    bool vi = i < n;
-    int32_t j0 = tj * 32;
-    int32_t jn = min(32, n - j0);
-    uint32_t share = 0;
-    for (int64_t w0 = 0; w0 < W; w0 += 8) {
-      uint32_t ri[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) ri[k] = (vi && w0 + k < W) ? base[(int64_t)i * W + w0 + k] : 0u;
-      for (int jj = 0; jj < jn; ++jj) {
-        const uint32_t *rj = base + (int64_t)(j0 + jj) * W + w0;
-        uint32_t acc = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (w0 + k < W) acc |= ri[k] & __ldg(rj + k);
-        if (acc) share |= 1u << jj;
-      }
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
+    if (own[x] == 0) {
+      if (lane == 0) q[x] = 0;
+      continue;
     }
-    if (ti == tj) share &= ~(1u << lane);
-    if (!vi) share = 0;
-    int32_t rc = __popc(share);
-    int32_t pairs = rc;
-    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_down_sync(0xffffffffu, pairs, o);
-    const int32_t *members = cm_list + cm_rowptr[C];
-    if (vi && rc) atomicAdd(&q[members[i]], rc);
-    if (ti != tj) {
-      int32_t colcnt = 0;
-      for (int jj = 0; jj < 32; ++jj) {
-        int32_t cc = __popc(__ballot_sync(0xffffffffu, (share >> jj) & 1u));
-        if (lane == jj) colcnt = cc;
-      }
-      if (lane < jn && colcnt) atomicAdd(&q[members[j0 + lane]], colcnt);
-    } else {
-      pairs >>= 1;  // each pair of the diagonal tile was seen from both rows
+    const int32_t C = method_class[x];
+    const int64_t a0 = acc_rowptr[x];
+    const int32_t u = accessor_union(acc_idx + a0, acc_rowptr[x + 1] - a0, C, attr_class, own_ptr, own_list, bm,
+                                     lane);
+    if (lane == 0) {
+      q[x] = u - 1;
+      if (u > 1) atomicAdd(reinterpret_cast<unsigned long long *>(&cls_Q[C]), (unsigned long long)(u - 1));
     }
-    if (lane == 0 && pairs) atomicAdd(reinterpret_cast<unsigned long long *>(&cls_Q[C]), (unsigned long long)pairs);
   }
+}
+
+__global__ void finalize_classes(const int32_t *cls_n, int64_t *cls_Q, int32_t c, int64_t *cls_P) {
+  int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= c) return;
+  const int64_t n = cls_n[C];
+  const int64_t Q = cls_Q[C] / 2;  // each sharing pair was counted from both of its methods
+  cls_Q[C] = Q;
+  cls_P[C] = n * (n - 1) / 2 - Q;
 }
 
 // ---------------------------------------------------------------- coupling
@@ -194,12 +165,6 @@ __global__ void multigraph_fill(const uint64_t *keys, const int64_t *start, cons
   }
 }
 
-__global__ void finalize_classes(const int32_t *cls_n, const int64_t *cls_Q, int32_t c, int64_t *cls_P) {
-  int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (C >= c) return;
-  int64_t n = cls_n[C];
-  cls_P[C] = n * (n - 1) / 2 - cls_Q[C];
-}
 
 __global__ void summary_popc(const uint2 *sum, int64_t n, int32_t *cnt) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -242,36 +207,52 @@ __global__ void destination_records(const int32_t *cls_n, const int32_t *cls_a, 
 
 }  // namespace
 
+UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted) {
+  UnionBitmap ub;
+  ub.words = (int32_t)std::max<int64_t>(1, ceil_div(std::max(s->summary.max_class_methods, 1), 32));
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps_wanted, 8), 148 * 8));
+  ub.grid = (unsigned)blocks;
+  const size_t per_block = (size_t)ub.words * 8 * sizeof(uint32_t);
+  if (per_block <= 48 * 1024) {
+    ub.smem = per_block;
+    ub.gbm = nullptr;
+  } else {
+    ub.smem = 0;
+    const size_t bytes = per_block * (size_t)blocks;
+    ub.gbm = static_cast<uint32_t *>(s->union_ws.need(bytes, s->stream));
+    MM_CUDA_TRY(cudaMemsetAsync(ub.gbm, 0, bytes, s->stream));
+  }
+  return ub;
+}
+
 void build_metrics(mm_system *s) {
   cudaStream_t st = s->stream;
   const int32_t c = s->c, M = s->M;
 
-  // bitset and tile offsets
-  int64_t *tmp = static_cast<int64_t *>(s->eval_ws.need(sizeof(int64_t) * 2 * ((size_t)c + 1), st));
-  int64_t *words = tmp, *tiles = tmp + c + 1;
-  class_sizes_to_words<<<grid_for(c), TPB, 0, st>>>(s->cls_n, s->cls_a, c, words, tiles);
-  MM_LAUNCH_CHECK();
-  scan_exclusive_i64(words, s->bits_off, c, s->bits_off + c, s->sort_ws, st);
-  scan_exclusive_i64(tiles, s->tile_off, c, s->tile_off + c, s->sort_ws, st);
-
-  // bitsets, own, S
-  if (s->summary.bits_words > 0)
-    MM_CUDA_TRY(cudaMemsetAsync(s->bits, 0, sizeof(uint32_t) * (size_t)s->summary.bits_words, st));
+  // inverted index of own accesses, own, S
+  const int64_t A = s->A;
+  int64_t *acnt = static_cast<int64_t *>(s->eval_ws.need(sizeof(int64_t) * ((size_t)A + 1), st));
+  MM_CUDA_TRY(cudaMemsetAsync(acnt, 0, sizeof(int64_t) * ((size_t)A + 1), st));
   MM_CUDA_TRY(cudaMemsetAsync(s->cls_S, 0, sizeof(int64_t) * (size_t)c, st));
   MM_CUDA_TRY(cudaMemsetAsync(s->cls_Q, 0, sizeof(int64_t) * (size_t)c, st));
   MM_CUDA_TRY(cudaMemsetAsync(s->q, 0, sizeof(int32_t) * (size_t)std::max(M, 1), st));
   if (M > 0) {
-    build_bitsets<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->method_local, s->acc_rowptr, s->acc_idx,
-                                               s->attr_class, s->attr_local, s->cls_a, s->bits_off, s->bits, M,
-                                               s->own, s->cls_S);
+    own_access_count<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class, M,
+                                                   acnt, s->own, s->cls_S);
     MM_LAUNCH_CHECK();
   }
-  // LCOM pair tiles
-  if (s->summary.lcom_tiles > 0) {
-    int64_t want = ceil_div(s->summary.lcom_tiles, 8);
-    unsigned g = (unsigned)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)grid_persistent() * 4);
-    lcom_pairs<<<g, 256, 0, st>>>(s->tile_off, s->cls_n, s->cls_a, s->bits_off, s->bits, s->cm_rowptr, s->cm_list,
-                                  c, s->summary.lcom_tiles, s->q, s->cls_Q);
+  scan_exclusive_i64(acnt, s->own_ptr, A, s->own_ptr + A, s->sort_ws, st);
+  if (M > 0 && A > 0) {
+    int32_t *cursor = reinterpret_cast<int32_t *>(acnt);  // counts are consumed: reuse as cursors
+    MM_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)A, st));
+    own_access_fill<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->method_local, s->acc_rowptr, s->acc_idx,
+                                                  s->attr_class, M, s->own_ptr, cursor, s->own_list);
+    MM_LAUNCH_CHECK();
+    // LCOM pair counts from accessor unions
+    const UnionBitmap ub = union_bitmap(s, M);
+    lcom_union<<<ub.grid, 256, ub.smem, st>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class,
+                                               s->own_ptr, s->own_list, s->own, M, ub.words, ub.gbm, s->q,
+                                               s->cls_Q);
     MM_LAUNCH_CHECK();
   }
   finalize_classes<<<grid_for(c), TPB, 0, st>>>(s->cls_n, s->cls_Q, c, s->cls_P);

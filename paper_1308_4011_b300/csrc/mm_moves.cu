@@ -133,41 +133,31 @@ __global__ void use_runs_fill(const uint64_t *keys, const int64_t *start, const 
   }
 }
 
-// s for list-L entries with t > 0: one warp per entry, lanes over the methods of D
-__global__ void l_entries_s(const int4 *l_list, const int32_t *l_x, const int64_t *n_l, const int64_t *acc_rowptr,
-                            const int32_t *acc_idx, const int32_t *attr_class, const int32_t *attr_local,
-                            const int32_t *cls_n, const int32_t *cls_a, const int64_t *bits_off,
-                            const uint32_t *bits, int32_t *l_s) {
-  const int lane = threadIdx.x & 31;
+// s for list-L entries with t > 0: the methods of D sharing an attribute of D
+// with m = the union of the accessor lists of m's accesses into D (m is not in
+// D).  One warp per entry, bitmap over D's method ranks as in the LCOM counts.
+__global__ void __launch_bounds__(256) l_entries_s(const int4 *l_list, const int32_t *l_x, const int64_t *n_l,
+                                                   const int64_t *acc_rowptr, const int32_t *acc_idx,
+                                                   const int32_t *attr_class, const int64_t *own_ptr,
+                                                   const int32_t *own_list, int32_t words, uint32_t *gbm,
+                                                   int32_t *l_s) {
+  extern __shared__ uint32_t ls_smem[];
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  uint32_t *bm = gbm ? gbm + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wid) * words : ls_smem + wid * words;
+  if (!gbm)
+    for (int32_t i = (int32_t)lane; i < words; i += 32) bm[i] = 0u;
+  __syncwarp();
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t nl = *n_l;
   for (int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < nl; l += nwarps) {
-    int4 v = l_list[l];
-    if (v.w == 0) {
-      if (lane == 0) l_s[l] = 0;
-      continue;
+    const int4 v = l_list[l];
+    int32_t sv = 0;
+    if (v.w > 0) {
+      const int32_t x = l_x[l];
+      const int64_t a0 = acc_rowptr[x];
+      sv = accessor_union(acc_idx + a0, acc_rowptr[x + 1] - a0, v.x, attr_class, own_ptr, own_list, bm, lane);
     }
-    int32_t D = v.x, x = l_x[l];
-    int32_t nD = cls_n[D];
-    int64_t W = ((int64_t)cls_a[D] + 31) >> 5;
-    const uint32_t *base = bits + bits_off[D];
-    int32_t s = 0;
-    for (int32_t j0 = 0; j0 < nD; j0 += 32) {
-      int32_t j = j0 + lane;
-      bool sh = false;
-      if (j < nD) {
-        const uint32_t *row = base + (int64_t)j * W;
-        for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1] && !sh; ++e) {
-          int32_t al = acc_idx[e];
-          if (attr_class[al] == D) {
-            int32_t b = attr_local[al];
-            sh = (row[b >> 5] >> (b & 31)) & 1u;
-          }
-        }
-      }
-      s += __popc(__ballot_sync(0xffffffffu, sh));
-    }
-    if (lane == 0) l_s[l] = s;
+    if (lane == 0) l_s[l] = sv;
   }
 }
 
@@ -294,10 +284,9 @@ void build_move_precompute(mm_system *s) {
                                                 s->cbo_attrs, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list,
                                                 s->l_x, l_off, l_len, nu);
     MM_LAUNCH_CHECK();
-    l_entries_s<<<(unsigned)std::min<int64_t>(ceil_div(nu * 32, TPB), 148 * 32), TPB, 0, st>>>(s->l_list, s->l_x,
-                                                   &counters[1], s->acc_rowptr, s->acc_idx, s->attr_class,
-                                                   s->attr_local, s->cls_n, s->cls_a, s->bits_off, s->bits,
-                                                   s->l_s);
+    const UnionBitmap ub = union_bitmap(s, nu);
+    l_entries_s<<<ub.grid, 256, ub.smem, st>>>(s->l_list, s->l_x, &counters[1], s->acc_rowptr, s->acc_idx,
+                                                s->attr_class, s->own_ptr, s->own_list, ub.words, ub.gbm, s->l_s);
     MM_LAUNCH_CHECK();
   }
   // list R: runs of (m, X) over the classes of m's callers
