@@ -322,7 +322,8 @@ void apply_edit(mm_system *s, const mm_edit &e) {
   s->edits++;
   resummarise(s);
   // ---- recompute the class metrics and the per-method move data
-  const bool had_cache = s->kept_valid;
+  const bool had_cache = s->kept_valid && !s->kept_lists;  // only the full cross product is maintained
+  s->kept_valid = false;
   const uint32_t kmask = s->kept_mask;
   const int32_t kmin = s->kept_min;
   build_structures(s);

@@ -134,9 +134,12 @@ struct mm_system {
   Scratch kept_ws;     // kept moves + per-method marks of the last evaluation
   Scratch edit_ws;     // edit patches and incremental re-evaluation
   Scratch union_ws;    // per-warp bitmaps of accessor unions (largest classes only)
-  bool kept_valid = false;   // kept_ws holds the full cross product's kept moves for:
+  bool kept_valid = false;   // kept_ws holds the kept moves of the last evaluation for:
   uint32_t kept_mask = 0;    //   this metric mask
   int32_t kept_min = 0;      //   and this min_improved
+  bool kept_lists = false;   //   over explicit candidate lists (else the full cross product)
+  uint64_t kept_hash = 0;    //   whose content hash was this
+  int64_t kept_ncand = 0;    //   and length this
   int64_t kept_cap = 0;
 
   // inputs

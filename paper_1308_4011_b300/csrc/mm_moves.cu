@@ -1229,24 +1229,40 @@ int64_t grouped_resident_grid() {
   return v;
 }
 
+// Candidate lists: range / self / row-pointer checks, one warp per method row
+// (coalesced), and a content hash of the lists (every (index, destination) and
+// every row end), which keys the cached kept moves of a list evaluation.
 __global__ void validate_candidates(const int64_t *rowptr, const int32_t *dst, const int32_t *method_class,
-                                    int32_t M, int32_t c, int64_t n_cand, uint32_t *err) {
-  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= M) return;
+                                    int32_t M, int32_t c, int64_t n_cand, uint32_t *err,
+                                    unsigned long long *hash) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   uint32_t e = 0;
-  if (x == 0 && (rowptr[0] != 0 || rowptr[M] != n_cand)) e |= VE_CAND_ROWPTR;
-  int64_t a = rowptr[x], b = rowptr[x + 1];
-  if (a < 0 || b < a || b > n_cand) {
-    e |= VE_CAND_ROWPTR;
-  } else {
-    int32_t C = method_class[x];
-    for (int64_t i = a; i < b; ++i) {
-      int32_t D = dst[i];
+  uint64_t h = 0;
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
+    const int64_t a = rowptr[x], b = rowptr[x + 1];
+    if (x == 0 && (a != 0 || rowptr[M] != n_cand)) e |= VE_CAND_ROWPTR;
+    if (a < 0 || b < a || b > n_cand) {
+      e |= VE_CAND_ROWPTR;
+      continue;
+    }
+    const int32_t C = method_class[x];
+    for (int64_t i = a + lane; i < b; i += 32) {
+      const int32_t D = dst[i];
       if (D < 0 || D >= c) e |= VE_CAND_RANGE;
       else if (D == C) e |= VE_CAND_SELF;
+      h += smix(((uint64_t)i << 32) ^ (uint32_t)D);
     }
+    if (lane == 0) h += smix(0x6a09e667f3bcc909ULL ^ (uint64_t)b ^ ((uint64_t)x << 40));
   }
-  if (e) atomicOr(err, e);
+  for (int o = 16; o > 0; o >>= 1) {
+    e |= __shfl_xor_sync(0xffffffffu, e, o);
+    h += __shfl_xor_sync(0xffffffffu, h, o);
+  }
+  if (lane == 0) {
+    if (e) atomicOr(err, e);
+    if (h) atomicAdd(hash, (unsigned long long)h);
+  }
 }
 
 template <bool REC, bool DIG, bool KEEP>
@@ -1401,7 +1417,7 @@ static void check_criteria(const mm_criteria &crit) {
 
 // Upload (if host) and validate an explicit candidate list; returns device pointers.
 static void prepare_candidates(mm_system *s, const mm_candidates *cands, const int64_t **rowptr,
-                               const int32_t **dst, int64_t *n_cand, Scratch &ws) {
+                               const int32_t **dst, int64_t *n_cand, Scratch &ws, uint64_t *hash = nullptr) {
   *rowptr = nullptr;
   *dst = nullptr;
   if (!cands || !cands->rowptr) {
@@ -1427,13 +1443,16 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
     throw MmError{MM_EINVAL, "candidates: bad ptr_kind"};
   }
   MM_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(uint32_t), st));
+  MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 3, 0, sizeof(unsigned long long), st));
   if (s->M > 0) {
-    validate_candidates<<<grid_for(s->M), TPB, 0, st>>>(*rowptr, *dst, s->method_class, s->M, s->c, *n_cand,
-                                                        s->d_err);
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)s->M * 32, TPB), 148 * 16);
+    validate_candidates<<<g, TPB, 0, st>>>(*rowptr, *dst, s->method_class, s->M, s->c, *n_cand, s->d_err,
+                                           s->d_u64 + 3);
     MM_LAUNCH_CHECK();
   }
   uint32_t err = 0;
   MM_CUDA_TRY(cudaMemcpyAsync(&err, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (hash) MM_CUDA_TRY(cudaMemcpyAsync(hash, s->d_u64 + 3, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
   MM_CUDA_TRY(cudaStreamSynchronize(st));
   if (err & VE_CAND_ROWPTR) throw MmError{MM_EINVAL, "candidates: rowptr must start at 0, be non-decreasing and end at n_cand"};
   if (err & VE_CAND_RANGE) throw MmError{MM_EINVAL, "candidates: destination class out of range"};
@@ -1486,7 +1505,8 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
   const int64_t *rowptr;
   const int32_t *dst;
   int64_t n_cand;
-  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, s->stage_ws);
+  uint64_t chash = 0;
+  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, s->stage_ws, &chash);
   s->kept_valid = false;
   if (n_cand == 0 || s->M == 0) {
     if (digest) {
@@ -1507,18 +1527,19 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
     oc.digest = s->d_u64;
     MM_CUDA_TRY(cudaMemsetAsync(s->d_u64, 0, sizeof(unsigned long long), st));
   }
-  // The full cross product also compacts its kept moves in the same pass, so a
-  // following mm_suggest_moves with the same criteria needs no second pass.
-  const bool fuse_kept = rowptr == nullptr;
+  // The pass also compacts the kept moves, so a following mm_suggest_moves with
+  // the same criteria (and, for explicit lists, lists of the same content hash)
+  // needs no second pass.
   const int64_t cap = kept_capacity(s);
-  if (fuse_kept) attach_kept(s, oc, cap);
+  attach_kept(s, oc, cap);
   dispatch_eval(s, cx, oc, rowptr, dst);
-  if (fuse_kept) {
-    s->kept_valid = true;
-    s->kept_mask = crit.metric_mask;
-    s->kept_min = crit.min_improved;
-    s->kept_cap = cap;
-  }
+  s->kept_valid = true;
+  s->kept_mask = crit.metric_mask;
+  s->kept_min = crit.min_improved;
+  s->kept_cap = cap;
+  s->kept_lists = rowptr != nullptr;
+  s->kept_hash = chash;
+  s->kept_ncand = n_cand;
   if (records && kind == MM_PTR_HOST)
     MM_CUDA_TRY(cudaMemcpyAsync(records, rec_dev, sizeof(uint4) * (size_t)n_cand, cudaMemcpyDeviceToHost, st));
   if (digest) {
@@ -1570,12 +1591,15 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
   const int64_t *rowptr;
   const int32_t *dst;
   int64_t n_cand;
-  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, s->stage_ws);
+  uint64_t chash = 0;
+  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, s->stage_ws, &chash);
   int64_t K = 0, nm = 0;
   mm_move *kept = nullptr;
   if (n_cand > 0 && s->M > 0) {
     EvalCtx cx = make_ctx(s, crit);
-    const bool reuse = rowptr == nullptr && s->kept_valid && s->kept_mask == crit.metric_mask &&
+    const bool same_cands = rowptr == nullptr ? !s->kept_lists
+                                              : (s->kept_lists && s->kept_hash == chash && s->kept_ncand == n_cand);
+    const bool reuse = s->kept_valid && same_cands && s->kept_mask == crit.metric_mask &&
                        s->kept_min == crit.min_improved;
     int64_t cap = reuse ? s->kept_cap : kept_capacity(s);
     if (!reuse) s->kept_valid = false;
@@ -1599,12 +1623,14 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
       cap = K + K / 8 + 1024;  // grow and evaluate again
       s->kept_valid = false;
     }
-    if (rowptr == nullptr) {  // the full cross product's kept moves stay cached for these criteria
-      s->kept_cap = std::max(s->kept_cap, cap);
-      s->kept_valid = true;
-      s->kept_mask = crit.metric_mask;
-      s->kept_min = crit.min_improved;
-    }
+    // the kept moves stay cached for these criteria and candidates
+    s->kept_cap = std::max(s->kept_cap, cap);
+    s->kept_valid = true;
+    s->kept_mask = crit.metric_mask;
+    s->kept_min = crit.min_improved;
+    s->kept_lists = rowptr != nullptr;
+    s->kept_hash = chash;
+    s->kept_ncand = n_cand;
     sort_kept_moves(s, kept, K);
   }
   int64_t nout = std::min<int64_t>(k, K);
