@@ -225,28 +225,51 @@ struct UnionBitmap {
 UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted);
 // Number of distinct methods of class K that access at least one of the
 // attributes of K in acc_row[0 .. len): the union of their accessor lists,
-// counted in a per-warp bitmap over K's method ranks (set, then read back and
-// cleared word by word, so the bitmap is all zero again on return).
-__device__ __forceinline__ int32_t accessor_union(const int32_t *acc_row, int64_t len, int32_t K, const int32_t *attr_class,
-                                  const int64_t *own_ptr, const int32_t *own_list, uint32_t *bm, uint32_t lane) {
+// counted in a per-warp bitmap over K's method ranks.  The accessor elements
+// of all the row's attributes are spread over the lanes at once (lane e holds
+// attribute e's list; element k goes to the lane whose prefix range holds it),
+// set in the bitmap, then read back and cleared word by word, so the bitmap is
+// all zero again on return.
+__device__ __forceinline__ int32_t accessor_union(const int32_t *acc_row, int64_t len, int32_t K,
+                                                  const int32_t *attr_class, const int64_t *own_ptr,
+                                                  const int32_t *own_list, uint32_t *bm, uint32_t lane) {
   int32_t cnt = 0;
-  for (int phase = 0; phase < 2; ++phase) {
-    for (int64_t e0 = 0; e0 < len; e0 += 32) {
-      const int32_t al = e0 + lane < len ? acc_row[e0 + lane] : -1;
-      uint32_t mine = __ballot_sync(0xffffffffu, al >= 0 && attr_class[al] == K);
-      while (mine) {
-        const int b = __ffs(mine) - 1;
-        mine &= mine - 1u;
-        const int32_t a = __shfl_sync(0xffffffffu, al, b);
-        const int64_t p1 = own_ptr[a + 1];
-        for (int64_t p = own_ptr[a] + lane; p < p1; p += 32) {
-          const int32_t j = own_list[p];
+  for (int64_t e0 = 0; e0 < len; e0 += 32) {
+    const int32_t al = e0 + lane < len ? acc_row[e0 + lane] : -1;
+    int64_t p0 = 0;
+    int32_t n = 0;
+    if (al >= 0 && attr_class[al] == K) {
+      p0 = own_ptr[al];
+      n = (int32_t)(own_ptr[al + 1] - p0);
+    }
+    int32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)lane >= o) incl += t;
+    }
+    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int phase = 0; phase < 2; ++phase) {
+      for (int32_t k0 = 0; k0 < total; k0 += 32) {
+        const int32_t k = k0 + (int32_t)lane;
+        // lane holding element k: the first lane whose inclusive prefix exceeds k
+        int32_t lo = 0, hi = 31;
+#pragma unroll
+        for (int step = 0; step < 5; ++step) {
+          const int32_t mid = (lo + hi) >> 1;
+          const int32_t pm = __shfl_sync(0xffffffffu, incl, mid);
+          if (pm > k) hi = mid; else lo = mid + 1;
+        }
+        const int32_t excl = __shfl_sync(0xffffffffu, incl, lo) - __shfl_sync(0xffffffffu, n, lo);
+        const int64_t base = __shfl_sync(0xffffffffu, p0, lo);
+        if (k < total) {
+          const int32_t j = own_list[base + (k - excl)];
           if (phase == 0) atomicOr(&bm[j >> 5], 1u << (j & 31));
           else cnt += __popc(atomicExch(&bm[j >> 5], 0u));
         }
       }
+      __syncwarp();
     }
-    __syncwarp();
   }
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   return cnt;

@@ -100,62 +100,62 @@ __global__ void scan_tiles_kernel(const Tin *in, Tout *out, int64_t n, const Tou
   }
 }
 
-// Small inputs: one block walks the array in 16K-element chunks with a carry
-// (one launch instead of three).
+// Small inputs: one block of 32 warps walks the array in 16K-element chunks
+// with a carry (one launch instead of three).  Warp w owns the 512 consecutive
+// elements [512 w, 512 w + 512) of a chunk and reads them as 16 coalesced rows
+// of 32; the block scans the 32 warp totals, then every warp rescans its rows.
 constexpr int SCAN1_THREADS = 1024;
-constexpr int SCAN1_ITEMS = 16;
+constexpr int SCAN1_ROWS = 16;
+constexpr int SCAN1_CHUNK = SCAN1_THREADS * SCAN1_ROWS;
 constexpr int64_t SCAN1_MAX = 1 << 16;
-
-template <class T>
-__device__ T block1024_exclusive_sum(T v, T *total) {
-  __shared__ T warp_sums[SCAN1_THREADS / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) warp_sums[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    T w = warp_sums[lane];
-    T wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      T y = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += y;
-    }
-    warp_sums[lane] = wi - w;
-    if (lane == 31) *total = wi;
-  }
-  __syncthreads();
-  T r = incl - v + warp_sums[warp];
-  __syncthreads();
-  return r;
-}
 
 template <class Tin, class Tout>
 __global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(const Tin *in, Tout *out, int64_t n,
                                                                    Tout *total_out) {
-  __shared__ Tout tot;
+  __shared__ Tout wsum[SCAN1_THREADS / 32];
+  __shared__ Tout chunk_total;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Tout carry = 0;
-  for (int64_t base = 0; base < n; base += (int64_t)SCAN1_THREADS * SCAN1_ITEMS) {
-    const int64_t b = base + (int64_t)threadIdx.x * SCAN1_ITEMS;
-    Tout v[SCAN1_ITEMS];
-    Tout sum = 0;
+  for (int64_t base = 0; base < n; base += SCAN1_CHUNK) {
+    const int64_t seg = base + (int64_t)warp * (32 * SCAN1_ROWS);
+    Tout v[SCAN1_ROWS];
+    Tout lsum = 0;
 #pragma unroll
-    for (int i = 0; i < SCAN1_ITEMS; ++i) {
-      v[i] = b + i < n ? (Tout)in[b + i] : Tout(0);
-      sum += v[i];
+    for (int i = 0; i < SCAN1_ROWS; ++i) {
+      const int64_t k = seg + i * 32 + lane;
+      v[i] = k < n ? (Tout)in[k] : Tout(0);
+      lsum += v[i];
     }
-    Tout ex = block1024_exclusive_sum<Tout>(sum, &tot) + carry;
 #pragma unroll
-    for (int i = 0; i < SCAN1_ITEMS; ++i) {
-      if (b + i < n) out[b + i] = ex;
-      ex += v[i];
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) wsum[warp] = lsum;
+    __syncthreads();
+    if (warp == 0) {
+      const Tout w = wsum[lane];
+      Tout wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const Tout y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      wsum[lane] = wi - w;
+      if (lane == 31) chunk_total = wi;
     }
-    carry += tot;
+    __syncthreads();
+    Tout run = carry + wsum[warp];
+#pragma unroll
+    for (int i = 0; i < SCAN1_ROWS; ++i) {
+      Tout incl = v[i];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const Tout y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int64_t k = seg + i * 32 + lane;
+      if (k < n) out[k] = run + incl - v[i];
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    carry += chunk_total;
     __syncthreads();
   }
   if (threadIdx.x == 0 && total_out) *total_out = carry;
