@@ -205,9 +205,10 @@ MMREF_API mm_status mm_set_stream(mm_system *sys, void *cuda_stream);
 /*
  * Compute every class and method metric (Sec. II.A, II.B) and the per-method
  * data that move evaluation needs.  Builds, on the device: the class->method
- * and class->attribute lists, the callers of each method, per-class attribute
- * bitsets, the LCOM method-pair counts, the class-use multigraph (segmented
- * sort + unique) with CBO and class adjacency bitsets, and fan-in/out.
+ * and class->attribute lists, an inverted index of own-attribute accesses,
+ * the LCOM method-pair counts (unions of accessor lists), the class-use
+ * multigraph (segmented sort + unique) with CBO, class adjacency bitsets and
+ * their compressed two-level form, and fan-in/out.
  * out_c[n_classes] and out_m[n_methods] are optional (NULL = keep on device);
  * out_kind says where they live.
  */
@@ -223,7 +224,11 @@ MMREF_API mm_status mm_compute_metrics(mm_system *sys, mm_class_metrics *out_c, 
  *   h = sm(key ^ sm(lo ^ sm(hi))),  key = (uint64)m << 32 | D,
  * where lo/hi are the record's first/last 8 bytes (little endian) and sm is
  * the SplitMix64 output function (Steele, Lea, Flood 2014).  records and
- * digest live in out_kind memory.  Errors: MM_EINVAL (no metrics computed,
+ * digest live in out_kind memory.  The same pass compacts the kept moves for
+ * `crit` into the handle, so a following mm_suggest_moves with the same
+ * criteria and the same candidates (the full cross product, or lists with the
+ * same 64-bit content hash, computed while validating them) does not evaluate
+ * again.  Errors: MM_EINVAL (no metrics computed,
  * bad criteria, a candidate out of range or equal to the method's class),
  * MM_ENOMEM, MM_ECUDA.
  */
