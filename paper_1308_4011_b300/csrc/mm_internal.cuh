@@ -199,7 +199,8 @@ struct mm_system {
 // *total_dev when non-null.  Uses sys->sort_ws-independent scratch `ws`.
 void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, Scratch &ws,
                         cudaStream_t st);
-void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch &ws, cudaStream_t st);
+void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch &ws, cudaStream_t st,
+                            int64_t *total_dev = nullptr);
 
 // Stable LSD radix sort of n keys (and optional uint32 values) on bits [0, nbits).
 // The result is left in keys/vals; alt buffers are scratch of the same size.

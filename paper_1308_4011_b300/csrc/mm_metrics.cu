@@ -106,65 +106,135 @@ __global__ void finalize_classes(const int32_t *cls_n, int64_t *cls_Q, int32_t c
 
 // ---------------------------------------------------------------- coupling
 
-// keys of every use edge of x: (Y, E) -> Y * c + E, intra-class edges -> sentinel c*c
-__global__ void coupling_keys(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
+// Class-use multigraph without a sort.  Pass 1: every use edge (Y = class of
+// x, E = class it uses, E != Y) sets bit E of Y's out-row and the summary bit
+// of that word (already-set bits are only read).
+__device__ __forceinline__ void mark_use(uint32_t *out_adj, uint2 *csum, int64_t aw, int64_t sw, int32_t Y,
+                                         int32_t E) {
+  uint32_t *w = &out_adj[(int64_t)Y * aw + (E >> 5)];
+  const uint32_t bit = 1u << (E & 31);
+  if (!(*w & bit)) atomicOr(w, bit);
+  uint32_t *r = &csum[(int64_t)Y * sw + (E >> 10)].x;
+  const uint32_t rbit = 1u << ((E >> 5) & 31);
+  if (!(*r & rbit)) atomicOr(r, rbit);
+}
+
+__global__ void coupling_mark(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
                               const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
-                              int32_t M, int32_t c, int32_t cbo_attrs, uint64_t *keys) {
+                              int32_t M, int32_t cbo_attrs, uint32_t *out_adj, int64_t aw, uint2 *csum,
+                              int64_t sw) {
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
-  const uint64_t sent = (uint64_t)c * (uint64_t)c;
-  int32_t Y = method_class[x];
-  int64_t pos = call_rowptr[x] + (cbo_attrs ? acc_rowptr[x] : 0);
+  const int32_t Y = method_class[x];
   for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e) {
-    int32_t E = method_class[call_idx[e]];
-    keys[pos++] = E != Y ? (uint64_t)Y * c + E : sent;
+    const int32_t E = method_class[call_idx[e]];
+    if (E != Y) mark_use(out_adj, csum, aw, sw, Y, E);
   }
   if (cbo_attrs)
     for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
-      int32_t E = attr_class[acc_idx[e]];
-      keys[pos++] = E != Y ? (uint64_t)Y * c + E : sent;
+      const int32_t E = attr_class[acc_idx[e]];
+      if (E != Y) mark_use(out_adj, csum, aw, sw, Y, E);
     }
 }
 
-__global__ void run_heads(const uint64_t *keys, int64_t n, uint64_t sent, int64_t *head, int64_t *n_valid) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint64_t k = keys[i];
-  bool valid = k != sent;
-  head[i] = (valid && (i == 0 || keys[i - 1] != k)) ? 1 : 0;
-  if (valid && (i + 1 == n || keys[i + 1] == sent)) *n_valid = i + 1;
+// Classes marked in the full words that summary record k of out-row Y marks.
+__device__ __forceinline__ int32_t record_classes(const uint2 *csum, const uint32_t *out_adj, int64_t aw,
+                                                  int64_t sw, int32_t Y, int64_t k) {
+  uint32_t bits = csum[(int64_t)Y * sw + k].x;
+  int32_t n = 0;
+  while (bits) {
+    const int j = __ffs(bits) - 1;
+    bits &= bits - 1u;
+    n += __popc(out_adj[(int64_t)Y * aw + k * 32 + j]);
+  }
+  return n;
 }
 
-__global__ void run_starts(const uint64_t *keys, const int64_t *head_scan, int64_t n, uint64_t sent,
-                           int64_t *start) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint64_t k = keys[i];
-  if (k != sent && (i == 0 || keys[i - 1] != k)) start[head_scan[i]] = i;
-}
-
-__global__ void multigraph_fill(const uint64_t *keys, const int64_t *start, const int64_t *n_unique,
-                                const int64_t *n_valid, int32_t c, int64_t cap, int32_t *mg_dst, int32_t *mg_cnt,
-                                int32_t *row_count, uint32_t *out_adj, uint32_t *in_adj, int64_t aw,
-                                uint2 *csum, int64_t sw) {
-  const int64_t nu = *n_unique, nv = *n_valid;
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu && u < cap;
-       u += (int64_t)gridDim.x * blockDim.x) {
-    int64_t s0 = start[u];
-    int64_t s1 = (u + 1 < nu) ? start[u + 1] : nv;
-    uint64_t k = keys[s0];
-    int32_t Y = (int32_t)(k / (uint64_t)c), E = (int32_t)(k % (uint64_t)c);
-    mg_dst[u] = E;
-    mg_cnt[u] = (int32_t)(s1 - s0);
-    atomicAdd(&row_count[Y], 1);
-    atomicOr(&out_adj[(int64_t)Y * aw + (E >> 5)], 1u << (E & 31));
-    atomicOr(&in_adj[(int64_t)E * aw + (Y >> 5)], 1u << (Y & 31));
-    // bit (w & 31) of record (w >> 5) marks full word w = E >> 5 (resp. Y >> 5) non-zero
-    atomicOr(&csum[(int64_t)Y * sw + (E >> 10)].x, 1u << ((E >> 5) & 31));
-    atomicOr(&csum[((int64_t)c + E) * sw + (Y >> 10)].x, 1u << ((Y >> 5) & 31));
+// Pass 2: CBO(Y) = number of marked classes of out-row Y (warp per row,
+// lanes over its summary records).
+__global__ void row_distinct(const uint2 *csum, const uint32_t *out_adj, int32_t c, int64_t aw, int64_t sw,
+                             int32_t *row_count) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t Y = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; Y < c; Y += nwarps) {
+    int32_t n = 0;
+    for (int64_t k = lane; k < sw; k += 32) n += record_classes(csum, out_adj, aw, sw, (int32_t)Y, k);
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if (lane == 0) row_count[Y] = n;
   }
 }
 
+// Pass 3: write each out-row's classes in ascending order at mg_rowptr[Y]
+// (lane k owns record k; records ascend with the lane), zero their counts, and
+// set the transposed in-row bits and their summary bits.
+__global__ void row_enumerate(uint2 *csum, const uint32_t *out_adj, uint32_t *in_adj, int32_t c, int64_t aw,
+                              int64_t sw, const int64_t *mg_rowptr, int32_t *mg_dst, int32_t *mg_cnt) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t Y = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; Y < c; Y += nwarps) {
+    int64_t pos = mg_rowptr[Y];
+    for (int64_t k0 = 0; k0 < sw; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const int32_t n = k < sw ? record_classes(csum, out_adj, aw, sw, (int32_t)Y, k) : 0;
+      int32_t incl = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += t;
+      }
+      int64_t p = pos + incl - n;
+      if (n) {
+        uint32_t bits = csum[Y * sw + k].x;
+        while (bits) {
+          const int j = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const int64_t wi = k * 32 + j;
+          uint32_t word = out_adj[Y * aw + wi];
+          while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1u;
+            const int32_t E = (int32_t)(wi * 32 + b);
+            mg_dst[p] = E;
+            mg_cnt[p] = 0;
+            ++p;
+            atomicOr(&in_adj[(int64_t)E * aw + (Y >> 5)], 1u << (Y & 31));
+            atomicOr(&csum[((int64_t)c + E) * sw + (Y >> 10)].x, 1u << ((Y >> 5) & 31));
+          }
+        }
+      }
+      pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
+__device__ __forceinline__ void count_use(const int64_t *mg_rowptr, const int32_t *mg_dst, int32_t *mg_cnt,
+                                          int32_t Y, int32_t E) {
+  int64_t lo = mg_rowptr[Y], hi = mg_rowptr[Y + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (mg_dst[mid] < E) lo = mid + 1; else hi = mid;
+  }
+  atomicAdd(&mg_cnt[lo], 1);
+}
+
+// Pass 4: multiplicities cnt[Y][E] = number of use edges (binary search of E in row Y).
+__global__ void coupling_count(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
+                               const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
+                               int32_t M, int32_t cbo_attrs, const int64_t *mg_rowptr, const int32_t *mg_dst,
+                               int32_t *mg_cnt) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  const int32_t Y = method_class[x];
+  for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e) {
+    const int32_t E = method_class[call_idx[e]];
+    if (E != Y) count_use(mg_rowptr, mg_dst, mg_cnt, Y, E);
+  }
+  if (cbo_attrs)
+    for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
+      const int32_t E = attr_class[acc_idx[e]];
+      if (E != Y) count_use(mg_rowptr, mg_dst, mg_cnt, Y, E);
+    }
+}
 
 __global__ void summary_popc(const uint2 *sum, int64_t n, int32_t *cnt) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -258,40 +328,34 @@ void build_metrics(mm_system *s) {
   finalize_classes<<<grid_for(c), TPB, 0, st>>>(s->cls_n, s->cls_Q, c, s->cls_P);
   MM_LAUNCH_CHECK();
 
-  // coupling: keys -> sort -> runs -> multigraph, CBO, adjacency bitsets
-  const int64_t nk = s->n_call + (s->cbo_attrs ? s->n_acc : 0);
-  const uint64_t sent = (uint64_t)c * (uint64_t)c;
-  MM_CUDA_TRY(cudaMemsetAsync(s->out_adj, 0, sizeof(uint32_t) * (size_t)(s->adj_words * c), st));
-  MM_CUDA_TRY(cudaMemsetAsync(s->in_adj, 0, sizeof(uint32_t) * (size_t)(s->adj_words * c), st));
-  MM_CUDA_TRY(cudaMemsetAsync(s->csum, 0, sizeof(uint2) * (size_t)(s->sum_words * (2 * c + 1)), st));
+  // coupling: mark the use edges in the out-rows, count and enumerate the
+  // marked classes row by row (ascending, so no sort), then count multiplicities
+  const int64_t aw = s->adj_words, sw = s->sum_words;
+  MM_CUDA_TRY(cudaMemsetAsync(s->out_adj, 0, sizeof(uint32_t) * (size_t)(aw * c), st));
+  MM_CUDA_TRY(cudaMemsetAsync(s->in_adj, 0, sizeof(uint32_t) * (size_t)(aw * c), st));
+  MM_CUDA_TRY(cudaMemsetAsync(s->csum, 0, sizeof(uint2) * (size_t)(sw * (2 * c + 1)), st));
   int32_t *row_count = s->cls_cbo;
-  MM_CUDA_TRY(cudaMemsetAsync(row_count, 0, sizeof(int32_t) * (size_t)c, st));
-  MM_CUDA_TRY(cudaMemsetAsync(s->mg_count, 0, sizeof(int64_t) * 2, st));
-  if (nk > 0) {
-    size_t bytes = sizeof(uint64_t) * 2 * (size_t)nk + sizeof(int64_t) * 2 * (size_t)nk;
-    char *b = static_cast<char *>(s->eval_ws.need(bytes, st));
-    uint64_t *keys = reinterpret_cast<uint64_t *>(b);
-    uint64_t *keys_alt = keys + nk;
-    int64_t *head = reinterpret_cast<int64_t *>(keys_alt + nk);
-    int64_t *start = head + nk;
-    coupling_keys<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
-                                               s->acc_idx, s->attr_class, M, c, s->cbo_attrs, keys);
-    MM_LAUNCH_CHECK();
-    radix_sort_u64(keys, keys_alt, nullptr, nullptr, nk, bits_for(sent), s->sort_ws, st);
-    int64_t *n_valid = s->mg_count + 1;
-    run_heads<<<grid_for(nk), TPB, 0, st>>>(keys, nk, sent, head, n_valid);
-    MM_LAUNCH_CHECK();
-    scan_exclusive_i64(head, head, nk, s->mg_count, s->sort_ws, st);
-    run_starts<<<grid_for(nk), TPB, 0, st>>>(keys, head, nk, sent, start);
-    MM_LAUNCH_CHECK();
-    multigraph_fill<<<grid_for(nk), TPB, 0, st>>>(keys, start, s->mg_count, n_valid, c, nk, s->mg_dst, s->mg_cnt,
-                                                  row_count, s->out_adj, s->in_adj, s->adj_words,
-                                                  s->csum, s->sum_words);
+  if (M > 0) {
+    coupling_mark<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
+                                               s->acc_idx, s->attr_class, M, s->cbo_attrs, s->out_adj, aw,
+                                               s->csum, sw);
     MM_LAUNCH_CHECK();
   }
+  const unsigned grow = (unsigned)std::min<int64_t>(ceil_div((int64_t)c * 32, TPB), 148 * 16);
+  row_distinct<<<grow, TPB, 0, st>>>(s->csum, s->out_adj, c, aw, sw, row_count);
+  MM_LAUNCH_CHECK();
   // mg_rowptr = exclusive scan of the row counts (CBO); last entry = distinct pairs
-  scan_exclusive_i32to64(row_count, s->mg_rowptr, c, s->sort_ws, st);
-  MM_CUDA_TRY(cudaMemcpyAsync(s->mg_rowptr + c, s->mg_count, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  scan_exclusive_i32to64(row_count, s->mg_rowptr, c, s->sort_ws, st, s->mg_rowptr + c);
+  row_enumerate<<<grow, TPB, 0, st>>>(s->csum, s->out_adj, s->in_adj, c, aw, sw, s->mg_rowptr, s->mg_dst,
+                                      s->mg_cnt);
+  MM_LAUNCH_CHECK();
+  if (M > 0) {
+    coupling_count<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
+                                                s->acc_idx, s->attr_class, M, s->cbo_attrs, s->mg_rowptr,
+                                                s->mg_dst, s->mg_cnt);
+    MM_LAUNCH_CHECK();
+  }
+  MM_CUDA_TRY(cudaMemcpyAsync(s->mg_count, s->mg_rowptr + c, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
   // compressed adjacency: record counts -> exclusive scan -> packed non-zero words
   {
     const int64_t ns = s->sum_words * (2 * (int64_t)c + 1);

@@ -48,91 +48,6 @@ __device__ __forceinline__ int32_t mg_lookup(const int64_t *rowptr, const int32_
 
 // ---------------------------------------------------------------- precompute
 
-// use keys of m: ((m * c + E) << 1) | kind, kind 0 = call into E, 1 = access of an attribute of E
-__global__ void method_use_keys(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
-                                const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
-                                int32_t M, int32_t c, uint64_t *keys) {
-  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= M) return;
-  int64_t pos = call_rowptr[x] + acc_rowptr[x];
-  uint64_t base = (uint64_t)x * (uint64_t)c;
-  for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e)
-    keys[pos++] = ((base + (uint64_t)method_class[call_idx[e]]) << 1);
-  for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e)
-    keys[pos++] = ((base + (uint64_t)attr_class[acc_idx[e]]) << 1) | 1u;
-}
-
-// caller-class keys, one per call edge y -> x: x * c + class(y) (sorted later,
-// so the callers of x come out grouped by class without a transpose)
-__global__ void caller_class_keys(const int64_t *call_rowptr, const int32_t *call_idx,
-                                  const int32_t *method_class, int32_t M, int32_t c, uint64_t *keys) {
-  int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (y >= M) return;
-  const uint64_t cy = (uint64_t)method_class[y];
-  for (int64_t e = call_rowptr[y]; e < call_rowptr[y + 1]; ++e)
-    keys[e] = (uint64_t)call_idx[e] * (uint64_t)c + cy;
-}
-
-__global__ void heads_shifted(const uint64_t *keys, int64_t n, int shift, int64_t *head) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  head[i] = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) ? 1 : 0;
-}
-
-__global__ void starts_shifted(const uint64_t *keys, const int64_t *head_scan, int64_t n, int shift,
-                               int64_t *start) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) start[head_scan[i]] = i;
-}
-
-// One thread per run (m, E) of m's use keys: split into the own-class run
-// (out_self) and list-L entries; L entries are placed by a second scan.
-__global__ void use_runs_classify(const uint64_t *keys, const int64_t *start, const int64_t *n_runs, int64_t n,
-                                  const int32_t *method_class, int32_t c, int32_t cbo_attrs, int32_t *out_self,
-                                  int64_t *lflag, int64_t cap) {
-  const int64_t nr = *n_runs;
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < cap; u += (int64_t)gridDim.x * blockDim.x) {
-    if (u >= nr) { lflag[u] = 0; continue; }
-    int64_t s0 = start[u], s1 = (u + 1 < nr) ? start[u + 1] : n;
-    uint64_t me = keys[s0] >> 1;
-    int32_t x = (int32_t)(me / (uint64_t)c), E = (int32_t)(me % (uint64_t)c);
-    int32_t C = method_class[x];
-    if (E == C) {
-      int32_t calls = 0, accs = 0;
-      for (int64_t i = s0; i < s1; ++i) (keys[i] & 1u) ? ++accs : ++calls;
-      out_self[x] = calls + (cbo_attrs ? accs : 0);
-      lflag[u] = 0;
-    } else {
-      lflag[u] = 1;
-    }
-  }
-}
-
-__global__ void use_runs_fill(const uint64_t *keys, const int64_t *start, const int64_t *n_runs, int64_t n,
-                              const int64_t *lpos, const int32_t *method_class, int32_t c, int32_t cbo_attrs,
-                              const int64_t *mg_rowptr, const int32_t *mg_dst, const int32_t *mg_cnt, int4 *l_list,
-                              int32_t *l_x, int32_t *l_off, int32_t *l_len, int64_t cap) {
-  const int64_t nr = *n_runs;
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nr && u < cap;
-       u += (int64_t)gridDim.x * blockDim.x) {
-    int64_t s0 = start[u], s1 = (u + 1 < nr) ? start[u + 1] : n;
-    uint64_t me = keys[s0] >> 1;
-    int32_t x = (int32_t)(me / (uint64_t)c), E = (int32_t)(me % (uint64_t)c);
-    int32_t C = method_class[x];
-    if (E == C) continue;
-    int32_t calls = 0, accs = 0;
-    for (int64_t i = s0; i < s1; ++i) (keys[i] & 1u) ? ++accs : ++calls;
-    int32_t out = calls + (cbo_attrs ? accs : 0);
-    int32_t cnt = out > 0 ? mg_lookup(mg_rowptr, mg_dst, mg_cnt, C, E) : 0;
-    int64_t l = lpos[u];
-    l_list[l] = make_int4(E, out, cnt, accs);
-    l_x[l] = x;
-    atomicMin(&l_off[x], (int32_t)l);
-    atomicAdd(&l_len[x], 1);
-  }
-}
-
 // s for list-L entries with t > 0: the methods of D sharing an attribute of D
 // with m = the union of the accessor lists of m's accesses into D (m is not in
 // D).  One warp per entry, bitmap over D's method ranks as in the LCOM counts.
@@ -161,37 +76,177 @@ __global__ void __launch_bounds__(256) l_entries_s(const int4 *l_list, const int
   }
 }
 
-__global__ void caller_runs_fill(const uint64_t *keys, const int64_t *start, const int64_t *n_runs, int64_t n,
-                                 const int64_t *rpos, const int32_t *method_class, int32_t c,
-                                 const int64_t *mg_rowptr, const int32_t *mg_dst, const int32_t *mg_cnt,
-                                 int4 *r_list, int32_t *in_self, int32_t *r_off, int32_t *r_len, int64_t cap) {
-  const int64_t nr = *n_runs;
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nr && u < cap;
-       u += (int64_t)gridDim.x * blockDim.x) {
-    int64_t s0 = start[u], s1 = (u + 1 < nr) ? start[u + 1] : n;
-    uint64_t k = keys[s0];
-    int32_t x = (int32_t)(k / (uint64_t)c), X = (int32_t)(k % (uint64_t)c);
-    int32_t C = method_class[x];
-    int32_t in = (int32_t)(s1 - s0);
-    if (X == C) {
-      in_self[x] = in;
+// ---- lists L and R without a global sort
+//
+// Each method's use keys ((E << 1) | kind, kind 1 = an attribute access) are
+// written at its segment call_rowptr[x] + acc_rowptr[x]; the class of every
+// caller of x at its segment of a counting sort by callee (offsets: exclusive
+// scan of fan-in).  One warp sorts each segment (rank by counting, ties by
+// position, so the order is deterministic), then walks its runs twice: once to
+// count the list entries (and the own-class run), once, after a scan of the
+// counts, to write them in method order.
+
+__global__ void method_use_keys32(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
+                                  const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
+                                  int32_t M, uint32_t *keys) {
+  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= M) return;
+  int64_t pos = call_rowptr[x] + acc_rowptr[x];
+  for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e)
+    keys[pos++] = (uint32_t)method_class[call_idx[e]] << 1;
+  for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e)
+    keys[pos++] = ((uint32_t)attr_class[acc_idx[e]] << 1) | 1u;
+}
+
+// class of every caller y of x, bucketed by callee x (order inside a bucket is arbitrary)
+__global__ void caller_classes_scatter(const int32_t *method_class, const int64_t *call_rowptr,
+                                       const int32_t *call_idx, int32_t M, const int64_t *rin_off,
+                                       int32_t *cursor, uint32_t *keys) {
+  int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= M) return;
+  const uint32_t cy = (uint32_t)method_class[y];
+  for (int64_t e = call_rowptr[y]; e < call_rowptr[y + 1]; ++e) {
+    const int32_t x = call_idx[e];
+    keys[rin_off[x] + atomicAdd(&cursor[x], 1)] = cy;
+  }
+}
+
+// segment of x: [a[x] + (b ? b[x] : 0), a[x + 1] + (b ? b[x + 1] : 0))
+__device__ __forceinline__ void segment(const int64_t *a, const int64_t *b, int64_t x, int64_t *p0, int64_t *len) {
+  const int64_t s = a[x] + (b ? b[x] : 0), e = a[x + 1] + (b ? b[x + 1] : 0);
+  *p0 = s;
+  *len = e - s;
+}
+
+// One warp per segment: out[p0 + rank(i)] = in[p0 + i], rank = number of keys
+// smaller, or equal and earlier.
+__global__ void segment_sort(const int64_t *a, const int64_t *b, int32_t M, const uint32_t *in, uint32_t *out) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
+    int64_t p0, len;
+    segment(a, b, x, &p0, &len);
+    if (len <= 32) {
+      const uint32_t k = (int64_t)lane < len ? in[p0 + lane] : 0xffffffffu;
+      int32_t rank = 0;
+      for (int32_t j = 0; j < (int32_t)len; ++j) {
+        const uint32_t kj = __shfl_sync(0xffffffffu, k, j);
+        rank += (kj < k) || (kj == k && j < (int32_t)lane);
+      }
+      if ((int64_t)lane < len) out[p0 + rank] = k;
     } else {
-      int64_t r = rpos[u];
-      r_list[r] = make_int4(X, in, mg_lookup(mg_rowptr, mg_dst, mg_cnt, X, C), 0);
-      atomicMin(&r_off[x], (int32_t)r);
-      atomicAdd(&r_len[x], 1);
+      for (int64_t i = lane; i < len; i += 32) {
+        const uint32_t k = in[p0 + i];
+        int64_t rank = 0;
+        for (int64_t j = 0; j < len; ++j) {
+          const uint32_t kj = in[p0 + j];
+          rank += (kj < k) || (kj == k && j < i);
+        }
+        out[p0 + rank] = k;
+      }
     }
   }
 }
 
-__global__ void caller_runs_flag(const uint64_t *keys, const int64_t *start, const int64_t *n_runs,
-                                 const int32_t *method_class, int32_t c, int64_t *rflag, int64_t cap) {
-  const int64_t nr = *n_runs;
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < cap; u += (int64_t)gridDim.x * blockDim.x) {
-    if (u >= nr) { rflag[u] = 0; continue; }
-    uint64_t k = keys[start[u]];
-    int32_t x = (int32_t)(k / (uint64_t)c), X = (int32_t)(k % (uint64_t)c);
-    rflag[u] = X != method_class[x] ? 1 : 0;
+// Runs of a sorted segment of use keys (L) or caller classes (R).  For each run
+// of equal classes, `f(class, n0, n1, index among the runs whose class is not
+// C)` is called by one lane; n0/n1 count kind-0/kind-1 keys (R keys are all
+// kind 0: the key is the class itself, so `shift` is 0 there).  Returns the
+// number of runs whose class is not C.
+template <class F>
+__device__ __forceinline__ int32_t segment_runs(const uint32_t *keys, int64_t p0, int64_t len, int shift, int32_t C,
+                                                uint32_t lane, F f) {
+  if (len <= 32) {
+    const bool act = (int64_t)lane < len;
+    const uint32_t k = act ? keys[p0 + lane] : 0xffffffffu;
+    const uint32_t kp = __shfl_up_sync(0xffffffffu, k, 1);
+    const int32_t E = (int32_t)(k >> shift);
+    const bool head = act && (lane == 0 || (kp >> shift) != (k >> shift));
+    const bool acc = act && shift && (k & 1u);
+    const uint32_t heads = __ballot_sync(0xffffffffu, head);
+    const uint32_t accs = __ballot_sync(0xffffffffu, acc);
+    const uint32_t other = __ballot_sync(0xffffffffu, head && E != C);
+    if (head) {
+      const uint32_t above = heads & ~((2u << lane) - 1u);
+      const int32_t end = above ? __ffs(above) - 1 : (int32_t)len;
+      const uint32_t run = (end >= 32 ? 0xffffffffu : ((1u << end) - 1u)) & ~((1u << lane) - 1u);
+      const int32_t n1 = __popc(accs & run), n = end - (int32_t)lane;
+      f(E, n - n1, n1, __popc(other & ((1u << lane) - 1u)));
+    }
+    return __popc(other);
+  }
+  int32_t idx = 0;
+  if (lane == 0) {
+    int64_t i = 0;
+    while (i < len) {
+      const uint32_t E = keys[p0 + i] >> shift;
+      int32_t n0 = 0, n1 = 0;
+      for (; i < len && (keys[p0 + i] >> shift) == E; ++i) ((shift && (keys[p0 + i] & 1u)) ? n1 : n0)++;
+      f((int32_t)E, n0, n1, idx);
+      if ((int32_t)E != C) ++idx;
+    }
+  }
+  return __shfl_sync(0xffffffffu, idx, 0);
+}
+
+// Count pass: l_len / r_len per method and the own-class run (out_self / in_self).
+__global__ void lists_count(const int64_t *a, const int64_t *b, int32_t M, const uint32_t *sorted, int shift,
+                            const int32_t *method_class, int32_t cbo_attrs, int32_t *len_out, int32_t *self_out) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
+    int64_t p0, len;
+    segment(a, b, x, &p0, &len);
+    const int32_t C = method_class[x];
+    int32_t self = 0;
+    const int32_t n = segment_runs(sorted, p0, len, shift, C, lane, [&](int32_t E, int32_t n0, int32_t n1, int32_t) {
+      if (E == C) self = n0 + (cbo_attrs ? n1 : 0);
+    });
+    for (int o = 16; o > 0; o >>= 1) self += __shfl_xor_sync(0xffffffffu, self, o);
+    if (lane == 0) {
+      len_out[x] = n;
+      self_out[x] = self;
+    }
+  }
+}
+
+// Fill pass for list L: {E, out, cnt(C, E), t} at l_off[x] + run index, l_x = x.
+__global__ void lists_fill_l(const int64_t *call_rowptr, const int64_t *acc_rowptr, int32_t M,
+                             const uint32_t *sorted, const int32_t *method_class, int32_t cbo_attrs,
+                             const int64_t *l_off, const int64_t *mg_rowptr, const int32_t *mg_dst,
+                             const int32_t *mg_cnt, int4 *l_list, int32_t *l_x) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
+    int64_t p0, len;
+    segment(call_rowptr, acc_rowptr, x, &p0, &len);
+    const int32_t C = method_class[x];
+    const int64_t base = l_off[x];
+    segment_runs(sorted, p0, len, 1, C, lane, [&](int32_t E, int32_t n0, int32_t n1, int32_t idx) {
+      if (E == C) return;
+      const int32_t out = n0 + (cbo_attrs ? n1 : 0);
+      const int32_t cnt = out > 0 ? mg_lookup(mg_rowptr, mg_dst, mg_cnt, C, E) : 0;
+      l_list[base + idx] = make_int4(E, out, cnt, n1);
+      l_x[base + idx] = (int32_t)x;
+    });
+  }
+}
+
+// Fill pass for list R: {X, in, cnt(X, C), 0} at r_off[x] + run index.
+__global__ void lists_fill_r(const int64_t *rin_off, int32_t M, const uint32_t *sorted,
+                             const int32_t *method_class, const int64_t *r_off, const int64_t *mg_rowptr,
+                             const int32_t *mg_dst, const int32_t *mg_cnt, int4 *r_list) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
+    int64_t p0, len;
+    segment(rin_off, nullptr, x, &p0, &len);
+    const int32_t C = method_class[x];
+    const int64_t base = r_off[x];
+    segment_runs(sorted, p0, len, 0, C, lane, [&](int32_t X, int32_t n0, int32_t, int32_t idx) {
+      if (X == C) return;
+      r_list[base + idx] = make_int4(X, n0, mg_lookup(mg_rowptr, mg_dst, mg_cnt, X, C), 0);
+    });
   }
 }
 
@@ -200,14 +255,14 @@ __device__ __forceinline__ uint32_t enc_sign(int s) { return s < 0 ? 1u : (s > 0
 
 __global__ void build_headers(const int32_t *method_class, const int32_t *cls_n, const int32_t *cls_a,
                               const int64_t *cls_P, const int64_t *cls_Q, const int64_t *cls_S, const int32_t *own,
-                              const int32_t *q, const int32_t *l_off, const int32_t *l_len, const int32_t *r_off,
+                              const int32_t *q, const int64_t *l_off, const int32_t *l_len, const int64_t *r_off,
                               const int32_t *r_len, const int32_t *out_self, const int32_t *in_self,
                               const int4 *l_list, int32_t M, MoveHdr *hdr) {
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
   int32_t C = method_class[x];
-  int32_t ll = l_len[x], lo = ll ? l_off[x] : 0;
-  int32_t rl = r_len[x], ro = rl ? r_off[x] : 0;
+  int32_t ll = l_len[x], lo = ll ? (int32_t)l_off[x] : 0;
+  int32_t rl = r_len[x], ro = rl ? (int32_t)r_off[x] : 0;
   int32_t l_all = 0;
   for (int32_t e = 0; e < ll; ++e) {
     int4 v = l_list[lo + e];
@@ -235,77 +290,63 @@ __global__ void build_headers(const int32_t *method_class, const int32_t *cls_n,
 
 void build_move_precompute(mm_system *s) {
   cudaStream_t st = s->stream;
-  const int32_t c = s->c, M = s->M;
+  const int32_t M = s->M;
   if (M == 0) return;
-  const int64_t nu = s->n_call + s->n_acc;
-  const int64_t nmax = std::max<int64_t>(std::max<int64_t>(nu, s->n_call), 1);
-  // scratch: keys, keys_alt (u64), head, start, flag/pos (i64), per-method temps
-  size_t bytes = sizeof(uint64_t) * 2 * (size_t)nmax + sizeof(int64_t) * 3 * (size_t)nmax +
-                 sizeof(int32_t) * 8 * (size_t)M + sizeof(int64_t) * 4 + 1024;
+  const int64_t nu = s->n_call + s->n_acc, nc = s->n_call;
+  const int64_t nk = std::max<int64_t>(std::max<int64_t>(nu, nc), 1);
+  // scratch: keys, sorted keys (u32); rin_off, l_off, r_off (i64, M + 1); per-method temps
+  size_t bytes = sizeof(uint32_t) * 2 * (size_t)nk + sizeof(int64_t) * 3 * ((size_t)M + 1) +
+                 sizeof(int32_t) * 6 * (size_t)M + 1024;
   char *b = static_cast<char *>(s->eval_ws.need(bytes, st));
-  uint64_t *keys = reinterpret_cast<uint64_t *>(b);
-  uint64_t *keys_alt = keys + nmax;
-  int64_t *head = reinterpret_cast<int64_t *>(keys_alt + nmax);
-  int64_t *start = head + nmax;
-  int64_t *flag = start + nmax;
-  int32_t *out_self = reinterpret_cast<int32_t *>(flag + nmax);
+  uint32_t *keys = reinterpret_cast<uint32_t *>(b);
+  uint32_t *sorted = keys + nk;
+  int64_t *rin_off = reinterpret_cast<int64_t *>((reinterpret_cast<uintptr_t>(sorted + nk) + 15) & ~uintptr_t(15));
+  int64_t *l_off = rin_off + (M + 1);
+  int64_t *r_off = l_off + (M + 1);
+  int32_t *out_self = reinterpret_cast<int32_t *>(r_off + (M + 1));
   int32_t *in_self = out_self + M;
-  int32_t *l_off = in_self + M;
-  int32_t *l_len = l_off + M;
-  int32_t *r_off = l_len + M;
-  int32_t *r_len = r_off + M;
-  int64_t *counters = reinterpret_cast<int64_t *>(r_len + 2 * (size_t)M);  // n_runs, n_l, n_rruns, n_r
-  counters = reinterpret_cast<int64_t *>((reinterpret_cast<uintptr_t>(counters) + 15) & ~uintptr_t(15));
+  int32_t *l_len = in_self + M;
+  int32_t *r_len = l_len + M;
+  int32_t *cursor = r_len + M;
+  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * 32, TPB), 148 * 16);
 
-  MM_CUDA_TRY(cudaMemsetAsync(out_self, 0, sizeof(int32_t) * 2 * (size_t)M, st));
-  MM_CUDA_TRY(cudaMemsetAsync(l_off, 0x7f, sizeof(int32_t) * (size_t)M, st));
-  MM_CUDA_TRY(cudaMemsetAsync(l_len, 0, sizeof(int32_t) * (size_t)M, st));
-  MM_CUDA_TRY(cudaMemsetAsync(r_off, 0x7f, sizeof(int32_t) * (size_t)M, st));
-  MM_CUDA_TRY(cudaMemsetAsync(r_len, 0, sizeof(int32_t) * (size_t)M, st));
-  MM_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(int64_t) * 4, st));
-
-  // list L: runs of (m, E) over m's use keys
+  // list L: per-method sort of the use keys, runs counted, scanned, written
   if (nu > 0) {
-    method_use_keys<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
-                                                 s->acc_idx, s->attr_class, M, c, keys);
+    method_use_keys32<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
+                                                   s->acc_idx, s->attr_class, M, keys);
     MM_LAUNCH_CHECK();
-    uint64_t maxkey = (((uint64_t)M * (uint64_t)c - 1) << 1) | 1u;
-    radix_sort_u64(keys, keys_alt, nullptr, nullptr, nu, bits_for(maxkey), s->sort_ws, st);
-    heads_shifted<<<grid_for(nu), TPB, 0, st>>>(keys, nu, 1, head);
+    segment_sort<<<gw, TPB, 0, st>>>(s->call_rowptr, s->acc_rowptr, M, keys, sorted);
     MM_LAUNCH_CHECK();
-    scan_exclusive_i64(head, head, nu, &counters[0], s->sort_ws, st);
-    starts_shifted<<<grid_for(nu), TPB, 0, st>>>(keys, head, nu, 1, start);
-    MM_LAUNCH_CHECK();
-    use_runs_classify<<<grid_for(nu), TPB, 0, st>>>(keys, start, &counters[0], nu, s->method_class, c, s->cbo_attrs,
-                                                    out_self, flag, nu);
-    MM_LAUNCH_CHECK();
-    scan_exclusive_i64(flag, flag, nu, &counters[1], s->sort_ws, st);
-    use_runs_fill<<<grid_for(nu), TPB, 0, st>>>(keys, start, &counters[0], nu, flag, s->method_class, c,
-                                                s->cbo_attrs, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list,
-                                                s->l_x, l_off, l_len, nu);
-    MM_LAUNCH_CHECK();
+  }
+  lists_count<<<gw, TPB, 0, st>>>(s->call_rowptr, s->acc_rowptr, M, sorted, 1, s->method_class, s->cbo_attrs,
+                                  l_len, out_self);
+  MM_LAUNCH_CHECK();
+  scan_exclusive_i32to64(l_len, l_off, M, s->sort_ws, st, l_off + M);
+  lists_fill_l<<<gw, TPB, 0, st>>>(s->call_rowptr, s->acc_rowptr, M, sorted, s->method_class, s->cbo_attrs, l_off,
+                                   s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list, s->l_x);
+  MM_LAUNCH_CHECK();
+  if (nu > 0) {
     const UnionBitmap ub = union_bitmap(s, nu);
-    l_entries_s<<<ub.grid, 256, ub.smem, st>>>(s->l_list, s->l_x, &counters[1], s->acc_rowptr, s->acc_idx,
+    l_entries_s<<<ub.grid, 256, ub.smem, st>>>(s->l_list, s->l_x, l_off + M, s->acc_rowptr, s->acc_idx,
                                                 s->attr_class, s->own_ptr, s->own_list, ub.words, ub.gbm, s->l_s);
     MM_LAUNCH_CHECK();
   }
-  // list R: runs of (m, X) over the classes of m's callers
-  if (s->n_call > 0) {
-    const int64_t nc = s->n_call;
-    caller_class_keys<<<grid_for(M), TPB, 0, st>>>(s->call_rowptr, s->call_idx, s->method_class, M, c, keys);
+  // list R: callers bucketed by callee (counting sort on fan-in), per-callee sort, runs
+  scan_exclusive_i32to64(s->fan_in, rin_off, M, s->sort_ws, st, rin_off + M);
+  if (nc > 0) {
+    MM_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)M, st));
+    caller_classes_scatter<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, M, rin_off,
+                                                        cursor, keys);
     MM_LAUNCH_CHECK();
-    radix_sort_u64(keys, keys_alt, nullptr, nullptr, nc, bits_for((uint64_t)M * (uint64_t)c - 1), s->sort_ws, st);
-    heads_shifted<<<grid_for(nc), TPB, 0, st>>>(keys, nc, 0, head);
+    segment_sort<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, keys, sorted);
     MM_LAUNCH_CHECK();
-    scan_exclusive_i64(head, head, nc, &counters[2], s->sort_ws, st);
-    starts_shifted<<<grid_for(nc), TPB, 0, st>>>(keys, head, nc, 0, start);
-    MM_LAUNCH_CHECK();
-    caller_runs_flag<<<grid_for(nc), TPB, 0, st>>>(keys, start, &counters[2], s->method_class, c, flag, nc);
-    MM_LAUNCH_CHECK();
-    scan_exclusive_i64(flag, flag, nc, &counters[3], s->sort_ws, st);
-    caller_runs_fill<<<grid_for(nc), TPB, 0, st>>>(keys, start, &counters[2], nc, flag, s->method_class, c,
-                                                   s->mg_rowptr, s->mg_dst, s->mg_cnt, s->r_list, in_self, r_off,
-                                                   r_len, nc);
+  }
+  lists_count<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, sorted, 0, s->method_class, s->cbo_attrs, r_len, in_self);
+  MM_LAUNCH_CHECK();
+  scan_exclusive_i32to64(r_len, r_off, M, s->sort_ws, st);
+  if (nc > 0) {
+    lists_fill_r<<<gw, TPB, 0, st>>>(rin_off, M, sorted, s->method_class, r_off, s->mg_rowptr, s->mg_dst,
+                                     s->mg_cnt, s->r_list);
     MM_LAUNCH_CHECK();
   }
   build_headers<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S,

@@ -302,8 +302,9 @@ void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tot
   scan_exclusive<int64_t, int64_t>(in, out, n, total_dev, ws, st);
 }
 
-void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch &ws, cudaStream_t st) {
-  scan_exclusive<int32_t, int64_t>(in, out, n, nullptr, ws, st);
+void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch &ws, cudaStream_t st,
+                            int64_t *total_dev) {
+  scan_exclusive<int32_t, int64_t>(in, out, n, total_dev, ws, st);
 }
 
 void radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int nbits,
