@@ -593,6 +593,7 @@ struct DenseStage {
   uint4 word[DB_ECAP][DB_WARPS];  // [slot][w] = contribution words w, w+8, w+16, w+24
   uint4 cw[DB_MB][2][DB_WARPS];   // adjacency words of row C: [0] = in_adj (D uses C), [1] = out_adj (C uses D)
   int16_t hit[DB_ECAP];           // slots whose class lies in the block's span
+  uint32_t hitw[DB_MB][DB_SPAN / 32];  // per method: bit rel set iff D0 + rel is in one of its lists
   // source-side outcome of method j for b = [m's callers in C make C start using D]:
   //   pc = improved + (worsened << 16) of class C, fc = sign bits 0-5, rc = record word 1 (dCBO(C) << 16)
   int32_t pc[DB_MB][2], fc[DB_MB][2], rc[DB_MB][2];
@@ -753,6 +754,8 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
         const MoveHdr h = st.hdr[j];
         const int32_t nl = h.w0.z, nr = h.w1.x, C = h.w0.x;
         int32_t nh = 0;
+        st.hitw[j][lane] = 0u;
+        __syncwarp();
         const int32_t hb = st.lb[j];  // the method's hits are stored from its first slot on
         const int32_t items = 4 * (nl + nr);
         for (int32_t i0 = 0; i0 < items; i0 += 32) {
@@ -804,7 +807,10 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
           const int32_t rel = v.x - D0;
           const bool is_hit = ok && c4 == 0 && rel >= 0 && rel < DB_SPAN;
           const uint32_t hm = __ballot_sync(0xffffffffu, is_hit);
-          if (is_hit) st.hit[hb + nh + __popc(hm & ((1u << lane) - 1u))] = (int16_t)slot;
+          if (is_hit) {
+            st.hit[hb + nh + __popc(hm & ((1u << lane) - 1u))] = (int16_t)slot;
+            atomicOr(&st.hitw[j][rel >> 5], 1u << (rel & 31));
+          }
           nh += __popc(hm);
         }
         if (lane == 0) { st.hb[j] = hb; st.hn[j] = nh; }
@@ -863,16 +869,10 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
           }
         }
       }
-      // hits: destinations of this thread that appear in m's lists
+      // hits: destinations of this thread that appear in m's lists (evaluated after the batch)
       uint32_t hitq = 0;
-      {
-        const int32_t hb = st.hb[j], hn = st.hn[j];
-        for (int32_t i = 0; i < hn; ++i) {
-          const int32_t X = st.ent[st.hit[hb + i]].x;
-          const int32_t rel = X - D0 - (int32_t)threadIdx.x;
-          if (rel >= 0 && (rel & (DB_THREADS - 1)) == 0) hitq |= 1u << (rel >> 8);
-        }
-      }
+#pragma unroll
+      for (int q = 0; q < DQ; ++q) hitq |= ((st.hitw[j][warp + 8 * q] >> lane) & 1u) << q;
       const uint4 cin = st.cw[j][0][warp], cout = st.cw[j][1][warp];
       const uint32_t os = h.w1.y > 0 ? 1u : 0u, is = h.w1.z > 0 ? 1u : 0u;
       const int32_t pc0 = st.pc[j][0], pc1 = st.pc[j][1], fc0 = st.fc[j][0], fc1 = st.fc[j][1];
@@ -903,22 +903,32 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
           emit_kept(oc, kk, m, D, r.z >> 16, dck, (int32_t)b - h.w1.w + dD, lane);
         }
       }
-      // exact general path for destinations that appear in m's lists (rare)
-      uint32_t pending = hitq;
-      while (__any_sync(0xffffffffu, pending != 0)) {
-        int q = -1;
-        if (pending) {
-          q = __ffs(pending) - 1;
-          pending &= pending - 1;
+    }
+    // exact general path for the destinations that appear in the lists of the
+    // batch's methods (rare): all threads of the block over the hit bitmaps
+    if (!overflow) {
+      const int32_t nw = k * (DB_SPAN / 32);
+      for (int32_t base = 0; base < nw; base += DB_THREADS) {
+        const int32_t wi = base + (int32_t)threadIdx.x;
+        uint32_t bits = wi < nw ? st.hitw[wi >> 5][wi & 31] : 0u;
+        while (__any_sync(0xffffffffu, bits != 0u)) {
+          const bool have = bits != 0u;
+          const int32_t bpos = have ? __ffs(bits) - 1 : 0;
+          if (have) bits &= bits - 1u;
+          const int32_t j = wi >> 5, rel = (wi & 31) * 32 + bpos;
+          const int32_t D = D0 + rel;
+          const int32_t m = mb + j;
+          const int32_t C = have ? st.hdr[j].w0.x : -1;
+          const bool act = have && D < c && D != C;
+          int32_t dck = 0, dcbo = 0;
+          uint4 r = make_uint4(0, 0, 0, 0);
+          if (act)
+            r = dense_hit_path(cx, st, j, D, rel >> 8, (uint32_t)(rel & 31), (rel & (DB_THREADS - 1)) >> 5, cls_n,
+                               cls_a, cls_P, cls_Q, cls_S, &dck, &dcbo);
+          if (REC && act) __stcs(oc.records + (int64_t)m * row + D - (D > C ? 1 : 0), r);
+          if (DIG && act) dig += record_hash(m, D, r);
+          if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
         }
-        const int32_t D = D0 + (int32_t)threadIdx.x + (q < 0 ? 0 : q) * DB_THREADS;
-        const bool act = q >= 0 && D < c && D != C;
-        int32_t dck = 0, dcbo = 0;
-        uint4 r = make_uint4(0, 0, 0, 0);
-        if (act) r = dense_hit_path(cx, st, j, D, q, lane, warp, cls_n, cls_a, cls_P, cls_Q, cls_S, &dck, &dcbo);
-        if (REC && act) __stcs(oc.records + rowbase + D - (D > C ? 1 : 0), r);
-        if (DIG && act) dig += record_hash(m, D, r);
-        if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
       }
     }
     mb += k;

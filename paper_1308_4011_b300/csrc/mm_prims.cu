@@ -107,7 +107,7 @@ __global__ void scan_tiles_kernel(const Tin *in, Tout *out, int64_t n, const Tou
 constexpr int SCAN1_THREADS = 1024;
 constexpr int SCAN1_ROWS = 16;
 constexpr int SCAN1_CHUNK = SCAN1_THREADS * SCAN1_ROWS;
-constexpr int64_t SCAN1_MAX = 1 << 16;
+constexpr int64_t SCAN1_MAX = SCAN1_CHUNK;  // one chunk; larger inputs use the three-kernel scan
 
 template <class Tin, class Tout>
 __global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(const Tin *in, Tout *out, int64_t n,
