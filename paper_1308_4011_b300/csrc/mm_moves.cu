@@ -877,28 +877,46 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
       const uint32_t os = h.w1.y > 0 ? 1u : 0u, is = h.w1.z > 0 ? 1u : 0u;
       const int32_t pc0 = st.pc[j][0], pc1 = st.pc[j][1], fc0 = st.fc[j][0], fc1 = st.fc[j][1];
       const int32_t rc0 = st.rc[j][0], rc1 = st.rc[j][1];
-#pragma unroll
-      for (int q = 0; q < DQ; ++q) {
-        const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
-        const bool act = D < c && D != C && !((hitq >> q) & 1u);
-        // common path: m shares nothing with D and D is in neither of m's lists
+      // common path: m shares nothing with D and D is in neither of m's lists
+      auto common = [&](int q, uint4 &r, bool &kept, int32_t &dD, uint32_t &b) {
         const uint32_t bDC = (sel4(cin, q) >> lane) & 1u, bCD = (sel4(cout, q) >> lane) & 1u;
-        const uint32_t b = is & (bCD ^ 1u);                          // C starts using D
-        const int32_t dD = (int32_t)(gain[q] + (os & (bDC ^ 1u)));   // >= 0 on this path
+        b = is & (bCD ^ 1u);                                  // C starts using D
+        dD = (int32_t)(gain[q] + (os & (bDC ^ 1u)));          // >= 0 on this path
         const bool p = dD != 0;
         const int32_t P = (b ? pc1 : pc0) + (p ? pd1[q] : pd0[q]) + (int32_t)iw[q];
-        const bool kept = (P >> 16) == 0 && (P & 0xffff) >= cx.min_improved;
+        kept = (P >> 16) == 0 && (P & 0xffff) >= cx.min_improved;
         const uint32_t flags = (uint32_t)(b ? fc1 : fc0) | (uint32_t)fd0[q] | (p ? (2u << 10) : 0u) |
                                (kept ? 0x8000u : 0u);
-        uint4 r;
         r.x = 0u;
         r.y = (uint32_t)(b ? rc1 : rc0);
         r.z = (uint32_t)dD | ((uint32_t)P << 16);
         r.w = ((uint32_t)P >> 16) | (flags << 16);
+      };
+      uint32_t keptq = 0;
+#pragma unroll
+      for (int q = 0; q < DQ; ++q) {
+        const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
+        const bool act = D < c && D != C && !((hitq >> q) & 1u);
+        uint4 r;
+        bool kept;
+        int32_t dD;
+        uint32_t b;
+        common(q, r, kept, dD, b);
         if (REC && act) __stcs(oc.records + rowbase + D - (D > C ? 1 : 0), r);
         if (DIG && act) dig += record_hash(m, D, r);
-        if (KEEP) {
-          const bool kk = act && kept;
+        keptq |= (uint32_t)(act && kept) << q;
+      }
+      // kept moves are rare: one vote per method, the compaction only when a lane has one
+      if (KEEP && __any_sync(0xffffffffu, keptq != 0u)) {
+#pragma unroll
+        for (int q = 0; q < DQ; ++q) {
+          const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
+          uint4 r;
+          bool kept;
+          int32_t dD;
+          uint32_t b;
+          common(q, r, kept, dD, b);
+          const bool kk = (keptq >> q) & 1u;
           const int32_t dck = kk ? h.w2.y + dck0[q] : 0;
           emit_kept(oc, kk, m, D, r.z >> 16, dck, (int32_t)b - h.w1.w + dD, lane);
         }
