@@ -64,9 +64,11 @@ __global__ void own_access_fill(const int32_t *method_class, const int32_t *meth
 }
 
 // LCOM pair counts: q_x = methods of x's class sharing an own attribute with x
-// = |union of the accessors of x's own attributes| - 1 (x itself), and
-// sum_x q_x = 2 Q_C.  One warp per method; bitmap words per warp in shared
-// memory, or in a zeroed global slice when the largest class is too big.
+// = |union of the accessor lists of x's own attributes| - 1 (x itself), and
+// sum_x q_x = 2 Q_C.  One thread per method: with one own attribute the union
+// is its accessor list; methods with two or more are taken by the whole warp
+// in turn, with bitmap words per warp in shared memory, or in a zeroed global
+// slice when the largest class is too big.
 __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, const int64_t *acc_rowptr,
                                                   const int32_t *acc_idx, const int32_t *attr_class,
                                                   const int64_t *own_ptr, const int32_t *own_list,
@@ -78,19 +80,36 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
   if (!gbm)
     for (int32_t i = (int32_t)lane; i < words; i += 32) bm[i] = 0u;
   __syncwarp();
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
-    if (own[x] == 0) {
-      if (lane == 0) q[x] = 0;
-      continue;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < M; base += stride) {
+    const int64_t x = base + threadIdx.x;
+    const int32_t ox = x < M ? own[x] : 0;
+    const int32_t C = x < M ? method_class[x] : 0;
+    int32_t u = 0;
+    if (ox == 1) {
+      for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
+        const int32_t al = acc_idx[e];
+        if (attr_class[al] == C) {
+          u = (int32_t)(own_ptr[al + 1] - own_ptr[al]);
+          break;
+        }
+      }
     }
-    const int32_t C = method_class[x];
-    const int64_t a0 = acc_rowptr[x];
-    const int32_t u = accessor_union(acc_idx + a0, acc_rowptr[x + 1] - a0, C, attr_class, own_ptr, own_list, bm,
-                                     lane);
-    if (lane == 0) {
-      q[x] = u - 1;
-      if (u > 1) atomicAdd(reinterpret_cast<unsigned long long *>(&cls_Q[C]), (unsigned long long)(u - 1));
+    uint32_t multi = __ballot_sync(0xffffffffu, ox >= 2);
+    while (multi) {
+      const int src = __ffs(multi) - 1;
+      multi &= multi - 1u;
+      const int64_t xs = base + (threadIdx.x & ~31u) + src;  // method of lane src
+      const int32_t Cs = __shfl_sync(0xffffffffu, C, src);
+      const int64_t a0 = acc_rowptr[xs];
+      const int32_t v = accessor_union(acc_idx + a0, acc_rowptr[xs + 1] - a0, Cs, attr_class, own_ptr, own_list,
+                                       bm, lane);
+      if ((int)lane == src) u = v;
+    }
+    if (x < M) {
+      const int32_t qx = u > 0 ? u - 1 : 0;
+      q[x] = qx;
+      if (qx) atomicAdd(reinterpret_cast<unsigned long long *>(&cls_Q[C]), (unsigned long long)qx);
     }
   }
 }
@@ -319,7 +338,7 @@ void build_metrics(mm_system *s) {
                                                   s->attr_class, M, s->own_ptr, cursor, s->own_list);
     MM_LAUNCH_CHECK();
     // LCOM pair counts from accessor unions
-    const UnionBitmap ub = union_bitmap(s, M);
+    const UnionBitmap ub = union_bitmap(s, ceil_div(M, 32));
     lcom_union<<<ub.grid, 256, ub.smem, st>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class,
                                                s->own_ptr, s->own_list, s->own, M, ub.words, ub.gbm, s->q,
                                                s->cls_Q);

@@ -50,7 +50,9 @@ __device__ __forceinline__ int32_t mg_lookup(const int64_t *rowptr, const int32_
 
 // s for list-L entries with t > 0: the methods of D sharing an attribute of D
 // with m = the union of the accessor lists of m's accesses into D (m is not in
-// D).  One warp per entry, bitmap over D's method ranks as in the LCOM counts.
+// D).  One thread per entry: with t = 1 the union is the one accessor list, so
+// s is its length; entries with t >= 2 are taken by the whole warp in turn
+// (bitmap over D's method ranks, as in the LCOM counts).
 __global__ void __launch_bounds__(256) l_entries_s(const int4 *l_list, const int32_t *l_x, const int64_t *n_l,
                                                    const int64_t *acc_rowptr, const int32_t *acc_idx,
                                                    const int32_t *attr_class, const int64_t *own_ptr,
@@ -62,17 +64,37 @@ __global__ void __launch_bounds__(256) l_entries_s(const int4 *l_list, const int
   if (!gbm)
     for (int32_t i = (int32_t)lane; i < words; i += 32) bm[i] = 0u;
   __syncwarp();
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t nl = *n_l;
-  for (int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < nl; l += nwarps) {
-    const int4 v = l_list[l];
-    int32_t sv = 0;
-    if (v.w > 0) {
-      const int32_t x = l_x[l];
-      const int64_t a0 = acc_rowptr[x];
-      sv = accessor_union(acc_idx + a0, acc_rowptr[x + 1] - a0, v.x, attr_class, own_ptr, own_list, bm, lane);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nl; base += stride) {
+    const int64_t l = base + threadIdx.x;
+    int4 v = make_int4(0, 0, 0, 0);
+    int32_t x = 0;
+    if (l < nl) {
+      v = l_list[l];
+      x = l_x[l];
     }
-    if (lane == 0) l_s[l] = sv;
+    int32_t sv = 0;
+    if (v.w == 1) {
+      for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
+        const int32_t al = acc_idx[e];
+        if (attr_class[al] == v.x) {
+          sv = (int32_t)(own_ptr[al + 1] - own_ptr[al]);
+          break;
+        }
+      }
+    }
+    uint32_t multi = __ballot_sync(0xffffffffu, v.w >= 2);
+    while (multi) {
+      const int src = __ffs(multi) - 1;
+      multi &= multi - 1u;
+      const int32_t xs = __shfl_sync(0xffffffffu, x, src), Ds = __shfl_sync(0xffffffffu, v.x, src);
+      const int64_t a0 = acc_rowptr[xs];
+      const int32_t u = accessor_union(acc_idx + a0, acc_rowptr[xs + 1] - a0, Ds, attr_class, own_ptr, own_list,
+                                       bm, lane);
+      if ((int)lane == src) sv = u;
+    }
+    if (l < nl) l_s[l] = sv;
   }
 }
 
@@ -326,7 +348,7 @@ void build_move_precompute(mm_system *s) {
                                    s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list, s->l_x);
   MM_LAUNCH_CHECK();
   if (nu > 0) {
-    const UnionBitmap ub = union_bitmap(s, nu);
+    const UnionBitmap ub = union_bitmap(s, ceil_div(nu, 32));
     l_entries_s<<<ub.grid, 256, ub.smem, st>>>(s->l_list, s->l_x, l_off + M, s->acc_rowptr, s->acc_idx,
                                                 s->attr_class, s->own_ptr, s->own_list, ub.words, ub.gbm, s->l_s);
     MM_LAUNCH_CHECK();
@@ -1298,31 +1320,70 @@ int64_t grouped_resident_grid() {
   return v;
 }
 
-// Candidate lists: range / self / row-pointer checks, one warp per method row
-// (coalesced), and a content hash of the lists (every (index, destination) and
-// every row end), which keys the cached kept moves of a list evaluation.
-__global__ void validate_candidates(const int64_t *rowptr, const int32_t *dst, const int32_t *method_class,
-                                    int32_t M, int32_t c, int64_t n_cand, uint32_t *err,
-                                    unsigned long long *hash) {
+// Candidate lists: row-pointer checks (thread per method) and range / self
+// checks streamed over the destinations (a warp per 256 consecutive entries,
+// each lane finding its method by a forward scan from the chunk's first
+// method), plus a content hash of the lists (every (index, destination) and
+// every row end) that keys the cached kept moves of a list evaluation.
+__device__ __forceinline__ uint64_t cand_mix(uint64_t v) {
+  v *= 0x9E3779B97F4A7C15ULL;
+  return v ^ (v >> 31);
+}
+
+__global__ void validate_cand_rows(const int64_t *rowptr, int32_t M, int64_t n_cand, uint32_t *err,
+                                   unsigned long long *hash) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t e = 0;
+  uint64_t h = 0;
+  if (x < M) {
+    const int64_t a = rowptr[x], b = rowptr[x + 1];
+    if (x == 0 && (a != 0 || rowptr[M] != n_cand)) e |= VE_CAND_ROWPTR;
+    if (a < 0 || b < a || b > n_cand) e |= VE_CAND_ROWPTR;
+    h = cand_mix((uint64_t)b ^ ((uint64_t)x << 40) ^ 0x6a09e667f3bcc909ULL);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    e |= __shfl_xor_sync(0xffffffffu, e, o);
+    h += __shfl_xor_sync(0xffffffffu, h, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (e) atomicOr(err, e);
+    if (h) atomicAdd(hash, (unsigned long long)h);
+  }
+}
+
+// first method whose row ends after entry i (rows are only trusted to be
+// in bounds here; a bad row pointer is reported by validate_cand_rows)
+__device__ __forceinline__ int32_t owner_of(const int64_t *rowptr, int32_t M, int64_t i) {
+  int32_t lo = 0, hi = M;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (rowptr[mid + 1] <= i) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void validate_cand_dst(const int64_t *rowptr, const int32_t *dst, const int32_t *method_class,
+                                  int32_t M, int32_t c, int64_t n_cand, uint32_t *err,
+                                  unsigned long long *hash) {
   const uint32_t lane = threadIdx.x & 31u;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   uint32_t e = 0;
   uint64_t h = 0;
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
-    const int64_t a = rowptr[x], b = rowptr[x + 1];
-    if (x == 0 && (a != 0 || rowptr[M] != n_cand)) e |= VE_CAND_ROWPTR;
-    if (a < 0 || b < a || b > n_cand) {
-      e |= VE_CAND_ROWPTR;
-      continue;
+  for (int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 256; i0 < n_cand;
+       i0 += nwarps * 256) {
+    int32_t m = owner_of(rowptr, M, i0);
+    for (int64_t k = 0; k < 256; k += 32) {
+      const int64_t i = i0 + k + lane;
+      int32_t mi = m;
+      if (i < n_cand) {
+        while (mi < M && rowptr[mi + 1] <= i) ++mi;
+        const int32_t D = dst[i];
+        if (D < 0 || D >= c) e |= VE_CAND_RANGE;
+        else if (mi < M && D == method_class[mi]) e |= VE_CAND_SELF;
+        h += cand_mix(((uint64_t)i << 32) | (uint32_t)D);
+      }
+      m = __shfl_sync(0xffffffffu, mi, 31);
     }
-    const int32_t C = method_class[x];
-    for (int64_t i = a + lane; i < b; i += 32) {
-      const int32_t D = dst[i];
-      if (D < 0 || D >= c) e |= VE_CAND_RANGE;
-      else if (D == C) e |= VE_CAND_SELF;
-      h += smix(((uint64_t)i << 32) ^ (uint32_t)D);
-    }
-    if (lane == 0) h += smix(0x6a09e667f3bcc909ULL ^ (uint64_t)b ^ ((uint64_t)x << 40));
   }
   for (int o = 16; o > 0; o >>= 1) {
     e |= __shfl_xor_sync(0xffffffffu, e, o);
@@ -1514,10 +1575,14 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
   MM_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(uint32_t), st));
   MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 3, 0, sizeof(unsigned long long), st));
   if (s->M > 0) {
-    const unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)s->M * 32, TPB), 148 * 16);
-    validate_candidates<<<g, TPB, 0, st>>>(*rowptr, *dst, s->method_class, s->M, s->c, *n_cand, s->d_err,
-                                           s->d_u64 + 3);
+    validate_cand_rows<<<grid_for(s->M), TPB, 0, st>>>(*rowptr, s->M, *n_cand, s->d_err, s->d_u64 + 3);
     MM_LAUNCH_CHECK();
+    if (*n_cand > 0) {
+      const unsigned g = (unsigned)std::min<int64_t>(ceil_div(ceil_div(*n_cand, 256) * 32, TPB), 148 * 16);
+      validate_cand_dst<<<g, TPB, 0, st>>>(*rowptr, *dst, s->method_class, s->M, s->c, *n_cand, s->d_err,
+                                          s->d_u64 + 3);
+      MM_LAUNCH_CHECK();
+    }
   }
   uint32_t err = 0;
   MM_CUDA_TRY(cudaMemcpyAsync(&err, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
