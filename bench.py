@@ -40,6 +40,11 @@ UNIT = "candidates/s"
 WORKLOAD = "medium synthetic system: 5,000 classes, 60,000 methods, 30,000 attributes, seed 1; full cross product"
 TOPK = 100
 L2_FLUSH_BYTES = 512 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant
+# kernel, from the ncu captures summarised in profiles/ (set to None when the
+# kernel changes until it is captured again)
+EVAL_DENSE_TRAFFIC = 4781826560      # medium, eval_dense<records, kept>
+EVAL_CSR_TRAFFIC = 858472704         # large restricted, eval_csr_grouped<records, kept>
 
 
 def _env_int(k, d):
@@ -234,8 +239,10 @@ def run_ours(args, rank, world, local_rank):
     eval_s = statistics.median(eval_ms) / 1e3
     alg_bytes = 16 * n_cand
     achieved = alg_bytes / eval_s / 1e9
+    # DRAM bytes of one medium eval_dense launch (ncu one-pass capture, profiles/eval_dense_small_case.md)
+    traffic = EVAL_DENSE_TRAFFIC if args.case == "medium" else None
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4), "traffic": traffic,
             "kernel": "eval_dense<records>", "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
             "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(eval_s * 1e3, 4)}
     cpu = cpu_baseline(system, mask, min_imp) if (rank == 0 and not args.no_cpu_baseline) else None
@@ -432,7 +439,8 @@ def run_large(args, rank, world, local_rank):
                        "candidates_per_step": n_cand, "criteria": {"metric_mask": mask, "min_improved": min_imp},
                        "topk": TOPK, "l2": "512 MB L2 flush between steps (outside events)"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": "eval_csr_grouped<records>",
+                         "frac": round(achieved / peak, 4), "traffic": EVAL_CSR_TRAFFIC,
+                         "kernel": "eval_csr_grouped<records>",
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(eval_s * 1e3, 4)},
             "eval_value": n_cand / eval_s, "eval_ms_median": statistics.median(eval_ms),
