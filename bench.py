@@ -41,8 +41,8 @@ WORKLOAD = "medium synthetic system: 5,000 classes, 60,000 methods, 30,000 attri
 TOPK = 100
 L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant
-# kernel, from the ncu captures summarised in profiles/ (set to None when the
-# kernel changes until it is captured again)
+# kernel on the same workload, from a one-pass ncu capture (set to None when the
+# kernel changes, until it is captured again)
 EVAL_DENSE_TRAFFIC = 4781826560      # medium, eval_dense<records, kept>
 EVAL_CSR_TRAFFIC = 858472704         # large restricted, eval_csr_grouped<records, kept>
 
@@ -239,7 +239,7 @@ def run_ours(args, rank, world, local_rank):
     eval_s = statistics.median(eval_ms) / 1e3
     alg_bytes = 16 * n_cand
     achieved = alg_bytes / eval_s / 1e9
-    # DRAM bytes of one medium eval_dense launch (ncu one-pass capture, profiles/eval_dense_small_case.md)
+    # DRAM bytes of one medium eval_dense launch (ncu one-pass capture)
     traffic = EVAL_DENSE_TRAFFIC if args.case == "medium" else None
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
