@@ -45,7 +45,7 @@ struct mm_batch {
   // graphs of (metrics of every system + batched evaluation + per-system sort),
   // without [0] and with [1] the record digests
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  std::vector<std::tuple<void *, void *>> scratch_at_capture;  // (sort_ws, eval_ws) of each system
+  std::vector<std::vector<void *>> scratch_at_capture;  // scratch buffers of each system at capture
   bool ran = false;
 };
 
@@ -141,13 +141,18 @@ void enqueue_metrics(mm_batch *b) {
   }
 }
 
-// The metric pipeline uses only the systems' sort and eval scratch buffers.
+// The scratch buffers the metric pipeline uses (their addresses are baked into
+// a captured graph).
+std::vector<void *> pipeline_scratch(const mm_system *s) {
+  return {s->sort_ws.ptr,      s->eval_ws.ptr,      s->union_ws.ptr,     s->side_eval[0].ptr,
+          s->side_eval[1].ptr, s->side_sort[0].ptr, s->side_sort[1].ptr, s->side_union[0].ptr,
+          s->side_union[1].ptr};
+}
+
 bool scratch_moved(const mm_batch *b) {
   if (b->scratch_at_capture.size() != b->sys.size()) return true;
-  for (size_t i = 0; i < b->sys.size(); ++i) {
-    const mm_system *s = b->sys[i];
-    if (b->scratch_at_capture[i] != std::make_tuple(s->sort_ws.ptr, s->eval_ws.ptr)) return true;
-  }
+  for (size_t i = 0; i < b->sys.size(); ++i)
+    if (b->scratch_at_capture[i] != pipeline_scratch(b->sys[i])) return true;
   return false;
 }
 
@@ -180,7 +185,7 @@ void capture(mm_batch *b, bool digest) {
   cudaGraphDestroy(g);
   MM_CUDA_TRY(e);
   b->scratch_at_capture.clear();
-  for (auto *s : b->sys) b->scratch_at_capture.emplace_back(s->sort_ws.ptr, s->eval_ws.ptr);
+  for (auto *s : b->sys) b->scratch_at_capture.push_back(pipeline_scratch(s));
 }
 
 }  // namespace

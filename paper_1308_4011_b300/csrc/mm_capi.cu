@@ -45,6 +45,19 @@ void use_device(mm_system *s) {
   if (cur != s->device) MM_CUDA_TRY(cudaSetDevice(s->device));
 }
 
+// Free everything a system holds: device memory in stream order on its stream,
+// then its events (released by the runtime once their last use completes).
+void release_system(mm_system *s) {
+  s->arena.release();
+  for (Scratch *w : {&s->sort_ws, &s->eval_ws, &s->stage_ws, &s->kept_ws, &s->edit_ws, &s->union_ws,
+                     &s->side_eval[0], &s->side_eval[1], &s->side_sort[0], &s->side_sort[1], &s->side_union[0],
+                     &s->side_union[1]})
+    w->release(s->stream);
+  for (cudaEvent_t e : {s->fork_ev, s->join_ev[0], s->join_ev[1]})
+    if (e) cudaEventDestroy(e);
+  delete s;
+}
+
 void keep_pool_memory(int device) {
   static bool done[64] = {false};
   if (device < 0 || device >= 64 || done[device]) return;
@@ -191,6 +204,9 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     keep_pool_memory(s->device);
     s->stream = static_cast<cudaStream_t>(cuda_stream);
     s->arena.stream = s->stream;
+    MM_CUDA_TRY(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
+    MM_CUDA_TRY(cudaEventCreateWithFlags(&s->join_ev[0], cudaEventDisableTiming));
+    MM_CUDA_TRY(cudaEventCreateWithFlags(&s->join_ev[1], cudaEventDisableTiming));
     s->c = desc->n_classes;
     s->M = desc->n_methods;
     s->A = desc->n_attrs;
@@ -232,13 +248,7 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     *out = s;
   });
   if (st != MM_OK && s) {
-    s->arena.release();
-    s->sort_ws.release(s->stream);
-    s->eval_ws.release(s->stream);
-    s->stage_ws.release(s->stream);
-    s->kept_ws.release(s->stream);
-    cudaStreamSynchronize(s->stream);
-    delete s;
+    release_system(s);
     if (out) *out = nullptr;
   }
   return st;
@@ -316,7 +326,9 @@ mm_status mm_system_info_get(mm_system *s, mm_system_info *info) {
     }
     info->device_bytes =
         s->arena.bytes + (int64_t)(s->sort_ws.cap + s->eval_ws.cap + s->stage_ws.cap + s->kept_ws.cap +
-                                   s->edit_ws.cap + s->union_ws.cap);
+                                   s->edit_ws.cap + s->union_ws.cap + s->side_eval[0].cap + s->side_eval[1].cap +
+                                   s->side_sort[0].cap + s->side_sort[1].cap + s->side_union[0].cap +
+                                   s->side_union[1].cap);
   });
 }
 
@@ -326,14 +338,7 @@ void mm_free_system(mm_system *s) {
   const int dev = s->device;
   cudaGetDevice(&cur);
   if (cur != dev) cudaSetDevice(dev);
-  s->arena.release();
-  s->sort_ws.release(s->stream);
-  s->eval_ws.release(s->stream);
-  s->stage_ws.release(s->stream);
-  s->kept_ws.release(s->stream);
-  s->edit_ws.release(s->stream);
-  s->union_ws.release(s->stream);
-  delete s;
+  release_system(s);
   if (cur >= 0 && cur != dev) cudaSetDevice(cur);
 }
 

@@ -134,6 +134,11 @@ struct mm_system {
   Scratch kept_ws;     // kept moves + per-method marks of the last evaluation
   Scratch edit_ws;     // edit patches and incremental re-evaluation
   Scratch union_ws;    // per-warp bitmaps of accessor unions (largest classes only)
+  // independent branches of the metric pipeline run on side streams, each with
+  // its own scratch: [0] LCOM (own-access index, pair counts), [1] list L
+  Scratch side_eval[2], side_sort[2], side_union[2];
+  cudaEvent_t fork_ev = nullptr, join_ev[2] = {nullptr, nullptr};
+  cudaStream_t side_pending[2] = {nullptr, nullptr};  // stream a branch was issued on
   bool kept_valid = false;   // kept_ws holds the kept moves of the last evaluation for:
   uint32_t kept_mask = 0;    //   this metric mask
   int32_t kept_min = 0;      //   and this min_improved
@@ -223,7 +228,15 @@ struct UnionBitmap {
   uint32_t *gbm;
   unsigned grid;
 };
-UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted);
+UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted, Scratch &ws, cudaStream_t st);
+// Side streams of the calling thread on the current device (created on first
+// use).  fork_side() returns the stream a branch runs on: side stream i, made
+// to wait for the work so far on s->stream, or s->stream itself when the
+// stream is being captured into a graph (the batch's graph already runs the
+// systems as parallel branches) or the system has no events.
+cudaStream_t fork_side(mm_system *s, int i);
+// Make s->stream wait for branch i (no-op when the branch ran on s->stream).
+void join_side(mm_system *s, int i, cudaStream_t branch);
 // Number of distinct methods of class K that access at least one of the
 // attributes of K in acc_row[0 .. len): the union of their accessor lists,
 // counted in a per-warp bitmap over K's method ranks.  The accessor elements

@@ -296,7 +296,7 @@ __global__ void destination_records(const int32_t *cls_n, const int32_t *cls_a, 
 
 }  // namespace
 
-UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted) {
+UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted, Scratch &ws, cudaStream_t st) {
   UnionBitmap ub;
   ub.words = (int32_t)std::max<int64_t>(1, ceil_div(std::max(s->summary.max_class_methods, 1), 32));
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps_wanted, 8), 148 * 8));
@@ -308,44 +308,82 @@ UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted) {
   } else {
     ub.smem = 0;
     const size_t bytes = per_block * (size_t)blocks;
-    ub.gbm = static_cast<uint32_t *>(s->union_ws.need(bytes, s->stream));
-    MM_CUDA_TRY(cudaMemsetAsync(ub.gbm, 0, bytes, s->stream));
+    ub.gbm = static_cast<uint32_t *>(ws.need(bytes, st));
+    MM_CUDA_TRY(cudaMemsetAsync(ub.gbm, 0, bytes, st));
   }
   return ub;
+}
+
+namespace {
+struct SideStreams {
+  int device = -1;
+  cudaStream_t s[2] = {nullptr, nullptr};
+};
+thread_local SideStreams tl_side[8];
+}  // namespace
+
+cudaStream_t fork_side(mm_system *s, int i) {
+  if (!s->fork_ev || s->device < 0 || s->device >= 8) return s->stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  MM_CUDA_TRY(cudaStreamIsCapturing(s->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return s->stream;
+  SideStreams &ss = tl_side[s->device];
+  if (!ss.s[i]) MM_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s[i], cudaStreamNonBlocking));
+  MM_CUDA_TRY(cudaEventRecord(s->fork_ev, s->stream));
+  MM_CUDA_TRY(cudaStreamWaitEvent(ss.s[i], s->fork_ev, 0));
+  return ss.s[i];
+}
+
+void join_side(mm_system *s, int i, cudaStream_t branch) {
+  if (branch == s->stream) return;
+  MM_CUDA_TRY(cudaEventRecord(s->join_ev[i], branch));
+  MM_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->join_ev[i], 0));
 }
 
 void build_metrics(mm_system *s) {
   cudaStream_t st = s->stream;
   const int32_t c = s->c, M = s->M;
 
-  // inverted index of own accesses, own, S
-  const int64_t A = s->A;
-  int64_t *acnt = static_cast<int64_t *>(s->eval_ws.need(sizeof(int64_t) * ((size_t)A + 1), st));
-  MM_CUDA_TRY(cudaMemsetAsync(acnt, 0, sizeof(int64_t) * ((size_t)A + 1), st));
-  MM_CUDA_TRY(cudaMemsetAsync(s->cls_S, 0, sizeof(int64_t) * (size_t)c, st));
-  MM_CUDA_TRY(cudaMemsetAsync(s->cls_Q, 0, sizeof(int64_t) * (size_t)c, st));
-  MM_CUDA_TRY(cudaMemsetAsync(s->q, 0, sizeof(int32_t) * (size_t)std::max(M, 1), st));
-  if (M > 0) {
-    own_access_count<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class, M,
-                                                   acnt, s->own, s->cls_S);
+  // branch A (side stream 0): inverted index of own accesses, own, S, LCOM pair
+  // counts, P and Q, destination records; branch B (below, on the system's
+  // stream): coupling and the adjacency structures.  They share no buffer.
+  {
+    cudaStream_t sa = fork_side(s, 0);
+    Scratch &ev = s->side_eval[0];  // own scratch whether or not the branch runs concurrently
+    Scratch &sw_ = s->side_sort[0];
+    Scratch &uw = s->side_union[0];
+    const int64_t A = s->A;
+    int64_t *acnt = static_cast<int64_t *>(ev.need(sizeof(int64_t) * ((size_t)A + 1), sa));
+    MM_CUDA_TRY(cudaMemsetAsync(acnt, 0, sizeof(int64_t) * ((size_t)A + 1), sa));
+    MM_CUDA_TRY(cudaMemsetAsync(s->cls_S, 0, sizeof(int64_t) * (size_t)c, sa));
+    MM_CUDA_TRY(cudaMemsetAsync(s->cls_Q, 0, sizeof(int64_t) * (size_t)c, sa));
+    MM_CUDA_TRY(cudaMemsetAsync(s->q, 0, sizeof(int32_t) * (size_t)std::max(M, 1), sa));
+    if (M > 0) {
+      own_access_count<<<grid_for(M), TPB, 0, sa>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class, M,
+                                                     acnt, s->own, s->cls_S);
+      MM_LAUNCH_CHECK();
+    }
+    scan_exclusive_i64(acnt, s->own_ptr, A, s->own_ptr + A, sw_, sa);
+    if (M > 0 && A > 0) {
+      int32_t *cursor = reinterpret_cast<int32_t *>(acnt);  // counts are consumed: reuse as cursors
+      MM_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)A, sa));
+      own_access_fill<<<grid_for(M), TPB, 0, sa>>>(s->method_class, s->method_local, s->acc_rowptr, s->acc_idx,
+                                                    s->attr_class, M, s->own_ptr, cursor, s->own_list);
+      MM_LAUNCH_CHECK();
+      // LCOM pair counts from accessor unions
+      const UnionBitmap ub = union_bitmap(s, ceil_div(M, 32), uw, sa);
+      lcom_union<<<ub.grid, 256, ub.smem, sa>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class,
+                                                 s->own_ptr, s->own_list, s->own, M, ub.words, ub.gbm, s->q,
+                                                 s->cls_Q);
+      MM_LAUNCH_CHECK();
+    }
+    finalize_classes<<<grid_for(c), TPB, 0, sa>>>(s->cls_n, s->cls_Q, c, s->cls_P);
     MM_LAUNCH_CHECK();
+    destination_records<<<grid_for(c), TPB, 0, sa>>>(s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, c,
+                                                     s->dest_rec);
+    MM_LAUNCH_CHECK();
+    s->side_pending[0] = sa;
   }
-  scan_exclusive_i64(acnt, s->own_ptr, A, s->own_ptr + A, s->sort_ws, st);
-  if (M > 0 && A > 0) {
-    int32_t *cursor = reinterpret_cast<int32_t *>(acnt);  // counts are consumed: reuse as cursors
-    MM_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)A, st));
-    own_access_fill<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->method_local, s->acc_rowptr, s->acc_idx,
-                                                  s->attr_class, M, s->own_ptr, cursor, s->own_list);
-    MM_LAUNCH_CHECK();
-    // LCOM pair counts from accessor unions
-    const UnionBitmap ub = union_bitmap(s, ceil_div(M, 32));
-    lcom_union<<<ub.grid, 256, ub.smem, st>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class,
-                                               s->own_ptr, s->own_list, s->own, M, ub.words, ub.gbm, s->q,
-                                               s->cls_Q);
-    MM_LAUNCH_CHECK();
-  }
-  finalize_classes<<<grid_for(c), TPB, 0, st>>>(s->cls_n, s->cls_Q, c, s->cls_P);
-  MM_LAUNCH_CHECK();
 
   // coupling: mark the use edges in the out-rows, count and enumerate the
   // marked classes row by row (ascending, so no sort), then count multiplicities
@@ -389,7 +427,5 @@ void build_metrics(mm_system *s) {
                                     s->cpk);
     MM_LAUNCH_CHECK();
   }
-  destination_records<<<grid_for(c), TPB, 0, st>>>(s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, c,
-                                                   s->dest_rec);
-  MM_LAUNCH_CHECK();
+  join_side(s, 0, s->side_pending[0]);
 }

@@ -315,62 +315,77 @@ void build_move_precompute(mm_system *s) {
   const int32_t M = s->M;
   if (M == 0) return;
   const int64_t nu = s->n_call + s->n_acc, nc = s->n_call;
-  const int64_t nk = std::max<int64_t>(std::max<int64_t>(nu, nc), 1);
-  // scratch: keys, sorted keys (u32); rin_off, l_off, r_off (i64, M + 1); per-method temps
-  size_t bytes = sizeof(uint32_t) * 2 * (size_t)nk + sizeof(int64_t) * 3 * ((size_t)M + 1) +
-                 sizeof(int32_t) * 6 * (size_t)M + 1024;
-  char *b = static_cast<char *>(s->eval_ws.need(bytes, st));
-  uint32_t *keys = reinterpret_cast<uint32_t *>(b);
-  uint32_t *sorted = keys + nk;
-  int64_t *rin_off = reinterpret_cast<int64_t *>((reinterpret_cast<uintptr_t>(sorted + nk) + 15) & ~uintptr_t(15));
-  int64_t *l_off = rin_off + (M + 1);
-  int64_t *r_off = l_off + (M + 1);
-  int32_t *out_self = reinterpret_cast<int32_t *>(r_off + (M + 1));
-  int32_t *in_self = out_self + M;
-  int32_t *l_len = in_self + M;
-  int32_t *r_len = l_len + M;
-  int32_t *cursor = r_len + M;
   const unsigned gw = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * 32, TPB), 148 * 16);
+  // Two branches sharing no buffer: list L on side stream 1, list R on the
+  // system's stream; the headers join them.
+  cudaStream_t sl = fork_side(s, 1);
+  // L part: keys, sorted keys (u32, nu); l_off (i64, M + 1); l_len, out_self (i32, M)
+  // R part: keys, sorted keys (u32, nc); rin_off, r_off (i64, M + 1); r_len, in_self, cursor (i32, M)
+  auto part_bytes = [&](int64_t nkeys, int n64, int n32) {
+    return (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nkeys, 1) + 15) / 16 * 16 +
+           sizeof(int64_t) * (size_t)n64 * ((size_t)M + 1) + sizeof(int32_t) * (size_t)n32 * (size_t)M + 64;
+  };
+  const size_t lb = (part_bytes(nu, 1, 2) + 255) / 256 * 256, rbytes = part_bytes(nc, 2, 3);
+  // the branches use their own scratch whether or not they run concurrently, so
+  // the buffers (and a captured graph's pointers) do not depend on the mode
+  char *lbase = static_cast<char *>(s->side_eval[1].need(lb, sl));
+  char *rbase = static_cast<char *>(s->eval_ws.need(rbytes, st));
+  uint32_t *lkeys = reinterpret_cast<uint32_t *>(lbase), *lsorted = lkeys + std::max<int64_t>(nu, 1);
+  int64_t *l_off = reinterpret_cast<int64_t *>(lbase + (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nu, 1) + 15) / 16 * 16);
+  int32_t *l_len = reinterpret_cast<int32_t *>(l_off + (M + 1));
+  int32_t *out_self = l_len + M;
+  uint32_t *rkeys = reinterpret_cast<uint32_t *>(rbase), *rsorted = rkeys + std::max<int64_t>(nc, 1);
+  int64_t *rin_off = reinterpret_cast<int64_t *>(rbase + (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nc, 1) + 15) / 16 * 16);
+  int64_t *r_off = rin_off + (M + 1);
+  int32_t *r_len = reinterpret_cast<int32_t *>(r_off + (M + 1));
+  int32_t *in_self = r_len + M;
+  int32_t *cursor = in_self + M;
 
-  // list L: per-method sort of the use keys, runs counted, scanned, written
-  if (nu > 0) {
-    method_use_keys32<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
-                                                   s->acc_idx, s->attr_class, M, keys);
+  // list L: per-method sort of the use keys, runs counted, scanned, written; s per entry
+  {
+    Scratch &sw_ = s->side_sort[1];
+    Scratch &uw = s->side_union[1];
+    if (nu > 0) {
+      method_use_keys32<<<grid_for(M), TPB, 0, sl>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
+                                                     s->acc_idx, s->attr_class, M, lkeys);
+      MM_LAUNCH_CHECK();
+      segment_sort<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lkeys, lsorted);
+      MM_LAUNCH_CHECK();
+    }
+    lists_count<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lsorted, 1, s->method_class, s->cbo_attrs,
+                                    l_len, out_self);
     MM_LAUNCH_CHECK();
-    segment_sort<<<gw, TPB, 0, st>>>(s->call_rowptr, s->acc_rowptr, M, keys, sorted);
+    scan_exclusive_i32to64(l_len, l_off, M, sw_, sl, l_off + M);
+    lists_fill_l<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lsorted, s->method_class, s->cbo_attrs,
+                                     l_off, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list, s->l_x);
     MM_LAUNCH_CHECK();
-  }
-  lists_count<<<gw, TPB, 0, st>>>(s->call_rowptr, s->acc_rowptr, M, sorted, 1, s->method_class, s->cbo_attrs,
-                                  l_len, out_self);
-  MM_LAUNCH_CHECK();
-  scan_exclusive_i32to64(l_len, l_off, M, s->sort_ws, st, l_off + M);
-  lists_fill_l<<<gw, TPB, 0, st>>>(s->call_rowptr, s->acc_rowptr, M, sorted, s->method_class, s->cbo_attrs, l_off,
-                                   s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list, s->l_x);
-  MM_LAUNCH_CHECK();
-  if (nu > 0) {
-    const UnionBitmap ub = union_bitmap(s, ceil_div(nu, 32));
-    l_entries_s<<<ub.grid, 256, ub.smem, st>>>(s->l_list, s->l_x, l_off + M, s->acc_rowptr, s->acc_idx,
-                                                s->attr_class, s->own_ptr, s->own_list, ub.words, ub.gbm, s->l_s);
-    MM_LAUNCH_CHECK();
+    if (nu > 0) {
+      const UnionBitmap ub = union_bitmap(s, ceil_div(nu, 32), uw, sl);
+      l_entries_s<<<ub.grid, 256, ub.smem, sl>>>(s->l_list, s->l_x, l_off + M, s->acc_rowptr, s->acc_idx,
+                                                  s->attr_class, s->own_ptr, s->own_list, ub.words, ub.gbm,
+                                                  s->l_s);
+      MM_LAUNCH_CHECK();
+    }
   }
   // list R: callers bucketed by callee (counting sort on fan-in), per-callee sort, runs
   scan_exclusive_i32to64(s->fan_in, rin_off, M, s->sort_ws, st, rin_off + M);
   if (nc > 0) {
     MM_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)M, st));
     caller_classes_scatter<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, M, rin_off,
-                                                        cursor, keys);
+                                                        cursor, rkeys);
     MM_LAUNCH_CHECK();
-    segment_sort<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, keys, sorted);
+    segment_sort<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, rkeys, rsorted);
     MM_LAUNCH_CHECK();
   }
-  lists_count<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, sorted, 0, s->method_class, s->cbo_attrs, r_len, in_self);
+  lists_count<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, rsorted, 0, s->method_class, s->cbo_attrs, r_len, in_self);
   MM_LAUNCH_CHECK();
   scan_exclusive_i32to64(r_len, r_off, M, s->sort_ws, st);
   if (nc > 0) {
-    lists_fill_r<<<gw, TPB, 0, st>>>(rin_off, M, sorted, s->method_class, r_off, s->mg_rowptr, s->mg_dst,
+    lists_fill_r<<<gw, TPB, 0, st>>>(rin_off, M, rsorted, s->method_class, r_off, s->mg_rowptr, s->mg_dst,
                                      s->mg_cnt, s->r_list);
     MM_LAUNCH_CHECK();
   }
+  join_side(s, 1, sl);
   build_headers<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S,
                                              s->own, s->q, l_off, l_len, r_off, r_len, out_self, in_self,
                                              s->l_list, M, s->hdr);
