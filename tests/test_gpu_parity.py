@@ -230,6 +230,54 @@ def test_large_class_multi_tile_lcom():
     check_metrics(s, oracle.Oracle(s), cm, mm_)
 
 
+def test_long_rows_take_the_general_list_paths():
+    """A method using 150 classes and one called from 120 classes: its use keys
+    and its callers' classes exceed one warp (the per-method sort and run walk
+    fall back to their long-segment paths); attributes of many classes, several
+    per class (sharing counts from unions of two or more accessor lists); an
+    explicit candidate list with long rows (more than 62 list entries: the
+    general per-candidate path of the restricted kernel)."""
+    rng = np.random.default_rng(11)
+    c, per = 160, 3
+    method_class = [C for C in range(c) for _ in range(per)]      # methods 3C, 3C+1, 3C+2 in class C
+    attr_class = [C for C in range(c) for _ in range(2)]          # attributes 2C, 2C+1
+    M = len(method_class)
+    acc = [sorted(rng.choice(len(attr_class), size=rng.integers(0, 4), replace=False).tolist()) for _ in range(M)]
+    calls = [sorted(set(rng.choice(M, size=rng.integers(0, 4)).tolist()) - {x}) for x in range(M)]
+    hub = 0                                                       # uses 150 classes, reads 2 attributes of 70
+    calls[hub] = sorted({3 * C + 1 for C in range(1, 151)})
+    acc[hub] = sorted({2 * C + k for C in range(1, 71) for k in (0, 1)})
+    callee = 4                                                    # called from methods of 120 classes
+    for C in range(10, 130):
+        y = 3 * C + 2
+        calls[y] = sorted(set(calls[y]) | {callee})
+    s = make_system(method_class, attr_class, acc, calls, n_classes=c)
+    _eval_all_ways(s)
+    _eval_all_ways(s, cbo_attrs=False)
+    # restricted lists: every other class for the hub and the callee, 5 classes for the rest
+    rows = []
+    for x in range(M):
+        C = method_class[x]
+        if x in (hub, callee):
+            rows.append([D for D in range(c) if D != C])
+        else:
+            rows.append(sorted(set(rng.choice(c, size=5).tolist()) - {C}))
+    rp = np.zeros(M + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    dst = np.asarray([D for r in rows for D in r], dtype=np.int32)
+    g, _, _ = gpu_load(s, device=True)
+    o = oracle.Oracle(s, threads=1)
+    for mask, mi in ((7, 1), (3, 1)):
+        ref = o.evaluate(mask=mask, min_improved=mi, cand_rowptr=rp, cand_dst=dst, method=1, records=True)
+        rec, dig = gpu_records(g, mask, mi, torch.from_numpy(rp).cuda(), torch.from_numpy(dst).cuda())
+        assert same_records(rec, ref.records) and dig == ref.digest
+        top, nk, nm = mmref.suggest_moves(g, k=100000, mask=mask, min_improved=mi,
+                                          cand_rowptr=torch.from_numpy(rp).cuda(),
+                                          cand_dst=torch.from_numpy(dst).cuda())
+        assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+        assert kept_tuples(top) == oracle_kept(ref)
+
+
 def test_relabelled_system_gives_permuted_results():
     s = tiny_random(5)
     p, pc, pm, pa = permute(s, 3)
