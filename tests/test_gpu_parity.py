@@ -278,6 +278,29 @@ def test_long_rows_take_the_general_list_paths():
         assert kept_tuples(top) == oracle_kept(ref)
 
 
+def test_class_too_big_for_shared_bitmaps():
+    """A class of 50,000 methods: the accessor-union bitmaps (one bit per
+    method of the class) no longer fit shared memory and live in global
+    memory.  Closed forms: a methods read {a0, a1}, b methods read {a1}, k
+    methods read {a2}, the rest read nothing, so the sharing pairs are the
+    pairs inside the first a + b methods and inside the k methods."""
+    n, a, b, k = 50000, 40, 25, 30
+    acc = [[0, 1]] * a + [[1]] * b + [[2]] * k + [[]] * (n - a - b - k)
+    # class 1: m reads a0 and a2 of class 0 (t = 2: the union of two accessor lists) and its own attribute
+    acc = acc + [[0, 2, 3], [3]]
+    s = make_system([0] * n + [1, 1], [0, 0, 0, 1], acc, [[] for _ in range(n + 2)], n_classes=2)
+    g, cm, mm_ = gpu_load(s, device=True)
+    Q = (a + b) * (a + b - 1) // 2 + k * (k - 1) // 2
+    assert int(cm["Q"][0]) == Q and int(cm["P"][0]) == n * (n - 1) // 2 - Q
+    q = mm_["q"][:n]
+    assert (q[: a + b] == a + b - 1).all() and (q[a + b: a + b + k] == k - 1).all() and (q[a + b + k:] == 0).all()
+    assert int(cm["Q"][1]) == 1 and int(cm["P"][1]) == 0
+    rp = torch.tensor([0] * (n + 1) + [1, 1], dtype=torch.int64, device="cuda")  # one candidate: m = n -> class 0
+    dst = torch.tensor([0], dtype=torch.int32, device="cuda")
+    rec, _ = gpu_records(g, 7, 1, rp, dst)
+    assert int(rec["s"][0]) == a + k and int(rec["t"][0]) == 2
+
+
 def test_relabelled_system_gives_permuted_results():
     s = tiny_random(5)
     p, pc, pm, pa = permute(s, 3)
