@@ -1336,10 +1336,11 @@ int64_t grouped_resident_grid() {
 }
 
 // Candidate lists: row-pointer checks (thread per method) and range / self
-// checks streamed over the destinations (a warp per 256 consecutive entries,
-// each lane finding its method by a forward scan from the chunk's first
-// method), plus a content hash of the lists (every (index, destination) and
-// every row end) that keys the cached kept moves of a list evaluation.
+// checks streamed over the destinations (a warp per contiguous range of
+// entries: one binary search for the range's first method, then each lane
+// finds its method by a forward scan), plus a content hash of the lists
+// (every (index, destination) and every row end) that keys the cached kept
+// moves of a list evaluation.
 __device__ __forceinline__ uint64_t cand_mix(uint64_t v) {
   v *= 0x9E3779B97F4A7C15ULL;
   return v ^ (v >> 31);
@@ -1378,19 +1379,19 @@ __device__ __forceinline__ int32_t owner_of(const int64_t *rowptr, int32_t M, in
 }
 
 __global__ void validate_cand_dst(const int64_t *rowptr, const int32_t *dst, const int32_t *method_class,
-                                  int32_t M, int32_t c, int64_t n_cand, uint32_t *err,
+                                  int32_t M, int32_t c, int64_t n_cand, int64_t per_warp, uint32_t *err,
                                   unsigned long long *hash) {
   const uint32_t lane = threadIdx.x & 31u;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t i_begin = w * per_warp, i_end = min(n_cand, i_begin + per_warp);
   uint32_t e = 0;
   uint64_t h = 0;
-  for (int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 256; i0 < n_cand;
-       i0 += nwarps * 256) {
-    int32_t m = owner_of(rowptr, M, i0);
-    for (int64_t k = 0; k < 256; k += 32) {
-      const int64_t i = i0 + k + lane;
+  if (i_begin < i_end) {
+    int32_t m = owner_of(rowptr, M, i_begin);  // one search per warp, then forward scans
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += 32) {
+      const int64_t i = i0 + lane;
       int32_t mi = m;
-      if (i < n_cand) {
+      if (i < i_end) {
         while (mi < M && rowptr[mi + 1] <= i) ++mi;
         const int32_t D = dst[i];
         if (D < 0 || D >= c) e |= VE_CAND_RANGE;
@@ -1593,9 +1594,12 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
     validate_cand_rows<<<grid_for(s->M), TPB, 0, st>>>(*rowptr, s->M, *n_cand, s->d_err, s->d_u64 + 3);
     MM_LAUNCH_CHECK();
     if (*n_cand > 0) {
-      const unsigned g = (unsigned)std::min<int64_t>(ceil_div(ceil_div(*n_cand, 256) * 32, TPB), 148 * 16);
-      validate_cand_dst<<<g, TPB, 0, st>>>(*rowptr, *dst, s->method_class, s->M, s->c, *n_cand, s->d_err,
-                                          s->d_u64 + 3);
+      // one contiguous range per warp (a multiple of 32 entries), at most 148 x 16 blocks of 8 warps
+      const int64_t warps = std::min<int64_t>(ceil_div(*n_cand, 32), (int64_t)148 * 16 * (TPB / 32));
+      const int64_t per_warp = ceil_div(ceil_div(*n_cand, warps), 32) * 32;
+      const unsigned g = (unsigned)ceil_div(ceil_div(*n_cand, per_warp) * 32, TPB);
+      validate_cand_dst<<<g, TPB, 0, st>>>(*rowptr, *dst, s->method_class, s->M, s->c, *n_cand, per_warp,
+                                          s->d_err, s->d_u64 + 3);
       MM_LAUNCH_CHECK();
     }
   }
