@@ -197,19 +197,11 @@ void ensure_capacity(mm_system *s, int64_t n_acc, int64_t n_call) {
   }
 }
 
-// Recompute the load-time summary from the per-class sizes of the mirror.
+// Recompute the load-time summary (largest class) from the per-class sizes of the mirror.
 void resummarise(mm_system *s) {
-  EditMirror &mr = s->mirror;
-  int64_t words = 0, tiles = 0;
+  const EditMirror &mr = s->mirror;
   int32_t nmax = 0;
-  for (int32_t C = 0; C < s->c; ++C) {
-    const int64_t n = mr.cls_n[C], W = ((int64_t)mr.cls_a[C] + 31) / 32, T = (n + 31) / 32;
-    words += n * W;
-    tiles += T * (T + 1) / 2;
-    nmax = std::max<int32_t>(nmax, (int32_t)n);
-  }
-  s->summary.bits_words = words;
-  s->summary.lcom_tiles = tiles;
+  for (int32_t C = 0; C < s->c; ++C) nmax = std::max<int32_t>(nmax, mr.cls_n[C]);
   s->summary.max_class_methods = nmax;
 }
 

@@ -91,8 +91,6 @@ enum : uint32_t {
 struct LoadSummary {
   uint32_t err;
   int32_t max_class_methods;
-  int64_t bits_words;   // sum over classes of n_C * ceil(a_C / 32)
-  int64_t lcom_tiles;   // sum over classes of T_C (T_C + 1) / 2, T_C = ceil(n_C / 32)
 };
 
 // Per-method header for move evaluation (3 x int4 = 48 bytes):
@@ -211,9 +209,6 @@ void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch 
 // The result is left in keys/vals; alt buffers are scratch of the same size.
 void radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
                     int nbits, Scratch &ws, cudaStream_t st);
-void radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
-                    int nbits, Scratch &ws, cudaStream_t st);
-
 // ---------------------------------------------------------------- pipeline stages
 
 void load_validate_and_summarise(mm_system *s);     // mm_system.cu

@@ -129,28 +129,11 @@ __global__ void class_histograms(const int32_t *method_class, const int32_t *att
   }
 }
 
-__global__ void summarise_classes(const int32_t *cls_n, const int32_t *cls_a, int32_t c, LoadSummary *sum) {
+__global__ void summarise_classes(const int32_t *cls_n, int32_t c, LoadSummary *sum) {
   int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t words = 0, tiles = 0;
-  int32_t nmax = 0;
-  if (C < c) {
-    int64_t n = cls_n[C], a = cls_a[C];
-    int64_t W = (a + 31) / 32;
-    int64_t T = (n + 31) / 32;
-    words = n * W;
-    tiles = T * (T + 1) / 2;
-    nmax = (int32_t)n;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    words += __shfl_down_sync(0xffffffffu, words, o);
-    tiles += __shfl_down_sync(0xffffffffu, tiles, o);
-    nmax = max(nmax, __shfl_down_sync(0xffffffffu, nmax, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (words) atomicAdd((unsigned long long *)&sum->bits_words, (unsigned long long)words);
-    if (tiles) atomicAdd((unsigned long long *)&sum->lcom_tiles, (unsigned long long)tiles);
-    atomicMax(&sum->max_class_methods, nmax);
-  }
+  int32_t nmax = C < c ? cls_n[C] : 0;
+  for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_down_sync(0xffffffffu, nmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&sum->max_class_methods, nmax);
 }
 
 // ---------------------------------------------------------------- structures
@@ -208,7 +191,7 @@ void load_validate_and_summarise(mm_system *s) {
   MM_LAUNCH_CHECK();
   LoadSummary *dsum = reinterpret_cast<LoadSummary *>(s->d_u64 + 4);
   MM_CUDA_TRY(cudaMemsetAsync(dsum, 0, sizeof(LoadSummary), st));
-  summarise_classes<<<grid_for(s->c), TPB, 0, st>>>(s->cls_n, s->cls_a, s->c, dsum);
+  summarise_classes<<<grid_for(s->c), TPB, 0, st>>>(s->cls_n, s->c, dsum);
   MM_LAUNCH_CHECK();
   LoadSummary h{};
   MM_CUDA_TRY(cudaMemcpyAsync(&h, dsum, sizeof(LoadSummary), cudaMemcpyDeviceToHost, st));
