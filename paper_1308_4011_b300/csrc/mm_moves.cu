@@ -1008,34 +1008,40 @@ __global__ void __launch_bounds__(DB_THREADS, 3) eval_dense(DenseSys sy, OutCtx 
 // compressed adjacency.  A warp owns groups of 8 consecutive methods: one
 // coalesced pass loads their row bounds and headers, asynchronous copies bring
 // their L and R lists (stored in method order by the list build) into shared
-// memory.  For each method the warp lays out its probe rows -- the in-row of
-// each class m uses, the out-row of each class calling m, C's in-row and
-// out-row -- in pages of 32 with three masks per page, then walks the
-// candidates 32 at a time.  A lane probes every row at its destination D (one
-// 8-byte summary record, plus one packed word only when the record marks D's
-// word non-zero; a method's records are re-read from L1 by all its candidates,
-// the packed words come from L2), collects the answers of a page as a bit mask
-// and reduces it with the page masks:  gain = L rows without the bit, impX = R
-// rows of callers that drop C and already use D, worX = R rows of callers that
-// keep C and do not use D yet; a row whose class is D itself is masked out and
-// supplies the D-specific list fields instead.  Methods whose lists exceed the
-// stage take the general per-candidate path.
+// memory.  For a run of methods whose lists fit, the warp lays out every
+// method's probe rows -- the in-row of each class m uses, C's in-row and
+// out-row, the out-row of each class calling m -- with three masks per page of
+// 32 rows, then walks the run's candidates 32 at a time across method
+// boundaries (a lane finds its method by a forward scan), so lanes are not
+// left idle at the end of each method.  A lane probes every row of its method
+// at its destination D (one 8-byte summary record, plus one packed word only
+// when the record marks D's word non-zero; a method's records are re-read from
+// L1 by all its candidates, the packed words come from L2), collects the
+// answers of a page as a bit mask and reduces it with the page masks:  gain =
+// L rows without the bit, impX = R rows of callers that drop C and already use
+// D, worX = R rows of callers that keep C and do not use D yet; a row whose
+// class is D itself is masked out and supplies the D-specific list fields
+// instead.  Methods whose lists exceed the stage take the general
+// per-candidate path.
 constexpr int CG_M = 8;               // methods per group
-constexpr int CG_LCAP = 96;           // staged L entries per warp
-constexpr int CG_RCAP = 96;           // staged R entries per warp
+constexpr int CG_LCAP = 64;           // staged L entries per warp
+constexpr int CG_RCAP = 64;           // staged R entries per warp
 constexpr int CG_PMAX = 128;          // probe rows per method (4 pages of 32)
+constexpr int CG_TCAP = 256;          // probe rows of a run of methods (each padded to whole batches)
 constexpr int CG_WARPS = 8;
-constexpr int CG_PB = 4;              // probes per batch (rows are padded to whole batches)
+constexpr int CG_PB = 4;              // probes per batch
 
 struct CsrGroup {
   MoveHdr hdr[CG_M];
   int64_t rp[CG_M + 2];               // candidate row bounds of the group
   int32_t loff[CG_M], roff[CG_M];     // list offsets in the stage
+  int32_t rbase[CG_M + 1];            // first probe row of each method of the current run
   int4 lent[CG_LCAP];
   int4 rent[CG_RCAP];
   int32_t lsh[CG_LCAP];
-  uint2 prow[CG_PMAX];                // probe rows of the current method: {record offset, class}
-  uint4 pmask[CG_PMAX / 32];          // per page: {L rows with a use edge, R rows dropping C, R rows keeping C}
+  uint2 prow[CG_TCAP];                // probe rows of the run: {record offset, class}
+  uint4 pmask[CG_M][CG_PMAX / 32];    // per method and page: {L rows with a use edge, R rows dropping C,
+                                      //                        R rows keeping C}
 };
 constexpr int CG_WARP_BYTES = (int)((sizeof(CsrGroup) + 15) / 16 * 16);
 static_assert(CG_WARPS * CG_WARP_BYTES <= 48 * 1024, "stage fits the default shared-memory window");
@@ -1120,7 +1126,8 @@ __device__ __noinline__ uint64_t csr_general_row(const EvalCtx cx, const OutCtx 
 // matter to the callers' CBO, so without CBO in the mask they are only
 // compared with D, not probed.
 __device__ __forceinline__ uint4 csr_candidate(const CsrSys &sy, const CsrGroup &w, const MoveHdr &h, int32_t lo,
-                                               int32_t ro, int32_t D, int32_t &dck, int32_t &dcbo) {
+                                               int32_t ro, const uint2 *prow, const uint4 *pmask, int32_t D,
+                                               int32_t &dck, int32_t &dcbo) {
   const DState ds = dstate_rec(sy.dest_rec, D);
   const int32_t nL = h.w0.z, nR = h.w1.x;
   const int32_t nprobe = (sy.cx.mask & 4u) ? nL + nR + 2 : nL + 2;
@@ -1137,7 +1144,7 @@ __device__ __forceinline__ uint4 csr_candidate(const CsrSys &sy, const CsrGroup 
       uint2 rec[CG_PB];
 #pragma unroll
       for (int u = 0; u < CG_PB; ++u) {
-        const uint2 pw = w.prow[p0 + k0 + u];  // rows past the probed ones are the zero row
+        const uint2 pw = prow[p0 + k0 + u];  // rows past the probed ones are the zero row
         match |= (uint32_t)((int32_t)pw.y == D) << (k0 + u);
         rec[u] = __ldg(sy.csum + (pw.x + rw));
       }
@@ -1148,7 +1155,7 @@ __device__ __forceinline__ uint4 csr_candidate(const CsrSys &sy, const CsrGroup 
 #pragma unroll
       for (int u = 0; u < CG_PB; ++u) bits |= ((word[u] >> dsh) & 1u) << (k0 + u);
     }
-    const uint4 pm = w.pmask[p0 >> 5];
+    const uint4 pm = pmask[p0 >> 5];
     const uint32_t valid = ~match;
     const uint32_t lv = pm.x & valid;
     g.gain += __popc(lv) - __popc(bits & lv);
@@ -1232,16 +1239,19 @@ __global__ void __launch_bounds__(CG_WARPS * 32, 3) eval_csr_grouped(CsrSys sy, 
       }
       // longest run j..k-1 without a big method whose lists fit together
       const bool inrun = (int32_t)lane >= j && (int32_t)lane < nm;
+      const int32_t nalloc = (nl + nr + 2 + CG_PB - 1) / CG_PB * CG_PB;  // probe rows, padded to whole batches
       const int32_t cl = warp_scan_incl(inrun ? nl : 0, lane);
       const int32_t cr = warp_scan_incl(inrun ? nr : 0, lane);
+      const int32_t ct = warp_scan_incl(inrun ? nalloc : 0, lane);
       const uint32_t after = bigm & ~((2u << j) - 1u);  // big methods after j
       const int32_t fb = after ? __ffs(after) - 1 : 32;
-      const uint32_t fits =
-          __ballot_sync(0xffffffffu, inrun && (int32_t)lane < fb && cl <= CG_LCAP && cr <= CG_RCAP);
+      const uint32_t fits = __ballot_sync(0xffffffffu, inrun && (int32_t)lane < fb && cl <= CG_LCAP &&
+                                                           cr <= CG_RCAP && ct <= CG_TCAP);
       const int32_t k = j + __popc(fits);
       const bool mine = (int32_t)lane >= j && (int32_t)lane < k;
       const int32_t totL = __shfl_sync(0xffffffffu, cl, k - 1);
       const int32_t totR = __shfl_sync(0xffffffffu, cr, k - 1);
+      const int32_t totT = __shfl_sync(0xffffffffu, ct, k - 1);
       const uint32_t hasl = __ballot_sync(0xffffffffu, mine && nl > 0);
       const uint32_t hasr = __ballot_sync(0xffffffffu, mine && nr > 0);
       const int32_t l0 = __shfl_sync(0xffffffffu, h.w0.y, hasl ? __ffs(hasl) - 1 : 0);
@@ -1249,7 +1259,11 @@ __global__ void __launch_bounds__(CG_WARPS * 32, 3) eval_csr_grouped(CsrSys sy, 
       if (mine) {
         w.loff[lane] = cl - nl;
         w.roff[lane] = cr - nr;
+        w.rbase[lane] = ct - nalloc;
+#pragma unroll
+        for (int pg = 0; pg < CG_PMAX / 32; ++pg) w.pmask[lane][pg] = make_uint4(0u, 0u, 0u, 0u);
       }
+      if ((int32_t)lane == k) w.rbase[lane] = totT;
       for (int32_t e = (int32_t)lane; e < totL; e += 32) {
         cp_async16(&w.lent[e], sy.cx.l_list + l0 + e);
         cp_async4(&w.lsh[e], sy.cx.l_s + l0 + e);
@@ -1257,56 +1271,61 @@ __global__ void __launch_bounds__(CG_WARPS * 32, 3) eval_csr_grouped(CsrSys sy, 
       for (int32_t e = (int32_t)lane; e < totR; e += 32) cp_async16(&w.rent[e], sy.cx.r_list + r0 + e);
       cp_async_wait();
       __syncwarp();
-      for (int32_t jm = j; jm < k; ++jm) {
-        const int64_t b0 = w.rp[jm], b1 = w.rp[jm + 1];
-        if (b0 == b1) continue;
-        const MoveHdr hm = w.hdr[jm];
-        const int32_t lo = w.loff[jm], ro = w.roff[jm];
-        const int32_t nL = hm.w0.z, nR = hm.w1.x, nP = nL + nR + 2;
-        const int32_t C = hm.w0.x;
-        int32_t Dn = b0 + (int64_t)lane < b1 ? __ldg(cand_dst + b0 + lane) : C;
-        __syncwarp();  // the previous method's readers are done with the row table
-        // row table, page by page: lane describes row p0 + lane (rows past nP: the zero row).
-        // Order: L entries, C's in-row, C's out-row, R entries.
-        for (int32_t p0 = 0; p0 < nP; p0 += 32) {
-          const int32_t kk = p0 + (int32_t)lane;
-          uint32_t off = zero_row, cls = 0xffffffffu;
-          bool isl = false, isrl = false, isrk = false;
-          if (kk < nL) {
-            const int4 v = w.lent[lo + kk];
-            cls = (uint32_t)v.x;
-            off = (sy.c + cls) * sw;
-            isl = v.y > 0;
-          } else if (kk < nL + 2) {
-            off = (kk == nL ? sy.c + (uint32_t)C : (uint32_t)C) * sw;  // C is never a candidate: no class
-          } else if (kk < nP) {
-            const int4 v = w.rent[ro + kk - nL - 2];
-            cls = (uint32_t)v.x;
-            off = cls * sw;
-            isrl = v.z == v.y;
-            isrk = !isrl;
-          }
-          w.prow[kk] = make_uint2(off, cls);
-          const uint32_t lm = __ballot_sync(0xffffffffu, isl);
-          const uint32_t rl = __ballot_sync(0xffffffffu, isrl);
-          const uint32_t rk = __ballot_sync(0xffffffffu, isrk);
-          if (lane == 0) w.pmask[p0 >> 5] = make_uint4(lm, rl, rk, 0u);
+      // probe rows of the whole run: row t belongs to method mi with rbase[mi] <= t < rbase[mi + 1];
+      // order per method: L entries, C's in-row, C's out-row, R entries, zero rows up to the batch end
+      for (int32_t t = (int32_t)lane; t < totT; t += 32) {
+        int32_t mi = j;
+        while (w.rbase[mi + 1] <= t) ++mi;
+        const int32_t kk = t - w.rbase[mi];
+        const MoveHdr hm = w.hdr[mi];
+        const int32_t nL = hm.w0.z, nR = hm.w1.x, C = hm.w0.x, lo = w.loff[mi], ro = w.roff[mi];
+        uint32_t off = zero_row, cls = 0xffffffffu;
+        if (kk < nL) {
+          const int4 v = w.lent[lo + kk];
+          cls = (uint32_t)v.x;
+          off = (sy.c + cls) * sw;
+          if (v.y > 0) atomicOr(&w.pmask[mi][kk >> 5].x, 1u << (kk & 31));
+        } else if (kk < nL + 2) {
+          off = (kk == nL ? sy.c + (uint32_t)C : (uint32_t)C) * sw;  // C is never a candidate: no class
+        } else if (kk < nL + nR + 2) {
+          const int4 v = w.rent[ro + kk - nL - 2];
+          cls = (uint32_t)v.x;
+          off = cls * sw;
+          if (v.z == v.y) atomicOr(&w.pmask[mi][kk >> 5].y, 1u << (kk & 31));
+          else atomicOr(&w.pmask[mi][kk >> 5].z, 1u << (kk & 31));
         }
-        __syncwarp();
-        for (int64_t i0 = b0; i0 < b1; i0 += 32) {
+        w.prow[t] = make_uint2(off, cls);
+      }
+      __syncwarp();
+      // the run's candidates, 32 at a time across method boundaries; a lane finds
+      // its method by a forward scan from the method of the chunk's first candidate
+      {
+        const int64_t ce = w.rp[k];
+        int32_t k0 = j;
+        int64_t i0 = w.rp[j];
+        int32_t Dn = i0 + (int64_t)lane < ce ? __ldg(cand_dst + i0 + lane) : 0;
+        for (; i0 < ce; i0 += 32) {
           const int64_t i = i0 + lane;
-          const bool act = i < b1;
+          const bool act = i < ce;
           const int32_t D = Dn;
-          if (i0 + 32 + (int64_t)lane < b1) Dn = __ldg(cand_dst + i0 + 32 + lane);  // next chunk in flight
+          if (i0 + 32 + (int64_t)lane < ce) Dn = __ldg(cand_dst + i0 + 32 + lane);  // next chunk in flight
+          int32_t mi = k0;
+          if (act)
+            while (w.rp[mi + 1] <= i) ++mi;
           int32_t dck = 0, dcbo = 0;
           uint4 r = make_uint4(0, 0, 0, 0);
-          if (act) r = csr_candidate(sy, w, hm, lo, ro, D, dck, dcbo);
+          if (act) {
+            const MoveHdr hm = w.hdr[mi];
+            r = csr_candidate(sy, w, hm, w.loff[mi], w.roff[mi], &w.prow[w.rbase[mi]], w.pmask[mi], D, dck,
+                              dcbo);
+          }
           if (REC && act) __stcs(oc.records + i, r);
-          if (DIG && act) dig += record_hash(ma + jm, D, r);
-          if (KEEP) emit_kept(oc, act && (r.w >> 31), ma + jm, D, r.z >> 16, dck, dcbo, lane);
+          if (DIG && act) dig += record_hash(ma + mi, D, r);
+          if (KEEP) emit_kept(oc, act && (r.w >> 31), ma + mi, D, r.z >> 16, dck, dcbo, lane);
+          k0 = __shfl_sync(0xffffffffu, mi, 31);
         }
       }
-      __syncwarp();  // lists reused by the next run
+      __syncwarp();  // lists and rows reused by the next run
       j = k;
     }
   }
