@@ -207,6 +207,8 @@ void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch 
 
 // Stable LSD radix sort of n keys (and optional uint32 values) on bits [0, nbits).
 // The result is left in keys/vals; alt buffers are scratch of the same size.
+void radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int nbits,
+                    Scratch &ws, cudaStream_t st);
 void radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
                     int nbits, Scratch &ws, cudaStream_t st);
 // ---------------------------------------------------------------- pipeline stages

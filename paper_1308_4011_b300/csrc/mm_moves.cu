@@ -1549,9 +1549,54 @@ __global__ void gather_field(const mm_move *v, const uint32_t *perm, int64_t n, 
     case 1: f = a.m; break;
     case 2: f = (int64_t)a.d_cbo_sum + bias; break;
     case 3: f = (int64_t)a.d_lcom_ck_sum + bias; break;
-    default: f = 65535 - (int64_t)a.n_improved; break;
+    default: f = bias - (int64_t)a.n_improved; break;  // descending: bias = the largest n_improved
   }
   key[i] = (uint32_t)f;
+}
+
+// min and max of n_improved, d_lcom_ck_sum and d_cbo_sum over the kept moves
+// (mm = {min, max} x 3, initialised to {INT_MAX, INT_MIN})
+__global__ void kept_ranges(const mm_move *v, int64_t n, int32_t *mm) {
+  int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const mm_move a = v[i];
+    const int32_t f[3] = {a.n_improved, a.d_lcom_ck_sum, a.d_cbo_sum};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = min(lo[k], f[k]);
+      hi[k] = max(hi[k], f[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&mm[2 * k], lo[k]);
+      atomicMax(&mm[2 * k + 1], hi[k]);
+    }
+  }
+}
+
+// One 64-bit key per kept move in the suggestion order: (n_improved desc,
+// dLCOM asc, dCBO asc, m asc, d asc), each field biased by its minimum and
+// packed into the bits its range needs (field widths from kept_ranges).
+struct KeyLayout {
+  int32_t nimp_max, ck_min, cbo_min;
+  int s_m, s_cbo, s_ck, s_nimp;
+};
+
+__global__ void kept_keys(const mm_move *v, int64_t n, KeyLayout kl, uint64_t *key, uint32_t *perm) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const mm_move a = v[i];
+  key[i] = ((uint64_t)(uint32_t)(kl.nimp_max - a.n_improved) << kl.s_nimp) |
+           ((uint64_t)(uint32_t)(a.d_lcom_ck_sum - kl.ck_min) << kl.s_ck) |
+           ((uint64_t)(uint32_t)(a.d_cbo_sum - kl.cbo_min) << kl.s_cbo) | ((uint64_t)(uint32_t)a.m << kl.s_m) |
+           (uint64_t)(uint32_t)a.d;
+  perm[i] = (uint32_t)i;
 }
 
 __global__ void iota_perm(uint32_t *p, int64_t n) {
@@ -1730,18 +1775,50 @@ void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K) {
     bitonic_sort_moves<<<1, 1024, 0, st>>>(kept, (int32_t)K);
     MM_LAUNCH_CHECK();
   } else if (K > BITONIC_MAX) {
-    // permutation sort, least significant field first (d, m, dCBO, dLCOM, n_improved desc)
+    // the fields' actual ranges decide whether one 64-bit composite key holds them all
+    int32_t *d_mm = reinterpret_cast<int32_t *>(s->d_u64 + 24);
+    const int32_t init[6] = {INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN};
+    MM_CUDA_TRY(cudaMemcpyAsync(d_mm, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    kept_ranges<<<(unsigned)std::min<int64_t>(ceil_div(K, TPB), 148 * 4), TPB, 0, st>>>(kept, K, d_mm);
+    MM_LAUNCH_CHECK();
+    int32_t r[6];
+    MM_CUDA_TRY(cudaMemcpyAsync(r, d_mm, sizeof(r), cudaMemcpyDeviceToHost, st));
+    MM_CUDA_TRY(cudaStreamSynchronize(st));
+    const int w_d = bits_for((uint64_t)std::max(s->c - 1, 0)), w_m = bits_for((uint64_t)std::max(s->M - 1, 0));
+    const int w_cbo = bits_for((uint64_t)((int64_t)r[5] - r[4])), w_ck = bits_for((uint64_t)((int64_t)r[3] - r[2]));
+    const int w_n = bits_for((uint64_t)((int64_t)r[1] - r[0]));
+    const int total = w_d + w_m + w_cbo + w_ck + w_n;
+    if (total <= 64) {
+      size_t kb = sizeof(uint64_t) * 2 * (size_t)K, pb = sizeof(uint32_t) * 2 * (size_t)K;
+      char *base = static_cast<char *>(s->stage_ws.need(kb + pb + sizeof(mm_move) * (size_t)K + 512, st));
+      uint64_t *key = reinterpret_cast<uint64_t *>(base), *key_alt = key + K;
+      uint32_t *perm = reinterpret_cast<uint32_t *>(key_alt + K), *perm_alt = perm + K;
+      mm_move *sorted = reinterpret_cast<mm_move *>((reinterpret_cast<uintptr_t>(perm_alt + K) + 15) & ~uintptr_t(15));
+      KeyLayout kl;
+      kl.nimp_max = r[1];
+      kl.ck_min = r[2];
+      kl.cbo_min = r[4];
+      kl.s_m = w_d;
+      kl.s_cbo = w_d + w_m;
+      kl.s_ck = kl.s_cbo + w_cbo;
+      kl.s_nimp = kl.s_ck + w_ck;
+      kept_keys<<<grid_for(K), TPB, 0, st>>>(kept, K, kl, key, perm);
+      MM_LAUNCH_CHECK();
+      radix_sort_u64(key, key_alt, perm, perm_alt, K, total, s->sort_ws, st);
+      permute_moves<<<grid_for(K), TPB, 0, st>>>(kept, perm, K, sorted);
+      MM_LAUNCH_CHECK();
+      MM_CUDA_TRY(cudaMemcpyAsync(kept, sorted, sizeof(mm_move) * (size_t)K, cudaMemcpyDeviceToDevice, st));
+      return;
+    }
+    // else a permutation sort field by field, least significant first (d, m, dCBO, dLCOM, n_improved desc)
     size_t pb = sizeof(uint32_t) * 4 * (size_t)K;
     uint32_t *pw = static_cast<uint32_t *>(s->stage_ws.need(pb + sizeof(mm_move) * (size_t)K + 256, st));
     uint32_t *key = pw, *key_alt = pw + K, *perm = pw + 2 * K, *perm_alt = pw + 3 * K;
     mm_move *sorted = reinterpret_cast<mm_move *>(pw + 4 * K);
     iota_perm<<<grid_for(K), TPB, 0, st>>>(perm, K);
     MM_LAUNCH_CHECK();
-    const int64_t bias_cbo = 2 * (int64_t)s->c + 4;
-    const int64_t bias_ck = 4 * (int64_t)std::max(s->summary.max_class_methods, 1) + 4;
-    const int fbits[5] = {bits_for((uint64_t)std::max(s->c - 1, 0)), bits_for((uint64_t)std::max(s->M - 1, 0)),
-                          bits_for((uint64_t)(2 * bias_cbo)), bits_for((uint64_t)(2 * bias_ck)), 16};
-    const int64_t bias[5] = {0, 0, bias_cbo, bias_ck, 0};
+    const int fbits[5] = {w_d, w_m, w_cbo, w_ck, w_n};
+    const int64_t bias[5] = {0, 0, -(int64_t)r[4], -(int64_t)r[2], (int64_t)r[1]};
     for (int f = 0; f < 5; ++f) {
       gather_field<<<grid_for(K), TPB, 0, st>>>(kept, perm, K, f, bias[f], key);
       MM_LAUNCH_CHECK();

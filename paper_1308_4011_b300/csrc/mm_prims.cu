@@ -307,6 +307,11 @@ void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch 
   scan_exclusive<int32_t, int64_t>(in, out, n, total_dev, ws, st);
 }
 
+void radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int nbits,
+                    Scratch &ws, cudaStream_t st) {
+  radix_sort<uint64_t>(keys, keys_alt, vals, vals_alt, n, nbits, ws, st);
+}
+
 void radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int nbits,
                     Scratch &ws, cudaStream_t st) {
   radix_sort<uint32_t>(keys, keys_alt, vals, vals_alt, n, nbits, ws, st);
