@@ -140,36 +140,6 @@ __device__ __forceinline__ void segment(const int64_t *a, const int64_t *b, int6
   *len = e - s;
 }
 
-// One warp per segment: out[p0 + rank(i)] = in[p0 + i], rank = number of keys
-// smaller, or equal and earlier.
-__global__ void segment_sort(const int64_t *a, const int64_t *b, int32_t M, const uint32_t *in, uint32_t *out) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
-    int64_t p0, len;
-    segment(a, b, x, &p0, &len);
-    if (len <= 32) {
-      const uint32_t k = (int64_t)lane < len ? in[p0 + lane] : 0xffffffffu;
-      int32_t rank = 0;
-      for (int32_t j = 0; j < (int32_t)len; ++j) {
-        const uint32_t kj = __shfl_sync(0xffffffffu, k, j);
-        rank += (kj < k) || (kj == k && j < (int32_t)lane);
-      }
-      if ((int64_t)lane < len) out[p0 + rank] = k;
-    } else {
-      for (int64_t i = lane; i < len; i += 32) {
-        const uint32_t k = in[p0 + i];
-        int64_t rank = 0;
-        for (int64_t j = 0; j < len; ++j) {
-          const uint32_t kj = in[p0 + j];
-          rank += (kj < k) || (kj == k && j < i);
-        }
-        out[p0 + rank] = k;
-      }
-    }
-  }
-}
-
 // Runs of a sorted segment of use keys (L) or caller classes (R).  For each run
 // of equal classes, `f(class, n0, n1, index among the runs whose class is not
 // C)` is called by one lane; n0/n1 count kind-0/kind-1 keys (R keys are all
@@ -211,19 +181,56 @@ __device__ __forceinline__ int32_t segment_runs(const uint32_t *keys, int64_t p0
   return __shfl_sync(0xffffffffu, idx, 0);
 }
 
-// Count pass: l_len / r_len per method and the own-class run (out_self / in_self).
-__global__ void lists_count(const int64_t *a, const int64_t *b, int32_t M, const uint32_t *sorted, int shift,
-                            const int32_t *method_class, int32_t cbo_attrs, int32_t *len_out, int32_t *self_out) {
-  const uint32_t lane = threadIdx.x & 31u;
+// Sort and count in one pass: one warp sorts the segment (a segment of at most
+// 32 keys also into its shared-memory row, read back for the run walk), then
+// counts the runs: l_len / r_len per method and the own-class run (out_self /
+// in_self).
+__global__ void __launch_bounds__(256) segment_sort_count(const int64_t *a, const int64_t *b, int32_t M,
+                                                          const uint32_t *in, uint32_t *out, int shift,
+                                                          const int32_t *method_class, int32_t cbo_attrs,
+                                                          int32_t *len_out, int32_t *self_out) {
+  __shared__ uint32_t sk[8][32];
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
     int64_t p0, len;
     segment(a, b, x, &p0, &len);
+    const uint32_t *runs_keys;
+    int64_t runs_p0;
+    __syncwarp();  // the previous segment's readers are done with the row
+    if (len <= 32) {
+      const uint32_t k = (int64_t)lane < len ? in[p0 + lane] : 0xffffffffu;
+      int32_t rank = 0;
+      for (int32_t j = 0; j < (int32_t)len; ++j) {
+        const uint32_t kj = __shfl_sync(0xffffffffu, k, j);
+        rank += (kj < k) || (kj == k && j < (int32_t)lane);
+      }
+      if ((int64_t)lane < len) {
+        out[p0 + rank] = k;
+        sk[wid][rank] = k;
+      }
+      runs_keys = sk[wid];
+      runs_p0 = 0;
+    } else {
+      for (int64_t i = lane; i < len; i += 32) {
+        const uint32_t k = in[p0 + i];
+        int64_t rank = 0;
+        for (int64_t j = 0; j < len; ++j) {
+          const uint32_t kj = in[p0 + j];
+          rank += (kj < k) || (kj == k && j < i);
+        }
+        out[p0 + rank] = k;
+      }
+      runs_keys = out;
+      runs_p0 = p0;
+    }
+    __syncwarp();  // sorted keys visible to the whole warp
     const int32_t C = method_class[x];
     int32_t self = 0;
-    const int32_t n = segment_runs(sorted, p0, len, shift, C, lane, [&](int32_t E, int32_t n0, int32_t n1, int32_t) {
-      if (E == C) self = n0 + (cbo_attrs ? n1 : 0);
-    });
+    const int32_t n = segment_runs(runs_keys, runs_p0, len, shift, C, lane,
+                                   [&](int32_t E, int32_t n0, int32_t n1, int32_t) {
+                                     if (E == C) self = n0 + (cbo_attrs ? n1 : 0);
+                                   });
     for (int o = 16; o > 0; o >>= 1) self += __shfl_xor_sync(0xffffffffu, self, o);
     if (lane == 0) {
       len_out[x] = n;
@@ -349,11 +356,9 @@ void build_move_precompute(mm_system *s) {
       method_use_keys32<<<grid_for(M), TPB, 0, sl>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
                                                      s->acc_idx, s->attr_class, M, lkeys);
       MM_LAUNCH_CHECK();
-      segment_sort<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lkeys, lsorted);
-      MM_LAUNCH_CHECK();
     }
-    lists_count<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lsorted, 1, s->method_class, s->cbo_attrs,
-                                    l_len, out_self);
+    segment_sort_count<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lkeys, lsorted, 1, s->method_class,
+                                           s->cbo_attrs, l_len, out_self);
     MM_LAUNCH_CHECK();
     scan_exclusive_i32to64(l_len, l_off, M, sw_, sl, l_off + M);
     lists_fill_l<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lsorted, s->method_class, s->cbo_attrs,
@@ -374,10 +379,9 @@ void build_move_precompute(mm_system *s) {
     caller_classes_scatter<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, M, rin_off,
                                                         cursor, rkeys);
     MM_LAUNCH_CHECK();
-    segment_sort<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, rkeys, rsorted);
-    MM_LAUNCH_CHECK();
   }
-  lists_count<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, rsorted, 0, s->method_class, s->cbo_attrs, r_len, in_self);
+  segment_sort_count<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, rkeys, rsorted, 0, s->method_class, s->cbo_attrs,
+                                         r_len, in_self);
   MM_LAUNCH_CHECK();
   scan_exclusive_i32to64(r_len, r_off, M, s->sort_ws, st);
   if (nc > 0) {
