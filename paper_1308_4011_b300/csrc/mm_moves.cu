@@ -22,6 +22,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstring>
+#include <vector>
 
 #include "mm_internal.cuh"
 
@@ -1848,6 +1850,11 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
   prepare_candidates(s, cands, &rowptr, &dst, &n_cand, s->stage_ws, &chash);
   int64_t K = 0, nm = 0;
   mm_move *kept = nullptr;
+  // Host outputs of up to BITONIC_MAX kept moves need one round trip: the sort
+  // (which checks the count on the device) and the copy of the first moves
+  // are queued before the count is read back.
+  std::vector<mm_move> staged;
+  bool sorted_early = false;
   if (n_cand > 0 && s->M > 0) {
     EvalCtx cx = make_ctx(s, crit);
     const bool same_cands = rowptr == nullptr ? !s->kept_lists
@@ -1867,6 +1874,14 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
       MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 2, 0, sizeof(unsigned long long), st));
       count_marks<<<148 * 4, 256, 0, st>>>(mark, s->M, s->d_u64 + 2);
       MM_LAUNCH_CHECK();
+      // sorts the kept moves in place when 2 <= K <= min(cap, BITONIC_MAX), else leaves them
+      bitonic_sort_segments<<<1, 1024, 0, st>>>(kept, cap, s->d_u64 + 1);
+      MM_LAUNCH_CHECK();
+      const int64_t nstage = kind == MM_PTR_HOST ? std::min<int64_t>({(int64_t)k, cap, BITONIC_MAX}) : 0;
+      staged.resize((size_t)nstage);
+      if (nstage > 0)
+        MM_CUDA_TRY(cudaMemcpyAsync(staged.data(), kept, sizeof(mm_move) * (size_t)nstage,
+                                    cudaMemcpyDeviceToHost, st));
       unsigned long long hc[2];
       MM_CUDA_TRY(cudaMemcpyAsync(hc, s->d_u64 + 1, sizeof(hc), cudaMemcpyDeviceToHost, st));
       MM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1884,12 +1899,20 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
     s->kept_lists = rowptr != nullptr;
     s->kept_hash = chash;
     s->kept_ncand = n_cand;
-    sort_kept_moves(s, kept, K);
+    sorted_early = K <= BITONIC_MAX;
+    if (!sorted_early) sort_kept_moves(s, kept, K);
   }
-  int64_t nout = std::min<int64_t>(k, K);
-  if (nout > 0)
+  const int64_t nout = std::min<int64_t>(k, K);
+  if (nout > 0) {
+    if (sorted_early && kind == MM_PTR_HOST && (int64_t)staged.size() >= nout) {
+      std::memcpy(out, staged.data(), sizeof(mm_move) * (size_t)nout);
+      if (n_kept) *n_kept = K;
+      if (n_mk) *n_mk = nm;
+      return;
+    }
     MM_CUDA_TRY(cudaMemcpyAsync(out, kept, sizeof(mm_move) * (size_t)nout,
                                 kind == MM_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  }
   MM_CUDA_TRY(cudaStreamSynchronize(st));
   if (n_kept) *n_kept = K;
   if (n_mk) *n_mk = nm;
