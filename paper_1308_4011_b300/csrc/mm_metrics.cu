@@ -315,9 +315,19 @@ UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted, Scratch &ws, cudaSt
 }
 
 namespace {
+// Side streams of one host thread on one device; destroyed with the thread
+// (errors ignored: at process exit the runtime may already be gone).
 struct SideStreams {
   int device = -1;
   cudaStream_t s[2] = {nullptr, nullptr};
+  ~SideStreams() {
+    for (cudaStream_t &x : s)
+      if (x) {
+        cudaSetDevice(device);
+        cudaStreamDestroy(x);
+        x = nullptr;
+      }
+  }
 };
 thread_local SideStreams tl_side[8];
 }  // namespace
@@ -328,6 +338,7 @@ cudaStream_t fork_side(mm_system *s, int i) {
   MM_CUDA_TRY(cudaStreamIsCapturing(s->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) return s->stream;
   SideStreams &ss = tl_side[s->device];
+  ss.device = s->device;
   if (!ss.s[i]) MM_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s[i], cudaStreamNonBlocking));
   MM_CUDA_TRY(cudaEventRecord(s->fork_ev, s->stream));
   MM_CUDA_TRY(cudaStreamWaitEvent(ss.s[i], s->fork_ev, 0));
