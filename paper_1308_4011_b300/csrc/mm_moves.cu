@@ -241,11 +241,12 @@ __global__ void __launch_bounds__(256) segment_sort_count(const int64_t *a, cons
   }
 }
 
-// Fill pass for list L: {E, out, cnt(C, E), t} at l_off[x] + run index, l_x = x.
+// Fill pass for list L: {E, out, -, t} at l_off[x] + run index, l_x = x; the
+// multiplicities cnt(C, E) follow in lists_lookup_l (one thread per entry, so
+// the row searches of all entries are in flight together).
 __global__ void lists_fill_l(const int64_t *call_rowptr, const int64_t *acc_rowptr, int32_t M,
                              const uint32_t *sorted, const int32_t *method_class, int32_t cbo_attrs,
-                             const int64_t *l_off, const int64_t *mg_rowptr, const int32_t *mg_dst,
-                             const int32_t *mg_cnt, int4 *l_list, int32_t *l_x) {
+                             const int64_t *l_off, int4 *l_list, int32_t *l_x) {
   const uint32_t lane = threadIdx.x & 31u;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
@@ -255,18 +256,27 @@ __global__ void lists_fill_l(const int64_t *call_rowptr, const int64_t *acc_rowp
     const int64_t base = l_off[x];
     segment_runs(sorted, p0, len, 1, C, lane, [&](int32_t E, int32_t n0, int32_t n1, int32_t idx) {
       if (E == C) return;
-      const int32_t out = n0 + (cbo_attrs ? n1 : 0);
-      const int32_t cnt = out > 0 ? mg_lookup(mg_rowptr, mg_dst, mg_cnt, C, E) : 0;
-      l_list[base + idx] = make_int4(E, out, cnt, n1);
+      l_list[base + idx] = make_int4(E, n0 + (cbo_attrs ? n1 : 0), 0, n1);
       l_x[base + idx] = (int32_t)x;
     });
   }
 }
 
-// Fill pass for list R: {X, in, cnt(X, C), 0} at r_off[x] + run index.
+// cnt(C, E) of every L entry with a use edge (C = class of its method)
+__global__ void lists_lookup_l(const int64_t *n_l, const int32_t *l_x, const int32_t *method_class,
+                               const int64_t *mg_rowptr, const int32_t *mg_dst, const int32_t *mg_cnt,
+                               int4 *l_list) {
+  const int64_t nl = *n_l;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += (int64_t)gridDim.x * blockDim.x) {
+    const int4 v = l_list[l];
+    if (v.y > 0) l_list[l].z = mg_lookup(mg_rowptr, mg_dst, mg_cnt, method_class[l_x[l]], v.x);
+  }
+}
+
+// Fill pass for list R: {X, in, -, C} at r_off[x] + run index (C, the callee's
+// class, is replaced by cnt(X, C) in lists_lookup_r).
 __global__ void lists_fill_r(const int64_t *rin_off, int32_t M, const uint32_t *sorted,
-                             const int32_t *method_class, const int64_t *r_off, const int64_t *mg_rowptr,
-                             const int32_t *mg_dst, const int32_t *mg_cnt, int4 *r_list) {
+                             const int32_t *method_class, const int64_t *r_off, int4 *r_list) {
   const uint32_t lane = threadIdx.x & 31u;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
@@ -276,8 +286,18 @@ __global__ void lists_fill_r(const int64_t *rin_off, int32_t M, const uint32_t *
     const int64_t base = r_off[x];
     segment_runs(sorted, p0, len, 0, C, lane, [&](int32_t X, int32_t n0, int32_t, int32_t idx) {
       if (X == C) return;
-      r_list[base + idx] = make_int4(X, n0, mg_lookup(mg_rowptr, mg_dst, mg_cnt, X, C), 0);
+      r_list[base + idx] = make_int4(X, n0, 0, C);
     });
+  }
+}
+
+// cnt(X, C) of every R entry: {X, in, cnt(X, C), 0}
+__global__ void lists_lookup_r(const int64_t *n_r, const int64_t *mg_rowptr, const int32_t *mg_dst,
+                               const int32_t *mg_cnt, int4 *r_list) {
+  const int64_t nr = *n_r;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
+    const int4 v = r_list[r];
+    r_list[r] = make_int4(v.x, v.y, mg_lookup(mg_rowptr, mg_dst, mg_cnt, v.x, v.w), 0);
   }
 }
 
@@ -364,8 +384,13 @@ void build_move_precompute(mm_system *s) {
     MM_LAUNCH_CHECK();
     scan_exclusive_i32to64(l_len, l_off, M, sw_, sl, l_off + M);
     lists_fill_l<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lsorted, s->method_class, s->cbo_attrs,
-                                     l_off, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list, s->l_x);
+                                     l_off, s->l_list, s->l_x);
     MM_LAUNCH_CHECK();
+    if (nu > 0) {
+      lists_lookup_l<<<(unsigned)std::min<int64_t>(ceil_div(nu, TPB), 148 * 16), TPB, 0, sl>>>(
+          l_off + M, s->l_x, s->method_class, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list);
+      MM_LAUNCH_CHECK();
+    }
     if (nu > 0) {
       const UnionBitmap ub = union_bitmap(s, ceil_div(nu, 32), uw, sl);
       l_entries_s<<<ub.grid, 256, ub.smem, sl>>>(s->l_list, s->l_x, l_off + M, s->acc_rowptr, s->acc_idx,
@@ -385,10 +410,12 @@ void build_move_precompute(mm_system *s) {
   segment_sort_count<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, rkeys, rsorted, 0, s->method_class, s->cbo_attrs,
                                          r_len, in_self);
   MM_LAUNCH_CHECK();
-  scan_exclusive_i32to64(r_len, r_off, M, s->sort_ws, st);
+  scan_exclusive_i32to64(r_len, r_off, M, s->sort_ws, st, r_off + M);
   if (nc > 0) {
-    lists_fill_r<<<gw, TPB, 0, st>>>(rin_off, M, rsorted, s->method_class, r_off, s->mg_rowptr, s->mg_dst,
-                                     s->mg_cnt, s->r_list);
+    lists_fill_r<<<gw, TPB, 0, st>>>(rin_off, M, rsorted, s->method_class, r_off, s->r_list);
+    MM_LAUNCH_CHECK();
+    lists_lookup_r<<<(unsigned)std::min<int64_t>(ceil_div(nc, TPB), 148 * 16), TPB, 0, st>>>(
+        r_off + M, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->r_list);
     MM_LAUNCH_CHECK();
   }
   join_side(s, 1, sl);
