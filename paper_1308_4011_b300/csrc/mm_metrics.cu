@@ -141,18 +141,22 @@ __device__ __forceinline__ void mark_use(uint32_t *out_adj, uint2 *csum, int64_t
 __global__ void coupling_mark(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
                               const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
                               int32_t M, int32_t cbo_attrs, uint32_t *out_adj, int64_t aw, uint2 *csum,
-                              int64_t sw) {
+                              int64_t sw, uint64_t *edges) {
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
   const int32_t Y = method_class[x];
+  // edge keys (Y << 32 | E, or ~0 inside the class) at the method's calls, then its accesses
+  int64_t pos = call_rowptr[x] + (cbo_attrs ? acc_rowptr[x] : 0);
   for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e) {
     const int32_t E = method_class[call_idx[e]];
     if (E != Y) mark_use(out_adj, csum, aw, sw, Y, E);
+    edges[pos++] = E != Y ? ((uint64_t)(uint32_t)Y << 32) | (uint32_t)E : ~0ull;
   }
   if (cbo_attrs)
     for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
       const int32_t E = attr_class[acc_idx[e]];
       if (E != Y) mark_use(out_adj, csum, aw, sw, Y, E);
+      edges[pos++] = E != Y ? ((uint64_t)(uint32_t)Y << 32) | (uint32_t)E : ~0ull;
     }
 }
 
@@ -226,33 +230,21 @@ __global__ void row_enumerate(uint2 *csum, const uint32_t *out_adj, uint32_t *in
   }
 }
 
-__device__ __forceinline__ void count_use(const int64_t *mg_rowptr, const int32_t *mg_dst, int32_t *mg_cnt,
-                                          int32_t Y, int32_t E) {
-  int64_t lo = mg_rowptr[Y], hi = mg_rowptr[Y + 1];
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (mg_dst[mid] < E) lo = mid + 1; else hi = mid;
-  }
-  atomicAdd(&mg_cnt[lo], 1);
-}
-
-// Pass 4: multiplicities cnt[Y][E] = number of use edges (binary search of E in row Y).
-__global__ void coupling_count(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
-                               const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
-                               int32_t M, int32_t cbo_attrs, const int64_t *mg_rowptr, const int32_t *mg_dst,
+// Pass 4: multiplicities cnt[Y][E] = number of use edges, one thread per edge
+// (binary search of E in row Y).
+__global__ void coupling_count(const uint64_t *edges, int64_t n, const int64_t *mg_rowptr, const int32_t *mg_dst,
                                int32_t *mg_cnt) {
-  int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= M) return;
-  const int32_t Y = method_class[x];
-  for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e) {
-    const int32_t E = method_class[call_idx[e]];
-    if (E != Y) count_use(mg_rowptr, mg_dst, mg_cnt, Y, E);
-  }
-  if (cbo_attrs)
-    for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
-      const int32_t E = attr_class[acc_idx[e]];
-      if (E != Y) count_use(mg_rowptr, mg_dst, mg_cnt, Y, E);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = edges[i];
+    if (k == ~0ull) continue;
+    const int32_t Y = (int32_t)(k >> 32), E = (int32_t)(uint32_t)k;
+    int64_t lo = mg_rowptr[Y], hi = mg_rowptr[Y + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (mg_dst[mid] < E) lo = mid + 1; else hi = mid;
     }
+    atomicAdd(&mg_cnt[lo], 1);
+  }
 }
 
 __global__ void summary_popc(const uint2 *sum, int64_t n, int32_t *cnt) {
@@ -403,10 +395,12 @@ void build_metrics(mm_system *s) {
   MM_CUDA_TRY(cudaMemsetAsync(s->in_adj, 0, sizeof(uint32_t) * (size_t)(aw * c), st));
   MM_CUDA_TRY(cudaMemsetAsync(s->csum, 0, sizeof(uint2) * (size_t)(sw * (2 * c + 1)), st));
   int32_t *row_count = s->cls_cbo;
+  const int64_t nk = s->n_call + (s->cbo_attrs ? s->n_acc : 0);
+  uint64_t *edges = static_cast<uint64_t *>(s->eval_ws.need(sizeof(uint64_t) * (size_t)std::max<int64_t>(nk, 1), st));
   if (M > 0) {
     coupling_mark<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
                                                s->acc_idx, s->attr_class, M, s->cbo_attrs, s->out_adj, aw,
-                                               s->csum, sw);
+                                               s->csum, sw, edges);
     MM_LAUNCH_CHECK();
   }
   const unsigned grow = (unsigned)std::min<int64_t>(ceil_div((int64_t)c * 32, TPB), 148 * 16);
@@ -418,9 +412,8 @@ void build_metrics(mm_system *s) {
                                       s->mg_cnt);
   MM_LAUNCH_CHECK();
   if (M > 0) {
-    coupling_count<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
-                                                s->acc_idx, s->attr_class, M, s->cbo_attrs, s->mg_rowptr,
-                                                s->mg_dst, s->mg_cnt);
+    coupling_count<<<(unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(nk, 1), TPB), 148 * 16), TPB, 0, st>>>(
+        edges, nk, s->mg_rowptr, s->mg_dst, s->mg_cnt);
     MM_LAUNCH_CHECK();
   }
   MM_CUDA_TRY(cudaMemcpyAsync(s->mg_count, s->mg_rowptr + c, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
