@@ -183,18 +183,82 @@ __device__ __forceinline__ int32_t segment_runs(const uint32_t *keys, int64_t p0
   return __shfl_sync(0xffffffffu, idx, 0);
 }
 
-// Sort and count in one pass: one warp sorts the segment (a segment of at most
+// Sort and count, block version: a block of 256 threads takes 256 consecutive
+// segments, whose keys are one contiguous range; it loads the range into shared
+// memory (coalesced), each thread sorts its own segment there (insertion sort)
+// and walks its runs, and the block writes the sorted range back.  Segments of
+// more than SB_SEG keys, and every segment of a block whose range exceeds
+// SB_KEYS, are left to the warp version (flag set).
+constexpr int SB_KEYS = 6144;
+constexpr int SB_SEG = 64;
+
+__global__ void __launch_bounds__(256) segment_sort_count_block(const int64_t *a, const int64_t *b, int32_t M,
+                                                                const uint32_t *in, uint32_t *out, int shift,
+                                                                const int32_t *method_class, int32_t cbo_attrs,
+                                                                int32_t *len_out, int32_t *self_out,
+                                                                uint8_t *long_seg) {
+  __shared__ uint32_t sk[SB_KEYS];
+  const int64_t x0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t xl = (x0 + (int64_t)blockDim.x < (int64_t)M ? x0 + (int64_t)blockDim.x : (int64_t)M) - 1;
+  int64_t q0, l0, ql, ll;
+  segment(a, b, x0, &q0, &l0);
+  segment(a, b, xl, &ql, &ll);
+  const int64_t K0 = q0, nk = ql + ll - q0;
+  const bool fits = nk <= SB_KEYS;
+  if (fits)
+    for (int64_t k = threadIdx.x; k < nk; k += blockDim.x) sk[k] = in[K0 + k];
+  __syncthreads();
+  const int64_t x = x0 + threadIdx.x;
+  if (x < M) {
+    int64_t p0, len;
+    segment(a, b, x, &p0, &len);
+    if (!fits || len > SB_SEG) {
+      long_seg[x] = 1;
+    } else {
+      long_seg[x] = 0;
+      uint32_t *v = sk + (p0 - K0);
+      for (int32_t i = 1; i < (int32_t)len; ++i) {  // insertion sort (stable)
+        const uint32_t key = v[i];
+        int32_t j = i - 1;
+        while (j >= 0 && v[j] > key) {
+          v[j + 1] = v[j];
+          --j;
+        }
+        v[j + 1] = key;
+      }
+      const int32_t C = method_class[x];
+      int32_t n = 0, self = 0;
+      for (int32_t i = 0; i < (int32_t)len;) {
+        const uint32_t E = v[i] >> shift;
+        int32_t n0 = 0, n1 = 0;
+        for (; i < (int32_t)len && (v[i] >> shift) == E; ++i) ((shift && (v[i] & 1u)) ? n1 : n0)++;
+        if ((int32_t)E == C) self = n0 + (cbo_attrs ? n1 : 0);
+        else ++n;
+      }
+      len_out[x] = n;
+      self_out[x] = self;
+    }
+  }
+  __syncthreads();
+  if (fits)
+    for (int64_t k = threadIdx.x; k < nk; k += blockDim.x) out[K0 + k] = sk[k];
+}
+
+// Sort and count in one pass, warp version (segments the block version left):
+// one warp sorts the segment (a segment of at most
 // 32 keys also into its shared-memory row, read back for the run walk), then
 // counts the runs: l_len / r_len per method and the own-class run (out_self /
 // in_self).
 __global__ void __launch_bounds__(256) segment_sort_count(const int64_t *a, const int64_t *b, int32_t M,
                                                           const uint32_t *in, uint32_t *out, int shift,
                                                           const int32_t *method_class, int32_t cbo_attrs,
-                                                          int32_t *len_out, int32_t *self_out) {
+                                                          int32_t *len_out, int32_t *self_out,
+                                                          const uint8_t *only) {
   __shared__ uint32_t sk[8][32];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
+    if (only && !only[x]) continue;  // done by the block version
     int64_t p0, len;
     segment(a, b, x, &p0, &len);
     const uint32_t *runs_keys;
@@ -354,7 +418,7 @@ void build_move_precompute(mm_system *s) {
     return (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nkeys, 1) + 15) / 16 * 16 +
            sizeof(int64_t) * (size_t)n64 * ((size_t)M + 1) + sizeof(int32_t) * (size_t)n32 * (size_t)M + 64;
   };
-  const size_t lb = (part_bytes(nu, 1, 2) + 255) / 256 * 256, rbytes = part_bytes(nc, 2, 3);
+  const size_t lb = (part_bytes(nu, 1, 2) + (size_t)M + 255) / 256 * 256, rbytes = part_bytes(nc, 2, 3) + (size_t)M;
   // the branches use their own scratch whether or not they run concurrently, so
   // the buffers (and a captured graph's pointers) do not depend on the mode
   char *lbase = static_cast<char *>(s->side_eval[1].need(lb, sl));
@@ -363,12 +427,14 @@ void build_move_precompute(mm_system *s) {
   int64_t *l_off = reinterpret_cast<int64_t *>(lbase + (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nu, 1) + 15) / 16 * 16);
   int32_t *l_len = reinterpret_cast<int32_t *>(l_off + (M + 1));
   int32_t *out_self = l_len + M;
+  uint8_t *llong = reinterpret_cast<uint8_t *>(out_self + M);  // segments left to the warp version
   uint32_t *rkeys = reinterpret_cast<uint32_t *>(rbase), *rsorted = rkeys + std::max<int64_t>(nc, 1);
   int64_t *rin_off = reinterpret_cast<int64_t *>(rbase + (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nc, 1) + 15) / 16 * 16);
   int64_t *r_off = rin_off + (M + 1);
   int32_t *r_len = reinterpret_cast<int32_t *>(r_off + (M + 1));
   int32_t *in_self = r_len + M;
   int32_t *cursor = in_self + M;
+  uint8_t *rlong = reinterpret_cast<uint8_t *>(cursor + M);
 
   // list L: per-method sort of the use keys, runs counted, scanned, written; s per entry
   {
@@ -379,8 +445,11 @@ void build_move_precompute(mm_system *s) {
                                                      s->acc_idx, s->attr_class, M, lkeys);
       MM_LAUNCH_CHECK();
     }
+    segment_sort_count_block<<<grid_for(M), 256, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lkeys, lsorted, 1,
+                                                          s->method_class, s->cbo_attrs, l_len, out_self, llong);
+    MM_LAUNCH_CHECK();
     segment_sort_count<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lkeys, lsorted, 1, s->method_class,
-                                           s->cbo_attrs, l_len, out_self);
+                                           s->cbo_attrs, l_len, out_self, llong);
     MM_LAUNCH_CHECK();
     scan_exclusive_i32to64(l_len, l_off, M, sw_, sl, l_off + M);
     lists_fill_l<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lsorted, s->method_class, s->cbo_attrs,
@@ -407,8 +476,11 @@ void build_move_precompute(mm_system *s) {
                                                         cursor, rkeys);
     MM_LAUNCH_CHECK();
   }
+  segment_sort_count_block<<<grid_for(M), 256, 0, st>>>(rin_off, nullptr, M, rkeys, rsorted, 0, s->method_class,
+                                                        s->cbo_attrs, r_len, in_self, rlong);
+  MM_LAUNCH_CHECK();
   segment_sort_count<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, rkeys, rsorted, 0, s->method_class, s->cbo_attrs,
-                                         r_len, in_self);
+                                         r_len, in_self, rlong);
   MM_LAUNCH_CHECK();
   scan_exclusive_i32to64(r_len, r_off, M, s->sort_ws, st, r_off + M);
   if (nc > 0) {
