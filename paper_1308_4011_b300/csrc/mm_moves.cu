@@ -307,22 +307,39 @@ __global__ void __launch_bounds__(256) segment_sort_count(const int64_t *a, cons
 
 // Fill pass for list L: {E, out, -, t} at l_off[x] + run index, l_x = x; the
 // multiplicities cnt(C, E) follow in lists_lookup_l (one thread per entry, so
-// the row searches of all entries are in flight together).
-__global__ void lists_fill_l(const int64_t *call_rowptr, const int64_t *acc_rowptr, int32_t M,
-                             const uint32_t *sorted, const int32_t *method_class, int32_t cbo_attrs,
-                             const int64_t *l_off, int4 *l_list, int32_t *l_x) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
-    int64_t p0, len;
-    segment(call_rowptr, acc_rowptr, x, &p0, &len);
-    const int32_t C = method_class[x];
-    const int64_t base = l_off[x];
-    segment_runs(sorted, p0, len, 1, C, lane, [&](int32_t E, int32_t n0, int32_t n1, int32_t idx) {
-      if (E == C) return;
-      l_list[base + idx] = make_int4(E, n0 + (cbo_attrs ? n1 : 0), 0, n1);
-      l_x[base + idx] = (int32_t)x;
-    });
+// the row searches of all entries are in flight together).  A block takes 256
+// consecutive methods: their sorted keys are one contiguous range, loaded into
+// shared memory when it fits, and each thread walks its own method's runs.
+__global__ void __launch_bounds__(256) lists_fill_l(const int64_t *call_rowptr, const int64_t *acc_rowptr, int32_t M,
+                                                    const uint32_t *sorted, const int32_t *method_class,
+                                                    int32_t cbo_attrs, const int64_t *l_off, int4 *l_list,
+                                                    int32_t *l_x) {
+  __shared__ uint32_t sk[SB_KEYS];
+  const int64_t x0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t xl = (x0 + (int64_t)blockDim.x < (int64_t)M ? x0 + (int64_t)blockDim.x : (int64_t)M) - 1;
+  int64_t q0, l0, ql, ll;
+  segment(call_rowptr, acc_rowptr, x0, &q0, &l0);
+  segment(call_rowptr, acc_rowptr, xl, &ql, &ll);
+  const int64_t nk = ql + ll - q0;
+  const bool fits = nk <= SB_KEYS;
+  if (fits)
+    for (int64_t k = threadIdx.x; k < nk; k += blockDim.x) sk[k] = sorted[q0 + k];
+  __syncthreads();
+  const int64_t x = x0 + threadIdx.x;
+  if (x >= M) return;
+  int64_t p0, len;
+  segment(call_rowptr, acc_rowptr, x, &p0, &len);
+  const uint32_t *v = fits ? sk + (p0 - q0) : sorted + p0;
+  const int32_t C = method_class[x];
+  int64_t o = l_off[x];
+  for (int32_t i = 0; i < (int32_t)len;) {
+    const int32_t E = (int32_t)(v[i] >> 1);
+    int32_t n0 = 0, n1 = 0;
+    for (; i < (int32_t)len && (int32_t)(v[i] >> 1) == E; ++i) ((v[i] & 1u) ? n1 : n0)++;
+    if (E == C) continue;
+    l_list[o] = make_int4(E, n0 + (cbo_attrs ? n1 : 0), 0, n1);
+    l_x[o] = (int32_t)x;
+    ++o;
   }
 }
 
@@ -338,20 +355,30 @@ __global__ void lists_lookup_l(const int64_t *n_l, const int32_t *l_x, const int
 }
 
 // Fill pass for list R: {X, in, -, C} at r_off[x] + run index (C, the callee's
-// class, is replaced by cnt(X, C) in lists_lookup_r).
-__global__ void lists_fill_r(const int64_t *rin_off, int32_t M, const uint32_t *sorted,
-                             const int32_t *method_class, const int64_t *r_off, int4 *r_list) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
-    int64_t p0, len;
-    segment(rin_off, nullptr, x, &p0, &len);
-    const int32_t C = method_class[x];
-    const int64_t base = r_off[x];
-    segment_runs(sorted, p0, len, 0, C, lane, [&](int32_t X, int32_t n0, int32_t, int32_t idx) {
-      if (X == C) return;
-      r_list[base + idx] = make_int4(X, n0, 0, C);
-    });
+// class, is replaced by cnt(X, C) in lists_lookup_r); blocks as for list L.
+__global__ void __launch_bounds__(256) lists_fill_r(const int64_t *rin_off, int32_t M, const uint32_t *sorted,
+                                                    const int32_t *method_class, const int64_t *r_off,
+                                                    int4 *r_list) {
+  __shared__ uint32_t sk[SB_KEYS];
+  const int64_t x0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t xl = (x0 + (int64_t)blockDim.x < (int64_t)M ? x0 + (int64_t)blockDim.x : (int64_t)M) - 1;
+  const int64_t q0 = rin_off[x0], nk = rin_off[xl + 1] - q0;
+  const bool fits = nk <= SB_KEYS;
+  if (fits)
+    for (int64_t k = threadIdx.x; k < nk; k += blockDim.x) sk[k] = sorted[q0 + k];
+  __syncthreads();
+  const int64_t x = x0 + threadIdx.x;
+  if (x >= M) return;
+  const int64_t p0 = rin_off[x], len = rin_off[x + 1] - p0;
+  const uint32_t *v = fits ? sk + (p0 - q0) : sorted + p0;
+  const int32_t C = method_class[x];
+  int64_t o = r_off[x];
+  for (int64_t i = 0; i < len;) {
+    const int32_t X = (int32_t)v[i];
+    int32_t n0 = 0;
+    for (; i < len && (int32_t)v[i] == X; ++i) ++n0;
+    if (X == C) continue;
+    r_list[o++] = make_int4(X, n0, 0, C);
   }
 }
 
@@ -452,8 +479,8 @@ void build_move_precompute(mm_system *s) {
                                            s->cbo_attrs, l_len, out_self, llong);
     MM_LAUNCH_CHECK();
     scan_exclusive_i32to64(l_len, l_off, M, sw_, sl, l_off + M);
-    lists_fill_l<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lsorted, s->method_class, s->cbo_attrs,
-                                     l_off, s->l_list, s->l_x);
+    lists_fill_l<<<grid_for(M), 256, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lsorted, s->method_class,
+                                               s->cbo_attrs, l_off, s->l_list, s->l_x);
     MM_LAUNCH_CHECK();
     if (nu > 0) {
       lists_lookup_l<<<(unsigned)std::min<int64_t>(ceil_div(nu, TPB), 148 * 16), TPB, 0, sl>>>(
@@ -484,7 +511,7 @@ void build_move_precompute(mm_system *s) {
   MM_LAUNCH_CHECK();
   scan_exclusive_i32to64(r_len, r_off, M, s->sort_ws, st, r_off + M);
   if (nc > 0) {
-    lists_fill_r<<<gw, TPB, 0, st>>>(rin_off, M, rsorted, s->method_class, r_off, s->r_list);
+    lists_fill_r<<<grid_for(M), 256, 0, st>>>(rin_off, M, rsorted, s->method_class, r_off, s->r_list);
     MM_LAUNCH_CHECK();
     lists_lookup_r<<<(unsigned)std::min<int64_t>(ceil_div(nc, TPB), 148 * 16), TPB, 0, st>>>(
         r_off + M, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->r_list);
