@@ -1539,17 +1539,22 @@ __global__ void validate_cand_dst(const int64_t *rowptr, const int32_t *dst, con
   uint64_t h = 0;
   if (i_begin < i_end) {
     int32_t m = owner_of(rowptr, M, i_begin);  // one search per warp, then forward scans
-    for (int64_t i0 = i_begin; i0 < i_end; i0 += 32) {
-      const int64_t i = i0 + lane;
-      int32_t mi = m;
-      if (i < i_end) {
-        while (mi < M && rowptr[mi + 1] <= i) ++mi;
-        const int32_t D = dst[i];
-        if (D < 0 || D >= c) e |= VE_CAND_RANGE;
-        else if (mi < M && D == method_class[mi]) e |= VE_CAND_SELF;
-        h += cand_mix(((uint64_t)i << 32) | (uint32_t)D);
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += 128) {
+      // four independent entries per lane: their scans and loads overlap
+      int32_t mi[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + 32 * u + lane;
+        mi[u] = m;
+        if (i < i_end) {
+          while (mi[u] < M && rowptr[mi[u] + 1] <= i) ++mi[u];
+          const int32_t D = dst[i];
+          if (D < 0 || D >= c) e |= VE_CAND_RANGE;
+          else if (mi[u] < M && D == method_class[mi[u]]) e |= VE_CAND_SELF;
+          h += cand_mix(((uint64_t)i << 32) | (uint32_t)D);
+        }
       }
-      m = __shfl_sync(0xffffffffu, mi, 31);
+      m = __shfl_sync(0xffffffffu, max(max(mi[0], mi[1]), max(mi[2], mi[3])), 31);
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -1658,6 +1663,15 @@ __device__ __forceinline__ void bitonic_block(mm_move *v, int32_t n, mm_move *sm
 __global__ void __launch_bounds__(1024) bitonic_sort_moves(mm_move *v, int32_t n) {
   __shared__ mm_move sm[BITONIC_MAX];
   bitonic_block(v, n, sm);
+}
+
+// One block with dynamic shared memory (next power of two >= n moves, at most
+// BITONIC_BIG): the same bitonic sort for kept lists past the static limit.
+constexpr int BITONIC_BIG = 8192;
+
+__global__ void __launch_bounds__(1024) bitonic_sort_moves_big(mm_move *v, int32_t n) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  bitonic_block(v, n, reinterpret_cast<mm_move *>(bsm));
 }
 
 // block i sorts segment i (base + i*stride, counts[i] moves) when it fits in one block
@@ -1790,9 +1804,9 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
     validate_cand_rows<<<grid_for(s->M), TPB, 0, st>>>(*rowptr, s->M, *n_cand, s->d_err, s->d_u64 + 3);
     MM_LAUNCH_CHECK();
     if (*n_cand > 0) {
-      // one contiguous range per warp (a multiple of 32 entries), at most 148 x 16 blocks of 8 warps
-      const int64_t warps = std::min<int64_t>(ceil_div(*n_cand, 32), (int64_t)148 * 16 * (TPB / 32));
-      const int64_t per_warp = ceil_div(ceil_div(*n_cand, warps), 32) * 32;
+      // one contiguous range per warp (a multiple of 128 entries), at most 148 x 16 blocks of 8 warps
+      const int64_t warps = std::min<int64_t>(ceil_div(*n_cand, 128), (int64_t)148 * 16 * (TPB / 32));
+      const int64_t per_warp = ceil_div(ceil_div(*n_cand, warps), 128) * 128;
       const unsigned g = (unsigned)ceil_div(ceil_div(*n_cand, per_warp) * 32, TPB);
       validate_cand_dst<<<g, TPB, 0, st>>>(*rowptr, *dst, s->method_class, s->M, s->c, *n_cand, per_warp,
                                           s->d_err, s->d_u64 + 3);
@@ -1906,7 +1920,15 @@ void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K) {
   if (K > 1 && K <= BITONIC_MAX) {
     bitonic_sort_moves<<<1, 1024, 0, st>>>(kept, (int32_t)K);
     MM_LAUNCH_CHECK();
-  } else if (K > BITONIC_MAX) {
+  } else if (K > BITONIC_MAX && K <= BITONIC_BIG) {
+    int32_t np = 1;
+    while (np < K) np <<= 1;
+    const size_t smem = sizeof(mm_move) * (size_t)np;
+    MM_CUDA_TRY(cudaFuncSetAttribute(bitonic_sort_moves_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(mm_move) * BITONIC_BIG)));
+    bitonic_sort_moves_big<<<1, 1024, smem, st>>>(kept, (int32_t)K);
+    MM_LAUNCH_CHECK();
+  } else if (K > BITONIC_BIG) {
     // the fields' actual ranges decide whether one 64-bit composite key holds them all
     int32_t *d_mm = reinterpret_cast<int32_t *>(s->d_u64 + 24);
     const int32_t init[6] = {INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN};
