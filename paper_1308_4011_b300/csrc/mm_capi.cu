@@ -243,8 +243,9 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
       MM_CUDA_TRY(cudaMemsetAsync(s->call_rowptr, 0, sizeof(int64_t), stv));
     }
     load_validate_and_summarise(s);
+    allocate_compute_buffers(s);  // host allocation calls overlap the checks on the device
+    load_finish(s);
     if (s->summary.err) throw MmError{MM_EINVAL, "load_system: " + describe(s->summary.err)};
-    allocate_compute_buffers(s);
     *out = s;
   });
   if (st != MM_OK && s) {

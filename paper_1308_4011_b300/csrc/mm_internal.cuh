@@ -120,6 +120,7 @@ struct mm_system {
   int32_t c = 0, M = 0, A = 0, cbo_attrs = 1;
   int64_t n_acc = 0, n_call = 0;
   LoadSummary summary{};
+  uint32_t load_err = 0;           // validation word read back at load (host)
   bool metrics_ready = false;
   bool methods_by_class = false;   // method ids contiguous by class: no sort needed
   bool attrs_by_class = false;
@@ -214,6 +215,7 @@ void radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t
 // ---------------------------------------------------------------- pipeline stages
 
 void load_validate_and_summarise(mm_system *s);     // mm_system.cu
+void load_finish(mm_system *s);                     // mm_system.cu
 void build_structures(mm_system *s);                // mm_system.cu
 // Per-warp bitmaps for accessor unions over the methods of one class: words
 // per warp (largest class), shared-memory bytes per block of 256 threads, or a

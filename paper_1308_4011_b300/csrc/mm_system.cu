@@ -174,6 +174,8 @@ __global__ void fan_in_hist(const int32_t *call_idx, int64_t n_call, int32_t *fa
 
 }  // namespace
 
+// Queue the load checks (validation, class histograms, load summary);
+// load_finish reads their results back.
 void load_validate_and_summarise(mm_system *s) {
   cudaStream_t st = s->stream;
   MM_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(uint32_t), st));
@@ -193,15 +195,21 @@ void load_validate_and_summarise(mm_system *s) {
   MM_CUDA_TRY(cudaMemsetAsync(dsum, 0, sizeof(LoadSummary), st));
   summarise_classes<<<grid_for(s->c), TPB, 0, st>>>(s->cls_n, s->c, dsum);
   MM_LAUNCH_CHECK();
-  LoadSummary h{};
-  MM_CUDA_TRY(cudaMemcpyAsync(&h, dsum, sizeof(LoadSummary), cudaMemcpyDeviceToHost, st));
-  uint32_t err = 0;
-  MM_CUDA_TRY(cudaMemcpyAsync(&err, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+}
+
+// Read back and wait for the load checks queued by load_validate_and_summarise
+// (the caller may allocate in between: a read-back into pageable memory blocks
+// the host, so it comes last).
+void load_finish(mm_system *s) {
+  cudaStream_t st = s->stream;
+  MM_CUDA_TRY(cudaMemcpyAsync(&s->summary, reinterpret_cast<LoadSummary *>(s->d_u64 + 4), sizeof(LoadSummary),
+                              cudaMemcpyDeviceToHost, st));
+  MM_CUDA_TRY(cudaMemcpyAsync(&s->load_err, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   MM_CUDA_TRY(cudaStreamSynchronize(st));
-  h.err = err & VE_ERRORS;
+  const uint32_t err = s->load_err;
+  s->summary.err = err & VE_ERRORS;
   s->methods_by_class = !(err & VI_METHODS_UNSORTED);
   s->attrs_by_class = !(err & VI_ATTRS_UNSORTED);
-  s->summary = h;
 }
 
 namespace {
