@@ -762,12 +762,33 @@ struct DenseStage {
   uint4 word[DB_ECAP][DB_WARPS];  // [slot][w] = contribution words w, w+8, w+16, w+24
   uint4 cw[DB_MB][2][DB_WARPS];   // adjacency words of row C: [0] = in_adj (D uses C), [1] = out_adj (C uses D)
   int16_t hit[DB_ECAP];           // slots whose class lies in the block's span
-  uint32_t hitw[DB_MB][DB_SPAN / 32];  // per method: bit rel set iff D0 + rel is in one of its lists
-  // source-side outcome of method j for b = [m's callers in C make C start using D]:
-  //   pc = improved + (worsened << 16) of class C, fc = sign bits 0-5, rc = record word 1 (dCBO(C) << 16)
-  int32_t pc[DB_MB][2], fc[DB_MB][2], rc[DB_MB][2];
+  uint4 hitw[DB_MB][DB_WARPS];    // per method: bit rel set iff D0 + rel is in one of its lists;
+                                  // word g = w + 8 q is stored at [w] component q (as word)
+  // per method, for b = [m's callers in C make C start using D] (bytes replicated over the four
+  // destinations of a thread, plus their change from b = 0 to b = 1):
+  //   [0] = {improved of C, worsened of C, change, change},
+  //   [1] = {flag bits 0-5 (C's signs), change, record word 1 (dCBO(C) << 16), change},
+  //   [2] = {C, 0x01010101 if m uses members of C, 0x01010101 if methods of C call m, 0}
+  int4 mc[DB_MB][3];
   int32_t k, overflow;
 };
+
+// Bit `lane` of each word of v as one byte (0 or 1) per word; gsel picks the
+// byte of a word that holds the bit, gsh its position there.
+__device__ __forceinline__ uint32_t lane_bits4(const uint4 &v, uint32_t gsel, uint32_t gsh) {
+  const uint32_t lo = __byte_perm(v.x, v.y, gsel), hi = __byte_perm(v.z, v.w, gsel);
+  return (__byte_perm(lo, hi, 0x5410) >> gsh) & 0x01010101u;
+}
+// 1 in each byte of x that is not zero.
+__device__ __forceinline__ uint32_t bytes_nonzero(uint32_t x) {
+  return ((((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x) >> 7) & 0x01010101u;
+}
+// 1 in each byte of x that is >= t, given k9 = (256 - t) * 0x00010001 for t in [0, 256]:
+// each byte plus 256 - t, in a 16-bit lane, carries into bit 8 exactly when byte >= t.
+__device__ __forceinline__ uint32_t bytes_ge(uint32_t x, uint32_t k9) {
+  const uint32_t ev = (x & 0x00ff00ffu) + k9, od = ((x >> 8) & 0x00ff00ffu) + k9;
+  return ((ev >> 8) & 0x00010001u) | (od & 0x01000100u);
+}
 
 __device__ __forceinline__ uint32_t sel4(const uint4 &v, int q) {
   return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
@@ -775,6 +796,11 @@ __device__ __forceinline__ uint32_t sel4(const uint4 &v, int q) {
 
 __device__ __forceinline__ int32_t clamp16(int32_t v) { return max(-32768, min(32767, v)); }
 __device__ __forceinline__ uint32_t enc_small(int32_t v) { return (uint32_t)(v < 0) | ((uint32_t)(v > 0) << 1); }
+
+// Word g of method j's hit bitmap (stored so that a warp's four words form one uint4).
+__device__ __forceinline__ uint32_t *hit_word(DenseStage &st, int32_t j, int32_t g) {
+  return reinterpret_cast<uint32_t *>(&st.hitw[j][0]) + ((g & 7) * 4 + (g >> 3));
+}
 
 // Rare paths of the dense kernel, kept out of line so they do not cost the
 // common path registers.
@@ -852,22 +878,30 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
   const int64_t dw0 = D0 >> 5;
   const uint32_t mk = cx.mask;
   const int32_t mk4 = (mk & 4u) ? 1 : 0;
-  // destination constants: target outcome when m shares nothing with D, for
-  // p = [dCBO(D) > 0] (in that case dCBO(D) >= 0): pd = improved + (worsened << 16),
-  // fd = sign bits 6-11
-  int32_t pd0[DQ], pd1[DQ], fd0[DQ], dck0[DQ];
+  // destination constants of the common path (m shares nothing with D), one
+  // byte per destination q of this thread: improved / worsened counts of D for
+  // p = [dCBO(D) > 0] = 0 (pdi, pdw) and their change when p = 1 (-negi, +posw;
+  // only CBO moves with p), D's sign bits of the flags (bits 6-7 in fdlo, 8-9 in
+  // fdhi) and whether D exists
+  uint32_t pdi = 0u, pdw = 0u, negi = 0u, posw = 0u, fdlo = 0u, fdhi = 0u, valid = 0u;
 #pragma unroll
   for (int q = 0; q < DQ; ++q) {
     const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
     DState ds = load_dstate(D < c ? D : 0, cls_n, cls_a, cls_P, cls_Q, cls_S);
-    const int32_t up = ((mk & 1u) && ds.sck0 > 0) | ((mk & 2u) && ds.shs0 > 0);
-    const int32_t dn = ((mk & 1u) && ds.sck0 < 0) | ((mk & 2u) && ds.shs0 < 0);
-    const int32_t up1 = up | mk4;
-    pd0[q] = (dn & (up ^ 1)) + (up << 16);
-    pd1[q] = (dn & (up1 ^ 1)) + (up1 << 16);
-    fd0[q] = (int32_t)((enc_sign(ds.sck0) << 6) | (enc_sign(ds.shs0) << 8));
-    dck0[q] = ds.dck0;
+    const uint32_t up = ((mk & 1u) && ds.sck0 > 0) | ((mk & 2u) && ds.shs0 > 0);
+    const uint32_t dn = ((mk & 1u) && ds.sck0 < 0) | ((mk & 2u) && ds.shs0 < 0);
+    const uint32_t sh = 8u * (uint32_t)q;
+    pdi |= (dn & (up ^ 1u)) << sh;
+    pdw |= up << sh;
+    negi |= (dn & (up ^ 1u) & (uint32_t)mk4) << sh;
+    posw |= ((up ^ 1u) & (uint32_t)mk4) << sh;
+    fdlo |= (enc_sign(ds.sck0) << 6) << sh;
+    fdhi |= enc_sign(ds.shs0) << sh;
+    valid |= (uint32_t)(D < c) << sh;
   }
+  const uint32_t gsel = (lane >> 3) | (((lane >> 3) + 4u) << 4), gsh = lane & 7u;
+  const int32_t mi = min(max(cx.min_improved, 0), 256);
+  const uint32_t k9 = (uint32_t)(256 - mi) * 0x00010001u;
   const int64_t row = (int64_t)c - 1;
   const int64_t seg_words = cx.aw - dw0;  // adjacency words left in a row from dw0 (may exceed 32)
   uint64_t dig = 0;
@@ -903,14 +937,21 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
         const int sckC = dec_sign(sC & 3u), shsC = dec_sign(sC >> 2);
         const int32_t upCl = ((mk & 1u) && sckC > 0) | ((mk & 2u) && shsC > 0);
         const int32_t dnCl = ((mk & 1u) && sckC < 0) | ((mk & 2u) && shsC < 0);
+        int32_t pci[2], pcw[2], fcb[2], rcb[2];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           const int32_t dC = b - h.w1.w;  // -l_all, plus one when C starts using D
           const int32_t upC = upCl | (mk4 & (dC > 0)), dnC = dnCl | (mk4 & (dC < 0));
-          st.pc[lane][b] = (dnC & (upC ^ 1)) + (upC << 16);
-          st.fc[lane][b] = (int32_t)(sC | (enc_small(dC) << 4));
-          st.rc[lane][b] = (int32_t)((uint32_t)(uint16_t)(int16_t)clamp16(dC) << 16);
+          pci[b] = dnC & (upC ^ 1);
+          pcw[b] = upC;
+          fcb[b] = (int32_t)(sC | (enc_small(dC) << 4));
+          rcb[b] = (int32_t)((uint32_t)(uint16_t)(int16_t)clamp16(dC) << 16);
         }
+        st.mc[lane][0] = make_int4((int32_t)((uint32_t)pci[0] * 0x01010101u), (int32_t)((uint32_t)pcw[0] * 0x01010101u),
+                                   pci[1] - pci[0], pcw[1] - pcw[0]);
+        st.mc[lane][1] = make_int4((int32_t)((uint32_t)fcb[0] * 0x01010101u), fcb[1] - fcb[0], rcb[0],
+                                   (int32_t)((uint32_t)rcb[1] - (uint32_t)rcb[0]));
+        st.mc[lane][2] = make_int4(h.w0.x, h.w1.y > 0 ? 0x01010101 : 0, h.w1.z > 0 ? 0x01010101 : 0, 0);
       }
       if (lane == 0) { st.k = k; st.overflow = overflow; }
     }
@@ -923,7 +964,7 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
         const MoveHdr h = st.hdr[j];
         const int32_t nl = h.w0.z, nr = h.w1.x, C = h.w0.x;
         int32_t nh = 0;
-        st.hitw[j][lane] = 0u;
+        reinterpret_cast<uint32_t *>(&st.hitw[j][0])[lane] = 0u;
         __syncwarp();
         const int32_t hb = st.lb[j];  // the method's hits are stored from its first slot on
         const int32_t items = 4 * (nl + nr);
@@ -978,7 +1019,7 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
           const uint32_t hm = __ballot_sync(0xffffffffu, is_hit);
           if (is_hit) {
             st.hit[hb + nh + __popc(hm & ((1u << lane) - 1u))] = (int16_t)slot;
-            atomicOr(&st.hitw[j][rel >> 5], 1u << (rel & 31));
+            atomicOr(hit_word(st, j, rel >> 5), 1u << (rel & 31));
           }
           nh += __popc(hm);
         }
@@ -1016,78 +1057,81 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
         }
         continue;
       }
-      uint32_t gain[DQ] = {0, 0, 0, 0}, iw[DQ] = {0, 0, 0, 0};
+      // contribution counts of the thread's four destinations, one byte each
+      uint32_t gain = 0u, iwl = 0u, iwk = 0u;
       {
         const int32_t lb = st.lb[j], nl = h.w0.z;
-        for (int32_t e = 0; e < nl; ++e) {
-          const uint4 wd = st.word[lb + e][warp];
-          gain[0] += (wd.x >> lane) & 1u;
-          gain[1] += (wd.y >> lane) & 1u;
-          gain[2] += (wd.z >> lane) & 1u;
-          gain[3] += (wd.w >> lane) & 1u;
-        }
+        for (int32_t e = 0; e < nl; ++e) gain += lane_bits4(st.word[lb + e][warp], gsel, gsh);
         if (mk4) {  // caller classes only matter when CBO is selected
           const int32_t rb = st.rb[j], nr = h.w1.x;
           for (int32_t e = 0; e < nr; ++e) {
-            const uint32_t sh = (uint32_t)st.ent[rb + e].w;
-            const uint4 wd = st.word[rb + e][warp];
-            iw[0] += ((wd.x >> lane) & 1u) << sh;
-            iw[1] += ((wd.y >> lane) & 1u) << sh;
-            iw[2] += ((wd.z >> lane) & 1u) << sh;
-            iw[3] += ((wd.w >> lane) & 1u) << sh;
+            const uint32_t v = lane_bits4(st.word[rb + e][warp], gsel, gsh);
+            if (st.ent[rb + e].w == 0) iwl += v;  // X stops using C: improved
+            else iwk += v;                        // X keeps C: worsened
           }
         }
       }
+      const int4 mc0 = st.mc[j][0], mc1 = st.mc[j][1], mc2 = st.mc[j][2];
       // hits: destinations of this thread that appear in m's lists (evaluated after the batch)
-      uint32_t hitq = 0;
-#pragma unroll
-      for (int q = 0; q < DQ; ++q) hitq |= ((st.hitw[j][warp + 8 * q] >> lane) & 1u) << q;
-      const uint4 cin = st.cw[j][0][warp], cout = st.cw[j][1][warp];
-      const uint32_t os = h.w1.y > 0 ? 1u : 0u, is = h.w1.z > 0 ? 1u : 0u;
-      const int32_t pc0 = st.pc[j][0], pc1 = st.pc[j][1], fc0 = st.fc[j][0], fc1 = st.fc[j][1];
-      const int32_t rc0 = st.rc[j][0], rc1 = st.rc[j][1];
+      const uint32_t hit = lane_bits4(st.hitw[j][warp], gsel, gsh);
+      const uint32_t bdc = lane_bits4(st.cw[j][0][warp], gsel, gsh), bcd = lane_bits4(st.cw[j][1][warp], gsel, gsh);
       // common path: m shares nothing with D and D is in neither of m's lists
-      auto common = [&](int q, uint4 &r, bool &kept, int32_t &dD, uint32_t &b) {
-        const uint32_t bDC = (sel4(cin, q) >> lane) & 1u, bCD = (sel4(cout, q) >> lane) & 1u;
-        b = is & (bCD ^ 1u);                                  // C starts using D
-        dD = (int32_t)(gain[q] + (os & (bDC ^ 1u)));          // >= 0 on this path
-        const bool p = dD != 0;
-        const int32_t P = (b ? pc1 : pc0) + (p ? pd1[q] : pd0[q]) + (int32_t)iw[q];
-        kept = (P >> 16) == 0 && (P & 0xffff) >= cx.min_improved;
-        const uint32_t flags = (uint32_t)(b ? fc1 : fc0) | (uint32_t)fd0[q] | (p ? (2u << 10) : 0u) |
-                               (kept ? 0x8000u : 0u);
-        r.x = 0u;
-        r.y = (uint32_t)(b ? rc1 : rc0);
-        r.z = (uint32_t)dD | ((uint32_t)P << 16);
-        r.w = ((uint32_t)P >> 16) | (flags << 16);
+      const uint32_t dd = gain + (~bdc & (uint32_t)mc2.y);  // dCBO(D) >= 0
+      const uint32_t bb = ~bcd & (uint32_t)mc2.z;           // C starts using D
+      const uint32_t pb = bytes_nonzero(dd);                // dCBO(D) > 0
+      const uint32_t imp = (uint32_t)mc0.x + pdi + bb * (uint32_t)mc0.z - (pb & negi) + iwl;
+      const uint32_t wor = (uint32_t)mc0.y + pdw + bb * (uint32_t)mc0.w + (pb & posw) + iwk;
+      const uint32_t kb = bytes_ge(imp, k9) & ~bytes_nonzero(wor);
+      const uint32_t flo = (uint32_t)mc1.x + fdlo + bb * (uint32_t)mc1.y;  // flag bits 0-7
+      const uint32_t fhi = fdhi + pb * 8u + kb * 128u;                     // flag bits 8-15
+      const int32_t relC = C - D0;
+      const bool cspan = relC >= 0 && relC < DB_SPAN;
+      uint32_t act = valid & ~hit;
+      if (cspan && (relC & (DB_THREADS - 1)) == (int32_t)threadIdx.x) act &= ~(1u << (8 * (relC / DB_THREADS)));
+      // records: {sh = 0, t = 0 | dC << 16, dD | imp << 16, wor | flags << 16}
+      const uint32_t dd01 = __byte_perm(dd, 0u, 0x4140), dd23 = __byte_perm(dd, 0u, 0x4342);
+      const uint32_t im01 = __byte_perm(imp, 0u, 0x4140), im23 = __byte_perm(imp, 0u, 0x4342);
+      const uint32_t wo01 = __byte_perm(wor, 0u, 0x4140), wo23 = __byte_perm(wor, 0u, 0x4342);
+      const uint32_t fl01 = __byte_perm(flo, fhi, 0x5140), fl23 = __byte_perm(flo, fhi, 0x7362);
+      const uint32_t rc0 = (uint32_t)mc1.z, drc = (uint32_t)mc1.w;
+      auto rec = [&](int q) {
+        const uint32_t lo = q < 2 ? dd01 : dd23, il = q < 2 ? im01 : im23, wl = q < 2 ? wo01 : wo23,
+                       fl = q < 2 ? fl01 : fl23, sel = (q & 1) ? 0x7632u : 0x5410u;
+        return make_uint4(0u, rc0 + ((bb >> (8 * q)) & 1u) * drc, __byte_perm(lo, il, sel), __byte_perm(wl, fl, sel));
       };
-      uint32_t keptq = 0;
+      uint4 *rp = oc.records + rowbase + D0 + (int32_t)threadIdx.x;
+      if (!cspan) {
+        if (relC < 0) rp -= 1;  // every destination of the span lies past C
 #pragma unroll
-      for (int q = 0; q < DQ; ++q) {
-        const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
-        const bool act = D < c && D != C && !((hitq >> q) & 1u);
-        uint4 r;
-        bool kept;
-        int32_t dD;
-        uint32_t b;
-        common(q, r, kept, dD, b);
-        if (REC && act) __stcs(oc.records + rowbase + D - (D > C ? 1 : 0), r);
-        if (DIG && act) dig += record_hash(m, D, r);
-        keptq |= (uint32_t)(act && kept) << q;
-      }
-      // kept moves are rare: one vote per method, the compaction only when a lane has one
-      if (KEEP && __any_sync(0xffffffffu, keptq != 0u)) {
+        for (int q = 0; q < DQ; ++q) {
+          const bool a = (act >> (8 * q)) & 1u;
+          const uint4 r = rec(q);
+          if (REC && a) __stcs(rp + q * DB_THREADS, r);
+          if (DIG && a) dig += record_hash(m, D0 + (int32_t)threadIdx.x + q * DB_THREADS, r);
+        }
+      } else {
 #pragma unroll
         for (int q = 0; q < DQ; ++q) {
           const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
-          uint4 r;
-          bool kept;
-          int32_t dD;
-          uint32_t b;
-          common(q, r, kept, dD, b);
-          const bool kk = (keptq >> q) & 1u;
-          const int32_t dck = kk ? h.w2.y + dck0[q] : 0;
-          emit_kept(oc, kk, m, D, r.z >> 16, dck, (int32_t)b - h.w1.w + dD, lane);
+          const bool a = (act >> (8 * q)) & 1u;
+          const uint4 r = rec(q);
+          if (REC && a) __stcs(rp + q * DB_THREADS - (D > C ? 1 : 0), r);
+          if (DIG && a) dig += record_hash(m, D, r);
+        }
+      }
+      // kept moves are rare: one vote per method, the compaction only when a lane has one
+      const uint32_t kact = kb & act;
+      if (KEEP && __any_sync(0xffffffffu, kact != 0u)) {
+#pragma unroll
+        for (int q = 0; q < DQ; ++q) {
+          const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
+          const bool kk = (kact >> (8 * q)) & 1u;
+          int32_t dck = 0, dcbo = 0;
+          if (kk) {
+            dck = h.w2.y + load_dstate(D, cls_n, cls_a, cls_P, cls_Q, cls_S).dck0;
+            dcbo = (int32_t)((bb >> (8 * q)) & 1u) - h.w1.w + (int32_t)((dd >> (8 * q)) & 0xffu);
+          }
+          emit_kept(oc, kk, m, D, (imp >> (8 * q)) & 0xffu, dck, dcbo, lane);
         }
       }
     }
@@ -1097,7 +1141,7 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
       const int32_t nw = k * (DB_SPAN / 32);
       for (int32_t base = 0; base < nw; base += DB_THREADS) {
         const int32_t wi = base + (int32_t)threadIdx.x;
-        uint32_t bits = wi < nw ? st.hitw[wi >> 5][wi & 31] : 0u;
+        uint32_t bits = wi < nw ? *hit_word(st, wi >> 5, wi & 31) : 0u;
         while (__any_sync(0xffffffffu, bits != 0u)) {
           const bool have = bits != 0u;
           const int32_t bpos = have ? __ffs(bits) - 1 : 0;
@@ -1573,8 +1617,9 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
   if (!rowptr) {
     const int32_t c = s->c, M = s->M;
     unsigned gx = (unsigned)ceil_div(c, DB_SPAN);
-    // enough blocks for ~16 per SM, each walking a chunk of methods
-    int64_t want_y = std::max<int64_t>(1, (148 * 16 + gx - 1) / gx);
+    // about 30 waves of resident blocks (3 per SM): short method chunks keep
+    // the last wave's tail small relative to the whole launch
+    int64_t want_y = std::max<int64_t>(1, (148 * 3 * 30) / gx);
     int32_t mchunk = (int32_t)std::max<int64_t>(1, ceil_div(M, want_y));
     unsigned gy = (unsigned)ceil_div(M, mchunk);
     DenseSys sy{cx, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, c, M};
