@@ -553,6 +553,22 @@ __device__ __forceinline__ DState load_dstate(int32_t D, const int32_t *cls_n, c
   return d;
 }
 
+// destination constants: {P - Q, S} and {n, a, dck0, sck0 | shs0 << 8}
+__device__ __forceinline__ DState dstate_rec(const int4 *rec, int32_t D) {
+  const int4 a = __ldg(rec + 2 * (int64_t)D), b = __ldg(rec + 2 * (int64_t)D + 1);
+  DState d;
+  d.D = D;
+  d.nD = b.x;
+  d.aD = b.y;
+  d.dck0 = b.z;
+  d.sck0 = (int32_t)(int8_t)(b.w & 0xff);
+  d.shs0 = (int32_t)(int8_t)((b.w >> 8) & 0xff);
+  d.diffD = (int64_t)(((uint64_t)(uint32_t)a.y << 32) | (uint32_t)a.x);
+  d.SD = (int64_t)(((uint64_t)(uint32_t)a.w << 32) | (uint32_t)a.z);
+  d.ckD = d.diffD > 0 ? d.diffD : 0;
+  return d;
+}
+
 struct EvalCtx {
   const MoveHdr *hdr;
   const int4 *l_list;
@@ -754,6 +770,8 @@ constexpr int DB_SPAN = DB_THREADS * DQ;
 constexpr int DB_MB = 32;
 constexpr int DB_ECAP = 192;
 
+static_assert(DB_SPAN == 1024 && DB_MB <= 32, "hit codes (method << 10 | rel) fit 16 bits");
+
 struct DenseStage {
   MoveHdr hdr[DB_MB];
   int32_t lb[DB_MB], rb[DB_MB], hb[DB_MB], hn[DB_MB];
@@ -762,6 +780,8 @@ struct DenseStage {
   uint4 word[DB_ECAP][DB_WARPS];  // [slot][w] = contribution words w, w+8, w+16, w+24
   uint4 cw[DB_MB][2][DB_WARPS];   // adjacency words of row C: [0] = in_adj (D uses C), [1] = out_adj (C uses D)
   int16_t hit[DB_ECAP];           // slots whose class lies in the block's span
+  int16_t hl[DB_ECAP];            // distinct listed destinations of the batch: method << 10 | rel
+  int32_t nhl;
   uint4 hitw[DB_MB][DB_WARPS];    // per method: bit rel set iff D0 + rel is in one of its lists;
                                   // word g = w + 8 q is stored at [w] component q (as word)
   // per method, for b = [m's callers in C make C start using D] (bytes replicated over the four
@@ -805,9 +825,8 @@ __device__ __forceinline__ uint32_t *hit_word(DenseStage &st, int32_t j, int32_t
 // Rare paths of the dense kernel, kept out of line so they do not cost the
 // common path registers.
 __device__ __noinline__ uint4 dense_hit_path(const EvalCtx cx, const DenseStage &st, int32_t j, int32_t D, int q,
-                                             uint32_t lane, int warp, const int32_t *cls_n, const int32_t *cls_a,
-                                             const int64_t *cls_P, const int64_t *cls_Q, const int64_t *cls_S,
-                                             int32_t *dck, int32_t *dcbo) {
+                                             uint32_t lane, int warp, const int4 *dest_rec, int32_t *dck,
+                                             int32_t *dcbo) {
   const MoveHdr h = st.hdr[j];
   Gathered g;
   g.gain = 0; g.impX = 0; g.worX = 0;
@@ -833,7 +852,7 @@ __device__ __noinline__ uint4 dense_hit_path(const EvalCtx cx, const DenseStage 
   }
   g.bDC = (int32_t)((sel4(st.cw[j][0][warp], q) >> lane) & 1u);
   g.bCD = (int32_t)((sel4(st.cw[j][1][warp], q) >> lane) & 1u);
-  DState ds = load_dstate(D, cls_n, cls_a, cls_P, cls_Q, cls_S);
+  const DState ds = dstate_rec(dest_rec, D);
   int32_t a = 0, b = 0;
   uint4 r = finish_move(h, ds, g, cx.mask, cx.min_improved, a, b);
   *dck = a;
@@ -841,11 +860,9 @@ __device__ __noinline__ uint4 dense_hit_path(const EvalCtx cx, const DenseStage 
   return r;
 }
 
-__device__ __noinline__ uint4 dense_global_path(const EvalCtx cx, const MoveHdr &h, int32_t D,
-                                                const int32_t *cls_n, const int32_t *cls_a, const int64_t *cls_P,
-                                                const int64_t *cls_Q, const int64_t *cls_S, int32_t *dck,
-                                                int32_t *dcbo) {
-  DState ds = load_dstate(D, cls_n, cls_a, cls_P, cls_Q, cls_S);
+__device__ __noinline__ uint4 dense_global_path(const EvalCtx cx, const MoveHdr &h, int32_t D, const int4 *dest_rec,
+                                                int32_t *dck, int32_t *dcbo) {
+  const DState ds = dstate_rec(dest_rec, D);
   int32_t a = 0, b = 0;
   uint4 r = eval_move(cx, h, ds, a, b);
   *dck = a;
@@ -857,8 +874,7 @@ __device__ __noinline__ uint4 dense_global_path(const EvalCtx cx, const MoveHdr 
 // batched persistent kernel).
 struct DenseSys {
   EvalCtx cx;
-  const int32_t *cls_n, *cls_a;
-  const int64_t *cls_P, *cls_Q, *cls_S;
+  const int4 *dest_rec;  // per class: {P - Q, S}, {n, a, dck0, sck0 | shs0 << 8}
   int32_t c, M;
 };
 
@@ -869,8 +885,7 @@ template <bool REC, bool DIG, bool KEEP>
 __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx &oc, DenseStage &st, int32_t bx,
                                                int32_t m0, int32_t m1) {
   const EvalCtx &cx = sy.cx;
-  const int32_t *cls_n = sy.cls_n, *cls_a = sy.cls_a;
-  const int64_t *cls_P = sy.cls_P, *cls_Q = sy.cls_Q, *cls_S = sy.cls_S;
+  const int4 *dest_rec = sy.dest_rec;
   const int32_t c = sy.c;
   const uint32_t lane = threadIdx.x & 31u;
   const int warp = (int)(threadIdx.x >> 5);
@@ -887,16 +902,18 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
 #pragma unroll
   for (int q = 0; q < DQ; ++q) {
     const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
-    DState ds = load_dstate(D < c ? D : 0, cls_n, cls_a, cls_P, cls_Q, cls_S);
-    const uint32_t up = ((mk & 1u) && ds.sck0 > 0) | ((mk & 2u) && ds.shs0 > 0);
-    const uint32_t dn = ((mk & 1u) && ds.sck0 < 0) | ((mk & 2u) && ds.shs0 < 0);
+    // sign bytes of dLCOM_CK and dLCOM_HS when D gains a method sharing nothing
+    const uint32_t sg = (uint32_t)__ldg(&dest_rec[2 * (int64_t)(D < c ? D : 0) + 1].w);
+    const int32_t sck0 = (int32_t)(int8_t)(sg & 0xffu), shs0 = (int32_t)(int8_t)((sg >> 8) & 0xffu);
+    const uint32_t up = ((mk & 1u) && sck0 > 0) | ((mk & 2u) && shs0 > 0);
+    const uint32_t dn = ((mk & 1u) && sck0 < 0) | ((mk & 2u) && shs0 < 0);
     const uint32_t sh = 8u * (uint32_t)q;
     pdi |= (dn & (up ^ 1u)) << sh;
     pdw |= up << sh;
     negi |= (dn & (up ^ 1u) & (uint32_t)mk4) << sh;
     posw |= ((up ^ 1u) & (uint32_t)mk4) << sh;
-    fdlo |= (enc_sign(ds.sck0) << 6) << sh;
-    fdhi |= enc_sign(ds.shs0) << sh;
+    fdlo |= (enc_sign(sck0) << 6) << sh;
+    fdhi |= enc_sign(shs0) << sh;
     valid |= (uint32_t)(D < c) << sh;
   }
   const uint32_t gsel = (lane >> 3) | (((lane >> 3) + 4u) << 4), gsh = lane & 7u;
@@ -953,7 +970,7 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
                                    (int32_t)((uint32_t)rcb[1] - (uint32_t)rcb[0]));
         st.mc[lane][2] = make_int4(h.w0.x, h.w1.y > 0 ? 0x01010101 : 0, h.w1.z > 0 ? 0x01010101 : 0, 0);
       }
-      if (lane == 0) { st.k = k; st.overflow = overflow; }
+      if (lane == 0) { st.k = k; st.overflow = overflow; st.nhl = 0; }
     }
     __syncthreads();
     const int32_t k = st.k;
@@ -1019,7 +1036,9 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
           const uint32_t hm = __ballot_sync(0xffffffffu, is_hit);
           if (is_hit) {
             st.hit[hb + nh + __popc(hm & ((1u << lane) - 1u))] = (int16_t)slot;
-            atomicOr(hit_word(st, j, rel >> 5), 1u << (rel & 31));
+            const uint32_t hbit = 1u << (rel & 31);
+            if (!(atomicOr(hit_word(st, j, rel >> 5), hbit) & hbit))  // first entry of this class
+              st.hl[atomicAdd(&st.nhl, 1)] = (int16_t)((j << 10) | rel);
           }
           nh += __popc(hm);
         }
@@ -1050,7 +1069,7 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
           const bool act = D < c && D != C;
           int32_t dck = 0, dcbo = 0;
           uint4 r = make_uint4(0, 0, 0, 0);
-          if (act) r = dense_global_path(cx, h, D, cls_n, cls_a, cls_P, cls_Q, cls_S, &dck, &dcbo);
+          if (act) r = dense_global_path(cx, h, D, dest_rec, &dck, &dcbo);
           if (REC && act) __stcs(oc.records + rowbase + D - (D > C ? 1 : 0), r);
           if (DIG && act) dig += record_hash(m, D, r);
           if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
@@ -1128,7 +1147,7 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
           const bool kk = (kact >> (8 * q)) & 1u;
           int32_t dck = 0, dcbo = 0;
           if (kk) {
-            dck = h.w2.y + load_dstate(D, cls_n, cls_a, cls_P, cls_Q, cls_S).dck0;
+            dck = h.w2.y + __ldg(&dest_rec[2 * (int64_t)D + 1].z);
             dcbo = (int32_t)((bb >> (8 * q)) & 1u) - h.w1.w + (int32_t)((dd >> (8 * q)) & 0xffu);
           }
           emit_kept(oc, kk, m, D, (imp >> (8 * q)) & 0xffu, dck, dcbo, lane);
@@ -1136,30 +1155,26 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
       }
     }
     // exact general path for the destinations that appear in the lists of the
-    // batch's methods (rare): all threads of the block over the hit bitmaps
+    // batch's methods (rare): one listed (method, destination) per thread
     if (!overflow) {
-      const int32_t nw = k * (DB_SPAN / 32);
-      for (int32_t base = 0; base < nw; base += DB_THREADS) {
-        const int32_t wi = base + (int32_t)threadIdx.x;
-        uint32_t bits = wi < nw ? *hit_word(st, wi >> 5, wi & 31) : 0u;
-        while (__any_sync(0xffffffffu, bits != 0u)) {
-          const bool have = bits != 0u;
-          const int32_t bpos = have ? __ffs(bits) - 1 : 0;
-          if (have) bits &= bits - 1u;
-          const int32_t j = wi >> 5, rel = (wi & 31) * 32 + bpos;
-          const int32_t D = D0 + rel;
-          const int32_t m = mb + j;
-          const int32_t C = have ? st.hdr[j].w0.x : -1;
-          const bool act = have && D < c && D != C;
-          int32_t dck = 0, dcbo = 0;
-          uint4 r = make_uint4(0, 0, 0, 0);
-          if (act)
-            r = dense_hit_path(cx, st, j, D, rel >> 8, (uint32_t)(rel & 31), (rel & (DB_THREADS - 1)) >> 5, cls_n,
-                               cls_a, cls_P, cls_Q, cls_S, &dck, &dcbo);
-          if (REC && act) __stcs(oc.records + (int64_t)m * row + D - (D > C ? 1 : 0), r);
-          if (DIG && act) dig += record_hash(m, D, r);
-          if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
-        }
+      const int32_t nh = st.nhl;
+      for (int32_t i0 = 0; i0 < nh; i0 += DB_THREADS) {
+        const int32_t i = i0 + (int32_t)threadIdx.x;
+        const bool have = i < nh;
+        const int32_t code = have ? (int32_t)st.hl[i] : 0;
+        const int32_t j = code >> 10, rel = code & (DB_SPAN - 1);
+        const int32_t D = D0 + rel;
+        const int32_t m = mb + j;
+        const int32_t C = have ? st.hdr[j].w0.x : -1;
+        const bool act = have && D < c && D != C;
+        int32_t dck = 0, dcbo = 0;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        if (act)
+          r = dense_hit_path(cx, st, j, D, rel >> 8, (uint32_t)(rel & 31), (rel & (DB_THREADS - 1)) >> 5, dest_rec,
+                             &dck, &dcbo);
+        if (REC && act) __stcs(oc.records + (int64_t)m * row + D - (D > C ? 1 : 0), r);
+        if (DIG && act) dig += record_hash(m, D, r);
+        if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
       }
     }
     mb += k;
@@ -1255,21 +1270,6 @@ __device__ __forceinline__ uint32_t ldg_if(const uint32_t *p, bool pred) {
   return v;
 }
 
-// destination constants: {P - Q, S} and {n, a, dck0, sck0 | shs0 << 8}
-__device__ __forceinline__ DState dstate_rec(const int4 *rec, int32_t D) {
-  const int4 a = __ldg(rec + 2 * (int64_t)D), b = __ldg(rec + 2 * (int64_t)D + 1);
-  DState d;
-  d.D = D;
-  d.nD = b.x;
-  d.aD = b.y;
-  d.dck0 = b.z;
-  d.sck0 = (int32_t)(int8_t)(b.w & 0xff);
-  d.shs0 = (int32_t)(int8_t)((b.w >> 8) & 0xff);
-  d.diffD = (int64_t)(((uint64_t)(uint32_t)a.y << 32) | (uint32_t)a.x);
-  d.SD = (int64_t)(((uint64_t)(uint32_t)a.w << 32) | (uint32_t)a.z);
-  d.ckD = d.diffD > 0 ? d.diffD : 0;
-  return d;
-}
 
 // Methods whose lists exceed the stage: the general per-candidate path.  Its
 // arguments are values: a reference to a kernel parameter would keep the whole
@@ -1622,7 +1622,7 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
     int64_t want_y = std::max<int64_t>(1, (148 * 3 * 30) / gx);
     int32_t mchunk = (int32_t)std::max<int64_t>(1, ceil_div(M, want_y));
     unsigned gy = (unsigned)ceil_div(M, mchunk);
-    DenseSys sy{cx, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, c, M};
+    DenseSys sy{cx, s->dest_rec, c, M};
     eval_dense<REC, DIG, KEEP><<<dim3(gx, gy), DB_THREADS, 0, st>>>(sy, oc, mchunk);
   } else {
     CsrSys sy;
@@ -2212,7 +2212,7 @@ void batch_fill_items(const BatchLaunchSpec *specs, int32_t n, const mm_criteria
     mm_system *s = specs[i].sys;
     EvalCtx cx = make_ctx(s, crit);
     BatchItem &it = items[i];
-    it.sy = DenseSys{cx, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, s->c, s->M};
+    it.sy = DenseSys{cx, s->dest_rec, s->c, s->M};
     it.oc = OutCtx{};
     it.oc.digest = specs[i].digest;
     it.oc.kept = specs[i].kept;
