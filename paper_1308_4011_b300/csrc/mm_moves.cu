@@ -781,7 +781,9 @@ struct DenseStage {
   uint4 cw[DB_MB][2][DB_WARPS];   // adjacency words of row C: [0] = in_adj (D uses C), [1] = out_adj (C uses D)
   int16_t hit[DB_ECAP];           // slots whose class lies in the block's span
   int16_t hl[DB_ECAP];            // distinct listed destinations of the batch: method << 10 | rel
-  int32_t nhl;
+  int8_t sm[DB_ECAP];             // method of each slot
+  uint8_t sk[DB_ECAP];            // row of each slot: 1 in-row (else out-row), 2 inverted, 4 counted
+  int32_t nhl, ns;
   uint4 hitw[DB_MB][DB_WARPS];    // per method: bit rel set iff D0 + rel is in one of its lists;
                                   // word g = w + 8 q is stored at [w] component q (as word)
   // per method, for b = [m's callers in C make C start using D] (bytes replicated over the four
@@ -923,6 +925,8 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
   const int64_t seg_words = cx.aw - dw0;  // adjacency words left in a row from dw0 (may exceed 32)
   uint64_t dig = 0;
   for (int32_t mb = m0; mb < m1;) {
+    for (int32_t i = (int32_t)threadIdx.x; i < DB_MB * DB_WARPS * 4; i += DB_THREADS)
+      reinterpret_cast<uint32_t *>(&st.hitw[0][0])[i] = 0u;
     // ---- plan: warp 0 scans the list lengths of up to 32 methods
     if (warp == 0) {
       const int32_t m = mb + (int32_t)lane;
@@ -950,6 +954,9 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
         st.hdr[lane] = h;
         st.lb[lane] = incl - len;
         st.rb[lane] = incl - len + h.w0.z;
+        st.hb[lane] = incl - len;  // the method's listed slots are kept from its first slot on
+        st.hn[lane] = 0;
+        for (int32_t e = incl - len; e < incl; ++e) st.sm[e] = (int8_t)lane;
         const uint32_t sC = (uint32_t)h.w2.x & 15u;
         const int sckC = dec_sign(sC & 3u), shsC = dec_sign(sC >> 2);
         const int32_t upCl = ((mk & 1u) && sckC > 0) | ((mk & 2u) && shsC > 0);
@@ -970,88 +977,91 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
                                    (int32_t)((uint32_t)rcb[1] - (uint32_t)rcb[0]));
         st.mc[lane][2] = make_int4(h.w0.x, h.w1.y > 0 ? 0x01010101 : 0, h.w1.z > 0 ? 0x01010101 : 0, 0);
       }
-      if (lane == 0) { st.k = k; st.overflow = overflow; st.nhl = 0; }
+      const int32_t ns = __shfl_sync(0xffffffffu, incl, k - 1);
+      if (lane == 0) { st.k = k; st.overflow = overflow; st.nhl = 0; st.ns = overflow ? 0 : ns; }
     }
     __syncthreads();
     const int32_t k = st.k;
     const bool overflow = st.overflow != 0;
-    // ---- stage: warp w prepares methods w, w+8, ... (lanes over list entries)
+    // ---- stage, block-wide: (1) every slot's list entry and the adjacency
+    // words of each method's own class C, (2) every slot's 32 row words
+    // turned into per-destination contributions
     if (!overflow) {
-      for (int32_t j = warp; j < k; j += DB_WARPS) {
-        const MoveHdr h = st.hdr[j];
-        const int32_t nl = h.w0.z, nr = h.w1.x, C = h.w0.x;
-        int32_t nh = 0;
-        reinterpret_cast<uint32_t *>(&st.hitw[j][0])[lane] = 0u;
-        __syncwarp();
-        const int32_t hb = st.lb[j];  // the method's hits are stored from its first slot on
-        const int32_t items = 4 * (nl + nr);
-        for (int32_t i0 = 0; i0 < items; i0 += 32) {
-          const int32_t it = i0 + (int32_t)lane;
-          const bool ok = it < items;
-          const int32_t e = it >> 2, c4 = it & 3;
-          const bool isL = e < nl;
-          int4 v = make_int4(-1, 0, 0, 0);
-          int32_t slot = 0;
-          if (ok) {
-            if (isL) {
-              v = __ldg(cx.l_list + h.w0.y + e);
-              slot = st.lb[j] + e;
-              if (c4 == 0) st.ents[slot] = v.w > 0 ? __ldg(cx.l_s + h.w0.y + e) : 0;
-            } else {
-              v = __ldg(cx.r_list + h.w0.w + (e - nl));
-              slot = st.rb[j] + (e - nl);
-            }
-            // contribution = (adjacency ^ xr) & am:
-            //   L: D does not use E yet (only if m really uses E);  R: loss ? X uses D : X does not use D
-            uint32_t xr, am;
-            if (isL) {
-              xr = 0xffffffffu;
-              am = v.y > 0 ? 0xffffffffu : 0u;
-            } else {
-              const bool loss = v.z == v.y;  // X stops using C
-              xr = loss ? 0u : 0xffffffffu;
-              am = 0xffffffffu;
-              v.w = loss ? 0 : 16;           // drop -> improved counter, rise -> worsened counter
-            }
-            const int32_t relv = v.x - D0;
-            const int32_t hw = (relv >= 0 && relv < DB_SPAN) ? (relv >> 5) : -1;
-            const uint32_t hbit = 1u << (relv & 31);
-            const uint4 *rowp = reinterpret_cast<const uint4 *>((isL ? cx.in_adj : cx.out_adj) +
-                                                                (int64_t)v.x * cx.aw + dw0);
-            uint4 a = make_uint4(0, 0, 0, 0), b = make_uint4(0, 0, 0, 0);
-            if (8 * c4 < seg_words) a = __ldg(rowp + 2 * c4);
-            if (8 * c4 + 4 < seg_words) b = __ldg(rowp + 2 * c4 + 1);
-            const uint32_t wv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-            uint32_t *dstw = reinterpret_cast<uint32_t *>(&st.word[slot][0]);
-#pragma unroll
-            for (int w = 0; w < DB_WARPS; ++w) {  // word g = 8 c4 + w is stored at [w][c4]
-              uint32_t x = (wv[w] ^ xr) & am;
-              if (hw == 8 * c4 + w) x &= ~hbit;
-              dstw[4 * w + c4] = x;
-            }
-            if (c4 == 0) st.ent[slot] = v;
-          }
-          const int32_t rel = v.x - D0;
-          const bool is_hit = ok && c4 == 0 && rel >= 0 && rel < DB_SPAN;
-          const uint32_t hm = __ballot_sync(0xffffffffu, is_hit);
-          if (is_hit) {
-            st.hit[hb + nh + __popc(hm & ((1u << lane) - 1u))] = (int16_t)slot;
-            const uint32_t hbit = 1u << (rel & 31);
-            if (!(atomicOr(hit_word(st, j, rel >> 5), hbit) & hbit))  // first entry of this class
-              st.hl[atomicAdd(&st.nhl, 1)] = (int16_t)((j << 10) | rel);
-          }
-          nh += __popc(hm);
+      const int32_t ns = st.ns;
+      for (int32_t slot = (int32_t)threadIdx.x; slot < ns; slot += DB_THREADS) {
+        const int32_t j = st.sm[slot];
+        const int4 w0 = st.hdr[j].w0;
+        const int32_t rb = st.rb[j], lb = st.lb[j];
+        const bool isL = slot < rb;
+        int4 v;
+        uint32_t kind;
+        if (isL) {
+          v = __ldg(cx.l_list + w0.y + (slot - lb));
+          const int32_t sv = __ldg(cx.l_s + w0.y + (slot - lb));
+          st.ents[slot] = v.w > 0 ? sv : 0;
+          kind = 1u | 2u | (v.y > 0 ? 4u : 0u);  // in-row, inverted: D does not use E yet; only if m uses E
+        } else {
+          v = __ldg(cx.r_list + w0.w + (slot - rb));
+          const bool loss = v.z == v.y;            // X stops using C
+          v.w = loss ? 0 : 16;                     // drop -> improved counter, rise -> worsened counter
+          kind = (loss ? 0u : 2u) | 4u;            // out-row: loss ? X uses D : X does not use D
         }
-        if (lane == 0) { st.hb[j] = hb; st.hn[j] = nh; }
-        if (lane < 2 * DB_WARPS) {
-          const int which = (int)lane / DB_WARPS, w = (int)lane % DB_WARPS;
-          const uint32_t *rowp = (which ? cx.out_adj : cx.in_adj) + (int64_t)C * cx.aw + dw0;
-          uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-          if (w < seg_words) a0 = __ldg(rowp + w);
-          if (w + 8 < seg_words) a1 = __ldg(rowp + w + 8);
-          if (w + 16 < seg_words) a2 = __ldg(rowp + w + 16);
-          if (w + 24 < seg_words) a3 = __ldg(rowp + w + 24);
-          st.cw[j][which][w] = make_uint4(a0, a1, a2, a3);
+        st.ent[slot] = v;
+        st.sk[slot] = (uint8_t)kind;
+        const int32_t rel = v.x - D0;
+        if (rel >= 0 && rel < DB_SPAN) {  // listed destination in this block's span
+          st.hit[lb + atomicAdd(&st.hn[j], 1)] = (int16_t)slot;
+          const uint32_t hbit = 1u << (rel & 31);
+          if (!(atomicOr(hit_word(st, j, rel >> 5), hbit) & hbit))  // first entry of this class
+            st.hl[atomicAdd(&st.nhl, 1)] = (int16_t)((j << 10) | rel);
+        }
+      }
+      for (int32_t ci = (int32_t)threadIdx.x; ci < k * 2 * DB_WARPS; ci += DB_THREADS) {
+        const int32_t j = ci / (2 * DB_WARPS), which = (ci / DB_WARPS) & 1, w = ci % DB_WARPS;
+        const uint32_t *rowp = (which ? cx.out_adj : cx.in_adj) + (int64_t)st.hdr[j].w0.x * cx.aw + dw0;
+        uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        if (w < seg_words) a0 = __ldg(rowp + w);
+        if (w + 8 < seg_words) a1 = __ldg(rowp + w + 8);
+        if (w + 16 < seg_words) a2 = __ldg(rowp + w + 16);
+        if (w + 24 < seg_words) a3 = __ldg(rowp + w + 24);
+        st.cw[j][which][w] = make_uint4(a0, a1, a2, a3);
+      }
+      __syncthreads();
+      // four items per slot, each 8 of its 32 words: word g = 8 c4 + w is stored at [w][c4];
+      // a thread issues the loads of all its items before storing any
+      constexpr int SI = (4 * DB_ECAP + DB_THREADS - 1) / DB_THREADS;
+      uint4 ra[SI], rb4[SI];
+#pragma unroll
+      for (int u = 0; u < SI; ++u) {
+        const int32_t it = (int32_t)threadIdx.x + u * DB_THREADS;
+        ra[u] = make_uint4(0, 0, 0, 0);
+        rb4[u] = make_uint4(0, 0, 0, 0);
+        if (it < 4 * ns) {
+          const int32_t slot = it >> 2, c4 = it & 3;
+          const uint4 *rowp = reinterpret_cast<const uint4 *>(((st.sk[slot] & 1u) ? cx.in_adj : cx.out_adj) +
+                                                              (int64_t)st.ent[slot].x * cx.aw + dw0);
+          if (8 * c4 < seg_words) ra[u] = __ldg(rowp + 2 * c4);
+          if (8 * c4 + 4 < seg_words) rb4[u] = __ldg(rowp + 2 * c4 + 1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < SI; ++u) {
+        const int32_t it = (int32_t)threadIdx.x + u * DB_THREADS;
+        if (it < 4 * ns) {
+          const int32_t slot = it >> 2, c4 = it & 3;
+          const uint32_t kind = st.sk[slot];
+          const uint32_t xr = (kind & 2u) ? 0xffffffffu : 0u, am = (kind & 4u) ? 0xffffffffu : 0u;
+          const int32_t relv = st.ent[slot].x - D0;
+          const int32_t hw = (relv >= 0 && relv < DB_SPAN) ? (relv >> 5) : -1;
+          const uint32_t hbit = 1u << (relv & 31);
+          const uint32_t wv[8] = {ra[u].x, ra[u].y, ra[u].z, ra[u].w, rb4[u].x, rb4[u].y, rb4[u].z, rb4[u].w};
+          uint32_t *dstw = reinterpret_cast<uint32_t *>(&st.word[slot][0]);
+#pragma unroll
+          for (int w = 0; w < DB_WARPS; ++w) {
+            uint32_t x = (wv[w] ^ xr) & am;
+            if (hw == 8 * c4 + w) x &= ~hbit;  // D == E or D == X: the listed path counts it
+            dstw[4 * w + c4] = x;
+          }
         }
       }
     }
@@ -1184,7 +1194,7 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
 }
 
 template <bool REC, bool DIG, bool KEEP>
-__global__ void __launch_bounds__(DB_THREADS, 3) eval_dense(DenseSys sy, OutCtx oc, int32_t mchunk) {
+__global__ void __launch_bounds__(DB_THREADS, 4) eval_dense(DenseSys sy, OutCtx oc, int32_t mchunk) {
   __shared__ __align__(16) DenseStage st;
   const int32_t m0 = blockIdx.y * mchunk;
   const int32_t m1 = min(sy.M, m0 + mchunk);
@@ -1617,7 +1627,7 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
   if (!rowptr) {
     const int32_t c = s->c, M = s->M;
     unsigned gx = (unsigned)ceil_div(c, DB_SPAN);
-    // about 30 waves of resident blocks (3 per SM): short method chunks keep
+    // about 90 blocks per SM (4 resident at a time): short method chunks keep
     // the last wave's tail small relative to the whole launch
     int64_t want_y = std::max<int64_t>(1, (148 * 3 * 30) / gx);
     int32_t mchunk = (int32_t)std::max<int64_t>(1, ceil_div(M, want_y));
