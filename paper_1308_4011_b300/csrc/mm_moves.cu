@@ -862,14 +862,27 @@ __device__ __noinline__ uint4 dense_hit_path(const EvalCtx cx, const DenseStage 
   return r;
 }
 
-__device__ __noinline__ uint4 dense_global_path(const EvalCtx cx, const MoveHdr &h, int32_t D, const int4 *dest_rec,
-                                                int32_t *dck, int32_t *dcbo) {
-  const DState ds = dstate_rec(dest_rec, D);
-  int32_t a = 0, b = 0;
-  uint4 r = eval_move(cx, h, ds, a, b);
-  *dck = a;
-  *dcbo = b;
-  return r;
+// One method against the block's destinations from global memory (its lists
+// do not fit the stage).  Its arguments are values: a reference to a kernel
+// parameter would keep the whole parameter block in local memory.
+template <bool REC, bool DIG, bool KEEP>
+__device__ __noinline__ uint64_t dense_overflow_method(const EvalCtx cx, const OutCtx oc, const MoveHdr h, int32_t m,
+                                                       int32_t D0, int32_t c, const int4 *dest_rec) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int32_t C = h.w0.x;
+  const int64_t rowbase = (int64_t)m * ((int64_t)c - 1);
+  uint64_t dig = 0;
+  for (int q = 0; q < DQ; ++q) {
+    const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
+    const bool act = D < c && D != C;
+    int32_t dck = 0, dcbo = 0;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (act) r = eval_move(cx, h, dstate_rec(dest_rec, D), dck, dcbo);
+    if (REC && act) __stcs(oc.records + rowbase + D - (D > C ? 1 : 0), r);
+    if (DIG && act) dig += record_hash(m, D, r);
+    if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
+  }
+  return dig;
 }
 
 // Parameters of one system for the dense evaluation (also the unit of the
@@ -1066,26 +1079,15 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
       }
     }
     __syncthreads();
-    // ---- evaluate the batch
-    for (int32_t j = 0; j < k; ++j) {
+    // ---- evaluate the batch (a method whose lists exceed the stage comes alone
+    // and takes the general path, called outside the loop so that the loop
+    // keeps no call frame)
+    if (overflow) dig += dense_overflow_method<REC, DIG, KEEP>(cx, oc, st.hdr[0], mb, D0, c, dest_rec);
+    for (int32_t j = 0; j < k && !overflow; ++j) {
       const int32_t m = mb + j;
       const MoveHdr h = st.hdr[j];
       const int32_t C = h.w0.x;
       const int64_t rowbase = (int64_t)m * row;
-      if (overflow) {
-#pragma unroll
-        for (int q = 0; q < DQ; ++q) {
-          const int32_t D = D0 + (int32_t)threadIdx.x + q * DB_THREADS;
-          const bool act = D < c && D != C;
-          int32_t dck = 0, dcbo = 0;
-          uint4 r = make_uint4(0, 0, 0, 0);
-          if (act) r = dense_global_path(cx, h, D, dest_rec, &dck, &dcbo);
-          if (REC && act) __stcs(oc.records + rowbase + D - (D > C ? 1 : 0), r);
-          if (DIG && act) dig += record_hash(m, D, r);
-          if (KEEP) emit_kept(oc, act && (r.w >> 31), m, D, r.z >> 16, dck, dcbo, lane);
-        }
-        continue;
-      }
       // contribution counts of the thread's four destinations, one byte each
       uint32_t gain = 0u, iwl = 0u, iwk = 0u;
       {
