@@ -203,6 +203,9 @@ struct mm_system {
 // *total_dev when non-null.  Uses sys->sort_ws-independent scratch `ws`.
 void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, Scratch &ws,
                         cudaStream_t st);
+// Copies the device flag of bounded waits that gave up (nonzero) to *host once
+// the stream reaches this point; the caller synchronises before reading it.
+void read_wait_fault(uint32_t *host, cudaStream_t st);
 void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch &ws, cudaStream_t st,
                             int64_t *total_dev = nullptr);
 

@@ -2088,8 +2088,11 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
         MM_CUDA_TRY(cudaMemcpyAsync(staged.data(), kept, sizeof(mm_move) * (size_t)nstage,
                                     cudaMemcpyDeviceToHost, st));
       unsigned long long hc[2];
+      uint32_t fault = 0;
       MM_CUDA_TRY(cudaMemcpyAsync(hc, s->d_u64 + 1, sizeof(hc), cudaMemcpyDeviceToHost, st));
+      read_wait_fault(&fault, st);
       MM_CUDA_TRY(cudaStreamSynchronize(st));
+      if (fault) throw MmError{MM_ETIMEOUT, "suggest: a bounded device-side wait gave up"};
       K = (int64_t)hc[0];
       nm = (int64_t)hc[1];
       if (K <= cap) break;

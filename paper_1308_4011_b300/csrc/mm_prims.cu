@@ -10,6 +10,9 @@
 
 #include "mm_internal.cuh"
 
+// Set by a bounded device-side wait that ran out (see scan_onepass).
+__device__ unsigned int g_wait_fault = 0;
+
 namespace {
 
 constexpr int SCAN_THREADS = 256;
@@ -43,61 +46,6 @@ __device__ T block_exclusive_sum(T v, T *total) {
   T r = incl - v + warp_sums[warp];
   __syncthreads();
   return r;
-}
-
-template <class Tin, class Tout>
-__global__ void scan_reduce_kernel(const Tin *in, Tout *partial, int64_t n) {
-  int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-  Tout s = 0;
-  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
-    int64_t k = base + i;
-    if (k < n) s += (Tout)in[k];
-  }
-  __shared__ Tout tot;
-  Tout dummy = block_exclusive_sum<Tout>(s, &tot);
-  (void)dummy;
-  __syncthreads();
-  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-}
-
-template <class T>
-__global__ void scan_partials_kernel(T *partial, int64_t nb, T *total_out) {
-  __shared__ T carry_s;
-  __shared__ T tot;
-  if (threadIdx.x == 0) carry_s = 0;
-  __syncthreads();
-  for (int64_t base = 0; base < nb; base += SCAN_THREADS) {
-    int64_t k = base + threadIdx.x;
-    T v = k < nb ? partial[k] : T(0);
-    T ex = block_exclusive_sum<T>(v, &tot);
-    T carry = carry_s;
-    if (k < nb) partial[k] = ex + carry;
-    __syncthreads();
-    if (threadIdx.x == 0) carry_s = carry + tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && total_out) *total_out = carry_s;
-}
-
-template <class Tin, class Tout>
-__global__ void scan_tiles_kernel(const Tin *in, Tout *out, int64_t n, const Tout *partial) {
-  int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-  Tout v[SCAN_ITEMS];
-  Tout s = 0;
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) {
-    int64_t k = base + i;
-    v[i] = k < n ? (Tout)in[k] : Tout(0);
-    s += v[i];
-  }
-  __shared__ Tout tot;
-  Tout ex = block_exclusive_sum<Tout>(s, &tot) + partial[blockIdx.x];
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) {
-    int64_t k = base + i;
-    if (k < n) out[k] = ex;
-    ex += v[i];
-  }
 }
 
 // Small inputs: one block of 32 warps walks the array in 16K-element chunks
@@ -161,6 +109,76 @@ __global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(const Tin *in
   if (threadIdx.x == 0 && total_out) *total_out = carry;
 }
 
+// Larger inputs: one pass over tiles of SCAN_TILE elements with decoupled
+// look-back (Merrill and Garland, "Single-pass Parallel Prefix Scan with
+// Decoupled Look-back", 2016).  Tiles are numbered in the order blocks start,
+// so every tile a block waits for belongs to a block that is already running.
+// A tile publishes its total (flag 1), then, once the tiles before it are
+// summed, its inclusive prefix (flag 2), both as one 64-bit word (sum << 2 |
+// flag).  The wait is bounded: past the limit the block records a fault in
+// g_wait_fault (read back by the host at its next synchronisation) and goes on.
+constexpr unsigned long long SP_AGG = 1ull, SP_INCL = 2ull;
+constexpr int SP_WAIT_LIMIT = 1 << 22;
+
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(const Tin *in, Tout *out, int64_t n, Tout *total_out,
+                                                              unsigned long long *status, unsigned int *tile_ctr) {
+  static_assert(sizeof(Tout) <= 8, "scan sums are packed with a 2-bit flag");
+  __shared__ unsigned int s_tile;
+  __shared__ Tout s_prefix;
+  __shared__ Tout tot;
+  if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  Tout v[SCAN_ITEMS];
+  Tout sum = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const int64_t k = base + i;
+    v[i] = k < n ? (Tout)in[k] : Tout(0);
+    sum += v[i];
+  }
+  Tout ex = block_exclusive_sum<Tout>(sum, &tot);
+  if (threadIdx.x == 0) {
+    const Tout agg = tot;
+    Tout prefix = 0;
+    volatile unsigned long long *vs = status;
+    if (tile == 0) {
+      atomicExch(&status[0], ((unsigned long long)agg << 2) | SP_INCL);
+    } else {
+      atomicExch(&status[tile], ((unsigned long long)agg << 2) | SP_AGG);
+      int spins = 0;
+      for (int64_t j = tile - 1; j >= 0;) {
+        const unsigned long long w = vs[j];
+        const unsigned long long f = w & 3ull;
+        if (f == 0ull) {
+          if (++spins > SP_WAIT_LIMIT) {
+            atomicOr(&g_wait_fault, 1u);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        prefix += (Tout)(w >> 2);
+        if (f == SP_INCL) break;
+        --j;
+      }
+      atomicExch(&status[tile], ((unsigned long long)(prefix + agg) << 2) | SP_INCL);
+    }
+    s_prefix = prefix;
+    if (total_out && base + SCAN_TILE >= n) *total_out = prefix + agg;  // the last tile
+  }
+  __syncthreads();
+  ex += s_prefix;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const int64_t k = base + i;
+    if (k < n) out[k] = ex;
+    ex += v[i];
+  }
+}
+
 template <class Tin, class Tout>
 void scan_exclusive(const Tin *in, Tout *out, int64_t n, Tout *total_dev, Scratch &ws, cudaStream_t st) {
   if (n <= 0) {
@@ -172,13 +190,12 @@ void scan_exclusive(const Tin *in, Tout *out, int64_t n, Tout *total_dev, Scratc
     MM_LAUNCH_CHECK();
     return;
   }
-  int64_t nb = ceil_div(n, SCAN_TILE);
-  Tout *partial = static_cast<Tout *>(ws.need(sizeof(Tout) * (size_t)nb, st));
-  scan_reduce_kernel<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, partial, n);
-  MM_LAUNCH_CHECK();
-  scan_partials_kernel<Tout><<<1, SCAN_THREADS, 0, st>>>(partial, nb, total_dev);
-  MM_LAUNCH_CHECK();
-  scan_tiles_kernel<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, partial);
+  const int64_t nb = ceil_div(n, SCAN_TILE);
+  // tile states and the tile counter, cleared together
+  unsigned long long *status = static_cast<unsigned long long *>(ws.need(sizeof(unsigned long long) * (size_t)(nb + 1), st));
+  MM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(nb + 1), st));
+  scan_onepass<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, total_dev, status,
+                                                                  reinterpret_cast<unsigned int *>(status + nb));
   MM_LAUNCH_CHECK();
 }
 
@@ -296,6 +313,10 @@ void radix_sort(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_
 }
 
 }  // namespace
+
+void read_wait_fault(uint32_t *host, cudaStream_t st) {
+  MM_CUDA_TRY(cudaMemcpyFromSymbolAsync(host, g_wait_fault, sizeof(uint32_t), 0, cudaMemcpyDeviceToHost, st));
+}
 
 void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, Scratch &ws,
                         cudaStream_t st) {

@@ -205,7 +205,10 @@ void load_finish(mm_system *s) {
   MM_CUDA_TRY(cudaMemcpyAsync(&s->summary, reinterpret_cast<LoadSummary *>(s->d_u64 + 4), sizeof(LoadSummary),
                               cudaMemcpyDeviceToHost, st));
   MM_CUDA_TRY(cudaMemcpyAsync(&s->load_err, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  uint32_t fault = 0;
+  read_wait_fault(&fault, st);
   MM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (fault) throw MmError{MM_ETIMEOUT, "load: a bounded device-side wait gave up"};
   const uint32_t err = s->load_err;
   s->summary.err = err & VE_ERRORS;
   s->methods_by_class = !(err & VI_METHODS_UNSORTED);
