@@ -429,6 +429,14 @@ MMREF_API int32_t mm_abi_version(void);
  * (all threads, all systems); for accounting in benchmarks. */
 MMREF_API int64_t mm_launch_count(void);
 
+/* Failure-detection self test of the bounded device-side waits (the look-back
+ * of the exclusive scan used by load, metrics and lists; Merrill and Garland,
+ * 2016).  Runs one scan tile on the current device whose predecessor tile is
+ * never processed, so its wait gives up after about a second; returns
+ * MM_ETIMEOUT when the host read the fault flag as designed (and clears it),
+ * MM_OK if the wait did not run out, MM_ECUDA on a CUDA error.  Needs a GPU. */
+MMREF_API mm_status mm_selftest_bounded_wait(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -380,4 +380,10 @@ int32_t mm_abi_version(void) { return MMREF_ABI_VERSION; }
 
 int64_t mm_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
+mm_status mm_selftest_bounded_wait(void) {
+  return guarded([&] {
+    if (stalled_scan_probe()) throw MmError{MM_ETIMEOUT, "selftest: the stalled scan's wait gave up as designed"};
+  });
+}
+
 }  // extern "C"

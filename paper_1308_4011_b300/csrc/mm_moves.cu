@@ -2092,7 +2092,10 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
       MM_CUDA_TRY(cudaMemcpyAsync(hc, s->d_u64 + 1, sizeof(hc), cudaMemcpyDeviceToHost, st));
       read_wait_fault(&fault, st);
       MM_CUDA_TRY(cudaStreamSynchronize(st));
-      if (fault) throw MmError{MM_ETIMEOUT, "suggest: a bounded device-side wait gave up"};
+        if (fault) {
+        clear_wait_fault();
+        throw MmError{MM_ETIMEOUT, "suggest: a bounded device-side wait gave up"};
+      }
       K = (int64_t)hc[0];
       nm = (int64_t)hc[1];
       if (K <= cap) break;

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(const Tin *in
 // flag).  The wait is bounded: past the limit the block records a fault in
 // g_wait_fault (read back by the host at its next synchronisation) and goes on.
 constexpr unsigned long long SP_AGG = 1ull, SP_INCL = 2ull;
-constexpr int SP_WAIT_LIMIT = 1 << 22;
+constexpr int SP_WAIT_LIMIT = 1 << 21;  // about a second of polling
 
 template <class Tin, class Tout>
 __global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(const Tin *in, Tout *out, int64_t n, Tout *total_out,
@@ -316,6 +316,39 @@ void radix_sort(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_
 
 void read_wait_fault(uint32_t *host, cudaStream_t st) {
   MM_CUDA_TRY(cudaMemcpyFromSymbolAsync(host, g_wait_fault, sizeof(uint32_t), 0, cudaMemcpyDeviceToHost, st));
+}
+
+void clear_wait_fault() {
+  const uint32_t zero = 0;
+  MM_CUDA_TRY(cudaMemcpyToSymbol(g_wait_fault, &zero, sizeof(zero)));
+}
+
+// One block scans tile 1 of a two-tile input while tile 0 is never processed
+// (the tile counter starts at 1), so its look-back wait runs out.  Returns the
+// fault flag the host reads afterwards (and clears it).
+uint32_t stalled_scan_probe() {
+  int32_t *in = nullptr;
+  int64_t *out = nullptr;
+  unsigned long long *status = nullptr;
+  const int64_t n = 2 * (int64_t)SCAN_TILE;
+  MM_CUDA_TRY(cudaMalloc(&in, sizeof(int32_t) * (size_t)n));
+  MM_CUDA_TRY(cudaMalloc(&out, sizeof(int64_t) * (size_t)n));
+  MM_CUDA_TRY(cudaMalloc(&status, sizeof(unsigned long long) * 3));
+  MM_CUDA_TRY(cudaMemset(in, 0, sizeof(int32_t) * (size_t)n));
+  MM_CUDA_TRY(cudaMemset(status, 0, sizeof(unsigned long long) * 3));
+  const unsigned int first = 1;
+  MM_CUDA_TRY(cudaMemcpy(status + 2, &first, sizeof(first), cudaMemcpyHostToDevice));
+  scan_onepass<int32_t, int64_t><<<1, SCAN_THREADS>>>(in, out, n, nullptr, status,
+                                                       reinterpret_cast<unsigned int *>(status + 2));
+  MM_LAUNCH_CHECK();
+  MM_CUDA_TRY(cudaDeviceSynchronize());
+  uint32_t fault = 0;
+  MM_CUDA_TRY(cudaMemcpyFromSymbol(&fault, g_wait_fault, sizeof(fault)));
+  clear_wait_fault();
+  cudaFree(in);
+  cudaFree(out);
+  cudaFree(status);
+  return fault;
 }
 
 void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, Scratch &ws,

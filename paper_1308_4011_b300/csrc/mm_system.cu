@@ -208,7 +208,10 @@ void load_finish(mm_system *s) {
   uint32_t fault = 0;
   read_wait_fault(&fault, st);
   MM_CUDA_TRY(cudaStreamSynchronize(st));
-  if (fault) throw MmError{MM_ETIMEOUT, "load: a bounded device-side wait gave up"};
+  if (fault) {
+    clear_wait_fault();
+    throw MmError{MM_ETIMEOUT, "load: a bounded device-side wait gave up"};
+  }
   const uint32_t err = s->load_err;
   s->summary.err = err & VE_ERRORS;
   s->methods_by_class = !(err & VI_METHODS_UNSORTED);

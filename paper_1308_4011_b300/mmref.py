@@ -34,7 +34,7 @@ EXPORTED = ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluat
             "mm_launch_count", "mm_suggest_moves_noalloc", "mm_batch_create", "mm_batch_set_tile",
             "mm_batch_autotune", "mm_batch_run", "mm_batch_suggestions", "mm_batch_free", "mm_apply_edit",
             "mm_export_system", "mm_server_create", "mm_server_add_system", "mm_server_run", "mm_server_stats_get",
-            "mm_server_snapshot", "mm_server_free")
+            "mm_server_snapshot", "mm_server_free", "mm_selftest_bounded_wait")
 
 CLASS_METRICS_DTYPE = np.dtype([("n_methods", "<i4"), ("n_attrs", "<i4"), ("P", "<i8"), ("Q", "<i8"),
                                 ("S", "<i8"), ("lcom_ck", "<i8"), ("hs_num", "<i8"), ("hs_den", "<i8"),
@@ -130,6 +130,12 @@ def _check(st: int):
 
 def abi_version() -> int:
     return int(_lib.mm_abi_version())
+
+
+def selftest_bounded_wait() -> int:
+    """mm_selftest_bounded_wait: the status the host reads after a device-side
+    wait that cannot be satisfied ran out (MM_ETIMEOUT when it works)."""
+    return int(_lib.mm_selftest_bounded_wait())
 
 
 def launch_count() -> int:
