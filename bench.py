@@ -141,8 +141,8 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     seed_offset = 1000 * rank  # independent replica per rank (weak scaling)
     params = dict(synth.MEDIUM)
-    if args.case == "small":  # profiling case: medium degrees and locality, 1,000 classes x 12,000 methods
-        params.update(n_classes=1000, n_methods=12000, n_attrs=6000, max_class=80)
+    if args.case == "small":  # profiling case: medium class count, degrees and locality, 12,000 methods
+        params.update(n_methods=12000, n_attrs=6000)
     params["seed"] = params["seed"] + seed_offset
     system = synth.generate(**params, name="medium")
     c, M = system.n_classes, system.n_methods
@@ -630,7 +630,7 @@ def main():
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--case", choices=["medium", "small"], default="medium",
-                    help="small = profiling case (1,000 classes, 12,000 methods, 192 MB of records); "
+                    help="small = profiling case (5,000 classes, 12,000 methods, 0.96 GB of records); "
                          "not a bench line")
     args = ap.parse_args()
     if args.warmup < 3:
