@@ -1722,13 +1722,117 @@ __global__ void __launch_bounds__(1024) bitonic_sort_moves(mm_move *v, int32_t n
   bitonic_block(v, n, sm);
 }
 
-// One block with dynamic shared memory (next power of two >= n moves, at most
-// BITONIC_BIG): the same bitonic sort for kept lists past the static limit.
-constexpr int BITONIC_BIG = 8192;
+// One block sorts up to KEYED_MAX kept moves in place.  Every move gets one
+// 64-bit key in the suggestion order (n_improved descending, then dLCOM, dCBO,
+// m, d ascending; each field biased by its minimum over the moves and given the
+// bits its range needs); keys and 16-bit indices go through a bitonic network
+// in shared memory (a tie, only ever with padding, is broken by the index),
+// then the moves are gathered in key order through the same shared memory.
+// If the fields' ranges need more than 64 bits, the moves themselves go
+// through the network.  The count is read on the device when count is given,
+// so a caller needs no round trip first; nothing happens unless
+// 2 <= K <= min(cap, KEYED_MAX).
+constexpr int KEYED_MAX = 8192;
+constexpr size_t KEYED_SMEM = (sizeof(mm_move) + sizeof(uint16_t)) * KEYED_MAX;
 
-__global__ void __launch_bounds__(1024) bitonic_sort_moves_big(mm_move *v, int32_t n) {
-  extern __shared__ __align__(16) unsigned char bsm[];
-  bitonic_block(v, n, reinterpret_cast<mm_move *>(bsm));
+__device__ __forceinline__ int bits_dev(uint32_t v) { return v ? 32 - __clz(v) : 0; }  // bits for [0, v]
+
+__global__ void __launch_bounds__(1024) sort_kept_keyed(mm_move *v, const unsigned long long *count, int32_t n,
+                                                        int64_t cap, int32_t c, int32_t M) {
+  extern __shared__ __align__(16) unsigned char ksm[];
+  __shared__ int32_t red[6][32];
+  const int64_t K = count ? (int64_t)*count : (int64_t)n;
+  if (K < 2 || K > cap || K > KEYED_MAX) return;
+  const int32_t k = (int32_t)K;
+  int32_t np = 1;
+  while (np < k) np <<= 1;
+  const int tid = (int)threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // ranges of n_improved, dLCOM, dCBO
+  int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+  for (int32_t i = tid; i < k; i += 1024) {
+    const mm_move a = v[i];
+    const int32_t f[3] = {a.n_improved, a.d_lcom_ck_sum, a.d_cbo_sum};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      lo[q] = min(lo[q], f[q]);
+      hi[q] = max(hi[q], f[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[q] = min(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+      hi[q] = max(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+    }
+    if (lane == 0) {
+      red[2 * q][warp] = lo[q];
+      red[2 * q + 1][warp] = hi[q];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    lo[q] = red[2 * q][lane];
+    hi[q] = red[2 * q + 1][lane];
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[q] = min(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+      hi[q] = max(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+    }
+  }
+  const int w_d = bits_dev((uint32_t)max(c - 1, 0)), w_m = bits_dev((uint32_t)max(M - 1, 0));
+  const int w_cbo = bits_dev((uint32_t)((int64_t)hi[2] - lo[2])), w_ck = bits_dev((uint32_t)((int64_t)hi[1] - lo[1]));
+  const int w_n = bits_dev((uint32_t)((int64_t)hi[0] - lo[0]));
+  if (w_d + w_m + w_cbo + w_ck + w_n > 64) {  // every block thread sees the same ranges
+    __syncthreads();
+    bitonic_block(v, k, reinterpret_cast<mm_move *>(ksm));
+    return;
+  }
+  const int s_cbo = w_d + w_m, s_ck = s_cbo + w_cbo, s_n = s_ck + w_ck;
+  uint64_t *key = reinterpret_cast<uint64_t *>(ksm);
+  uint16_t *idx = reinterpret_cast<uint16_t *>(ksm + sizeof(mm_move) * KEYED_MAX);
+  for (int32_t i = tid; i < np; i += 1024) {
+    uint64_t kk = ~0ull;  // padding sorts last
+    if (i < k) {
+      const mm_move a = v[i];
+      kk = ((uint64_t)(uint32_t)a.m << w_d) | (uint64_t)(uint32_t)a.d;
+      if (w_cbo) kk |= (uint64_t)((uint32_t)a.d_cbo_sum - (uint32_t)lo[2]) << s_cbo;
+      if (w_ck) kk |= (uint64_t)((uint32_t)a.d_lcom_ck_sum - (uint32_t)lo[1]) << s_ck;
+      if (w_n) kk |= (uint64_t)((uint32_t)hi[0] - (uint32_t)a.n_improved) << s_n;
+    }
+    key[i] = kk;
+    idx[i] = (uint16_t)i;
+  }
+  __syncthreads();
+  for (int32_t k2 = 2; k2 <= np; k2 <<= 1) {
+    for (int32_t j = k2 >> 1; j > 0; j >>= 1) {
+      for (int32_t p = tid; p < (np >> 1); p += 1024) {
+        const int32_t i = ((p & ~(j - 1)) << 1) | (p & (j - 1)), ixj = i | j;
+        const uint64_t a = key[i], b = key[ixj];
+        const uint16_t ia = idx[i], ib = idx[ixj];
+        const bool gt = a > b || (a == b && ia > ib);
+        if (gt == ((i & k2) == 0)) {
+          key[i] = b;
+          key[ixj] = a;
+          idx[i] = ib;
+          idx[ixj] = ia;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  mm_move *mv = reinterpret_cast<mm_move *>(ksm);  // the keys are no longer needed
+  for (int32_t i = tid; i < k; i += 1024) mv[i] = v[idx[i]];
+  __syncthreads();
+  for (int32_t i = tid; i < k; i += 1024) v[i] = mv[i];
+}
+
+static void keyed_sort_launch(mm_move *v, const unsigned long long *count, int32_t n, int64_t cap, int32_t c,
+                              int32_t M, cudaStream_t st) {
+  static const cudaError_t attr = cudaFuncSetAttribute(sort_kept_keyed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)KEYED_SMEM);
+  MM_CUDA_TRY(attr);
+  sort_kept_keyed<<<1, 1024, KEYED_SMEM, st>>>(v, count, n, cap, c, M);
+  MM_LAUNCH_CHECK();
 }
 
 // block i sorts segment i (base + i*stride, counts[i] moves) when it fits in one block
@@ -1969,23 +2073,15 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
   if (kind == MM_PTR_HOST) MM_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
-// Sort kept moves in the suggestion order: one-block bitonic sort up to 2,048,
-// else a stable LSD radix sort field by field (d, m, dCBO, dLCOM, n_improved desc)
-// through a permutation.
+// Sort kept moves in the suggestion order: one-block keyed bitonic sort up to
+// 8,192, else a radix sort of 64-bit composite keys when the fields' ranges fit,
+// else a stable LSD radix sort field by field (d, m, dCBO, dLCOM, n_improved
+// desc) through a permutation.
 void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K) {
   cudaStream_t st = s->stream;
-  if (K > 1 && K <= BITONIC_MAX) {
-    bitonic_sort_moves<<<1, 1024, 0, st>>>(kept, (int32_t)K);
-    MM_LAUNCH_CHECK();
-  } else if (K > BITONIC_MAX && K <= BITONIC_BIG) {
-    int32_t np = 1;
-    while (np < K) np <<= 1;
-    const size_t smem = sizeof(mm_move) * (size_t)np;
-    MM_CUDA_TRY(cudaFuncSetAttribute(bitonic_sort_moves_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(sizeof(mm_move) * BITONIC_BIG)));
-    bitonic_sort_moves_big<<<1, 1024, smem, st>>>(kept, (int32_t)K);
-    MM_LAUNCH_CHECK();
-  } else if (K > BITONIC_BIG) {
+  if (K > 1 && K <= KEYED_MAX) {
+    keyed_sort_launch(kept, nullptr, (int32_t)K, K, s->c, s->M, st);
+  } else if (K > KEYED_MAX) {
     // the fields' actual ranges decide whether one 64-bit composite key holds them all
     int32_t *d_mm = reinterpret_cast<int32_t *>(s->d_u64 + 24);
     const int32_t init[6] = {INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN};
@@ -2055,7 +2151,7 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
   prepare_candidates(s, cands, &rowptr, &dst, &n_cand, s->stage_ws, &chash);
   int64_t K = 0, nm = 0;
   mm_move *kept = nullptr;
-  // Host outputs of up to BITONIC_MAX kept moves need one round trip: the sort
+  // Host outputs of up to KEYED_MAX kept moves need one round trip: the sort
   // (which checks the count on the device) and the copy of the first moves
   // are queued before the count is read back.
   std::vector<mm_move> staged;
@@ -2079,10 +2175,9 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
       MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 2, 0, sizeof(unsigned long long), st));
       count_marks<<<148 * 4, 256, 0, st>>>(mark, s->M, s->d_u64 + 2);
       MM_LAUNCH_CHECK();
-      // sorts the kept moves in place when 2 <= K <= min(cap, BITONIC_MAX), else leaves them
-      bitonic_sort_segments<<<1, 1024, 0, st>>>(kept, cap, s->d_u64 + 1);
-      MM_LAUNCH_CHECK();
-      const int64_t nstage = kind == MM_PTR_HOST ? std::min<int64_t>({(int64_t)k, cap, BITONIC_MAX}) : 0;
+      // sorts the kept moves in place when 2 <= K <= min(cap, KEYED_MAX), else leaves them
+      keyed_sort_launch(kept, s->d_u64 + 1, 0, cap, s->c, s->M, st);
+      const int64_t nstage = kind == MM_PTR_HOST ? std::min<int64_t>({(int64_t)k, cap, (int64_t)KEYED_MAX}) : 0;
       staged.resize((size_t)nstage);
       if (nstage > 0)
         MM_CUDA_TRY(cudaMemcpyAsync(staged.data(), kept, sizeof(mm_move) * (size_t)nstage,
@@ -2110,7 +2205,7 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
     s->kept_lists = rowptr != nullptr;
     s->kept_hash = chash;
     s->kept_ncand = n_cand;
-    sorted_early = K <= BITONIC_MAX;
+    sorted_early = K <= KEYED_MAX;
     if (!sorted_early) sort_kept_moves(s, kept, K);
   }
   const int64_t nout = std::min<int64_t>(k, K);

@@ -301,6 +301,24 @@ def test_class_too_big_for_shared_bitmaps():
     assert int(rec["s"][0]) == a + k and int(rec["t"][0]) == 2
 
 
+@pytest.mark.parametrize("c,M", [(200, 2500), (300, 5000), (300, 10000)])
+def test_kept_sort_regimes(c, M):
+    """About 1,900, 4,000 and 32,000 kept moves (CBO, min_improved 1): the
+    one-block keyed sort below and above 2,048 moves and the radix sort above
+    8,192 give the oracle's full suggestion order, straight after the metrics
+    and after an evaluation cached the kept moves."""
+    s = synth.generate(n_classes=c, n_methods=M, n_attrs=M, max_class=max(40, 3 * M // c), seed=7)
+    ref = oracle.Oracle(s, threads=4).evaluate(mask=4, min_improved=1)
+    g, _, _ = gpu_load(s)
+    top, nk, nm = mmref.suggest_moves(g, k=ref.n_kept, mask=4, min_improved=1)
+    assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+    assert kept_tuples(top) == oracle_kept(ref)
+    assert gpu_digest(g, 4, 1) == ref.digest
+    top2, nk2, _ = mmref.suggest_moves(g, k=100, mask=4, min_improved=1)
+    assert nk2 == nk and kept_tuples(top2) == oracle_kept(ref)[:100]
+    g.free()
+
+
 def test_relabelled_system_gives_permuted_results():
     s = tiny_random(5)
     p, pc, pm, pa = permute(s, 3)
