@@ -144,9 +144,9 @@ void enqueue_metrics(mm_batch *b) {
 // The scratch buffers the metric pipeline uses (their addresses are baked into
 // a captured graph).
 std::vector<void *> pipeline_scratch(const mm_system *s) {
-  return {s->sort_ws.ptr,      s->eval_ws.ptr,      s->union_ws.ptr,     s->side_eval[0].ptr,
-          s->side_eval[1].ptr, s->side_sort[0].ptr, s->side_sort[1].ptr, s->side_union[0].ptr,
-          s->side_union[1].ptr};
+  return {s->sort_ws.ptr,       s->eval_ws.ptr,       s->union_ws.ptr,      s->side_eval[0].ptr,
+          s->side_eval[1].ptr,  s->side_eval[2].ptr,  s->side_sort[0].ptr,  s->side_sort[1].ptr,
+          s->side_sort[2].ptr,  s->side_union[0].ptr, s->side_union[1].ptr, s->side_union[2].ptr};
 }
 
 bool scratch_moved(const mm_batch *b) {

@@ -50,10 +50,10 @@ void use_device(mm_system *s) {
 void release_system(mm_system *s) {
   s->arena.release();
   for (Scratch *w : {&s->sort_ws, &s->eval_ws, &s->stage_ws, &s->kept_ws, &s->edit_ws, &s->union_ws,
-                     &s->side_eval[0], &s->side_eval[1], &s->side_sort[0], &s->side_sort[1], &s->side_union[0],
-                     &s->side_union[1]})
+                     &s->side_eval[0], &s->side_eval[1], &s->side_eval[2], &s->side_sort[0], &s->side_sort[1],
+                     &s->side_sort[2], &s->side_union[0], &s->side_union[1], &s->side_union[2]})
     w->release(s->stream);
-  for (cudaEvent_t e : {s->fork_ev, s->join_ev[0], s->join_ev[1]})
+  for (cudaEvent_t e : {s->fork_ev, s->join_ev[0], s->join_ev[1], s->join_ev[2], s->mid_ev[0], s->mid_ev[1]})
     if (e) cudaEventDestroy(e);
   delete s;
 }
@@ -207,6 +207,9 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     MM_CUDA_TRY(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
     MM_CUDA_TRY(cudaEventCreateWithFlags(&s->join_ev[0], cudaEventDisableTiming));
     MM_CUDA_TRY(cudaEventCreateWithFlags(&s->join_ev[1], cudaEventDisableTiming));
+    MM_CUDA_TRY(cudaEventCreateWithFlags(&s->join_ev[2], cudaEventDisableTiming));
+    MM_CUDA_TRY(cudaEventCreateWithFlags(&s->mid_ev[0], cudaEventDisableTiming));
+    MM_CUDA_TRY(cudaEventCreateWithFlags(&s->mid_ev[1], cudaEventDisableTiming));
     s->c = desc->n_classes;
     s->M = desc->n_methods;
     s->A = desc->n_attrs;
@@ -328,8 +331,9 @@ mm_status mm_system_info_get(mm_system *s, mm_system_info *info) {
     info->device_bytes =
         s->arena.bytes + (int64_t)(s->sort_ws.cap + s->eval_ws.cap + s->stage_ws.cap + s->kept_ws.cap +
                                    s->edit_ws.cap + s->union_ws.cap + s->side_eval[0].cap + s->side_eval[1].cap +
-                                   s->side_sort[0].cap + s->side_sort[1].cap + s->side_union[0].cap +
-                                   s->side_union[1].cap);
+                                   s->side_eval[2].cap + s->side_sort[0].cap + s->side_sort[1].cap +
+                                   s->side_sort[2].cap + s->side_union[0].cap + s->side_union[1].cap +
+                                   s->side_union[2].cap);
   });
 }
 

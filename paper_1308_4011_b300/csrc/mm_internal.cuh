@@ -134,10 +134,12 @@ struct mm_system {
   Scratch edit_ws;     // edit patches and incremental re-evaluation
   Scratch union_ws;    // per-warp bitmaps of accessor unions (largest classes only)
   // independent branches of the metric pipeline run on side streams, each with
-  // its own scratch: [0] LCOM (own-access index, pair counts), [1] list L
-  Scratch side_eval[2], side_sort[2], side_union[2];
-  cudaEvent_t fork_ev = nullptr, join_ev[2] = {nullptr, nullptr};
-  cudaStream_t side_pending[2] = {nullptr, nullptr};  // stream a branch was issued on
+  // its own scratch: [0] LCOM (own-access index, pair counts), [1] list L,
+  // [2] list R; mid_ev marks points other branches wait for: [0] the multigraph
+  // is built (system stream), [1] the own-access lists are built (branch 0)
+  Scratch side_eval[3], side_sort[3], side_union[3];
+  cudaEvent_t fork_ev = nullptr, join_ev[3] = {nullptr, nullptr, nullptr}, mid_ev[2] = {nullptr, nullptr};
+  cudaStream_t side_pending[3] = {nullptr, nullptr, nullptr};  // stream a branch was issued on
   bool kept_valid = false;   // kept_ws holds the kept moves of the last evaluation for:
   uint32_t kept_mask = 0;    //   this metric mask
   int32_t kept_min = 0;      //   and this min_improved
@@ -241,6 +243,14 @@ UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted, Scratch &ws, cudaSt
 cudaStream_t fork_side(mm_system *s, int i);
 // Make s->stream wait for branch i (no-op when the branch ran on s->stream).
 void join_side(mm_system *s, int i, cudaStream_t branch);
+// Marks point k (mid_ev[k]) on stream from; makes stream to wait for it (no-op
+// when both are the same stream, as during capture).
+void mark_point(mm_system *s, int k, cudaStream_t from);
+void wait_point(mm_system *s, int k, cudaStream_t from, cudaStream_t to);
+// The move lists' first half (per-method keys, sorts, offsets, fills), forked
+// onto side streams 1 and 2 before the coupling branch; build_move_precompute
+// finishes them (multigraph look-ups, s per L entry, headers).
+void begin_move_lists(mm_system *s);
 // Number of distinct methods of class K that access at least one of the
 // attributes of K in acc_row[0 .. len): the union of their accessor lists,
 // counted in a per-warp bitmap over K's method ranks.  The accessor elements

@@ -69,6 +69,12 @@ __global__ void own_access_fill(const int32_t *method_class, const int32_t *meth
 // is its accessor list; methods with two or more are taken by the whole warp
 // in turn, with bitmap words per warp in shared memory, or in a zeroed global
 // slice when the largest class is too big.
+// A warp owns LU_G consecutive methods (one per lane); each method with two or
+// more own attributes takes the whole warp for its accessor union, one after
+// the other, so the methods per warp set the length of its chain of dependent
+// loads: a small group keeps that chain short.
+constexpr int LU_G = 8;
+
 __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, const int64_t *acc_rowptr,
                                                   const int32_t *acc_idx, const int32_t *attr_class,
                                                   const int64_t *own_ptr, const int32_t *own_list,
@@ -80,11 +86,12 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
   if (!gbm)
     for (int32_t i = (int32_t)lane; i < words; i += 32) bm[i] = 0u;
   __syncwarp();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < M; base += stride) {
-    const int64_t x = base + threadIdx.x;
-    const int32_t ox = x < M ? own[x] : 0;
-    const int32_t C = x < M ? method_class[x] : 0;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t wg = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; wg * LU_G < M; wg += nwarps) {
+    const int64_t base = wg * LU_G, x = base + lane;
+    const bool mine = lane < (uint32_t)LU_G && x < M;
+    const int32_t ox = mine ? own[x] : 0;
+    const int32_t C = mine ? method_class[x] : 0;
     int32_t u = 0;
     if (ox == 1) {
       for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
@@ -99,14 +106,14 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
     while (multi) {
       const int src = __ffs(multi) - 1;
       multi &= multi - 1u;
-      const int64_t xs = base + (threadIdx.x & ~31u) + src;  // method of lane src
+      const int64_t xs = base + src;  // method of lane src
       const int32_t Cs = __shfl_sync(0xffffffffu, C, src);
       const int64_t a0 = acc_rowptr[xs];
       const int32_t v = accessor_union(acc_idx + a0, acc_rowptr[xs + 1] - a0, Cs, attr_class, own_ptr, own_list,
                                        bm, lane);
       if ((int)lane == src) u = v;
     }
-    if (x < M) {
+    if (mine) {
       const int32_t qx = u > 0 ? u - 1 : 0;
       q[x] = qx;
       if (qx) atomicAdd(reinterpret_cast<unsigned long long *>(&cls_Q[C]), (unsigned long long)qx);
@@ -311,7 +318,7 @@ namespace {
 // (errors ignored: at process exit the runtime may already be gone).
 struct SideStreams {
   int device = -1;
-  cudaStream_t s[2] = {nullptr, nullptr};
+  cudaStream_t s[3] = {nullptr, nullptr, nullptr};
   ~SideStreams() {
     for (cudaStream_t &x : s)
       if (x) {
@@ -343,12 +350,21 @@ void join_side(mm_system *s, int i, cudaStream_t branch) {
   MM_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->join_ev[i], 0));
 }
 
+void mark_point(mm_system *s, int k, cudaStream_t from) {
+  if (s->mid_ev[k]) MM_CUDA_TRY(cudaEventRecord(s->mid_ev[k], from));
+}
+
+void wait_point(mm_system *s, int k, cudaStream_t from, cudaStream_t to) {
+  if (from != to && s->mid_ev[k]) MM_CUDA_TRY(cudaStreamWaitEvent(to, s->mid_ev[k], 0));
+}
+
 void build_metrics(mm_system *s) {
   cudaStream_t st = s->stream;
   const int32_t c = s->c, M = s->M;
 
   // branch A (side stream 0): inverted index of own accesses, own, S, LCOM pair
-  // counts, P and Q, destination records; branch B (below, on the system's
+  // counts, P and Q, destination records; lists L and R (side streams 1 and 2,
+  // finished by build_move_precompute); branch B (below, on the system's
   // stream): coupling and the adjacency structures.  They share no buffer.
   {
     cudaStream_t sa = fork_side(s, 0);
@@ -373,8 +389,11 @@ void build_metrics(mm_system *s) {
       own_access_fill<<<grid_for(M), TPB, 0, sa>>>(s->method_class, s->method_local, s->acc_rowptr, s->acc_idx,
                                                     s->attr_class, M, s->own_ptr, cursor, s->own_list);
       MM_LAUNCH_CHECK();
+    }
+    mark_point(s, 1, sa);  // own-access lists built (the s of list L entries needs them)
+    if (M > 0 && A > 0) {
       // LCOM pair counts from accessor unions
-      const UnionBitmap ub = union_bitmap(s, ceil_div(M, 32), uw, sa);
+      const UnionBitmap ub = union_bitmap(s, ceil_div(M, LU_G), uw, sa);
       lcom_union<<<ub.grid, 256, ub.smem, sa>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class,
                                                  s->own_ptr, s->own_list, s->own, M, ub.words, ub.gbm, s->q,
                                                  s->cls_Q);
@@ -387,6 +406,8 @@ void build_metrics(mm_system *s) {
     MM_LAUNCH_CHECK();
     s->side_pending[0] = sa;
   }
+  // lists L and R (first half) on side streams 1 and 2
+  begin_move_lists(s);
 
   // coupling: mark the use edges in the out-rows, count and enumerate the
   // marked classes row by row (ascending, so no sort), then count multiplicities
@@ -417,6 +438,7 @@ void build_metrics(mm_system *s) {
     MM_LAUNCH_CHECK();
   }
   MM_CUDA_TRY(cudaMemcpyAsync(s->mg_count, s->mg_rowptr + c, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  mark_point(s, 0, st);  // multigraph rows and counts built (the list look-ups need them)
   // compressed adjacency: record counts -> exclusive scan -> packed non-zero words
   {
     const int64_t ns = s->sum_words * (2 * (int64_t)c + 1);

@@ -430,96 +430,127 @@ __global__ void build_headers(const int32_t *method_class, const int32_t *cls_n,
 
 }  // namespace
 
-void build_move_precompute(mm_system *s) {
-  cudaStream_t st = s->stream;
+// Scratch of the two list branches: list L in side_eval[1] (side stream 1),
+// list R in side_eval[2] (side stream 2).  Both halves of the list build call
+// this with the same sizes, so they see the same buffers.
+namespace {
+struct ListBufs {
+  uint32_t *lkeys, *lsorted, *rkeys, *rsorted;
+  int64_t *l_off, *rin_off, *r_off;
+  int32_t *l_len, *out_self, *r_len, *in_self, *cursor;
+  uint8_t *llong, *rlong;
+};
+
+ListBufs list_bufs(mm_system *s, cudaStream_t sl, cudaStream_t sr) {
   const int32_t M = s->M;
-  if (M == 0) return;
   const int64_t nu = s->n_call + s->n_acc, nc = s->n_call;
-  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * 32, TPB), 148 * 16);
-  // Two branches sharing no buffer: list L on side stream 1, list R on the
-  // system's stream; the headers join them.
-  cudaStream_t sl = fork_side(s, 1);
   // L part: keys, sorted keys (u32, nu); l_off (i64, M + 1); l_len, out_self (i32, M)
   // R part: keys, sorted keys (u32, nc); rin_off, r_off (i64, M + 1); r_len, in_self, cursor (i32, M)
   auto part_bytes = [&](int64_t nkeys, int n64, int n32) {
     return (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nkeys, 1) + 15) / 16 * 16 +
            sizeof(int64_t) * (size_t)n64 * ((size_t)M + 1) + sizeof(int32_t) * (size_t)n32 * (size_t)M + 64;
   };
-  const size_t lb = (part_bytes(nu, 1, 2) + (size_t)M + 255) / 256 * 256, rbytes = part_bytes(nc, 2, 3) + (size_t)M;
-  // the branches use their own scratch whether or not they run concurrently, so
-  // the buffers (and a captured graph's pointers) do not depend on the mode
+  const size_t lb = part_bytes(nu, 1, 2) + (size_t)M, rbytes = part_bytes(nc, 2, 3) + (size_t)M;
   char *lbase = static_cast<char *>(s->side_eval[1].need(lb, sl));
-  char *rbase = static_cast<char *>(s->eval_ws.need(rbytes, st));
-  uint32_t *lkeys = reinterpret_cast<uint32_t *>(lbase), *lsorted = lkeys + std::max<int64_t>(nu, 1);
-  int64_t *l_off = reinterpret_cast<int64_t *>(lbase + (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nu, 1) + 15) / 16 * 16);
-  int32_t *l_len = reinterpret_cast<int32_t *>(l_off + (M + 1));
-  int32_t *out_self = l_len + M;
-  uint8_t *llong = reinterpret_cast<uint8_t *>(out_self + M);  // segments left to the warp version
-  uint32_t *rkeys = reinterpret_cast<uint32_t *>(rbase), *rsorted = rkeys + std::max<int64_t>(nc, 1);
-  int64_t *rin_off = reinterpret_cast<int64_t *>(rbase + (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nc, 1) + 15) / 16 * 16);
-  int64_t *r_off = rin_off + (M + 1);
-  int32_t *r_len = reinterpret_cast<int32_t *>(r_off + (M + 1));
-  int32_t *in_self = r_len + M;
-  int32_t *cursor = in_self + M;
-  uint8_t *rlong = reinterpret_cast<uint8_t *>(cursor + M);
+  char *rbase = static_cast<char *>(s->side_eval[2].need(rbytes, sr));
+  ListBufs b;
+  b.lkeys = reinterpret_cast<uint32_t *>(lbase);
+  b.lsorted = b.lkeys + std::max<int64_t>(nu, 1);
+  b.l_off = reinterpret_cast<int64_t *>(lbase + (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nu, 1) + 15) / 16 * 16);
+  b.l_len = reinterpret_cast<int32_t *>(b.l_off + (M + 1));
+  b.out_self = b.l_len + M;
+  b.llong = reinterpret_cast<uint8_t *>(b.out_self + M);  // segments left to the warp version
+  b.rkeys = reinterpret_cast<uint32_t *>(rbase);
+  b.rsorted = b.rkeys + std::max<int64_t>(nc, 1);
+  b.rin_off = reinterpret_cast<int64_t *>(rbase + (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nc, 1) + 15) / 16 * 16);
+  b.r_off = b.rin_off + (M + 1);
+  b.r_len = reinterpret_cast<int32_t *>(b.r_off + (M + 1));
+  b.in_self = b.r_len + M;
+  b.cursor = b.in_self + M;
+  b.rlong = reinterpret_cast<uint8_t *>(b.cursor + M);
+  return b;
+}
+}  // namespace
 
-  // list L: per-method sort of the use keys, runs counted, scanned, written; s per entry
-  {
-    Scratch &sw_ = s->side_sort[1];
-    Scratch &uw = s->side_union[1];
-    if (nu > 0) {
-      method_use_keys32<<<grid_for(M), TPB, 0, sl>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
-                                                     s->acc_idx, s->attr_class, M, lkeys);
-      MM_LAUNCH_CHECK();
-    }
-    segment_sort_count_block<<<grid_for(M), 256, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lkeys, lsorted, 1,
-                                                          s->method_class, s->cbo_attrs, l_len, out_self, llong);
+// First half of the move lists; needs only the input CSR and the class
+// structures, so it runs beside the metric branches.
+void begin_move_lists(mm_system *s) {
+  const int32_t M = s->M;
+  s->side_pending[1] = s->side_pending[2] = s->stream;
+  if (M == 0) return;
+  const int64_t nu = s->n_call + s->n_acc, nc = s->n_call;
+  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * 32, TPB), 148 * 16);
+  cudaStream_t sl = fork_side(s, 1), sr = fork_side(s, 2);
+  s->side_pending[1] = sl;
+  s->side_pending[2] = sr;
+  const ListBufs b = list_bufs(s, sl, sr);
+  // list L: per-method sort of the use keys, runs counted, scanned, written
+  if (nu > 0) {
+    method_use_keys32<<<grid_for(M), TPB, 0, sl>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
+                                                   s->acc_idx, s->attr_class, M, b.lkeys);
     MM_LAUNCH_CHECK();
-    segment_sort_count<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lkeys, lsorted, 1, s->method_class,
-                                           s->cbo_attrs, l_len, out_self, llong);
-    MM_LAUNCH_CHECK();
-    scan_exclusive_i32to64(l_len, l_off, M, sw_, sl, l_off + M);
-    lists_fill_l<<<grid_for(M), 256, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, lsorted, s->method_class,
-                                               s->cbo_attrs, l_off, s->l_list, s->l_x);
-    MM_LAUNCH_CHECK();
-    if (nu > 0) {
-      lists_lookup_l<<<(unsigned)std::min<int64_t>(ceil_div(nu, TPB), 148 * 16), TPB, 0, sl>>>(
-          l_off + M, s->l_x, s->method_class, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list);
-      MM_LAUNCH_CHECK();
-    }
-    if (nu > 0) {
-      const UnionBitmap ub = union_bitmap(s, ceil_div(nu, 32), uw, sl);
-      l_entries_s<<<ub.grid, 256, ub.smem, sl>>>(s->l_list, s->l_x, l_off + M, s->acc_rowptr, s->acc_idx,
-                                                  s->attr_class, s->own_ptr, s->own_list, ub.words, ub.gbm,
-                                                  s->l_s);
-      MM_LAUNCH_CHECK();
-    }
   }
+  segment_sort_count_block<<<grid_for(M), 256, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, b.lkeys, b.lsorted, 1,
+                                                        s->method_class, s->cbo_attrs, b.l_len, b.out_self, b.llong);
+  MM_LAUNCH_CHECK();
+  segment_sort_count<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, b.lkeys, b.lsorted, 1, s->method_class,
+                                         s->cbo_attrs, b.l_len, b.out_self, b.llong);
+  MM_LAUNCH_CHECK();
+  scan_exclusive_i32to64(b.l_len, b.l_off, M, s->side_sort[1], sl, b.l_off + M);
+  lists_fill_l<<<grid_for(M), 256, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, b.lsorted, s->method_class,
+                                             s->cbo_attrs, b.l_off, s->l_list, s->l_x);
+  MM_LAUNCH_CHECK();
   // list R: callers bucketed by callee (counting sort on fan-in), per-callee sort, runs
-  scan_exclusive_i32to64(s->fan_in, rin_off, M, s->sort_ws, st, rin_off + M);
+  scan_exclusive_i32to64(s->fan_in, b.rin_off, M, s->side_sort[2], sr, b.rin_off + M);
   if (nc > 0) {
-    MM_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)M, st));
-    caller_classes_scatter<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, M, rin_off,
-                                                        cursor, rkeys);
+    MM_CUDA_TRY(cudaMemsetAsync(b.cursor, 0, sizeof(int32_t) * (size_t)M, sr));
+    caller_classes_scatter<<<grid_for(M), TPB, 0, sr>>>(s->method_class, s->call_rowptr, s->call_idx, M, b.rin_off,
+                                                        b.cursor, b.rkeys);
     MM_LAUNCH_CHECK();
   }
-  segment_sort_count_block<<<grid_for(M), 256, 0, st>>>(rin_off, nullptr, M, rkeys, rsorted, 0, s->method_class,
-                                                        s->cbo_attrs, r_len, in_self, rlong);
+  segment_sort_count_block<<<grid_for(M), 256, 0, sr>>>(b.rin_off, nullptr, M, b.rkeys, b.rsorted, 0,
+                                                        s->method_class, s->cbo_attrs, b.r_len, b.in_self, b.rlong);
   MM_LAUNCH_CHECK();
-  segment_sort_count<<<gw, TPB, 0, st>>>(rin_off, nullptr, M, rkeys, rsorted, 0, s->method_class, s->cbo_attrs,
-                                         r_len, in_self, rlong);
+  segment_sort_count<<<gw, TPB, 0, sr>>>(b.rin_off, nullptr, M, b.rkeys, b.rsorted, 0, s->method_class,
+                                         s->cbo_attrs, b.r_len, b.in_self, b.rlong);
   MM_LAUNCH_CHECK();
-  scan_exclusive_i32to64(r_len, r_off, M, s->sort_ws, st, r_off + M);
+  scan_exclusive_i32to64(b.r_len, b.r_off, M, s->side_sort[2], sr, b.r_off + M);
   if (nc > 0) {
-    lists_fill_r<<<grid_for(M), 256, 0, st>>>(rin_off, M, rsorted, s->method_class, r_off, s->r_list);
+    lists_fill_r<<<grid_for(M), 256, 0, sr>>>(b.rin_off, M, b.rsorted, s->method_class, b.r_off, s->r_list);
     MM_LAUNCH_CHECK();
-    lists_lookup_r<<<(unsigned)std::min<int64_t>(ceil_div(nc, TPB), 148 * 16), TPB, 0, st>>>(
-        r_off + M, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->r_list);
+  }
+}
+
+// Second half: multigraph counts of every entry (after the coupling branch),
+// s per L entry (after the own-access lists), then the per-method headers.
+void build_move_precompute(mm_system *s) {
+  cudaStream_t st = s->stream;
+  const int32_t M = s->M;
+  if (M == 0) return;
+  const int64_t nu = s->n_call + s->n_acc, nc = s->n_call;
+  cudaStream_t sl = s->side_pending[1], sr = s->side_pending[2];
+  const ListBufs b = list_bufs(s, sl, sr);
+  wait_point(s, 0, st, sl);
+  if (nu > 0) {
+    lists_lookup_l<<<(unsigned)std::min<int64_t>(ceil_div(nu, TPB), 148 * 16), TPB, 0, sl>>>(
+        b.l_off + M, s->l_x, s->method_class, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list);
+    MM_LAUNCH_CHECK();
+    wait_point(s, 1, s->side_pending[0], sl);
+    const UnionBitmap ub = union_bitmap(s, ceil_div(nu, 32), s->side_union[1], sl);
+    l_entries_s<<<ub.grid, 256, ub.smem, sl>>>(s->l_list, s->l_x, b.l_off + M, s->acc_rowptr, s->acc_idx,
+                                                s->attr_class, s->own_ptr, s->own_list, ub.words, ub.gbm, s->l_s);
+    MM_LAUNCH_CHECK();
+  }
+  wait_point(s, 0, st, sr);
+  if (nc > 0) {
+    lists_lookup_r<<<(unsigned)std::min<int64_t>(ceil_div(nc, TPB), 148 * 16), TPB, 0, sr>>>(
+        b.r_off + M, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->r_list);
     MM_LAUNCH_CHECK();
   }
   join_side(s, 1, sl);
+  join_side(s, 2, sr);
   build_headers<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S,
-                                             s->own, s->q, l_off, l_len, r_off, r_len, out_self, in_self,
+                                             s->own, s->q, b.l_off, b.l_len, b.r_off, b.r_len, b.out_self, b.in_self,
                                              s->l_list, M, s->hdr);
   MM_LAUNCH_CHECK();
 }

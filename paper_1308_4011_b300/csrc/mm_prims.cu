@@ -48,65 +48,57 @@ __device__ T block_exclusive_sum(T v, T *total) {
   return r;
 }
 
-// Small inputs: one block of 32 warps walks the array in 16K-element chunks
-// with a carry (one launch instead of three).  Warp w owns the 512 consecutive
-// elements [512 w, 512 w + 512) of a chunk and reads them as 16 coalesced rows
-// of 32; the block scans the 32 warp totals, then every warp rescans its rows.
+// Small inputs: one block of 32 warps; thread t scans its own run of
+// ceil(n / 1024) <= 16 consecutive elements (so an in-place scan is safe), the
+// block scans the 1,024 run totals, then every thread writes its run.
 constexpr int SCAN1_THREADS = 1024;
 constexpr int SCAN1_ROWS = 16;
-constexpr int SCAN1_CHUNK = SCAN1_THREADS * SCAN1_ROWS;
-constexpr int64_t SCAN1_MAX = SCAN1_CHUNK;  // one chunk; larger inputs use the three-kernel scan
+constexpr int64_t SCAN1_MAX = (int64_t)SCAN1_THREADS * SCAN1_ROWS;  // larger inputs: the one-pass scan
 
 template <class Tin, class Tout>
 __global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(const Tin *in, Tout *out, int64_t n,
                                                                    Tout *total_out) {
   __shared__ Tout wsum[SCAN1_THREADS / 32];
-  __shared__ Tout chunk_total;
+  __shared__ Tout block_total;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Tout carry = 0;
-  for (int64_t base = 0; base < n; base += SCAN1_CHUNK) {
-    const int64_t seg = base + (int64_t)warp * (32 * SCAN1_ROWS);
-    Tout v[SCAN1_ROWS];
-    Tout lsum = 0;
+  const int ipt = (int)((n + SCAN1_THREADS - 1) / SCAN1_THREADS);
+  const int64_t b0 = (int64_t)threadIdx.x * ipt;
+  Tout v[SCAN1_ROWS];
+  Tout sum = 0;
 #pragma unroll
-    for (int i = 0; i < SCAN1_ROWS; ++i) {
-      const int64_t k = seg + i * 32 + lane;
-      v[i] = k < n ? (Tout)in[k] : Tout(0);
-      lsum += v[i];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    if (lane == 0) wsum[warp] = lsum;
-    __syncthreads();
-    if (warp == 0) {
-      const Tout w = wsum[lane];
-      Tout wi = w;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const Tout y = __shfl_up_sync(0xffffffffu, wi, o);
-        if (lane >= o) wi += y;
-      }
-      wsum[lane] = wi - w;
-      if (lane == 31) chunk_total = wi;
-    }
-    __syncthreads();
-    Tout run = carry + wsum[warp];
-#pragma unroll
-    for (int i = 0; i < SCAN1_ROWS; ++i) {
-      Tout incl = v[i];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const Tout y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int64_t k = seg + i * 32 + lane;
-      if (k < n) out[k] = run + incl - v[i];
-      run += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    carry += chunk_total;
-    __syncthreads();
+  for (int i = 0; i < SCAN1_ROWS; ++i) {
+    const int64_t k = b0 + i;
+    v[i] = (i < ipt && k < n) ? (Tout)in[k] : Tout(0);
+    sum += v[i];
   }
-  if (threadIdx.x == 0 && total_out) *total_out = carry;
+  Tout incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const Tout y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const Tout w = wsum[lane];
+    Tout wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const Tout y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    wsum[lane] = wi - w;
+    if (lane == 31) block_total = wi;
+  }
+  __syncthreads();
+  Tout run = wsum[warp] + incl - sum;
+#pragma unroll
+  for (int i = 0; i < SCAN1_ROWS; ++i) {
+    const int64_t k = b0 + i;
+    if (i < ipt && k < n) out[k] = run;
+    run += v[i];
+  }
+  if (threadIdx.x == 0 && total_out) *total_out = block_total;
 }
 
 // Larger inputs: one pass over tiles of SCAN_TILE elements with decoupled
