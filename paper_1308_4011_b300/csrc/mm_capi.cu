@@ -69,6 +69,35 @@ void keep_pool_memory(int device) {
   done[device] = true;
 }
 
+// Up to six device-to-device copies (sizes in bytes, multiples of 4) in one launch.
+struct CopySeg {
+  void *dst;
+  const void *src;
+  int64_t bytes;
+};
+struct CopySegs {
+  CopySeg seg[6];
+  int n;
+};
+
+__global__ void copy_segments_kernel(CopySegs cs) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int k = 0; k < cs.n; ++k) {
+    const uint32_t *src = static_cast<const uint32_t *>(cs.seg[k].src);
+    uint32_t *dst = static_cast<uint32_t *>(cs.seg[k].dst);
+    const int64_t nw = cs.seg[k].bytes / 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) dst[i] = src[i];
+  }
+}
+
+void copy_segments(const CopySegs &cs, cudaStream_t st) {
+  int64_t words = 0;
+  for (int k = 0; k < cs.n; ++k) words = std::max<int64_t>(words, cs.seg[k].bytes / 4);
+  if (words == 0) return;
+  copy_segments_kernel<<<(unsigned)std::min<int64_t>(ceil_div(words, 256), 148 * 8), 256, 0, st>>>(cs);
+  MM_LAUNCH_CHECK();
+}
+
 template <class T>
 void upload(T *dst, const T *src, int64_t n, int32_t kind, cudaStream_t st) {
   if (n <= 0) return;
@@ -224,23 +253,37 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     s->acc_idx = a.get<int32_t>(s->n_acc);
     s->call_rowptr = a.get<int64_t>(M + 1);
     s->call_idx = a.get<int32_t>(s->n_call);
-    s->cls_n = a.get<int32_t>(c);
-    s->cls_a = a.get<int32_t>(c);
+    s->cls_n = a.get<int32_t>(2 * c);  // cls_a follows cls_n: one clear for both
+    s->cls_a = s->cls_n + c;
     s->cm_rowptr = a.get<int64_t>(c + 1);
     s->cm_list = a.get<int32_t>(M);
     s->method_local = a.get<int32_t>(M);
     s->ca_rowptr = a.get<int64_t>(c + 1);
     s->attr_local = a.get<int32_t>(A);
     s->fan_in = a.get<int32_t>(M);
-    s->d_err = a.get<uint32_t>(4);
     s->d_u64 = a.get<unsigned long long>(32);
+    s->d_err = reinterpret_cast<uint32_t *>(s->d_u64 + 6);  // cleared with the load summary
     cudaStream_t stv = s->stream;
-    upload(s->method_class, desc->method_class, M, desc->ptr_kind, stv);
-    upload(s->attr_class, desc->attr_class, A, desc->ptr_kind, stv);
-    if (M >= 0 && desc->acc_rowptr) upload(s->acc_rowptr, desc->acc_rowptr, M + 1, desc->ptr_kind, stv);
-    upload(s->acc_idx, desc->acc_idx, s->n_acc, desc->ptr_kind, stv);
-    if (desc->call_rowptr) upload(s->call_rowptr, desc->call_rowptr, M + 1, desc->ptr_kind, stv);
-    upload(s->call_idx, desc->call_idx, s->n_call, desc->ptr_kind, stv);
+    if (desc->ptr_kind == MM_PTR_DEVICE) {  // one copy kernel for the six device arrays
+      CopySegs cs{};
+      auto add = [&](void *dst, const void *src, int64_t bytes) {
+        if (bytes > 0 && src) cs.seg[cs.n++] = {dst, src, bytes};
+      };
+      add(s->method_class, desc->method_class, 4 * M);
+      add(s->attr_class, desc->attr_class, 4 * A);
+      add(s->acc_rowptr, desc->acc_rowptr, 8 * (M + 1));
+      add(s->acc_idx, desc->acc_idx, 4 * s->n_acc);
+      add(s->call_rowptr, desc->call_rowptr, 8 * (M + 1));
+      add(s->call_idx, desc->call_idx, 4 * s->n_call);
+      copy_segments(cs, stv);
+    } else {
+      upload(s->method_class, desc->method_class, M, desc->ptr_kind, stv);
+      upload(s->attr_class, desc->attr_class, A, desc->ptr_kind, stv);
+      if (M >= 0 && desc->acc_rowptr) upload(s->acc_rowptr, desc->acc_rowptr, M + 1, desc->ptr_kind, stv);
+      upload(s->acc_idx, desc->acc_idx, s->n_acc, desc->ptr_kind, stv);
+      if (desc->call_rowptr) upload(s->call_rowptr, desc->call_rowptr, M + 1, desc->ptr_kind, stv);
+      upload(s->call_idx, desc->call_idx, s->n_call, desc->ptr_kind, stv);
+    }
     if (M == 0) {
       MM_CUDA_TRY(cudaMemsetAsync(s->acc_rowptr, 0, sizeof(int64_t), stv));
       MM_CUDA_TRY(cudaMemsetAsync(s->call_rowptr, 0, sizeof(int64_t), stv));

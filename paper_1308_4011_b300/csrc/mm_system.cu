@@ -178,21 +178,19 @@ __global__ void fan_in_hist(const int32_t *call_idx, int64_t n_call, int32_t *fa
 // load_finish reads their results back.
 void load_validate_and_summarise(mm_system *s) {
   cudaStream_t st = s->stream;
-  MM_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(uint32_t), st));
+  LoadSummary *dsum = reinterpret_cast<LoadSummary *>(s->d_u64 + 4);
+  MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 4, 0, 4 * sizeof(unsigned long long), st));  // summary and error word
+  MM_CUDA_TRY(cudaMemsetAsync(s->cls_n, 0, sizeof(int32_t) * 2 * (size_t)s->c, st));  // cls_n, cls_a
   if (s->M > 0)
     validate_methods<<<grid_for(s->M), TPB, 0, st>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->call_rowptr,
                                                      s->call_idx, s->c, s->M, s->A, s->n_acc, s->n_call, s->d_err);
   MM_LAUNCH_CHECK();
   if (s->A > 0) validate_attrs<<<grid_for(s->A), TPB, 0, st>>>(s->attr_class, s->c, s->A, s->d_err);
   MM_LAUNCH_CHECK();
-  MM_CUDA_TRY(cudaMemsetAsync(s->cls_n, 0, sizeof(int32_t) * (size_t)s->c, st));
-  MM_CUDA_TRY(cudaMemsetAsync(s->cls_a, 0, sizeof(int32_t) * (size_t)s->c, st));
   int64_t nmax = std::max<int64_t>(s->M, s->A);
   class_histograms<<<grid_for(nmax), TPB, 0, st>>>(s->method_class, s->attr_class, s->c, s->M, s->A, s->cls_n,
                                                    s->cls_a);
   MM_LAUNCH_CHECK();
-  LoadSummary *dsum = reinterpret_cast<LoadSummary *>(s->d_u64 + 4);
-  MM_CUDA_TRY(cudaMemsetAsync(dsum, 0, sizeof(LoadSummary), st));
   summarise_classes<<<grid_for(s->c), TPB, 0, st>>>(s->cls_n, s->c, dsum);
   MM_LAUNCH_CHECK();
 }
@@ -218,10 +216,6 @@ void load_finish(mm_system *s) {
   s->attrs_by_class = !(err & VI_ATTRS_UNSORTED);
 }
 
-namespace {
-__global__ void set_i64(int64_t *p, int64_t v) { *p = v; }
-}  // namespace
-
 void build_structures(mm_system *s) {
   cudaStream_t st = s->stream;
   const int64_t c = s->c, M = s->M, A = s->A, E = s->n_call;
@@ -232,9 +226,7 @@ void build_structures(mm_system *s) {
   const int cbits = bits_for((uint64_t)(c > 0 ? c - 1 : 0));
 
   // class -> methods: stable sort of method ids by owner class
-  scan_exclusive_i32to64(s->cls_n, s->cm_rowptr, c, s->sort_ws, st);
-  set_i64<<<1, 1, 0, st>>>(s->cm_rowptr + c, M);
-  MM_LAUNCH_CHECK();
+  scan_exclusive_i32to64(s->cls_n, s->cm_rowptr, c, s->sort_ws, st, s->cm_rowptr + c);  // total = M
   if (M > 0 && s->methods_by_class) {
     local_ranks_sorted<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->cm_rowptr, M, s->method_local, s->cm_list);
     MM_LAUNCH_CHECK();
@@ -247,9 +239,7 @@ void build_structures(mm_system *s) {
     MM_LAUNCH_CHECK();
   }
   // class -> attributes
-  scan_exclusive_i32to64(s->cls_a, s->ca_rowptr, c, s->sort_ws, st);
-  set_i64<<<1, 1, 0, st>>>(s->ca_rowptr + c, A);
-  MM_LAUNCH_CHECK();
+  scan_exclusive_i32to64(s->cls_a, s->ca_rowptr, c, s->sort_ws, st, s->ca_rowptr + c);  // total = A
   if (A > 0 && s->attrs_by_class) {
     local_ranks_sorted<<<grid_for(A), TPB, 0, st>>>(s->attr_class, s->ca_rowptr, A, s->attr_local, nullptr);
     MM_LAUNCH_CHECK();
