@@ -69,17 +69,21 @@ __global__ void own_access_fill(const int32_t *method_class, const int32_t *meth
 // is its accessor list; methods with two or more are taken by the whole warp
 // in turn, with bitmap words per warp in shared memory, or in a zeroed global
 // slice when the largest class is too big.
-// A warp owns LU_G consecutive methods (one per lane); each method with two or
-// more own attributes takes the whole warp for its accessor union, one after
-// the other, so the methods per warp set the length of its chain of dependent
-// loads: a small group keeps that chain short.
-constexpr int LU_G = 8;
+// A warp owns g consecutive methods (one per lane, g = 8, 16 or 32); each
+// method with two or more own attributes takes the whole warp for its accessor
+// union, one after the other, so g sets the length of a warp's chain of
+// dependent loads: small groups when the methods do not fill the GPU's warps,
+// 32 when they do.
+inline int lcom_group(int64_t M) {
+  const int64_t per_warp = M / (148 * 64);
+  return per_warp >= 32 ? 32 : (per_warp >= 16 ? 16 : 8);
+}
 
 __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, const int64_t *acc_rowptr,
                                                   const int32_t *acc_idx, const int32_t *attr_class,
                                                   const int64_t *own_ptr, const int32_t *own_list,
                                                   const int32_t *own, int32_t M, int32_t words,
-                                                  uint32_t *gbm, int32_t *q, int64_t *cls_Q) {
+                                                  uint32_t *gbm, int32_t *q, int64_t *cls_Q, int32_t g) {
   extern __shared__ uint32_t lu_smem[];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   uint32_t *bm = gbm ? gbm + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wid) * words : lu_smem + wid * words;
@@ -87,9 +91,9 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
     for (int32_t i = (int32_t)lane; i < words; i += 32) bm[i] = 0u;
   __syncwarp();
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t wg = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; wg * LU_G < M; wg += nwarps) {
-    const int64_t base = wg * LU_G, x = base + lane;
-    const bool mine = lane < (uint32_t)LU_G && x < M;
+  for (int64_t wg = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; wg * g < M; wg += nwarps) {
+    const int64_t base = wg * g, x = base + lane;
+    const bool mine = lane < (uint32_t)g && x < M;
     const int32_t ox = mine ? own[x] : 0;
     const int32_t C = mine ? method_class[x] : 0;
     int32_t u = 0;
@@ -393,10 +397,11 @@ void build_metrics(mm_system *s) {
     mark_point(s, 1, sa);  // own-access lists built (the s of list L entries needs them)
     if (M > 0 && A > 0) {
       // LCOM pair counts from accessor unions
-      const UnionBitmap ub = union_bitmap(s, ceil_div(M, LU_G), uw, sa);
+      const int g = lcom_group(M);
+      const UnionBitmap ub = union_bitmap(s, ceil_div(M, g), uw, sa);
       lcom_union<<<ub.grid, 256, ub.smem, sa>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class,
                                                  s->own_ptr, s->own_list, s->own, M, ub.words, ub.gbm, s->q,
-                                                 s->cls_Q);
+                                                 s->cls_Q, g);
       MM_LAUNCH_CHECK();
     }
     finalize_classes<<<grid_for(c), TPB, 0, sa>>>(s->cls_n, s->cls_Q, c, s->cls_P);

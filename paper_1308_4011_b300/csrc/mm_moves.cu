@@ -1616,32 +1616,85 @@ __device__ __forceinline__ int32_t owner_of(const int64_t *rowptr, int32_t M, in
   return lo;
 }
 
-__global__ void validate_cand_dst(const int64_t *rowptr, const int32_t *dst, const int32_t *method_class,
-                                  int32_t M, int32_t c, int64_t n_cand, int64_t per_warp, uint32_t *err,
-                                  unsigned long long *hash) {
-  const uint32_t lane = threadIdx.x & 31u;
+// One warp per range of per_warp candidates (a multiple of 128).  For each
+// chunk of 128 the warp loads the row ends of the next 32 methods; when they
+// cover the chunk, the owner of every candidate comes from a count of the row
+// ends at each chunk position and its prefix sum (shared memory, no search),
+// else (more than 32 rows end inside the chunk) each lane walks the row
+// pointers forward.  The hash is a sum over candidates, so the order of the
+// walk does not change it.
+__global__ void __launch_bounds__(256) validate_cand_dst(const int64_t *rowptr, const int32_t *dst,
+                                                         const int32_t *method_class, int32_t M, int32_t c,
+                                                         int64_t n_cand, int64_t per_warp, uint32_t *err,
+                                                         unsigned long long *hash) {
+  __shared__ int32_t s_cnt[8][128];
+  __shared__ int32_t s_cls[8][32];
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t i_begin = w * per_warp, i_end = min(n_cand, i_begin + per_warp);
   uint32_t e = 0;
   uint64_t h = 0;
   if (i_begin < i_end) {
-    int32_t m = owner_of(rowptr, M, i_begin);  // one search per warp, then forward scans
+    int32_t m = owner_of(rowptr, M, i_begin);  // one search per warp
     for (int64_t i0 = i_begin; i0 < i_end; i0 += 128) {
-      // four independent entries per lane: their scans and loads overlap
-      int32_t mi[4];
+      const int64_t cend = min(i0 + 128, i_end);
+      const int32_t mk = m + (int32_t)lane;
+      const int64_t ek = mk < M ? rowptr[mk + 1] : INT64_MAX;
+      s_cls[wid][lane] = mk < M ? method_class[mk] : -1;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t i = i0 + 32 * u + lane;
-        mi[u] = m;
-        if (i < i_end) {
-          while (mi[u] < M && rowptr[mi[u] + 1] <= i) ++mi[u];
-          const int32_t D = dst[i];
-          if (D < 0 || D >= c) e |= VE_CAND_RANGE;
-          else if (mi[u] < M && D == method_class[mi[u]]) e |= VE_CAND_SELF;
-          h += cand_mix(((uint64_t)i << 32) | (uint32_t)D);
+      for (int j = 0; j < 4; ++j) s_cnt[wid][4 * lane + j] = 0;
+      __syncwarp();
+      if (__shfl_sync(0xffffffffu, ek, 31) >= cend) {
+        // rows ending at each position of the chunk (ek > i0: method m owns i0)
+        if (ek < cend) atomicAdd(&s_cnt[wid][ek - i0], 1);
+        __syncwarp();
+        int32_t v[4], run = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          run += s_cnt[wid][4 * lane + j];
+          v[j] = run;  // rows ended at or before this position
         }
+        int32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+          if ((int)lane >= o) incl += t;
+        }
+        const int32_t before = incl - run;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int64_t i = i0 + 4 * lane + j;
+          if (i < cend) {
+            const int32_t D = dst[i];
+            const int32_t own = before + v[j];  // rows of m, m+1, ... that ended at or before i
+            if (D < 0 || D >= c) e |= VE_CAND_RANGE;
+            else if (D == s_cls[wid][own]) e |= VE_CAND_SELF;
+            h += cand_mix(((uint64_t)i << 32) | (uint32_t)D);
+          }
+        }
+        m += __shfl_sync(0xffffffffu, incl, 31);
+      } else {
+        int32_t mi[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + 32 * u + lane;
+          mi[u] = m;
+          if (i < cend) {
+            while (mi[u] < M && rowptr[mi[u] + 1] <= i) ++mi[u];
+            const int32_t D = dst[i];
+            if (D < 0 || D >= c) e |= VE_CAND_RANGE;
+            else if (mi[u] < M && D == method_class[mi[u]]) e |= VE_CAND_SELF;
+            h += cand_mix(((uint64_t)i << 32) | (uint32_t)D);
+          }
+        }
+        // owner of the chunk's last candidate (or later: rows ending there are empty)
+        const int64_t last = cend - 1;
+        int32_t ml = m;
+        if (lane == 0)
+          while (ml < M && rowptr[ml + 1] <= last) ++ml;
+        m = __shfl_sync(0xffffffffu, ml, 0);
       }
-      m = __shfl_sync(0xffffffffu, max(max(mi[0], mi[1]), max(mi[2], mi[3])), 31);
+      __syncwarp();  // s_cnt and s_cls are rewritten by the next chunk
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
