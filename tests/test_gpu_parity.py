@@ -391,6 +391,47 @@ def test_unsorted_and_self_calls_rejected():
         mmref.load_system(10, s.method_class, s.attr_class, s.acc_rowptr, s.acc_idx, s.call_rowptr, ci)
 
 
+def _short_row_candidates(s, seed):
+    """Candidate lists where most rows hold 0-3 destinations (so a chunk of 128
+    candidates spans more than 32 rows) and a few hold 40."""
+    rng = np.random.default_rng(seed)
+    lens = rng.choice([0, 0, 1, 2, 3, 40], size=s.n_methods)
+    rows = []
+    for m in range(s.n_methods):
+        others = np.array([d for d in range(s.n_classes) if d != s.method_class[m]], dtype=np.int32)
+        rows.append(np.sort(rng.choice(others, size=min(int(lens[m]), len(others)), replace=False)))
+    rowptr = np.zeros(s.n_methods + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    return rowptr, np.concatenate(rows).astype(np.int32)
+
+
+def test_candidate_validation_with_short_rows():
+    """Validation and hashing of lists whose chunks span many rows (the
+    per-lane walk) and few rows (the per-position count): results equal the
+    oracle, the kept cache is reused, and a self move or an out-of-range class
+    deep inside the short rows is rejected."""
+    s = synth.generate(n_classes=50, n_methods=3000, n_attrs=1500, max_class=120, seed=5)
+    rowptr, dst = _short_row_candidates(s, 5)
+    ref = oracle.Oracle(s, threads=4).evaluate(mask=4, min_improved=1, cand_rowptr=rowptr, cand_dst=dst)
+    g, _, _ = gpu_load(s)
+    assert gpu_digest(g, 4, 1, rowptr, dst) == ref.digest
+    top, nk, nm = mmref.suggest_moves(g, k=ref.n_kept, mask=4, min_improved=1, cand_rowptr=rowptr, cand_dst=dst)
+    assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+    assert kept_tuples(top) == oracle_kept(ref)
+    lens = np.diff(rowptr)
+    m = int(np.nonzero(lens[2000:] >= 1)[0][0]) + 2000
+    bad = dst.copy()
+    bad[rowptr[m]] = s.method_class[m]
+    with pytest.raises(mmref.MMError, match="own class"):
+        mmref.evaluate_moves(g, 4, 1, rowptr, bad, digest=np.zeros(1, np.uint64))
+    bad = dst.copy()
+    bad[rowptr[m]] = s.n_classes
+    with pytest.raises(mmref.MMError):
+        mmref.evaluate_moves(g, 4, 1, rowptr, bad, digest=np.zeros(1, np.uint64))
+    assert gpu_digest(g, 4, 1, rowptr, dst) == ref.digest  # the valid lists still evaluate
+    g.free()
+
+
 def test_invalid_candidates_and_criteria_rejected():
     s = synth.generate(10, 40, 20, max_class=10, seed=1)
     g, _, _ = gpu_load(s)
