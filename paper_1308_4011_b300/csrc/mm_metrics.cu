@@ -417,9 +417,8 @@ void build_metrics(mm_system *s) {
   // coupling: mark the use edges in the out-rows, count and enumerate the
   // marked classes row by row (ascending, so no sort), then count multiplicities
   const int64_t aw = s->adj_words, sw = s->sum_words;
-  MM_CUDA_TRY(cudaMemsetAsync(s->out_adj, 0, sizeof(uint32_t) * (size_t)(aw * c), st));
-  MM_CUDA_TRY(cudaMemsetAsync(s->in_adj, 0, sizeof(uint32_t) * (size_t)(aw * c), st));
-  MM_CUDA_TRY(cudaMemsetAsync(s->csum, 0, sizeof(uint2) * (size_t)(sw * (2 * c + 1)), st));
+  zero_buffers(s->out_adj, sizeof(uint32_t) * (size_t)(aw * c), s->in_adj, sizeof(uint32_t) * (size_t)(aw * c),
+               s->csum, sizeof(uint2) * (size_t)(sw * (2 * c + 1)), st);
   int32_t *row_count = s->cls_cbo;
   const int64_t nk = s->n_call + (s->cbo_attrs ? s->n_acc : 0);
   uint64_t *edges = static_cast<uint64_t *>(s->eval_ws.need(sizeof(uint64_t) * (size_t)std::max<int64_t>(nk, 1), st));

@@ -306,6 +306,36 @@ void radix_sort(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_
 
 }  // namespace
 
+namespace {
+// Zero up to three buffers (16-byte aligned) in one launch with 16-byte stores.
+struct ZeroSegs {
+  void *p[3];
+  size_t bytes[3];
+};
+
+__global__ void zero_segments_kernel(ZeroSegs z) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    uint4 *q = static_cast<uint4 *>(z.p[k]);
+    const int64_t n16 = (int64_t)(z.bytes[k] / 16);
+    for (int64_t i = t; i < n16; i += stride) q[i] = make_uint4(0u, 0u, 0u, 0u);
+    unsigned char *tail = static_cast<unsigned char *>(z.p[k]) + 16 * n16;
+    if (t < (int64_t)(z.bytes[k] % 16)) tail[t] = 0;
+  }
+}
+}  // namespace
+
+void zero_buffers(void *a, size_t na, void *b, size_t nb, void *c, size_t nc, cudaStream_t st) {
+  ZeroSegs z{{a, b, c}, {a ? na : 0, b ? nb : 0, c ? nc : 0}};
+  const size_t most = std::max(z.bytes[0], std::max(z.bytes[1], z.bytes[2]));
+  if (most == 0) return;
+  const int64_t blocks = std::min<int64_t>(ceil_div((int64_t)(most / 16) + 1, 256), 148 * 16);
+  zero_segments_kernel<<<(unsigned)blocks, 256, 0, st>>>(z);
+  MM_LAUNCH_CHECK();
+}
+
 void read_wait_fault(uint32_t *host, cudaStream_t st) {
   MM_CUDA_TRY(cudaMemcpyFromSymbolAsync(host, g_wait_fault, sizeof(uint32_t), 0, cudaMemcpyDeviceToHost, st));
 }
