@@ -195,7 +195,9 @@ typedef struct {
  * NULL = default stream) and validates them on the device.  The stream is
  * kept for every later call on the handle.  Errors: MM_EINVAL for any rule of
  * mm_system_desc broken (the message names the first rule found), MM_ENOMEM,
- * MM_ECUDA.  Synchronises the stream (validation result).
+ * MM_ECUDA, MM_ETIMEOUT if a bounded device-side wait of an earlier queued
+ * scan gave up (see mm_selftest_bounded_wait).  Synchronises the stream
+ * (validation result).
  */
 MMREF_API mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_system **out);
 
@@ -207,8 +209,10 @@ MMREF_API mm_status mm_set_stream(mm_system *sys, void *cuda_stream);
  * data that move evaluation needs.  Builds, on the device: the class->method
  * and class->attribute lists, an inverted index of own-attribute accesses,
  * the LCOM method-pair counts (unions of accessor lists), the class-use
- * multigraph (segmented sort + unique) with CBO, class adjacency bitsets and
- * their compressed two-level form, and fan-in/out.
+ * multigraph (marked adjacency rows, counted and enumerated per row) with
+ * CBO, class adjacency bitsets and their compressed two-level form, and
+ * fan-in/out.  Independent parts run on side streams of the calling thread
+ * and rejoin the system's stream before the call returns.
  * out_c[n_classes] and out_m[n_methods] are optional (NULL = keep on device);
  * out_kind says where they live.
  */
@@ -241,7 +245,10 @@ MMREF_API mm_status mm_evaluate_moves(mm_system *sys, const mm_criteria *crit, c
  * order given at mm_move and write the first min(k, n_kept) to out_topk
  * (out_kind memory; may be NULL when k == 0).  *n_kept and
  * *n_methods_with_kept (host, nullable) receive the number of kept moves and
- * of distinct methods among them.  Synchronises the stream.
+ * of distinct methods among them.  Up to 8,192 kept moves are sorted on the
+ * device before the one read-back of the counts.  Errors as mm_evaluate_moves,
+ * plus MM_ETIMEOUT if a bounded device-side wait (the look-back of a scan in
+ * this or an earlier queued call) gave up.  Synchronises the stream.
  */
 MMREF_API mm_status mm_suggest_moves(mm_system *sys, const mm_criteria *crit, const mm_candidates *cands,
                            int32_t k, mm_move *out_topk, int32_t out_kind, int64_t *n_kept,
