@@ -391,6 +391,20 @@ def test_unsorted_and_self_calls_rejected():
         mmref.load_system(10, s.method_class, s.attr_class, s.acc_rowptr, s.acc_idx, s.call_rowptr, ci)
 
 
+@pytest.mark.parametrize("M,A", [(4097, 4096), (16384, 16385), (16385, 16384)])
+def test_scan_size_boundaries(M, A):
+    """Method and attribute counts at the edges of the scans: one block up to
+    16,384 elements, one pass over tiles of 4,096 above (a last tile of one
+    element included).  Metrics and every record's digest equal the oracle."""
+    s = synth.generate(n_classes=40, n_methods=M, n_attrs=A, max_class=max(2 * M // 40, 40), seed=M + A)
+    o = oracle.Oracle(s, threads=4)
+    g, cm, mm_ = gpu_load(s)
+    check_metrics(s, o, cm, mm_)
+    ref = o.evaluate(mask=7, min_improved=1)
+    assert gpu_digest(g, 7, 1) == ref.digest
+    g.free()
+
+
 def _short_row_candidates(s, seed):
     """Candidate lists where most rows hold 0-3 destinations (so a chunk of 128
     candidates spans more than 32 rows) and a few hold 40."""
