@@ -2357,7 +2357,7 @@ struct BatchItem {
 // (system, destination block, method chunk) tiles from a global counter and run
 // the same dense_tile as the single-system kernel.
 template <bool DIG, bool KEEP>
-__global__ void __launch_bounds__(DB_THREADS, 3) eval_dense_batched(const BatchItem *items, int32_t n,
+__global__ void __launch_bounds__(DB_THREADS, 4) eval_dense_batched(const BatchItem *items, int32_t n,
                                                                     int64_t total_tiles, int32_t mchunk,
                                                                     unsigned long long *next_tile) {
   __shared__ __align__(16) DenseStage st;
