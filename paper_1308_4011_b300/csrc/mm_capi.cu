@@ -81,6 +81,7 @@ struct CopySegs {
 };
 
 __global__ void copy_segments_kernel(CopySegs cs) {
+  pdl_wait();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int k = 0; k < cs.n; ++k) {
     const uint32_t *src = static_cast<const uint32_t *>(cs.seg[k].src);
@@ -94,7 +95,7 @@ void copy_segments(const CopySegs &cs, cudaStream_t st) {
   int64_t words = 0;
   for (int k = 0; k < cs.n; ++k) words = std::max<int64_t>(words, cs.seg[k].bytes / 4);
   if (words == 0) return;
-  copy_segments_kernel<<<(unsigned)std::min<int64_t>(ceil_div(words, 256), 148 * 8), 256, 0, st>>>(cs);
+  pdl_launch(copy_segments_kernel, (unsigned)std::min<int64_t>(ceil_div(words, 256), 148 * 8), 256, 0, st, cs);
   MM_LAUNCH_CHECK();
 }
 
@@ -149,6 +150,7 @@ std::string describe(uint32_t err) {
 
 __global__ void export_class_kernel(const int32_t *cls_n, const int32_t *cls_a, const int64_t *P, const int64_t *Q,
                                     const int64_t *S, const int32_t *cbo, int32_t c, mm_class_metrics *out) {
+  pdl_wait();
   int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (C >= c) return;
   mm_class_metrics r;
@@ -168,6 +170,7 @@ __global__ void export_class_kernel(const int32_t *cls_n, const int32_t *cls_a, 
 
 __global__ void export_method_kernel(const int32_t *fan_in, const int64_t *call_rowptr, const int32_t *own,
                                      const int32_t *q, int32_t M, mm_method_metrics *out) {
+  pdl_wait();
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
   mm_method_metrics r;
@@ -186,7 +189,7 @@ void export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *ou
     mm_class_metrics *d = kind == MM_PTR_DEVICE
                               ? out_c
                               : static_cast<mm_class_metrics *>(s->stage_ws.need(sizeof(mm_class_metrics) * s->c, st));
-    export_class_kernel<<<(unsigned)ceil_div(s->c, 256), 256, 0, st>>>(s->cls_n, s->cls_a, s->cls_P, s->cls_Q,
+    pdl_launch(export_class_kernel, (unsigned)ceil_div(s->c, 256), 256, 0, st, s->cls_n, s->cls_a, s->cls_P, s->cls_Q,
                                                                       s->cls_S, s->cls_cbo, s->c, d);
     MM_LAUNCH_CHECK();
     if (kind == MM_PTR_HOST)
@@ -197,7 +200,7 @@ void export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *ou
     mm_method_metrics *d =
         kind == MM_PTR_DEVICE ? out_m
                               : static_cast<mm_method_metrics *>(s->stage_ws.need(sizeof(mm_method_metrics) * s->M, st));
-    export_method_kernel<<<(unsigned)ceil_div(s->M, 256), 256, 0, st>>>(s->fan_in, s->call_rowptr, s->own, s->q,
+    pdl_launch(export_method_kernel, (unsigned)ceil_div(s->M, 256), 256, 0, st, s->fan_in, s->call_rowptr, s->own, s->q,
                                                                        s->M, d);
     MM_LAUNCH_CHECK();
     if (kind == MM_PTR_HOST) {

@@ -35,6 +35,7 @@ inline unsigned grid_for(int64_t n, int tpb = TPB) {
 __global__ void own_access_count(const int32_t *method_class, const int64_t *acc_rowptr, const int32_t *acc_idx,
                                  const int32_t *attr_class, int32_t M, int64_t *acnt, int32_t *own,
                                  int64_t *cls_S) {
+  pdl_wait();
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
   const int32_t C = method_class[x];
@@ -54,6 +55,7 @@ __global__ void own_access_count(const int32_t *method_class, const int64_t *acc
 __global__ void own_access_fill(const int32_t *method_class, const int32_t *method_local, const int64_t *acc_rowptr,
                                 const int32_t *acc_idx, const int32_t *attr_class, int32_t M,
                                 const int64_t *own_ptr, int32_t *cursor, int32_t *own_list) {
+  pdl_wait();
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
   const int32_t C = method_class[x], r = method_local[x];
@@ -84,6 +86,7 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
                                                   const int64_t *own_ptr, const int32_t *own_list,
                                                   const int32_t *own, int32_t M, int32_t words,
                                                   uint32_t *gbm, int32_t *q, int64_t *cls_Q, int32_t g) {
+  pdl_wait();
   extern __shared__ uint32_t lu_smem[];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   uint32_t *bm = gbm ? gbm + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wid) * words : lu_smem + wid * words;
@@ -126,6 +129,7 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
 }
 
 __global__ void finalize_classes(const int32_t *cls_n, int64_t *cls_Q, int32_t c, int64_t *cls_P) {
+  pdl_wait();
   int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (C >= c) return;
   const int64_t n = cls_n[C];
@@ -153,6 +157,7 @@ __global__ void coupling_mark(const int32_t *method_class, const int64_t *call_r
                               const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
                               int32_t M, int32_t cbo_attrs, uint32_t *out_adj, int64_t aw, uint2 *csum,
                               int64_t sw, uint64_t *edges) {
+  pdl_wait();
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
   const int32_t Y = method_class[x];
@@ -188,6 +193,7 @@ __device__ __forceinline__ int32_t record_classes(const uint2 *csum, const uint3
 // lanes over its summary records).
 __global__ void row_distinct(const uint2 *csum, const uint32_t *out_adj, int32_t c, int64_t aw, int64_t sw,
                              int32_t *row_count) {
+  pdl_wait();
   const uint32_t lane = threadIdx.x & 31u;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t Y = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; Y < c; Y += nwarps) {
@@ -203,6 +209,7 @@ __global__ void row_distinct(const uint2 *csum, const uint32_t *out_adj, int32_t
 // set the transposed in-row bits and their summary bits.
 __global__ void row_enumerate(uint2 *csum, const uint32_t *out_adj, uint32_t *in_adj, int32_t c, int64_t aw,
                               int64_t sw, const int64_t *mg_rowptr, int32_t *mg_dst, int32_t *mg_cnt) {
+  pdl_wait();
   const uint32_t lane = threadIdx.x & 31u;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t Y = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; Y < c; Y += nwarps) {
@@ -245,6 +252,7 @@ __global__ void row_enumerate(uint2 *csum, const uint32_t *out_adj, uint32_t *in
 // (binary search of E in row Y).
 __global__ void coupling_count(const uint64_t *edges, int64_t n, const int64_t *mg_rowptr, const int32_t *mg_dst,
                                int32_t *mg_cnt) {
+  pdl_wait();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = edges[i];
     if (k == ~0ull) continue;
@@ -259,6 +267,7 @@ __global__ void coupling_count(const uint64_t *edges, int64_t n, const int64_t *
 }
 
 __global__ void summary_popc(const uint2 *sum, int64_t n, int32_t *cnt) {
+  pdl_wait();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     cnt[i] = __popc(sum[i].x);
 }
@@ -267,6 +276,7 @@ __global__ void summary_popc(const uint2 *sum, int64_t n, int32_t *cnt) {
 // copied there (rows below c from the out-bitsets, the next c from the in-bitsets)
 __global__ void summary_pack(uint2 *sum, const int64_t *first, const uint32_t *out_adj, const uint32_t *in_adj,
                              int64_t c, int64_t aw, int64_t sw, int64_t n, uint32_t *packed) {
+  pdl_wait();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / sw, k = i % sw;
     uint32_t bits = sum[i].x;
@@ -286,6 +296,7 @@ __global__ void summary_pack(uint2 *sum, const int64_t *first, const uint32_t *o
 // in the second, where the last three are D's LCOM outcome when m shares nothing with D
 __global__ void destination_records(const int32_t *cls_n, const int32_t *cls_a, const int64_t *P, const int64_t *Q,
                                     const int64_t *S, int32_t c, int4 *rec) {
+  pdl_wait();
   int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (C >= c) return;
   const int64_t d = P[C] - Q[C], sv = S[C];
@@ -382,7 +393,7 @@ void build_metrics(mm_system *s) {
     MM_CUDA_TRY(cudaMemsetAsync(s->cls_Q, 0, sizeof(int64_t) * (size_t)c, sa));
     MM_CUDA_TRY(cudaMemsetAsync(s->q, 0, sizeof(int32_t) * (size_t)std::max(M, 1), sa));
     if (M > 0) {
-      own_access_count<<<grid_for(M), TPB, 0, sa>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class, M,
+      pdl_launch(own_access_count, grid_for(M), TPB, 0, sa, s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class, M,
                                                      acnt, s->own, s->cls_S);
       MM_LAUNCH_CHECK();
     }
@@ -390,7 +401,7 @@ void build_metrics(mm_system *s) {
     if (M > 0 && A > 0) {
       int32_t *cursor = reinterpret_cast<int32_t *>(acnt);  // counts are consumed: reuse as cursors
       MM_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)A, sa));
-      own_access_fill<<<grid_for(M), TPB, 0, sa>>>(s->method_class, s->method_local, s->acc_rowptr, s->acc_idx,
+      pdl_launch(own_access_fill, grid_for(M), TPB, 0, sa, s->method_class, s->method_local, s->acc_rowptr, s->acc_idx,
                                                     s->attr_class, M, s->own_ptr, cursor, s->own_list);
       MM_LAUNCH_CHECK();
     }
@@ -399,14 +410,14 @@ void build_metrics(mm_system *s) {
       // LCOM pair counts from accessor unions
       const int g = lcom_group(M);
       const UnionBitmap ub = union_bitmap(s, ceil_div(M, g), uw, sa);
-      lcom_union<<<ub.grid, 256, ub.smem, sa>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class,
+      pdl_launch(lcom_union, ub.grid, 256, ub.smem, sa, s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class,
                                                  s->own_ptr, s->own_list, s->own, M, ub.words, ub.gbm, s->q,
                                                  s->cls_Q, g);
       MM_LAUNCH_CHECK();
     }
-    finalize_classes<<<grid_for(c), TPB, 0, sa>>>(s->cls_n, s->cls_Q, c, s->cls_P);
+    pdl_launch(finalize_classes, grid_for(c), TPB, 0, sa, s->cls_n, s->cls_Q, c, s->cls_P);
     MM_LAUNCH_CHECK();
-    destination_records<<<grid_for(c), TPB, 0, sa>>>(s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, c,
+    pdl_launch(destination_records, grid_for(c), TPB, 0, sa, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, c,
                                                      s->dest_rec);
     MM_LAUNCH_CHECK();
     s->side_pending[0] = sa;
@@ -423,21 +434,21 @@ void build_metrics(mm_system *s) {
   const int64_t nk = s->n_call + (s->cbo_attrs ? s->n_acc : 0);
   uint64_t *edges = static_cast<uint64_t *>(s->eval_ws.need(sizeof(uint64_t) * (size_t)std::max<int64_t>(nk, 1), st));
   if (M > 0) {
-    coupling_mark<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
+    pdl_launch(coupling_mark, grid_for(M), TPB, 0, st, s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
                                                s->acc_idx, s->attr_class, M, s->cbo_attrs, s->out_adj, aw,
                                                s->csum, sw, edges);
     MM_LAUNCH_CHECK();
   }
   const unsigned grow = (unsigned)std::min<int64_t>(ceil_div((int64_t)c * 32, TPB), 148 * 16);
-  row_distinct<<<grow, TPB, 0, st>>>(s->csum, s->out_adj, c, aw, sw, row_count);
+  pdl_launch(row_distinct, grow, TPB, 0, st, s->csum, s->out_adj, c, aw, sw, row_count);
   MM_LAUNCH_CHECK();
   // mg_rowptr = exclusive scan of the row counts (CBO); last entry = distinct pairs
   scan_exclusive_i32to64(row_count, s->mg_rowptr, c, s->sort_ws, st, s->mg_rowptr + c);
-  row_enumerate<<<grow, TPB, 0, st>>>(s->csum, s->out_adj, s->in_adj, c, aw, sw, s->mg_rowptr, s->mg_dst,
+  pdl_launch(row_enumerate, grow, TPB, 0, st, s->csum, s->out_adj, s->in_adj, c, aw, sw, s->mg_rowptr, s->mg_dst,
                                       s->mg_cnt);
   MM_LAUNCH_CHECK();
   if (M > 0) {
-    coupling_count<<<(unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(nk, 1), TPB), 148 * 16), TPB, 0, st>>>(
+    pdl_launch(coupling_count, (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(nk, 1), TPB), 148 * 16), TPB, 0, st, 
         edges, nk, s->mg_rowptr, s->mg_dst, s->mg_cnt);
     MM_LAUNCH_CHECK();
   }
@@ -450,10 +461,10 @@ void build_metrics(mm_system *s) {
     int64_t *first = reinterpret_cast<int64_t *>(b);
     int32_t *cnt = reinterpret_cast<int32_t *>(first + ns);
     const unsigned g = (unsigned)std::min<int64_t>(ceil_div(ns, TPB), 148 * 16);
-    summary_popc<<<g, TPB, 0, st>>>(s->csum, ns, cnt);
+    pdl_launch(summary_popc, g, TPB, 0, st, s->csum, ns, cnt);
     MM_LAUNCH_CHECK();
     scan_exclusive_i32to64(cnt, first, ns, s->sort_ws, st);
-    summary_pack<<<g, TPB, 0, st>>>(s->csum, first, s->out_adj, s->in_adj, c, s->adj_words, s->sum_words, ns,
+    pdl_launch(summary_pack, g, TPB, 0, st, s->csum, first, s->out_adj, s->in_adj, c, s->adj_words, s->sum_words, ns,
                                     s->cpk);
     MM_LAUNCH_CHECK();
   }

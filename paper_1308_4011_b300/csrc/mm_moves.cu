@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(256) l_entries_s(const int4 *l_list, const int
                                                    const int32_t *attr_class, const int64_t *own_ptr,
                                                    const int32_t *own_list, int32_t words, uint32_t *gbm,
                                                    int32_t *l_s) {
+  pdl_wait();
   extern __shared__ uint32_t ls_smem[];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   uint32_t *bm = gbm ? gbm + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wid) * words : ls_smem + wid * words;
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(256) l_entries_s(const int4 *l_list, const int
 __global__ void method_use_keys32(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
                                   const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
                                   int32_t M, uint32_t *keys) {
+  pdl_wait();
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
   int64_t pos = call_rowptr[x] + acc_rowptr[x];
@@ -126,6 +128,7 @@ __global__ void method_use_keys32(const int32_t *method_class, const int64_t *ca
 __global__ void caller_classes_scatter(const int32_t *method_class, const int64_t *call_rowptr,
                                        const int32_t *call_idx, int32_t M, const int64_t *rin_off,
                                        int32_t *cursor, uint32_t *keys) {
+  pdl_wait();
   int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (y >= M) return;
   const uint32_t cy = (uint32_t)method_class[y];
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(256) segment_sort_count_block(const int64_t *a
                                                                 const int32_t *method_class, int32_t cbo_attrs,
                                                                 int32_t *len_out, int32_t *self_out,
                                                                 uint8_t *long_seg) {
+  pdl_wait();
   __shared__ uint32_t sk[SB_KEYS];
   const int64_t x0 = (int64_t)blockIdx.x * blockDim.x;
   const int64_t xl = (x0 + (int64_t)blockDim.x < (int64_t)M ? x0 + (int64_t)blockDim.x : (int64_t)M) - 1;
@@ -254,6 +258,7 @@ __global__ void __launch_bounds__(256) segment_sort_count(const int64_t *a, cons
                                                           const int32_t *method_class, int32_t cbo_attrs,
                                                           int32_t *len_out, int32_t *self_out,
                                                           const uint8_t *only) {
+  pdl_wait();
   __shared__ uint32_t sk[8][32];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -314,6 +319,7 @@ __global__ void __launch_bounds__(256) lists_fill_l(const int64_t *call_rowptr, 
                                                     const uint32_t *sorted, const int32_t *method_class,
                                                     int32_t cbo_attrs, const int64_t *l_off, int4 *l_list,
                                                     int32_t *l_x) {
+  pdl_wait();
   __shared__ uint32_t sk[SB_KEYS];
   const int64_t x0 = (int64_t)blockIdx.x * blockDim.x;
   const int64_t xl = (x0 + (int64_t)blockDim.x < (int64_t)M ? x0 + (int64_t)blockDim.x : (int64_t)M) - 1;
@@ -347,6 +353,7 @@ __global__ void __launch_bounds__(256) lists_fill_l(const int64_t *call_rowptr, 
 __global__ void lists_lookup_l(const int64_t *n_l, const int32_t *l_x, const int32_t *method_class,
                                const int64_t *mg_rowptr, const int32_t *mg_dst, const int32_t *mg_cnt,
                                int4 *l_list) {
+  pdl_wait();
   const int64_t nl = *n_l;
   for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += (int64_t)gridDim.x * blockDim.x) {
     const int4 v = l_list[l];
@@ -359,6 +366,7 @@ __global__ void lists_lookup_l(const int64_t *n_l, const int32_t *l_x, const int
 __global__ void __launch_bounds__(256) lists_fill_r(const int64_t *rin_off, int32_t M, const uint32_t *sorted,
                                                     const int32_t *method_class, const int64_t *r_off,
                                                     int4 *r_list) {
+  pdl_wait();
   __shared__ uint32_t sk[SB_KEYS];
   const int64_t x0 = (int64_t)blockIdx.x * blockDim.x;
   const int64_t xl = (x0 + (int64_t)blockDim.x < (int64_t)M ? x0 + (int64_t)blockDim.x : (int64_t)M) - 1;
@@ -385,6 +393,7 @@ __global__ void __launch_bounds__(256) lists_fill_r(const int64_t *rin_off, int3
 // cnt(X, C) of every R entry: {X, in, cnt(X, C), 0}
 __global__ void lists_lookup_r(const int64_t *n_r, const int64_t *mg_rowptr, const int32_t *mg_dst,
                                const int32_t *mg_cnt, int4 *r_list) {
+  pdl_wait();
   const int64_t nr = *n_r;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
     const int4 v = r_list[r];
@@ -400,6 +409,7 @@ __global__ void build_headers(const int32_t *method_class, const int32_t *cls_n,
                               const int32_t *q, const int64_t *l_off, const int32_t *l_len, const int64_t *r_off,
                               const int32_t *r_len, const int32_t *out_self, const int32_t *in_self,
                               const int4 *l_list, int32_t M, MoveHdr *hdr) {
+  pdl_wait();
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
   int32_t C = method_class[x];
@@ -486,37 +496,37 @@ void begin_move_lists(mm_system *s) {
   const ListBufs b = list_bufs(s, sl, sr);
   // list L: per-method sort of the use keys, runs counted, scanned, written
   if (nu > 0) {
-    method_use_keys32<<<grid_for(M), TPB, 0, sl>>>(s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
+    pdl_launch(method_use_keys32, grid_for(M), TPB, 0, sl, s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
                                                    s->acc_idx, s->attr_class, M, b.lkeys);
     MM_LAUNCH_CHECK();
   }
-  segment_sort_count_block<<<grid_for(M), 256, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, b.lkeys, b.lsorted, 1,
+  pdl_launch(segment_sort_count_block, grid_for(M), 256, 0, sl, s->call_rowptr, s->acc_rowptr, M, b.lkeys, b.lsorted, 1,
                                                         s->method_class, s->cbo_attrs, b.l_len, b.out_self, b.llong);
   MM_LAUNCH_CHECK();
-  segment_sort_count<<<gw, TPB, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, b.lkeys, b.lsorted, 1, s->method_class,
+  pdl_launch(segment_sort_count, gw, TPB, 0, sl, s->call_rowptr, s->acc_rowptr, M, b.lkeys, b.lsorted, 1, s->method_class,
                                          s->cbo_attrs, b.l_len, b.out_self, b.llong);
   MM_LAUNCH_CHECK();
   scan_exclusive_i32to64(b.l_len, b.l_off, M, s->side_sort[1], sl, b.l_off + M);
-  lists_fill_l<<<grid_for(M), 256, 0, sl>>>(s->call_rowptr, s->acc_rowptr, M, b.lsorted, s->method_class,
+  pdl_launch(lists_fill_l, grid_for(M), 256, 0, sl, s->call_rowptr, s->acc_rowptr, M, b.lsorted, s->method_class,
                                              s->cbo_attrs, b.l_off, s->l_list, s->l_x);
   MM_LAUNCH_CHECK();
   // list R: callers bucketed by callee (counting sort on fan-in), per-callee sort, runs
   scan_exclusive_i32to64(s->fan_in, b.rin_off, M, s->side_sort[2], sr, b.rin_off + M);
   if (nc > 0) {
     MM_CUDA_TRY(cudaMemsetAsync(b.cursor, 0, sizeof(int32_t) * (size_t)M, sr));
-    caller_classes_scatter<<<grid_for(M), TPB, 0, sr>>>(s->method_class, s->call_rowptr, s->call_idx, M, b.rin_off,
+    pdl_launch(caller_classes_scatter, grid_for(M), TPB, 0, sr, s->method_class, s->call_rowptr, s->call_idx, M, b.rin_off,
                                                         b.cursor, b.rkeys);
     MM_LAUNCH_CHECK();
   }
-  segment_sort_count_block<<<grid_for(M), 256, 0, sr>>>(b.rin_off, nullptr, M, b.rkeys, b.rsorted, 0,
+  pdl_launch(segment_sort_count_block, grid_for(M), 256, 0, sr, b.rin_off, nullptr, M, b.rkeys, b.rsorted, 0,
                                                         s->method_class, s->cbo_attrs, b.r_len, b.in_self, b.rlong);
   MM_LAUNCH_CHECK();
-  segment_sort_count<<<gw, TPB, 0, sr>>>(b.rin_off, nullptr, M, b.rkeys, b.rsorted, 0, s->method_class,
+  pdl_launch(segment_sort_count, gw, TPB, 0, sr, b.rin_off, nullptr, M, b.rkeys, b.rsorted, 0, s->method_class,
                                          s->cbo_attrs, b.r_len, b.in_self, b.rlong);
   MM_LAUNCH_CHECK();
   scan_exclusive_i32to64(b.r_len, b.r_off, M, s->side_sort[2], sr, b.r_off + M);
   if (nc > 0) {
-    lists_fill_r<<<grid_for(M), 256, 0, sr>>>(b.rin_off, M, b.rsorted, s->method_class, b.r_off, s->r_list);
+    pdl_launch(lists_fill_r, grid_for(M), 256, 0, sr, b.rin_off, M, b.rsorted, s->method_class, b.r_off, s->r_list);
     MM_LAUNCH_CHECK();
   }
 }
@@ -532,24 +542,24 @@ void build_move_precompute(mm_system *s) {
   const ListBufs b = list_bufs(s, sl, sr);
   wait_point(s, 0, st, sl);
   if (nu > 0) {
-    lists_lookup_l<<<(unsigned)std::min<int64_t>(ceil_div(nu, TPB), 148 * 16), TPB, 0, sl>>>(
+    pdl_launch(lists_lookup_l, (unsigned)std::min<int64_t>(ceil_div(nu, TPB), 148 * 16), TPB, 0, sl, 
         b.l_off + M, s->l_x, s->method_class, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list);
     MM_LAUNCH_CHECK();
     wait_point(s, 1, s->side_pending[0], sl);
     const UnionBitmap ub = union_bitmap(s, ceil_div(nu, 32), s->side_union[1], sl);
-    l_entries_s<<<ub.grid, 256, ub.smem, sl>>>(s->l_list, s->l_x, b.l_off + M, s->acc_rowptr, s->acc_idx,
+    pdl_launch(l_entries_s, ub.grid, 256, ub.smem, sl, s->l_list, s->l_x, b.l_off + M, s->acc_rowptr, s->acc_idx,
                                                 s->attr_class, s->own_ptr, s->own_list, ub.words, ub.gbm, s->l_s);
     MM_LAUNCH_CHECK();
   }
   wait_point(s, 0, st, sr);
   if (nc > 0) {
-    lists_lookup_r<<<(unsigned)std::min<int64_t>(ceil_div(nc, TPB), 148 * 16), TPB, 0, sr>>>(
+    pdl_launch(lists_lookup_r, (unsigned)std::min<int64_t>(ceil_div(nc, TPB), 148 * 16), TPB, 0, sr, 
         b.r_off + M, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->r_list);
     MM_LAUNCH_CHECK();
   }
   join_side(s, 1, sl);
   join_side(s, 2, sr);
-  build_headers<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S,
+  pdl_launch(build_headers, grid_for(M), TPB, 0, st, s->method_class, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S,
                                              s->own, s->q, b.l_off, b.l_len, b.r_off, b.r_len, b.out_self, b.in_self,
                                              s->l_list, M, s->hdr);
   MM_LAUNCH_CHECK();
@@ -1228,6 +1238,7 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
 
 template <bool REC, bool DIG, bool KEEP>
 __global__ void __launch_bounds__(DB_THREADS, 4) eval_dense(DenseSys sy, OutCtx oc, int32_t mchunk) {
+  pdl_wait();
   __shared__ __align__(16) DenseStage st;
   const int32_t m0 = blockIdx.y * mchunk;
   const int32_t m1 = min(sy.M, m0 + mchunk);
@@ -1420,6 +1431,7 @@ template <bool REC, bool DIG, bool KEEP>
 __global__ void __launch_bounds__(CG_WARPS * 32, 3) eval_csr_grouped(CsrSys sy, OutCtx oc,
                                                                      const int64_t *cand_rowptr,
                                                                      const int32_t *cand_dst) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char cg_smem[];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   CsrGroup &w = *reinterpret_cast<CsrGroup *>(cg_smem + (size_t)wid * CG_WARP_BYTES);
@@ -1586,6 +1598,7 @@ __device__ __forceinline__ uint64_t cand_mix(uint64_t v) {
 
 __global__ void validate_cand_rows(const int64_t *rowptr, int32_t M, int64_t n_cand, uint32_t *err,
                                    unsigned long long *hash) {
+  pdl_wait();
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t e = 0;
   uint64_t h = 0;
@@ -1627,6 +1640,7 @@ __global__ void __launch_bounds__(256) validate_cand_dst(const int64_t *rowptr, 
                                                          const int32_t *method_class, int32_t M, int32_t c,
                                                          int64_t n_cand, int64_t per_warp, uint32_t *err,
                                                          unsigned long long *hash) {
+  pdl_wait();
   __shared__ int32_t s_cnt[8][128];
   __shared__ int32_t s_cls[8][32];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
@@ -1719,7 +1733,7 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
     int32_t mchunk = (int32_t)std::max<int64_t>(1, ceil_div(M, want_y));
     unsigned gy = (unsigned)ceil_div(M, mchunk);
     DenseSys sy{cx, s->dest_rec, c, M};
-    eval_dense<REC, DIG, KEEP><<<dim3(gx, gy), DB_THREADS, 0, st>>>(sy, oc, mchunk);
+    pdl_launch(eval_dense<REC, DIG, KEEP>, dim3(gx, gy), DB_THREADS, 0, st, sy, oc, mchunk);
   } else {
     CsrSys sy;
     sy.cx = cx;
@@ -1739,7 +1753,7 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
     const int64_t groups = ceil_div((int64_t)s->M, CG_M);
     const int64_t full = grouped_resident_grid<REC, DIG, KEEP>();
     unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(groups, CG_WARPS), full));
-    eval_csr_grouped<REC, DIG, KEEP><<<g, CG_WARPS * 32, CG_WARPS * CG_WARP_BYTES, st>>>(sy, oc, rowptr, dst);
+    pdl_launch(eval_csr_grouped<REC, DIG, KEEP>, g, CG_WARPS * 32, CG_WARPS * CG_WARP_BYTES, st, sy, oc, rowptr, dst);
   }
   MM_LAUNCH_CHECK();
 }
@@ -1802,6 +1816,7 @@ __device__ __forceinline__ void bitonic_block(mm_move *v, int32_t n, mm_move *sm
 }
 
 __global__ void __launch_bounds__(1024) bitonic_sort_moves(mm_move *v, int32_t n) {
+  pdl_wait();
   __shared__ mm_move sm[BITONIC_MAX];
   bitonic_block(v, n, sm);
 }
@@ -1823,6 +1838,7 @@ __device__ __forceinline__ int bits_dev(uint32_t v) { return v ? 32 - __clz(v) :
 
 __global__ void __launch_bounds__(1024) sort_kept_keyed(mm_move *v, const unsigned long long *count, int32_t n,
                                                         int64_t cap, int32_t c, int32_t M) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char ksm[];
   __shared__ int32_t red[6][32];
   const int64_t K = count ? (int64_t)*count : (int64_t)n;
@@ -1915,7 +1931,7 @@ static void keyed_sort_launch(mm_move *v, const unsigned long long *count, int32
   static const cudaError_t attr = cudaFuncSetAttribute(sort_kept_keyed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                        (int)KEYED_SMEM);
   MM_CUDA_TRY(attr);
-  sort_kept_keyed<<<1, 1024, KEYED_SMEM, st>>>(v, count, n, cap, c, M);
+  pdl_launch(sort_kept_keyed, 1, 1024, KEYED_SMEM, st, v, count, n, cap, c, M);
   MM_LAUNCH_CHECK();
 }
 
@@ -1931,6 +1947,7 @@ __global__ void __launch_bounds__(1024) bitonic_sort_segments(mm_move *base, int
 // field-wise LSD radix sort of kept moves through a permutation
 __global__ void gather_field(const mm_move *v, const uint32_t *perm, int64_t n, int field, int64_t bias,
                              uint32_t *key) {
+  pdl_wait();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const mm_move &a = v[perm[i]];
@@ -1948,6 +1965,7 @@ __global__ void gather_field(const mm_move *v, const uint32_t *perm, int64_t n, 
 // min and max of n_improved, d_lcom_ck_sum and d_cbo_sum over the kept moves
 // (mm = {min, max} x 3, initialised to {INT_MAX, INT_MIN})
 __global__ void kept_ranges(const mm_move *v, int64_t n, int32_t *mm) {
+  pdl_wait();
   int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const mm_move a = v[i];
@@ -1980,6 +1998,7 @@ struct KeyLayout {
 };
 
 __global__ void kept_keys(const mm_move *v, int64_t n, KeyLayout kl, uint64_t *key, uint32_t *perm) {
+  pdl_wait();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const mm_move a = v[i];
@@ -1991,16 +2010,19 @@ __global__ void kept_keys(const mm_move *v, int64_t n, KeyLayout kl, uint64_t *k
 }
 
 __global__ void iota_perm(uint32_t *p, int64_t n) {
+  pdl_wait();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = (uint32_t)i;
 }
 
 __global__ void permute_moves(const mm_move *in, const uint32_t *perm, int64_t n, mm_move *out) {
+  pdl_wait();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = in[perm[i]];
 }
 
 __global__ void count_marks(const uint8_t *mark, int64_t n, unsigned long long *out) {
+  pdl_wait();
   unsigned long long c = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     c += mark[i];
@@ -2046,14 +2068,14 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
   MM_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(uint32_t), st));
   MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 3, 0, sizeof(unsigned long long), st));
   if (s->M > 0) {
-    validate_cand_rows<<<grid_for(s->M), TPB, 0, st>>>(*rowptr, s->M, *n_cand, s->d_err, s->d_u64 + 3);
+    pdl_launch(validate_cand_rows, grid_for(s->M), TPB, 0, st, *rowptr, s->M, *n_cand, s->d_err, s->d_u64 + 3);
     MM_LAUNCH_CHECK();
     if (*n_cand > 0) {
       // one contiguous range per warp (a multiple of 128 entries), at most 148 x 16 blocks of 8 warps
       const int64_t warps = std::min<int64_t>(ceil_div(*n_cand, 128), (int64_t)148 * 16 * (TPB / 32));
       const int64_t per_warp = ceil_div(ceil_div(*n_cand, warps), 128) * 128;
       const unsigned g = (unsigned)ceil_div(ceil_div(*n_cand, per_warp) * 32, TPB);
-      validate_cand_dst<<<g, TPB, 0, st>>>(*rowptr, *dst, s->method_class, s->M, s->c, *n_cand, per_warp,
+      pdl_launch(validate_cand_dst, g, TPB, 0, st, *rowptr, *dst, s->method_class, s->M, s->c, *n_cand, per_warp,
                                           s->d_err, s->d_u64 + 3);
       MM_LAUNCH_CHECK();
     }
@@ -2170,7 +2192,7 @@ void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K) {
     int32_t *d_mm = reinterpret_cast<int32_t *>(s->d_u64 + 24);
     const int32_t init[6] = {INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN};
     MM_CUDA_TRY(cudaMemcpyAsync(d_mm, init, sizeof(init), cudaMemcpyHostToDevice, st));
-    kept_ranges<<<(unsigned)std::min<int64_t>(ceil_div(K, TPB), 148 * 4), TPB, 0, st>>>(kept, K, d_mm);
+    pdl_launch(kept_ranges, (unsigned)std::min<int64_t>(ceil_div(K, TPB), 148 * 4), TPB, 0, st, kept, K, d_mm);
     MM_LAUNCH_CHECK();
     int32_t r[6];
     MM_CUDA_TRY(cudaMemcpyAsync(r, d_mm, sizeof(r), cudaMemcpyDeviceToHost, st));
@@ -2193,10 +2215,10 @@ void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K) {
       kl.s_cbo = w_d + w_m;
       kl.s_ck = kl.s_cbo + w_cbo;
       kl.s_nimp = kl.s_ck + w_ck;
-      kept_keys<<<grid_for(K), TPB, 0, st>>>(kept, K, kl, key, perm);
+      pdl_launch(kept_keys, grid_for(K), TPB, 0, st, kept, K, kl, key, perm);
       MM_LAUNCH_CHECK();
       radix_sort_u64(key, key_alt, perm, perm_alt, K, total, s->sort_ws, st);
-      permute_moves<<<grid_for(K), TPB, 0, st>>>(kept, perm, K, sorted);
+      pdl_launch(permute_moves, grid_for(K), TPB, 0, st, kept, perm, K, sorted);
       MM_LAUNCH_CHECK();
       MM_CUDA_TRY(cudaMemcpyAsync(kept, sorted, sizeof(mm_move) * (size_t)K, cudaMemcpyDeviceToDevice, st));
       return;
@@ -2206,16 +2228,16 @@ void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K) {
     uint32_t *pw = static_cast<uint32_t *>(s->stage_ws.need(pb + sizeof(mm_move) * (size_t)K + 256, st));
     uint32_t *key = pw, *key_alt = pw + K, *perm = pw + 2 * K, *perm_alt = pw + 3 * K;
     mm_move *sorted = reinterpret_cast<mm_move *>(pw + 4 * K);
-    iota_perm<<<grid_for(K), TPB, 0, st>>>(perm, K);
+    pdl_launch(iota_perm, grid_for(K), TPB, 0, st, perm, K);
     MM_LAUNCH_CHECK();
     const int fbits[5] = {w_d, w_m, w_cbo, w_ck, w_n};
     const int64_t bias[5] = {0, 0, -(int64_t)r[4], -(int64_t)r[2], (int64_t)r[1]};
     for (int f = 0; f < 5; ++f) {
-      gather_field<<<grid_for(K), TPB, 0, st>>>(kept, perm, K, f, bias[f], key);
+      pdl_launch(gather_field, grid_for(K), TPB, 0, st, kept, perm, K, f, bias[f], key);
       MM_LAUNCH_CHECK();
       radix_sort_u32(key, key_alt, perm, perm_alt, K, fbits[f], s->sort_ws, st);
     }
-    permute_moves<<<grid_for(K), TPB, 0, st>>>(kept, perm, K, sorted);
+    pdl_launch(permute_moves, grid_for(K), TPB, 0, st, kept, perm, K, sorted);
     MM_LAUNCH_CHECK();
     MM_CUDA_TRY(cudaMemcpyAsync(kept, sorted, sizeof(mm_move) * (size_t)K, cudaMemcpyDeviceToDevice, st));
   }
@@ -2257,7 +2279,7 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
         dispatch_eval(s, cx, oc, rowptr, dst);
       }
       MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 2, 0, sizeof(unsigned long long), st));
-      count_marks<<<148 * 4, 256, 0, st>>>(mark, s->M, s->d_u64 + 2);
+      pdl_launch(count_marks, 148 * 4, 256, 0, st, mark, s->M, s->d_u64 + 2);
       MM_LAUNCH_CHECK();
       // sorts the kept moves in place when 2 <= K <= min(cap, KEYED_MAX), else leaves them
       keyed_sort_launch(kept, s->d_u64 + 1, 0, cap, s->c, s->M, st);
@@ -2337,7 +2359,7 @@ void eval_kept_into(mm_system *s, const mm_criteria &crit, const mm_candidates *
 void sort_moves_small(mm_move *v, int32_t n, cudaStream_t st) {
   if (n <= 1) return;
   if (n > BITONIC_MAX) throw MmError{MM_EINVAL, "sort_moves_small: more than 2048 moves"};
-  bitonic_sort_moves<<<1, 1024, 0, st>>>(v, n);
+  pdl_launch(bitonic_sort_moves, 1, 1024, 0, st, v, n);
   MM_LAUNCH_CHECK();
 }
 

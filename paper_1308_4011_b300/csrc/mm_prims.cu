@@ -58,6 +58,7 @@ constexpr int64_t SCAN1_MAX = (int64_t)SCAN1_THREADS * SCAN1_ROWS;  // larger in
 template <class Tin, class Tout>
 __global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(const Tin *in, Tout *out, int64_t n,
                                                                    Tout *total_out) {
+  pdl_wait();
   __shared__ Tout wsum[SCAN1_THREADS / 32];
   __shared__ Tout block_total;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -115,6 +116,7 @@ constexpr int SP_WAIT_LIMIT = 1 << 21;  // about a second of polling
 template <class Tin, class Tout>
 __global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(const Tin *in, Tout *out, int64_t n, Tout *total_out,
                                                               unsigned long long *status, unsigned int *tile_ctr) {
+  pdl_wait();
   static_assert(sizeof(Tout) <= 8, "scan sums are packed with a 2-bit flag");
   __shared__ unsigned int s_tile;
   __shared__ Tout s_prefix;
@@ -178,7 +180,7 @@ void scan_exclusive(const Tin *in, Tout *out, int64_t n, Tout *total_dev, Scratc
     return;
   }
   if (n <= SCAN1_MAX) {
-    scan_single_block<Tin, Tout><<<1, SCAN1_THREADS, 0, st>>>(in, out, n, total_dev);
+    pdl_launch(scan_single_block<Tin, Tout>, 1, SCAN1_THREADS, 0, st, in, out, n, total_dev);
     MM_LAUNCH_CHECK();
     return;
   }
@@ -186,7 +188,7 @@ void scan_exclusive(const Tin *in, Tout *out, int64_t n, Tout *total_dev, Scratc
   // tile states and the tile counter, cleared together
   unsigned long long *status = static_cast<unsigned long long *>(ws.need(sizeof(unsigned long long) * (size_t)(nb + 1), st));
   MM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(nb + 1), st));
-  scan_onepass<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, total_dev, status,
+  pdl_launch(scan_onepass<Tin, Tout>, (unsigned)nb, SCAN_THREADS, 0, st, in, out, n, total_dev, status,
                                                                   reinterpret_cast<unsigned int *>(status + nb));
   MM_LAUNCH_CHECK();
 }
@@ -201,6 +203,7 @@ constexpr int RS_RADIX = 256;
 
 template <class K>
 __global__ void radix_upsweep(const K *keys, int64_t n, int shift, uint32_t *hist, int64_t ntiles) {
+  pdl_wait();
   __shared__ uint32_t cnt[RS_RADIX];
   for (int i = threadIdx.x; i < RS_RADIX; i += RS_THREADS) cnt[i] = 0;
   __syncthreads();
@@ -218,6 +221,7 @@ __global__ void __launch_bounds__(RS_THREADS) radix_downsweep(const K *keys_in, 
                                                                K *keys_out, uint32_t *vals_out, int64_t n,
                                                                int shift, const uint32_t *offsets,
                                                                int64_t ntiles) {
+  pdl_wait();
   __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < RS_WARPS * RS_RADIX; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
@@ -285,14 +289,14 @@ void radix_sort(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_
   uint32_t *vin = vals, *vout = vals_alt;
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
-    radix_upsweep<K><<<(unsigned)ntiles, RS_THREADS, 0, st>>>(kin, n, shift, hist, ntiles);
+    pdl_launch(radix_upsweep<K>, (unsigned)ntiles, RS_THREADS, 0, st, kin, n, shift, hist, ntiles);
     MM_LAUNCH_CHECK();
     scan_exclusive<uint32_t, uint32_t>(hist, hist, nh, nullptr, part_ws, st);
     if (vals)
-      radix_downsweep<K, true><<<(unsigned)ntiles, RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, shift, hist,
+      pdl_launch(radix_downsweep<K, true>, (unsigned)ntiles, RS_THREADS, 0, st, kin, vin, kout, vout, n, shift, hist,
                                                                       ntiles);
     else
-      radix_downsweep<K, false><<<(unsigned)ntiles, RS_THREADS, 0, st>>>(kin, nullptr, kout, nullptr, n, shift,
+      pdl_launch(radix_downsweep<K, false>, (unsigned)ntiles, RS_THREADS, 0, st, kin, nullptr, kout, nullptr, n, shift,
                                                                        hist, ntiles);
     MM_LAUNCH_CHECK();
     K *tk = kin; kin = kout; kout = tk;
@@ -314,6 +318,7 @@ struct ZeroSegs {
 };
 
 __global__ void zero_segments_kernel(ZeroSegs z) {
+  pdl_wait();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 #pragma unroll
@@ -332,7 +337,7 @@ void zero_buffers(void *a, size_t na, void *b, size_t nb, void *c, size_t nc, cu
   const size_t most = std::max(z.bytes[0], std::max(z.bytes[1], z.bytes[2]));
   if (most == 0) return;
   const int64_t blocks = std::min<int64_t>(ceil_div((int64_t)(most / 16) + 1, 256), 148 * 16);
-  zero_segments_kernel<<<(unsigned)blocks, 256, 0, st>>>(z);
+  pdl_launch(zero_segments_kernel, (unsigned)blocks, 256, 0, st, z);
   MM_LAUNCH_CHECK();
 }
 
@@ -360,7 +365,7 @@ uint32_t stalled_scan_probe() {
   MM_CUDA_TRY(cudaMemset(status, 0, sizeof(unsigned long long) * 3));
   const unsigned int first = 1;
   MM_CUDA_TRY(cudaMemcpy(status + 2, &first, sizeof(first), cudaMemcpyHostToDevice));
-  scan_onepass<int32_t, int64_t><<<1, SCAN_THREADS>>>(in, out, n, nullptr, status,
+  pdl_launch(scan_onepass<int32_t, int64_t>, 1, SCAN_THREADS, 0, 0, in, out, n, nullptr, status,
                                                        reinterpret_cast<unsigned int *>(status + 2));
   MM_LAUNCH_CHECK();
   MM_CUDA_TRY(cudaDeviceSynchronize());

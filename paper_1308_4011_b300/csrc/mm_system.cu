@@ -68,6 +68,7 @@ inline unsigned grid_for(int64_t n, int tpb = TPB) {
 __global__ void validate_methods(const int32_t *method_class, const int64_t *acc_rowptr, const int32_t *acc_idx,
                                  const int64_t *call_rowptr, const int32_t *call_idx, int32_t c, int32_t M,
                                  int32_t A, int64_t n_acc, int64_t n_call, uint32_t *err) {
+  pdl_wait();
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
   uint32_t e = 0;
@@ -107,6 +108,7 @@ __global__ void validate_methods(const int32_t *method_class, const int64_t *acc
 }
 
 __global__ void validate_attrs(const int32_t *attr_class, int32_t c, int32_t A, uint32_t *err) {
+  pdl_wait();
   int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= A) return;
   int32_t C = attr_class[a];
@@ -118,6 +120,7 @@ __global__ void validate_attrs(const int32_t *attr_class, int32_t c, int32_t A, 
 
 __global__ void class_histograms(const int32_t *method_class, const int32_t *attr_class, int32_t c, int32_t M,
                                  int32_t A, int32_t *cls_n, int32_t *cls_a) {
+  pdl_wait();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < M) {
     int32_t C = method_class[i];
@@ -130,6 +133,7 @@ __global__ void class_histograms(const int32_t *method_class, const int32_t *att
 }
 
 __global__ void summarise_classes(const int32_t *cls_n, int32_t c, LoadSummary *sum) {
+  pdl_wait();
   int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int32_t nmax = C < c ? cls_n[C] : 0;
   for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_down_sync(0xffffffffu, nmax, o));
@@ -139,11 +143,13 @@ __global__ void summarise_classes(const int32_t *cls_n, int32_t c, LoadSummary *
 // ---------------------------------------------------------------- structures
 
 __global__ void iota_u32(uint32_t *v, int64_t n) {
+  pdl_wait();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = (uint32_t)i;
 }
 
 __global__ void copy_i32_to_u32(const int32_t *in, uint32_t *out, int64_t n) {
+  pdl_wait();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (uint32_t)in[i];
 }
@@ -151,6 +157,7 @@ __global__ void copy_i32_to_u32(const int32_t *in, uint32_t *out, int64_t n) {
 // rank of each item inside its class after the stable sort by class
 __global__ void local_ranks(const uint32_t *sorted_cls, const uint32_t *sorted_item, const int64_t *rowptr,
                             int64_t n, int32_t *local, int32_t *list) {
+  pdl_wait();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t C = sorted_cls[i], it = sorted_item[i];
@@ -161,6 +168,7 @@ __global__ void local_ranks(const uint32_t *sorted_cls, const uint32_t *sorted_i
 // ids already grouped by class in ascending order: the rank is id - first id of the class
 __global__ void local_ranks_sorted(const int32_t *cls, const int64_t *rowptr, int64_t n, int32_t *local,
                                    int32_t *list) {
+  pdl_wait();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   local[i] = (int32_t)(i - rowptr[cls[i]]);
@@ -168,6 +176,7 @@ __global__ void local_ranks_sorted(const int32_t *cls, const int64_t *rowptr, in
 }
 
 __global__ void fan_in_hist(const int32_t *call_idx, int64_t n_call, int32_t *fan_in) {
+  pdl_wait();
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n_call) atomicAdd(&fan_in[call_idx[e]], 1);
 }
@@ -182,16 +191,16 @@ void load_validate_and_summarise(mm_system *s) {
   MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 4, 0, 4 * sizeof(unsigned long long), st));  // summary and error word
   MM_CUDA_TRY(cudaMemsetAsync(s->cls_n, 0, sizeof(int32_t) * 2 * (size_t)s->c, st));  // cls_n, cls_a
   if (s->M > 0)
-    validate_methods<<<grid_for(s->M), TPB, 0, st>>>(s->method_class, s->acc_rowptr, s->acc_idx, s->call_rowptr,
+    pdl_launch(validate_methods, grid_for(s->M), TPB, 0, st, s->method_class, s->acc_rowptr, s->acc_idx, s->call_rowptr,
                                                      s->call_idx, s->c, s->M, s->A, s->n_acc, s->n_call, s->d_err);
   MM_LAUNCH_CHECK();
-  if (s->A > 0) validate_attrs<<<grid_for(s->A), TPB, 0, st>>>(s->attr_class, s->c, s->A, s->d_err);
+  if (s->A > 0) pdl_launch(validate_attrs, grid_for(s->A), TPB, 0, st, s->attr_class, s->c, s->A, s->d_err);
   MM_LAUNCH_CHECK();
   int64_t nmax = std::max<int64_t>(s->M, s->A);
-  class_histograms<<<grid_for(nmax), TPB, 0, st>>>(s->method_class, s->attr_class, s->c, s->M, s->A, s->cls_n,
+  pdl_launch(class_histograms, grid_for(nmax), TPB, 0, st, s->method_class, s->attr_class, s->c, s->M, s->A, s->cls_n,
                                                    s->cls_a);
   MM_LAUNCH_CHECK();
-  summarise_classes<<<grid_for(s->c), TPB, 0, st>>>(s->cls_n, s->c, dsum);
+  pdl_launch(summarise_classes, grid_for(s->c), TPB, 0, st, s->cls_n, s->c, dsum);
   MM_LAUNCH_CHECK();
 }
 
@@ -228,34 +237,34 @@ void build_structures(mm_system *s) {
   // class -> methods: stable sort of method ids by owner class
   scan_exclusive_i32to64(s->cls_n, s->cm_rowptr, c, s->sort_ws, st, s->cm_rowptr + c);  // total = M
   if (M > 0 && s->methods_by_class) {
-    local_ranks_sorted<<<grid_for(M), TPB, 0, st>>>(s->method_class, s->cm_rowptr, M, s->method_local, s->cm_list);
+    pdl_launch(local_ranks_sorted, grid_for(M), TPB, 0, st, s->method_class, s->cm_rowptr, M, s->method_local, s->cm_list);
     MM_LAUNCH_CHECK();
   } else if (M > 0) {
-    copy_i32_to_u32<<<grid_for(M), TPB, 0, st>>>(s->method_class, k, M);
-    iota_u32<<<grid_for(M), TPB, 0, st>>>(v, M);
+    pdl_launch(copy_i32_to_u32, grid_for(M), TPB, 0, st, s->method_class, k, M);
+    pdl_launch(iota_u32, grid_for(M), TPB, 0, st, v, M);
     MM_LAUNCH_CHECK();
     radix_sort_u32(k, ka, v, va, M, cbits, s->sort_ws, st);
-    local_ranks<<<grid_for(M), TPB, 0, st>>>(k, v, s->cm_rowptr, M, s->method_local, s->cm_list);
+    pdl_launch(local_ranks, grid_for(M), TPB, 0, st, k, v, s->cm_rowptr, M, s->method_local, s->cm_list);
     MM_LAUNCH_CHECK();
   }
   // class -> attributes
   scan_exclusive_i32to64(s->cls_a, s->ca_rowptr, c, s->sort_ws, st, s->ca_rowptr + c);  // total = A
   if (A > 0 && s->attrs_by_class) {
-    local_ranks_sorted<<<grid_for(A), TPB, 0, st>>>(s->attr_class, s->ca_rowptr, A, s->attr_local, nullptr);
+    pdl_launch(local_ranks_sorted, grid_for(A), TPB, 0, st, s->attr_class, s->ca_rowptr, A, s->attr_local, nullptr);
     MM_LAUNCH_CHECK();
   } else if (A > 0) {
-    copy_i32_to_u32<<<grid_for(A), TPB, 0, st>>>(s->attr_class, k, A);
-    iota_u32<<<grid_for(A), TPB, 0, st>>>(v, A);
+    pdl_launch(copy_i32_to_u32, grid_for(A), TPB, 0, st, s->attr_class, k, A);
+    pdl_launch(iota_u32, grid_for(A), TPB, 0, st, v, A);
     MM_LAUNCH_CHECK();
     radix_sort_u32(k, ka, v, va, A, cbits, s->sort_ws, st);
-    local_ranks<<<grid_for(A), TPB, 0, st>>>(k, v, s->ca_rowptr, A, s->attr_local, nullptr);
+    pdl_launch(local_ranks, grid_for(A), TPB, 0, st, k, v, s->ca_rowptr, A, s->attr_local, nullptr);
     MM_LAUNCH_CHECK();
   }
   // fan-in: number of callers of each method (the callers themselves are
   // grouped by class later, from the call edges, by the move precompute's sort)
   MM_CUDA_TRY(cudaMemsetAsync(s->fan_in, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(M, 1), st));
   if (E > 0) {
-    fan_in_hist<<<grid_for(E), TPB, 0, st>>>(s->call_idx, E, s->fan_in);
+    pdl_launch(fan_in_hist, grid_for(E), TPB, 0, st, s->call_idx, E, s->fan_in);
     MM_LAUNCH_CHECK();
   }
 }
