@@ -194,7 +194,6 @@ void export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *ou
     MM_LAUNCH_CHECK();
     if (kind == MM_PTR_HOST)
       MM_CUDA_TRY(cudaMemcpyAsync(out_c, d, sizeof(mm_class_metrics) * s->c, cudaMemcpyDeviceToHost, st));
-    if (kind == MM_PTR_HOST) MM_CUDA_TRY(cudaStreamSynchronize(st));
   }
   if (out_m && s->M > 0) {
     mm_method_metrics *d =
@@ -203,11 +202,11 @@ void export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *ou
     pdl_launch(export_method_kernel, (unsigned)ceil_div(s->M, 256), 256, 0, st, s->fan_in, s->call_rowptr, s->own, s->q,
                                                                        s->M, d);
     MM_LAUNCH_CHECK();
-    if (kind == MM_PTR_HOST) {
+    if (kind == MM_PTR_HOST)
       MM_CUDA_TRY(cudaMemcpyAsync(out_m, d, sizeof(mm_method_metrics) * s->M, cudaMemcpyDeviceToHost, st));
-      MM_CUDA_TRY(cudaStreamSynchronize(st));
-    }
   }
+  // one synchronisation for both host copies (stream order keeps the shared staging buffer safe)
+  if (kind == MM_PTR_HOST && ((out_c && s->c > 0) || (out_m && s->M > 0))) MM_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
 extern "C" {
