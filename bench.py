@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import tempfile
 import statistics
 import subprocess
 import sys
@@ -73,7 +74,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"mm_bench_clocks_{os.getpid()}_rank{gpu_index}.csv")
         self.window = None  # (t0, t1) wall-clock seconds of the timed region
 
     def mark(self, t0: float, t1: float):
