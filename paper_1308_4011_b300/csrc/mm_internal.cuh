@@ -221,7 +221,8 @@ struct mm_system {
   // device scalars
   uint32_t *d_err;
   unsigned long long *d_u64;       // [0] digest, [1] kept count, [2] methods with kept, [3] candidate hash,
-                                   // [4] load summary, [6..7] error word (d_err), [24..] kept field ranges
+                                   // [4] load summary, [5] group counter of the restricted evaluation,
+                                   // [6..7] error word (d_err), [24..] kept field ranges
 };
 
 // ---------------------------------------------------------------- primitives (mm_prims.cu)

@@ -1302,6 +1302,7 @@ struct CsrSys {
   uint32_t c;
   int32_t M;
   int32_t staged;                     // 0: every method takes the general path
+  unsigned long long *next_group;     // counter handing out groups (zero at launch)
 };
 
 // Asynchronous global -> shared copies (completion awaited by cp_async_wait).
@@ -1437,9 +1438,13 @@ __global__ void __launch_bounds__(CG_WARPS * 32, 3) eval_csr_grouped(CsrSys sy, 
   CsrGroup &w = *reinterpret_cast<CsrGroup *>(cg_smem + (size_t)wid * CG_WARP_BYTES);
   const uint32_t sw = sy.sw, zero_row = 2u * sy.c * sw;
   const int64_t ngroups = ((int64_t)sy.M + CG_M - 1) / CG_M;
-  const int64_t nwarps = (int64_t)gridDim.x * CG_WARPS;
   uint64_t dig = 0;
-  for (int64_t grp = (int64_t)blockIdx.x * CG_WARPS + wid; grp < ngroups; grp += nwarps) {
+  // warps take groups from a counter as they finish (groups differ widely in
+  // work: list lengths, big methods), in increasing order
+  auto take = [&]() {
+    return __shfl_sync(0xffffffffu, lane == 0 ? (int64_t)atomicAdd(sy.next_group, 1ull) : (int64_t)0, 0);
+  };
+  for (int64_t grp = take(); grp < ngroups; grp = take()) {
     const int32_t ma = (int32_t)(grp * CG_M);
     const int32_t nm = min(CG_M, sy.M - ma);
     __syncwarp();  // the previous group's readers are done with the stage
@@ -1753,6 +1758,8 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
     const int64_t groups = ceil_div((int64_t)s->M, CG_M);
     const int64_t full = grouped_resident_grid<REC, DIG, KEEP>();
     unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(groups, CG_WARPS), full));
+    sy.next_group = s->d_u64 + 5;
+    MM_CUDA_TRY(cudaMemsetAsync(sy.next_group, 0, sizeof(unsigned long long), st));
     pdl_launch(eval_csr_grouped<REC, DIG, KEEP>, g, CG_WARPS * 32, CG_WARPS * CG_WARP_BYTES, st, sy, oc, rowptr, dst);
   }
   MM_LAUNCH_CHECK();
