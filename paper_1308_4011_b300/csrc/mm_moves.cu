@@ -1429,7 +1429,7 @@ __device__ __forceinline__ int32_t warp_scan_incl(int32_t v, uint32_t lane) {
 }
 
 template <bool REC, bool DIG, bool KEEP>
-__global__ void __launch_bounds__(CG_WARPS * 32, 3) eval_csr_grouped(CsrSys sy, OutCtx oc,
+__global__ void __launch_bounds__(CG_WARPS * 32, 4) eval_csr_grouped(CsrSys sy, OutCtx oc,
                                                                      const int64_t *cand_rowptr,
                                                                      const int32_t *cand_dst) {
   pdl_wait();
