@@ -45,7 +45,7 @@ L2_FLUSH_BYTES = 512 << 20
 # kernel on the same workload, from a one-pass ncu capture (set to None when the
 # kernel changes, until it is captured again)
 EVAL_DENSE_TRAFFIC = 4771644416      # medium, eval_dense<records, kept>
-EVAL_CSR_TRAFFIC = 872560896         # large restricted, eval_csr_grouped<records, kept>
+EVAL_CSR_TRAFFIC = 897806848         # large restricted, eval_csr_grouped<records, kept>
 
 
 def _env_int(k, d):
