@@ -222,7 +222,8 @@ struct mm_system {
   uint32_t *d_err;
   unsigned long long *d_u64;       // [0] digest, [1] kept count, [2] methods with kept, [3] candidate hash,
                                    // [4] load summary, [5] group counter of the restricted evaluation,
-                                   // [6..7] error word (d_err), [24..] kept field ranges
+                                   // [6..7] error word (d_err), [8] group counter of the LCOM unions,
+                                   // [24..] kept field ranges
 };
 
 // ---------------------------------------------------------------- primitives (mm_prims.cu)

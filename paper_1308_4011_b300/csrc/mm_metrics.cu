@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
                                                   const int32_t *acc_idx, const int32_t *attr_class,
                                                   const int64_t *own_ptr, const int32_t *own_list,
                                                   const int32_t *own, int32_t M, int32_t words,
-                                                  uint32_t *gbm, int32_t *q, int64_t *cls_Q, int32_t g) {
+                                                  uint32_t *gbm, int32_t *q, int64_t *cls_Q, int32_t g,
+                                                  unsigned long long *next) {
   pdl_wait();
   extern __shared__ uint32_t lu_smem[];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
@@ -93,8 +94,9 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
   if (!gbm)
     for (int32_t i = (int32_t)lane; i < words; i += 32) bm[i] = 0u;
   __syncwarp();
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t wg = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; wg * g < M; wg += nwarps) {
+  // warps take groups from a counter (unions differ widely in length)
+  auto take = [&]() { return __shfl_sync(0xffffffffu, lane == 0 ? (int64_t)atomicAdd(next, 1ull) : (int64_t)0, 0); };
+  for (int64_t wg = take(); wg * g < M; wg = take()) {
     const int64_t base = wg * g, x = base + lane;
     const bool mine = lane < (uint32_t)g && x < M;
     const int32_t ox = mine ? own[x] : 0;
@@ -410,9 +412,10 @@ void build_metrics(mm_system *s) {
       // LCOM pair counts from accessor unions
       const int g = lcom_group(M);
       const UnionBitmap ub = union_bitmap(s, ceil_div(M, g), uw, sa);
+      MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 8, 0, sizeof(unsigned long long), sa));
       pdl_launch(lcom_union, ub.grid, 256, ub.smem, sa, s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class,
                                                  s->own_ptr, s->own_list, s->own, M, ub.words, ub.gbm, s->q,
-                                                 s->cls_Q, g);
+                                                 s->cls_Q, g, s->d_u64 + 8);
       MM_LAUNCH_CHECK();
     }
     pdl_launch(finalize_classes, grid_for(c), TPB, 0, sa, s->cls_n, s->cls_Q, c, s->cls_P);
