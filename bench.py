@@ -140,11 +140,10 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    seed_offset = 1000 * rank  # independent replica per rank (weak scaling)
     params = dict(synth.MEDIUM)
     if args.case == "small":  # profiling case: medium class count, degrees and locality, 12,000 methods
         params.update(n_methods=12000, n_attrs=6000)
-    params["seed"] = params["seed"] + seed_offset
+    params["seed"] = replica_seed(params["seed"], rank)  # independent replica per rank (weak scaling)
     system = synth.generate(**params, name="medium")
     c, M = system.n_classes, system.n_methods
     n_cand = M * (c - 1)
@@ -225,13 +224,9 @@ def run_ours(args, rank, world, local_rank):
         clk.mark(t_epoch0, time.time())
         time.sleep(0.25)  # one more sample after the region
     launches = mmref.launch_count() - launches0
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = n_cand * world * args.steps / (total_ms / 1e3)
+    value = job_value(n_cand, world, args.steps, total_ms)
 
     # end to end through the C ABI with host buffers (pinned), copies included
     e2e = run_e2e(args, system, dev, stream, mask, min_imp)
@@ -262,6 +257,28 @@ def run_ours(args, rank, world, local_rank):
                                        round(max(step_ms), 3)],
             "wall_s_timed_region": round(t_wall, 3), "verified_vs_oracle": verified}
     return line
+
+
+def max_over_ranks(total_ms, dist, device):
+    """The job's time: the slowest rank's (all-reduce MAX); the local time without
+    a process group."""
+    if dist is None:
+        return total_ms
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_cand, world, steps, total_ms):
+    """Whole-job throughput: the candidates every replica evaluated in all
+    steps over the job's time (weak scaling: each rank holds its own system)."""
+    return n_cand * world * steps / (total_ms / 1e3)
+
+
+def replica_seed(seed, rank):
+    """Each rank evaluates an independent replica of the workload."""
+    return seed + 1000 * rank
 
 
 def run_e2e(args, system, dev, stream, mask, min_imp):
@@ -360,7 +377,7 @@ def run_large(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     params = dict(synth.LARGE)
-    params["seed"] = params["seed"] + 1000 * rank  # independent replica per rank
+    params["seed"] = replica_seed(params["seed"], rank)  # independent replica per rank
     system = synth.generate(**params, name="large")
     rp, dst = synth.candidates(system, synth.LARGE_EXTRA_CANDIDATES, seed=params["seed"])
     c, M, n_cand = system.n_classes, system.n_methods, len(dst)
