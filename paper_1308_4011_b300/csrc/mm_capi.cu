@@ -95,7 +95,7 @@ void copy_segments(const CopySegs &cs, cudaStream_t st) {
   int64_t words = 0;
   for (int k = 0; k < cs.n; ++k) words = std::max<int64_t>(words, cs.seg[k].bytes / 4);
   if (words == 0) return;
-  pdl_launch(copy_segments_kernel, (unsigned)std::min<int64_t>(ceil_div(words, 256), 148 * 8), 256, 0, st, cs);
+  pdl_launch(copy_segments_kernel, (unsigned)std::min<int64_t>(ceil_div(words, 256), B300_SMS * 8), 256, 0, st, cs);
   MM_LAUNCH_CHECK();
 }
 

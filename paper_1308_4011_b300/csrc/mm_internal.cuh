@@ -38,6 +38,9 @@ void mm_count_launch();
 
 static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Streaming multiprocessors of a B300 (two dies of 74); grid caps are multiples of it.
+constexpr int B300_SMS = 148;
+
 // Programmatic dependent launch: a kernel of the pipeline is launched so that
 // the GPU may schedule its blocks while the previous kernel of the stream is
 // still finishing; every such kernel first waits (griddepcontrol.wait) until

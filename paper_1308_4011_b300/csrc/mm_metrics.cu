@@ -77,7 +77,7 @@ __global__ void own_access_fill(const int32_t *method_class, const int32_t *meth
 // dependent loads: small groups when the methods do not fill the GPU's warps,
 // 32 when they do.
 inline int lcom_group(int64_t M) {
-  const int64_t per_warp = M / (148 * 64);
+  const int64_t per_warp = M / (B300_SMS * 64);
   return per_warp >= 32 ? 32 : (per_warp >= 16 ? 16 : 8);
 }
 
@@ -315,7 +315,7 @@ __global__ void destination_records(const int32_t *cls_n, const int32_t *cls_a, 
 UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted, Scratch &ws, cudaStream_t st) {
   UnionBitmap ub;
   ub.words = (int32_t)std::max<int64_t>(1, ceil_div(std::max(s->summary.max_class_methods, 1), 32));
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps_wanted, 8), 148 * 8));
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps_wanted, 8), B300_SMS * 8));
   ub.grid = (unsigned)blocks;
   const size_t per_block = (size_t)ub.words * 8 * sizeof(uint32_t);
   if (per_block <= 48 * 1024) {
@@ -442,7 +442,7 @@ void build_metrics(mm_system *s) {
                                                s->csum, sw, edges);
     MM_LAUNCH_CHECK();
   }
-  const unsigned grow = (unsigned)std::min<int64_t>(ceil_div((int64_t)c * 32, TPB), 148 * 16);
+  const unsigned grow = (unsigned)std::min<int64_t>(ceil_div((int64_t)c * 32, TPB), B300_SMS * 16);
   pdl_launch(row_distinct, grow, TPB, 0, st, s->csum, s->out_adj, c, aw, sw, row_count);
   MM_LAUNCH_CHECK();
   // mg_rowptr = exclusive scan of the row counts (CBO); last entry = distinct pairs
@@ -451,7 +451,7 @@ void build_metrics(mm_system *s) {
                                       s->mg_cnt);
   MM_LAUNCH_CHECK();
   if (M > 0) {
-    pdl_launch(coupling_count, (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(nk, 1), TPB), 148 * 16), TPB, 0, st, 
+    pdl_launch(coupling_count, (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(nk, 1), TPB), B300_SMS * 16), TPB, 0, st, 
         edges, nk, s->mg_rowptr, s->mg_dst, s->mg_cnt);
     MM_LAUNCH_CHECK();
   }
@@ -463,7 +463,7 @@ void build_metrics(mm_system *s) {
     char *b = static_cast<char *>(s->eval_ws.need((sizeof(int32_t) + sizeof(int64_t)) * (size_t)ns + 16, st));
     int64_t *first = reinterpret_cast<int64_t *>(b);
     int32_t *cnt = reinterpret_cast<int32_t *>(first + ns);
-    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(ns, TPB), 148 * 16);
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(ns, TPB), B300_SMS * 16);
     pdl_launch(summary_popc, g, TPB, 0, st, s->csum, ns, cnt);
     MM_LAUNCH_CHECK();
     scan_exclusive_i32to64(cnt, first, ns, s->sort_ws, st);

@@ -489,7 +489,7 @@ void begin_move_lists(mm_system *s) {
   s->side_pending[1] = s->side_pending[2] = s->stream;
   if (M == 0) return;
   const int64_t nu = s->n_call + s->n_acc, nc = s->n_call;
-  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * 32, TPB), 148 * 16);
+  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * 32, TPB), B300_SMS * 16);
   cudaStream_t sl = fork_side(s, 1), sr = fork_side(s, 2);
   s->side_pending[1] = sl;
   s->side_pending[2] = sr;
@@ -542,7 +542,7 @@ void build_move_precompute(mm_system *s) {
   const ListBufs b = list_bufs(s, sl, sr);
   wait_point(s, 0, st, sl);
   if (nu > 0) {
-    pdl_launch(lists_lookup_l, (unsigned)std::min<int64_t>(ceil_div(nu, TPB), 148 * 16), TPB, 0, sl, 
+    pdl_launch(lists_lookup_l, (unsigned)std::min<int64_t>(ceil_div(nu, TPB), B300_SMS * 16), TPB, 0, sl, 
         b.l_off + M, s->l_x, s->method_class, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list);
     MM_LAUNCH_CHECK();
     wait_point(s, 1, s->side_pending[0], sl);
@@ -553,7 +553,7 @@ void build_move_precompute(mm_system *s) {
   }
   wait_point(s, 0, st, sr);
   if (nc > 0) {
-    pdl_launch(lists_lookup_r, (unsigned)std::min<int64_t>(ceil_div(nc, TPB), 148 * 16), TPB, 0, sr, 
+    pdl_launch(lists_lookup_r, (unsigned)std::min<int64_t>(ceil_div(nc, TPB), B300_SMS * 16), TPB, 0, sr, 
         b.r_off + M, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->r_list);
     MM_LAUNCH_CHECK();
   }
@@ -1578,7 +1578,7 @@ int64_t grouped_resident_grid() {
   static std::atomic<int64_t> cached{0};
   int64_t v = cached.load(std::memory_order_relaxed);
   if (!v) {
-    int dev = 0, sms = 148, per = 1;
+    int dev = 0, sms = B300_SMS, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, eval_csr_grouped<REC, DIG, KEEP>, CG_WARPS * 32,
@@ -1734,7 +1734,7 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
     unsigned gx = (unsigned)ceil_div(c, DB_SPAN);
     // about 90 blocks per SM (4 resident at a time): short method chunks keep
     // the last wave's tail small relative to the whole launch
-    int64_t want_y = std::max<int64_t>(1, (148 * 3 * 30) / gx);
+    int64_t want_y = std::max<int64_t>(1, (B300_SMS * 3 * 30) / gx);
     int32_t mchunk = (int32_t)std::max<int64_t>(1, ceil_div(M, want_y));
     unsigned gy = (unsigned)ceil_div(M, mchunk);
     DenseSys sy{cx, s->dest_rec, c, M};
@@ -2078,8 +2078,8 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
     pdl_launch(validate_cand_rows, grid_for(s->M), TPB, 0, st, *rowptr, s->M, *n_cand, s->d_err, s->d_u64 + 3);
     MM_LAUNCH_CHECK();
     if (*n_cand > 0) {
-      // one contiguous range per warp (a multiple of 128 entries), at most 148 x 16 blocks of 8 warps
-      const int64_t warps = std::min<int64_t>(ceil_div(*n_cand, 128), (int64_t)148 * 16 * (TPB / 32));
+      // one contiguous range per warp (a multiple of 128 entries), at most B300_SMS x 16 blocks of 8 warps
+      const int64_t warps = std::min<int64_t>(ceil_div(*n_cand, 128), (int64_t)B300_SMS * 16 * (TPB / 32));
       const int64_t per_warp = ceil_div(ceil_div(*n_cand, warps), 128) * 128;
       const unsigned g = (unsigned)ceil_div(ceil_div(*n_cand, per_warp) * 32, TPB);
       pdl_launch(validate_cand_dst, g, TPB, 0, st, *rowptr, *dst, s->method_class, s->M, s->c, *n_cand, per_warp,
@@ -2199,7 +2199,7 @@ void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K) {
     int32_t *d_mm = reinterpret_cast<int32_t *>(s->d_u64 + 24);
     const int32_t init[6] = {INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN};
     MM_CUDA_TRY(cudaMemcpyAsync(d_mm, init, sizeof(init), cudaMemcpyHostToDevice, st));
-    pdl_launch(kept_ranges, (unsigned)std::min<int64_t>(ceil_div(K, TPB), 148 * 4), TPB, 0, st, kept, K, d_mm);
+    pdl_launch(kept_ranges, (unsigned)std::min<int64_t>(ceil_div(K, TPB), B300_SMS * 4), TPB, 0, st, kept, K, d_mm);
     MM_LAUNCH_CHECK();
     int32_t r[6];
     MM_CUDA_TRY(cudaMemcpyAsync(r, d_mm, sizeof(r), cudaMemcpyDeviceToHost, st));
@@ -2286,7 +2286,7 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
         dispatch_eval(s, cx, oc, rowptr, dst);
       }
       MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 2, 0, sizeof(unsigned long long), st));
-      pdl_launch(count_marks, 148 * 4, 256, 0, st, mark, s->M, s->d_u64 + 2);
+      pdl_launch(count_marks, B300_SMS * 4, 256, 0, st, mark, s->M, s->d_u64 + 2);
       MM_LAUNCH_CHECK();
       // sorts the kept moves in place when 2 <= K <= min(cap, KEYED_MAX), else leaves them
       keyed_sort_launch(kept, s->d_u64 + 1, 0, cap, s->c, s->M, st);
@@ -2471,7 +2471,7 @@ void batch_launch(const void *items_dev, int32_t n, int64_t total_tiles, int32_t
 }
 
 int batch_persistent_grid() {
-  int dev = 0, sms = 148, per_sm = 1;
+  int dev = 0, sms = B300_SMS, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_dense_batched<true, true>, DB_THREADS, 0);

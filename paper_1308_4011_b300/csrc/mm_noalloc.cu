@@ -109,7 +109,7 @@ extern "C" MMREF_API mm_status mm_suggest_moves_noalloc(mm_system *s, const mm_c
     if (s->M > 0) MM_CUDA_TRY(cudaMemsetAsync(mark, 0, (size_t)s->M, st));
     eval_kept_into(s, *crit, cands, kept, MM_NOALLOC_MAX_KEPT, &counters[0], mark);
     if (s->M > 0) {
-      count_bytes<<<148 * 4, 256, 0, st>>>(mark, s->M, &counters[1]);
+      count_bytes<<<B300_SMS * 4, 256, 0, st>>>(mark, s->M, &counters[1]);
       MM_LAUNCH_CHECK();
     }
     unsigned long long hc[2] = {0, 0};

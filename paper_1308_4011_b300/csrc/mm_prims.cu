@@ -336,7 +336,7 @@ void zero_buffers(void *a, size_t na, void *b, size_t nb, void *c, size_t nc, cu
   ZeroSegs z{{a, b, c}, {a ? na : 0, b ? nb : 0, c ? nc : 0}};
   const size_t most = std::max(z.bytes[0], std::max(z.bytes[1], z.bytes[2]));
   if (most == 0) return;
-  const int64_t blocks = std::min<int64_t>(ceil_div((int64_t)(most / 16) + 1, 256), 148 * 16);
+  const int64_t blocks = std::min<int64_t>(ceil_div((int64_t)(most / 16) + 1, 256), B300_SMS * 16);
   pdl_launch(zero_segments_kernel, (unsigned)blocks, 256, 0, st, z);
   MM_LAUNCH_CHECK();
 }
