@@ -193,6 +193,10 @@ __device__ __forceinline__ int32_t record_classes(const uint2 *csum, const uint3
 
 // Pass 2: CBO(Y) = number of marked classes of out-row Y (warp per row,
 // lanes over its summary records).
+// Rows of at most this many words (8,192 classes) are walked word by word with
+// every lane busy; longer rows through their summary records.
+constexpr int64_t ROW_WORDS_DIRECT = 256;
+
 __global__ void row_distinct(const uint2 *csum, const uint32_t *out_adj, int32_t c, int64_t aw, int64_t sw,
                              int32_t *row_count) {
   pdl_wait();
@@ -200,7 +204,10 @@ __global__ void row_distinct(const uint2 *csum, const uint32_t *out_adj, int32_t
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t Y = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; Y < c; Y += nwarps) {
     int32_t n = 0;
-    for (int64_t k = lane; k < sw; k += 32) n += record_classes(csum, out_adj, aw, sw, (int32_t)Y, k);
+    if (aw <= ROW_WORDS_DIRECT)  // short rows: lanes over the words themselves
+      for (int64_t k = lane; k < aw; k += 32) n += __popc(out_adj[Y * aw + k]);
+    else  // long rows: lanes over the summary records, only marked words read
+      for (int64_t k = lane; k < sw; k += 32) n += record_classes(csum, out_adj, aw, sw, (int32_t)Y, k);
     for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
     if (lane == 0) row_count[Y] = n;
   }
@@ -216,6 +223,32 @@ __global__ void row_enumerate(uint2 *csum, const uint32_t *out_adj, uint32_t *in
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t Y = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; Y < c; Y += nwarps) {
     int64_t pos = mg_rowptr[Y];
+    if (aw <= ROW_WORDS_DIRECT) {  // lane per word: ascending words, ascending bits within a word
+      for (int64_t k0 = 0; k0 < aw; k0 += 32) {
+        const int64_t wi = k0 + lane;
+        uint32_t word = wi < aw ? out_adj[Y * aw + wi] : 0u;
+        const int32_t n = __popc(word);
+        int32_t incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+          if ((int)lane >= o) incl += t;
+        }
+        int64_t p = pos + incl - n;
+        while (word) {
+          const int b = __ffs(word) - 1;
+          word &= word - 1u;
+          const int32_t E = (int32_t)(wi * 32 + b);
+          mg_dst[p] = E;
+          mg_cnt[p] = 0;
+          ++p;
+          atomicOr(&in_adj[(int64_t)E * aw + (Y >> 5)], 1u << (Y & 31));
+          atomicOr(&csum[((int64_t)c + E) * sw + (Y >> 10)].x, 1u << ((Y >> 5) & 31));
+        }
+        pos += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      continue;
+    }
     for (int64_t k0 = 0; k0 < sw; k0 += 32) {
       const int64_t k = k0 + lane;
       const int32_t n = k < sw ? record_classes(csum, out_adj, aw, sw, (int32_t)Y, k) : 0;
