@@ -801,9 +801,12 @@ __device__ __forceinline__ void emit_kept(const OutCtx &oc, bool kept, int32_t m
 //   R entry X (X calls m):  bit D = 1 iff CBO(X) drops (X stops using C and
 //                           already uses D) or rises (X keeps C, starts using D);
 //                           which of the two is the entry's uniform "shift".
-// The evaluation loops are then shift/and/add on shared-memory broadcasts.  A
-// destination that appears in m's own lists (D == E or D == X) takes the exact
-// general path; everything else uses destination constants precomputed once.
+// The evaluation then takes a thread's four destinations at once, one byte
+// lane each: byte permutes gather the thread's bit of an entry's four words,
+// and the counts, the outcome and the record words are packed byte arithmetic
+// over per-method and per-destination constants.  A destination that appears
+// in m's own lists (D == E or D == X) takes the exact general path, one per
+// thread after the batch.
 constexpr int DQ = 4;
 constexpr int DB_THREADS = 256;
 constexpr int DB_WARPS = DB_THREADS / 32;
