@@ -238,6 +238,10 @@ void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tot
 // Copies the device flag of bounded waits that gave up (nonzero) to *host once
 // the stream reaches this point; the caller synchronises before reading it.
 void read_wait_fault(uint32_t *host, cudaStream_t st);
+// Page-locked host memory of the calling thread for small read-backs (grow-only,
+// freed when the thread exits): copies into it are asynchronous, so a call's
+// read-backs need one synchronisation between them, not one each.
+void *host_staging(size_t bytes);
 // Zeroes three buffers (null or 16-byte aligned starts) in one launch of
 // 16-byte stores (faster than cudaMemsetAsync on large buffers here).
 void zero_buffers(void *a, size_t na, void *b, size_t nb, void *c, size_t nc, cudaStream_t st);

@@ -2270,7 +2270,8 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
   // Host outputs of up to KEYED_MAX kept moves need one round trip: the sort
   // (which checks the count on the device) and the copy of the first moves
   // are queued before the count is read back.
-  std::vector<mm_move> staged;
+  const mm_move *staged = nullptr;  // the first moves, copied back with the counts
+  int64_t nstaged = 0;
   bool sorted_early = false;
   if (n_cand > 0 && s->M > 0) {
     EvalCtx cx = make_ctx(s, crit);
@@ -2294,15 +2295,19 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
       // sorts the kept moves in place when 2 <= K <= min(cap, KEYED_MAX), else leaves them
       keyed_sort_launch(kept, s->d_u64 + 1, 0, cap, s->c, s->M, st);
       const int64_t nstage = kind == MM_PTR_HOST ? std::min<int64_t>({(int64_t)k, cap, (int64_t)KEYED_MAX}) : 0;
-      staged.resize((size_t)nstage);
+      // page-locked staging: {counts (2 x u64), fault flag, pad, moves}
+      unsigned char *hb = static_cast<unsigned char *>(host_staging(32 + sizeof(mm_move) * (size_t)nstage));
+      unsigned long long *hc = reinterpret_cast<unsigned long long *>(hb);
+      uint32_t *hfault = reinterpret_cast<uint32_t *>(hb + 16);
+      *hfault = 0;
       if (nstage > 0)
-        MM_CUDA_TRY(cudaMemcpyAsync(staged.data(), kept, sizeof(mm_move) * (size_t)nstage,
-                                    cudaMemcpyDeviceToHost, st));
-      unsigned long long hc[2];
-      uint32_t fault = 0;
-      MM_CUDA_TRY(cudaMemcpyAsync(hc, s->d_u64 + 1, sizeof(hc), cudaMemcpyDeviceToHost, st));
-      read_wait_fault(&fault, st);
+        MM_CUDA_TRY(cudaMemcpyAsync(hb + 32, kept, sizeof(mm_move) * (size_t)nstage, cudaMemcpyDeviceToHost, st));
+      MM_CUDA_TRY(cudaMemcpyAsync(hc, s->d_u64 + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+      read_wait_fault(hfault, st);
       MM_CUDA_TRY(cudaStreamSynchronize(st));
+      staged = reinterpret_cast<const mm_move *>(hb + 32);
+      nstaged = nstage;
+      const uint32_t fault = *hfault;
         if (fault) {
         clear_wait_fault();
         throw MmError{MM_ETIMEOUT, "suggest: a bounded device-side wait gave up"};
@@ -2326,8 +2331,8 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
   }
   const int64_t nout = std::min<int64_t>(k, K);
   if (nout > 0) {
-    if (sorted_early && kind == MM_PTR_HOST && (int64_t)staged.size() >= nout) {
-      std::memcpy(out, staged.data(), sizeof(mm_move) * (size_t)nout);
+    if (sorted_early && kind == MM_PTR_HOST && staged && nstaged >= nout) {
+      std::memcpy(out, staged, sizeof(mm_move) * (size_t)nout);
       if (n_kept) *n_kept = K;
       if (n_mk) *n_mk = nm;
       return;

@@ -6,6 +6,8 @@
 
 #include <algorithm>
 
+#include <cstring>
+
 #include "mm_internal.cuh"
 
 // ---------------------------------------------------------------- memory helpers
@@ -207,14 +209,40 @@ void load_validate_and_summarise(mm_system *s) {
 // Read back and wait for the load checks queued by load_validate_and_summarise
 // (the caller may allocate in between: a read-back into pageable memory blocks
 // the host, so it comes last).
+namespace {
+struct HostStaging {
+  void *p = nullptr;
+  size_t cap = 0;
+  ~HostStaging() {
+    if (p) cudaFreeHost(p);  // at process exit the runtime may be gone: errors ignored
+  }
+};
+thread_local HostStaging tl_host;
+}  // namespace
+
+void *host_staging(size_t bytes) {
+  if (tl_host.p && bytes <= tl_host.cap) return tl_host.p;
+  const size_t want = std::max<size_t>(bytes, std::max<size_t>(2 * tl_host.cap, 4096));
+  if (tl_host.p) cudaFreeHost(tl_host.p);  // between calls: no copy targets it any more
+  tl_host.p = nullptr;
+  tl_host.cap = 0;
+  MM_CUDA_TRY(cudaMallocHost(&tl_host.p, want));
+  tl_host.cap = want;
+  return tl_host.p;
+}
+
 void load_finish(mm_system *s) {
   cudaStream_t st = s->stream;
-  MM_CUDA_TRY(cudaMemcpyAsync(&s->summary, reinterpret_cast<LoadSummary *>(s->d_u64 + 4), sizeof(LoadSummary),
-                              cudaMemcpyDeviceToHost, st));
-  MM_CUDA_TRY(cudaMemcpyAsync(&s->load_err, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  uint32_t fault = 0;
-  read_wait_fault(&fault, st);
+  // d_u64[4] = load summary, d_u64[6] = error word: one copy, plus the fault flag
+  unsigned char *h = static_cast<unsigned char *>(host_staging(48));
+  MM_CUDA_TRY(cudaMemcpyAsync(h, s->d_u64 + 4, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  uint32_t *hfault = reinterpret_cast<uint32_t *>(h + 32);
+  *hfault = 0;
+  read_wait_fault(hfault, st);
   MM_CUDA_TRY(cudaStreamSynchronize(st));
+  std::memcpy(&s->summary, h, sizeof(LoadSummary));
+  std::memcpy(&s->load_err, h + 16, sizeof(uint32_t));
+  const uint32_t fault = *hfault;
   if (fault) {
     clear_wait_fault();
     throw MmError{MM_ETIMEOUT, "load: a bounded device-side wait gave up"};
