@@ -2090,10 +2090,13 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
       MM_LAUNCH_CHECK();
     }
   }
-  uint32_t err = 0;
-  MM_CUDA_TRY(cudaMemcpyAsync(&err, s->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  if (hash) MM_CUDA_TRY(cudaMemcpyAsync(hash, s->d_u64 + 3, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  // d_u64[3] = hash, d_u64[6] = error word: one copy into page-locked staging
+  unsigned char *hb = static_cast<unsigned char *>(host_staging(32));
+  MM_CUDA_TRY(cudaMemcpyAsync(hb, s->d_u64 + 3, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   MM_CUDA_TRY(cudaStreamSynchronize(st));
+  uint32_t err = 0;
+  std::memcpy(&err, hb + 24, sizeof(uint32_t));
+  if (hash) std::memcpy(hash, hb, sizeof(uint64_t));
   if (err & VE_CAND_ROWPTR) throw MmError{MM_EINVAL, "candidates: rowptr must start at 0, be non-decreasing and end at n_cand"};
   if (err & VE_CAND_RANGE) throw MmError{MM_EINVAL, "candidates: destination class out of range"};
   if (err & VE_CAND_SELF) throw MmError{MM_EINVAL, "candidates: destination equals the method's own class"};
