@@ -106,6 +106,27 @@ void upload(T *dst, const T *src, int64_t n, int32_t kind, cudaStream_t st) {
                               kind == MM_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
 }
 
+void allocate_load_buffers(mm_system *s) {
+  DevArena &a = s->arena;
+  const int64_t c = s->c, M = s->M, A = s->A;
+  s->method_class = a.get<int32_t>(M);
+  s->attr_class = a.get<int32_t>(A);
+  s->acc_rowptr = a.get<int64_t>(M + 1);
+  s->acc_idx = a.get<int32_t>(s->n_acc);
+  s->call_rowptr = a.get<int64_t>(M + 1);
+  s->call_idx = a.get<int32_t>(s->n_call);
+  s->cls_n = a.get<int32_t>(2 * c);  // cls_a follows cls_n: one clear for both
+  s->cls_a = s->cls_n ? s->cls_n + c : nullptr;
+  s->cm_rowptr = a.get<int64_t>(c + 1);
+  s->cm_list = a.get<int32_t>(M);
+  s->method_local = a.get<int32_t>(M);
+  s->ca_rowptr = a.get<int64_t>(c + 1);
+  s->attr_local = a.get<int32_t>(A);
+  s->fan_in = a.get<int32_t>(M);
+  s->d_u64 = a.get<unsigned long long>(32);
+  s->d_err = s->d_u64 ? reinterpret_cast<uint32_t *>(s->d_u64 + 6) : nullptr;  // cleared with the load summary
+}
+
 void allocate_compute_buffers(mm_system *s) {
   DevArena &a = s->arena;
   const int64_t c = s->c, M = s->M, nu = s->n_call + s->n_acc;
@@ -247,24 +268,14 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     s->n_acc = desc->n_acc;
     s->n_call = desc->n_call;
     s->cbo_attrs = desc->cbo_attrs ? 1 : 0;
-    DevArena &a = s->arena;
     const int64_t c = s->c, M = s->M, A = s->A;
-    s->method_class = a.get<int32_t>(M);
-    s->attr_class = a.get<int32_t>(A);
-    s->acc_rowptr = a.get<int64_t>(M + 1);
-    s->acc_idx = a.get<int32_t>(s->n_acc);
-    s->call_rowptr = a.get<int64_t>(M + 1);
-    s->call_idx = a.get<int32_t>(s->n_call);
-    s->cls_n = a.get<int32_t>(2 * c);  // cls_a follows cls_n: one clear for both
-    s->cls_a = s->cls_n + c;
-    s->cm_rowptr = a.get<int64_t>(c + 1);
-    s->cm_list = a.get<int32_t>(M);
-    s->method_local = a.get<int32_t>(M);
-    s->ca_rowptr = a.get<int64_t>(c + 1);
-    s->attr_local = a.get<int32_t>(A);
-    s->fan_in = a.get<int32_t>(M);
-    s->d_u64 = a.get<unsigned long long>(32);
-    s->d_err = reinterpret_cast<uint32_t *>(s->d_u64 + 6);  // cleared with the load summary
+    // size every load-time buffer, reserve one slab, then carve them out of it
+    s->arena.sizing = true;
+    allocate_load_buffers(s);
+    allocate_compute_buffers(s);
+    s->arena.sizing = false;
+    s->arena.reserve(s->arena.sized);
+    allocate_load_buffers(s);
     cudaStream_t stv = s->stream;
     if (desc->ptr_kind == MM_PTR_DEVICE) {  // one copy kernel for the six device arrays
       CopySegs cs{};

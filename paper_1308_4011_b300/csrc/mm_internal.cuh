@@ -77,9 +77,17 @@ struct DevArena {
   cudaStream_t stream = nullptr;
   std::vector<void *> ptrs;
   int64_t bytes = 0;
+  // One slab reserved at load holds the load-time buffers (one allocation and
+  // one free instead of dozens); later or larger requests get their own.  In
+  // sizing mode alloc() only adds up the sizes and returns null.
+  bool sizing = false;
+  size_t sized = 0;
+  char *slab = nullptr;
+  size_t slab_cap = 0, slab_used = 0;
+  void reserve(size_t n);
   void *alloc(size_t n);
   void release();
-  void forget(void *p);  // free one allocation now (stream-ordered)
+  void forget(void *p);  // free one allocation now (stream-ordered); slab memory stays until release
   template <class T>
   T *get(int64_t count) {
     return static_cast<T *>(alloc(sizeof(T) * (size_t)(count > 0 ? count : 1)));

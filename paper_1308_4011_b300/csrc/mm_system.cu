@@ -12,9 +12,29 @@
 
 // ---------------------------------------------------------------- memory helpers
 
+void DevArena::reserve(size_t n) {
+  if (n == 0 || slab) return;
+  n = (n + 255) & ~size_t(255);
+  void *p = nullptr;
+  MM_CUDA_TRY(cudaMallocAsync(&p, n, stream));
+  slab = static_cast<char *>(p);
+  slab_cap = n;
+  slab_used = 0;
+  bytes += (int64_t)n;
+}
+
 void *DevArena::alloc(size_t n) {
   void *p = nullptr;
   n = (n + 255) & ~size_t(255);
+  if (sizing) {
+    sized += n;
+    return nullptr;
+  }
+  if (slab && slab_used + n <= slab_cap) {
+    p = slab + slab_used;
+    slab_used += n;
+    return p;
+  }
   MM_CUDA_TRY(cudaMallocAsync(&p, n, stream));
   ptrs.push_back(p);
   bytes += (int64_t)n;
@@ -22,6 +42,7 @@ void *DevArena::alloc(size_t n) {
 }
 
 void DevArena::forget(void *p) {
+  if (slab && static_cast<char *>(p) >= slab && static_cast<char *>(p) < slab + slab_cap) return;
   for (size_t i = 0; i < ptrs.size(); ++i)
     if (ptrs[i] == p) {
       cudaFreeAsync(p, stream);
@@ -33,6 +54,9 @@ void DevArena::forget(void *p) {
 void DevArena::release() {
   for (void *p : ptrs) cudaFreeAsync(p, stream);
   ptrs.clear();
+  if (slab) cudaFreeAsync(slab, stream);
+  slab = nullptr;
+  slab_cap = slab_used = 0;
   bytes = 0;
 }
 
