@@ -49,9 +49,9 @@ void use_device(mm_system *s) {
 // then its events (released by the runtime once their last use completes).
 void release_system(mm_system *s) {
   s->arena.release();
-  for (Scratch *w : {&s->sort_ws, &s->eval_ws, &s->stage_ws, &s->kept_ws, &s->edit_ws, &s->union_ws,
-                     &s->side_eval[0], &s->side_eval[1], &s->side_eval[2], &s->side_sort[0], &s->side_sort[1],
-                     &s->side_sort[2], &s->side_union[0], &s->side_union[1], &s->side_union[2]})
+  for (Scratch *w : {&s->sort_ws, &s->eval_ws, &s->stage_ws, &s->kept_ws, &s->keyed_ws, &s->edit_ws,
+                     &s->union_ws, &s->side_eval[0], &s->side_eval[1], &s->side_eval[2], &s->side_sort[0],
+                     &s->side_sort[1], &s->side_sort[2], &s->side_union[0], &s->side_union[1], &s->side_union[2]})
     w->release(s->stream);
   for (cudaEvent_t e : {s->fork_ev, s->join_ev[0], s->join_ev[1], s->join_ev[2], s->mid_ev[0], s->mid_ev[1]})
     if (e) cudaEventDestroy(e);
@@ -386,10 +386,10 @@ mm_status mm_system_info_get(mm_system *s, mm_system_info *info) {
     }
     info->device_bytes =
         s->arena.bytes + (int64_t)(s->sort_ws.cap + s->eval_ws.cap + s->stage_ws.cap + s->kept_ws.cap +
-                                   s->edit_ws.cap + s->union_ws.cap + s->side_eval[0].cap + s->side_eval[1].cap +
-                                   s->side_eval[2].cap + s->side_sort[0].cap + s->side_sort[1].cap +
-                                   s->side_sort[2].cap + s->side_union[0].cap + s->side_union[1].cap +
-                                   s->side_union[2].cap);
+                                   s->keyed_ws.cap + s->edit_ws.cap + s->union_ws.cap + s->side_eval[0].cap +
+                                   s->side_eval[1].cap + s->side_eval[2].cap + s->side_sort[0].cap +
+                                   s->side_sort[1].cap + s->side_sort[2].cap + s->side_union[0].cap +
+                                   s->side_union[1].cap + s->side_union[2].cap);
   });
 }
 

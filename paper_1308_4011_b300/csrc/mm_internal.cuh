@@ -166,6 +166,7 @@ struct mm_system {
   Scratch eval_ws;     // evaluate/suggest scratch (kept lists, staging)
   Scratch stage_ws;    // host-output staging
   Scratch kept_ws;     // kept moves + per-method marks of the last evaluation
+  Scratch keyed_ws;    // keys and a copy of the kept moves while they are ranked
   Scratch edit_ws;     // edit patches and incremental re-evaluation
   Scratch union_ws;    // per-warp bitmaps of accessor unions (largest classes only)
   // independent branches of the metric pipeline run on side streams, each with

@@ -1831,32 +1831,41 @@ __global__ void __launch_bounds__(1024) bitonic_sort_moves(mm_move *v, int32_t n
   bitonic_block(v, n, sm);
 }
 
-// One block sorts up to KEYED_MAX kept moves in place.  Every move gets one
-// 64-bit key in the suggestion order (n_improved descending, then dLCOM, dCBO,
-// m, d ascending; each field biased by its minimum over the moves and given the
-// bits its range needs); keys and 16-bit indices go through a bitonic network
-// in shared memory (a tie, only ever with padding, is broken by the index),
-// then the moves are gathered in key order through the same shared memory.
-// If the fields' ranges need more than 64 bits, the moves themselves go
-// through the network.  The count is read on the device when count is given,
-// so a caller needs no round trip first; nothing happens unless
+// Kept moves sorted in the suggestion order, up to KEYED_MAX of them, in two
+// launches.  Every move gets one 64-bit key (n_improved descending, then dLCOM,
+// dCBO, m, d ascending; each field biased by its minimum over the moves and
+// given the bits its range needs).  kept_sort_keys (one block) reads the count,
+// reduces the fields' ranges and writes the keys and a copy of the moves to
+// scratch; kept_sort_rank (many blocks) gives each move its rank -- how many
+// moves have a smaller key, or the same key at an earlier position -- and
+// writes it there.  The position settles ties (equal keys mean equal moves,
+// possible only when a candidate list repeats a destination), so the ranks
+// are a permutation.  If the ranges need more than 64 bits, the first launch
+// sorts the moves themselves through a bitonic network in shared memory and
+// the second does nothing.  The count is read on the device when count is
+// given, so a caller needs no round trip first; nothing happens unless
 // 2 <= K <= min(cap, KEYED_MAX).
 constexpr int KEYED_MAX = 8192;
-constexpr size_t KEYED_SMEM = (sizeof(mm_move) + sizeof(uint16_t)) * KEYED_MAX;
+constexpr size_t KEYED_SMEM = sizeof(mm_move) * KEYED_MAX;  // the bitonic fallback
+// scratch: {K to rank (0 = none), pad, keys[KEYED_MAX], moves[KEYED_MAX]}
+constexpr size_t KEYED_WS = 16 + (sizeof(uint64_t) + sizeof(mm_move)) * KEYED_MAX;
+constexpr int RANK_ITEMS = 32, RANK_PARTS = 8;  // moves per block, key ranges per move
+constexpr size_t RANK_SMEM = sizeof(uint64_t) * KEYED_MAX;
 
 __device__ __forceinline__ int bits_dev(uint32_t v) { return v ? 32 - __clz(v) : 0; }  // bits for [0, v]
 
-__global__ void __launch_bounds__(1024) sort_kept_keyed(mm_move *v, const unsigned long long *count, int32_t n,
-                                                        int64_t cap, int32_t c, int32_t M) {
+__global__ void __launch_bounds__(1024) kept_sort_keys(mm_move *v, const unsigned long long *count, int32_t n,
+                                                       int64_t cap, int32_t c, int32_t M, unsigned long long *ws) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char ksm[];
   __shared__ int32_t red[6][32];
-  const int64_t K = count ? (int64_t)*count : (int64_t)n;
-  if (K < 2 || K > cap || K > KEYED_MAX) return;
-  const int32_t k = (int32_t)K;
-  int32_t np = 1;
-  while (np < k) np <<= 1;
   const int tid = (int)threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t K = count ? (int64_t)*count : (int64_t)n;
+  if (K < 2 || K > cap || K > KEYED_MAX) {
+    if (tid == 0) ws[0] = 0;
+    return;
+  }
+  const int32_t k = (int32_t)K;
   // ranges of n_improved, dLCOM, dCBO
   int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
   for (int32_t i = tid; i < k; i += 1024) {
@@ -1893,55 +1902,75 @@ __global__ void __launch_bounds__(1024) sort_kept_keyed(mm_move *v, const unsign
   const int w_cbo = bits_dev((uint32_t)((int64_t)hi[2] - lo[2])), w_ck = bits_dev((uint32_t)((int64_t)hi[1] - lo[1]));
   const int w_n = bits_dev((uint32_t)((int64_t)hi[0] - lo[0]));
   if (w_d + w_m + w_cbo + w_ck + w_n > 64) {  // every block thread sees the same ranges
+    if (tid == 0) ws[0] = 0;
     __syncthreads();
     bitonic_block(v, k, reinterpret_cast<mm_move *>(ksm));
     return;
   }
   const int s_cbo = w_d + w_m, s_ck = s_cbo + w_cbo, s_n = s_ck + w_ck;
-  uint64_t *key = reinterpret_cast<uint64_t *>(ksm);
-  uint16_t *idx = reinterpret_cast<uint16_t *>(ksm + sizeof(mm_move) * KEYED_MAX);
-  for (int32_t i = tid; i < np; i += 1024) {
-    uint64_t kk = ~0ull;  // padding sorts last
-    if (i < k) {
-      const mm_move a = v[i];
-      kk = ((uint64_t)(uint32_t)a.m << w_d) | (uint64_t)(uint32_t)a.d;
-      if (w_cbo) kk |= (uint64_t)((uint32_t)a.d_cbo_sum - (uint32_t)lo[2]) << s_cbo;
-      if (w_ck) kk |= (uint64_t)((uint32_t)a.d_lcom_ck_sum - (uint32_t)lo[1]) << s_ck;
-      if (w_n) kk |= (uint64_t)((uint32_t)hi[0] - (uint32_t)a.n_improved) << s_n;
-    }
+  uint64_t *key = reinterpret_cast<uint64_t *>(ws + 2);
+  mm_move *mv = reinterpret_cast<mm_move *>(ws + 2 + KEYED_MAX);
+  for (int32_t i = tid; i < k; i += 1024) {
+    const mm_move a = v[i];
+    uint64_t kk = ((uint64_t)(uint32_t)a.m << w_d) | (uint64_t)(uint32_t)a.d;
+    if (w_cbo) kk |= (uint64_t)((uint32_t)a.d_cbo_sum - (uint32_t)lo[2]) << s_cbo;
+    if (w_ck) kk |= (uint64_t)((uint32_t)a.d_lcom_ck_sum - (uint32_t)lo[1]) << s_ck;
+    if (w_n) kk |= (uint64_t)((uint32_t)hi[0] - (uint32_t)a.n_improved) << s_n;
     key[i] = kk;
-    idx[i] = (uint16_t)i;
+    mv[i] = a;
   }
-  __syncthreads();
-  for (int32_t k2 = 2; k2 <= np; k2 <<= 1) {
-    for (int32_t j = k2 >> 1; j > 0; j >>= 1) {
-      for (int32_t p = tid; p < (np >> 1); p += 1024) {
-        const int32_t i = ((p & ~(j - 1)) << 1) | (p & (j - 1)), ixj = i | j;
-        const uint64_t a = key[i], b = key[ixj];
-        const uint16_t ia = idx[i], ib = idx[ixj];
-        const bool gt = a > b || (a == b && ia > ib);
-        if (gt == ((i & k2) == 0)) {
-          key[i] = b;
-          key[ixj] = a;
-          idx[i] = ib;
-          idx[ixj] = ia;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  mm_move *mv = reinterpret_cast<mm_move *>(ksm);  // the keys are no longer needed
-  for (int32_t i = tid; i < k; i += 1024) mv[i] = v[idx[i]];
-  __syncthreads();
-  for (int32_t i = tid; i < k; i += 1024) v[i] = mv[i];
+  if (tid == 0) ws[0] = (unsigned long long)k;
 }
 
-static void keyed_sort_launch(mm_move *v, const unsigned long long *count, int32_t n, int64_t cap, int32_t c,
-                              int32_t M, cudaStream_t st) {
-  static const cudaError_t attr = cudaFuncSetAttribute(sort_kept_keyed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)KEYED_SMEM);
-  MM_CUDA_TRY(attr);
-  pdl_launch(sort_kept_keyed, 1, 1024, KEYED_SMEM, st, v, count, n, cap, c, M);
+// Block b ranks moves b*RANK_ITEMS .. +RANK_ITEMS-1: lane l of warp q counts,
+// for move b*RANK_ITEMS + l, the keys before it among the q-th of RANK_PARTS
+// ranges of positions (a warp's lanes read the same key: a broadcast).
+__global__ void __launch_bounds__(RANK_ITEMS * RANK_PARTS) kept_sort_rank(mm_move *v,
+                                                                          const unsigned long long *ws) {
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char rsm[];
+  __shared__ int32_t part[RANK_PARTS][RANK_ITEMS];
+  const int32_t k = (int32_t)ws[0];  // 0 <= k <= KEYED_MAX
+  const int32_t i0 = (int32_t)blockIdx.x * RANK_ITEMS;
+  if (i0 >= k) return;  // the same for the whole block
+  const uint64_t *key = reinterpret_cast<const uint64_t *>(ws + 2);
+  const mm_move *mv = reinterpret_cast<const mm_move *>(ws + 2 + KEYED_MAX);
+  uint64_t *sk = reinterpret_cast<uint64_t *>(rsm);
+  const int tid = (int)threadIdx.x, lane = tid & 31, q = tid >> 5;
+  for (int32_t j = tid; j < k; j += RANK_ITEMS * RANK_PARTS) sk[j] = key[j];
+  __syncthreads();
+  const int32_t i = i0 + lane;
+  const uint64_t ki = i < k ? sk[i] : 0ull;
+  const int32_t j0 = (int32_t)((int64_t)k * q / RANK_PARTS), j1 = (int32_t)((int64_t)k * (q + 1) / RANK_PARTS);
+  int32_t r = 0;
+#pragma unroll 4
+  for (int32_t j = j0; j < j1; ++j) {
+    const uint64_t kj = sk[j];
+    r += (int32_t)((kj < ki) | ((kj == ki) & (j < i)));
+  }
+  part[q][lane] = r;
+  __syncthreads();
+  if (q == 0 && i < k) {
+    int32_t rank = 0;
+#pragma unroll
+    for (int p = 0; p < RANK_PARTS; ++p) rank += part[p][lane];
+    v[rank] = mv[i];
+  }
+}
+
+static void keyed_sort_launch(mm_system *s, mm_move *v, const unsigned long long *count, int32_t n, int64_t cap,
+                              cudaStream_t st) {
+  static const cudaError_t attr_keys =
+      cudaFuncSetAttribute(kept_sort_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KEYED_SMEM);
+  static const cudaError_t attr_rank =
+      cudaFuncSetAttribute(kept_sort_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RANK_SMEM);
+  MM_CUDA_TRY(attr_keys);
+  MM_CUDA_TRY(attr_rank);
+  auto *ws = static_cast<unsigned long long *>(s->keyed_ws.need(KEYED_WS, st));
+  pdl_launch(kept_sort_keys, 1, 1024, KEYED_SMEM, st, v, count, n, cap, s->c, s->M, ws);
+  MM_LAUNCH_CHECK();
+  pdl_launch(kept_sort_rank, KEYED_MAX / RANK_ITEMS, RANK_ITEMS * RANK_PARTS, RANK_SMEM, st, v,
+             static_cast<const unsigned long long *>(ws));
   MM_LAUNCH_CHECK();
 }
 
@@ -2192,14 +2221,14 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
   if (kind == MM_PTR_HOST) MM_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
-// Sort kept moves in the suggestion order: one-block keyed bitonic sort up to
-// 8,192, else a radix sort of 64-bit composite keys when the fields' ranges fit,
+// Sort kept moves in the suggestion order: keys by one block and ranks by many
+// up to 8,192, else a radix sort of 64-bit composite keys when the fields' ranges fit,
 // else a stable LSD radix sort field by field (d, m, dCBO, dLCOM, n_improved
 // desc) through a permutation.
 void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K) {
   cudaStream_t st = s->stream;
   if (K > 1 && K <= KEYED_MAX) {
-    keyed_sort_launch(kept, nullptr, (int32_t)K, K, s->c, s->M, st);
+    keyed_sort_launch(s, kept, nullptr, (int32_t)K, K, st);
   } else if (K > KEYED_MAX) {
     // the fields' actual ranges decide whether one 64-bit composite key holds them all
     int32_t *d_mm = reinterpret_cast<int32_t *>(s->d_u64 + 24);
@@ -2296,7 +2325,7 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
       pdl_launch(count_marks, B300_SMS * 4, 256, 0, st, mark, s->M, s->d_u64 + 2);
       MM_LAUNCH_CHECK();
       // sorts the kept moves in place when 2 <= K <= min(cap, KEYED_MAX), else leaves them
-      keyed_sort_launch(kept, s->d_u64 + 1, 0, cap, s->c, s->M, st);
+      keyed_sort_launch(s, kept, s->d_u64 + 1, 0, cap, st);
       const int64_t nstage = kind == MM_PTR_HOST ? std::min<int64_t>({(int64_t)k, cap, (int64_t)KEYED_MAX}) : 0;
       // page-locked staging: {counts (2 x u64), fault flag, pad, moves}
       unsigned char *hb = static_cast<unsigned char *>(host_staging(32 + sizeof(mm_move) * (size_t)nstage));
