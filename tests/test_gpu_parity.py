@@ -446,6 +446,35 @@ def test_candidate_validation_with_short_rows():
     g.free()
 
 
+@pytest.mark.parametrize("offset", [0, 1, 3])
+def test_device_lists_at_any_alignment(offset):
+    """Device-resident candidate lists whose destinations start 0, 4 or 12
+    bytes past a 16-byte boundary (vector and scalar loads of the validation
+    pass), with chunks of 128 entries that span few and many rows: digest and
+    kept moves equal the oracle's, and a self move in the middle is found."""
+    s = synth.generate(n_classes=60, n_methods=4000, n_attrs=2000, max_class=150, seed=9)
+    rowptr, dst = _short_row_candidates(s, 9)
+    ref = oracle.Oracle(s, threads=4).evaluate(mask=4, min_improved=1, cand_rowptr=rowptr, cand_dst=dst)
+    n = len(dst)
+    buf = torch.zeros(n + 4, dtype=torch.int32, device="cuda")
+    buf[offset: offset + n] = torch.from_numpy(dst).cuda()
+    ddst = buf[offset: offset + n]
+    drp = torch.from_numpy(rowptr).cuda()
+    torch.cuda.synchronize()
+    g, _, _ = gpu_load(s)
+    assert gpu_digest(g, 4, 1, drp, ddst) == ref.digest
+    top, nk, nm = mmref.suggest_moves(g, k=ref.n_kept, mask=4, min_improved=1, cand_rowptr=drp, cand_dst=ddst)
+    assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+    assert kept_tuples(top) == oracle_kept(ref)
+    mid = n // 2
+    owner = int(np.searchsorted(rowptr, mid, side="right")) - 1
+    ddst[mid] = int(s.method_class[owner])
+    torch.cuda.synchronize()
+    with pytest.raises(mmref.MMError, match="own class"):
+        mmref.evaluate_moves(g, 4, 1, drp, ddst, digest=np.zeros(1, np.uint64))
+    g.free()
+
+
 def test_invalid_candidates_and_criteria_rejected():
     s = synth.generate(10, 40, 20, max_class=10, seed=1)
     g, _, _ = gpu_load(s)
