@@ -1794,7 +1794,8 @@ __device__ __forceinline__ bool move_before(const mm_move &a, const mm_move &b) 
 
 constexpr int BITONIC_MAX = 2048;
 
-// one block sorts up to 2048 kept moves in shared memory (bitonic network)
+// one block sorts n kept moves through shared memory sm, which holds n rounded up
+// to a power of two (bitonic network; padding sorts last)
 __device__ __forceinline__ void bitonic_block(mm_move *v, int32_t n, mm_move *sm) {
   int32_t np = 1;
   while (np < n) np <<= 1;

@@ -304,9 +304,10 @@ def test_class_too_big_for_shared_bitmaps():
 @pytest.mark.parametrize("c,M", [(200, 2500), (300, 5000), (300, 10000)])
 def test_kept_sort_regimes(c, M):
     """About 1,900, 4,000 and 32,000 kept moves (CBO, min_improved 1): the
-    one-block keyed sort below and above 2,048 moves and the radix sort above
-    8,192 give the oracle's full suggestion order, straight after the metrics
-    and after an evaluation cached the kept moves."""
+    keyed sort (keys by one block, ranks by a block per 32 moves) at 60 and 125
+    rank blocks and the radix sort above 8,192 give the oracle's full
+    suggestion order, straight after the metrics and after an evaluation
+    cached the kept moves."""
     s = synth.generate(n_classes=c, n_methods=M, n_attrs=M, max_class=max(40, 3 * M // c), seed=7)
     ref = oracle.Oracle(s, threads=4).evaluate(mask=4, min_improved=1)
     g, _, _ = gpu_load(s)
