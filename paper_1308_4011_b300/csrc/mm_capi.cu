@@ -268,7 +268,7 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     s->n_acc = desc->n_acc;
     s->n_call = desc->n_call;
     s->cbo_attrs = desc->cbo_attrs ? 1 : 0;
-    const int64_t c = s->c, M = s->M, A = s->A;
+    const int64_t M = s->M, A = s->A;
     // size every load-time buffer, reserve one slab, then carve them out of it
     s->arena.sizing = true;
     allocate_load_buffers(s);
