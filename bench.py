@@ -46,6 +46,10 @@ L2_FLUSH_BYTES = 512 << 20
 # kernel changes, until it is captured again)
 EVAL_DENSE_TRAFFIC = 4771699968      # medium, eval_dense<records, kept>
 EVAL_CSR_TRAFFIC = 897806848         # large restricted, eval_csr_grouped<records, kept>
+# busy fraction of the integer ALU pipe in one launch of the restricted
+# evaluation (ncu sectioned capture, sm__pipe_alu_cycles_active); that kernel is
+# bound by integer instruction throughput, not by DRAM (None once it changes)
+EVAL_CSR_ALU_BUSY = 0.768
 
 
 def _env_int(k, d):
@@ -460,7 +464,8 @@ def run_large(args, rank, world, local_rank):
                          "frac": round(achieved / peak, 4), "traffic": EVAL_CSR_TRAFFIC,
                          "kernel": "eval_csr_grouped<records>",
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                         "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(eval_s * 1e3, 4)},
+                         "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(eval_s * 1e3, 4),
+                         "alu_pipe_busy_ncu": EVAL_CSR_ALU_BUSY},
             "eval_value": n_cand / eval_s, "eval_ms_median": statistics.median(eval_ms),
             "metrics_and_rest_ms": ms_per_step - statistics.median(eval_ms),
             "gpu_launches_per_step": launches / max(args.steps, 1), "clocks": clk.summary(),
