@@ -39,7 +39,22 @@ def test_table1_value_counts():
     assert rounded == 12
     # the paper's worked example: JUnit, 1,200 methods and 231 classes -> "1.2 millions"
     assert 1.2e6 <= count_values(231, 1200) < 1.3e6
-    assert lcom_values(231, 1200) == 231 * 1201
+
+
+def test_lcom_values_counts_the_assessed_classes():
+    """#LCOM values (Sec. III.B) counted from what the oracle assesses: one LCOM
+    per class as it is, plus one per (class, method) pair -- the oracle's own
+    candidate count (every method to every other class, m(c-1)) and, for each
+    method, its own class after it is moved out (m).  The count is taken from
+    the oracle's evaluation, not from the formula."""
+    s = tiny_random(3)
+    o = oracle.Oracle(s, threads=1)
+    n_cand = o.evaluate(mask=3, min_improved=2).n_cand
+    c, m = s.n_classes, s.n_methods
+    assert n_cand == m * (c - 1)
+    assert lcom_values(c, m) == c + n_cand + m
+    # and its share of Table I's total: removing it (or the CBO term) breaks the JUnit row
+    assert count_values(231, 1200) - lcom_values(231, 1200) < 1.2e6
 
 
 # ---------------------------------------------------------------- hand-worked

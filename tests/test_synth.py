@@ -60,3 +60,22 @@ def test_batched_class_counts():
     cs = [synth.logu_classes(100 + i) for i in range(256)]
     assert min(cs) >= 100 and max(cs) <= 20000
     assert 300 < np.exp(np.mean(np.log(cs))) < 5000
+
+
+def test_workload_checksums():
+    """Every named workload (tiny, medium, large and its candidate lists, the
+    256 batched systems of seeds 100..355, the 64 served systems of seeds
+    100..163) hashes to the digest stored in tests/golden/synth_checksums.json:
+    a generator change cannot silently change the workloads."""
+    import json
+    import os
+    import sys
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, golden)
+    try:
+        import make_synth_checksums as mk
+    finally:
+        sys.path.remove(golden)
+    with open(os.path.join(golden, "synth_checksums.json")) as f:
+        stored = json.load(f)
+    assert mk.compute() == stored
