@@ -276,9 +276,9 @@ void radix_sort(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_
   if (n >= (int64_t)0xffffffffLL) throw MmError{MM_EINVAL, "radix sort: more than 2^32-1 keys"};
   int64_t ntiles = ceil_div(n, RS_TILE);
   int64_t nh = ntiles * RS_RADIX;
-  // scratch: hist (uint32 nh) + scan partials
+  // scratch: hist (uint32 nh) + the scan's tile states and tile counter
   size_t hist_bytes = sizeof(uint32_t) * (size_t)nh;
-  size_t part_bytes = sizeof(uint32_t) * (size_t)ceil_div(nh, SCAN_TILE);
+  size_t part_bytes = sizeof(unsigned long long) * (size_t)(ceil_div(nh, SCAN_TILE) + 2);
   char *base = static_cast<char *>(ws.need(hist_bytes + part_bytes + 256, st));
   uint32_t *hist = reinterpret_cast<uint32_t *>(base);
   Scratch part_ws;  // view into the same allocation for the scan partials

@@ -580,3 +580,89 @@ def test_large_restricted_candidates(large):
                                       cand_dst=dd)
     assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
     assert kept_tuples(top) == oracle_kept(ref)[:5000]
+
+
+# ---------------------------------------------------------------- many classes
+
+def test_forty_thousand_classes_restricted():
+    """40,000 classes and 50,000 methods with restricted lists (classes used +
+    16 others): adjacency rows of 1,252 words, compressed records over 40
+    summary words per row; every record equals the oracle's."""
+    s = synth.generate(40000, 50000, 25000, max_class=400, seed=41, lambda_acc=4, lambda_call=6, p_loc=0.75)
+    rp, dst = synth.candidates(s, 16, seed=41)
+    g, cm, mm_ = gpu_load(s, device=True)
+    o = oracle.Oracle(s)
+    check_metrics(s, o, cm, mm_)
+    assert g.info()["n_class_edges"] == len(o.multigraph()[1])
+    rpd, dd = torch.from_numpy(rp).cuda(), torch.from_numpy(dst).cuda()
+    for mask, mi in ((7, 1), (3, 2), (4, 1)):
+        ref = o.evaluate(mask=mask, min_improved=mi, cand_rowptr=rp, cand_dst=dst, method=1, records=True)
+        rec, dig = gpu_records(g, mask, mi, rpd, dd)
+        assert same_records(rec, ref.records) and dig == ref.digest, mask
+        top, nk, nm = mmref.suggest_moves(g, k=100000, mask=mask, min_improved=mi, cand_rowptr=rpd, cand_dst=dd)
+        assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+        assert kept_tuples(top) == oracle_kept(ref)
+
+
+def test_many_empty_classes_full_cross_product():
+    """33,000 classes of which 32,000 are empty: the full cross product over
+    rows of 1,032 words (moves into empty classes everywhere)."""
+    base = synth.generate(1000, 3000, 1500, max_class=40, seed=43, lambda_acc=3, lambda_call=4, p_loc=0.7)
+    # the same system with its classes spread over 33,000 ids (32,000 empty classes)
+    s = synth.System(33000, base.n_methods, base.n_attrs, base.method_class * 33, base.attr_class * 33,
+                     base.acc_rowptr, base.acc_idx, base.call_rowptr, base.call_idx, name="spread")
+    g, cm, mm_ = gpu_load(s, device=True)
+    o = oracle.Oracle(s)
+    check_metrics(s, o, cm, mm_)
+    ref = o.evaluate(mask=7, min_improved=1, method=1)
+    assert gpu_digest(g, 7, 1) == ref.digest
+    top, nk, nm = mmref.suggest_moves(g, k=100000, mask=7, min_improved=1)
+    assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+    assert kept_tuples(top) == oracle_kept(ref)
+    # after the metrics are computed again, restricted lists over the same system agree too
+    mmref.compute_metrics(g, None, None)
+    rp, dst = synth.candidates(s, 8, seed=43)
+    ref = o.evaluate(mask=7, min_improved=1, cand_rowptr=rp, cand_dst=dst, method=1, records=True)
+    rec, dig = gpu_records(g, 7, 1, rp, dst)
+    assert same_records(rec, ref.records) and dig == ref.digest
+
+
+def test_repeated_destinations_in_lists(tiny):
+    """A list may name a destination twice: both positions get the same record."""
+    s, o, _ = tiny
+    g, _, _ = gpu_load(s)
+    rng = np.random.default_rng(3)
+    rows = []
+    for m in range(s.n_methods):
+        C = int(s.method_class[m])
+        r = [int(D) for D in rng.choice(s.n_classes, size=12) if D != C]
+        rows.append(r + r[: len(r) // 2])  # repeats, unsorted
+    rp = np.zeros(s.n_methods + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    dst = np.asarray([D for r in rows for D in r], dtype=np.int32)
+    for mask, mi in ((7, 1), (3, 2)):
+        ref = o.evaluate(mask=mask, min_improved=mi, cand_rowptr=rp, cand_dst=dst, method=1, records=True)
+        rec, dig = gpu_records(g, mask, mi, rp, dst)
+        assert same_records(rec, ref.records) and dig == ref.digest
+        top, nk, nm = mmref.suggest_moves(g, k=100000, mask=mask, min_improved=mi, cand_rowptr=rp, cand_dst=dst)
+        assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+        assert kept_tuples(top) == oracle_kept(ref)
+
+
+def test_more_than_65535_classes():
+    """70,000 classes (35 ids per class of a 2,000-class system): class ids
+    past 16 bits in every key, row and record offset of the restricted path."""
+    base = synth.generate(2000, 10000, 5000, max_class=60, seed=47, lambda_acc=3, lambda_call=4, p_loc=0.7)
+    s = synth.System(70000, base.n_methods, base.n_attrs, base.method_class * 35, base.attr_class * 35,
+                     base.acc_rowptr, base.acc_idx, base.call_rowptr, base.call_idx, name="spread-wide")
+    g, cm, mm_ = gpu_load(s, device=True)
+    o = oracle.Oracle(s)
+    check_metrics(s, o, cm, mm_)
+    rp, dst = synth.candidates(s, 8, seed=47)
+    for mask, mi in ((7, 1), (3, 2)):
+        ref = o.evaluate(mask=mask, min_improved=mi, cand_rowptr=rp, cand_dst=dst, method=1, records=True)
+        rec, dig = gpu_records(g, mask, mi, rp, dst)
+        assert same_records(rec, ref.records) and dig == ref.digest
+        top, nk, nm = mmref.suggest_moves(g, k=100000, mask=mask, min_improved=mi, cand_rowptr=rp, cand_dst=dst)
+        assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+        assert kept_tuples(top) == oracle_kept(ref)
