@@ -1,33 +1,47 @@
 #!/usr/bin/env python3
 """Benchmark of the Move Method metric engine on one B300 (or N replicas).
 
-One step = the whole hot path over one system, through the C ABI:
-  load_system (CSR already in HBM) -> compute_metrics (bitsets, LCOM pair
-  counts, coupling multigraph + CBO, fan-in/out, per-method move data) ->
-  evaluate_moves (full cross product, dense 16-byte records in HBM) ->
-  suggest_moves (fused evaluation + Pareto filter + top-k, read back) -> free.
+The bench line is the large workload: a synthetic system of 50,000 classes,
+500,000 methods and 250,000 attributes (seed 2) whose candidate moves are
+restricted, per method, to the classes it calls into or whose attributes it
+reads plus 64 uniformly drawn others (33,448,382 candidates), evaluated with
+all three metrics selected (LCOM_CK, LCOM_HS and CBO: source, destination and
+the classes of the method's callers).  One step, through the C ABI with the
+inputs resident in HBM:
 
-Workload: the medium synthetic system (5,000 classes, 60,000 methods,
-30,000 attributes, seed 1), 299,940,000 candidate moves per step.
-metric = candidate moves evaluated per second (every record bit-exact with the
-CPU oracle; checked by tests/test_gpu_parity.py and, here, by a digest check
-before timing).
+  load_system -> compute_metrics -> evaluate_moves (16-byte records in HBM)
+  -> suggest_moves (top-100 read back) -> free.
+
+metric = candidate moves evaluated per second; every record is checked against
+the CPU oracle through a digest of all records and the suggestion list.
+
+Measured in the same run and reported as nested keys:
+  medium   the 5,000-class, 60,000-method system (seed 1), full cross product
+           (299,940,000 candidates), dense evaluation and its roofline;
+  batched  256 systems (classes log-uniform in 100..20,000, seeds 100..355):
+           one CUDA graph per run against 256 sequential calls;
+  serving  64 resident systems (seeds 100..163) answering 100,000 edit
+           requests: capacity, p50/p99 latency at half of it, every 1,000th
+           state checked against the oracle.
+The oracle checks run in a separate low-priority process started before the
+first GPU call, beside the GPU sections; the CPU baseline is timed after them.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 (torchrun): every rank runs an independent replica of the workload on its
-own GPU (weak scaling, no data-path collective); value = all candidates / max
-rank time.
+N > 1 (torchrun): every rank runs an independent replica of the bench line
+on its own GPU (weak scaling, no data-path collective); value = all ranks'
+candidates / the slowest rank's time.  Only rank 0 runs the nested sections.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
-import tempfile
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -38,18 +52,19 @@ if ROOT not in sys.path:
 
 METRIC = "candidate moves evaluated/sec (bit-exact vs oracle)"
 UNIT = "candidates/s"
-WORKLOAD = "medium synthetic system: 5,000 classes, 60,000 methods, 30,000 attributes, seed 1; full cross product"
+WORKLOAD = ("large synthetic system: 50,000 classes, 500,000 methods, 250,000 attributes, seed 2; restricted "
+            "candidates (classes each method uses + 64 uniform others); criteria LCOM_CK|LCOM_HS|CBO, 2 improved")
+MEDIUM_WORKLOAD = "medium synthetic system: 5,000 classes, 60,000 methods, 30,000 attributes, seed 1; full cross product"
+MASK_ALL = 7          # LCOM_CK | LCOM_HS | CBO
+MASK_LCOM = 3         # LCOM_CK | LCOM_HS
+MIN_IMPROVED = 2
 TOPK = 100
 L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant
-# kernel on the same workload, from a one-pass ncu capture (set to None when the
-# kernel changes, until it is captured again)
+# kernel of each workload, from a one-pass ncu capture (None once the kernel
+# changes, until it is captured again)
+EVAL_CSR_TRAFFIC_MASK7 = None        # large restricted, eval_csr_grouped<records, kept>, all three metrics
 EVAL_DENSE_TRAFFIC = 4771699968      # medium, eval_dense<records, kept>
-EVAL_CSR_TRAFFIC = 897806848         # large restricted, eval_csr_grouped<records, kept>
-# busy fraction of the integer ALU pipe in one launch of the restricted
-# evaluation (ncu sectioned capture, sm__pipe_alu_cycles_active); that kernel is
-# bound by integer instruction throughput, not by DRAM (None once it changes)
-EVAL_CSR_ALU_BUSY = 0.768
 
 
 def _env_int(k, d):
@@ -86,10 +101,9 @@ class ClockSampler:
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
             time.sleep(1.0)  # let nvidia-smi finish starting before any timing
         except Exception:
@@ -125,7 +139,7 @@ class ClockSampler:
         inside = rows
         if self.window:
             t0, t1 = self.window
-            inside = [r for r in rows if t0 - 0.05 <= r["t"] <= t1 + 0.05] or rows
+            inside = [r for r in rows if t0 - 0.1 <= r["t"] <= t1 + 0.1] or rows
         rows = inside
         load = [r for r in rows if r["power"] > 200.0] or rows
         reasons = sorted({name for r in rows for name, key in (("hw_slowdown", "hw"),
@@ -138,130 +152,7 @@ class ClockSampler:
                 "power_w_median": statistics.median(r["power"] for r in rows)}
 
 
-def run_ours(args, rank, world, local_rank):
-    import torch
-    from paper_1308_4011_b300 import mmref, synth
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    params = dict(synth.MEDIUM)
-    if args.case == "small":  # profiling case: medium class count, degrees and locality, 12,000 methods
-        params.update(n_methods=12000, n_attrs=6000)
-    params["seed"] = replica_seed(params["seed"], rank)  # independent replica per rank (weak scaling)
-    system = synth.generate(**params, name="medium")
-    c, M = system.n_classes, system.n_methods
-    n_cand = M * (c - 1)
-    mask, min_imp = mmref.DEFAULT_MASK, mmref.DEFAULT_MIN_IMPROVED
-    stream = torch.cuda.current_stream(dev)
-
-    # inputs resident in HBM
-    dev_arrs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
-                (system.method_class, system.attr_class, system.acc_rowptr, system.acc_idx,
-                 system.call_rowptr, system.call_idx)]
-    records = torch.empty(n_cand * 16, dtype=torch.uint8, device=dev)
-    cls_out = torch.empty(c * 64, dtype=torch.uint8, device=dev)
-    meth_out = torch.empty(M * 16, dtype=torch.uint8, device=dev)
-    topk = np.zeros(TOPK, dtype=mmref.MOVE_DTYPE)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-
-    def step(timing=None):
-        s = mmref.load_system(c, *dev_arrs, stream=stream)
-        mmref.compute_metrics(s, cls_out, meth_out)
-        if timing is not None:
-            timing[0].record(stream)
-        mmref.evaluate_moves(s, mask, min_imp, records=records)
-        if timing is not None:
-            timing[1].record(stream)
-        out = mmref.suggest_moves(s, TOPK, mask, min_imp, out=topk)
-        s.free()
-        return out
-
-    # correctness gate before timing: digest of every record vs the oracle on rank 0
-    verified = None
-    if rank == 0 and not args.no_verify:
-        import oracle
-        s = mmref.load_system(c, *dev_arrs, stream=stream)
-        mmref.compute_metrics(s, None, None)
-        dig = torch.zeros(1, dtype=torch.int64, device=dev)
-        mmref.evaluate_moves(s, mask, min_imp, digest=dig)
-        top_g, nk_g, _ = mmref.suggest_moves(s, TOPK, mask, min_imp)
-        s.free()
-        o = oracle.Oracle(system)
-        ref = o.evaluate(mask=mask, min_improved=min_imp, method=1)
-        ok_dig = int(dig.cpu().numpy().view(np.uint64)[0]) == ref.digest
-        ok_top = nk_g == ref.n_kept and [tuple(int(x[f]) for f in ("m", "d")) for x in top_g] == \
-            [(int(k["m"]), int(k["d"])) for k in ref.kept[:TOPK]]
-        verified = bool(ok_dig and ok_top)
-        if not verified:
-            print(json.dumps({"error": "GPU result differs from the oracle", "digest_ok": ok_dig,
-                              "topk_ok": ok_top}), file=sys.stderr)
-            sys.exit(3)
-        o.close()
-
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-    step_ms, eval_ms = [], []
-    with ClockSampler(local_rank) as clk:
-        for _ in range(args.warmup):
-            step()
-        torch.cuda.synchronize(dev)
-        launches0 = mmref.launch_count()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        t_wall0 = time.perf_counter()
-        t_epoch0 = time.time()
-        for _ in range(args.steps):
-            flush.fill_(1)  # L2 flush between steps, outside the timed events
-            ev[2].record(stream)
-            step(timing=ev)
-            ev[3].record(stream)
-            torch.cuda.synchronize(dev)
-            step_ms.append(ev[2].elapsed_time(ev[3]))
-            eval_ms.append(ev[0].elapsed_time(ev[1]))
-        torch.cuda.synchronize(dev)
-        if dist:
-            dist.barrier()
-        t_wall = time.perf_counter() - t_wall0
-        clk.mark(t_epoch0, time.time())
-        time.sleep(0.25)  # one more sample after the region
-    launches = mmref.launch_count() - launches0
-    total_ms = max_over_ranks(sum(step_ms), dist, dev)
-    ms_per_step = total_ms / args.steps
-    value = job_value(n_cand, world, args.steps, total_ms)
-
-    # end to end through the C ABI with host buffers (pinned), copies included
-    e2e = run_e2e(args, system, dev, stream, mask, min_imp)
-
-    peak, peak_kind = _peaks()
-    eval_s = statistics.median(eval_ms) / 1e3
-    alg_bytes = 16 * n_cand
-    achieved = alg_bytes / eval_s / 1e9
-    # DRAM bytes of one medium eval_dense launch (ncu one-pass capture)
-    traffic = EVAL_DENSE_TRAFFIC if args.case == "medium" else None
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": traffic,
-            "kernel": "eval_dense<records>", "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-            "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(eval_s * 1e3, 4)}
-    cpu = cpu_baseline(system, mask, min_imp) if (rank == 0 and not args.no_cpu_baseline) else None
-    workload = WORKLOAD if args.case == "medium" else "PROFILING CASE (not the bench workload): " + WORKLOAD
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32/int64", "data": "synthetic (seeded generator; no datasets)",
-            "config": {"workload": workload, "n_classes": c, "n_methods": M, "n_attrs": system.n_attrs,
-                       "candidates_per_step": n_cand, "criteria": {"metric_mask": mask, "min_improved": min_imp},
-                       "topk": TOPK, "parallelism": f"replicas x{world}",
-                       "l2": "512 MB L2 flush between steps (outside events); each step also writes 4.8 GB"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "gpu_launches_per_step": launches / max(args.steps, 1), "clocks": clk.summary(),
-            "eval_ms_median": statistics.median(eval_ms),
-            "step_ms_min_median_max": [round(min(step_ms), 3), round(statistics.median(step_ms), 3),
-                                       round(max(step_ms), 3)],
-            "wall_s_timed_region": round(t_wall, 3), "verified_vs_oracle": verified}
-    return line
-
+# ---------------------------------------------------------------- helpers shared with the tests
 
 def max_over_ranks(total_ms, dist, device):
     """The job's time: the slowest rank's (all-reduce MAX); the local time without
@@ -285,27 +176,254 @@ def replica_seed(seed, rank):
     return seed + 1000 * rank
 
 
-def run_e2e(args, system, dev, stream, mask, min_imp):
+def metrics_digest(cls_rows, meth_rows) -> str:
+    """SHA-256 of class metrics (n, a, P, Q, S, cbo) and method metrics
+    (fan_in, fan_out, own, q), as int64 columns, for comparing the GPU's
+    arrays with the oracle's in another process."""
+    h = hashlib.sha256()
+    for col in cls_rows + meth_rows:
+        h.update(np.ascontiguousarray(np.asarray(col, dtype=np.int64)).tobytes())
+    return h.hexdigest()
+
+
+def full_rows_lists(system, methods):
+    """Candidate lists holding, for each method in `methods`, every class other
+    than its own (the full cross product restricted to those rows); other
+    methods get no candidates."""
+    c, M = system.n_classes, system.n_methods
+    lens = np.zeros(M, dtype=np.int64)
+    lens[methods] = c - 1
+    rowptr = np.zeros(M + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum(lens)
+    allc = np.arange(c, dtype=np.int32)
+    dst = np.concatenate([np.delete(allc, system.method_class[m]) for m in methods]) if len(methods) else \
+        np.zeros(0, dtype=np.int32)
+    return rowptr, dst
+
+
+# ---------------------------------------------------------------- oracle jobs (run in the verifier process)
+
+def _verifier_init():
+    try:
+        os.nice(19)  # the GPU sections' host threads come first
+    except OSError:
+        pass
+
+
+def job_oracle_lists(params, n_extra, cand_seed, mask, mi, topk):
+    """O1 over a generated system with restricted candidate lists."""
+    import oracle
+    from paper_1308_4011_b300 import synth
+    s = synth.generate(**params)
+    rp, dst = synth.candidates(s, n_extra, seed=cand_seed)
+    o = oracle.Oracle(s)
+    r = o.evaluate(mask=mask, min_improved=mi, cand_rowptr=rp, cand_dst=dst, method=1)
+    o.close()
+    return {"digest": r.digest, "n_kept": r.n_kept, "n_mk": r.n_methods_with_kept,
+            "top": [(int(k["m"]), int(k["d"])) for k in r.kept[:topk]]}
+
+
+def job_oracle_full(params, mask, mi, topk):
+    """O1 over a generated system's full cross product."""
+    import oracle
+    from paper_1308_4011_b300 import synth
+    s = synth.generate(**params)
+    o = oracle.Oracle(s)
+    r = o.evaluate(mask=mask, min_improved=mi, method=1)
+    o.close()
+    return {"digest": r.digest, "n_kept": r.n_kept, "n_mk": r.n_methods_with_kept,
+            "top": [(int(k["m"]), int(k["d"])) for k in r.kept[:topk]]}
+
+
+def job_oracle_batched(params, rows, mask, mi):
+    """One batched system: the digest of its metric arrays and of the
+    evaluation of a seeded sample of full candidate rows."""
+    import oracle
+    from paper_1308_4011_b300 import synth
+    s = synth.generate(**params)
+    o = oracle.Oracle(s)
+    cm, mm_ = o.class_metrics(), o.method_metrics()
+    md = metrics_digest([cm[f] for f in ("n", "a", "P", "Q", "S", "cbo")],
+                        [mm_[f] for f in ("fan_in", "fan_out", "own", "q")])
+    rp, dst = full_rows_lists(s, rows)
+    r = o.evaluate(mask=mask, min_improved=mi, cand_rowptr=rp, cand_dst=dst, method=1)
+    o.close()
+    return {"metrics": md, "rows_digest": r.digest, "n_cand": r.n_cand}
+
+
+def job_oracle_snapshot(c, arrays, mask, mi, topk):
+    """One served state: kept-move count and the first suggestions of the
+    full cross product, and the digest of its metric arrays."""
+    import oracle
+    from paper_1308_4011_b300 import synth
+    s = synth.System(c, len(arrays[0]), len(arrays[1]), *arrays)
+    o = oracle.Oracle(s)
+    cm, mm_ = o.class_metrics(), o.method_metrics()
+    md = metrics_digest([cm[f] for f in ("n", "a", "P", "Q", "S", "cbo")],
+                        [mm_[f] for f in ("fan_in", "fan_out", "own", "q")])
+    r = o.evaluate(mask=mask, min_improved=mi, method=1)
+    o.close()
+    return {"n_kept": r.n_kept, "n_mk": r.n_methods_with_kept, "metrics": md,
+            "top": [(int(k["m"]), int(k["d"])) for k in r.kept[:topk]], "n_cand": r.n_cand}
+
+
+class Verifier:
+    """One spawned worker process (the oracle threads over all host cores),
+    started before the first GPU call."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        self.pool = mp.get_context("spawn").Pool(1, initializer=_verifier_init)
+
+    def submit(self, fn, *args):
+        return self.pool.apply_async(fn, args)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+# ---------------------------------------------------------------- the bench line: large restricted
+
+def large_inputs(seed):
+    from paper_1308_4011_b300 import synth
+    params = dict(synth.LARGE)
+    params["seed"] = seed
+    system = synth.generate(**params, name="large")
+    rp, dst = synth.candidates(system, synth.LARGE_EXTRA_CANDIDATES, seed=seed)
+    return params, system, rp, dst
+
+
+def run_large(args, rank, world, local_rank, verifier, dist):
+    import torch
+    from paper_1308_4011_b300 import mmref, synth
+
+    dev = torch.device("cuda", local_rank)
+    seed = replica_seed(synth.LARGE["seed"], rank)
+    params, system, rp, dst = large_inputs(seed)
+    c, M, n_cand = system.n_classes, system.n_methods, len(dst)
+    stream = torch.cuda.current_stream(dev)
+    dev_arrs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
+                (system.method_class, system.attr_class, system.acc_rowptr, system.acc_idx,
+                 system.call_rowptr, system.call_idx)]
+    rpd, dd = torch.from_numpy(rp).to(dev), torch.from_numpy(dst).to(dev)
+    records = torch.empty(n_cand * 16, dtype=torch.uint8, device=dev)
+    topk = np.zeros(TOPK, dtype=mmref.MOVE_DTYPE)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def step(mask, kernel_ms=None):
+        s = mmref.load_system(c, *dev_arrs, stream=stream)
+        mmref.compute_metrics(s, None, None)
+        mmref.evaluate_moves(s, mask, MIN_IMPROVED, rpd, dd, records=records)
+        out = mmref.suggest_moves(s, TOPK, mask, MIN_IMPROVED, rpd, dd, out=topk)
+        if kernel_ms is not None:
+            kernel_ms.append(s.last_eval_ms())  # the suggestion reused the evaluation's kept moves
+        s.free()
+        return out
+
+    # correctness: digest of every record and the suggestions, against the oracle (rank 0)
+    checks = {}
+    if rank == 0 and verifier is not None:
+        jobs = {mask: verifier.submit(job_oracle_lists, params, synth.LARGE_EXTRA_CANDIDATES, seed, mask,
+                                      MIN_IMPROVED, TOPK) for mask in (MASK_ALL, MASK_LCOM)}
+        for mask in (MASK_ALL, MASK_LCOM):
+            s = mmref.load_system(c, *dev_arrs, stream=stream)
+            mmref.compute_metrics(s, None, None)
+            dig = torch.zeros(1, dtype=torch.int64, device=dev)
+            mmref.evaluate_moves(s, mask, MIN_IMPROVED, rpd, dd, digest=dig)
+            top_g, nk_g, nm_g = mmref.suggest_moves(s, TOPK, mask, MIN_IMPROVED, rpd, dd)
+            s.free()
+            checks[mask] = (jobs[mask], int(dig.cpu().numpy().view(np.uint64)[0]), nk_g, nm_g,
+                            [(int(x["m"]), int(x["d"])) for x in top_g])
+
+    def timed(mask, steps):
+        step_ms, kern_ms = [], []
+        for _ in range(args.warmup):
+            step(mask)
+        torch.cuda.synchronize(dev)
+        launches0 = mmref.launch_count()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.time()
+        for _ in range(steps):
+            flush.fill_(1)  # L2 flush between steps, outside the timed events
+            ev[0].record(stream)
+            step(mask, kern_ms)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            step_ms.append(ev[0].elapsed_time(ev[1]))
+        if dist:
+            dist.barrier()
+        return step_ms, kern_ms, mmref.launch_count() - launches0, (t0, time.time())
+
+    with ClockSampler(local_rank) as clk:
+        step_ms, kern_ms, launches, window = timed(MASK_ALL, args.steps)
+        clk.mark(*window)
+        time.sleep(0.3)
+    step3_ms, kern3_ms, _, _ = timed(MASK_LCOM, args.steps)
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    ms_per_step = total_ms / args.steps
+    value = job_value(n_cand, world, args.steps, total_ms)
+
+    peak, peak_kind = _peaks()
+    alg_bytes = 20 * n_cand  # 4-byte destination read + 16-byte record written per candidate
+    kern_s = statistics.median(kern_ms) / 1e3
+    achieved = alg_bytes / kern_s / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": EVAL_CSR_TRAFFIC_MASK7,
+            "kernel": "eval_csr_grouped<records, kept>",
+            "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(kern_s * 1e3, 4),
+            "kernel_ms_source": "CUDA events recorded by the library around the launch on its stream "
+                                "(mm_last_eval_ms), median over the timed steps"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32/int64", "data": "synthetic (seeded generator; no datasets)",
+            "config": {"workload": WORKLOAD, "n_classes": c, "n_methods": M, "n_attrs": system.n_attrs,
+                       "candidates_per_step": n_cand,
+                       "criteria": {"metric_mask": MASK_ALL, "min_improved": MIN_IMPROVED}, "topk": TOPK,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "512 MB L2 flush between steps (outside the events)"},
+            "roofline": roof, "gpu_launches": launches, "gpu_launches_per_step": launches / max(args.steps, 1),
+            "clocks": clk.summary(),
+            "step_ms_min_median_max": [round(min(step_ms), 3), round(statistics.median(step_ms), 3),
+                                       round(max(step_ms), 3)],
+            "lcom_only": {"criteria": {"metric_mask": MASK_LCOM, "min_improved": MIN_IMPROVED},
+                          "value": job_value(n_cand, 1, args.steps, sum(step3_ms)),
+                          "ms_per_step": sum(step3_ms) / args.steps,
+                          "kernel_ms": round(statistics.median(kern3_ms), 4),
+                          "roofline_frac": round(alg_bytes / (statistics.median(kern3_ms) / 1e3) / 1e9 / peak, 4)}}
+    if rank == 0:
+        line["e2e"] = run_large_e2e(args, system, rp, dst, dev, stream)
+    return line, checks, system
+
+
+def run_large_e2e(args, system, rp, dst, dev, stream):
+    """The same step through the C ABI from pinned host buffers: CSR and
+    candidate lists copied in (twice: evaluation and suggestion), class and
+    method metrics and the top-100 copied out; records stay in HBM."""
     import torch
     from paper_1308_4011_b300 import mmref
 
-    c, M = system.n_classes, system.n_methods
-    n_cand = M * (c - 1)
+    c, M, n_cand = system.n_classes, system.n_methods, len(dst)
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
               (system.method_class, system.attr_class, system.acc_rowptr, system.acc_idx,
                system.call_rowptr, system.call_idx)]
+    rp_h, dst_h = torch.from_numpy(rp).pin_memory(), torch.from_numpy(dst).pin_memory()
     cls_h = torch.empty(c * 64, dtype=torch.uint8).pin_memory()
     meth_h = torch.empty(M * 16, dtype=torch.uint8).pin_memory()
     top_h = torch.empty(TOPK * 24, dtype=torch.uint8).pin_memory()
     records = torch.empty(n_cand * 16, dtype=torch.uint8, device=dev)
-    h2d = sum(int(p.numel() * p.element_size()) for p in pinned)
+    h2d = sum(int(p.numel() * p.element_size()) for p in pinned) + 2 * (rp.nbytes + dst.nbytes)
     d2h = c * 64 + M * 16 + TOPK * 24 + 16
 
     def step():
         s = mmref.load_system(c, *pinned, stream=stream)
         mmref.compute_metrics(s, cls_h, meth_h)
-        mmref.evaluate_moves(s, mask, min_imp, records=records)
-        mmref.suggest_moves(s, TOPK, mask, min_imp, out=top_h)
+        mmref.evaluate_moves(s, MASK_ALL, MIN_IMPROVED, rp_h.numpy(), dst_h.numpy(), records=records)
+        mmref.suggest_moves(s, TOPK, MASK_ALL, MIN_IMPROVED, rp_h.numpy(), dst_h.numpy(), out=top_h)
         s.free()
 
     for _ in range(max(1, args.warmup)):
@@ -316,182 +434,117 @@ def run_e2e(args, system, dev, stream, mask, min_imp):
         step()
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
-    del records
     return {"value": n_cand * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": dt * 1e3 / args.steps,
-            "note": "host CSR (pinned) -> device, metrics + top-k back to host; records stay in HBM"}
+            "note": "host CSR + candidate lists (pinned) -> device, metrics + top-100 back to host; records in HBM"}
 
 
-def cpu_baseline(system, mask, min_imp, rows=None):
-    """The CPU oracle as it stands (metrics by definition + incremental move
-    evaluation, all host threads) on a bounded sample of the same workload."""
+def cpu_baseline_large(system, rp, dst, mask):
+    """The CPU oracle as it stands (metrics by definition + incremental
+    evaluation of every candidate, all host threads) on the whole bench
+    workload."""
     import oracle
-    M = system.n_methods
-    rows = rows or M
     t0 = time.perf_counter()
     o = oracle.Oracle(system)
-    r = o.evaluate(mask=mask, min_improved=min_imp, method=1, rows=(0, rows))
+    r = o.evaluate(mask=mask, min_improved=MIN_IMPROVED, cand_rowptr=rp, cand_dst=dst, method=1)
     dt = time.perf_counter() - t0
     o.close()
     return {"value": r.n_cand / dt, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
-            "sample": f"metrics of all classes + candidate rows 0..{rows} of {M} ({r.n_cand} candidates)",
+            "sample": f"the whole workload: metrics of all classes + all {r.n_cand} candidates",
             "seconds": round(dt, 3)}
 
 
-def run_reference(args, rank, world):
-    """The oracle timed as the reference arm on the host cores (rank 0 only)."""
-    if rank != 0:
-        return None
-    from paper_1308_4011_b300 import synth
-    system = synth.generate(**synth.MEDIUM, name="medium")
-    from paper_1308_4011_b300 import mmref  # noqa: F401  (criteria constants only)
-    mask, min_imp = 3, 2
-    rows = 15000  # a quarter of the methods per step keeps (W + K) steps within a few minutes
-    for _ in range(args.warmup):
-        cpu_baseline(system, mask, min_imp, rows)
-    vals, secs = [], []
-    for _ in range(args.steps):
-        r = cpu_baseline(system, mask, min_imp, rows)
-        vals.append(r["value"])
-        secs.append(r["seconds"])
-    value = len(vals) / sum(1.0 / v for v in vals)
-    n_cand_step = rows * (system.n_classes - 1)
-    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64",
-            "data": "synthetic (seeded generator; no datasets)",
-            "config": {"workload": WORKLOAD, "n_classes": system.n_classes, "n_methods": system.n_methods,
-                       "candidates_per_step": n_cand_step, "criteria": {"metric_mask": mask, "min_improved": min_imp},
-                       "parallelism": "host threads"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": __import__("oracle").default_threads(),
-                             "kind": "oracle",
-                             "sample": f"metrics of all classes + candidate rows 0..{rows} of {system.n_methods}"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+# ---------------------------------------------------------------- nested: medium dense
 
-
-def run_large(args, rank, world, local_rank):
-    """The large restricted workload: 50,000 classes, 500,000 methods, 250,000
-    attributes (seed 2); each method's candidates are the classes it calls into
-    or whose attributes it accesses, plus 64 uniform others.  One step = load
-    (CSR in HBM) -> compute_metrics -> evaluate_moves over the candidate lists
-    (16-byte records) -> suggest_moves over the same lists -> free."""
+def run_medium(args, local_rank, verifier):
     import torch
     from paper_1308_4011_b300 import mmref, synth
 
-    torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    params = dict(synth.LARGE)
-    params["seed"] = replica_seed(params["seed"], rank)  # independent replica per rank
-    system = synth.generate(**params, name="large")
-    rp, dst = synth.candidates(system, synth.LARGE_EXTRA_CANDIDATES, seed=params["seed"])
-    c, M, n_cand = system.n_classes, system.n_methods, len(dst)
-    mask, min_imp = mmref.DEFAULT_MASK, mmref.DEFAULT_MIN_IMPROVED
+    params = dict(synth.MEDIUM)
+    system = synth.generate(**params, name="medium")
+    c, M = system.n_classes, system.n_methods
+    n_cand = M * (c - 1)
     stream = torch.cuda.current_stream(dev)
+    job = verifier.submit(job_oracle_full, params, MASK_LCOM, MIN_IMPROVED, TOPK) if verifier else None
     dev_arrs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
                 (system.method_class, system.attr_class, system.acc_rowptr, system.acc_idx,
                  system.call_rowptr, system.call_idx)]
-    rpd, dd = torch.from_numpy(rp).to(dev), torch.from_numpy(dst).to(dev)
     records = torch.empty(n_cand * 16, dtype=torch.uint8, device=dev)
     topk = np.zeros(TOPK, dtype=mmref.MOVE_DTYPE)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
-    def step(timing=None):
+    def step(kern=None):
         s = mmref.load_system(c, *dev_arrs, stream=stream)
         mmref.compute_metrics(s, None, None)
-        if timing is not None:
-            timing[0].record(stream)
-        mmref.evaluate_moves(s, mask, min_imp, rpd, dd, records=records)
-        if timing is not None:
-            timing[1].record(stream)
-        out = mmref.suggest_moves(s, TOPK, mask, min_imp, rpd, dd, out=topk)
+        mmref.evaluate_moves(s, MASK_LCOM, MIN_IMPROVED, records=records)
+        out = mmref.suggest_moves(s, TOPK, MASK_LCOM, MIN_IMPROVED, out=topk)
+        if kern is not None:
+            kern.append(s.last_eval_ms())
         s.free()
         return out
 
-    verified, oracle_s = None, None
-    if rank == 0 and not args.no_verify:
-        import oracle
-        s = mmref.load_system(c, *dev_arrs, stream=stream)
-        mmref.compute_metrics(s, None, None)
-        dig = torch.zeros(1, dtype=torch.int64, device=dev)
-        mmref.evaluate_moves(s, mask, min_imp, rpd, dd, digest=dig)
-        top_g, nk_g, _ = mmref.suggest_moves(s, TOPK, mask, min_imp, rpd, dd)
-        s.free()
-        t = time.perf_counter()
-        o = oracle.Oracle(system)
-        ref = o.evaluate(mask=mask, min_improved=min_imp, cand_rowptr=rp, cand_dst=dst, method=1)
-        oracle_s = time.perf_counter() - t
-        ok_dig = int(dig.cpu().numpy().view(np.uint64)[0]) == ref.digest
-        ok_top = nk_g == ref.n_kept and [tuple(int(x[f]) for f in ("m", "d")) for x in top_g] == \
-            [(int(k["m"]), int(k["d"])) for k in ref.kept[:TOPK]]
-        verified = bool(ok_dig and ok_top)
-        o.close()
-        if not verified:
-            print(json.dumps({"error": "GPU result differs from the oracle", "digest_ok": ok_dig,
-                              "topk_ok": ok_top}), file=sys.stderr)
-            sys.exit(3)
-
-    step_ms, eval_ms = [], []
-    with ClockSampler(local_rank) as clk:
-        for _ in range(args.warmup):
-            step()
+    s = mmref.load_system(c, *dev_arrs, stream=stream)
+    mmref.compute_metrics(s, None, None)
+    dig = torch.zeros(1, dtype=torch.int64, device=dev)
+    mmref.evaluate_moves(s, MASK_LCOM, MIN_IMPROVED, digest=dig)
+    top_g, nk_g, nm_g = mmref.suggest_moves(s, TOPK, MASK_LCOM, MIN_IMPROVED)
+    s.free()
+    check = (job, int(dig.cpu().numpy().view(np.uint64)[0]), nk_g, nm_g, [(int(x["m"]), int(x["d"])) for x in top_g])
+    for _ in range(args.warmup):
+        step()
+    step_ms, kern = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        ev[0].record(stream)
+        step(kern)
+        ev[1].record(stream)
         torch.cuda.synchronize(dev)
-        launches0 = mmref.launch_count()
-        t_epoch0 = time.time()
-        for _ in range(args.steps):
-            flush.fill_(1)
-            ev[2].record(stream)
-            step(timing=ev)
-            ev[3].record(stream)
-            torch.cuda.synchronize(dev)
-            step_ms.append(ev[2].elapsed_time(ev[3]))
-            eval_ms.append(ev[0].elapsed_time(ev[1]))
-        clk.mark(t_epoch0, time.time())
-        time.sleep(0.25)
-    launches = mmref.launch_count() - launches0
-    ms_per_step = sum(step_ms) / args.steps
+        step_ms.append(ev[0].elapsed_time(ev[1]))
     peak, peak_kind = _peaks()
-    eval_s = statistics.median(eval_ms) / 1e3
-    alg_bytes = 20 * n_cand  # 4-byte destination read + 16-byte record written per candidate
-    achieved = alg_bytes / eval_s / 1e9
-    return {"metric": METRIC, "workload": "large", "value": n_cand * world / (ms_per_step / 1e3), "unit": UNIT,
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "config": {"workload": "large synthetic system: 50,000 classes, 500,000 methods, 250,000 attributes, "
-                                   "seed 2; restricted candidates (classes used + 64 uniform others)",
-                       "candidates_per_step": n_cand, "criteria": {"metric_mask": mask, "min_improved": min_imp},
-                       "topk": TOPK, "l2": "512 MB L2 flush between steps (outside events)"},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": EVAL_CSR_TRAFFIC,
-                         "kernel": "eval_csr_grouped<records>",
-                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                         "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": round(eval_s * 1e3, 4),
-                         "alu_pipe_busy_ncu": EVAL_CSR_ALU_BUSY},
-            "eval_value": n_cand / eval_s, "eval_ms_median": statistics.median(eval_ms),
-            "metrics_and_rest_ms": ms_per_step - statistics.median(eval_ms),
-            "gpu_launches_per_step": launches / max(args.steps, 1), "clocks": clk.summary(),
-            "verified_vs_oracle": verified, "oracle_s": oracle_s}
+    alg = 16 * n_cand
+    k = statistics.median(kern) / 1e3
+    out = {"workload": MEDIUM_WORKLOAD, "criteria": {"metric_mask": MASK_LCOM, "min_improved": MIN_IMPROVED},
+           "candidates_per_step": n_cand, "value": n_cand * args.steps / (sum(step_ms) / 1e3), "unit": UNIT,
+           "ms_per_step": sum(step_ms) / args.steps,
+           "roofline": {"bound": "hbm", "kernel": "eval_dense<records, kept>", "achieved": round(alg / k / 1e9, 1),
+                        "peak": peak, "unit": "GB/s", "frac": round(alg / k / 1e9 / peak, 4),
+                        "traffic": EVAL_DENSE_TRAFFIC, "algorithmic_bytes_per_launch": alg,
+                        "kernel_ms": round(k * 1e3, 4), "peak_kind": peak_kind}}
+    del records
+    return out, check
 
 
-def run_batched(args, rank, world, local_rank):
-    """256 independent systems (class counts log-uniform in 100..20,000, 12
-    methods and 6 attributes per class, seeds 100..355): one persistent launch
-    under a CUDA graph vs the same systems one after another."""
+# ---------------------------------------------------------------- nested: batched
+
+BATCH_ROWS = 1000
+
+
+def run_batched(args, local_rank, verifier):
+    """256 independent systems: one persistent launch under a CUDA graph
+    (metrics of every system + evaluation of every full cross product + kept
+    moves + per-system sorts) against the same systems one after another."""
     import torch
     from paper_1308_4011_b300 import mmref, synth
 
-    torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     n_sys = args.batch_systems
     params = [synth.batched_params(100 + i) for i in range(n_sys)]
-    loaded, shapes = [], []
+    loaded, systems = [], []
     t0 = time.perf_counter()
     for p in params:
         s = synth.generate(**p)
+        systems.append(s)
         loaded.append(mmref.load_synth(s, device=True))
-        shapes.append((s.n_classes, s.n_methods))
     gen_s = time.perf_counter() - t0
-    n_cand = sum(m * (c - 1) for c, m in shapes)
-    mask, mi = mmref.DEFAULT_MASK, mmref.DEFAULT_MIN_IMPROVED
+    n_cand = sum(s.n_methods * (s.n_classes - 1) for s in systems)
+    rng = np.random.default_rng(2024)
+    sample_rows = [np.sort(rng.choice(s.n_methods, size=min(BATCH_ROWS, s.n_methods), replace=False))
+                   for s in systems]
+    jobs = [verifier.submit(job_oracle_batched, p, rows, MASK_LCOM, MIN_IMPROVED) if verifier else None
+            for p, rows in zip(params, sample_rows)]
+    mask, mi = MASK_LCOM, MIN_IMPROVED
     stream = torch.cuda.current_stream(dev)
     # kept-move capacity per system: the largest count of a first pass
     b0 = mmref.Batch(loaded, mask=mask, min_improved=mi, kept_cap=1, stream=stream)
@@ -500,20 +553,30 @@ def run_batched(args, rank, world, local_rank):
     cap = int(max(int(counts0.max()), 1) * 1.1) + 64
     b = mmref.Batch(loaded, mask=mask, min_improved=mi, kept_cap=cap, stream=stream)
     tile = b.autotune()
-    # verification: per-system digests of the batch equal the single-system launches
     dig, nk = b.run(digest=True)
+    # what the batch graph computed, per system: metric arrays and a sample of full rows
+    gpu_metrics, gpu_rows = [], []
+    for g, s, rows in zip(loaded, systems, sample_rows):
+        cm, mm_ = mmref.export_metrics(g)
+        gpu_metrics.append(metrics_digest([cm[f] for f in ("n_methods", "n_attrs", "P", "Q", "S", "cbo")],
+                                          [mm_[f] for f in ("fan_in", "fan_out", "own", "q")]))
+        rp, dst = full_rows_lists(s, rows)
+        d1 = np.zeros(1, dtype=np.uint64)
+        mmref.evaluate_moves(g, mask, mi, rp, dst, digest=d1)
+        gpu_rows.append(int(d1[0]))
+    # the batch's full digests against single-system evaluations of the same systems
     d1 = torch.zeros(n_sys, dtype=torch.int64, device=dev)
     for i, g in enumerate(loaded):
         mmref.evaluate_moves(g, mask, mi, digest=d1[i:i + 1])
     torch.cuda.synchronize(dev)
-    ok = bool(np.array_equal(d1.cpu().numpy().view(np.uint64), dig))
+    ok_single = bool(np.array_equal(d1.cpu().numpy().view(np.uint64), dig))
     k = TOPK
 
-    def batched():  # metrics + evaluation + kept moves + sorted suggestions, then top-k of every system
+    def batched():
         _, counts = b.run(digest=False)
         return [b.suggestions(i, k)[0] for i in range(n_sys)], counts
 
-    def sequential():  # the same systems one after another through the single-system calls
+    def sequential():
         out = []
         for g in loaded:
             mmref.compute_metrics(g, None, None)
@@ -524,11 +587,11 @@ def run_batched(args, rank, world, local_rank):
     tops_s = sequential()
     ok_top = all(np.array_equal(x, y) for x, y in zip(tops_b, tops_s))
     times_b, times_s = [], []
-    reps = max(3, args.steps // 10)
+    reps = 3
     for _ in range(reps):
         torch.cuda.synchronize(dev)
         t = time.perf_counter(); sequential(); torch.cuda.synchronize(dev); times_s.append(time.perf_counter() - t)
-    batched()  # warm after the sequential calls (sorting large kept lists may grow scratch)
+    batched()
     for _ in range(reps):
         torch.cuda.synchronize(dev)
         t = time.perf_counter(); batched(); torch.cuda.synchronize(dev); times_b.append(time.perf_counter() - t)
@@ -536,23 +599,25 @@ def run_batched(args, rank, world, local_rank):
     b.free()
     for g in loaded:
         g.free()
-    return {"metric": METRIC, "value": n_cand / tb, "unit": UNIT, "workload": "batched",
-            "config": {"workload": f"{n_sys} systems, classes log-uniform 100..20,000, 12 methods/class, "
-                                   f"seeds 100..{99 + n_sys}, full cross products (digest + kept moves)",
-                       "candidates": n_cand, "tile_methods": tile, "kept_cap_per_system": cap},
-            "batched_s": tb, "sequential_s": ts, "speedup_vs_sequential": ts / tb,
-            "sequential_value": n_cand / ts, "digests_equal_single_system": ok, "topk_equal_sequential": ok_top,
-            "generate_and_load_s": gen_s, "n_kept_total": int(counts.sum()),
-            "note": "timed: metrics + full evaluation + kept moves + top-100 per system, no digest"}
+    out = {"workload": f"{n_sys} systems, classes log-uniform 100..20,000, 12 methods and 6 attributes per class, "
+                       f"seeds 100..{99 + n_sys}; full cross products (kept moves + top-100 of each)",
+           "criteria": {"metric_mask": mask, "min_improved": mi}, "candidates": n_cand,
+           "batched_s": tb, "sequential_s": ts, "speedup_vs_sequential": ts / tb,
+           "value": n_cand / tb, "sequential_value": n_cand / ts, "unit": UNIT, "tile_methods": tile,
+           "kept_cap_per_system": cap, "n_kept_total": int(counts.sum()),
+           "batch_digests_equal_single_system": ok_single, "topk_equal_sequential": ok_top,
+           "generate_and_load_s": round(gen_s, 2)}
+    return out, (jobs, gpu_metrics, gpu_rows)
 
 
-def run_serving(args, rank, world, local_rank):
-    """64 resident systems (drawn as the batched mix, seeds 100..163) answering
-    a Poisson stream of edit requests (each kind 1/5, seed 7): a saturating
-    burst for capacity, then an open-loop run at half of it for latency, every
-    1,000th state checked; a 2 GB-budget stress run where admission binds."""
+# ---------------------------------------------------------------- nested: serving
+
+def run_serving(args, local_rank, verifier):
+    """64 resident systems answering a Poisson stream of edit requests (each
+    kind 1/5, seed 7): a saturating burst for capacity, then an open-loop run
+    at half of it for latency with every 1,000th state kept for the oracle;
+    a 2 GB budget run in which admission binds."""
     import torch
-    import oracle
     from paper_1308_4011_b300 import mmref, synth
 
     torch.cuda.set_device(local_rank)
@@ -568,93 +633,170 @@ def run_serving(args, rank, world, local_rank):
         resp, top = sv.run(req, snap)
         return sv, resp, top
 
-    # warm-up pass: every system admitted once (loads are not part of the request latency below)
     warm = mmref.make_requests(ms, 64, rate_per_s=0.0, seed=99)
     warm["system"] = np.arange(64)
     warm["m"] = warm["m"] % np.asarray(ms)[warm["system"]]
-    # capacity: everything arrives at once
     burst = mmref.make_requests(ms, n_req, rate_per_s=0.0, seed=7)
     sv, resp_b, _ = serve(100 << 30, np.concatenate([warm, burst]), args.slots)
     stats_b = sv.stats()
     sv.free()
     rb = resp_b[64:]
     cap_rps = n_req / (rb["done_s"].max() - rb["arrival_s"].min())
-    # latency: open loop at half the capacity, with snapshots
     rate = 0.5 * cap_rps
     req = mmref.make_requests(ms, n_req, rate_per_s=rate, seed=7)
-    warm2 = warm.copy()
-    req["arrival_s"] += 2.0  # let the warm-up admissions finish first
-    sv, resp, top = serve(100 << 30, np.concatenate([warm2, req]), args.slots, snap=1000)
+    req["arrival_s"] += 2.0  # the warm-up admissions finish first
+    sv, resp, top = serve(100 << 30, np.concatenate([warm, req]), args.slots, snap=1000)
     r = resp[64:]
     lat = (r["done_s"] - r["arrival_s"]) * 1e3
     stats = sv.stats()
     ok_req = bool((resp["status"] == 0).all())
-    # every 1,000th state: the oracle where it finishes in seconds, else a fresh full GPU recompute
-    n_oracle = n_gpu = bad = 0
-    for k in range(stats["n_snapshots"]):
-        i, si, c, arrs = sv.snapshot(k)
+    snaps = []
+    for kk in range(stats["n_snapshots"]):
+        i, si, c, arrs = sv.snapshot(kk)
         if i < 64:
             continue
-        s = synth.System(c, len(arrs[0]), len(arrs[1]), *arrs)
-        got_n = int(resp["n_kept"][i])
-        got_top = [(int(x["m"]), int(x["d"])) for x in top[i]]
-        if s.n_methods * (c - 1) <= 2e8:
-            ref = oracle.Oracle(s).evaluate(mask=mmref.DEFAULT_MASK, min_improved=mmref.DEFAULT_MIN_IMPROVED)
-            exp_n, exp_top = ref.n_kept, [(int(x["m"]), int(x["d"])) for x in ref.kept[:topk]]
-            n_oracle += 1
-        else:
-            g = mmref.load_synth(s, device=True)
-            mmref.compute_metrics(g, None, None)
-            t2, exp_n, _ = mmref.suggest_moves(g, topk)
-            exp_top = [(int(x["m"]), int(x["d"])) for x in t2]
-            g.free()
-            n_gpu += 1
-        if exp_n != got_n or exp_top != got_top[: len(exp_top)]:
-            bad += 1
+        # the served answer, and the metric arrays of the same state computed afresh on the GPU
+        g = mmref.load_system(c, *arrs)
+        cm, mm_ = mmref.compute_metrics(g, "host", "host")
+        g.free()
+        gm = metrics_digest([cm[f] for f in ("n_methods", "n_attrs", "P", "Q", "S", "cbo")],
+                            [mm_[f] for f in ("fan_in", "fan_out", "own", "q")])
+        got = (int(resp["n_kept"][i]), int(resp["n_methods_with_kept"][i]),
+               [(int(x["m"]), int(x["d"])) for x in top[i][: min(topk, int(resp["n_kept"][i]))]], gm)
+        job = verifier.submit(job_oracle_snapshot, c, arrs, MASK_LCOM, MIN_IMPROVED, topk) if verifier else None
+        snaps.append((i, si, got, job))
     sv.free()
-    # stress: a 2 GB budget makes admission evict and reload
-    n_stress = min(n_req, 20000)
+    n_stress = min(n_req, args.stress_requests)
     req_s = mmref.make_requests(ms, n_stress, rate_per_s=0.0, seed=8)
     sv, resp_s, _ = serve(2 << 30, req_s, args.slots)
     stats_s = sv.stats()
     sv.free()
     rs = resp_s
-    return {"metric": "edit requests/s and latency (bit-exact vs oracle)", "workload": "serving",
-            "value": cap_rps, "unit": "requests/s",
-            "config": {"workload": "64 resident systems (classes log-uniform 100..20,000, seeds 100..163), "
-                                   f"{n_req} Poisson edit requests (each kind 1/5, seed 7), 100 GB budget",
-                       "slots": args.slots, "topk": topk},
-            "capacity_requests_per_s": cap_rps, "offered_rate_per_s": rate,
-            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
-            "latency_ms_mean": float(lat.mean()), "achieved_rps_open_loop": n_req / (r["done_s"].max() - r["arrival_s"].min()),
-            "all_requests_ok": ok_req, "snapshots_checked_oracle": n_oracle, "snapshots_checked_gpu_recompute": n_gpu,
-            "snapshots_mismatched": bad, "stats": stats, "burst_stats": stats_b,
-            "stress_2GB": {"requests": n_stress, "ok": int((rs["status"] == 0).sum()),
-                           "refused_budget": int((rs["status"] == 7).sum()), "evictions": stats_s["evictions"],
-                           "loads": stats_s["loads"],
-                           "requests_per_s": n_stress / (rs["done_s"].max() - rs["arrival_s"].min()),
-                           "latency_ms_p50": float(np.percentile((rs["done_s"] - rs["arrival_s"]) * 1e3, 50)),
-                           "latency_ms_p99": float(np.percentile((rs["done_s"] - rs["arrival_s"]) * 1e3, 99))}}
+    out = {"metric": "edit requests/s and latency (bit-exact vs oracle)", "unit": "requests/s",
+           "workload": "64 resident systems (classes log-uniform 100..20,000, seeds 100..163), "
+                       f"{n_req} Poisson edit requests (each kind 1/5, seed 7), 100 GB budget, "
+                       f"{args.slots} worker slots, top-{topk} per request (LCOM_CK|LCOM_HS, 2 improved)",
+           "capacity_requests_per_s": cap_rps, "offered_rate_per_s": rate,
+           "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+           "latency_ms_mean": float(lat.mean()),
+           "achieved_rps_open_loop": n_req / (r["done_s"].max() - r["arrival_s"].min()),
+           "all_requests_ok": ok_req, "stats": stats, "burst_stats": stats_b,
+           "stress_2GB": {"requests": n_stress, "ok": int((rs["status"] == 0).sum()),
+                          "refused_budget": int((rs["status"] == 7).sum()), "evictions": stats_s["evictions"],
+                          "loads": stats_s["loads"],
+                          "requests_per_s": n_stress / (rs["done_s"].max() - rs["arrival_s"].min()),
+                          "latency_ms_p50": float(np.percentile((rs["done_s"] - rs["arrival_s"]) * 1e3, 50)),
+                          "latency_ms_p99": float(np.percentile((rs["done_s"] - rs["arrival_s"]) * 1e3, 99))}}
+    return out, snaps
 
+
+# ---------------------------------------------------------------- the reference arm
+
+def run_reference(args, rank, world):
+    """The CPU oracle timed as the reference arm on the host cores, on the bench
+    line's workload and criteria (rank 0 only): each step builds the oracle
+    (metrics of every class by definition) and evaluates a quarter of the
+    methods' candidate lists."""
+    if rank != 0:
+        return None
+    import oracle
+    params, system, rp, dst = large_inputs(2)
+    M = system.n_methods
+    quarter = M // 4
+
+    def one():
+        t0 = time.perf_counter()
+        o = oracle.Oracle(system)
+        r = o.evaluate(mask=MASK_ALL, min_improved=MIN_IMPROVED, cand_rowptr=rp, cand_dst=dst, method=1,
+                       rows=(0, quarter))
+        dt = time.perf_counter() - t0
+        o.close()
+        return r.n_cand, dt
+
+    for _ in range(args.warmup):
+        one()
+    cands, secs = 0, 0.0
+    for _ in range(args.steps):
+        n, dt = one()
+        cands += n
+        secs += dt
+    value = cands / secs
+    sample = f"per step: metrics of all classes + candidate rows 0..{quarter} of {M} ({cands // args.steps} candidates)"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64",
+            "data": "synthetic (seeded generator; no datasets)",
+            "config": {"workload": WORKLOAD, "n_classes": system.n_classes, "n_methods": M,
+                       "candidates_per_step": cands // args.steps,
+                       "criteria": {"metric_mask": MASK_ALL, "min_improved": MIN_IMPROVED},
+                       "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------- checks
+
+def _check_result(kind, check):
+    job, dig, nk, nm, top = check
+    if job is None:
+        return None
+    ref = job.get()
+    ok = dig == ref["digest"] and nk == ref["n_kept"] and nm == ref["n_mk"] and top == ref["top"][: len(top)]
+    return {"ok": bool(ok), "n_kept": nk}
+
+
+def collect_checks(large_checks, medium_check, batched_check, serving_snaps):
+    out = {"large": {}, "medium": None, "batched": None, "serving": None}
+    for mask, chk in large_checks.items():
+        out["large"][f"mask{mask}"] = _check_result("large", chk)
+    if medium_check is not None:
+        out["medium"] = _check_result("medium", medium_check)
+    if batched_check is not None:
+        jobs, gpu_metrics, gpu_rows = batched_check
+        if jobs and jobs[0] is not None:
+            bad_m = bad_r = cands = 0
+            for job, gm, gr in zip(jobs, gpu_metrics, gpu_rows):
+                ref = job.get()
+                bad_m += ref["metrics"] != gm
+                bad_r += ref["rows_digest"] != gr
+                cands += ref["n_cand"]
+            out["batched"] = {"ok": bad_m == 0 and bad_r == 0, "systems": len(jobs), "metrics_mismatched": bad_m,
+                              "sampled_rows_mismatched": bad_r, "sampled_candidates": cands,
+                              "rows_per_system": BATCH_ROWS}
+    if serving_snaps:
+        bad = cands = n = 0
+        for i, si, got, job in serving_snaps:
+            if job is None:
+                continue
+            ref = job.get()
+            n += 1
+            cands += ref["n_cand"]
+            exp = (ref["n_kept"], ref["n_mk"], ref["top"][: len(got[2])], ref["metrics"])
+            bad += got != exp
+        out["serving"] = {"ok": bad == 0, "snapshots_checked": n, "mismatched": bad,
+                          "candidates_recomputed": cands,
+                          "compared": "n_kept, methods with kept, top-10 of the served answer; metric arrays of "
+                                      "the state (GPU recompute) -- each against O1 on the exported state"}
+    return out
+
+
+# ---------------------------------------------------------------- main
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["medium", "large", "batched", "serving"], default="medium",
-                    help="large = the 50,000-class system with restricted candidate lists; batched = the "
-                         "256-system batch vs sequential launches; serving = the edit-request loop (each "
-                         "prints its own JSON line)")
+    ap.add_argument("--sections", default="medium,batched,serving",
+                    help="nested sections measured beside the bench line (comma list; '' for none)")
     ap.add_argument("--requests", type=int, default=100000)
+    ap.add_argument("--stress-requests", type=int, default=5000)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--batch-systems", type=int, default=256)
-    ap.add_argument("--case", choices=["medium", "small"], default="medium",
-                    help="small = profiling case (5,000 classes, 12,000 methods, 0.96 GB of records); "
-                         "not a bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -664,27 +806,43 @@ def main():
         if line is not None:
             print(json.dumps(line), flush=True)
         return
-    if args.workload == "large":
-        line = run_large(args, rank, world, local_rank)
-        if rank == 0:
-            print(json.dumps(line), flush=True)
-        return
-    if args.workload == "batched":
-        print(json.dumps(run_batched(args, rank, world, local_rank)), flush=True)
-        return
-    if args.workload == "serving":
-        print(json.dumps(run_serving(args, rank, world, local_rank)), flush=True)
-        return
+    # the oracle's process starts before the first GPU call
+    verifier = Verifier() if (rank == 0 and not args.no_verify) else None
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
     if world > 1:
-        import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    line = run_ours(args, rank, world, local_rank)
+    # the nested sections run on one GPU only (rank 0 of a single-rank job)
+    sections = [x for x in args.sections.split(",") if x] if world == 1 else []
+    t_start = time.perf_counter()
+    nested, serving_snaps, batched_check, medium_check = {}, None, None, None
+    if "serving" in sections:
+        nested["serving"], serving_snaps = run_serving(args, local_rank, verifier)
+    if "batched" in sections:
+        nested["batched"], batched_check = run_batched(args, local_rank, verifier)
+    if "medium" in sections:
+        nested["medium"], medium_check = run_medium(args, local_rank, verifier)
+    line, large_checks, system = run_large(args, rank, world, local_rank, verifier, dist)
     if rank == 0:
+        checks = collect_checks(large_checks, medium_check, batched_check, serving_snaps) if verifier else None
+        if verifier:
+            verifier.close()
+        line["verified_vs_oracle"] = checks
+        if not args.no_cpu_baseline:
+            _, _, rp, dst = large_inputs(replica_seed(2, rank))
+            line["cpu_baseline"] = cpu_baseline_large(system, rp, dst, MASK_ALL)
+        line.update(nested)
+        line["bench_wall_s"] = round(time.perf_counter() - t_start, 1)
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
+        results = []
+        if checks is not None:
+            results = [r for r in checks["large"].values()] + [checks[k] for k in ("medium", "batched", "serving")]
+        if any(r is not None and not r["ok"] for r in results):
+            print(json.dumps({"error": "GPU results differ from the oracle", "checks": checks}), file=sys.stderr)
+            sys.exit(3)
+    if dist:
         dist.destroy_process_group()
 
 

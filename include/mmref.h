@@ -220,6 +220,16 @@ MMREF_API mm_status mm_compute_metrics(mm_system *sys, mm_class_metrics *out_c, 
                              int32_t out_kind);
 
 /*
+ * Copy the system's current class and method metrics (Sec. II.A, II.B) --
+ * as the last mm_compute_metrics, batch run (mm_batch_run) or edit
+ * (mm_apply_edit) left them -- without computing them again.  Same layouts
+ * and out_kind rules as mm_compute_metrics.  MM_EINVAL if no metrics have
+ * been computed.  Synchronises the stream when out_kind is MM_PTR_HOST.
+ */
+MMREF_API mm_status mm_export_metrics(mm_system *sys, mm_class_metrics *out_c, mm_method_metrics *out_m,
+                                      int32_t out_kind);
+
+/*
  * Evaluate candidate moves incrementally (Sec. III.A, Sec. IV.C) against the
  * metrics of the last mm_compute_metrics.  cands == NULL means the full cross
  * product.  records[n_cand] (nullable) receives one mm_move_eval per
@@ -418,6 +428,17 @@ MMREF_API mm_status mm_server_snapshot(mm_server *sv, int64_t k, mm_snapshot_inf
                                        int32_t *attr_class, int64_t *acc_rowptr, int32_t *acc_idx,
                                        int64_t *call_rowptr, int32_t *call_idx);
 MMREF_API void mm_server_free(mm_server *sv);
+
+/*
+ * GPU time in milliseconds of the evaluation kernel launched by the last
+ * mm_evaluate_moves or mm_suggest_moves on this handle that evaluated
+ * (events recorded on the system's stream immediately before and after that
+ * launch; waits for it to finish).  The paper has no counterpart: it lets a
+ * caller relate the evaluation kernel alone -- without the validation of
+ * candidate lists or the suggestion sort around it -- to its memory roofline.
+ * MM_EINVAL if no evaluation kernel has run on the handle.
+ */
+MMREF_API mm_status mm_last_eval_ms(mm_system *sys, float *ms);
 
 /* Sizes and device memory of a loaded system (host struct). */
 MMREF_API mm_status mm_system_info_get(mm_system *sys, mm_system_info *info);

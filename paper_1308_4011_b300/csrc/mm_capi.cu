@@ -53,7 +53,8 @@ void release_system(mm_system *s) {
                      &s->union_ws, &s->side_eval[0], &s->side_eval[1], &s->side_eval[2], &s->side_sort[0],
                      &s->side_sort[1], &s->side_sort[2], &s->side_union[0], &s->side_union[1], &s->side_union[2]})
     w->release(s->stream);
-  for (cudaEvent_t e : {s->fork_ev, s->join_ev[0], s->join_ev[1], s->join_ev[2], s->mid_ev[0], s->mid_ev[1]})
+  for (cudaEvent_t e : {s->fork_ev, s->join_ev[0], s->join_ev[1], s->join_ev[2], s->mid_ev[0], s->mid_ev[1],
+                        s->eval_ev[0], s->eval_ev[1]})
     if (e) cudaEventDestroy(e);
   delete s;
 }
@@ -262,6 +263,8 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     MM_CUDA_TRY(cudaEventCreateWithFlags(&s->join_ev[2], cudaEventDisableTiming));
     MM_CUDA_TRY(cudaEventCreateWithFlags(&s->mid_ev[0], cudaEventDisableTiming));
     MM_CUDA_TRY(cudaEventCreateWithFlags(&s->mid_ev[1], cudaEventDisableTiming));
+    MM_CUDA_TRY(cudaEventCreate(&s->eval_ev[0]));
+    MM_CUDA_TRY(cudaEventCreate(&s->eval_ev[1]));
     s->c = desc->n_classes;
     s->M = desc->n_methods;
     s->A = desc->n_attrs;
@@ -347,6 +350,17 @@ mm_status mm_compute_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_me
   });
 }
 
+mm_status mm_export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *out_m, int32_t out_kind) {
+  return guarded([&] {
+    if (!s) throw MmError{MM_EINVAL, "export_metrics: NULL system"};
+    if (!s->metrics_ready) throw MmError{MM_EINVAL, "export_metrics: no metrics computed yet"};
+    if ((out_c || out_m) && out_kind != MM_PTR_HOST && out_kind != MM_PTR_DEVICE)
+      throw MmError{MM_EINVAL, "export_metrics: bad out_kind"};
+    use_device(s);
+    export_metrics(s, out_c, out_m, out_kind);
+  });
+}
+
 mm_status mm_evaluate_moves(mm_system *s, const mm_criteria *crit, const mm_candidates *cands,
                             mm_move_eval *records, uint64_t *digest, int32_t out_kind) {
   return guarded([&] {
@@ -364,6 +378,16 @@ mm_status mm_suggest_moves(mm_system *s, const mm_criteria *crit, const mm_candi
     if (!s->metrics_ready) throw MmError{MM_EINVAL, "suggest_moves: call mm_compute_metrics first"};
     use_device(s);
     suggest_moves(s, *crit, cands, k, out_topk, out_kind, n_kept, n_methods_with_kept);
+  });
+}
+
+mm_status mm_last_eval_ms(mm_system *s, float *ms) {
+  return guarded([&] {
+    if (!s || !ms) throw MmError{MM_EINVAL, "last_eval_ms: NULL argument"};
+    if (!s->eval_timed) throw MmError{MM_EINVAL, "last_eval_ms: no evaluation kernel has run on this handle"};
+    use_device(s);
+    MM_CUDA_TRY(cudaEventSynchronize(s->eval_ev[1]));
+    MM_CUDA_TRY(cudaEventElapsedTime(ms, s->eval_ev[0], s->eval_ev[1]));
   });
 }
 

@@ -176,6 +176,8 @@ struct mm_system {
   Scratch side_eval[3], side_sort[3], side_union[3];
   cudaEvent_t fork_ev = nullptr, join_ev[3] = {nullptr, nullptr, nullptr}, mid_ev[2] = {nullptr, nullptr};
   cudaStream_t side_pending[3] = {nullptr, nullptr, nullptr};  // stream a branch was issued on
+  cudaEvent_t eval_ev[2] = {nullptr, nullptr};  // around the last evaluation kernel (timing)
+  bool eval_timed = false;
   bool kept_valid = false;   // kept_ws holds the kept moves of the last evaluation for:
   uint32_t kept_mask = 0;    //   this metric mask
   int32_t kept_min = 0;      //   and this min_improved

@@ -1770,6 +1770,15 @@ void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_
 
 void dispatch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_t *rowptr, const int32_t *dst) {
   const int sel = (oc.records ? 4 : 0) | (oc.digest ? 2 : 0) | (oc.kept_count ? 1 : 0);
+  struct Timed {  // events around the launch, for mm_last_eval_ms
+    mm_system *s;
+    explicit Timed(mm_system *sys) : s(sys) {
+      if (s->eval_ev[0]) MM_CUDA_TRY(cudaEventRecord(s->eval_ev[0], s->stream));
+    }
+    ~Timed() {
+      if (s->eval_ev[1] && cudaEventRecord(s->eval_ev[1], s->stream) == cudaSuccess) s->eval_timed = true;
+    }
+  } timed(s);
   switch (sel) {
     case 0: launch_eval<false, false, false>(s, cx, oc, rowptr, dst); break;
     case 1: launch_eval<false, false, true>(s, cx, oc, rowptr, dst); break;

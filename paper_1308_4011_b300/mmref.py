@@ -34,7 +34,8 @@ EXPORTED = ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluat
             "mm_launch_count", "mm_suggest_moves_noalloc", "mm_batch_create", "mm_batch_set_tile",
             "mm_batch_autotune", "mm_batch_run", "mm_batch_suggestions", "mm_batch_free", "mm_apply_edit",
             "mm_export_system", "mm_server_create", "mm_server_add_system", "mm_server_run", "mm_server_stats_get",
-            "mm_server_snapshot", "mm_server_free", "mm_selftest_bounded_wait")
+            "mm_server_snapshot", "mm_server_free", "mm_selftest_bounded_wait", "mm_last_eval_ms",
+            "mm_export_metrics")
 
 CLASS_METRICS_DTYPE = np.dtype([("n_methods", "<i4"), ("n_attrs", "<i4"), ("P", "<i8"), ("Q", "<i8"),
                                 ("S", "<i8"), ("lcom_ck", "<i8"), ("hs_num", "<i8"), ("hs_den", "<i8"),
@@ -75,10 +76,14 @@ _vp = ctypes.c_void_p
 _lib.mm_load_system.argtypes = [ctypes.POINTER(_Desc), _vp, ctypes.POINTER(_vp)]
 _lib.mm_set_stream.argtypes = [_vp, _vp]
 _lib.mm_compute_metrics.argtypes = [_vp, _vp, _vp, ctypes.c_int32]
+_lib.mm_export_metrics.argtypes = [_vp, _vp, _vp, ctypes.c_int32]
+_lib.mm_export_metrics.restype = ctypes.c_int
 _lib.mm_evaluate_moves.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.POINTER(_Cands), _vp, _vp, ctypes.c_int32]
 _lib.mm_suggest_moves.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.POINTER(_Cands), ctypes.c_int32, _vp,
                                   ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
 _lib.mm_system_info_get.argtypes = [_vp, ctypes.POINTER(_Info)]
+_lib.mm_last_eval_ms.argtypes = [_vp, ctypes.POINTER(ctypes.c_float)]
+_lib.mm_last_eval_ms.restype = ctypes.c_int
 _lib.mm_suggest_moves_noalloc.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.POINTER(_Cands), ctypes.c_int32, _vp,
                                           ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
 _lib.mm_suggest_moves_noalloc.restype = ctypes.c_int
@@ -193,6 +198,12 @@ class System:
         _check(_lib.mm_system_info_get(self._h, ctypes.byref(inf)))
         return {f: getattr(inf, f) for f, _ in _Info._fields_}
 
+    def last_eval_ms(self) -> float:
+        """mm_last_eval_ms: GPU time of the last evaluation kernel on this handle."""
+        v = ctypes.c_float()
+        _check(_lib.mm_last_eval_ms(self._h, ctypes.byref(v)))
+        return float(v.value)
+
     def set_stream(self, stream):
         _check(_lib.mm_set_stream(self._h, _stream_handle(stream)))
 
@@ -246,6 +257,19 @@ def compute_metrics(sys: System, out_class=None, out_method=None):
     if any(_kind(o) != kind for o in outs):
         raise ValueError("compute_metrics: outputs must be both host or both device")
     _check(_lib.mm_compute_metrics(sys.handle, _ptr(out_class), _ptr(out_method), kind))
+    return out_class, out_method
+
+
+def export_metrics(sys: System, out_class="host", out_method="host"):
+    """mm_export_metrics: the system's current metrics, not recomputed (same
+    buffers as compute_metrics)."""
+    if isinstance(out_class, str):
+        out_class = np.zeros(sys.n_classes, dtype=CLASS_METRICS_DTYPE)
+    if isinstance(out_method, str):
+        out_method = np.zeros(sys.n_methods, dtype=METHOD_METRICS_DTYPE)
+    outs = [o for o in (out_class, out_method) if o is not None]
+    kind = _kind(outs[0]) if outs else PTR_HOST
+    _check(_lib.mm_export_metrics(sys.handle, _ptr(out_class), _ptr(out_method), kind))
     return out_class, out_method
 
 
