@@ -95,6 +95,13 @@ def _load():
         _lib.or_free_kept.argtypes = [ctypes.c_void_p]
         _lib.or_record_hash.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
         _lib.or_record_hash.restype = ctypes.c_uint64
+        _lib.or_similarity.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4
+        _lib.or_similarity.restype = ctypes.c_int64
+        _lib.or_similarity_row.argtypes = [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 3
+        _lib.or_similarity_row.restype = ctypes.c_int64
+        _lib.or_r1_threshold.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.c_void_p]
+        _lib.or_r1_threshold.restype = ctypes.c_double
     return _lib
 
 
@@ -194,6 +201,39 @@ class Oracle:
             raise ValueError("oracle: invalid candidate (out of range or equal to the source class)")
         return EvalResult(int(res.digest), int(res.n_cand), kept, int(res.n_methods_with_kept), rec)
 
+    def similarity(self, threads: int | None = None):
+        """Jaccard similarity (Sec. II.A) of every method pair x < y sharing a
+        property (called method or accessed attribute): arrays x, y, i =
+        |P(x) & P(y)|, u = |P(x) | P(y)|, in (x, y) order."""
+        lib = _load()
+        n = lib.or_similarity(self._h, threads or self.threads, None, None, None, None)
+        out = [np.zeros(max(n, 1), dtype=np.int32) for _ in range(4)]
+        lib.or_similarity(self._h, threads or self.threads, *[a.ctypes.data for a in out])
+        return tuple(a[:n] for a in out)
+
+    def similarity_row(self, x: int):
+        """Every y != x sharing a property with x: arrays y, i, u (ascending y)."""
+        lib = _load()
+        n = lib.or_similarity_row(self._h, int(x), None, None, None)
+        out = [np.zeros(max(n, 1), dtype=np.int32) for _ in range(3)]
+        lib.or_similarity_row(self._h, int(x), *[a.ctypes.data for a in out])
+        return tuple(a[:n] for a in out)
+
+    def r1(self, mask: int = 3, min_improved: int = 2):
+        """Rule R1 (Sec. III.A): every pair of methods in different classes
+        whose similarity exceeds the system average (footnote of Sec. III.A)
+        proposes moving either method to the other's class; the candidates
+        are evaluated (O1) and the kept ones, with LCOM of both the origin and
+        the destination improved under the default criteria, returned.
+        Returns (EvalResult, average, candidate rowptr, candidate dst,
+        number of similarity values, number of high pairs)."""
+        x, y, i, u = self.similarity()
+        umax = int(u.max()) if len(u) else 0
+        avg, thr = r1_threshold(i, u, umax)
+        rowptr, dst, n_high = r1_candidates(self.sys, x, y, i, u, thr)
+        res = self.evaluate(mask=mask, min_improved=min_improved, cand_rowptr=rowptr, cand_dst=dst, method=1)
+        return res, avg, rowptr, dst, len(x), n_high
+
     def evaluate_one(self, m: int, d: int, mask: int = 7, min_improved: int = 2, method: int = 1):
         rec = np.zeros(1, dtype=RECORD_DTYPE)
         a, b = ctypes.c_int64(), ctypes.c_int64()
@@ -203,6 +243,33 @@ class Oracle:
         if rc:
             raise ValueError("oracle: invalid candidate")
         return rec[0], int(a.value), int(b.value)
+
+
+def r1_threshold(i, u, umax: int):
+    """The R1 threshold over the similarity values (i, u): their average in
+    double precision (sum over u ascending of sum(i)/u, over the count) and,
+    per u = 0..umax, the smallest i with i/u above it (u + 1 if none)."""
+    i = np.ascontiguousarray(i, dtype=np.int32)
+    u = np.ascontiguousarray(u, dtype=np.int32)
+    thr = np.zeros(umax + 1, dtype=np.int32)
+    avg = _load().or_r1_threshold(i.ctypes.data if len(i) else None, u.ctypes.data if len(u) else None, len(i),
+                                  umax, thr.ctypes.data)
+    return float(avg), thr
+
+
+def r1_candidates(system, x, y, i, u, thr):
+    """Moves proposed by the high pairs (i >= thr[u]) whose methods are in
+    different classes: x to the class of y and y to the class of x, each
+    (method, class) once, as candidate lists (rows sorted by class)."""
+    mc = system.method_class
+    high = (i >= thr[u]) & (mc[x] != mc[y])
+    m = np.concatenate([x[high], y[high]]).astype(np.int64)
+    d = np.concatenate([mc[y[high]], mc[x[high]]]).astype(np.int64)
+    key = np.unique(m * system.n_classes + d)
+    m, d = key // system.n_classes, (key % system.n_classes).astype(np.int32)
+    rowptr = np.zeros(system.n_methods + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum(np.bincount(m, minlength=system.n_methods))
+    return rowptr, d, int(high.sum())
 
 
 def record_hash(m: int, d: int, rec) -> int:

@@ -803,3 +803,148 @@ int or_evaluate_one(const or_sys *s, const or_criteria *cr, int32_t m, int32_t D
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Jaccard similarity of method pairs (Sec. II.A) and rule R1 (Sec.      */
+/* III.A, first rule and its footnote)                                    */
+/*                                                                        */
+/* The properties of a method are the methods it calls and the          */
+/* attributes it accesses (two id spaces, never equal to each other).    */
+/* sim(x, y) = |P(x) and P(y)| / |P(x) or P(y)|, kept as the exact pair   */
+/* (i, u).  Only pairs with i > 0 are values (a pair sharing nothing has  */
+/* similarity 0 and is not stored, Sec. IV.C).                            */
+
+/* number of common elements of two strictly increasing rows (sorted merge) */
+static int64_t common_sorted(const int32_t *a, int64_t na, const int32_t *b, int64_t nb) {
+  int64_t i = 0, j = 0, k = 0;
+  while (i < na && j < nb) {
+    if (a[i] < b[j]) ++i;
+    else if (b[j] < a[i]) ++j;
+    else { ++k; ++i; ++j; }
+  }
+  return k;
+}
+
+/* i and u of the pair (x, y) by the definition */
+static void sim_pair(const or_input *in, int32_t x, int32_t y, int64_t *i_out, int64_t *u_out) {
+  const int64_t ax = in->acc_rowptr[x], nax = in->acc_rowptr[x + 1] - ax;
+  const int64_t ay = in->acc_rowptr[y], nay = in->acc_rowptr[y + 1] - ay;
+  const int64_t cx = in->call_rowptr[x], ncx = in->call_rowptr[x + 1] - cx;
+  const int64_t cy = in->call_rowptr[y], ncy = in->call_rowptr[y + 1] - cy;
+  const int64_t i = common_sorted(in->acc_idx + ax, nax, in->acc_idx + ay, nay) +
+                    common_sorted(in->call_idx + cx, ncx, in->call_idx + cy, ncy);
+  *i_out = i;
+  *u_out = nax + ncx + nay + ncy - i;
+}
+
+typedef struct {
+  const or_sys *s;
+  int32_t x0, x1;                  /* rows of this worker */
+  int64_t n;                       /* pairs found */
+  int32_t *px, *py, *pi, *pu;      /* output (NULL: count only) */
+  int64_t cap;
+} sim_job;
+
+static void *sim_worker(void *arg) {
+  sim_job *j = (sim_job *)arg;
+  const or_input *in = &j->s->in;
+  int64_t n = 0;
+  for (int32_t x = j->x0; x < j->x1; ++x)
+    for (int32_t y = x + 1; y < in->n_methods; ++y) {
+      int64_t i, u;
+      sim_pair(in, x, y, &i, &u);
+      if (i == 0) continue;
+      if (j->px && n < j->cap) {
+        j->px[n] = x; j->py[n] = y; j->pi[n] = (int32_t)i; j->pu[n] = (int32_t)u;
+      }
+      ++n;
+    }
+  j->n = n;
+  return NULL;
+}
+
+/*
+ * Every pair x < y with a common property, in (x, y) order: x, y, i, u.
+ * Returns the number of such pairs; with NULL outputs only counts.  Rows of
+ * x are split over threads in two passes (count, then write at the offsets).
+ */
+int64_t or_similarity(const or_sys *s, int n_threads, int32_t *px, int32_t *py, int32_t *pi, int32_t *pu) {
+  const int32_t M = s->in.n_methods;
+  if (n_threads < 1) n_threads = 1;
+  /* rows split so that each thread gets about the same number of pairs */
+  int32_t *bounds = (int32_t *)calloc((size_t)n_threads + 1, sizeof(int32_t));
+  sim_job *jobs = (sim_job *)calloc((size_t)n_threads, sizeof(sim_job));
+  pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+  if (!bounds || !jobs || !th) { free(bounds); free(jobs); free(th); return -1; }
+  {
+    const double total = (double)M * (M - 1) / 2.0;
+    int32_t x = 0;
+    double acc = 0;
+    for (int t = 1; t < n_threads; ++t) {
+      while (x < M && acc < total * t / n_threads) { acc += (double)(M - 1 - x); ++x; }
+      bounds[t] = x;
+    }
+    bounds[n_threads] = M;
+  }
+  for (int t = 0; t < n_threads; ++t) {
+    jobs[t].s = s; jobs[t].x0 = bounds[t]; jobs[t].x1 = bounds[t + 1];
+    jobs[t].px = NULL;
+    pthread_create(&th[t], NULL, sim_worker, &jobs[t]);
+  }
+  int64_t total = 0;
+  for (int t = 0; t < n_threads; ++t) { pthread_join(th[t], NULL); total += jobs[t].n; }
+  if (px) {
+    int64_t off = 0;
+    for (int t = 0; t < n_threads; ++t) {
+      const int64_t nt = jobs[t].n;
+      jobs[t].px = px + off; jobs[t].py = py + off; jobs[t].pi = pi + off; jobs[t].pu = pu + off;
+      jobs[t].cap = nt;
+      off += nt;
+      pthread_create(&th[t], NULL, sim_worker, &jobs[t]);
+    }
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+  }
+  free(bounds); free(jobs); free(th);
+  return total;
+}
+
+/* every y != x with a common property with x, ascending y: y, i, u */
+int64_t or_similarity_row(const or_sys *s, int32_t x, int32_t *py, int32_t *pi, int32_t *pu) {
+  int64_t n = 0;
+  for (int32_t y = 0; y < s->in.n_methods; ++y) {
+    if (y == x) continue;
+    int64_t i, u;
+    sim_pair(&s->in, x, y, &i, &u);
+    if (i == 0) continue;
+    if (py) { py[n] = y; pi[n] = (int32_t)i; pu[n] = (int32_t)u; }
+    ++n;
+  }
+  return n;
+}
+
+/*
+ * The R1 threshold (footnote of Sec. III.A: the average of the system's
+ * similarity values; the values are the pairs that share a property).  The
+ * average is taken in double precision in one fixed order -- the sum over u
+ * ascending of (sum of i over the pairs with union u) / u, divided by the
+ * number of pairs -- and a pair is "high" when (double)i / (double)u exceeds
+ * it.  thr[u] (u = 0 .. umax) receives the smallest i for which that holds
+ * (u + 1 when none).  Returns the average.
+ */
+double or_r1_threshold(const int32_t *pi, const int32_t *pu, int64_t n, int32_t umax, int32_t *thr) {
+  int64_t *sum_i = (int64_t *)calloc((size_t)umax + 1, sizeof(int64_t));
+  if (!sum_i) return -1.0;
+  for (int64_t k = 0; k < n; ++k) sum_i[pu[k]] += pi[k];
+  double s = 0.0;
+  for (int32_t u = 1; u <= umax; ++u)
+    if (sum_i[u]) s += (double)sum_i[u] / (double)u;
+  const double avg = n > 0 ? s / (double)n : 0.0;
+  for (int32_t u = 0; u <= umax; ++u) {
+    int32_t t = u + 1;
+    for (int32_t i = 0; i <= u; ++i)
+      if (u > 0 && (double)i / (double)u > avg) { t = i; break; }
+    thr[u] = t;
+  }
+  free(sum_i);
+  return avg;
+}

@@ -1841,6 +1841,15 @@ __global__ void __launch_bounds__(1024) bitonic_sort_moves(mm_move *v, int32_t n
   bitonic_block(v, n, sm);
 }
 
+// block b sorts v[b * BITONIC_MAX, min(n, (b + 1) * BITONIC_MAX))
+__global__ void __launch_bounds__(1024) bitonic_sort_chunks(mm_move *v, int64_t n) {
+  pdl_wait();
+  __shared__ mm_move sm[BITONIC_MAX];
+  const int64_t b0 = (int64_t)blockIdx.x * BITONIC_MAX;
+  const int32_t len = (int32_t)min((int64_t)BITONIC_MAX, n - b0);
+  if (len > 1) bitonic_block(v + b0, len, sm);
+}
+
 // Kept moves sorted in the suggestion order, up to KEYED_MAX of them, in two
 // launches.  Every move gets one 64-bit key (n_improved descending, then dLCOM,
 // dCBO, m, d ascending; each field biased by its minimum over the moves and
@@ -2088,8 +2097,12 @@ static void check_criteria(const mm_criteria &crit) {
 }
 
 // Upload (if host) and validate an explicit candidate list; returns device pointers.
+// staging = false: the validation word and hash are read back into host stack
+// memory instead of the thread's page-locked staging buffer (which is
+// allocated on first use), so nothing is allocated.
 static void prepare_candidates(mm_system *s, const mm_candidates *cands, const int64_t **rowptr,
-                               const int32_t **dst, int64_t *n_cand, Scratch &ws, uint64_t *hash = nullptr) {
+                               const int32_t **dst, int64_t *n_cand, Scratch &ws, uint64_t *hash = nullptr,
+                               bool staging = true) {
   *rowptr = nullptr;
   *dst = nullptr;
   if (!cands || !cands->rowptr) {
@@ -2129,8 +2142,9 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
       MM_LAUNCH_CHECK();
     }
   }
-  // d_u64[3] = hash, d_u64[6] = error word: one copy into page-locked staging
-  unsigned char *hb = static_cast<unsigned char *>(host_staging(32));
+  // d_u64[3] = hash, d_u64[6] = error word: one copy (page-locked staging, or host stack memory)
+  unsigned long long local[4] = {0, 0, 0, 0};
+  unsigned char *hb = staging ? static_cast<unsigned char *>(host_staging(32)) : reinterpret_cast<unsigned char *>(local);
   MM_CUDA_TRY(cudaMemcpyAsync(hb, s->d_u64 + 3, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   MM_CUDA_TRY(cudaStreamSynchronize(st));
   uint32_t err = 0;
@@ -2400,8 +2414,8 @@ void eval_kept_into(mm_system *s, const mm_criteria &crit, const mm_candidates *
   const int64_t *rowptr;
   const int32_t *dst;
   int64_t n_cand;
-  Scratch unused;
-  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, unused);
+  Scratch unused;  // only host lists would use it, and they are rejected above
+  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, unused, nullptr, false);
   if (n_cand == 0 || s->M == 0) return;
   EvalCtx cx = make_ctx(s, crit);
   OutCtx oc{};
@@ -2412,11 +2426,10 @@ void eval_kept_into(mm_system *s, const mm_criteria &crit, const mm_candidates *
   dispatch_eval(s, cx, oc, rowptr, dst);
 }
 
-// Sort up to 2,048 kept moves in place (single-block bitonic sort).
-void sort_moves_small(mm_move *v, int32_t n, cudaStream_t st) {
+// Sort n kept moves in runs of 2,048 in place: one launch, block b sorts run b.
+void sort_moves_chunks(mm_move *v, int64_t n, cudaStream_t st) {
   if (n <= 1) return;
-  if (n > BITONIC_MAX) throw MmError{MM_EINVAL, "sort_moves_small: more than 2048 moves"};
-  pdl_launch(bitonic_sort_moves, 1, 1024, 0, st, v, n);
+  pdl_launch(bitonic_sort_chunks, (unsigned)ceil_div(n, BITONIC_MAX), 1024, 0, st, v, n);
   MM_LAUNCH_CHECK();
 }
 

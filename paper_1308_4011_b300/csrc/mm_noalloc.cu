@@ -6,12 +6,13 @@
 
 #include <algorithm>
 #include <mutex>
+#include <new>
 
 #include "mm_internal.cuh"
 
 void eval_kept_into(mm_system *s, const mm_criteria &crit, const mm_candidates *cands, mm_move *kept, int64_t cap,
                     unsigned long long *count, uint8_t *mark);
-void sort_moves_small(mm_move *v, int32_t n, cudaStream_t st);
+void sort_moves_chunks(mm_move *v, int64_t n, cudaStream_t st);
 
 namespace {
 
@@ -95,9 +96,19 @@ extern "C" MMREF_API mm_status mm_suggest_moves_noalloc(mm_system *s, const mm_c
     if (k < 0 || (k > 0 && !out_topk)) throw MmError{MM_EINVAL, "suggest_moves_noalloc: bad k or out_topk"};
     if (out_kind != MM_PTR_HOST && out_kind != MM_PTR_DEVICE)
       throw MmError{MM_EINVAL, "suggest_moves_noalloc: bad out_kind"};
+    // the caller's current device is restored on every exit, errors included
+    struct DeviceGuard {
+      int prev = -1;
+      ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+      }
+    } guard;
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) throw MmError{MM_ECUDA, "cudaGetDevice failed"};
-    if (cur != s->device && cudaSetDevice(s->device) != cudaSuccess) throw MmError{MM_ECUDA, "cudaSetDevice failed"};
+    if (cur != s->device) {
+      if (cudaSetDevice(s->device) != cudaSuccess) throw MmError{MM_ECUDA, "cudaSetDevice failed"};
+      guard.prev = cur;
+    }
     unsigned char *base = scratch_for_device(s->device);
     unsigned long long *counters = reinterpret_cast<unsigned long long *>(base);  // [0] kept, [1] methods
     uint8_t *mark = base + NA_COUNTERS;
@@ -122,8 +133,7 @@ extern "C" MMREF_API mm_status mm_suggest_moves_noalloc(mm_system *s, const mm_c
     // sort: bitonic chunks of 2,048, then pairwise merges between the two halves of the array
     mm_move *cur_buf = kept, *other = tmp;
     if (K > 1) {
-      for (int64_t c0 = 0; c0 < K; c0 += NA_CHUNK)
-        sort_moves_small(kept + c0, (int32_t)std::min<int64_t>(NA_CHUNK, K - c0), st);
+      sort_moves_chunks(kept, K, st);  // runs of NA_CHUNK, one block each
       for (int64_t w = NA_CHUNK; w < K; w *= 2) {
         merge_runs<<<(unsigned)ceil_div(K, 256), 256, 0, st>>>(cur_buf, other, (int32_t)K, (int32_t)w);
         MM_LAUNCH_CHECK();
@@ -137,12 +147,14 @@ extern "C" MMREF_API mm_status mm_suggest_moves_noalloc(mm_system *s, const mm_c
     MM_CUDA_TRY(cudaStreamSynchronize(st));
     if (n_kept) *n_kept = K;
     if (n_methods_with_kept) *n_methods_with_kept = (int64_t)hc[1];
-    if (cur != s->device) cudaSetDevice(cur);
     mm_set_error("");
     return MM_OK;
   } catch (const MmError &e) {
     mm_set_error(e.msg);
     return e.st;
+  } catch (const std::bad_alloc &) {
+    mm_set_error("host allocation failed");
+    return MM_ENOMEM;
   } catch (...) {
     mm_set_error("unexpected exception");
     return MM_ECUDA;

@@ -340,3 +340,98 @@ def test_o0_equals_o1_sampled_medium_restricted():
             a = o.evaluate_one(int(m), int(D), method=0, mask=7, min_improved=1)
             b = o.evaluate_one(int(m), int(D), method=1, mask=7, min_improved=1)
             assert _rec_tuple(a[0]) == _rec_tuple(b[0]) and a[1:] == b[1:]
+
+
+# ---------------------------------------------------------------- similarity and rule R1 (Sec. II.A, III.A)
+
+def _py_props(s, x):
+    return {("m", int(t)) for t in s.calls(x)} | {("a", int(a)) for a in s.acc(x)}
+
+
+def _py_similarity(s):
+    """Jaccard similarity of every pair by Python sets (Sec. II.A)."""
+    P = [_py_props(s, x) for x in range(s.n_methods)]
+    out = {}
+    for x in range(s.n_methods):
+        for y in range(x + 1, s.n_methods):
+            i = len(P[x] & P[y])
+            if i:
+                out[(x, y)] = (i, len(P[x] | P[y]))
+    return out
+
+
+def test_similarity_closed_forms():
+    """Identical property sets give i = u = |P|; a subset gives i = |small|,
+    u = |big|; disjoint sets are no value; a method with no properties shares
+    nothing; method 1 (a callee) and attribute 1 are different properties."""
+    # P0 = P1 = {a0, a1, m2}, P2 = {a0, m3}, P3 = {a2, m1}, P4 = {}, P5 = {a1, m2}
+    s = make_system([0, 0, 1, 1, 2, 2], [0, 1, 2],
+                    [[0, 1], [0, 1], [0], [2], [], [1]],
+                    [[2], [2], [3], [1], [], [2]], n_classes=3)
+    o = oracle.Oracle(s, threads=1)
+    x, y, i, u = o.similarity()
+    got = {(int(a), int(b)): (int(c), int(d)) for a, b, c, d in zip(x, y, i, u)}
+    assert got == {(0, 1): (3, 3), (0, 2): (1, 4), (0, 5): (2, 3), (1, 2): (1, 4), (1, 5): (2, 3)}
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_similarity_brute_force(seed):
+    s = tiny_random(seed)
+    o = oracle.Oracle(s, threads=2)
+    x, y, i, u = o.similarity()
+    got = {(int(a), int(b)): (int(c), int(d)) for a, b, c, d in zip(x, y, i, u)}
+    assert got == _py_similarity(s)
+    # rows: every partner of x, both sides of the pair
+    for q in range(0, s.n_methods, 3):
+        ry, ri, ru = o.similarity_row(q)
+        exp = sorted((b if a == q else a, v) for (a, b), v in got.items() if q in (a, b))
+        assert [(int(a), (int(c), int(d))) for a, c, d in zip(ry, ri, ru)] == exp
+
+
+def test_r1_threshold_and_candidates_by_hand():
+    """The average of three values 1/2, 1/3, 2/3 is 1/2: only 2/3 is above it.
+    Pairs in the same class propose nothing; a high pair across classes
+    proposes both moves."""
+    i = np.array([1, 1, 2], dtype=np.int32)
+    u = np.array([2, 3, 3], dtype=np.int32)
+    avg, thr = oracle.r1_threshold(i, u, 3)
+    assert avg == pytest.approx(0.5)
+    assert list(thr) == [1, 1, 2, 2]  # u = 1: 1/1 > 1/2; u = 2: 2/2 (1/2 is not above); u = 3: 2/3
+    s = make_system([0, 0, 1, 2], [], [[], [], [], []], [[1], [0], [0], [0]], n_classes=3)
+    x = np.array([0, 1, 2], dtype=np.int32)
+    y = np.array([1, 2, 3], dtype=np.int32)
+    rowptr, dst, nh = oracle.r1_candidates(s, x, y, np.array([1, 1, 2], np.int32), np.array([1, 3, 3], np.int32),
+                                           np.array([1, 1, 2, 2], np.int32))
+    # (0,1): same class; (1,2): 1/3 below; (2,3): 2/3 above, classes 1 and 2 -> 2 -> class 2, 3 -> class 1
+    assert nh == 1 and list(rowptr) == [0, 0, 0, 1, 2] and list(dst) == [2, 1]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_r1_suggestions_brute_force(seed):
+    """R1 end to end against Python: similarity by sets, the average in the
+    same fixed order, the proposed moves, each evaluated by recomputing the
+    whole system (brute force), kept when LCOM of origin and destination
+    both improve and no LCOM value worsens."""
+    s = tiny_random(seed + 20)
+    o = oracle.Oracle(s, threads=1)
+    res, avg, rowptr, dst, nvals, nhigh = o.r1(mask=3, min_improved=2)
+    sims = _py_similarity(s)
+    by_u = {}
+    for (i, u) in sims.values():
+        by_u[u] = by_u.get(u, 0) + i
+    tot = 0.0
+    for uu in sorted(by_u):
+        tot += by_u[uu] / uu
+    py_avg = tot / len(sims) if sims else 0.0
+    assert avg == py_avg and nvals == len(sims)
+    mc = [int(v) for v in s.method_class]
+    cand = set()
+    for (x, y), (i, u) in sims.items():
+        if i / u > py_avg and mc[x] != mc[y]:
+            cand.add((x, mc[y]))
+            cand.add((y, mc[x]))
+    got = {(m, int(dst[k])) for m in range(s.n_methods) for k in range(rowptr[m], rowptr[m + 1])}
+    assert got == cand
+    ev = brute.evaluate(s, mask=3, min_improved=2, candidates=sorted(cand))
+    assert [tuple(int(v) for v in (k["m"], k["d"], k["n_improved"], k["d_ck_sum"], k["d_cbo_sum"]))
+            for k in res.kept] == brute.suggestions(ev)

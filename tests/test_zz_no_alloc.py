@@ -31,12 +31,15 @@ def _rows(a):
     return [tuple(int(x[f]) for f in FIELDS) for x in a]
 
 
-def _noalloc_c(g, k, mask, mi, out, kind):
-    """Direct C-ABI call of mm_suggest_moves_noalloc."""
+def _noalloc_c(g, k, mask, mi, out, kind, rowptr=None, dst=None):
+    """Direct C-ABI call of mm_suggest_moves_noalloc (candidate lists: CUDA tensors or None)."""
     crit = mmref._Crit(mask, mi)
     nk, nm = ctypes.c_int64(-1), ctypes.c_int64(-1)
     ptr = out.data_ptr() if kind == mmref.PTR_DEVICE else out.ctypes.data
-    rc = mmref._lib.mm_suggest_moves_noalloc(g.handle, ctypes.byref(crit), None, k, ptr, kind, ctypes.byref(nk),
+    cands = None
+    if rowptr is not None:
+        cands = ctypes.byref(mmref._Cands(rowptr.data_ptr(), dst.data_ptr(), int(dst.numel()), mmref.PTR_DEVICE, 0))
+    rc = mmref._lib.mm_suggest_moves_noalloc(g.handle, ctypes.byref(crit), cands, k, ptr, kind, ctypes.byref(nk),
                                              ctypes.byref(nm))
     return rc, nk.value, nm.value
 
@@ -101,4 +104,44 @@ def test_noalloc_rejects_systems_above_the_method_limit():
     out = np.zeros(1, dtype=mmref.MOVE_DTYPE)
     rc, _, _ = _noalloc_c(g, 1, 3, 2, out, mmref.PTR_HOST)
     assert rc == mmref.MM_EBUDGET and b"MM_NOALLOC_MAX_METHODS" in mmref._lib.mm_last_error()
+    g.free()
+
+
+def test_noalloc_first_call_on_a_fresh_system_equals_the_oracle():
+    """The main use: a system loaded and measured (compute_metrics only), then
+    asked for suggestions without allocating -- no earlier evaluation on the
+    handle -- gives exactly the oracle's kept list."""
+    import oracle
+    s = synth.named("tiny")
+    g = mmref.load_synth(s, device=True)
+    mmref.compute_metrics(g, None, None)
+    ref = oracle.Oracle(s).evaluate(mask=3, min_improved=2, method=1)
+    k = max(ref.n_kept, 1)
+    for _ in range(2):
+        out = np.zeros(k, dtype=mmref.MOVE_DTYPE)
+        rc, nk, nm = _noalloc_c(g, k, 3, 2, out, mmref.PTR_HOST)
+        assert rc == mmref.MM_OK, mmref._lib.mm_last_error()
+        assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept)
+        assert _rows(out[:nk]) == [tuple(int(x[f]) for f in ("m", "d", "n_improved", "d_ck_sum", "d_cbo_sum"))
+                                   for x in ref.kept]
+    g.free()
+
+
+def test_noalloc_with_device_candidate_lists():
+    """Candidate lists in device memory (validated on the device, read back
+    without allocating host memory) give what mm_suggest_moves gives."""
+    s = synth.generate(300, 4000, 2000, max_class=80, seed=12)
+    rp, dst = synth.candidates(s, 16, seed=12)
+    g = mmref.load_synth(s, device=True)
+    mmref.compute_metrics(g, None, None)
+    rpd, dd = torch.from_numpy(rp).cuda(), torch.from_numpy(dst).cuda()
+    for mask, mi in ((3, 2), (7, 1)):
+        ref, ref_nk, ref_nm = mmref.suggest_moves(g, 100000, mask, mi, rpd, dd)
+        k = max(ref_nk, 1)
+        for _ in range(2):
+            out = np.zeros(k, dtype=mmref.MOVE_DTYPE)
+            rc, nk, nm = _noalloc_c(g, k, mask, mi, out, mmref.PTR_HOST, rpd, dd)
+            assert rc == mmref.MM_OK, mmref._lib.mm_last_error()
+            assert (nk, nm) == (ref_nk, ref_nm)
+            assert _rows(out[:nk]) == _rows(ref)
     g.free()
