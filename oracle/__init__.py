@@ -275,3 +275,58 @@ def r1_candidates(system, x, y, i, u, thr):
 def record_hash(m: int, d: int, rec) -> int:
     arr = np.array([rec], dtype=RECORD_DTYPE) if not isinstance(rec, np.ndarray) else rec.reshape(1)
     return int(_load().or_record_hash(m, d, arr.ctypes.data))
+
+
+# ---------------------------------------------------------------- move sequences
+
+def affected_classes(system, m: int, d: int) -> set:
+    """Classes whose metrics or adjacency a move of m to d can change: its
+    class, d, the classes m uses (calls into or reads attributes of) and the
+    classes of m's callers (Sec. III.A: the origin and destination classes,
+    and through CBO the classes coupled to them)."""
+    mc = system.method_class
+    aff = {int(mc[m]), int(d)}
+    aff |= {int(mc[t]) for t in system.calls(m)}
+    aff |= {int(system.attr_class[a]) for a in system.acc(m)}
+    rows = np.repeat(np.arange(system.n_methods), np.diff(system.call_rowptr))  # the caller of each call
+    aff |= {int(mc[y]) for y in rows[system.call_idx == m]}
+    return aff
+
+
+def sequence(system, mask: int = 3, min_improved: int = 2, rounds: int = 4, per_round: int = 1 << 30,
+             cbo_attrs: bool = True):
+    """Several moves at once (abstract and Sec. I: several solutions): in each
+    round the kept moves of the current state, in suggestion order, are taken
+    greedily while their affected classes are disjoint from those of the moves
+    already taken (so none changes another's evaluation) and no method moves
+    twice; all of them are applied, and the next round starts from the new
+    state.  Returns [(round, m, from class, to class), ...] and the final
+    method_class array."""
+    from paper_1308_4011_b300 import synth as _synth
+    mc = system.method_class.copy()
+    out = []
+    for rnd in range(rounds):
+        cur = _synth.System(system.n_classes, system.n_methods, system.n_attrs, mc.copy(), system.attr_class,
+                            system.acc_rowptr, system.acc_idx, system.call_rowptr, system.call_idx)
+        o = Oracle(cur, cbo_attrs=cbo_attrs)
+        kept = o.evaluate(mask=mask, min_improved=min_improved, method=1).kept
+        o.close()
+        used, moved, taken = set(), set(), []
+        for k in kept:
+            if len(taken) >= per_round:
+                break
+            m, d = int(k["m"]), int(k["d"])
+            if m in moved:
+                continue
+            aff = affected_classes(cur, m, d)
+            if aff & used:
+                continue
+            used |= aff
+            moved.add(m)
+            taken.append((m, d))
+        if not taken:
+            break
+        for m, d in taken:
+            out.append((rnd, m, int(mc[m]), d))
+            mc[m] = d
+    return out, mc

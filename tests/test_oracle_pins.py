@@ -435,3 +435,49 @@ def test_r1_suggestions_brute_force(seed):
     ev = brute.evaluate(s, mask=3, min_improved=2, candidates=sorted(cand))
     assert [tuple(int(v) for v in (k["m"], k["d"], k["n_improved"], k["d_ck_sum"], k["d_cbo_sum"]))
             for k in res.kept] == brute.suggestions(ev)
+
+
+# ---------------------------------------------------------------- move sequences (abstract, Sec. I)
+
+@pytest.mark.parametrize("seed", range(5))
+def test_sequence_rounds_are_non_conflicting_and_additive(seed):
+    """Each round's moves: individually kept in the round's state (whole-system
+    brute force), pairwise disjoint affected classes, no method twice, and
+    maximal (every other kept move conflicts with a taken one).  Applying the
+    round changes every class metric by exactly the sum of what each move
+    alone changes (recomputed by definition), so the moves do not interact."""
+    s = tiny_random(seed + 60)
+    seq, final = oracle.sequence(s, mask=3, min_improved=1, rounds=3)
+    mc = s.method_class.copy()
+    for rnd in sorted({r for r, *_ in seq}):
+        moves = [(m, d) for r, m, c_, d in seq if r == rnd]
+        cur = synth.System(s.n_classes, s.n_methods, s.n_attrs, mc.copy(), s.attr_class, s.acc_rowptr, s.acc_idx,
+                           s.call_rowptr, s.call_idx)
+        ev = brute.evaluate(cur, mask=3, min_improved=1)
+        kept = brute.suggestions(ev)
+        assert all(ev[(m, d)]["flags"] & 0x8000 for m, d in moves)
+        affs = [oracle.affected_classes(cur, m, d) for m, d in moves]
+        assert all(not (affs[a] & affs[b]) for a in range(len(affs)) for b in range(a))
+        assert len({m for m, _ in moves}) == len(moves)
+        used = set().union(*affs)
+        taken = set(moves)
+        for m, d, *_ in kept:
+            if (m, d) not in taken:
+                assert m in {x for x, _ in moves} or oracle.affected_classes(cur, m, d) & used
+        base = brute.class_metrics(cur, [int(v) for v in cur.method_class])
+        after_all = mc.copy()
+        for m, d in moves:
+            after_all[m] = d
+        total = brute.class_metrics(cur, [int(v) for v in after_all])
+        summed = [dict(b) for b in base]
+        for m, d in moves:
+            one = mc.copy()
+            one[m] = d
+            single = brute.class_metrics(cur, [int(v) for v in one])
+            for Y in range(s.n_classes):
+                for f in ("ck", "cbo"):
+                    summed[Y][f] += single[Y][f] - base[Y][f]
+        for Y in range(s.n_classes):
+            assert (total[Y]["ck"], total[Y]["cbo"]) == (summed[Y]["ck"], summed[Y]["cbo"]), (rnd, Y)
+        mc = after_all
+    assert np.array_equal(mc, final)
