@@ -330,3 +330,54 @@ def sequence(system, mask: int = 3, min_improved: int = 2, rounds: int = 4, per_
             out.append((rnd, m, int(mc[m]), d))
             mc[m] = d
     return out, mc
+
+
+# ---------------------------------------------------------------- rule R3
+
+R3_DTYPE = np.dtype([("m", "<i4"), ("d", "<i4"), ("fan_in", "<i4"), ("fan_out", "<i4"), ("dcbo_src", "<i4"),
+                     ("dcbo_dst", "<i4")])
+
+
+def r3(system, cbo_attrs: bool = True, threads: int | None = None):
+    """Rule R3 (Sec. III.A, third rule): for every class whose CBO is above the
+    average CBO of all classes (exactly: CBO(C) * c > sum of CBO), relocate
+    its methods to the classes each method uses (calls into, or reads
+    attributes of when attribute uses count); a move is kept when CBO of the
+    origin drops and CBO of the destination does not rise.  Kept moves in
+    order of fan-in + fan-out (descending; the rule starts with the methods of
+    highest fan-in and fan-out), then dCBO(origin) + dCBO(destination)
+    (ascending), method, class.  Returns (kept R3_DTYPE array, candidate
+    rowptr, candidate dst, number of high classes)."""
+    o = Oracle(system, cbo_attrs=cbo_attrs, threads=threads)
+    cm, mm_ = o.class_metrics(), o.method_metrics()
+    cbo = cm["cbo"]
+    c, M = system.n_classes, system.n_methods
+    high = cbo * c > cbo.sum()
+    mc = system.method_class
+    rows = []
+    for m in range(M):
+        C = int(mc[m])
+        if not high[C]:
+            rows.append([])
+            continue
+        used = {int(mc[t]) for t in system.calls(m)}
+        if cbo_attrs:
+            used |= {int(system.attr_class[a]) for a in system.acc(m)}
+        used.discard(C)
+        rows.append(sorted(used))
+    rowptr = np.zeros(M + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    dst = np.asarray([d for r in rows for d in r], dtype=np.int32)
+    res = o.evaluate(mask=4, min_improved=1, cand_rowptr=rowptr, cand_dst=dst, method=1, records=True)
+    o.close()
+    mth = np.repeat(np.arange(M), np.diff(rowptr))
+    keep = (res.records["dcbo_src"] < 0) & (res.records["dcbo_dst"] <= 0) if len(dst) else np.zeros(0, bool)
+    out = np.zeros(int(keep.sum()), dtype=R3_DTYPE)
+    out["m"] = mth[keep]
+    out["d"] = dst[keep]
+    out["fan_in"] = mm_["fan_in"][mth[keep]]
+    out["fan_out"] = mm_["fan_out"][mth[keep]]
+    out["dcbo_src"] = res.records["dcbo_src"][keep]
+    out["dcbo_dst"] = res.records["dcbo_dst"][keep]
+    order = np.lexsort((out["d"], out["m"], out["dcbo_src"] + out["dcbo_dst"], -(out["fan_in"] + out["fan_out"])))
+    return out[order], rowptr, dst, int(high.sum())

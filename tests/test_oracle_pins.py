@@ -481,3 +481,51 @@ def test_sequence_rounds_are_non_conflicting_and_additive(seed):
             assert (total[Y]["ck"], total[Y]["cbo"]) == (summed[Y]["ck"], summed[Y]["cbo"]), (rnd, Y)
         mc = after_all
     assert np.array_equal(mc, final)
+
+
+# ---------------------------------------------------------------- rule R3 (Sec. III.A, third rule)
+
+@pytest.mark.parametrize("seed", range(6))
+def test_r3_brute_force(seed):
+    """R3 against Python: high classes by the exact average, candidates from
+    the classes each method uses, CBO changes by whole-system recomputation
+    (brute force), kept and ordered by the rule."""
+    s = tiny_random(seed + 80)
+    kept, rowptr, dst, nhigh = oracle.r3(s)
+    base = brute.class_metrics(s, [int(v) for v in s.method_class])
+    cbo = [b["cbo"] for b in base]
+    high = [v * s.n_classes > sum(cbo) for v in cbo]
+    assert nhigh == sum(high)
+    mc = [int(v) for v in s.method_class]
+    fan_in = [0] * s.n_methods
+    for x in range(s.n_methods):
+        for t in s.calls(x):
+            fan_in[int(t)] += 1
+    exp = []
+    for m in range(s.n_methods):
+        C = mc[m]
+        if not high[C]:
+            continue
+        used = ({mc[int(t)] for t in s.calls(m)} | {int(s.attr_class[a]) for a in s.acc(m)}) - {C}
+        for D in sorted(used):
+            cls2 = list(mc)
+            cls2[m] = D
+            after = brute.class_metrics(s, cls2)
+            ds, dd = after[C]["cbo"] - cbo[C], after[D]["cbo"] - cbo[D]
+            if ds < 0 and dd <= 0:
+                exp.append((m, D, fan_in[m], len(s.calls(m)), ds, dd))
+    exp.sort(key=lambda t: (-(t[2] + t[3]), t[4] + t[5], t[0], t[1]))
+    assert [tuple(int(v) for v in k) for k in kept] == exp
+
+
+def test_r3_hand_example():
+    """m0 (class 0) calls m2 (class 1) and m3 (class 2); m1 (class 0) calls m2;
+    m2 calls m3.  CBO = (2, 1, 0): only class 0 is above the average 1.
+    m0 -> 1: class 0 keeps only m1 (uses 1): CBO 2 -> 1; class 1 still uses
+    only 2: kept.  m0 -> 2: class 2 starts using 1: CBO(2) 0 -> 1, rejected.
+    m1 -> 1: class 0 still uses 1 and 2 through m0, rejected."""
+    s = make_system([0, 0, 1, 2], [], [[], [], [], []], [[2, 3], [2], [3], []], n_classes=3)
+    kept, rowptr, dst, nhigh = oracle.r3(s)
+    assert nhigh == 1
+    assert list(rowptr) == [0, 2, 3, 3, 3] and list(dst) == [1, 2, 1]
+    assert [tuple(int(v) for v in k) for k in kept] == [(0, 1, 0, 2, -1, 0)]
