@@ -293,6 +293,73 @@ MMREF_API mm_status mm_suggest_moves_noalloc(mm_system *sys, const mm_criteria *
                                              int64_t *n_methods_with_kept);
 
 /*
+ * Jaccard similarity of method pairs (Sec. II.A) and rule R1 (Sec. III.A).
+ * The properties of a method are the methods it calls and the attributes it
+ * accesses; sim(x, y) = |P(x) & P(y)| / |P(x) | P(y)|, kept as the exact
+ * integers (i, u).  The values are the pairs with a common property (i > 0;
+ * Sec. IV.C keeps only non-zero similarity values); every other pair has
+ * similarity 0.
+ */
+typedef struct {
+  int64_t n_values;        /* method pairs with a common property */
+  int64_t n_cooccurrences; /* (pair, common property) incidences they were counted from */
+  int64_t n_high;          /* R1: values above the average whose methods are in different classes */
+  int64_t n_candidates;    /* R1: distinct moves those pairs propose */
+  double average;          /* average of the values (footnote of Sec. III.A: R1's threshold) */
+  int32_t max_union;       /* upper bound of u: twice the largest property count */
+  int32_t reserved;
+} mm_similarity_info;
+
+/*
+ * Compute every similarity value of the system's current state (its input
+ * CSR; metrics need not be computed).  x[], y[], inter[], uni[] (nullable,
+ * cap entries each, out_kind memory) receive the first min(cap, n_values)
+ * values in (x, y) order, x < y, with inter = i and uni = u.  info
+ * (nullable, host) receives the counts and the average (n_high and
+ * n_candidates are 0).  Errors: MM_EBUDGET when the pairs sharing a property
+ * exceed 2^32, MM_ENOMEM, MM_ECUDA.  Synchronises the stream.
+ */
+MMREF_API mm_status mm_similarity(mm_system *sys, int32_t *x, int32_t *y, int32_t *inter, int32_t *uni, int64_t cap,
+                                  int32_t out_kind, mm_similarity_info *info);
+
+/*
+ * Suggestions of rule R1 (Sec. III.A, first rule): every pair of methods in
+ * different classes whose similarity is above the average of all similarity
+ * values (the average in double precision, summed over u ascending of
+ * sum(i)/u and divided by the number of values; a pair is above it when
+ * (double)i / (double)u is greater) proposes moving either method to the
+ * other's class.  The distinct proposed moves are evaluated and filtered by
+ * crit exactly as mm_suggest_moves does with them as candidate lists (R1
+ * itself asks for LCOM improved in both the origin and the destination:
+ * metric_mask = MM_LCOM_CK | MM_LCOM_HS, min_improved = 2).  Outputs as
+ * mm_suggest_moves; info (nullable, host) as mm_similarity plus n_high and
+ * n_candidates.  Needs mm_compute_metrics first.  Synchronises the stream.
+ */
+MMREF_API mm_status mm_suggest_r1(mm_system *sys, const mm_criteria *crit, int32_t k, mm_move *out_topk,
+                                  int32_t out_kind, int64_t *n_kept, int64_t *n_methods_with_kept,
+                                  mm_similarity_info *info);
+
+/*
+ * Suggestions of rule R3 (Sec. III.A, third rule).  Classes whose CBO is
+ * above the average CBO of all classes (exactly: CBO(C) * n_classes > sum of
+ * CBO) relocate their methods, each to every class it uses (calls into, or
+ * reads an attribute of when the system counts attribute uses); a relocation
+ * is kept when the origin's CBO drops and the destination's does not rise
+ * (dcbo_src < 0, dcbo_dst <= 0, as mm_move_eval computes them).  Kept moves
+ * are ordered by fan_in + fan_out of the method (descending: the rule starts
+ * with the methods of highest fan-in and fan-out), then dcbo_src + dcbo_dst
+ * (ascending), then m, then d.  out_topk (host, k entries) receives the first
+ * min(k, n_kept); *n_candidates the relocations evaluated, *n_high_classes
+ * the classes above the average (all nullable).  Needs mm_compute_metrics
+ * first.  Synchronises the stream.
+ */
+typedef struct {
+  int32_t m, d, fan_in, fan_out, dcbo_src, dcbo_dst;
+} mm_r3_move;
+MMREF_API mm_status mm_suggest_r3(mm_system *sys, int32_t k, mm_r3_move *out_topk, int64_t *n_kept,
+                                  int64_t *n_candidates, int32_t *n_high_classes);
+
+/*
  * Batched evaluation (no counterpart in the paper; the paper analyses one
  * system at a time, Sec. V).  A batch holds many loaded systems of very
  * uneven sizes.  mm_batch_run computes every system's metrics (as
@@ -359,6 +426,26 @@ typedef struct {
  * rows to a host mirror used to validate edits).
  */
 MMREF_API mm_status mm_apply_edit(mm_system *sys, const mm_edit *edit);
+
+/*
+ * Several moves at once (the "several solutions" of the abstract and Sec. I).
+ * In each of up to `rounds` rounds, the kept moves of the full cross product
+ * for crit (as mm_suggest_moves orders them) are taken greedily while the
+ * classes each one affects -- its source and destination, the classes the
+ * method uses and the classes of its callers -- are disjoint from those of the
+ * moves already taken, and no method moves twice (at most per_round moves,
+ * per_round <= 0: no limit).  Such moves do not change one another's
+ * evaluation.  The round's moves are applied to the system (as MM_EDIT_MOVE
+ * edits) and its metrics computed again before the next round; rounds stop
+ * early when nothing is kept.  out[cap] (host, nullable) receives the
+ * applied moves in order: {round, m, from class, to class}; *n_applied their
+ * number.  Needs mm_compute_metrics first.  Synchronises the stream.
+ */
+typedef struct {
+  int32_t round, m, from, to;
+} mm_applied_move;
+MMREF_API mm_status mm_apply_sequence(mm_system *sys, const mm_criteria *crit, int32_t rounds, int32_t per_round,
+                                      mm_applied_move *out, int64_t cap, int64_t *n_applied);
 
 /* Copy the system's current arrays (after edits) to host buffers sized from
  * mm_system_info_get (n_acc, n_call); any pointer may be NULL.  Synchronises

@@ -49,7 +49,8 @@ void use_device(mm_system *s) {
 // then its events (released by the runtime once their last use completes).
 void release_system(mm_system *s) {
   s->arena.release();
-  for (Scratch *w : {&s->sort_ws, &s->eval_ws, &s->stage_ws, &s->kept_ws, &s->keyed_ws, &s->edit_ws,
+  for (Scratch *w : {&s->sort_ws, &s->eval_ws, &s->stage_ws, &s->kept_ws, &s->keyed_ws, &s->edit_ws, &s->sim_ws,
+                     &s->sim_keys_ws, &s->sim_val_ws, &s->r1_ws,
                      &s->union_ws, &s->side_eval[0], &s->side_eval[1], &s->side_eval[2], &s->side_sort[0],
                      &s->side_sort[1], &s->side_sort[2], &s->side_union[0], &s->side_union[1], &s->side_union[2]})
     w->release(s->stream);
@@ -391,6 +392,56 @@ mm_status mm_last_eval_ms(mm_system *s, float *ms) {
   });
 }
 
+static void fill_similarity_info(const mm_system *s, mm_similarity_info *info, int64_t n_high, int64_t n_cand) {
+  if (!info) return;
+  info->n_values = s->sim_n;
+  info->n_cooccurrences = s->sim_cooc;
+  info->n_high = n_high;
+  info->n_candidates = n_cand;
+  info->average = s->sim_avg;
+  info->max_union = s->sim_umax;
+  info->reserved = 0;
+}
+
+mm_status mm_similarity(mm_system *s, int32_t *x, int32_t *y, int32_t *inter, int32_t *uni, int64_t cap,
+                        int32_t out_kind, mm_similarity_info *info) {
+  return guarded([&] {
+    if (!s) throw MmError{MM_EINVAL, "similarity: NULL system"};
+    if (cap < 0) throw MmError{MM_EINVAL, "similarity: cap < 0"};
+    if ((x || y || inter || uni) && out_kind != MM_PTR_HOST && out_kind != MM_PTR_DEVICE)
+      throw MmError{MM_EINVAL, "similarity: bad out_kind"};
+    use_device(s);
+    compute_similarity(s);
+    const int64_t n = std::min<int64_t>(cap, s->sim_n);
+    const cudaMemcpyKind kind = out_kind == MM_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const int32_t *src[4] = {s->sim_x, s->sim_y, s->sim_i, s->sim_u};
+    int32_t *dst[4] = {x, y, inter, uni};
+    for (int k = 0; k < 4; ++k)
+      if (dst[k] && n > 0) MM_CUDA_TRY(cudaMemcpyAsync(dst[k], src[k], sizeof(int32_t) * (size_t)n, kind, s->stream));
+    MM_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    fill_similarity_info(s, info, 0, 0);
+  });
+}
+
+mm_status mm_suggest_r1(mm_system *s, const mm_criteria *crit, int32_t k, mm_move *out_topk, int32_t out_kind,
+                        int64_t *n_kept, int64_t *n_methods_with_kept, mm_similarity_info *info) {
+  return guarded([&] {
+    if (!s || !crit) throw MmError{MM_EINVAL, "suggest_r1: NULL system or criteria"};
+    if (!s->metrics_ready) throw MmError{MM_EINVAL, "suggest_r1: call mm_compute_metrics first"};
+    use_device(s);
+    compute_similarity(s);
+    int64_t n_high = 0, n_cand = 0;
+    build_r1_candidates(s, &n_high, &n_cand);
+    mm_candidates cands{};
+    cands.rowptr = s->r1_rowptr;
+    cands.dst = s->r1_dst;
+    cands.n_cand = n_cand;
+    cands.ptr_kind = MM_PTR_DEVICE;
+    suggest_moves(s, *crit, &cands, k, out_topk, out_kind, n_kept, n_methods_with_kept);
+    fill_similarity_info(s, info, n_high, n_cand);
+  });
+}
+
 mm_status mm_system_info_get(mm_system *s, mm_system_info *info) {
   return guarded([&] {
     if (!s || !info) throw MmError{MM_EINVAL, "system_info: NULL argument"};
@@ -432,6 +483,24 @@ mm_status mm_apply_edit(mm_system *s, const mm_edit *e) {
     if (!s || !e) throw MmError{MM_EINVAL, "apply_edit: NULL argument"};
     use_device(s);
     apply_edit(s, *e);
+  });
+}
+
+mm_status mm_suggest_r3(mm_system *s, int32_t k, mm_r3_move *out_topk, int64_t *n_kept, int64_t *n_candidates,
+                        int32_t *n_high_classes) {
+  return guarded([&] {
+    if (!s) throw MmError{MM_EINVAL, "suggest_r3: NULL system"};
+    use_device(s);
+    suggest_r3(s, k, out_topk, n_kept, n_candidates, n_high_classes);
+  });
+}
+
+mm_status mm_apply_sequence(mm_system *s, const mm_criteria *crit, int32_t rounds, int32_t per_round,
+                            mm_applied_move *out, int64_t cap, int64_t *n_applied) {
+  return guarded([&] {
+    if (!s || !crit) throw MmError{MM_EINVAL, "apply_sequence: NULL system or criteria"};
+    use_device(s);
+    apply_sequence(s, *crit, rounds, per_round, out, cap, n_applied);
   });
 }
 

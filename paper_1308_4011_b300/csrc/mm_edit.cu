@@ -377,6 +377,82 @@ void apply_edit(mm_system *s, const mm_edit &e) {
   s->kept_min = kmin;
 }
 
+namespace {
+__global__ void scatter_moves(const int2 *moves, int32_t n, int32_t *method_class) {
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) method_class[moves[k].x] = moves[k].y;
+}
+}  // namespace
+
+// Rounds of non-conflicting kept moves (see mm_apply_sequence in mmref.h).
+void apply_sequence(mm_system *s, const mm_criteria &crit, int32_t rounds, int32_t per_round, mm_applied_move *out,
+                    int64_t cap, int64_t *n_applied) {
+  if (!s->metrics_ready) throw MmError{MM_EINVAL, "apply_sequence: call mm_compute_metrics first"};
+  check_criteria_public(crit);
+  if (rounds < 0) throw MmError{MM_EINVAL, "apply_sequence: rounds < 0"};
+  if (cap > 0 && !out) throw MmError{MM_EINVAL, "apply_sequence: out is NULL"};
+  ensure_mirror(s);
+  EditMirror &mr = s->mirror;
+  cudaStream_t st = s->stream;
+  int64_t applied = 0;
+  std::vector<uint8_t> used((size_t)s->c, 0);
+  std::vector<uint8_t> moved((size_t)s->M, 0);
+  for (int32_t rnd = 0; rnd < rounds; ++rnd) {
+    // the kept moves of the current state, sorted in the suggestion order
+    int64_t K = 0, nm = 0;
+    suggest_moves(s, crit, nullptr, 0, nullptr, MM_PTR_HOST, &K, &nm);
+    if (K == 0) break;
+    std::vector<mm_move> kept((size_t)K);
+    suggest_moves(s, crit, nullptr, (int32_t)std::min<int64_t>(K, INT32_MAX), kept.data(), MM_PTR_HOST, &K, &nm);
+    // greedy: disjoint affected classes, each method once
+    std::fill(used.begin(), used.end(), 0);
+    std::fill(moved.begin(), moved.end(), 0);
+    std::vector<int2> take;
+    std::vector<int32_t> aff;
+    for (const mm_move &mv : kept) {
+      if (per_round > 0 && (int32_t)take.size() >= per_round) break;
+      const int32_t m = mv.m, D = mv.d;
+      if (moved[(size_t)m]) continue;
+      aff.clear();
+      aff.push_back(mr.method_class[(size_t)m]);
+      aff.push_back(D);
+      for (int32_t t : mr.calls[(size_t)m]) aff.push_back(mr.method_class[(size_t)t]);
+      for (int32_t a : mr.acc[(size_t)m]) aff.push_back(mr.attr_class[(size_t)a]);
+      for (int32_t y : mr.callers[(size_t)m]) aff.push_back(mr.method_class[(size_t)y]);
+      bool clash = false;
+      for (int32_t Y : aff) clash |= used[(size_t)Y] != 0;
+      if (clash) continue;
+      for (int32_t Y : aff) used[(size_t)Y] = 1;
+      moved[(size_t)m] = 1;
+      take.push_back(make_int2(m, D));
+    }
+    // apply the round: owner classes on the device and in the mirror, class sizes, then the metrics
+    for (const int2 &mv : take) {
+      const int32_t C = mr.method_class[(size_t)mv.x];
+      if (out && applied < cap) out[applied] = mm_applied_move{rnd, mv.x, C, mv.y};
+      ++applied;
+      mr.method_class[(size_t)mv.x] = mv.y;
+      mr.cls_n[(size_t)C]--;
+      mr.cls_n[(size_t)mv.y]++;
+    }
+    int2 *dmv = static_cast<int2 *>(s->edit_ws.need(sizeof(int2) * take.size(), st));
+    MM_CUDA_TRY(cudaMemcpyAsync(dmv, take.data(), sizeof(int2) * take.size(), cudaMemcpyHostToDevice, st));
+    scatter_moves<<<(unsigned)ceil_div((int64_t)take.size(), 256), 256, 0, st>>>(dmv, (int32_t)take.size(),
+                                                                                s->method_class);
+    MM_LAUNCH_CHECK();
+    MM_CUDA_TRY(cudaMemcpyAsync(s->cls_n, mr.cls_n.data(), sizeof(int32_t) * (size_t)s->c, cudaMemcpyHostToDevice, st));
+    s->methods_by_class = false;
+    s->edits += (int64_t)take.size();
+    resummarise(s);
+    s->kept_valid = false;
+    build_structures(s);
+    build_metrics(s);
+    build_move_precompute(s);
+    MM_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors copied from go out of scope
+  }
+  if (n_applied) *n_applied = applied;
+}
+
 // Copy the system's current CSR (after edits) to host buffers.
 void export_system(mm_system *s, int32_t *method_class, int32_t *attr_class, int64_t *acc_rowptr,
                    int32_t *acc_idx, int64_t *call_rowptr, int32_t *call_idx) {

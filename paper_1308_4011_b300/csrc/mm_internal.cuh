@@ -186,6 +186,15 @@ struct mm_system {
   int64_t kept_ncand = 0;    //   and length this
   int64_t kept_cap = 0;
 
+  // similarity values (Sec. II.A) of the last mm_similarity / mm_suggest_r1
+  Scratch sim_ws, sim_keys_ws, sim_val_ws, r1_ws;
+  int32_t *sim_np = nullptr, *sim_x = nullptr, *sim_y = nullptr, *sim_i = nullptr, *sim_u = nullptr;
+  int64_t sim_n = 0, sim_cooc = 0;
+  int32_t sim_umax = 0;
+  double sim_avg = 0.0;
+  int64_t *r1_rowptr = nullptr;    // rule R1's candidate lists (device CSR over the methods)
+  int32_t *r1_dst = nullptr;
+
   // inputs
   int32_t *method_class, *attr_class, *acc_idx, *call_idx;
   int64_t *acc_rowptr, *call_rowptr;
@@ -382,6 +391,14 @@ int batch_persistent_grid();
 void sort_kept_moves(mm_system *s, mm_move *kept, int64_t K);
 void check_criteria_public(const mm_criteria &crit);
 
+// similarity and rule R1 (mm_similarity.cu)
+void compute_similarity(mm_system *s);
+void build_r1_candidates(mm_system *s, int64_t *n_high, int64_t *n_cand);
+
+// rule R3 (mm_rules.cu); records of internal (valid) device candidate lists (mm_moves.cu)
+void suggest_r3(mm_system *s, int32_t k, mm_r3_move *out, int64_t *n_kept, int64_t *n_cand, int32_t *n_high);
+void eval_lists_records(mm_system *s, const int64_t *rowptr, const int32_t *dst, mm_move_eval *records);
+
 // edit path (mm_edit.cu / mm_moves.cu)
 void eval_csr_kept_append(mm_system *s, const mm_criteria &crit, const int64_t *rowptr, const int32_t *dst,
                           mm_move *kept, int64_t cap, unsigned long long *count, uint8_t *mark);
@@ -390,4 +407,6 @@ void apply_edit(mm_system *s, const mm_edit &e);
 void export_system(mm_system *s, int32_t *method_class, int32_t *attr_class, int64_t *acc_rowptr,
                    int32_t *acc_idx, int64_t *call_rowptr, int32_t *call_idx);
 void ensure_mirror(mm_system *s);
+void apply_sequence(mm_system *s, const mm_criteria &crit, int32_t rounds, int32_t per_round, mm_applied_move *out,
+                    int64_t cap, int64_t *n_applied);
 mm_edit resolve_edit(mm_system *s, int32_t kind, int32_t m, uint64_t sel);

@@ -1835,12 +1835,6 @@ __device__ __forceinline__ void bitonic_block(mm_move *v, int32_t n, mm_move *sm
   for (int32_t i = threadIdx.x; i < n; i += blockDim.x) v[i] = sm[i];
 }
 
-__global__ void __launch_bounds__(1024) bitonic_sort_moves(mm_move *v, int32_t n) {
-  pdl_wait();
-  __shared__ mm_move sm[BITONIC_MAX];
-  bitonic_block(v, n, sm);
-}
-
 // block b sorts v[b * BITONIC_MAX, min(n, (b + 1) * BITONIC_MAX))
 __global__ void __launch_bounds__(1024) bitonic_sort_chunks(mm_move *v, int64_t n) {
   pdl_wait();
@@ -2561,6 +2555,16 @@ void eval_csr_kept_append(mm_system *s, const mm_criteria &crit, const int64_t *
   oc.kept_count = count;
   oc.kept_cap = cap;
   oc.kept_mark = mark;
+  dispatch_eval(s, cx, oc, rowptr, dst);
+}
+
+// Records of internal (valid by construction) device candidate lists; the
+// criteria only set the record's kept bit, so CBO alone, one improved, is used.
+void eval_lists_records(mm_system *s, const int64_t *rowptr, const int32_t *dst, mm_move_eval *records) {
+  const mm_criteria crit{4u, 1};
+  EvalCtx cx = make_ctx(s, crit);
+  OutCtx oc{};
+  oc.records = reinterpret_cast<uint4 *>(records);
   dispatch_eval(s, cx, oc, rowptr, dst);
 }
 

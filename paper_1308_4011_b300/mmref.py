@@ -35,7 +35,8 @@ EXPORTED = ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluat
             "mm_batch_autotune", "mm_batch_run", "mm_batch_suggestions", "mm_batch_free", "mm_apply_edit",
             "mm_export_system", "mm_server_create", "mm_server_add_system", "mm_server_run", "mm_server_stats_get",
             "mm_server_snapshot", "mm_server_free", "mm_selftest_bounded_wait", "mm_last_eval_ms",
-            "mm_export_metrics")
+            "mm_export_metrics", "mm_similarity", "mm_suggest_r1", "mm_apply_sequence",
+            "mm_suggest_r3")
 
 CLASS_METRICS_DTYPE = np.dtype([("n_methods", "<i4"), ("n_attrs", "<i4"), ("P", "<i8"), ("Q", "<i8"),
                                 ("S", "<i8"), ("lcom_ck", "<i8"), ("hs_num", "<i8"), ("hs_den", "<i8"),
@@ -66,6 +67,12 @@ class _Cands(ctypes.Structure):
                 ("ptr_kind", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class _SimInfo(ctypes.Structure):
+    _fields_ = [("n_values", ctypes.c_int64), ("n_cooccurrences", ctypes.c_int64), ("n_high", ctypes.c_int64),
+                ("n_candidates", ctypes.c_int64), ("average", ctypes.c_double), ("max_union", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class _Info(ctypes.Structure):
     _fields_ = [("n_classes", ctypes.c_int32), ("n_methods", ctypes.c_int32), ("n_attrs", ctypes.c_int32),
                 ("cbo_attrs", ctypes.c_int32), ("n_acc", ctypes.c_int64), ("n_call", ctypes.c_int64),
@@ -77,6 +84,11 @@ _lib.mm_load_system.argtypes = [ctypes.POINTER(_Desc), _vp, ctypes.POINTER(_vp)]
 _lib.mm_set_stream.argtypes = [_vp, _vp]
 _lib.mm_compute_metrics.argtypes = [_vp, _vp, _vp, ctypes.c_int32]
 _lib.mm_export_metrics.argtypes = [_vp, _vp, _vp, ctypes.c_int32]
+_lib.mm_similarity.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_SimInfo)]
+_lib.mm_similarity.restype = ctypes.c_int
+_lib.mm_suggest_r1.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.c_int32, _vp, ctypes.c_int32,
+                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_SimInfo)]
+_lib.mm_suggest_r1.restype = ctypes.c_int
 _lib.mm_export_metrics.restype = ctypes.c_int
 _lib.mm_evaluate_moves.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.POINTER(_Cands), _vp, _vp, ctypes.c_int32]
 _lib.mm_suggest_moves.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.POINTER(_Cands), ctypes.c_int32, _vp,
@@ -106,6 +118,15 @@ class _Edit(ctypes.Structure):
 _lib.mm_apply_edit.argtypes = [_vp, ctypes.POINTER(_Edit)]
 _lib.mm_apply_edit.restype = ctypes.c_int
 _lib.mm_export_system.argtypes = [_vp] + [_vp] * 6
+_lib.mm_apply_sequence.argtypes = [_vp, ctypes.POINTER(_Crit), ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int64,
+                                   ctypes.POINTER(ctypes.c_int64)]
+_lib.mm_apply_sequence.restype = ctypes.c_int
+R3_DTYPE = np.dtype([("m", "<i4"), ("d", "<i4"), ("fan_in", "<i4"), ("fan_out", "<i4"), ("dcbo_src", "<i4"),
+                     ("dcbo_dst", "<i4")])
+_lib.mm_suggest_r3.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
+_lib.mm_suggest_r3.restype = ctypes.c_int
+APPLIED_DTYPE = np.dtype([("round", "<i4"), ("m", "<i4"), ("from", "<i4"), ("to", "<i4")])
 _lib.mm_export_system.restype = ctypes.c_int
 EDIT_ADD_ACCESS, EDIT_REMOVE_ACCESS, EDIT_ADD_CALL, EDIT_REMOVE_CALL, EDIT_MOVE = 1, 2, 3, 4, 5
 NOALLOC_MAX_METHODS = 1048576
@@ -273,6 +294,34 @@ def export_metrics(sys: System, out_class="host", out_method="host"):
     return out_class, out_method
 
 
+def _sim_info(inf) -> dict:
+    return {f: getattr(inf, f) for f, _ in _SimInfo._fields_ if f != "reserved"}
+
+
+def similarity(sys: System, cap=None):
+    """mm_similarity: every similarity value (x < y, i, u) as host arrays (up
+    to cap of them; all by default), and the info dict."""
+    inf = _SimInfo()
+    _check(_lib.mm_similarity(sys.handle, None, None, None, None, 0, PTR_HOST, ctypes.byref(inf)))
+    n = inf.n_values if cap is None else min(int(cap), inf.n_values)
+    out = [np.zeros(max(n, 1), dtype=np.int32) for _ in range(4)]
+    _check(_lib.mm_similarity(sys.handle, *[a.ctypes.data for a in out], n, PTR_HOST, ctypes.byref(inf)))
+    return tuple(a[:n] for a in out), _sim_info(inf)
+
+
+def suggest_r1(sys: System, k: int, mask: int = DEFAULT_MASK, min_improved: int = DEFAULT_MIN_IMPROVED, out=None):
+    """mm_suggest_r1: (top-k moves, n_kept, n_methods_with_kept, info dict)."""
+    crit = _Crit(mask, min_improved)
+    if out is None:
+        out = np.zeros(max(k, 0), dtype=MOVE_DTYPE)
+    nk, nm = ctypes.c_int64(), ctypes.c_int64()
+    inf = _SimInfo()
+    _check(_lib.mm_suggest_r1(sys.handle, ctypes.byref(crit), int(k), _ptr(out), _kind(out), ctypes.byref(nk),
+                              ctypes.byref(nm), ctypes.byref(inf)))
+    n = min(int(k), int(nk.value))
+    return (out[:n] if _kind(out) == PTR_HOST else out), int(nk.value), int(nm.value), _sim_info(inf)
+
+
 def _cands(cand_rowptr, cand_dst):
     if cand_rowptr is None:
         return None, None
@@ -387,6 +436,28 @@ def apply_edit(sys: System, kind: int, m: int, target: int):
     """mm_apply_edit: one edit (EDIT_* kind, method m, attribute / callee / class)."""
     e = _Edit(int(kind), int(m), int(target), 0)
     _check(_lib.mm_apply_edit(sys.handle, ctypes.byref(e)))
+
+
+def apply_sequence(sys: System, rounds: int, mask: int = DEFAULT_MASK, min_improved: int = DEFAULT_MIN_IMPROVED,
+                   per_round: int = 0, cap: int | None = None):
+    """mm_apply_sequence: rounds of non-conflicting kept moves applied to the
+    system; returns the applied moves (APPLIED_DTYPE array, in order)."""
+    cap = sys.n_methods * max(rounds, 1) if cap is None else int(cap)
+    out = np.zeros(max(cap, 1), dtype=APPLIED_DTYPE)
+    n = ctypes.c_int64()
+    _check(_lib.mm_apply_sequence(sys.handle, ctypes.byref(_Crit(mask, min_improved)), int(rounds), int(per_round),
+                                  out.ctypes.data, cap, ctypes.byref(n)))
+    return out[: min(cap, n.value)]
+
+
+def suggest_r3(sys: System, k: int):
+    """mm_suggest_r3: (top-k R3 moves as an R3_DTYPE array, n_kept,
+    n_candidates, n_high_classes)."""
+    out = np.zeros(max(k, 1), dtype=R3_DTYPE)
+    nk, nc, nh = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(_lib.mm_suggest_r3(sys.handle, int(k), out.ctypes.data, ctypes.byref(nk), ctypes.byref(nc),
+                              ctypes.byref(nh)))
+    return out[: min(k, nk.value)], int(nk.value), int(nc.value), int(nh.value)
 
 
 def export_system(sys: System):

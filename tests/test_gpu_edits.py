@@ -128,3 +128,28 @@ def test_invalid_edits_change_nothing():
     assert dig0[0] == dig1[0]
     _check_state(g, tr, 7, 1)
     g.free()
+
+
+# ---------------------------------------------------------------- move sequences
+
+@pytest.mark.parametrize("name,mask,mi,rounds,per_round", [("tiny", 3, 2, 4, 0), ("tiny", 3, 1, 3, 5),
+                                                           ("tiny", 7, 1, 2, 0)])
+def test_sequence_equals_oracle(name, mask, mi, rounds, per_round):
+    """Rounds of non-conflicting kept moves applied on the GPU equal the
+    oracle's rounds, move for move, and the final state's metrics equal a
+    recomputation from the oracle."""
+    s = synth.named(name)
+    g = mmref.load_synth(s, device=True)
+    mmref.compute_metrics(g, None, None)
+    got = mmref.apply_sequence(g, rounds, mask, mi, per_round=per_round)
+    exp, final = oracle.sequence(s, mask=mask, min_improved=mi, rounds=rounds,
+                                 per_round=per_round if per_round > 0 else 1 << 30)
+    assert [tuple(int(v) for v in x) for x in got] == exp
+    mc = mmref.export_system(g)[0]
+    assert np.array_equal(mc, final)
+    cur = synth.System(s.n_classes, s.n_methods, s.n_attrs, final, s.attr_class, s.acc_rowptr, s.acc_idx,
+                       s.call_rowptr, s.call_idx)
+    cm, mm_ = mmref.export_metrics(g)
+    ocm = oracle.Oracle(cur).class_metrics()
+    assert np.array_equal(cm["P"], ocm["P"]) and np.array_equal(cm["cbo"].astype(np.int64), ocm["cbo"])
+    g.free()
