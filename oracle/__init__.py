@@ -16,7 +16,10 @@ What it computes (Napoli, Pappalardo, Tramontana, CISIS 2013):
     two independent routes: O0 recomputes the affected classes from the
     definitions after changing cls(m) (the re-evaluation of Sec. IV.C), O1
     applies the incremental update formulas;
-  * the sorted suggestion list (top-k) and an order-independent digest.
+  * the sorted suggestion list (top-k) and an order-independent digest;
+  * the LCOM and CBO variants of Sec. II.B (sharing over every accessed
+    attribute, unclamped differences, coupling in both directions) and the
+    ranking of classes by a metric.
 
 ``brute.py`` is a third, pure-Python route (whole-system recompute with
 Python sets) for tiny systems; ``tables.py`` holds the paper's value-count
@@ -42,6 +45,8 @@ CLASS_FIELDS = ("n", "a", "P", "Q", "S", "ck", "hs_num", "hs_den", "cbo")
 CLASS_DTYPE = np.dtype([(f, "<i8") for f in CLASS_FIELDS])
 
 LCOM_CK, LCOM_HS, CBO = 1, 2, 4
+VARIANT_FIELDS = ("P_all", "Q_all", "ck_all", "pq", "pq_all", "cbo_out", "cbo_in", "cbo_bi")
+VARIANT_DTYPE = np.dtype([(f, "<i8") for f in VARIANT_FIELDS])
 
 
 def build(force: bool = False) -> str:
@@ -102,6 +107,8 @@ def _load():
         _lib.or_r1_threshold.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                          ctypes.c_void_p]
         _lib.or_r1_threshold.restype = ctypes.c_double
+        _lib.or_class_variants.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        _lib.or_class_variants.restype = ctypes.c_int
     return _lib
 
 
@@ -201,6 +208,19 @@ class Oracle:
             raise ValueError("oracle: invalid candidate (out of range or equal to the source class)")
         return EvalResult(int(res.digest), int(res.n_cand), kept, int(res.n_methods_with_kept), rec)
 
+    def class_variants(self, threads: int | None = None):
+        """The LCOM and CBO variants of Sec. II.B for every class (VARIANT_DTYPE):
+        LCOM_CK with sharing over every accessed attribute (P_all, Q_all, ck_all),
+        the unclamped differences pq = P - Q and pq_all = P_all - Q_all, and
+        CBO outgoing (cbo_out), incoming (cbo_in) and either way (cbo_bi).
+        Also returns q_all per method (methods of its class sharing an accessed
+        attribute with it)."""
+        out = np.zeros(self.n_classes, dtype=VARIANT_DTYPE)
+        q_all = np.zeros(max(self.n_methods, 1), dtype=np.int32)
+        if _load().or_class_variants(self._h, threads or self.threads, out.ctypes.data, q_all.ctypes.data) != 0:
+            raise MemoryError("oracle: out of memory")
+        return out, q_all[: self.n_methods]
+
     def similarity(self, threads: int | None = None):
         """Jaccard similarity (Sec. II.A) of every method pair x < y sharing a
         property (called method or accessed attribute): arrays x, y, i =
@@ -243,6 +263,15 @@ class Oracle:
         if rc:
             raise ValueError("oracle: invalid candidate")
         return rec[0], int(a.value), int(b.value)
+
+
+def rank_classes(values, k: int):
+    """Classes ordered by a per-class value, largest first, equal values by
+    ascending class id (the order in which a rule takes the classes with the
+    highest LCOM or CBO, Sec. III.A); the first k ids."""
+    vals = [int(v) for v in values]
+    order = sorted(range(len(vals)), key=lambda C: (-vals[C], C))
+    return np.asarray(order[:k], dtype=np.int32)
 
 
 def r1_threshold(i, u, umax: int):

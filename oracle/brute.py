@@ -169,3 +169,33 @@ def record_hash(m, D, r):
 
 def digest(evals):
     return sum(record_hash(m, D, r) for (m, D), r in evals.items()) & MASK64
+
+
+def variants(sys, cbo_attrs=True):
+    """The LCOM and CBO variants of Sec. II.B per class, with Python sets:
+    sharing over every accessed attribute (P_all, Q_all, ck_all), the
+    unclamped differences pq and pq_all, and coupling outgoing, incoming and
+    either way (cbo_out, cbo_in, cbo_bi); and q_all per method."""
+    cls = [int(c) for c in sys.method_class]
+    mem = _members(cls, sys.n_classes)
+    base = class_metrics(sys, cls, cbo_attrs)
+    acc = [set(int(v) for v in sys.acc(x)) for x in range(sys.n_methods)]
+    calls = [set(int(v) for v in sys.calls(x)) for x in range(sys.n_methods)]
+    uses = [set() for _ in range(sys.n_classes)]      # classes each class uses
+    for x in range(sys.n_methods):
+        uses[cls[x]] |= {cls[t] for t in calls[x]}
+        if cbo_attrs:
+            uses[cls[x]] |= {int(sys.attr_class[a]) for a in acc[x]}
+    for Y in range(sys.n_classes):
+        uses[Y].discard(Y)
+    used_by = [{Y for Y in range(sys.n_classes) if E in uses[Y]} for E in range(sys.n_classes)]
+    q_all = [sum(1 for y in mem[cls[x]] if y != x and acc[x] & acc[y]) for x in range(sys.n_methods)]
+    out = []
+    for Y in range(sys.n_classes):
+        pairs = list(combinations(mem[Y], 2))
+        Q_all = sum(1 for x, y in pairs if acc[x] & acc[y])
+        P_all = len(pairs) - Q_all
+        out.append(dict(P_all=P_all, Q_all=Q_all, ck_all=max(P_all - Q_all, 0),
+                        pq=base[Y]["P"] - base[Y]["Q"], pq_all=P_all - Q_all,
+                        cbo_out=len(uses[Y]), cbo_in=len(used_by[Y]), cbo_bi=len(uses[Y] | used_by[Y])))
+    return out, q_all

@@ -948,3 +948,115 @@ double or_r1_threshold(const int32_t *pi, const int32_t *pu, int64_t n, int32_t 
   free(sum_i);
   return avg;
 }
+
+/* ------------------------------------------------------------------ */
+/* metric variants (Sec. II.B)                                          */
+/*
+ * The paper states LCOM as pairs sharing no attribute minus pairs sharing one
+ * without saying whose attributes, and CBO as the classes C uses; the CK suite
+ * it cites counts coupling in both directions.  The variants, by definition:
+ *   P_all, Q_all, ck_all: LCOM_CK with sharing over every accessed attribute
+ *                         (of any class), clamped at 0 like ck;
+ *   pq, pq_all:           the unclamped differences P - Q and P_all - Q_all;
+ *   cbo_out:              CBO as above (classes C uses);
+ *   cbo_in:               other classes that use C;
+ *   cbo_bi:               other classes coupled to C either way (|out u in|).
+ * q_all[x]: methods of x's class sharing an accessed attribute with x.
+ */
+typedef struct {
+  int64_t P_all, Q_all, ck_all, pq, pq_all, cbo_out, cbo_in, cbo_bi;
+} or_cv;
+
+/* is there an attribute (of any class) accessed by both x and y? (sorted merge) */
+static int shares_any(const or_input *in, int32_t x, int32_t y) {
+  int64_t i = in->acc_rowptr[x], ie = in->acc_rowptr[x + 1];
+  int64_t j = in->acc_rowptr[y], je = in->acc_rowptr[y + 1];
+  while (i < ie && j < je) {
+    int32_t u = in->acc_idx[i], v = in->acc_idx[j];
+    if (u < v) ++i;
+    else if (v < u) ++j;
+    else return 1;
+  }
+  return 0;
+}
+
+typedef struct {
+  const or_sys *s;
+  or_cv *out;
+  int32_t *q_all;
+  int32_t next, end;
+  pthread_mutex_t mu;
+} var_job;
+
+static void *var_worker(void *arg) {
+  var_job *j = (var_job *)arg;
+  const or_sys *s = j->s;
+  const or_input *in = &s->in;
+  for (;;) {
+    pthread_mutex_lock(&j->mu);
+    int32_t Y = j->next++;
+    pthread_mutex_unlock(&j->mu);
+    if (Y >= j->end) break;
+    const int32_t *mem = s->mem + s->mem_rowptr[Y];
+    int64_t n = s->mem_rowptr[Y + 1] - s->mem_rowptr[Y];
+    int64_t twice = 0; /* every sharing pair, once from each of its methods */
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t qx = 0;
+      for (int64_t k = 0; k < n; ++k)
+        if (k != i && shares_any(in, mem[i], mem[k])) ++qx;
+      j->q_all[mem[i]] = qx;
+      twice += qx;
+    }
+    or_cv *r = &j->out[Y];
+    r->Q_all = twice / 2;
+    r->P_all = n * (n - 1) / 2 - r->Q_all;
+    r->ck_all = r->P_all > r->Q_all ? r->P_all - r->Q_all : 0;
+    r->pq = s->cm[Y].P - s->cm[Y].Q;
+    r->pq_all = r->P_all - r->Q_all;
+  }
+  return NULL;
+}
+
+/* Fills out[n_classes] and q_all[n_methods]; 0 on success, -1 when out of memory. */
+int or_class_variants(const or_sys *s, int n_threads, or_cv *out, int32_t *q_all) {
+  const int32_t c = s->in.n_classes;
+  var_job j;
+  j.s = s; j.out = out; j.q_all = q_all; j.next = 0; j.end = c;
+  pthread_mutex_init(&j.mu, NULL);
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  pthread_t th[256];
+  for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, var_worker, &j);
+  for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+  pthread_mutex_destroy(&j.mu);
+  /* coupling both ways: out(Y) is row Y of the multigraph (ascending E);
+   * in(E) lists the rows Y that contain E, built by a counting pass over the
+   * rows in ascending Y, so each in-list is ascending too */
+  const int64_t u = s->mg_rowptr[c];
+  int64_t *in_ptr = (int64_t *)calloc((size_t)c + 1, sizeof(int64_t));
+  int32_t *in_row = (int32_t *)malloc(sizeof(int32_t) * ((size_t)u + 1));
+  int64_t *fill = (int64_t *)calloc((size_t)c + 1, sizeof(int64_t));
+  if (!in_ptr || !in_row || !fill) { free(in_ptr); free(in_row); free(fill); return -1; }
+  for (int64_t k = 0; k < u; ++k) in_ptr[s->mg_dst[k] + 1]++;
+  for (int32_t E = 0; E < c; ++E) in_ptr[E + 1] += in_ptr[E];
+  for (int32_t Y = 0; Y < c; ++Y)
+    for (int64_t k = s->mg_rowptr[Y]; k < s->mg_rowptr[Y + 1]; ++k) {
+      int32_t E = s->mg_dst[k];
+      in_row[in_ptr[E] + fill[E]++] = Y;
+    }
+  for (int32_t C = 0; C < c; ++C) {
+    int64_t i = s->mg_rowptr[C], ie = s->mg_rowptr[C + 1], k = in_ptr[C], ke = in_ptr[C + 1];
+    out[C].cbo_out = ie - i;
+    out[C].cbo_in = ke - k;
+    int64_t both = 0; /* size of the union of the two ascending lists */
+    while (i < ie || k < ke) {
+      if (k >= ke || (i < ie && s->mg_dst[i] < in_row[k])) ++i;
+      else if (i >= ie || in_row[k] < s->mg_dst[i]) ++k;
+      else { ++i; ++k; }
+      ++both;
+    }
+    out[C].cbo_bi = both;
+  }
+  free(in_ptr); free(in_row); free(fill);
+  return 0;
+}

@@ -529,3 +529,129 @@ def test_r3_hand_example():
     assert nhigh == 1
     assert list(rowptr) == [0, 2, 3, 3, 3] and list(dst) == [1, 2, 1]
     assert [tuple(int(v) for v in k) for k in kept] == [(0, 1, 0, 2, -1, 0)]
+
+
+# ---------------------------------------------------------------- metric variants (Sec. II.B)
+
+def _variants(s, cbo_attrs=True):
+    v, q_all = oracle.Oracle(s, cbo_attrs=cbo_attrs, threads=2).class_variants()
+    return v, q_all
+
+
+@pytest.mark.parametrize("k", [2, 3, 9])
+def test_variants_sharing_only_a_foreign_attribute(k):
+    """k methods of class 0 all read one attribute owned by class 1 and nothing
+    else: no pair shares an owned attribute (P = k(k-1)/2, Q = 0) but every pair
+    shares an accessed one (P_all = 0, Q_all = k(k-1)/2); unclamped
+    pq = k(k-1)/2 and pq_all = -k(k-1)/2, clamped ck_all = 0."""
+    s = make_system([0] * k + [1], [1], [[0]] * k + [[]], [[] for _ in range(k + 1)], n_classes=2)
+    v, q_all = _variants(s)
+    pairs = k * (k - 1) // 2
+    assert (v["P_all"][0], v["Q_all"][0], v["ck_all"][0]) == (0, pairs, 0)
+    assert (v["pq"][0], v["pq_all"][0]) == (pairs, -pairs)
+    assert list(q_all[:k]) == [k - 1] * k and q_all[k] == 0
+
+
+def test_variants_mix_of_own_and_foreign_sharing():
+    """Methods 0, 1 share an owned attribute, 1, 2 share a foreign one, 3 shares
+    nothing: Q = 1, Q_all = 2 of the 6 pairs; ck = 5 - 1 = 4, ck_all = 4 - 2 = 2."""
+    s = make_system([0, 0, 0, 0, 1], [0, 1, 0], [[0], [0, 1], [1], [2], []], [[] for _ in range(5)],
+                    n_classes=2)
+    cm = oracle.Oracle(s, threads=1).class_metrics()
+    v, q_all = _variants(s)
+    assert (cm["P"][0], cm["Q"][0], cm["ck"][0]) == (5, 1, 4)
+    assert (v["P_all"][0], v["Q_all"][0], v["ck_all"][0], v["pq"][0], v["pq_all"][0]) == (4, 2, 2, 4, 2)
+    assert list(q_all[:4]) == [1, 2, 1, 0]
+
+
+@pytest.mark.parametrize("k", [1, 4, 11])
+def test_variants_cbo_star_both_ways(k):
+    """k leaf classes each call one method of a hub class: the hub uses nothing
+    (cbo_out 0) and is used by k classes (cbo_in = cbo_bi = k); each leaf has
+    cbo_out = cbo_bi = 1, cbo_in = 0."""
+    mc = [0] + list(range(1, k + 1))
+    s = make_system(mc, [], [[] for _ in mc], [[]] + [[0] for _ in range(k)], n_classes=k + 1)
+    v, _ = _variants(s)
+    assert (v["cbo_out"][0], v["cbo_in"][0], v["cbo_bi"][0]) == (0, k, k)
+    assert all(v["cbo_out"][1:] == 1) and all(v["cbo_in"][1:] == 0) and all(v["cbo_bi"][1:] == 1)
+
+
+def test_variants_mutual_coupling_counts_once():
+    """Two classes calling each other: each is coupled to one class in each
+    direction and to one class either way (the union, not the sum)."""
+    s = make_system([0, 1], [], [[], []], [[1], [0]], n_classes=2)
+    v, _ = _variants(s)
+    assert list(v["cbo_out"]) == [1, 1] and list(v["cbo_in"]) == [1, 1] and list(v["cbo_bi"]) == [1, 1]
+
+
+def test_variants_attribute_coupling_switch():
+    """Reading another class's attribute couples both ways only when attribute
+    uses count (cbo_attrs)."""
+    s = make_system([0, 1], [1], [[0], []], [[], []], n_classes=2)
+    on, _ = _variants(s, cbo_attrs=True)
+    off, _ = _variants(s, cbo_attrs=False)
+    assert (on["cbo_out"][0], on["cbo_in"][1], on["cbo_bi"][1]) == (1, 1, 1)
+    assert (off["cbo_out"][0], off["cbo_in"][1], off["cbo_bi"][1]) == (0, 0, 0)
+
+
+@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("cbo_attrs", [True, False])
+def test_variants_match_brute_force(seed, cbo_attrs):
+    s = tiny_random(seed)
+    v, q_all = _variants(s, cbo_attrs)
+    bv, bq = brute.variants(s, cbo_attrs)
+    for f in oracle.VARIANT_FIELDS:
+        assert [int(x) for x in v[f]] == [r[f] for r in bv], f
+    assert [int(x) for x in q_all] == bq
+
+
+def test_variants_invariants_on_medium_sample():
+    """On a generated system: every coupled pair counts once on each side
+    (sum cbo_out = sum cbo_in = the multigraph's distinct pairs), max(out, in)
+    <= bi <= out + in, cbo_out equals CBO, owned sharing implies sharing
+    (Q <= Q_all, q <= q_all), and P_all + Q_all = n(n-1)/2."""
+    s = synth.generate(n_classes=400, n_methods=4000, n_attrs=2000, max_class=60, seed=5,
+                       lambda_acc=3.0, lambda_call=4.0, p_loc=0.7)
+    o = oracle.Oracle(s, threads=4)
+    cm, mm_ = o.class_metrics(), o.method_metrics()
+    v, q_all = o.class_variants()
+    rowptr, _, _ = o.multigraph()
+    assert v["cbo_out"].sum() == v["cbo_in"].sum() == rowptr[-1]
+    assert np.array_equal(v["cbo_out"], cm["cbo"])
+    assert np.all(np.maximum(v["cbo_out"], v["cbo_in"]) <= v["cbo_bi"])
+    assert np.all(v["cbo_bi"] <= v["cbo_out"] + v["cbo_in"])
+    assert np.all(cm["Q"] <= v["Q_all"]) and np.all(mm_["q"] <= q_all)
+    n = cm["n"]
+    assert np.array_equal(v["P_all"] + v["Q_all"], n * (n - 1) // 2)
+    assert np.array_equal(v["pq"], cm["P"] - cm["Q"])
+    assert np.array_equal(np.maximum(v["pq"], 0), cm["ck"])
+
+
+def test_variants_reduce_to_lcom_when_every_access_is_own():
+    """When every accessed attribute belongs to the accessing method's class,
+    sharing over accessed attributes is sharing over owned ones: Q_all = Q."""
+    s = synth.generate(n_classes=60, n_methods=900, n_attrs=500, max_class=40, seed=8,
+                       lambda_acc=3.0, lambda_call=2.0, p_loc=0.7)
+    keep = s.attr_class[s.acc_idx] == np.repeat(s.method_class, np.diff(s.acc_rowptr))
+    rows = [[int(a) for a, k in zip(s.acc(x), keep[s.acc_rowptr[x]:s.acc_rowptr[x + 1]]) if k]
+            for x in range(s.n_methods)]
+    own_only = make_system(s.method_class, s.attr_class, rows, [list(map(int, s.calls(x)))
+                                                              for x in range(s.n_methods)], s.n_classes)
+    o = oracle.Oracle(own_only, threads=2)
+    cm = o.class_metrics()
+    v, q_all = o.class_variants()
+    assert np.array_equal(v["Q_all"], cm["Q"]) and np.array_equal(q_all, o.method_metrics()["q"])
+    assert cm["Q"].sum() > 0
+
+
+def test_rank_classes_by_metric():
+    """Largest value first, equal values by ascending class id, first k."""
+    vals = np.array([3, -1, 7, 3, 0, 7, -5], dtype=np.int64)
+    assert list(oracle.rank_classes(vals, 7)) == [2, 5, 0, 3, 4, 1, 6]
+    assert list(oracle.rank_classes(vals, 3)) == [2, 5, 0]
+    assert list(oracle.rank_classes(vals, 0)) == []
+    s = tiny_random(4)
+    bv, _ = brute.variants(s)
+    by_pq = sorted(range(s.n_classes), key=lambda C: bv[C]["pq"], reverse=True)  # stable: ids ascending on ties
+    v, _ = _variants(s)
+    assert list(oracle.rank_classes(v["pq"], s.n_classes)) == by_pq
