@@ -242,7 +242,8 @@ class Oracle:
     def r1(self, mask: int = 3, min_improved: int = 2):
         """Rule R1 (Sec. III.A): every pair of methods in different classes
         whose similarity exceeds the system average (footnote of Sec. III.A)
-        proposes moving either method to the other's class; the candidates
+        proposes moving either method to the other's class or to another
+        class holding a method it calls; the candidates
         are evaluated (O1) and the kept ones, with LCOM of both the origin and
         the destination improved under the default criteria, returned.
         Returns (EvalResult, average, candidate rowptr, candidate dst,
@@ -288,12 +289,20 @@ def r1_threshold(i, u, umax: int):
 
 def r1_candidates(system, x, y, i, u, thr):
     """Moves proposed by the high pairs (i >= thr[u]) whose methods are in
-    different classes: x to the class of y and y to the class of x, each
-    (method, class) once, as candidate lists (rows sorted by class)."""
+    different classes (Sec. III.A, first rule): each method of such a pair to
+    the class of the other method, or to another class holding a method it
+    calls; each (method, class) once, as candidate lists (rows sorted by
+    class).  Returns (rowptr, dst, number of high pairs)."""
     mc = system.method_class
     high = (i >= thr[u]) & (mc[x] != mc[y])
-    m = np.concatenate([x[high], y[high]]).astype(np.int64)
-    d = np.concatenate([mc[y[high]], mc[x[high]]]).astype(np.int64)
+    m = [np.concatenate([x[high], y[high]]).astype(np.int64)]
+    d = [np.concatenate([mc[y[high]], mc[x[high]]]).astype(np.int64)]
+    for p in np.unique(np.concatenate([x[high], y[high]])):
+        called = np.unique(mc[system.calls(int(p))]).astype(np.int64)
+        called = called[called != mc[p]]
+        m.append(np.full(len(called), int(p), dtype=np.int64))
+        d.append(called)
+    m, d = np.concatenate(m), np.concatenate(d)
     key = np.unique(m * system.n_classes + d)
     m, d = key // system.n_classes, (key % system.n_classes).astype(np.int32)
     rowptr = np.zeros(system.n_methods + 1, dtype=np.int64)

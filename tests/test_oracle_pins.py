@@ -391,7 +391,8 @@ def test_similarity_brute_force(seed):
 def test_r1_threshold_and_candidates_by_hand():
     """The average of three values 1/2, 1/3, 2/3 is 1/2: only 2/3 is above it.
     Pairs in the same class propose nothing; a high pair across classes
-    proposes both moves."""
+    proposes both moves to the partner's class and each method's move to the
+    classes of the methods it calls."""
     i = np.array([1, 1, 2], dtype=np.int32)
     u = np.array([2, 3, 3], dtype=np.int32)
     avg, thr = oracle.r1_threshold(i, u, 3)
@@ -402,8 +403,9 @@ def test_r1_threshold_and_candidates_by_hand():
     y = np.array([1, 2, 3], dtype=np.int32)
     rowptr, dst, nh = oracle.r1_candidates(s, x, y, np.array([1, 1, 2], np.int32), np.array([1, 3, 3], np.int32),
                                            np.array([1, 1, 2, 2], np.int32))
-    # (0,1): same class; (1,2): 1/3 below; (2,3): 2/3 above, classes 1 and 2 -> 2 -> class 2, 3 -> class 1
-    assert nh == 1 and list(rowptr) == [0, 0, 0, 1, 2] and list(dst) == [2, 1]
+    # (0,1): same class; (1,2): 1/3 below; (2,3): 2/3 above, classes 1 and 2 -> 2 -> class 2, 3 -> class 1;
+    # both call method 0 (class 0) -> 2 -> class 0, 3 -> class 0; methods 0, 1 propose nothing
+    assert nh == 1 and list(rowptr) == [0, 0, 0, 2, 4] and list(dst) == [0, 2, 0, 1]
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -425,11 +427,14 @@ def test_r1_suggestions_brute_force(seed):
     py_avg = tot / len(sims) if sims else 0.0
     assert avg == py_avg and nvals == len(sims)
     mc = [int(v) for v in s.method_class]
-    cand = set()
+    cand, proposers = set(), set()
     for (x, y), (i, u) in sims.items():
         if i / u > py_avg and mc[x] != mc[y]:
             cand.add((x, mc[y]))
             cand.add((y, mc[x]))
+            proposers |= {x, y}
+    for p in proposers:
+        cand |= {(p, mc[int(t)]) for t in s.calls(p) if mc[int(t)] != mc[p]}
     got = {(m, int(dst[k])) for m in range(s.n_methods) for k in range(rowptr[m], rowptr[m + 1])}
     assert got == cand
     ev = brute.evaluate(s, mask=3, min_improved=2, candidates=sorted(cand))
