@@ -22,7 +22,10 @@ Measured in the same run and reported as nested keys:
            one CUDA graph per run against 256 sequential calls;
   serving  64 resident systems (seeds 100..163) answering 100,000 edit
            requests: capacity, p50/p99 latency at half of it, every 1,000th
-           state checked against the oracle.
+           state checked against the oracle;
+  rules    the similarity values of the large system (values/s, pairs
+           assessed/s), rule R1 on the medium system, rule R3 on the large
+           system, four rounds of non-conflicting moves on the medium system.
 The oracle checks run in a separate low-priority process started before the
 first GPU call, beside the GPU sections; the CPU baseline is timed after them.
 
@@ -63,7 +66,7 @@ L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant
 # kernel of each workload, from a one-pass ncu capture (None once the kernel
 # changes, until it is captured again)
-EVAL_CSR_TRAFFIC_MASK7 = None        # large restricted, eval_csr_grouped<records, kept>, all three metrics
+EVAL_CSR_TRAFFIC_MASK7 = 985741824   # large restricted, eval_csr_grouped<records, kept>, all three metrics
 EVAL_DENSE_TRAFFIC = 4771699968      # medium, eval_dense<records, kept>
 
 
@@ -690,6 +693,136 @@ def run_serving(args, local_rank, verifier):
     return out, snaps
 
 
+# ---------------------------------------------------------------- nested: similarity, rules R1 and R3, sequences
+
+SIM_ROWS = 40
+
+
+def job_oracle_similarity_rows(params, rows):
+    """The oracle's similarity values of sampled methods (every partner)."""
+    import oracle
+    from paper_1308_4011_b300 import synth
+    s = synth.generate(**params)
+    o = oracle.Oracle(s)
+    out = [tuple(a.tolist() for a in o.similarity_row(int(q))) for q in rows]
+    o.close()
+    return out
+
+
+def job_oracle_r1(params, mask, mi, topk):
+    import oracle
+    from paper_1308_4011_b300 import synth
+    s = synth.generate(**params)
+    o = oracle.Oracle(s)
+    res, avg, rp, dst, nv, nh = o.r1(mask=mask, min_improved=mi)
+    o.close()
+    return {"n_values": nv, "n_high": nh, "n_candidates": len(dst), "average": avg, "n_kept": res.n_kept,
+            "top": [(int(k["m"]), int(k["d"])) for k in res.kept[:topk]]}
+
+
+def job_oracle_r3(params):
+    import oracle
+    from paper_1308_4011_b300 import synth
+    kept, rp, dst, nh = oracle.r3(synth.generate(**params))
+    return {"n_kept": len(kept), "n_candidates": len(dst), "n_high": nh,
+            "top": [tuple(int(v) for v in k) for k in kept[:TOPK]]}
+
+
+def job_oracle_sequence(params, mask, mi, rounds):
+    import oracle
+    from paper_1308_4011_b300 import synth
+    seq, _ = oracle.sequence(synth.generate(**params), mask=mask, min_improved=mi, rounds=rounds)
+    return seq
+
+
+def run_rules(args, local_rank, verifier):
+    """Similarity values of the large system (the term that dominates the
+    paper's value count and its timed workload), rule R1 on the medium
+    system, rule R3 on the large system, four rounds of non-conflicting moves
+    on the medium system; each checked against the oracle."""
+    import torch
+    from paper_1308_4011_b300 import mmref, synth
+
+    dev = torch.device("cuda", local_rank)
+    out, jobs = {}, {}
+    peak, _ = _peaks()
+    large_p, medium_p = dict(synth.LARGE), dict(synth.MEDIUM)
+    large, medium = synth.generate(**large_p), synth.generate(**medium_p)
+    rows = np.random.default_rng(11).choice(large.n_methods, size=SIM_ROWS, replace=False)
+    if verifier:
+        jobs["sim"] = verifier.submit(job_oracle_similarity_rows, large_p, rows)
+        jobs["r1"] = verifier.submit(job_oracle_r1, medium_p, MASK_LCOM, MIN_IMPROVED, TOPK)
+        jobs["r3"] = verifier.submit(job_oracle_r3, large_p)
+        jobs["seq"] = verifier.submit(job_oracle_sequence, medium_p, MASK_LCOM, MIN_IMPROVED, 4)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            t = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize(dev)
+            ts.append(time.perf_counter() - t)
+        return statistics.median(ts), r
+
+    g = mmref.load_synth(large, device=True)
+    t, info = timed(lambda: mmref.similarity_info(g), 5)  # computed on the device, nothing read back
+    (x, y, i, u), _ = mmref.similarity(g)
+    M = large.n_methods
+    n_co, n_val = info["n_cooccurrences"], info["n_values"]
+    passes = (int(M * M - 1).bit_length() + 7) // 8
+    alg = n_co * 8 * (2 + 2 * passes) + n_val * 16  # keys written, sorted (read + write per pass), read; values
+    sim_rows = []
+    for q in rows:
+        sel = (x == q) | (y == q)
+        partner = np.where(x[sel] == q, y[sel], x[sel])
+        order = np.argsort(partner)
+        sim_rows.append((partner[order].tolist(), i[sel][order].tolist(), u[sel][order].tolist()))
+    out["similarity_large"] = {
+        "workload": "large system: every method pair sharing a called method or an accessed attribute",
+        "seconds": t, "n_values": n_val, "n_cooccurrences": n_co, "average": info["average"],
+        "values_per_s": n_val / t, "pairs_assessed_per_s": M * (M - 1) / 2 / t,
+        "roofline": {"bound": "hbm", "achieved": round(alg / t / 1e9, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(alg / t / 1e9 / peak, 4), "algorithmic_bytes": alg,
+                     "note": "whole call (posting lists, keys, radix sort, runs, count read-backs) against the "
+                             "bytes of its keys and values"}}
+    mmref.compute_metrics(g, None, None)
+    t, (top3, nk3, nc3, nh3) = timed(lambda: mmref.suggest_r3(g, TOPK), 5)
+    out["r3_large"] = {"seconds": t, "n_candidates": nc3, "n_kept": nk3, "n_high_classes": nh3,
+                       "candidates_per_s": nc3 / t}
+    r3_got = {"n_kept": nk3, "n_candidates": nc3, "n_high": nh3, "top": [tuple(int(v) for v in k) for k in top3]}
+    g.free()
+    g = mmref.load_synth(medium, device=True)
+    mmref.compute_metrics(g, None, None)
+    t, (top1, nk1, nm1, info1) = timed(lambda: mmref.suggest_r1(g, TOPK, MASK_LCOM, MIN_IMPROVED), 5)
+    out["r1_medium"] = {"seconds": t, "n_values": info1["n_values"], "n_high": info1["n_high"],
+                        "n_candidates": info1["n_candidates"], "n_kept": nk1}
+    r1_got = {"n_values": info1["n_values"], "n_high": info1["n_high"], "n_candidates": info1["n_candidates"],
+              "average": info1["average"], "n_kept": nk1, "top": [(int(k["m"]), int(k["d"])) for k in top1]}
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    seq = mmref.apply_sequence(g, 4, MASK_LCOM, MIN_IMPROVED)
+    t = time.perf_counter() - t0
+    out["sequence_medium"] = {"seconds": t, "rounds": 4, "moves_applied": len(seq),
+                              "per_round": np.bincount(seq["round"], minlength=4).tolist() if len(seq) else []}
+    seq_got = [tuple(int(v) for v in r) for r in seq]
+    g.free()
+    return out, (jobs, sim_rows, r1_got, r3_got, seq_got)
+
+
+def collect_rules(check):
+    jobs, sim_rows, r1_got, r3_got, seq_got = check
+    if not jobs:
+        return None
+    ok_sim = jobs["sim"].get() == sim_rows
+    ok_r1 = jobs["r1"].get() == r1_got
+    ok_r3 = jobs["r3"].get() == r3_got
+    ok_seq = jobs["seq"].get() == seq_got
+    return {"ok": bool(ok_sim and ok_r1 and ok_r3 and ok_seq), "similarity_sampled_rows": bool(ok_sim),
+            "similarity_rows": SIM_ROWS, "r1": bool(ok_r1), "r3": bool(ok_r3), "sequence": bool(ok_seq)}
+
+
 # ---------------------------------------------------------------- the reference arm
 
 def run_reference(args, rank, world):
@@ -746,8 +879,10 @@ def _check_result(kind, check):
     return {"ok": bool(ok), "n_kept": nk}
 
 
-def collect_checks(large_checks, medium_check, batched_check, serving_snaps):
-    out = {"large": {}, "medium": None, "batched": None, "serving": None}
+def collect_checks(large_checks, medium_check, batched_check, serving_snaps, rules_check=None):
+    out = {"large": {}, "medium": None, "batched": None, "serving": None, "rules": None}
+    if rules_check is not None:
+        out["rules"] = collect_rules(rules_check)
     for mask, chk in large_checks.items():
         out["large"][f"mask{mask}"] = _check_result("large", chk)
     if medium_check is not None:
@@ -791,7 +926,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sections", default="medium,batched,serving",
+    ap.add_argument("--sections", default="medium,batched,serving,rules",
                     help="nested sections measured beside the bench line (comma list; '' for none)")
     ap.add_argument("--requests", type=int, default=100000)
     ap.add_argument("--stress-requests", type=int, default=5000)
@@ -817,16 +952,19 @@ def main():
     # the nested sections run on one GPU only (rank 0 of a single-rank job)
     sections = [x for x in args.sections.split(",") if x] if world == 1 else []
     t_start = time.perf_counter()
-    nested, serving_snaps, batched_check, medium_check = {}, None, None, None
+    nested, serving_snaps, batched_check, medium_check, rules_check = {}, None, None, None, None
     if "serving" in sections:
         nested["serving"], serving_snaps = run_serving(args, local_rank, verifier)
     if "batched" in sections:
         nested["batched"], batched_check = run_batched(args, local_rank, verifier)
     if "medium" in sections:
         nested["medium"], medium_check = run_medium(args, local_rank, verifier)
+    if "rules" in sections:
+        nested["rules"], rules_check = run_rules(args, local_rank, verifier)
     line, large_checks, system = run_large(args, rank, world, local_rank, verifier, dist)
     if rank == 0:
-        checks = collect_checks(large_checks, medium_check, batched_check, serving_snaps) if verifier else None
+        checks = collect_checks(large_checks, medium_check, batched_check, serving_snaps,
+                                rules_check) if verifier else None
         if verifier:
             verifier.close()
         line["verified_vs_oracle"] = checks
@@ -838,7 +976,8 @@ def main():
         print(json.dumps(line), flush=True)
         results = []
         if checks is not None:
-            results = [r for r in checks["large"].values()] + [checks[k] for k in ("medium", "batched", "serving")]
+            results = [r for r in checks["large"].values()] + [checks[k] for k in ("medium", "batched", "serving",
+                                                                                      "rules")]
         if any(r is not None and not r["ok"] for r in results):
             print(json.dumps({"error": "GPU results differ from the oracle", "checks": checks}), file=sys.stderr)
             sys.exit(3)

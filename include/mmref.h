@@ -64,9 +64,23 @@ typedef enum {
   MM_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
   MM_ENOTFOUND = 4,  /* edit removes an edge that does not exist */
   MM_EEXIST = 5,     /* edit adds an edge that already exists */
-  MM_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  MM_ETIMEOUT = 6,   /* a bounded device-side wait gave up (see below) */
   MM_EBUDGET = 7     /* admission refused: memory budget exceeded */
 } mm_status;
+
+/* Bounded waits.  The one device-side wait of the library is the look-back
+ * of its one-pass exclusive scan (Merrill and Garland, 2016), used by load,
+ * metrics, lists, similarity and the rules.  It polls at most about a second;
+ * when it runs out, the block sums the input before its tile itself, so the
+ * scan's output and everything computed from it stay exact, and it sets the
+ * fault word of the system (or batch) whose call queued the scan.  Every
+ * system and batch has its own word: a give-up is reported to that handle
+ * only, as MM_ETIMEOUT from its next call that synchronises (mm_load_system,
+ * mm_compute_metrics and mm_export_metrics with host outputs,
+ * mm_evaluate_moves with host outputs, mm_suggest_moves,
+ * mm_suggest_moves_noalloc, mm_similarity, mm_suggest_r1, mm_suggest_r3,
+ * mm_apply_edit, mm_apply_sequence, mm_batch_run), which clears it.  The
+ * outputs of that call are written before the status is returned. */
 
 enum { MM_PTR_HOST = 0, MM_PTR_DEVICE = 1 };
 
@@ -328,7 +342,8 @@ MMREF_API mm_status mm_similarity(mm_system *sys, int32_t *x, int32_t *y, int32_
  * values (the average in double precision, summed over u ascending of
  * sum(i)/u and divided by the number of values; a pair is above it when
  * (double)i / (double)u is greater) proposes moving either method to the
- * other's class.  The distinct proposed moves are evaluated and filtered by
+ * other's class, or to another class holding a method it calls.  The
+ * distinct proposed moves are evaluated and filtered by
  * crit exactly as mm_suggest_moves does with them as candidate lists (R1
  * itself asks for LCOM improved in both the origin and the destination:
  * metric_mask = MM_LCOM_CK | MM_LCOM_HS, min_improved = 2).  Outputs as
@@ -358,6 +373,57 @@ typedef struct {
 } mm_r3_move;
 MMREF_API mm_status mm_suggest_r3(mm_system *sys, int32_t k, mm_r3_move *out_topk, int64_t *n_kept,
                                   int64_t *n_candidates, int32_t *n_high_classes);
+
+/*
+ * Metric variants (Sec. II.B).  The paper defines LCOM as the method pairs
+ * sharing no attribute minus the pairs sharing one, without saying whose
+ * attributes, and CBO as the classes C uses; the CK suite it cites counts
+ * coupling in both directions.  Per class:
+ *   P_all, Q_all   pairs of C's methods sharing no accessed attribute / at
+ *                  least one, over the attributes of every class (the
+ *                  mm_class_metrics P, Q count only C's own attributes);
+ *   lcom_ck_all    max(P_all - Q_all, 0);
+ *   lcom_pq        P - Q unclamped (negative when sharing pairs dominate);
+ *   lcom_pq_all    P_all - Q_all unclamped;
+ *   cbo_out        CBO as in mm_class_metrics (other classes C uses);
+ *   cbo_in         other classes that use C (same uses: calls, and attribute
+ *                  accesses when the system counts them);
+ *   cbo_bi         other classes coupled to C either way, |out u in|.
+ * out (n_classes entries) and out_q_all (n_methods: methods of m's class
+ * sharing an accessed attribute with m) are both in host or both in device
+ * memory per out_kind; either may be NULL.  Needs mm_compute_metrics first.
+ * Errors: MM_EINVAL (NULL system, metrics not computed, bad out_kind),
+ * MM_ENOMEM, MM_ECUDA.  Synchronises the stream when out_kind is host.
+ */
+typedef struct {
+  int64_t P_all, Q_all, lcom_ck_all, lcom_pq, lcom_pq_all;
+  int32_t cbo_out, cbo_in, cbo_bi, reserved;
+} mm_class_variants; /* 56 bytes */
+MMREF_API mm_status mm_metric_variants(mm_system *sys, mm_class_variants *out, int32_t *out_q_all,
+                                       int32_t out_kind);
+
+/*
+ * Classes ranked by one metric, largest first, equal values by ascending
+ * class id (the order in which a rule takes the classes of highest LCOM or
+ * CBO, Sec. III.A).  metric is one of MM_RANK_*; out_ids (k entries) and
+ * out_values (k entries, nullable) receive the first min(k, n_classes)
+ * classes and their values, both in host or both in device memory per
+ * out_kind.  Needs mm_compute_metrics first.  Errors: MM_EINVAL (NULL system,
+ * metrics not computed, unknown metric, k < 0, out_ids NULL with k > 0, bad
+ * out_kind), MM_ENOMEM, MM_ECUDA.  Synchronises the stream when out_kind is
+ * host.
+ */
+enum {
+  MM_RANK_LCOM_CK = 1,     /* max(P - Q, 0) */
+  MM_RANK_LCOM_PQ = 2,     /* P - Q, unclamped */
+  MM_RANK_LCOM_CK_ALL = 3, /* max(P_all - Q_all, 0) */
+  MM_RANK_LCOM_PQ_ALL = 4, /* P_all - Q_all, unclamped */
+  MM_RANK_CBO = 5,         /* classes used */
+  MM_RANK_CBO_IN = 6,      /* classes using it */
+  MM_RANK_CBO_BI = 7       /* classes coupled either way */
+};
+MMREF_API mm_status mm_rank_classes(mm_system *sys, int32_t metric, int32_t k, int32_t *out_ids,
+                                    int64_t *out_values, int32_t out_kind);
 
 /*
  * Batched evaluation (no counterpart in the paper; the paper analyses one
@@ -547,10 +613,21 @@ MMREF_API int64_t mm_launch_count(void);
 /* Failure-detection self test of the bounded device-side waits (the look-back
  * of the exclusive scan used by load, metrics and lists; Merrill and Garland,
  * 2016).  Runs one scan tile on the current device whose predecessor tile is
- * never processed, so its wait gives up after about a second; returns
- * MM_ETIMEOUT when the host read the fault flag as designed (and clears it),
- * MM_OK if the wait did not run out, MM_ECUDA on a CUDA error.  Needs a GPU. */
+ * never processed, so its wait gives up after about a second and its
+ * fallback sums the predecessor's input; returns MM_ETIMEOUT when the fault
+ * word was set and the output is the exact prefix sum (the designed outcome),
+ * MM_OK if the wait did not run out, MM_ECUDA if the output is wrong or on a
+ * CUDA error.  Uses its own buffers and fault word.  Needs a GPU. */
 MMREF_API mm_status mm_selftest_bounded_wait(void);
+
+/* Test hook for the bounded waits inside a real pipeline: the next n scans of
+ * more than 16,384 elements queued by calls on sys hold back their first
+ * tile's state until another tile's look-back has run out (polls cut to
+ * 4,096), so those tiles take the fallback and set sys's fault word.  The
+ * results stay exact; the next synchronising call on sys returns MM_ETIMEOUT
+ * (see "Bounded waits" above).  n = 0 ends it.  Errors: MM_EINVAL for a NULL
+ * system or n < 0.  No device work. */
+MMREF_API mm_status mm_selftest_stall_scans(mm_system *sys, int32_t n);
 
 #ifdef __cplusplus
 }

@@ -38,6 +38,7 @@ struct mm_batch {
   void *mem = nullptr;
   void *d_items = nullptr;
   unsigned long long *d_next = nullptr, *d_digest = nullptr, *d_kcount = nullptr, *d_tmp = nullptr;
+  uint32_t *d_fault = nullptr;  // fault word of the bounded waits inside the batch's graph
   mm_move *d_kept = nullptr;
   uint8_t *d_marks = nullptr;
   std::vector<int64_t> mark_off;
@@ -164,6 +165,7 @@ void drop_graph(mm_batch *b) {
 }
 
 void capture(mm_batch *b, bool digest) {
+  WaitScope wait(b->d_fault, nullptr);  // the graph's scans record into the batch's word
   if (b->exec[digest]) cudaGraphExecDestroy(b->exec[digest]);
   b->exec[digest] = nullptr;
   // run once outside capture so every scratch buffer already has its size; the
@@ -233,6 +235,8 @@ MMREF_API mm_status mm_batch_create(mm_system *const *systems, int32_t n, const 
     p += items;
     unsigned long long *c = reinterpret_cast<unsigned long long *>(p);
     b->d_next = c;
+    b->d_fault = reinterpret_cast<uint32_t *>(c + 7);
+    MM_CUDA_TRY(cudaMemsetAsync(b->d_fault, 0, sizeof(uint32_t), b->stream));
     b->d_digest = c + 8;
     b->d_kcount = c + 8 + n;
     b->d_tmp = c + 8 + 2 * n;
@@ -341,7 +345,10 @@ MMREF_API mm_status mm_batch_run(mm_batch *b, uint64_t *digests, int64_t *n_kept
     std::vector<unsigned long long> kc(b->n);
     MM_CUDA_TRY(cudaMemcpyAsync(kc.data(), b->d_kcount, sizeof(unsigned long long) * b->n, cudaMemcpyDeviceToHost,
                                 b->stream));
+    uint32_t hfault = 0;
+    read_wait_fault(&hfault, b->d_fault, b->stream);
     MM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    raise_wait_fault(hfault, b->d_fault, b->stream, "batch_run");
     if (n_kept)
       for (int32_t i = 0; i < b->n; ++i) n_kept[i] = (int64_t)kc[i];
     join(b->user_stream, b->stream, b->ev);
@@ -357,6 +364,7 @@ MMREF_API mm_status mm_batch_suggestions(mm_batch *b, int32_t i, int32_t k, mm_m
       throw MmError{MM_EINVAL, "batch_suggestions: bad arguments"};
     if (out_kind != MM_PTR_HOST && out_kind != MM_PTR_DEVICE) throw MmError{MM_EINVAL, "batch_suggestions: bad out_kind"};
     if (!b->ran) throw MmError{MM_EINVAL, "batch_suggestions: call mm_batch_run first"};
+    WaitScope wait(b->d_fault, nullptr);  // reported by the batch's next run
     join(b->stream, b->user_stream, b->ev);
     unsigned long long K = 0;
     MM_CUDA_TRY(cudaMemcpyAsync(&K, b->d_kcount + i, sizeof(K), cudaMemcpyDeviceToHost, b->stream));

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -45,12 +46,19 @@ void use_device(mm_system *s) {
   if (cur != s->device) MM_CUDA_TRY(cudaSetDevice(s->device));
 }
 
+// For the duration of an entry point: the system's device is current and its
+// fault word receives the bounded waits that run out.
+struct SystemScope {
+  explicit SystemScope(mm_system *s) : wait(s->d_fault, &s->test_stall_scans) { use_device(s); }
+  WaitScope wait;
+};
+
 // Free everything a system holds: device memory in stream order on its stream,
 // then its events (released by the runtime once their last use completes).
 void release_system(mm_system *s) {
   s->arena.release();
   for (Scratch *w : {&s->sort_ws, &s->eval_ws, &s->stage_ws, &s->kept_ws, &s->keyed_ws, &s->edit_ws, &s->sim_ws,
-                     &s->sim_keys_ws, &s->sim_val_ws, &s->r1_ws,
+                     &s->sim_keys_ws, &s->sim_val_ws, &s->r1_ws, &s->var_ws, &s->var_keys_ws,
                      &s->union_ws, &s->side_eval[0], &s->side_eval[1], &s->side_eval[2], &s->side_sort[0],
                      &s->side_sort[1], &s->side_sort[2], &s->side_union[0], &s->side_union[1], &s->side_union[2]})
     w->release(s->stream);
@@ -61,14 +69,17 @@ void release_system(mm_system *s) {
 }
 
 void keep_pool_memory(int device) {
-  static bool done[64] = {false};
-  if (device < 0 || device >= 64 || done[device]) return;
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
-    uint64_t thr = UINT64_MAX;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-  }
-  done[device] = true;
+  // Serving threads may load their first systems on one device at the same
+  // time: one flag per device, set once under call_once.
+  static std::once_flag done[64];
+  if (device < 0 || device >= 64) return;
+  std::call_once(done[device], [device] {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  });
 }
 
 // Up to six device-to-device copies (sizes in bytes, multiples of 4) in one launch.
@@ -127,6 +138,7 @@ void allocate_load_buffers(mm_system *s) {
   s->fan_in = a.get<int32_t>(M);
   s->d_u64 = a.get<unsigned long long>(32);
   s->d_err = s->d_u64 ? reinterpret_cast<uint32_t *>(s->d_u64 + 6) : nullptr;  // cleared with the load summary
+  s->d_fault = s->d_u64 ? reinterpret_cast<uint32_t *>(s->d_u64 + 9) : nullptr;  // likewise
 }
 
 void allocate_compute_buffers(mm_system *s) {
@@ -280,6 +292,7 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     s->arena.sizing = false;
     s->arena.reserve(s->arena.sized);
     allocate_load_buffers(s);
+    WaitScope wait(s->d_fault, &s->test_stall_scans);
     cudaStream_t stv = s->stream;
     if (desc->ptr_kind == MM_PTR_DEVICE) {  // one copy kernel for the six device arrays
       CopySegs cs{};
@@ -321,7 +334,7 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
 mm_status mm_set_stream(mm_system *s, void *cuda_stream) {
   return guarded([&] {
     if (!s) throw MmError{MM_EINVAL, "set_stream: NULL system"};
-    use_device(s);
+    SystemScope scope(s);
     // order the new stream after everything queued on the old one
     cudaStream_t ns = static_cast<cudaStream_t>(cuda_stream);
     if (ns != s->stream) {
@@ -341,13 +354,14 @@ mm_status mm_compute_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_me
     if (!s) throw MmError{MM_EINVAL, "compute_metrics: NULL system"};
     if ((out_c || out_m) && out_kind != MM_PTR_HOST && out_kind != MM_PTR_DEVICE)
       throw MmError{MM_EINVAL, "compute_metrics: bad out_kind"};
-    use_device(s);
+    SystemScope scope(s);
     s->kept_valid = false;
     build_structures(s);
     build_metrics(s);
     build_move_precompute(s);
     s->metrics_ready = true;
     export_metrics(s, out_c, out_m, out_kind);
+    if ((out_c || out_m) && out_kind == MM_PTR_HOST) check_wait_fault(s->d_fault, s->stream, "compute_metrics");
   });
 }
 
@@ -357,8 +371,9 @@ mm_status mm_export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_met
     if (!s->metrics_ready) throw MmError{MM_EINVAL, "export_metrics: no metrics computed yet"};
     if ((out_c || out_m) && out_kind != MM_PTR_HOST && out_kind != MM_PTR_DEVICE)
       throw MmError{MM_EINVAL, "export_metrics: bad out_kind"};
-    use_device(s);
+    SystemScope scope(s);
     export_metrics(s, out_c, out_m, out_kind);
+    if ((out_c || out_m) && out_kind == MM_PTR_HOST) check_wait_fault(s->d_fault, s->stream, "export_metrics");
   });
 }
 
@@ -367,8 +382,9 @@ mm_status mm_evaluate_moves(mm_system *s, const mm_criteria *crit, const mm_cand
   return guarded([&] {
     if (!s || !crit) throw MmError{MM_EINVAL, "evaluate_moves: NULL system or criteria"};
     if (!s->metrics_ready) throw MmError{MM_EINVAL, "evaluate_moves: call mm_compute_metrics first"};
-    use_device(s);
+    SystemScope scope(s);
     evaluate_moves(s, *crit, cands, records, digest, out_kind);
+    if ((records || digest) && out_kind == MM_PTR_HOST) check_wait_fault(s->d_fault, s->stream, "evaluate_moves");
   });
 }
 
@@ -377,7 +393,7 @@ mm_status mm_suggest_moves(mm_system *s, const mm_criteria *crit, const mm_candi
   return guarded([&] {
     if (!s || !crit) throw MmError{MM_EINVAL, "suggest_moves: NULL system or criteria"};
     if (!s->metrics_ready) throw MmError{MM_EINVAL, "suggest_moves: call mm_compute_metrics first"};
-    use_device(s);
+    SystemScope scope(s);
     suggest_moves(s, *crit, cands, k, out_topk, out_kind, n_kept, n_methods_with_kept);
   });
 }
@@ -386,7 +402,7 @@ mm_status mm_last_eval_ms(mm_system *s, float *ms) {
   return guarded([&] {
     if (!s || !ms) throw MmError{MM_EINVAL, "last_eval_ms: NULL argument"};
     if (!s->eval_timed) throw MmError{MM_EINVAL, "last_eval_ms: no evaluation kernel has run on this handle"};
-    use_device(s);
+    SystemScope scope(s);
     MM_CUDA_TRY(cudaEventSynchronize(s->eval_ev[1]));
     MM_CUDA_TRY(cudaEventElapsedTime(ms, s->eval_ev[0], s->eval_ev[1]));
   });
@@ -410,7 +426,7 @@ mm_status mm_similarity(mm_system *s, int32_t *x, int32_t *y, int32_t *inter, in
     if (cap < 0) throw MmError{MM_EINVAL, "similarity: cap < 0"};
     if ((x || y || inter || uni) && out_kind != MM_PTR_HOST && out_kind != MM_PTR_DEVICE)
       throw MmError{MM_EINVAL, "similarity: bad out_kind"};
-    use_device(s);
+    SystemScope scope(s);
     compute_similarity(s);
     const int64_t n = std::min<int64_t>(cap, s->sim_n);
     const cudaMemcpyKind kind = out_kind == MM_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -418,7 +434,7 @@ mm_status mm_similarity(mm_system *s, int32_t *x, int32_t *y, int32_t *inter, in
     int32_t *dst[4] = {x, y, inter, uni};
     for (int k = 0; k < 4; ++k)
       if (dst[k] && n > 0) MM_CUDA_TRY(cudaMemcpyAsync(dst[k], src[k], sizeof(int32_t) * (size_t)n, kind, s->stream));
-    MM_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    check_wait_fault(s->d_fault, s->stream, "similarity");
     fill_similarity_info(s, info, 0, 0);
   });
 }
@@ -428,7 +444,7 @@ mm_status mm_suggest_r1(mm_system *s, const mm_criteria *crit, int32_t k, mm_mov
   return guarded([&] {
     if (!s || !crit) throw MmError{MM_EINVAL, "suggest_r1: NULL system or criteria"};
     if (!s->metrics_ready) throw MmError{MM_EINVAL, "suggest_r1: call mm_compute_metrics first"};
-    use_device(s);
+    SystemScope scope(s);
     compute_similarity(s);
     int64_t n_high = 0, n_cand = 0;
     build_r1_candidates(s, &n_high, &n_cand);
@@ -445,7 +461,7 @@ mm_status mm_suggest_r1(mm_system *s, const mm_criteria *crit, int32_t k, mm_mov
 mm_status mm_system_info_get(mm_system *s, mm_system_info *info) {
   return guarded([&] {
     if (!s || !info) throw MmError{MM_EINVAL, "system_info: NULL argument"};
-    use_device(s);
+    SystemScope scope(s);
     info->n_classes = s->c;
     info->n_methods = s->M;
     info->n_attrs = s->A;
@@ -481,8 +497,9 @@ void mm_free_system(mm_system *s) {
 mm_status mm_apply_edit(mm_system *s, const mm_edit *e) {
   return guarded([&] {
     if (!s || !e) throw MmError{MM_EINVAL, "apply_edit: NULL argument"};
-    use_device(s);
+    SystemScope scope(s);
     apply_edit(s, *e);
+    check_wait_fault(s->d_fault, s->stream, "apply_edit");
   });
 }
 
@@ -490,8 +507,9 @@ mm_status mm_suggest_r3(mm_system *s, int32_t k, mm_r3_move *out_topk, int64_t *
                         int32_t *n_high_classes) {
   return guarded([&] {
     if (!s) throw MmError{MM_EINVAL, "suggest_r3: NULL system"};
-    use_device(s);
+    SystemScope scope(s);
     suggest_r3(s, k, out_topk, n_kept, n_candidates, n_high_classes);
+    check_wait_fault(s->d_fault, s->stream, "suggest_r3");
   });
 }
 
@@ -499,8 +517,49 @@ mm_status mm_apply_sequence(mm_system *s, const mm_criteria *crit, int32_t round
                             mm_applied_move *out, int64_t cap, int64_t *n_applied) {
   return guarded([&] {
     if (!s || !crit) throw MmError{MM_EINVAL, "apply_sequence: NULL system or criteria"};
-    use_device(s);
+    SystemScope scope(s);
     apply_sequence(s, *crit, rounds, per_round, out, cap, n_applied);
+    check_wait_fault(s->d_fault, s->stream, "apply_sequence");
+  });
+}
+
+mm_status mm_metric_variants(mm_system *s, mm_class_variants *out, int32_t *out_q_all, int32_t out_kind) {
+  return guarded([&] {
+    if (!s) throw MmError{MM_EINVAL, "metric_variants: NULL system"};
+    if (!s->metrics_ready) throw MmError{MM_EINVAL, "metric_variants: call mm_compute_metrics first"};
+    if ((out || out_q_all) && out_kind != MM_PTR_HOST && out_kind != MM_PTR_DEVICE)
+      throw MmError{MM_EINVAL, "metric_variants: bad out_kind"};
+    SystemScope scope(s);
+    mm_class_variants *var = nullptr;
+    int32_t *q_all = nullptr;
+    compute_variants(s, &var, &q_all);
+    const cudaMemcpyKind dir = out_kind == MM_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (out && s->c > 0)
+      MM_CUDA_TRY(cudaMemcpyAsync(out, var, sizeof(mm_class_variants) * (size_t)s->c, dir, s->stream));
+    if (out_q_all && s->M > 0)
+      MM_CUDA_TRY(cudaMemcpyAsync(out_q_all, q_all, sizeof(int32_t) * (size_t)s->M, dir, s->stream));
+    if ((out || out_q_all) && out_kind == MM_PTR_HOST) check_wait_fault(s->d_fault, s->stream, "metric_variants");
+  });
+}
+
+mm_status mm_rank_classes(mm_system *s, int32_t metric, int32_t k, int32_t *out_ids, int64_t *out_values,
+                          int32_t out_kind) {
+  return guarded([&] {
+    if (!s) throw MmError{MM_EINVAL, "rank_classes: NULL system"};
+    if (!s->metrics_ready) throw MmError{MM_EINVAL, "rank_classes: call mm_compute_metrics first"};
+    if (metric < MM_RANK_LCOM_CK || metric > MM_RANK_CBO_BI) throw MmError{MM_EINVAL, "rank_classes: unknown metric"};
+    if (k < 0 || (k > 0 && !out_ids)) throw MmError{MM_EINVAL, "rank_classes: bad k or out_ids"};
+    if (out_kind != MM_PTR_HOST && out_kind != MM_PTR_DEVICE) throw MmError{MM_EINVAL, "rank_classes: bad out_kind"};
+    SystemScope scope(s);
+    rank_classes(s, metric, k, out_ids, out_values, out_kind);
+    if (out_kind == MM_PTR_HOST) check_wait_fault(s->d_fault, s->stream, "rank_classes");
+  });
+}
+
+mm_status mm_selftest_stall_scans(mm_system *s, int32_t n) {
+  return guarded([&] {
+    if (!s || n < 0) throw MmError{MM_EINVAL, "selftest_stall_scans: NULL system or n < 0"};
+    s->test_stall_scans = n;
   });
 }
 
@@ -508,7 +567,7 @@ mm_status mm_export_system(mm_system *s, int32_t *method_class, int32_t *attr_cl
                            int32_t *acc_idx, int64_t *call_rowptr, int32_t *call_idx) {
   return guarded([&] {
     if (!s) throw MmError{MM_EINVAL, "export_system: NULL system"};
-    use_device(s);
+    SystemScope scope(s);
     export_system(s, method_class, attr_class, acc_rowptr, acc_idx, call_rowptr, call_idx);
   });
 }
@@ -535,7 +594,9 @@ int64_t mm_launch_count(void) { return (int64_t)g_launches.load(std::memory_orde
 
 mm_status mm_selftest_bounded_wait(void) {
   return guarded([&] {
-    if (stalled_scan_probe()) throw MmError{MM_ETIMEOUT, "selftest: the stalled scan's wait gave up as designed"};
+    const uint32_t r = stalled_scan_probe();
+    if (r == 2) throw MmError{MM_ECUDA, "selftest: the stalled scan's fallback did not give the exact prefix"};
+    if (r) throw MmError{MM_ETIMEOUT, "selftest: the stalled scan's wait gave up as designed; its output is exact"};
   });
 }
 

@@ -64,6 +64,19 @@ inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   MM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
 }
 
+// Carve consecutive, 256-byte aligned pieces out of one scratch buffer (a
+// buffer of sum over pieces of round_up(bytes, 256) bytes).
+struct Carve {
+  char *base;
+  size_t off = 0;
+  template <class T>
+  T *take(int64_t n) {
+    T *p = reinterpret_cast<T *>(base + off);
+    off += ((sizeof(T) * (size_t)(n > 1 ? n : 1)) + 255) / 256 * 256;
+    return p;
+  }
+};
+
 static inline int bits_for(uint64_t max_value) {  // bits needed to hold [0, max_value]
   int b = 0;
   while (b < 64 && (max_value >> b) != 0) ++b;
@@ -194,6 +207,8 @@ struct mm_system {
   double sim_avg = 0.0;
   int64_t *r1_rowptr = nullptr;    // rule R1's candidate lists (device CSR over the methods)
   int32_t *r1_dst = nullptr;
+  // metric variants (Sec. II.B) and class ranking
+  Scratch var_ws, var_keys_ws;
 
   // inputs
   int32_t *method_class, *attr_class, *acc_idx, *call_idx;
@@ -246,7 +261,9 @@ struct mm_system {
   unsigned long long *d_u64;       // [0] digest, [1] kept count, [2] methods with kept, [3] candidate hash,
                                    // [4] load summary, [5] group counter of the restricted evaluation,
                                    // [6..7] error word (d_err), [8] group counter of the LCOM unions,
-                                   // [24..] kept field ranges
+                                   // [9] fault word of bounded waits (d_fault), [24..] kept field ranges
+  uint32_t *d_fault;
+  int32_t test_stall_scans = 0;    // test hook: multi-tile scans still to be made to run out
 };
 
 // ---------------------------------------------------------------- primitives (mm_prims.cu)
@@ -255,9 +272,29 @@ struct mm_system {
 // *total_dev when non-null.  Uses sys->sort_ws-independent scratch `ws`.
 void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, Scratch &ws,
                         cudaStream_t st);
-// Copies the device flag of bounded waits that gave up (nonzero) to *host once
-// the stream reaches this point; the caller synchronises before reading it.
-void read_wait_fault(uint32_t *host, cudaStream_t st);
+// Bounded device-side waits (the look-back of the one-pass scan) record that
+// they ran out in the fault word of the system or batch whose entry point is
+// running on the calling thread, named by a WaitScope for the call's duration
+// (a process-wide word when none is).  stall, when non-null, points at the
+// test hook's counter: while it is positive, each multi-tile scan decrements
+// it and is made to run out of its wait.
+struct WaitScope {
+  WaitScope(uint32_t *fault, int32_t *stall);
+  ~WaitScope();
+  WaitScope(const WaitScope &) = delete;
+  WaitScope &operator=(const WaitScope &) = delete;
+  uint32_t *prev_fault;
+  int32_t *prev_stall;
+};
+uint32_t *current_fault_word();
+// Copies a fault word to *host once the stream reaches this point; the caller
+// synchronises before reading it.
+void read_wait_fault(uint32_t *host, const uint32_t *fault_dev, cudaStream_t st);
+// After that synchronisation: a nonzero word is cleared (in stream order) and
+// reported as MM_ETIMEOUT naming the call.
+void raise_wait_fault(uint32_t host_word, uint32_t *fault_dev, cudaStream_t st, const char *what);
+// Both, with a synchronisation between them.
+void check_wait_fault(uint32_t *fault_dev, cudaStream_t st, const char *what);
 // Page-locked host memory of the calling thread for small read-backs (grow-only,
 // freed when the thread exits): copies into it are asynchronous, so a call's
 // read-backs need one synchronisation between them, not one each.
@@ -265,7 +302,6 @@ void *host_staging(size_t bytes);
 // Zeroes three buffers (null or 16-byte aligned starts) in one launch of
 // 16-byte stores (faster than cudaMemsetAsync on large buffers here).
 void zero_buffers(void *a, size_t na, void *b, size_t nb, void *c, size_t nc, cudaStream_t st);
-void clear_wait_fault();
 uint32_t stalled_scan_probe();
 void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch &ws, cudaStream_t st,
                             int64_t *total_dev = nullptr);
@@ -319,22 +355,24 @@ __device__ __forceinline__ int32_t accessor_union(const int32_t *acc_row, int64_
                                                   const int32_t *attr_class, const int64_t *own_ptr,
                                                   const int32_t *own_list, uint32_t *bm, uint32_t lane) {
   int32_t cnt = 0;
-  for (int64_t e0 = 0; e0 < len; e0 += 32) {
-    const int32_t al = e0 + lane < len ? acc_row[e0 + lane] : -1;
-    int64_t p0 = 0;
-    int32_t n = 0;
-    if (al >= 0 && attr_class[al] == K) {
-      p0 = own_ptr[al];
-      n = (int32_t)(own_ptr[al + 1] - p0);
-    }
-    int32_t incl = n;
+  // phase 0 sets the bits of every accessor list, phase 1 counts and clears
+  // them; each phase walks all of the method's accesses, 32 at a time
+  for (int phase = 0; phase < 2; ++phase) {
+    for (int64_t e0 = 0; e0 < len; e0 += 32) {
+      const int32_t al = e0 + lane < len ? acc_row[e0 + lane] : -1;
+      int64_t p0 = 0;
+      int32_t n = 0;
+      if (al >= 0 && attr_class[al] == K) {
+        p0 = own_ptr[al];
+        n = (int32_t)(own_ptr[al + 1] - p0);
+      }
+      int32_t incl = n;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-      if ((int)lane >= o) incl += t;
-    }
-    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    for (int phase = 0; phase < 2; ++phase) {
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += t;
+      }
+      const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
       for (int32_t k0 = 0; k0 < total; k0 += 32) {
         const int32_t k = k0 + (int32_t)lane;
         // lane holding element k: the first lane whose inclusive prefix exceeds k
@@ -353,13 +391,17 @@ __device__ __forceinline__ int32_t accessor_union(const int32_t *acc_row, int64_
           else cnt += __popc(atomicExch(&bm[j >> 5], 0u));
         }
       }
-      __syncwarp();
     }
+    __syncwarp();
   }
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   return cnt;
 }
 
+// Metric variants of every class and q_all per method into the system's
+// variant buffers (mm_variants.cu); the first k classes by a metric.
+void compute_variants(mm_system *s, mm_class_variants **out, int32_t **q_all);
+void rank_classes(mm_system *s, int32_t metric, int32_t k, int32_t *out_ids, int64_t *out_values, int32_t kind);
 void build_metrics(mm_system *s);                   // mm_metrics.cu
 void build_move_precompute(mm_system *s);           // mm_moves.cu
 void export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *out_m, int32_t kind);

@@ -2353,15 +2353,11 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
       if (nstage > 0)
         MM_CUDA_TRY(cudaMemcpyAsync(hb + 32, kept, sizeof(mm_move) * (size_t)nstage, cudaMemcpyDeviceToHost, st));
       MM_CUDA_TRY(cudaMemcpyAsync(hc, s->d_u64 + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-      read_wait_fault(hfault, st);
+      read_wait_fault(hfault, s->d_fault, st);
       MM_CUDA_TRY(cudaStreamSynchronize(st));
       staged = reinterpret_cast<const mm_move *>(hb + 32);
       nstaged = nstage;
-      const uint32_t fault = *hfault;
-        if (fault) {
-        clear_wait_fault();
-        throw MmError{MM_ETIMEOUT, "suggest: a bounded device-side wait gave up"};
-      }
+      raise_wait_fault(*hfault, s->d_fault, st, "suggest");
       K = (int64_t)hc[0];
       nm = (int64_t)hc[1];
       if (K <= cap) break;

@@ -109,6 +109,7 @@ extern "C" MMREF_API mm_status mm_suggest_moves_noalloc(mm_system *s, const mm_c
       if (cudaSetDevice(s->device) != cudaSuccess) throw MmError{MM_ECUDA, "cudaSetDevice failed"};
       guard.prev = cur;
     }
+    WaitScope wait(s->d_fault, &s->test_stall_scans);
     unsigned char *base = scratch_for_device(s->device);
     unsigned long long *counters = reinterpret_cast<unsigned long long *>(base);  // [0] kept, [1] methods
     uint8_t *mark = base + NA_COUNTERS;
@@ -124,8 +125,11 @@ extern "C" MMREF_API mm_status mm_suggest_moves_noalloc(mm_system *s, const mm_c
       MM_LAUNCH_CHECK();
     }
     unsigned long long hc[2] = {0, 0};
+    uint32_t hfault = 0;
     MM_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    read_wait_fault(&hfault, s->d_fault, st);
     MM_CUDA_TRY(cudaStreamSynchronize(st));
+    raise_wait_fault(hfault, s->d_fault, st, "suggest_moves_noalloc");
     const int64_t K = (int64_t)hc[0];
     if (K > MM_NOALLOC_MAX_KEPT)
       throw MmError{MM_EBUDGET, "suggest_moves_noalloc: " + std::to_string(K) +

@@ -8,10 +8,37 @@
 // which makes every pass, and hence the sort, stable and deterministic.
 #include <cuda_runtime.h>
 
+#include <string>
+#include <vector>
+
 #include "mm_internal.cuh"
 
-// Set by a bounded device-side wait that ran out (see scan_onepass).
+// Set by a bounded device-side wait that ran out (see scan_onepass) when no
+// system or batch is named by the calling thread's WaitScope.
 __device__ unsigned int g_wait_fault = 0;
+
+namespace {
+// The fault word (and the stall counter of the test hook) of the system or
+// batch whose entry point is running on this thread.
+thread_local uint32_t *t_fault = nullptr;
+thread_local int32_t *t_stall = nullptr;
+}  // namespace
+
+WaitScope::WaitScope(uint32_t *fault, int32_t *stall) : prev_fault(t_fault), prev_stall(t_stall) {
+  t_fault = fault;
+  t_stall = stall;
+}
+WaitScope::~WaitScope() {
+  t_fault = prev_fault;
+  t_stall = prev_stall;
+}
+
+uint32_t *current_fault_word() {
+  if (t_fault) return t_fault;
+  void *p = nullptr;
+  MM_CUDA_TRY(cudaGetSymbolAddress(&p, g_wait_fault));
+  return static_cast<uint32_t *>(p);
+}
 
 namespace {
 
@@ -109,19 +136,32 @@ __global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(const Tin *in
 // A tile publishes its total (flag 1), then, once the tiles before it are
 // summed, its inclusive prefix (flag 2), both as one 64-bit word (sum << 2 |
 // flag).  The wait is bounded: past the limit the block records a fault in
-// g_wait_fault (read back by the host at its next synchronisation) and goes on.
+// the fault word of the calling system (read back by the host at its next
+// synchronisation), sums the input before its tile itself and goes on, so the
+// output is exact whether or not the wait ran out.
 constexpr unsigned long long SP_AGG = 1ull, SP_INCL = 2ull;
 constexpr int SP_WAIT_LIMIT = 1 << 21;  // about a second of polling
+constexpr int SP_STALL_LIMIT = 1 << 12;  // the test hook's short limit
 
+// stall != 0 (test hook): tile 0 holds back its state until another tile's
+// look-back has run out (or four limits have passed), so the tiles after it
+// take the fallback below.
 template <class Tin, class Tout>
 __global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(const Tin *in, Tout *out, int64_t n, Tout *total_out,
-                                                              unsigned long long *status, unsigned int *tile_ctr) {
+                                                              unsigned long long *status, unsigned int *tile_ctr,
+                                                              unsigned int *fault, int wait_limit, int stall) {
   pdl_wait();
   static_assert(sizeof(Tout) <= 8, "scan sums are packed with a 2-bit flag");
   __shared__ unsigned int s_tile;
   __shared__ Tout s_prefix;
+  __shared__ Tout s_agg;
   __shared__ Tout tot;
-  if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  __shared__ int64_t s_j;  // >= 0: the look-back gave up at tile s_j
+  __shared__ unsigned long long s_w;
+  if (threadIdx.x == 0) {
+    s_tile = atomicAdd(tile_ctr, 1u);
+    s_j = -1;
+  }
   __syncthreads();
   const int64_t tile = s_tile;
   const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
@@ -134,21 +174,26 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(const Tin *in, Tout
     sum += v[i];
   }
   Tout ex = block_exclusive_sum<Tout>(sum, &tot);
+  volatile unsigned long long *vs = status;
   if (threadIdx.x == 0) {
     const Tout agg = tot;
+    s_agg = agg;
     Tout prefix = 0;
-    volatile unsigned long long *vs = status;
-    if (tile == 0) {
-      atomicExch(&status[0], ((unsigned long long)agg << 2) | SP_INCL);
-    } else {
+    if (tile == 0 && stall) {
+      volatile unsigned int *vf = fault;
+      for (int spins = 0; *vf == 0u && spins < 4 * wait_limit; ++spins) __nanosleep(32);
+    }
+    if (tile > 0) {
       atomicExch(&status[tile], ((unsigned long long)agg << 2) | SP_AGG);
+      __threadfence();  // the state is visible before any output of this tile
       int spins = 0;
       for (int64_t j = tile - 1; j >= 0;) {
         const unsigned long long w = vs[j];
         const unsigned long long f = w & 3ull;
         if (f == 0ull) {
-          if (++spins > SP_WAIT_LIMIT) {
-            atomicOr(&g_wait_fault, 1u);
+          if (++spins > wait_limit) {
+            atomicOr(fault, 1u);
+            s_j = j;
             break;
           }
           __nanosleep(32);
@@ -158,12 +203,47 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(const Tin *in, Tout
         if (f == SP_INCL) break;
         --j;
       }
-      atomicExch(&status[tile], ((unsigned long long)(prefix + agg) << 2) | SP_INCL);
     }
     s_prefix = prefix;
-    if (total_out && base + SCAN_TILE >= n) *total_out = prefix + agg;  // the last tile
   }
   __syncthreads();
+  // Fallback after a wait that ran out: the block walks on from tile s_j,
+  // taking a published state where there is one and otherwise summing the
+  // tile's input itself.  A tile publishes its state before it writes any
+  // output, so an input summed while the state still reads 0 afterwards is
+  // the original input even when the scan runs in place.
+  while (s_j >= 0) {
+    const int64_t j = s_j;
+    if (threadIdx.x == 0) s_w = vs[j];
+    __syncthreads();
+    const unsigned long long w = s_w;
+    if ((w & 3ull) != 0ull) {
+      if (threadIdx.x == 0) {
+        s_prefix += (Tout)(w >> 2);
+        s_j = (w & 3ull) == SP_INCL ? -1 : j - 1;
+      }
+    } else {
+      Tout part = 0;
+      const int64_t lo = j * (int64_t)SCAN_TILE, hi = min(lo + (int64_t)SCAN_TILE, n);
+      for (int64_t k = lo + threadIdx.x; k < hi; k += SCAN_THREADS) part += (Tout)in[k];
+      block_exclusive_sum<Tout>(part, &tot);
+      if (threadIdx.x == 0) {
+        __threadfence();
+        if ((vs[j] & 3ull) == 0ull) {  // still unpublished: the input read was intact
+          s_prefix += tot;
+          s_j = j - 1;
+        }  // else: published meanwhile, take its state on the next pass
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const Tout prefix = s_prefix, agg = s_agg;
+    atomicExch(&status[tile], ((unsigned long long)(prefix + agg) << 2) | SP_INCL);
+    __threadfence();
+    if (total_out && base + SCAN_TILE >= n) *total_out = prefix + agg;  // the last tile
+  }
+  if (tile == 0) __syncthreads();  // tile 0's first state comes here: publish before writing (in-place scans)
   ex += s_prefix;
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
@@ -188,8 +268,14 @@ void scan_exclusive(const Tin *in, Tout *out, int64_t n, Tout *total_dev, Scratc
   // tile states and the tile counter, cleared together
   unsigned long long *status = static_cast<unsigned long long *>(ws.need(sizeof(unsigned long long) * (size_t)(nb + 1), st));
   MM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(nb + 1), st));
+  int stall = 0;
+  if (t_stall && *t_stall > 0) {  // test hook: this scan's look-back runs out
+    --*t_stall;
+    stall = 1;
+  }
   pdl_launch(scan_onepass<Tin, Tout>, (unsigned)nb, SCAN_THREADS, 0, st, in, out, n, total_dev, status,
-                                                                  reinterpret_cast<unsigned int *>(status + nb));
+             reinterpret_cast<unsigned int *>(status + nb), current_fault_word(),
+             stall ? SP_STALL_LIMIT : SP_WAIT_LIMIT, stall);
   MM_LAUNCH_CHECK();
 }
 
@@ -341,18 +427,28 @@ void zero_buffers(void *a, size_t na, void *b, size_t nb, void *c, size_t nc, cu
   MM_LAUNCH_CHECK();
 }
 
-void read_wait_fault(uint32_t *host, cudaStream_t st) {
-  MM_CUDA_TRY(cudaMemcpyFromSymbolAsync(host, g_wait_fault, sizeof(uint32_t), 0, cudaMemcpyDeviceToHost, st));
+void read_wait_fault(uint32_t *host, const uint32_t *fault_dev, cudaStream_t st) {
+  MM_CUDA_TRY(cudaMemcpyAsync(host, fault_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
 }
 
-void clear_wait_fault() {
-  const uint32_t zero = 0;
-  MM_CUDA_TRY(cudaMemcpyToSymbol(g_wait_fault, &zero, sizeof(zero)));
+void raise_wait_fault(uint32_t host_word, uint32_t *fault_dev, cudaStream_t st, const char *what) {
+  if (!host_word) return;
+  MM_CUDA_TRY(cudaMemsetAsync(fault_dev, 0, sizeof(uint32_t), st));
+  throw MmError{MM_ETIMEOUT, std::string(what) + ": a bounded device-side wait gave up (its result was completed "
+                                                 "by the fallback and is exact)"};
+}
+
+void check_wait_fault(uint32_t *fault_dev, cudaStream_t st, const char *what) {
+  uint32_t h = 0;
+  read_wait_fault(&h, fault_dev, st);
+  MM_CUDA_TRY(cudaStreamSynchronize(st));
+  raise_wait_fault(h, fault_dev, st, what);
 }
 
 // One block scans tile 1 of a two-tile input while tile 0 is never processed
-// (the tile counter starts at 1), so its look-back wait runs out.  Returns the
-// fault flag the host reads afterwards (and clears it).
+// (the tile counter starts at 1), so its look-back wait runs out and the
+// fallback sums tile 0's input.  Returns the fault word the host reads
+// afterwards, or 2 if the output is not the exact prefix sum of the input.
 uint32_t stalled_scan_probe() {
   int32_t *in = nullptr;
   int64_t *out = nullptr;
@@ -360,22 +456,31 @@ uint32_t stalled_scan_probe() {
   const int64_t n = 2 * (int64_t)SCAN_TILE;
   MM_CUDA_TRY(cudaMalloc(&in, sizeof(int32_t) * (size_t)n));
   MM_CUDA_TRY(cudaMalloc(&out, sizeof(int64_t) * (size_t)n));
-  MM_CUDA_TRY(cudaMalloc(&status, sizeof(unsigned long long) * 3));
-  MM_CUDA_TRY(cudaMemset(in, 0, sizeof(int32_t) * (size_t)n));
-  MM_CUDA_TRY(cudaMemset(status, 0, sizeof(unsigned long long) * 3));
+  MM_CUDA_TRY(cudaMalloc(&status, sizeof(unsigned long long) * 4));
+  std::vector<int32_t> h_in((size_t)n);
+  for (int64_t k = 0; k < n; ++k) h_in[(size_t)k] = (int32_t)(k % 7);
+  MM_CUDA_TRY(cudaMemcpy(in, h_in.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
+  MM_CUDA_TRY(cudaMemset(status, 0, sizeof(unsigned long long) * 4));
   const unsigned int first = 1;
   MM_CUDA_TRY(cudaMemcpy(status + 2, &first, sizeof(first), cudaMemcpyHostToDevice));
-  pdl_launch(scan_onepass<int32_t, int64_t>, 1, SCAN_THREADS, 0, 0, in, out, n, nullptr, status,
-                                                       reinterpret_cast<unsigned int *>(status + 2));
+  uint32_t *fault = reinterpret_cast<uint32_t *>(status + 3);
+  pdl_launch(scan_onepass<int32_t, int64_t>, 1, SCAN_THREADS, 0, 0, in, out, n, (int64_t *)nullptr, status,
+             reinterpret_cast<unsigned int *>(status + 2), fault, SP_WAIT_LIMIT, 0);
   MM_LAUNCH_CHECK();
   MM_CUDA_TRY(cudaDeviceSynchronize());
-  uint32_t fault = 0;
-  MM_CUDA_TRY(cudaMemcpyFromSymbol(&fault, g_wait_fault, sizeof(fault)));
-  clear_wait_fault();
+  uint32_t h_fault = 0;
+  MM_CUDA_TRY(cudaMemcpy(&h_fault, fault, sizeof(h_fault), cudaMemcpyDeviceToHost));
+  std::vector<int64_t> h_out((size_t)n);
+  MM_CUDA_TRY(cudaMemcpy(h_out.data(), out, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost));
+  int64_t run = 0;  // tile 1's outputs: the exclusive prefix over both tiles
+  for (int64_t k = 0; k < n; ++k) {
+    if (k >= SCAN_TILE && h_out[(size_t)k] != run) h_fault = 2;
+    run += h_in[(size_t)k];
+  }
   cudaFree(in);
   cudaFree(out);
   cudaFree(status);
-  return fault;
+  return h_fault;
 }
 
 void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, Scratch &ws,

@@ -12,7 +12,8 @@
 // proportional to the co-occurrences, sum over properties of deg(deg-1)/2.
 //
 // R1: a pair in different classes whose similarity exceeds the average of
-// all similarity values proposes moving either method to the other's class.
+// all similarity values proposes moving either method to the other's class,
+// or to another class holding a method it calls.
 // The average is taken on the host in double precision in one fixed order
 // (sum over u ascending of sum(i)/u, over the number of values), and turned
 // into the smallest i per u that exceeds it, so the device decides each pair
@@ -139,10 +140,11 @@ __global__ void similarity_values(const uint64_t *keys, int64_t n, const int32_t
 
 // Moves proposed by the high pairs: x -> cls(y) and y -> cls(x) when the
 // classes differ and i >= thr[u]; keys m * c + D.  A warp reserves its output
-// slots with one atomicAdd.
+// slots with one atomicAdd.  Both methods of such a pair are marked as
+// proposers.
 __global__ void high_pair_moves(const int32_t *px, const int32_t *py, const int32_t *pi, const int32_t *pu,
                                 int64_t n, const int32_t *thr, const int32_t *method_class, int32_t c,
-                                uint64_t *keys, unsigned long long *count) {
+                                uint64_t *keys, unsigned long long *count, uint8_t *proposer) {
   pdl_wait();
   const uint32_t lane = threadIdx.x & 31u;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -167,6 +169,28 @@ __global__ void high_pair_moves(const int32_t *px, const int32_t *py, const int3
       const unsigned long long o = base + 2ull * __popc(bal & ((1u << lane) - 1u));
       keys[o] = (uint64_t)x * (uint64_t)c + (uint64_t)cy;
       keys[o + 1] = (uint64_t)y * (uint64_t)c + (uint64_t)cx;
+      proposer[x] = 1;
+      proposer[y] = 1;
+    }
+  }
+}
+
+// The other moves of a proposer: to the class of each method it calls (when
+// not its own); keys appended after the pair moves.
+__global__ void called_class_moves(const uint8_t *proposer, const int64_t *call_rowptr, const int32_t *call_idx,
+                                   const int32_t *method_class, int32_t M, int32_t c, uint64_t *keys,
+                                   unsigned long long *count) {
+  pdl_wait();
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < M; x += (int64_t)gridDim.x * blockDim.x) {
+    if (!proposer[x]) continue;
+    const int32_t C = method_class[x];
+    int32_t nk = 0;
+    for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e) nk += method_class[call_idx[e]] != C;
+    if (!nk) continue;
+    unsigned long long o = atomicAdd(count, (unsigned long long)nk);
+    for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e) {
+      const int32_t D = method_class[call_idx[e]];
+      if (D != C) keys[o++] = (uint64_t)x * (uint64_t)c + (uint64_t)D;
     }
   }
 }
@@ -188,18 +212,6 @@ __global__ void move_lists(const uint64_t *keys, int64_t n, const int32_t *flag,
 // ---------------------------------------------------------------- host side
 
 namespace {
-
-// Carve consecutive, 256-byte aligned pieces out of one scratch buffer.
-struct Carve {
-  char *base;
-  size_t off = 0;
-  template <class T>
-  T *take(int64_t n) {
-    T *p = reinterpret_cast<T *>(base + off);
-    off += ((sizeof(T) * (size_t)std::max<int64_t>(n, 1)) + 255) / 256 * 256;
-    return p;
-  }
-};
 
 void read_back(void *host, const void *dev, size_t bytes, cudaStream_t st) {
   MM_CUDA_TRY(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st));
@@ -326,28 +338,36 @@ void build_r1_candidates(mm_system *s, int64_t *n_high, int64_t *n_cand) {
     thr[(size_t)u] = t;
   }
   const int64_t nv = s->sim_n;
+  const int64_t cap = 2 * nv + s->n_call;  // pair moves, then at most one move per call of a proposer
   Carve kv{static_cast<char *>(s->sim_keys_ws.need(((sizeof(uint64_t) * 2 + sizeof(int32_t) + sizeof(int64_t)) *
-                                                     (size_t)(2 * nv)) + 6 * 256 +
+                                                     (size_t)cap) + 8 * 256 + (size_t)M +
                                                         sizeof(int32_t) * (size_t)(umax + 1) + 64,
                                                     st))};
-  uint64_t *keys = kv.take<uint64_t>(2 * nv);
-  uint64_t *keys_alt = kv.take<uint64_t>(2 * nv);
-  int32_t *flag = kv.take<int32_t>(2 * nv);
-  int64_t *pos = kv.take<int64_t>(2 * nv);
+  uint64_t *keys = kv.take<uint64_t>(cap);
+  uint64_t *keys_alt = kv.take<uint64_t>(cap);
+  int32_t *flag = kv.take<int32_t>(cap);
+  int64_t *pos = kv.take<int64_t>(cap);
   int32_t *dthr = kv.take<int32_t>(umax + 1);
-  unsigned long long *count = kv.take<unsigned long long>(1);
+  unsigned long long *count = kv.take<unsigned long long>(2);
+  uint8_t *proposer = kv.take<uint8_t>(M);
   MM_CUDA_TRY(cudaMemcpyAsync(dthr, thr.data(), sizeof(int32_t) * thr.size(), cudaMemcpyHostToDevice, st));
-  MM_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st));
+  MM_CUDA_TRY(cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), st));
+  MM_CUDA_TRY(cudaMemsetAsync(proposer, 0, (size_t)M, st));
   pdl_launch(high_pair_moves, grid_for(nv), TPB, 0, st, static_cast<const int32_t *>(s->sim_x),
              static_cast<const int32_t *>(s->sim_y), static_cast<const int32_t *>(s->sim_i),
              static_cast<const int32_t *>(s->sim_u), nv, static_cast<const int32_t *>(dthr),
-             static_cast<const int32_t *>(s->method_class), c, keys, count);
+             static_cast<const int32_t *>(s->method_class), c, keys, count, proposer);
   MM_LAUNCH_CHECK();
-  unsigned long long nk = 0;
-  read_back(&nk, count, sizeof(nk), st);
-  *n_high = (int64_t)(nk / 2);
-  if (nk == 0) return;
-  const int64_t n = (int64_t)nk;
+  // count[1] = the pair moves (2 per high pair), kept before the appends
+  MM_CUDA_TRY(cudaMemcpyAsync(count + 1, count, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+  pdl_launch(called_class_moves, grid_for(M), TPB, 0, st, static_cast<const uint8_t *>(proposer), s->call_rowptr,
+             s->call_idx, static_cast<const int32_t *>(s->method_class), M, c, keys, count);
+  MM_LAUNCH_CHECK();
+  unsigned long long nk[2] = {0, 0};
+  read_back(nk, count, sizeof(nk), st);
+  *n_high = (int64_t)(nk[1] / 2);
+  if (nk[0] == 0) return;
+  const int64_t n = (int64_t)nk[0];
   radix_sort_u64(keys, keys_alt, nullptr, nullptr, n, bits_for((uint64_t)M * (uint64_t)c - 1), s->sort_ws, st);
   pdl_launch(run_heads, grid_for(n), TPB, 0, st, static_cast<const uint64_t *>(keys), n, flag);
   MM_LAUNCH_CHECK();

@@ -214,7 +214,8 @@ __global__ void fan_in_hist(const int32_t *call_idx, int64_t n_call, int32_t *fa
 void load_validate_and_summarise(mm_system *s) {
   cudaStream_t st = s->stream;
   LoadSummary *dsum = reinterpret_cast<LoadSummary *>(s->d_u64 + 4);
-  MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 4, 0, 4 * sizeof(unsigned long long), st));  // summary and error word
+  // summary, error word, fault word
+  MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 4, 0, 6 * sizeof(unsigned long long), st));
   MM_CUDA_TRY(cudaMemsetAsync(s->cls_n, 0, sizeof(int32_t) * 2 * (size_t)s->c, st));  // cls_n, cls_a
   if (s->M > 0)
     pdl_launch(validate_methods, grid_for(s->M), TPB, 0, st, s->method_class, s->acc_rowptr, s->acc_idx, s->call_rowptr,
@@ -262,15 +263,11 @@ void load_finish(mm_system *s) {
   MM_CUDA_TRY(cudaMemcpyAsync(h, s->d_u64 + 4, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   uint32_t *hfault = reinterpret_cast<uint32_t *>(h + 32);
   *hfault = 0;
-  read_wait_fault(hfault, st);
+  read_wait_fault(hfault, s->d_fault, st);
   MM_CUDA_TRY(cudaStreamSynchronize(st));
   std::memcpy(&s->summary, h, sizeof(LoadSummary));
   std::memcpy(&s->load_err, h + 16, sizeof(uint32_t));
-  const uint32_t fault = *hfault;
-  if (fault) {
-    clear_wait_fault();
-    throw MmError{MM_ETIMEOUT, "load: a bounded device-side wait gave up"};
-  }
+  raise_wait_fault(*hfault, s->d_fault, st, "load");
   const uint32_t err = s->load_err;
   s->summary.err = err & VE_ERRORS;
   s->methods_by_class = !(err & VI_METHODS_UNSORTED);

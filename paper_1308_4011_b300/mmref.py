@@ -36,7 +36,7 @@ EXPORTED = ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluat
             "mm_export_system", "mm_server_create", "mm_server_add_system", "mm_server_run", "mm_server_stats_get",
             "mm_server_snapshot", "mm_server_free", "mm_selftest_bounded_wait", "mm_last_eval_ms",
             "mm_export_metrics", "mm_similarity", "mm_suggest_r1", "mm_apply_sequence",
-            "mm_suggest_r3")
+            "mm_suggest_r3", "mm_selftest_stall_scans", "mm_metric_variants", "mm_rank_classes")
 
 CLASS_METRICS_DTYPE = np.dtype([("n_methods", "<i4"), ("n_attrs", "<i4"), ("P", "<i8"), ("Q", "<i8"),
                                 ("S", "<i8"), ("lcom_ck", "<i8"), ("hs_num", "<i8"), ("hs_den", "<i8"),
@@ -128,6 +128,17 @@ _lib.mm_suggest_r3.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c
 _lib.mm_suggest_r3.restype = ctypes.c_int
 APPLIED_DTYPE = np.dtype([("round", "<i4"), ("m", "<i4"), ("from", "<i4"), ("to", "<i4")])
 _lib.mm_export_system.restype = ctypes.c_int
+_lib.mm_selftest_stall_scans.argtypes = [_vp, ctypes.c_int32]
+_lib.mm_selftest_stall_scans.restype = ctypes.c_int
+VARIANTS_DTYPE = np.dtype([("P_all", "<i8"), ("Q_all", "<i8"), ("lcom_ck_all", "<i8"), ("lcom_pq", "<i8"),
+                           ("lcom_pq_all", "<i8"), ("cbo_out", "<i4"), ("cbo_in", "<i4"), ("cbo_bi", "<i4"),
+                           ("reserved", "<i4")])
+assert VARIANTS_DTYPE.itemsize == 56
+RANK_LCOM_CK, RANK_LCOM_PQ, RANK_LCOM_CK_ALL, RANK_LCOM_PQ_ALL, RANK_CBO, RANK_CBO_IN, RANK_CBO_BI = range(1, 8)
+_lib.mm_metric_variants.argtypes = [_vp, _vp, _vp, ctypes.c_int32]
+_lib.mm_metric_variants.restype = ctypes.c_int
+_lib.mm_rank_classes.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int32]
+_lib.mm_rank_classes.restype = ctypes.c_int
 EDIT_ADD_ACCESS, EDIT_REMOVE_ACCESS, EDIT_ADD_CALL, EDIT_REMOVE_CALL, EDIT_MOVE = 1, 2, 3, 4, 5
 NOALLOC_MAX_METHODS = 1048576
 NOALLOC_MAX_KEPT = 65536
@@ -162,6 +173,12 @@ def selftest_bounded_wait() -> int:
     """mm_selftest_bounded_wait: the status the host reads after a device-side
     wait that cannot be satisfied ran out (MM_ETIMEOUT when it works)."""
     return int(_lib.mm_selftest_bounded_wait())
+
+def selftest_stall_scans(sys: "System", n: int):
+    """mm_selftest_stall_scans: the next n multi-tile scans of calls on sys run
+    out of their bounded wait (results stay exact; the next synchronising call
+    reports MM_ETIMEOUT)."""
+    _check(_lib.mm_selftest_stall_scans(sys.handle, int(n)))
 
 
 def launch_count() -> int:
@@ -296,6 +313,14 @@ def export_metrics(sys: System, out_class="host", out_method="host"):
 
 def _sim_info(inf) -> dict:
     return {f: getattr(inf, f) for f, _ in _SimInfo._fields_ if f != "reserved"}
+
+
+def similarity_info(sys: System) -> dict:
+    """mm_similarity with no outputs: computes the similarity values of the
+    current state on the device and returns only the info dict."""
+    inf = _SimInfo()
+    _check(_lib.mm_similarity(sys.handle, None, None, None, None, 0, PTR_HOST, ctypes.byref(inf)))
+    return _sim_info(inf)
 
 
 def similarity(sys: System, cap=None):
@@ -458,6 +483,32 @@ def suggest_r3(sys: System, k: int):
     _check(_lib.mm_suggest_r3(sys.handle, int(k), out.ctypes.data, ctypes.byref(nk), ctypes.byref(nc),
                               ctypes.byref(nh)))
     return out[: min(k, nk.value)], int(nk.value), int(nc.value), int(nh.value)
+
+
+def metric_variants(sys: System, out="host", out_q_all="host"):
+    """mm_metric_variants: the LCOM and CBO variants per class (VARIANTS_DTYPE)
+    and q_all per method.  Buffers as compute_metrics ("host" = new numpy
+    arrays; CUDA uint8 tensors of 56*n_classes / 4*n_methods bytes)."""
+    if isinstance(out, str):
+        out = np.zeros(sys.n_classes, dtype=VARIANTS_DTYPE)
+    if isinstance(out_q_all, str):
+        out_q_all = np.zeros(sys.n_methods, dtype=np.int32)
+    outs = [o for o in (out, out_q_all) if o is not None]
+    kind = _kind(outs[0]) if outs else PTR_HOST
+    if any(_kind(o) != kind for o in outs):
+        raise ValueError("metric_variants: outputs must be both host or both device")
+    _check(_lib.mm_metric_variants(sys.handle, _ptr(out), _ptr(out_q_all), kind))
+    return out, out_q_all
+
+
+def rank_classes(sys: System, metric: int, k: int):
+    """mm_rank_classes: the first k classes by a metric (RANK_*), largest
+    first, ties by ascending id; returns (ids, values) as numpy arrays."""
+    n = max(0, min(int(k), sys.n_classes))
+    ids = np.zeros(max(n, 1), dtype=np.int32)
+    vals = np.zeros(max(n, 1), dtype=np.int64)
+    _check(_lib.mm_rank_classes(sys.handle, int(metric), int(k), ids.ctypes.data, vals.ctypes.data, PTR_HOST))
+    return ids[:n], vals[:n]
 
 
 def export_system(sys: System):

@@ -133,7 +133,7 @@ def test_invalid_edits_change_nothing():
 # ---------------------------------------------------------------- move sequences
 
 @pytest.mark.parametrize("name,mask,mi,rounds,per_round", [("tiny", 3, 2, 4, 0), ("tiny", 3, 1, 3, 5),
-                                                           ("tiny", 7, 1, 2, 0)])
+                                                           ("tiny", 7, 1, 2, 0), ("medium", 3, 2, 2, 0)])
 def test_sequence_equals_oracle(name, mask, mi, rounds, per_round):
     """Rounds of non-conflicting kept moves applied on the GPU equal the
     oracle's rounds, move for move, and the final state's metrics equal a
