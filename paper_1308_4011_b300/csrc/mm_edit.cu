@@ -89,26 +89,30 @@ __global__ void kept_filter(const mm_move *in, const unsigned long long *count_i
   }
 }
 
-__global__ void candidate_lengths(const int32_t *method_class, const uint8_t *classflag, int32_t M, int32_t c,
-                                  int32_t nA, int64_t *len) {
+// methods of the affected classes, compacted into a list (any order)
+__global__ void affected_methods(const int32_t *method_class, const uint8_t *classflag, int32_t M, int32_t *list,
+                                 unsigned long long *n) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < M; x += (int64_t)gridDim.x * blockDim.x)
-    len[x] = classflag[method_class[x]] ? (int64_t)(c - 1) : (int64_t)nA;
+    if (classflag[method_class[x]]) list[atomicAdd(n, 1ull)] = (int32_t)x;
 }
 
-// one warp per method row: all other classes for affected methods, the
-// affected classes for the others
+// candidate rows of the other methods: the affected classes (none for the
+// methods of affected classes, whose rows are evaluated in full)
+__global__ void candidate_lengths(const int32_t *method_class, const uint8_t *classflag, int32_t M, int32_t nA,
+                                  int64_t *len) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < M; x += (int64_t)gridDim.x * blockDim.x)
+    len[x] = classflag[method_class[x]] ? 0 : (int64_t)nA;
+}
+
+// one warp per method row
 __global__ void candidate_fill(const int32_t *method_class, const uint8_t *classflag, const int64_t *rowptr,
-                               const int32_t *alist, int32_t nA, int32_t M, int32_t c, int32_t *dst) {
+                               const int32_t *alist, int32_t nA, int32_t M, int32_t *dst) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nw) {
-    const int32_t C = method_class[x];
+    if (classflag[method_class[x]]) continue;
     int32_t *row = dst + rowptr[x];
-    if (classflag[C]) {
-      for (int32_t j = lane; j < c - 1; j += 32) row[j] = j < C ? j : j + 1;
-    } else {
-      for (int32_t j = lane; j < nA; j += 32) row[j] = alist[j];
-    }
+    for (int32_t j = lane; j < nA; j += 32) row[j] = alist[j];
   }
 }
 
@@ -332,14 +336,18 @@ void apply_edit(mm_system *s, const mm_edit &e) {
   const int32_t nA = (int32_t)affected.size();
   int64_t rows = 0;
   for (int32_t Y : affected) rows += mr.cls_n[Y];
-  const int64_t n_inc = rows * (int64_t)(c - 1) + ((int64_t)M - rows) * nA;
-  // scratch: classflag[c], alist[nA], len/rowptr[M+1], dst[n_inc], tmp kept[cap]
+  // rows: the methods of the affected classes to every class (dense tiles over
+  // a method list); columns: every other method to the affected classes
+  // (candidate lists of nA entries)
+  const int64_t n_inc = ((int64_t)M - rows) * nA;
+  // scratch: classflag[c], alist[nA], len/rowptr[M+1], dst[n_inc], tmp kept[cap], counters, method list[rows]
   size_t off_flag = 0, off_alist = (size_t)(c + 255) / 256 * 256;
   size_t off_rp = off_alist + ((size_t)nA * 4 + 255) / 256 * 256;
   size_t off_dst = off_rp + ((size_t)(M + 1) * 8 + 255) / 256 * 256;
   size_t off_tmp = off_dst + ((size_t)n_inc * 4 + 255) / 256 * 256;
   size_t off_cnt = off_tmp + (size_t)cap * sizeof(mm_move);
-  size_t bytes = off_cnt + 256;
+  size_t off_ml = off_cnt + 256;
+  size_t bytes = off_ml + ((size_t)rows * 4 + 255) / 256 * 256 + 256;
   char *w = static_cast<char *>(s->edit_ws.need(bytes, st));
   uint8_t *classflag = reinterpret_cast<uint8_t *>(w + off_flag);
   int32_t *alist = reinterpret_cast<int32_t *>(w + off_alist);
@@ -347,6 +355,8 @@ void apply_edit(mm_system *s, const mm_edit &e) {
   int32_t *dst = reinterpret_cast<int32_t *>(w + off_dst);
   mm_move *tmp = reinterpret_cast<mm_move *>(w + off_tmp);
   unsigned long long *cnt2 = reinterpret_cast<unsigned long long *>(w + off_cnt);
+  unsigned long long *nml = cnt2 + 1;
+  int32_t *mlist = reinterpret_cast<int32_t *>(w + off_ml);
   std::vector<uint8_t> hflag(c, 0);
   std::vector<int32_t> hal(affected.begin(), affected.end());
   for (int32_t Y : affected) hflag[Y] = 1;
@@ -359,14 +369,20 @@ void apply_edit(mm_system *s, const mm_edit &e) {
   MM_CUDA_TRY(cudaMemcpyAsync(kept, tmp, sizeof(mm_move) * (size_t)cap, cudaMemcpyDeviceToDevice, st));
   MM_CUDA_TRY(cudaMemcpyAsync(s->d_u64 + 1, cnt2, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
   // evaluate the affected rows and columns, appending kept moves
+  mm_criteria crit{kmask, kmin};
+  if (rows > 0) {
+    MM_CUDA_TRY(cudaMemsetAsync(nml, 0, sizeof(unsigned long long), st));
+    MM_CUDA_TRY(cudaMemsetAsync(mlist, 0, sizeof(int32_t) * (size_t)rows, st));  // every entry a valid id
+    affected_methods<<<grid_for(M), TPB, 0, st>>>(s->method_class, classflag, M, mlist, nml);
+    MM_LAUNCH_CHECK();
+    eval_dense_kept_subset(s, crit, mlist, (int32_t)rows, kept, cap, s->d_u64 + 1, mark);
+  }
   if (n_inc > 0) {
-    candidate_lengths<<<grid_for(M), TPB, 0, st>>>(s->method_class, classflag, M, c, nA, rowptr);
+    candidate_lengths<<<grid_for(M), TPB, 0, st>>>(s->method_class, classflag, M, nA, rowptr);
     MM_LAUNCH_CHECK();
     scan_exclusive_i64(rowptr, rowptr, M, rowptr + M, s->sort_ws, st);
-    candidate_fill<<<grid_for((int64_t)M * 32), TPB, 0, st>>>(s->method_class, classflag, rowptr, alist, nA, M, c,
-                                                              dst);
+    candidate_fill<<<grid_for((int64_t)M * 32), TPB, 0, st>>>(s->method_class, classflag, rowptr, alist, nA, M, dst);
     MM_LAUNCH_CHECK();
-    mm_criteria crit{kmask, kmin};
     eval_csr_kept_append(s, crit, rowptr, dst, kept, cap, s->d_u64 + 1, mark);
   }
   MM_CUDA_TRY(cudaMemsetAsync(mark, 0, (size_t)M, st));

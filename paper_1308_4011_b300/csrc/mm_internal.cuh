@@ -444,6 +444,8 @@ void eval_lists_records(mm_system *s, const int64_t *rowptr, const int32_t *dst,
 // edit path (mm_edit.cu / mm_moves.cu)
 void eval_csr_kept_append(mm_system *s, const mm_criteria &crit, const int64_t *rowptr, const int32_t *dst,
                           mm_move *kept, int64_t cap, unsigned long long *count, uint8_t *mark);
+void eval_dense_kept_subset(mm_system *s, const mm_criteria &crit, const int32_t *mlist, int32_t n, mm_move *kept,
+                            int64_t cap, unsigned long long *count, uint8_t *mark);
 bool kept_cache(mm_system *s, mm_move **kept, uint8_t **mark, int64_t *cap);
 void apply_edit(mm_system *s, const mm_edit &e);
 void export_system(mm_system *s, int32_t *method_class, int32_t *attr_class, int64_t *acc_rowptr,

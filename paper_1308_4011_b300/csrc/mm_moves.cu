@@ -836,6 +836,7 @@ struct DenseStage {
   //   [1] = {flag bits 0-5 (C's signs), change, record word 1 (dCBO(C) << 16), change},
   //   [2] = {C, 0x01010101 if m uses members of C, 0x01010101 if methods of C call m, 0}
   int4 mc[DB_MB][3];
+  int32_t mid[DB_MB];             // method id of each of the batch's methods
   int32_t k, overflow;
 };
 
@@ -934,7 +935,8 @@ __device__ __noinline__ uint64_t dense_overflow_method(const EvalCtx cx, const O
 struct DenseSys {
   EvalCtx cx;
   const int4 *dest_rec;  // per class: {P - Q, S}, {n, a, dck0, sck0 | shs0 << 8}
-  int32_t c, M;
+  int32_t c, M;          // M: methods evaluated (the length of mlist when it is set)
+  const int32_t *mlist;   // when non-null, position i evaluates method mlist[i] (else method i)
 };
 
 // One tile of the dense cross product: destinations [bx*DB_SPAN, +DB_SPAN) x
@@ -986,8 +988,9 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
       reinterpret_cast<uint32_t *>(&st.hitw[0][0])[i] = 0u;
     // ---- plan: warp 0 scans the list lengths of up to 32 methods
     if (warp == 0) {
-      const int32_t m = mb + (int32_t)lane;
-      const bool ok = m < m1;
+      const int32_t pos = mb + (int32_t)lane;
+      const bool ok = pos < m1;
+      const int32_t m = ok ? (sy.mlist ? __ldg(sy.mlist + pos) : pos) : 0;
       MoveHdr h;
       h.w0 = make_int4(0, 0, 0, 0);
       h.w1 = make_int4(0, 0, 0, 0);
@@ -1009,6 +1012,7 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
       if (k == 0) { k = 1; overflow = 1; }
       if ((int32_t)lane < k) {
         st.hdr[lane] = h;
+        st.mid[lane] = m;
         st.lb[lane] = incl - len;
         st.rb[lane] = incl - len + h.w0.z;
         st.hb[lane] = incl - len;  // the method's listed slots are kept from its first slot on
@@ -1126,9 +1130,9 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
     // ---- evaluate the batch (a method whose lists exceed the stage comes alone
     // and takes the general path, called outside the loop so that the loop
     // keeps no call frame)
-    if (overflow) dig += dense_overflow_method<REC, DIG, KEEP>(cx, oc, st.hdr[0], mb, D0, c, dest_rec);
+    if (overflow) dig += dense_overflow_method<REC, DIG, KEEP>(cx, oc, st.hdr[0], st.mid[0], D0, c, dest_rec);
     for (int32_t j = 0; j < k && !overflow; ++j) {
-      const int32_t m = mb + j;
+      const int32_t m = st.mid[j];
       const MoveHdr h = st.hdr[j];
       const int32_t C = h.w0.x;
       const int64_t rowbase = (int64_t)m * row;
@@ -1220,7 +1224,7 @@ __device__ __forceinline__ uint64_t dense_tile(const DenseSys &sy, const OutCtx 
         const int32_t code = have ? (int32_t)st.hl[i] : 0;
         const int32_t j = code >> 10, rel = code & (DB_SPAN - 1);
         const int32_t D = D0 + rel;
-        const int32_t m = mb + j;
+        const int32_t m = st.mid[j];
         const int32_t C = have ? st.hdr[j].w0.x : -1;
         const bool act = have && D < c && D != C;
         int32_t dck = 0, dcbo = 0;
@@ -2552,6 +2556,28 @@ void eval_csr_kept_append(mm_system *s, const mm_criteria &crit, const int64_t *
   oc.kept_cap = cap;
   oc.kept_mark = mark;
   dispatch_eval(s, cx, oc, rowptr, dst);
+}
+
+// Kept moves of the methods mlist[0..n) to every other class (the dense
+// tiles over a method list), appended to a kept list.
+void eval_dense_kept_subset(mm_system *s, const mm_criteria &crit, const int32_t *mlist, int32_t n, mm_move *kept,
+                            int64_t cap, unsigned long long *count, uint8_t *mark) {
+  if (n <= 0) return;
+  EvalCtx cx = make_ctx(s, crit);
+  OutCtx oc{};
+  oc.kept = kept;
+  oc.kept_count = count;
+  oc.kept_cap = cap;
+  oc.kept_mark = mark;
+  const int32_t c = s->c;
+  const unsigned gx = (unsigned)ceil_div(c, DB_SPAN);
+  const int64_t want_y = std::max<int64_t>(1, (B300_SMS * 3 * 30) / gx);
+  const int32_t mchunk = (int32_t)std::max<int64_t>(1, ceil_div(n, want_y));
+  const unsigned gy = (unsigned)ceil_div(n, mchunk);
+  DenseSys sy{cx, s->dest_rec, c, n};
+  sy.mlist = mlist;
+  pdl_launch(eval_dense<false, false, true>, dim3(gx, gy), DB_THREADS, 0, s->stream, sy, oc, mchunk);
+  MM_LAUNCH_CHECK();
 }
 
 // Records of internal (valid by construction) device candidate lists; the
