@@ -24,8 +24,9 @@ Measured in the same run and reported as nested keys:
            requests: capacity, p50/p99 latency at half of it, every 1,000th
            state checked against the oracle;
   rules    the similarity values of the large system (values/s, pairs
-           assessed/s), rule R1 on the medium system, rule R3 on the large
-           system, four rounds of non-conflicting moves on the medium system.
+           assessed/s), the LCOM/CBO variants of the large system, rule R1 on
+           the medium system, rule R3 on the large system, four rounds of
+           non-conflicting moves on the medium system.
 The oracle checks run in a separate low-priority process started before the
 first GPU call, beside the GPU sections; the CPU baseline is timed after them.
 
@@ -696,6 +697,9 @@ def run_serving(args, local_rank, verifier):
 # ---------------------------------------------------------------- nested: similarity, rules R1 and R3, sequences
 
 SIM_ROWS = 40
+# the same eight per-class values, in the same order, as the oracle and the library name them
+VARIANT_FIELDS_ORACLE = ("P_all", "Q_all", "ck_all", "pq", "pq_all", "cbo_out", "cbo_in", "cbo_bi")
+VARIANT_FIELDS_GPU = ("P_all", "Q_all", "lcom_ck_all", "lcom_pq", "lcom_pq_all", "cbo_out", "cbo_in", "cbo_bi")
 
 
 def job_oracle_similarity_rows(params, rows):
@@ -728,6 +732,21 @@ def job_oracle_r3(params):
             "top": [tuple(int(v) for v in k) for k in kept[:TOPK]]}
 
 
+def job_oracle_variants(params, topk):
+    """The oracle's metric variants of every class, q_all of every method, and
+    the first topk classes by unclamped LCOM over every accessed attribute
+    and by coupling either way."""
+    import oracle
+    from paper_1308_4011_b300 import synth
+    o = oracle.Oracle(synth.generate(**params))
+    v, q_all = o.class_variants()
+    o.close()
+    cols = np.stack([v[f].astype(np.int64) for f in VARIANT_FIELDS_ORACLE], axis=1)
+    return {"digest": hashlib.sha256(np.ascontiguousarray(cols).tobytes() + q_all.astype(np.int32).tobytes()).hexdigest(),
+            "rank_pq_all": oracle.rank_classes(v["pq_all"], topk).tolist(),
+            "rank_cbo_bi": oracle.rank_classes(v["cbo_bi"], topk).tolist()}
+
+
 def job_oracle_sequence(params, mask, mi, rounds):
     import oracle
     from paper_1308_4011_b300 import synth
@@ -754,6 +773,7 @@ def run_rules(args, local_rank, verifier):
         jobs["r1"] = verifier.submit(job_oracle_r1, medium_p, MASK_LCOM, MIN_IMPROVED, TOPK)
         jobs["r3"] = verifier.submit(job_oracle_r3, large_p)
         jobs["seq"] = verifier.submit(job_oracle_sequence, medium_p, MASK_LCOM, MIN_IMPROVED, 4)
+        jobs["var"] = verifier.submit(job_oracle_variants, large_p, TOPK)
 
     def timed(fn, reps):
         fn()
@@ -788,6 +808,18 @@ def run_rules(args, local_rank, verifier):
                      "note": "whole call (posting lists, keys, radix sort, runs, count read-backs) against the "
                              "bytes of its keys and values"}}
     mmref.compute_metrics(g, None, None)
+    vd = torch.empty(56 * large.n_classes, dtype=torch.uint8, device=dev)
+    qd = torch.empty(4 * large.n_methods, dtype=torch.uint8, device=dev)
+    t, _ = timed(lambda: mmref.metric_variants(g, vd, qd), 5)  # device outputs: nothing read back
+    v, q_all = mmref.metric_variants(g)
+    n_acc = int(large.acc_rowptr[-1])
+    out["variants_large"] = {"seconds": t, "classes_per_s": large.n_classes / t, "accesses_per_s": n_acc / t,
+                             "note": "LCOM over every accessed attribute, unclamped LCOM, CBO in and either way"}
+    cols = np.stack([v[f].astype(np.int64) for f in VARIANT_FIELDS_GPU], axis=1)
+    var_got = {"digest": hashlib.sha256(np.ascontiguousarray(cols).tobytes() +
+                                        q_all.astype(np.int32).tobytes()).hexdigest(),
+               "rank_pq_all": mmref.rank_classes(g, mmref.RANK_LCOM_PQ_ALL, TOPK)[0].tolist(),
+               "rank_cbo_bi": mmref.rank_classes(g, mmref.RANK_CBO_BI, TOPK)[0].tolist()}
     t, (top3, nk3, nc3, nh3) = timed(lambda: mmref.suggest_r3(g, TOPK), 5)
     out["r3_large"] = {"seconds": t, "n_candidates": nc3, "n_kept": nk3, "n_high_classes": nh3,
                        "candidates_per_s": nc3 / t}
@@ -808,19 +840,21 @@ def run_rules(args, local_rank, verifier):
                               "per_round": np.bincount(seq["round"], minlength=4).tolist() if len(seq) else []}
     seq_got = [tuple(int(v) for v in r) for r in seq]
     g.free()
-    return out, (jobs, sim_rows, r1_got, r3_got, seq_got)
+    return out, (jobs, sim_rows, r1_got, r3_got, seq_got, var_got)
 
 
 def collect_rules(check):
-    jobs, sim_rows, r1_got, r3_got, seq_got = check
+    jobs, sim_rows, r1_got, r3_got, seq_got, var_got = check
     if not jobs:
         return None
     ok_sim = jobs["sim"].get() == sim_rows
     ok_r1 = jobs["r1"].get() == r1_got
     ok_r3 = jobs["r3"].get() == r3_got
     ok_seq = jobs["seq"].get() == seq_got
-    return {"ok": bool(ok_sim and ok_r1 and ok_r3 and ok_seq), "similarity_sampled_rows": bool(ok_sim),
-            "similarity_rows": SIM_ROWS, "r1": bool(ok_r1), "r3": bool(ok_r3), "sequence": bool(ok_seq)}
+    ok_var = jobs["var"].get() == var_got
+    return {"ok": bool(ok_sim and ok_r1 and ok_r3 and ok_seq and ok_var), "similarity_sampled_rows": bool(ok_sim),
+            "similarity_rows": SIM_ROWS, "r1": bool(ok_r1), "r3": bool(ok_r3), "sequence": bool(ok_seq),
+            "variants": bool(ok_var)}
 
 
 # ---------------------------------------------------------------- the reference arm

@@ -219,6 +219,7 @@ MMREF_API mm_status mm_batch_create(mm_system *const *systems, int32_t n, const 
     for (int32_t i = 0; i < n; ++i) {
       if (!systems[i]) throw MmError{MM_EINVAL, "batch_create: NULL system"};
       if (systems[i]->device != b->device) throw MmError{MM_EINVAL, "batch_create: systems on another device"};
+      use_bitset_coupling(systems[i]);  // the captured dense evaluation reads the bitsets
       b->sys.push_back(systems[i]);
     }
     b->mark_off.resize(n);

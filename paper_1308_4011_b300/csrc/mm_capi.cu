@@ -58,7 +58,7 @@ struct SystemScope {
 void release_system(mm_system *s) {
   s->arena.release();
   for (Scratch *w : {&s->sort_ws, &s->eval_ws, &s->stage_ws, &s->kept_ws, &s->keyed_ws, &s->edit_ws, &s->sim_ws,
-                     &s->sim_keys_ws, &s->sim_val_ws, &s->r1_ws, &s->var_ws, &s->var_keys_ws,
+                     &s->sim_keys_ws, &s->sim_val_ws, &s->r1_ws, &s->var_ws, &s->var_keys_ws, &s->adj_ws,
                      &s->union_ws, &s->side_eval[0], &s->side_eval[1], &s->side_eval[2], &s->side_sort[0],
                      &s->side_sort[1], &s->side_sort[2], &s->side_union[0], &s->side_union[1], &s->side_union[2]})
     w->release(s->stream);
@@ -157,8 +157,13 @@ void allocate_compute_buffers(mm_system *s) {
   s->mg_cnt = a.get<int32_t>(nu);
   s->mg_count = a.get<int64_t>(2);
   s->adj_words = ((c + 127) / 128) * 4;  // rows padded to 16 bytes for vector loads
-  s->out_adj = a.get<uint32_t>(s->adj_words * c);
-  s->in_adj = a.get<uint32_t>(s->adj_words * c);
+  if (s->sorted_coupling) {  // built on demand from the multigraph rows
+    s->out_adj = nullptr;
+    s->in_adj = nullptr;
+  } else {
+    s->out_adj = a.get<uint32_t>(s->adj_words * c);
+    s->in_adj = a.get<uint32_t>(s->adj_words * c);
+  }
   s->sum_words = (s->adj_words + 31) / 32;
   s->csum = a.get<uint2>(s->sum_words * (2 * c + 1));
   s->cpk = a.get<uint32_t>(2 * nu);
@@ -284,6 +289,13 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     s->n_acc = desc->n_acc;
     s->n_call = desc->n_call;
     s->cbo_attrs = desc->cbo_attrs ? 1 : 0;
+    if (desc->flags & ~(int32_t)(MM_LOAD_SORTED_COUPLING | MM_LOAD_BITSET_COUPLING))
+      throw MmError{MM_EINVAL, "load_system: unknown flags"};
+    {
+      const double bitset_bytes = 8.0 * (double)((s->c + 127) / 128 * 4) * (double)s->c;
+      s->sorted_coupling = (desc->flags & MM_LOAD_SORTED_COUPLING) ||
+                           (!(desc->flags & MM_LOAD_BITSET_COUPLING) && bitset_bytes > MM_SORTED_COUPLING_BYTES);
+    }
     const int64_t M = s->M, A = s->A;
     // size every load-time buffer, reserve one slab, then carve them out of it
     s->arena.sizing = true;

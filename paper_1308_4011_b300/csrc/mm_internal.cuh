@@ -239,6 +239,12 @@ struct mm_system {
   int64_t *mg_count;               // device scalar: number of distinct (Y, E)
   uint32_t *out_adj, *in_adj;
   int64_t adj_words;
+  // coupling built by sorting the use edges (large systems): the full bitsets
+  // above are then built from the multigraph rows only when a dense
+  // evaluation needs them (adj_ws), and adj_built says whether they are current
+  bool sorted_coupling = false;
+  bool adj_built = false;
+  Scratch adj_ws;
   // compressed two-level adjacency for the restricted evaluation (L2-resident).
   // Rows 0..c-1 are the out-rows, rows c..2c-1 the in-rows, row 2c is all zero.
   // Record k of a row = {bits, first}: bit j set iff full word 32 k + j of the
@@ -402,6 +408,11 @@ __device__ __forceinline__ int32_t accessor_union(const int32_t *acc_row, int64_
 // variant buffers (mm_variants.cu); the first k classes by a metric.
 void compute_variants(mm_system *s, mm_class_variants **out, int32_t **q_all);
 void rank_classes(mm_system *s, int32_t metric, int32_t k, int32_t *out_ids, int64_t *out_values, int32_t kind);
+// Full adjacency bitsets current for the dense kernels (built from the
+// multigraph rows when the coupling was sorted); switch a system to building
+// them with its coupling (mm_metrics.cu).
+void ensure_adjacency(mm_system *s);
+void use_bitset_coupling(mm_system *s);
 void build_metrics(mm_system *s);                   // mm_metrics.cu
 void build_move_precompute(mm_system *s);           // mm_moves.cu
 void export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *out_m, int32_t kind);

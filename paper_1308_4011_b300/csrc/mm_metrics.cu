@@ -327,6 +327,147 @@ __global__ void summary_pack(uint2 *sum, const int64_t *first, const uint32_t *o
   }
 }
 
+// ---------------------------------------------------------------- coupling without the full bitsets
+//
+// For systems whose full adjacency bitsets would be large, the compressed
+// adjacency is built from the use edges themselves and the multigraph is read
+// off it: every edge (Y, E), E != Y, sets the summary bits of its out-row
+// record (Y, E >> 10) and in-row record (c + E, Y >> 10); the records' first
+// packed indices follow by a scan of their popcounts, and each edge ORs its
+// bit into the packed word its record points at (a repeated edge sets the
+// same bit).  The packed words of an out-row hold its classes in ascending
+// order, so counting and enumerating them gives the multigraph rows; the
+// multiplicities are counted per edge as in the bitset form.  The full
+// bitsets are built from the multigraph rows only when a dense evaluation
+// asks for them.
+
+__device__ __forceinline__ void mark_summary(uint2 *csum, int64_t sw, int64_t row, int32_t col) {
+  uint32_t *r = &csum[row * sw + (col >> 10)].x;
+  const uint32_t bit = 1u << ((col >> 5) & 31);
+  if (!(*r & bit)) atomicOr(r, bit);
+}
+
+// edge keys (Y << 32 | E, or ~0 inside the class) at the method's calls, then
+// its accesses, and the summary bits of both rows of every coupling edge
+__global__ void coupling_keys(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
+                              const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
+                              int32_t M, int32_t c, int32_t cbo_attrs, uint2 *csum, int64_t sw, uint64_t *edges) {
+  pdl_wait();
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < M; x += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t Y = method_class[x];
+    int64_t pos = call_rowptr[x] + (cbo_attrs ? acc_rowptr[x] : 0);
+    const int64_t ne = call_rowptr[x + 1] - call_rowptr[x];
+    const int64_t na = cbo_attrs ? acc_rowptr[x + 1] - acc_rowptr[x] : 0;
+    for (int64_t k = 0; k < ne + na; ++k) {
+      const int32_t E = k < ne ? method_class[call_idx[call_rowptr[x] + k]] : attr_class[acc_idx[acc_rowptr[x] + k - ne]];
+      if (E != Y) {
+        mark_summary(csum, sw, Y, E);
+        mark_summary(csum, sw, (int64_t)c + E, Y);
+        edges[pos++] = ((uint64_t)(uint32_t)Y << 32) | (uint32_t)E;
+      } else {
+        edges[pos++] = ~0ull;
+      }
+    }
+  }
+}
+
+__global__ void summary_first(uint2 *sum, const int64_t *first, int64_t n) {
+  pdl_wait();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    sum[i].y = (uint32_t)first[i];
+}
+
+__device__ __forceinline__ void pack_bit(const uint2 *csum, int64_t sw, int64_t row, int32_t col, uint32_t *cpk) {
+  const uint2 rec = csum[row * sw + (col >> 10)];
+  const uint32_t b = ((uint32_t)col >> 5) & 31u;
+  atomicOr(&cpk[rec.y + __popc(rec.x & ((1u << b) - 1u))], 1u << (col & 31));
+}
+
+// every edge's bit in the packed words of its out-row and in-row
+__global__ void coupling_pack(const uint64_t *edges, int64_t n, int32_t c, const uint2 *csum, int64_t sw,
+                              uint32_t *cpk) {
+  pdl_wait();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = edges[i];
+    if (k == ~0ull) continue;
+    const int32_t Y = (int32_t)(k >> 32), E = (int32_t)(uint32_t)k;
+    pack_bit(csum, sw, Y, E, cpk);
+    pack_bit(csum, sw, (int64_t)c + E, Y, cpk);
+  }
+}
+
+// CBO(Y) = classes in out-row Y = the bits of its packed words, which lie
+// between its first record's index and the next row's (warp per row)
+__global__ void packed_row_counts(const uint2 *csum, const uint32_t *cpk, int32_t c, int64_t sw, int32_t *row_count) {
+  pdl_wait();
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t Y = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; Y < c; Y += nwarps) {
+    const uint32_t w0 = csum[Y * sw].y, w1 = csum[(Y + 1) * sw].y;
+    int32_t n = 0;
+    for (uint32_t w = w0 + lane; w < w1; w += 32) n += __popc(cpk[w]);
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if (lane == 0) row_count[Y] = n;
+  }
+}
+
+// the classes of out-row Y in ascending order at mg_rowptr[Y], counts zeroed
+// (warp per row, lane per summary record; records ascend with the lane)
+__global__ void packed_row_enumerate(const uint2 *csum, const uint32_t *cpk, int32_t c, int64_t sw,
+                                     const int64_t *mg_rowptr, int32_t *mg_dst, int32_t *mg_cnt) {
+  pdl_wait();
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t Y = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; Y < c; Y += nwarps) {
+    int64_t pos = mg_rowptr[Y];
+    for (int64_t k0 = 0; k0 < sw; k0 += 32) {
+      const int64_t k = k0 + lane;
+      uint2 rec = make_uint2(0u, 0u);
+      int32_t n = 0;
+      if (k < sw) {
+        rec = csum[Y * sw + k];
+        const int32_t nw = __popc(rec.x);
+        for (int32_t j = 0; j < nw; ++j) n += __popc(cpk[rec.y + j]);
+      }
+      int32_t incl = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += t;
+      }
+      int64_t p = pos + incl - n;
+      uint32_t bits = rec.x;
+      for (uint32_t idx = rec.y; bits; ++idx) {
+        const int j = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        uint32_t word = cpk[idx];
+        while (word) {
+          const int b = __ffs(word) - 1;
+          word &= word - 1u;
+          mg_dst[p] = (int32_t)(((k * 32 + j) << 5) + b);
+          mg_cnt[p] = 0;
+          ++p;
+        }
+      }
+      pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
+// full bitsets from the multigraph rows: bit E of out-row Y and bit Y of in-row E
+__global__ void adjacency_from_rows(const int64_t *mg_rowptr, const int32_t *mg_dst, int32_t c, int64_t aw,
+                                    uint32_t *out_adj, uint32_t *in_adj) {
+  pdl_wait();
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t Y = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; Y < c; Y += nwarps)
+    for (int64_t k = mg_rowptr[Y] + lane; k < mg_rowptr[Y + 1]; k += 32) {
+      const int32_t E = mg_dst[k];
+      atomicOr(&out_adj[Y * aw + (E >> 5)], 1u << (E & 31));
+      atomicOr(&in_adj[(int64_t)E * aw + (Y >> 5)], 1u << (Y & 31));
+    }
+}
+
 // destination record: {P - Q, S} as int64 in the first int4; {n, a, dck0, sck0 | shs0 << 8}
 // in the second, where the last three are D's LCOM outcome when m shares nothing with D
 __global__ void destination_records(const int32_t *cls_n, const int32_t *cls_a, const int64_t *P, const int64_t *Q,
@@ -461,13 +602,62 @@ void build_metrics(mm_system *s) {
   // lists L and R (first half) on side streams 1 and 2
   begin_move_lists(s);
 
-  // coupling: mark the use edges in the out-rows, count and enumerate the
-  // marked classes row by row (ascending, so no sort), then count multiplicities
   const int64_t aw = s->adj_words, sw = s->sum_words;
-  zero_buffers(s->out_adj, sizeof(uint32_t) * (size_t)(aw * c), s->in_adj, sizeof(uint32_t) * (size_t)(aw * c),
-               s->csum, sizeof(uint2) * (size_t)(sw * (2 * c + 1)), st);
+  const int64_t ns = sw * (2 * (int64_t)c + 1);  // summary records: out-rows, in-rows, the zero row
   int32_t *row_count = s->cls_cbo;
   const int64_t nk = s->n_call + (s->cbo_attrs ? s->n_acc : 0);
+  if (s->sorted_coupling) {
+    // coupling from the use edges through the compressed rows; the full
+    // bitsets wait for a dense evaluation
+    s->adj_built = false;
+    Carve cv{static_cast<char *>(s->eval_ws.need(
+        256 * 4 + sizeof(uint64_t) * (size_t)std::max<int64_t>(nk, 1) + (sizeof(int64_t) + sizeof(int32_t)) * (size_t)ns,
+        st))};
+    uint64_t *edges = cv.take<uint64_t>(nk);
+    int64_t *first = cv.take<int64_t>(ns);
+    int32_t *cnt = cv.take<int32_t>(ns);
+    zero_buffers(s->csum, sizeof(uint2) * (size_t)ns, s->cpk, sizeof(uint32_t) * 2 * (size_t)nk, nullptr, 0, st);
+    if (M > 0) {
+      pdl_launch(coupling_keys, grid_for(M), TPB, 0, st, s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
+                 s->acc_idx, s->attr_class, M, c, s->cbo_attrs, s->csum, sw, edges);
+      MM_LAUNCH_CHECK();
+    }
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(ns, TPB), B300_SMS * 16);
+    pdl_launch(summary_popc, g, TPB, 0, st, static_cast<const uint2 *>(s->csum), ns, cnt);
+    MM_LAUNCH_CHECK();
+    scan_exclusive_i32to64(cnt, first, ns, s->sort_ws, st);
+    pdl_launch(summary_first, g, TPB, 0, st, s->csum, static_cast<const int64_t *>(first), ns);
+    MM_LAUNCH_CHECK();
+    const unsigned grow = (unsigned)std::min<int64_t>(ceil_div((int64_t)c * 32, TPB), B300_SMS * 16);
+    if (nk > 0) {
+      const unsigned gk = (unsigned)std::min<int64_t>(ceil_div(nk, TPB), B300_SMS * 16);
+      pdl_launch(coupling_pack, gk, TPB, 0, st, static_cast<const uint64_t *>(edges), nk, c,
+                 static_cast<const uint2 *>(s->csum), sw, s->cpk);
+      MM_LAUNCH_CHECK();
+    }
+    pdl_launch(packed_row_counts, grow, TPB, 0, st, static_cast<const uint2 *>(s->csum),
+               static_cast<const uint32_t *>(s->cpk), c, sw, row_count);
+    MM_LAUNCH_CHECK();
+    scan_exclusive_i32to64(row_count, s->mg_rowptr, c, s->sort_ws, st, s->mg_rowptr + c);
+    pdl_launch(packed_row_enumerate, grow, TPB, 0, st, static_cast<const uint2 *>(s->csum),
+               static_cast<const uint32_t *>(s->cpk), c, sw, static_cast<const int64_t *>(s->mg_rowptr), s->mg_dst,
+               s->mg_cnt);
+    MM_LAUNCH_CHECK();
+    if (nk > 0) {
+      pdl_launch(coupling_count, (unsigned)std::min<int64_t>(ceil_div(nk, TPB), B300_SMS * 16), TPB, 0, st,
+                 static_cast<const uint64_t *>(edges), nk, static_cast<const int64_t *>(s->mg_rowptr),
+                 static_cast<const int32_t *>(s->mg_dst), s->mg_cnt);
+      MM_LAUNCH_CHECK();
+    }
+    MM_CUDA_TRY(cudaMemcpyAsync(s->mg_count, s->mg_rowptr + c, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    mark_point(s, 0, st);  // multigraph rows and counts built (the list look-ups need them)
+    join_side(s, 0, s->side_pending[0]);
+    return;
+  }
+  // coupling (bitsets): mark the use edges in the out-rows, count and enumerate
+  // the marked classes row by row (ascending, so no sort), then count multiplicities
+  zero_buffers(s->out_adj, sizeof(uint32_t) * (size_t)(aw * c), s->in_adj, sizeof(uint32_t) * (size_t)(aw * c),
+               s->csum, sizeof(uint2) * (size_t)(sw * (2 * c + 1)), st);
   uint64_t *edges = static_cast<uint64_t *>(s->eval_ws.need(sizeof(uint64_t) * (size_t)std::max<int64_t>(nk, 1), st));
   if (M > 0) {
     pdl_launch(coupling_mark, grid_for(M), TPB, 0, st, s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
@@ -492,7 +682,6 @@ void build_metrics(mm_system *s) {
   mark_point(s, 0, st);  // multigraph rows and counts built (the list look-ups need them)
   // compressed adjacency: record counts -> exclusive scan -> packed non-zero words
   {
-    const int64_t ns = s->sum_words * (2 * (int64_t)c + 1);
     char *b = static_cast<char *>(s->eval_ws.need((sizeof(int32_t) + sizeof(int64_t)) * (size_t)ns + 16, st));
     int64_t *first = reinterpret_cast<int64_t *>(b);
     int32_t *cnt = reinterpret_cast<int32_t *>(first + ns);
@@ -504,5 +693,36 @@ void build_metrics(mm_system *s) {
                                     s->cpk);
     MM_LAUNCH_CHECK();
   }
+  s->adj_built = true;
   join_side(s, 0, s->side_pending[0]);
+}
+
+// The full adjacency bitsets, from the multigraph rows, for a system whose
+// coupling was built by sorting (allocated on first use).
+void ensure_adjacency(mm_system *s) {
+  if (s->adj_built) return;
+  cudaStream_t st = s->stream;
+  const int64_t words = s->adj_words * (int64_t)s->c;
+  uint32_t *p = static_cast<uint32_t *>(s->adj_ws.need(2 * sizeof(uint32_t) * (size_t)words, st));
+  s->out_adj = p;
+  s->in_adj = p + words;
+  zero_buffers(s->out_adj, sizeof(uint32_t) * (size_t)words, s->in_adj, sizeof(uint32_t) * (size_t)words, nullptr, 0,
+               st);
+  const unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)s->c * 32, TPB), B300_SMS * 16);
+  pdl_launch(adjacency_from_rows, g, TPB, 0, st, static_cast<const int64_t *>(s->mg_rowptr),
+             static_cast<const int32_t *>(s->mg_dst), s->c, s->adj_words, s->out_adj, s->in_adj);
+  MM_LAUNCH_CHECK();
+  s->adj_built = true;
+}
+
+// Build the coupling with the full bitsets from now on (for callers that read
+// them inside captured work, such as a batch's graph).
+void use_bitset_coupling(mm_system *s) {
+  if (!s->sorted_coupling) return;
+  const int64_t words = s->adj_words * (int64_t)s->c;
+  uint32_t *p = static_cast<uint32_t *>(s->adj_ws.need(2 * sizeof(uint32_t) * (size_t)words, s->stream));
+  s->out_adj = p;
+  s->in_adj = p + words;
+  s->sorted_coupling = false;
+  s->adj_built = false;
 }

@@ -615,11 +615,34 @@ struct EvalCtx {
   const int4 *l_list;
   const int32_t *l_s;
   const int4 *r_list;
-  const uint32_t *in_adj, *out_adj;
+  const uint32_t *in_adj, *out_adj;  // full bitsets (dense evaluation)
   int64_t aw;
+  const uint2 *csum;                 // compressed rows (candidate lists): out-rows, then in-rows
+  const uint32_t *cpk;
+  int64_t sw;
+  int32_t c;
+  int32_t packed;                    // general-path probes read the compressed rows, not the bitsets
   uint32_t mask;
   int32_t min_improved;
 };
+
+// bit col of compressed row r: its summary record, then the packed word if marked
+__device__ __forceinline__ int packed_bit(const EvalCtx &cx, int64_t r, int32_t col) {
+  const uint2 rec = __ldg(cx.csum + r * cx.sw + (col >> 10));
+  const uint32_t b = ((uint32_t)col >> 5) & 31u;
+  if (!((rec.x >> b) & 1u)) return 0;
+  return (int)((__ldg(cx.cpk + rec.y + __popc(rec.x & ((1u << b) - 1u))) >> (col & 31)) & 1u);
+}
+// does class D use class E (in-row of E at D)
+__device__ __forceinline__ int uses_in(const EvalCtx &cx, int32_t E, int32_t D) {
+  if (cx.packed) return packed_bit(cx, (int64_t)cx.c + E, D);
+  return (int)((__ldg(cx.in_adj + (int64_t)E * cx.aw + ((uint32_t)D >> 5)) >> ((uint32_t)D & 31u)) & 1u);
+}
+// does class X use class D (out-row of X at D)
+__device__ __forceinline__ int uses_out(const EvalCtx &cx, int32_t X, int32_t D) {
+  if (cx.packed) return packed_bit(cx, X, D);
+  return (int)((__ldg(cx.out_adj + (int64_t)X * cx.aw + ((uint32_t)D >> 5)) >> ((uint32_t)D & 31u)) & 1u);
+}
 
 __device__ __forceinline__ int dec_sign(uint32_t e) { return e == 1u ? -1 : (e == 2u ? 1 : 0); }
 __device__ __forceinline__ uint32_t sat_u16(int32_t v) { return v < 0 ? 0u : (v > 65535 ? 65535u : (uint32_t)v); }
@@ -708,7 +731,6 @@ __device__ __forceinline__ uint4 eval_move(const EvalCtx &cx, const MoveHdr &h, 
                                            int32_t &dcbo_sum) {
   const int32_t D = ds.D;
   const int32_t C = h.w0.x;
-  const uint32_t dword = (uint32_t)D >> 5, dbit = (uint32_t)D & 31u;
   Gathered g;
   g.gain = 0; g.impX = 0; g.worX = 0; g.t = 0; g.sh = 0; g.outD = 0; g.cntCD = 0; g.inD = 0; g.cntDC = 0;
   const int4 *L = cx.l_list + h.w0.y;
@@ -720,7 +742,7 @@ __device__ __forceinline__ uint4 eval_move(const EvalCtx &cx, const MoveHdr &h, 
       g.t = v.w;
       g.sh = v.w > 0 ? __ldg(cx.l_s + h.w0.y + e) : 0;
     } else if (v.y > 0) {
-      g.gain += 1 - (int)((__ldg(cx.in_adj + (int64_t)v.x * cx.aw + dword) >> dbit) & 1u);
+      g.gain += 1 - uses_in(cx, v.x, D);
     }
   }
   const int4 *R = cx.r_list + h.w0.w;
@@ -731,14 +753,14 @@ __device__ __forceinline__ uint4 eval_move(const EvalCtx &cx, const MoveHdr &h, 
       g.cntDC = v.z;
     } else {
       int loss = v.z == v.y;
-      int gx = 1 - (int)((__ldg(cx.out_adj + (int64_t)v.x * cx.aw + dword) >> dbit) & 1u);
+      int gx = 1 - uses_out(cx, v.x, D);
       int dx = gx - loss;
       g.impX += dx < 0;
       g.worX += dx > 0;
     }
   }
-  g.bDC = (int)((__ldg(cx.in_adj + (int64_t)C * cx.aw + dword) >> dbit) & 1u);
-  g.bCD = (int)((__ldg(cx.out_adj + (int64_t)C * cx.aw + dword) >> dbit) & 1u);
+  g.bDC = uses_in(cx, C, D);
+  g.bCD = uses_out(cx, C, D);
   return finish_move(h, ds, g, cx.mask, cx.min_improved, dck_sum, dcbo_sum);
 }
 
@@ -1734,8 +1756,17 @@ __global__ void __launch_bounds__(256) validate_cand_dst(const int64_t *rowptr, 
 }
 
 template <bool REC, bool DIG, bool KEEP>
-void launch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_t *rowptr, const int32_t *dst) {
+void launch_eval(mm_system *s, const EvalCtx &cx_in, const OutCtx &oc, const int64_t *rowptr, const int32_t *dst) {
   cudaStream_t st = s->stream;
+  EvalCtx cx = cx_in;
+  if (!rowptr) {  // the dense tiles read the full bitsets
+    ensure_adjacency(s);
+    cx.in_adj = s->in_adj;
+    cx.out_adj = s->out_adj;
+    cx.packed = 0;
+  } else {  // candidate lists: every probe reads the compressed rows
+    cx.packed = 1;
+  }
   if (!rowptr) {
     const int32_t c = s->c, M = s->M;
     unsigned gx = (unsigned)ceil_div(c, DB_SPAN);
@@ -2162,6 +2193,11 @@ static EvalCtx make_ctx(mm_system *s, const mm_criteria &crit) {
   cx.in_adj = s->in_adj;
   cx.out_adj = s->out_adj;
   cx.aw = s->adj_words;
+  cx.csum = s->csum;
+  cx.cpk = s->cpk;
+  cx.sw = s->sum_words;
+  cx.c = s->c;
+  cx.packed = 0;
   cx.mask = crit.metric_mask;
   cx.min_improved = crit.min_improved;
   return cx;
@@ -2563,6 +2599,7 @@ void eval_csr_kept_append(mm_system *s, const mm_criteria &crit, const int64_t *
 void eval_dense_kept_subset(mm_system *s, const mm_criteria &crit, const int32_t *mlist, int32_t n, mm_move *kept,
                             int64_t cap, unsigned long long *count, uint8_t *mark) {
   if (n <= 0) return;
+  ensure_adjacency(s);
   EvalCtx cx = make_ctx(s, crit);
   OutCtx oc{};
   oc.kept = kept;

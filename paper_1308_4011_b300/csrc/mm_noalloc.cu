@@ -109,6 +109,10 @@ extern "C" MMREF_API mm_status mm_suggest_moves_noalloc(mm_system *s, const mm_c
       if (cudaSetDevice(s->device) != cudaSuccess) throw MmError{MM_ECUDA, "cudaSetDevice failed"};
       guard.prev = cur;
     }
+    if ((!cands || !cands->rowptr) && !s->adj_built)
+      throw MmError{MM_EBUDGET, "suggest_moves_noalloc: the full cross product needs the system's adjacency "
+                                "bitsets, which are built on demand for systems with sorted coupling; use "
+                                "mm_suggest_moves"};
     WaitScope wait(s->d_fault, &s->test_stall_scans);
     unsigned char *base = scratch_for_device(s->device);
     unsigned long long *counters = reinterpret_cast<unsigned long long *>(base);  // [0] kept, [1] methods

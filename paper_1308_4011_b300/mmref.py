@@ -55,9 +55,10 @@ class _Desc(ctypes.Structure):
                 ("method_class", ctypes.c_void_p), ("attr_class", ctypes.c_void_p),
                 ("acc_rowptr", ctypes.c_void_p), ("acc_idx", ctypes.c_void_p),
                 ("call_rowptr", ctypes.c_void_p), ("call_idx", ctypes.c_void_p),
-                ("cbo_attrs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("cbo_attrs", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
+LOAD_SORTED_COUPLING, LOAD_BITSET_COUPLING = 1, 2
 class _Crit(ctypes.Structure):
     _fields_ = [("metric_mask", ctypes.c_uint32), ("min_improved", ctypes.c_int32)]
 
@@ -251,8 +252,9 @@ class System:
 
 
 def load_system(n_classes, method_class, attr_class, acc_rowptr, acc_idx, call_rowptr, call_idx, *,
-                cbo_attrs: bool = True, stream=None) -> System:
-    """mm_load_system.  Arrays are either all numpy (host) or all CUDA tensors."""
+                cbo_attrs: bool = True, stream=None, flags: int = 0) -> System:
+    """mm_load_system.  Arrays are either all numpy (host) or all CUDA tensors;
+    flags: 0 or LOAD_SORTED_COUPLING / LOAD_BITSET_COUPLING."""
     arrs = (method_class, attr_class, acc_rowptr, acc_idx, call_rowptr, call_idx)
     kinds = {_kind(a) for a in arrs}
     if len(kinds) != 1:
@@ -264,13 +266,13 @@ def load_system(n_classes, method_class, attr_class, acc_rowptr, acc_idx, call_r
     n_methods = int(arrs[0].shape[0])
     d = _Desc(int(n_classes), n_methods, int(arrs[1].shape[0]), kind, int(arrs[3].shape[0]), int(arrs[5].shape[0]),
               _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), _ptr(arrs[3]), _ptr(arrs[4]), _ptr(arrs[5]),
-              1 if cbo_attrs else 0, 0)
+              1 if cbo_attrs else 0, int(flags))
     h = ctypes.c_void_p()
     _check(_lib.mm_load_system(ctypes.byref(d), _stream_handle(stream), ctypes.byref(h)))
     return System(h.value, int(n_classes), n_methods, int(arrs[1].shape[0]), arrs)
 
 
-def load_synth(system, *, cbo_attrs: bool = True, device: bool = False, stream=None) -> System:
+def load_synth(system, *, cbo_attrs: bool = True, device: bool = False, stream=None, flags: int = 0) -> System:
     """Load a ``synth.System``; with device=True the arrays are first moved to
     CUDA tensors (the inputs-resident-in-HBM form)."""
     arrs = (system.method_class, system.attr_class, system.acc_rowptr, system.acc_idx, system.call_rowptr,
@@ -278,7 +280,7 @@ def load_synth(system, *, cbo_attrs: bool = True, device: bool = False, stream=N
     if device:
         import torch
         arrs = tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs)
-    return load_system(system.n_classes, *arrs, cbo_attrs=cbo_attrs, stream=stream)
+    return load_system(system.n_classes, *arrs, cbo_attrs=cbo_attrs, stream=stream, flags=flags)
 
 
 def compute_metrics(sys: System, out_class=None, out_method=None):
