@@ -197,14 +197,23 @@ typedef struct {
  * Otherwise a CSR over methods: rowptr[n_methods+1] (int64, rowptr[0] = 0,
  * non-decreasing, rowptr[n_methods] = n_cand) and dst[n_cand] destination
  * classes, each in range and different from the method's class; index i is
- * the position in dst.
+ * the position in dst.  Every call that takes lists checks them on the device
+ * and hashes their content (the key of the kept-move cache).  flags: 0, or
+ * MM_CANDS_UNCHANGED: the caller states that these are the same device lists
+ * (same rowptr and dst pointers, same n_cand, same content) as in the last
+ * call on this handle that took lists, with no edit of the system since; the
+ * library then reuses that call's check and hash.  When the pointers, length
+ * or edit count differ from that call's, the flag is ignored and the lists
+ * are checked again; lists rewritten in place under the flag are the
+ * caller's error (results undefined, no fault).
  */
+enum { MM_CANDS_UNCHANGED = 1 };
 typedef struct {
   const int64_t *rowptr;
   const int32_t *dst;
   int64_t n_cand;
   int32_t ptr_kind;
-  int32_t reserved;
+  int32_t flags;
 } mm_candidates;
 
 typedef struct {

@@ -2141,8 +2141,18 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
   }
   if (cands->n_cand < 0) throw MmError{MM_EINVAL, "candidates: n_cand < 0"};
   if (cands->n_cand > 0 && !cands->dst) throw MmError{MM_EINVAL, "candidates: dst is NULL"};
+  if (cands->flags & ~(int32_t)MM_CANDS_UNCHANGED) throw MmError{MM_EINVAL, "candidates: unknown flags"};
   *n_cand = cands->n_cand;
   cudaStream_t st = s->stream;
+  if ((cands->flags & MM_CANDS_UNCHANGED) && cands->ptr_kind == MM_PTR_DEVICE && s->lists_checked &&
+      s->lists_rowptr == cands->rowptr && s->lists_dst == cands->dst && s->lists_n == cands->n_cand &&
+      s->lists_edits == s->edits) {  // the caller's lists were checked and hashed by the last call
+    *rowptr = cands->rowptr;
+    *dst = cands->dst;
+    if (hash) *hash = s->lists_hash;
+    return;
+  }
+  s->lists_checked = false;
   if (cands->ptr_kind == MM_PTR_HOST) {
     size_t rb = sizeof(int64_t) * ((size_t)s->M + 1), db = sizeof(int32_t) * (size_t)cands->n_cand;
     char *b = static_cast<char *>(ws.need(rb + db + 256, st));
@@ -2178,10 +2188,20 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
   MM_CUDA_TRY(cudaStreamSynchronize(st));
   uint32_t err = 0;
   std::memcpy(&err, hb + 24, sizeof(uint32_t));
-  if (hash) std::memcpy(hash, hb, sizeof(uint64_t));
+  uint64_t h = 0;
+  std::memcpy(&h, hb, sizeof(uint64_t));
+  if (hash) *hash = h;
   if (err & VE_CAND_ROWPTR) throw MmError{MM_EINVAL, "candidates: rowptr must start at 0, be non-decreasing and end at n_cand"};
   if (err & VE_CAND_RANGE) throw MmError{MM_EINVAL, "candidates: destination class out of range"};
   if (err & VE_CAND_SELF) throw MmError{MM_EINVAL, "candidates: destination equals the method's own class"};
+  if (cands->ptr_kind == MM_PTR_DEVICE) {
+    s->lists_checked = true;
+    s->lists_rowptr = cands->rowptr;
+    s->lists_dst = cands->dst;
+    s->lists_n = cands->n_cand;
+    s->lists_edits = s->edits;
+    s->lists_hash = h;
+  }
 }
 
 static EvalCtx make_ctx(mm_system *s, const mm_criteria &crit) {

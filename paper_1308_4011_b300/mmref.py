@@ -65,7 +65,7 @@ class _Crit(ctypes.Structure):
 
 class _Cands(ctypes.Structure):
     _fields_ = [("rowptr", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("n_cand", ctypes.c_int64),
-                ("ptr_kind", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ptr_kind", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class _SimInfo(ctypes.Structure):
@@ -349,7 +349,10 @@ def suggest_r1(sys: System, k: int, mask: int = DEFAULT_MASK, min_improved: int 
     return (out[:n] if _kind(out) == PTR_HOST else out), int(nk.value), int(nm.value), _sim_info(inf)
 
 
-def _cands(cand_rowptr, cand_dst):
+CANDS_UNCHANGED = 1
+
+
+def _cands(cand_rowptr, cand_dst, flags=0):
     if cand_rowptr is None:
         return None, None
     kind = _kind(cand_rowptr)
@@ -357,17 +360,19 @@ def _cands(cand_rowptr, cand_dst):
         cand_rowptr = np.ascontiguousarray(cand_rowptr, dtype=np.int64)
         cand_dst = np.ascontiguousarray(cand_dst, dtype=np.int32)
     n = int(cand_dst.shape[0])
-    c = _Cands(_ptr(cand_rowptr), _ptr(cand_dst), n, kind, 0)
+    c = _Cands(_ptr(cand_rowptr), _ptr(cand_dst), n, kind, int(flags))
     return c, (cand_rowptr, cand_dst)
 
 
 def evaluate_moves(sys: System, mask: int = DEFAULT_MASK, min_improved: int = DEFAULT_MIN_IMPROVED,
-                   cand_rowptr=None, cand_dst=None, records=None, digest=None):
+                   cand_rowptr=None, cand_dst=None, records=None, digest=None, lists_unchanged: bool = False):
     """mm_evaluate_moves.  records: a numpy array of MOVE_EVAL_DTYPE or a CUDA
     uint8 tensor of 16*n_cand bytes (or None).  digest: a 1-element numpy
-    uint64 array or CUDA int64 tensor (or None).  Both in the same memory."""
+    uint64 array or CUDA int64 tensor (or None).  Both in the same memory.
+    lists_unchanged: the same device lists as the last call that took lists
+    (MM_CANDS_UNCHANGED)."""
     crit = _Crit(mask, min_improved)
-    cd, keep = _cands(cand_rowptr, cand_dst)
+    cd, keep = _cands(cand_rowptr, cand_dst, CANDS_UNCHANGED if lists_unchanged else 0)
     outs = [o for o in (records, digest) if o is not None]
     kind = _kind(outs[0]) if outs else PTR_DEVICE
     if any(_kind(o) != kind for o in outs):
@@ -379,11 +384,12 @@ def evaluate_moves(sys: System, mask: int = DEFAULT_MASK, min_improved: int = DE
 
 
 def suggest_moves(sys: System, k: int, mask: int = DEFAULT_MASK, min_improved: int = DEFAULT_MIN_IMPROVED,
-                  cand_rowptr=None, cand_dst=None, out=None):
+                  cand_rowptr=None, cand_dst=None, out=None, lists_unchanged: bool = False):
     """mm_suggest_moves.  Returns (top-k moves as a MOVE_DTYPE numpy array, or
-    the given out buffer), n_kept, n_methods_with_kept."""
+    the given out buffer), n_kept, n_methods_with_kept.  lists_unchanged: the
+    same device lists as the last call that took lists (MM_CANDS_UNCHANGED)."""
     crit = _Crit(mask, min_improved)
-    cd, keep = _cands(cand_rowptr, cand_dst)
+    cd, keep = _cands(cand_rowptr, cand_dst, CANDS_UNCHANGED if lists_unchanged else 0)
     if out is None:
         out = np.zeros(max(k, 0), dtype=MOVE_DTYPE)
     nk, nm = ctypes.c_int64(), ctypes.c_int64()

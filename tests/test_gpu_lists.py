@@ -1,0 +1,82 @@
+"""Candidate lists passed again with MM_CANDS_UNCHANGED: the evaluation's check
+and content hash are reused only for the same device lists with no edit in
+between; otherwise the lists are checked again."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1308_4011_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1308_4011_b300 import mmref  # noqa: E402
+
+KEPT = ("m", "d", "n_improved", "d_lcom_ck_sum", "d_cbo_sum")
+OKEPT = ("m", "d", "n_improved", "d_ck_sum", "d_cbo_sum")
+
+
+def _kept(a, names=KEPT):
+    return [tuple(int(x[f]) for f in names) for x in a]
+
+
+def test_unchanged_lists_reuse_the_check():
+    s = synth.named("tiny")
+    rp, dst = synth.candidates(s, 12, 5)
+    o = oracle.Oracle(s)
+    ref = o.evaluate(mask=3, min_improved=1, cand_rowptr=rp, cand_dst=dst)
+    g = mmref.load_synth(s, device=True)
+    mmref.compute_metrics(g, None, None)
+    rpd, dd = torch.from_numpy(rp).cuda(), torch.from_numpy(dst).cuda()
+    dig = np.zeros(1, dtype=np.uint64)
+    mmref.evaluate_moves(g, 3, 1, rpd, dd, digest=dig)
+    assert int(dig[0]) == ref.digest
+    top, nk, nm = mmref.suggest_moves(g, 50, 3, 1, rpd, dd, lists_unchanged=True)
+    assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept) and _kept(top) == _kept(ref.kept[:50], OKEPT)
+    # the same flag on the next call still answers the same
+    top2, nk2, _ = mmref.suggest_moves(g, 50, 3, 1, rpd, dd, lists_unchanged=True)
+    assert nk2 == nk and _kept(top2) == _kept(top)
+    g.free()
+
+
+def test_flag_ignored_for_other_lists_and_after_edits():
+    s = synth.named("tiny")
+    rp, dst = synth.candidates(s, 12, 5)
+    g = mmref.load_synth(s, device=True)
+    mmref.compute_metrics(g, None, None)
+    rpd, dd = torch.from_numpy(rp).cuda(), torch.from_numpy(dst).cuda()
+    mmref.suggest_moves(g, 10, 3, 1, rpd, dd)
+    # other lists (a copy holding an invalid destination) are checked despite the flag
+    bad = dd.clone()
+    bad[0] = int(s.method_class[0])
+    with pytest.raises(mmref.MMError) as e:
+        mmref.suggest_moves(g, 10, 3, 1, rpd, bad, lists_unchanged=True)
+    assert e.value.status == mmref.MM_EINVAL
+    mmref.suggest_moves(g, 10, 3, 1, rpd, dd)  # the good lists checked again
+    # after an edit the same lists are checked again: moving method 0 to its
+    # first listed destination makes that entry its own class
+    d0 = int(dst[0])
+    mmref.apply_edit(g, mmref.EDIT_MOVE, 0, d0)
+    with pytest.raises(mmref.MMError) as e:
+        mmref.suggest_moves(g, 10, 3, 1, rpd, dd, lists_unchanged=True)
+    assert e.value.status == mmref.MM_EINVAL
+    g.free()
+
+
+def test_unknown_list_flags_rejected():
+    s = synth.named("tiny")
+    rp, dst = synth.candidates(s, 4, 5)
+    g = mmref.load_synth(s, device=True)
+    mmref.compute_metrics(g, None, None)
+    cd, keep = mmref._cands(torch.from_numpy(rp).cuda(), torch.from_numpy(dst).cuda(), flags=6)
+    import ctypes
+    crit = mmref._Crit(3, 1)
+    st = mmref._lib.mm_evaluate_moves(g.handle, ctypes.byref(crit), ctypes.byref(cd), None, None, mmref.PTR_DEVICE)
+    assert st == mmref.MM_EINVAL
+    del keep
+    g.free()
