@@ -69,7 +69,7 @@ L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant
 # kernel of each workload, from a one-pass ncu capture (None once the kernel
 # changes, until it is captured again)
-EVAL_CSR_TRAFFIC_MASK7 = 985741824   # large restricted, eval_csr_grouped<records, kept>, all three metrics
+EVAL_CSR_TRAFFIC_MASK7 = 986456064   # large restricted, eval_csr_grouped<records, kept>, all three metrics
 EVAL_DENSE_TRAFFIC = 4771699968      # medium, eval_dense<records, kept>
 
 
@@ -412,8 +412,9 @@ def run_large(args, rank, world, local_rank, verifier, dist):
 
 def run_large_e2e(args, system, rp, dst, dev, stream):
     """The same step through the C ABI from pinned host buffers: CSR and
-    candidate lists copied in (twice: evaluation and suggestion), class and
-    method metrics and the top-100 copied out; records stay in HBM."""
+    candidate lists copied in (the suggestion reuses the evaluation's copy of
+    the unchanged lists), class and method metrics and the top-100 copied out;
+    records stay in HBM."""
     import torch
     from paper_1308_4011_b300 import mmref
 
@@ -426,14 +427,15 @@ def run_large_e2e(args, system, rp, dst, dev, stream):
     meth_h = torch.empty(M * 16, dtype=torch.uint8).pin_memory()
     top_h = torch.empty(TOPK * 24, dtype=torch.uint8).pin_memory()
     records = torch.empty(n_cand * 16, dtype=torch.uint8, device=dev)
-    h2d = sum(int(p.numel() * p.element_size()) for p in pinned) + 2 * (rp.nbytes + dst.nbytes)
+    h2d = sum(int(p.numel() * p.element_size()) for p in pinned) + rp.nbytes + dst.nbytes
     d2h = c * 64 + M * 16 + TOPK * 24 + 16
 
     def step():
         s = mmref.load_system(c, *pinned, stream=stream)
         mmref.compute_metrics(s, cls_h, meth_h)
         mmref.evaluate_moves(s, MASK_ALL, MIN_IMPROVED, rp_h.numpy(), dst_h.numpy(), records=records)
-        mmref.suggest_moves(s, TOPK, MASK_ALL, MIN_IMPROVED, rp_h.numpy(), dst_h.numpy(), out=top_h)
+        mmref.suggest_moves(s, TOPK, MASK_ALL, MIN_IMPROVED, rp_h.numpy(), dst_h.numpy(), out=top_h,
+                            lists_unchanged=True)
         s.free()
 
     for _ in range(max(1, args.warmup)):
@@ -563,6 +565,7 @@ def run_batched(args, local_rank, verifier):
     cap = int(max(int(counts0.max()), 1) * 1.1) + 64
     b = mmref.Batch(loaded, mask=mask, min_improved=mi, kept_cap=cap, stream=stream)
     tile = b.autotune()
+    blocks = b.config()[1]
     dig, nk = b.run(digest=True)
     # what the batch graph computed, per system: metric arrays and a sample of full rows
     gpu_metrics, gpu_rows = [], []
@@ -606,6 +609,14 @@ def run_batched(args, local_rank, verifier):
         torch.cuda.synchronize(dev)
         t = time.perf_counter(); batched(); torch.cuda.synchronize(dev); times_b.append(time.perf_counter() - t)
     tb, ts = statistics.median(times_b), statistics.median(times_s)
+    times_m = []  # the metric phase alone, one system after another
+    for _ in range(reps):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        for g in loaded:
+            mmref.compute_metrics(g, None, None)
+        torch.cuda.synchronize(dev)
+        times_m.append(time.perf_counter() - t)
     b.free()
     for g in loaded:
         g.free()
@@ -614,6 +625,7 @@ def run_batched(args, local_rank, verifier):
            "criteria": {"metric_mask": mask, "min_improved": mi}, "candidates": n_cand,
            "batched_s": tb, "sequential_s": ts, "speedup_vs_sequential": ts / tb,
            "value": n_cand / tb, "sequential_value": n_cand / ts, "unit": UNIT, "tile_methods": tile,
+           "persistent_blocks": blocks, "sequential_metrics_only_s": statistics.median(times_m),
            "kept_cap_per_system": cap, "n_kept_total": int(counts.sum()),
            "batch_digests_equal_single_system": ok_single, "topk_equal_sequential": ok_top,
            "generate_and_load_s": round(gen_s, 2)}

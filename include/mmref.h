@@ -79,8 +79,9 @@ typedef enum {
  * mm_compute_metrics and mm_export_metrics with host outputs,
  * mm_evaluate_moves with host outputs, mm_suggest_moves,
  * mm_suggest_moves_noalloc, mm_similarity, mm_suggest_r1, mm_suggest_r3,
- * mm_apply_edit, mm_apply_sequence, mm_batch_run), which clears it.  The
- * outputs of that call are written before the status is returned. */
+ * mm_apply_sequence, mm_metric_variants and mm_rank_classes with host
+ * outputs, mm_batch_run), which clears it.  The outputs of that call are
+ * written before the status is returned. */
 
 enum { MM_PTR_HOST = 0, MM_PTR_DEVICE = 1 };
 
@@ -198,14 +199,15 @@ typedef struct {
  * non-decreasing, rowptr[n_methods] = n_cand) and dst[n_cand] destination
  * classes, each in range and different from the method's class; index i is
  * the position in dst.  Every call that takes lists checks them on the device
- * and hashes their content (the key of the kept-move cache).  flags: 0, or
- * MM_CANDS_UNCHANGED: the caller states that these are the same device lists
- * (same rowptr and dst pointers, same n_cand, same content) as in the last
- * call on this handle that took lists, with no edit of the system since; the
- * library then reuses that call's check and hash.  When the pointers, length
- * or edit count differ from that call's, the flag is ignored and the lists
- * are checked again; lists rewritten in place under the flag are the
- * caller's error (results undefined, no fault).
+ * and hashes their content (the key of the kept-move cache); host lists are
+ * first copied to the device.  flags: 0, or MM_CANDS_UNCHANGED: the caller
+ * states that these are the same lists (same memory kind, same rowptr and dst
+ * pointers, same n_cand, same content) as in the last call on this handle
+ * that took lists, with no edit of the system since; the library then reuses
+ * that call's check, hash and, for host lists, its device copy.  When the
+ * kind, pointers, length or edit count differ from that call's, the flag is
+ * ignored and the lists are checked (and copied) again; lists rewritten in
+ * place under the flag are the caller's error (results undefined, no fault).
  */
 enum { MM_CANDS_UNCHANGED = 1 };
 typedef struct {
@@ -468,9 +470,15 @@ MMREF_API mm_status mm_batch_create(mm_system *const *systems, int32_t n, const 
                                     int64_t kept_cap, void *cuda_stream, mm_batch **out);
 /* Methods per evaluation tile (default 256, or the autotuned value). */
 MMREF_API mm_status mm_batch_set_tile(mm_batch *b, int32_t methods_per_tile);
-/* Time a few tile sizes on this batch, keep the fastest (cached in the
- * process per batch shape) and return it in *chosen. */
+/* Time a few launch configurations on this batch and keep the fastest (cached
+ * in the process per batch shape): first the methods per tile (32 .. 1,024)
+ * with every block the device can hold resident, then, for that tile, the
+ * number of persistent blocks (1 .. the resident limit per SM, times the SM
+ * count).  *chosen (nullable) receives the methods per tile. */
 MMREF_API mm_status mm_batch_autotune(mm_batch *b, int32_t *chosen);
+/* The batch's launch configuration: methods per tile and persistent blocks
+ * (either pointer nullable).  Errors: MM_EINVAL for a NULL batch. */
+MMREF_API mm_status mm_batch_config_get(const mm_batch *b, int32_t *methods_per_tile, int32_t *blocks);
 /* Run: digests[n] and n_kept[n] (host, nullable) receive each system's digest
  * and kept-move count.  Synchronises the batch stream. */
 MMREF_API mm_status mm_batch_run(mm_batch *b, uint64_t *digests, int64_t *n_kept);

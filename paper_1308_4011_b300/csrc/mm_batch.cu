@@ -53,7 +53,8 @@ struct mm_batch {
 namespace {
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int32_t, int64_t, int64_t, uint32_t, int32_t>, int32_t> g_tune_cache;
+// per batch shape: {methods per tile, persistent blocks}
+std::map<std::tuple<int32_t, int64_t, int64_t, uint32_t, int32_t>, std::pair<int32_t, int32_t>> g_tune_cache;
 
 std::tuple<int32_t, int64_t, int64_t, uint32_t, int32_t> tune_key(const mm_batch *b) {
   int64_t sc = 0, sm = 0;
@@ -249,7 +250,10 @@ MMREF_API mm_status mm_batch_create(mm_system *const *systems, int32_t n, const 
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_tune_cache.find(tune_key(b));
-      if (it != g_tune_cache.end()) b->mchunk = it->second;
+      if (it != g_tune_cache.end()) {
+        b->mchunk = it->second.first;
+        b->grid = it->second.second;
+      }
     }
     fill_and_upload_items(b);
     *out = b;
@@ -284,7 +288,8 @@ MMREF_API mm_status mm_batch_autotune(mm_batch *b, int32_t *chosen) {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_tune_cache.find(tune_key(b));
       if (it != g_tune_cache.end()) {
-        b->mchunk = it->second;
+        b->mchunk = it->second.first;
+        b->grid = it->second.second;
         fill_and_upload_items(b);
         drop_graph(b);
         if (chosen) *chosen = b->mchunk;
@@ -295,14 +300,14 @@ MMREF_API mm_status mm_batch_autotune(mm_batch *b, int32_t *chosen) {
     join(b->stream, b->user_stream, b->ev);
     enqueue_metrics(b);
     MM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    // two stages: methods per tile with every resident block, then the number
+    // of persistent blocks (the launch shape) for the best tile
     const int32_t trials[] = {32, 64, 128, 256, 512, 1024};
+    const int32_t full = batch_persistent_grid();
     cudaEvent_t e0, e1;
     MM_CUDA_TRY(cudaEventCreate(&e0));
     MM_CUDA_TRY(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int32_t best_m = b->mchunk;
-    for (int32_t mc : trials) {
-      b->mchunk = mc;
+    auto time_eval = [&]() {
       fill_and_upload_items(b);
       enqueue_eval(b, false);  // warm
       float ms_sum = 0;
@@ -315,18 +320,44 @@ MMREF_API mm_status mm_batch_autotune(mm_batch *b, int32_t *chosen) {
         MM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
         ms_sum += ms;
       }
-      if (ms_sum < best) { best = ms_sum; best_m = mc; }
+      return ms_sum;
+    };
+    float best = 1e30f;
+    int32_t best_m = b->mchunk, best_g = full;
+    b->grid = full;
+    for (int32_t mc : trials) {
+      b->mchunk = mc;
+      const float ms = time_eval();
+      if (ms < best) { best = ms; best_m = mc; }
+    }
+    b->mchunk = best_m;
+    int sms = B300_SMS;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    const int32_t per_sm = std::max(1, full / std::max(sms, 1));
+    for (int32_t k = 1; k < per_sm; ++k) {  // fewer blocks per SM than the occupancy limit
+      b->grid = full / per_sm * k;
+      const float ms = time_eval();
+      if (ms < best) { best = ms; best_g = b->grid; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->mchunk = best_m;
+    b->grid = best_g;
     fill_and_upload_items(b);
     drop_graph(b);
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
-      g_tune_cache[tune_key(b)] = best_m;
+      g_tune_cache[tune_key(b)] = std::make_pair(best_m, best_g);
     }
     if (chosen) *chosen = best_m;
+  });
+}
+
+MMREF_API mm_status mm_batch_config_get(const mm_batch *b, int32_t *methods_per_tile, int32_t *blocks) {
+  return guarded([&] {
+    if (!b) throw MmError{MM_EINVAL, "batch_config_get: NULL batch"};
+    if (methods_per_tile) *methods_per_tile = b->mchunk;
+    if (blocks) *blocks = b->grid;
   });
 }
 

@@ -58,7 +58,7 @@ struct SystemScope {
 void release_system(mm_system *s) {
   s->arena.release();
   for (Scratch *w : {&s->sort_ws, &s->eval_ws, &s->stage_ws, &s->kept_ws, &s->keyed_ws, &s->edit_ws, &s->sim_ws,
-                     &s->sim_keys_ws, &s->sim_val_ws, &s->r1_ws, &s->var_ws, &s->var_keys_ws, &s->adj_ws,
+                     &s->sim_keys_ws, &s->sim_val_ws, &s->r1_ws, &s->var_ws, &s->var_keys_ws, &s->adj_ws, &s->lists_ws,
                      &s->union_ws, &s->side_eval[0], &s->side_eval[1], &s->side_eval[2], &s->side_sort[0],
                      &s->side_sort[1], &s->side_sort[2], &s->side_union[0], &s->side_union[1], &s->side_union[2]})
     w->release(s->stream);
@@ -510,8 +510,7 @@ mm_status mm_apply_edit(mm_system *s, const mm_edit *e) {
   return guarded([&] {
     if (!s || !e) throw MmError{MM_EINVAL, "apply_edit: NULL argument"};
     SystemScope scope(s);
-    apply_edit(s, *e);
-    check_wait_fault(s->d_fault, s->stream, "apply_edit");
+    apply_edit(s, *e);  // queued: a bounded wait that ran out is reported by the next synchronising call
   });
 }
 

@@ -198,11 +198,17 @@ struct mm_system {
   uint64_t kept_hash = 0;    //   whose content hash was this
   int64_t kept_ncand = 0;    //   and length this
   int64_t kept_cap = 0;
-  // the last device candidate lists checked on this handle, for MM_CANDS_UNCHANGED
+  // the last candidate lists checked on this handle, for MM_CANDS_UNCHANGED:
+  // the caller's pointers and kind, and where the lists are on the device
+  // (the caller's own device lists, or the copy of host lists in lists_ws)
   bool lists_checked = false;
+  int32_t lists_kind = -1;
   const void *lists_rowptr = nullptr, *lists_dst = nullptr;
+  const int64_t *lists_dev_rowptr = nullptr;
+  const int32_t *lists_dev_dst = nullptr;
   int64_t lists_n = 0, lists_edits = -1;
   uint64_t lists_hash = 0;
+  Scratch lists_ws;
 
   // similarity values (Sec. II.A) of the last mm_similarity / mm_suggest_r1
   Scratch sim_ws, sim_keys_ws, sim_val_ws, r1_ws;

@@ -2130,7 +2130,7 @@ static void check_criteria(const mm_criteria &crit) {
 // memory instead of the thread's page-locked staging buffer (which is
 // allocated on first use), so nothing is allocated.
 static void prepare_candidates(mm_system *s, const mm_candidates *cands, const int64_t **rowptr,
-                               const int32_t **dst, int64_t *n_cand, Scratch &ws, uint64_t *hash = nullptr,
+                               const int32_t **dst, int64_t *n_cand, uint64_t *hash = nullptr,
                                bool staging = true) {
   *rowptr = nullptr;
   *dst = nullptr;
@@ -2144,18 +2144,18 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
   if (cands->flags & ~(int32_t)MM_CANDS_UNCHANGED) throw MmError{MM_EINVAL, "candidates: unknown flags"};
   *n_cand = cands->n_cand;
   cudaStream_t st = s->stream;
-  if ((cands->flags & MM_CANDS_UNCHANGED) && cands->ptr_kind == MM_PTR_DEVICE && s->lists_checked &&
+  if ((cands->flags & MM_CANDS_UNCHANGED) && s->lists_checked && s->lists_kind == cands->ptr_kind &&
       s->lists_rowptr == cands->rowptr && s->lists_dst == cands->dst && s->lists_n == cands->n_cand &&
-      s->lists_edits == s->edits) {  // the caller's lists were checked and hashed by the last call
-    *rowptr = cands->rowptr;
-    *dst = cands->dst;
+      s->lists_edits == s->edits) {  // checked and hashed by the last list call (host lists: already copied)
+    *rowptr = s->lists_dev_rowptr;
+    *dst = s->lists_dev_dst;
     if (hash) *hash = s->lists_hash;
     return;
   }
   s->lists_checked = false;
-  if (cands->ptr_kind == MM_PTR_HOST) {
+  if (cands->ptr_kind == MM_PTR_HOST) {  // copied into the handle's list buffer (kept for MM_CANDS_UNCHANGED)
     size_t rb = sizeof(int64_t) * ((size_t)s->M + 1), db = sizeof(int32_t) * (size_t)cands->n_cand;
-    char *b = static_cast<char *>(ws.need(rb + db + 256, st));
+    char *b = static_cast<char *>(s->lists_ws.need(rb + db + 256, st));
     MM_CUDA_TRY(cudaMemcpyAsync(b, cands->rowptr, rb, cudaMemcpyHostToDevice, st));
     if (db) MM_CUDA_TRY(cudaMemcpyAsync(b + ((rb + 255) & ~size_t(255)), cands->dst, db, cudaMemcpyHostToDevice, st));
     *rowptr = reinterpret_cast<const int64_t *>(b);
@@ -2194,14 +2194,15 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
   if (err & VE_CAND_ROWPTR) throw MmError{MM_EINVAL, "candidates: rowptr must start at 0, be non-decreasing and end at n_cand"};
   if (err & VE_CAND_RANGE) throw MmError{MM_EINVAL, "candidates: destination class out of range"};
   if (err & VE_CAND_SELF) throw MmError{MM_EINVAL, "candidates: destination equals the method's own class"};
-  if (cands->ptr_kind == MM_PTR_DEVICE) {
-    s->lists_checked = true;
-    s->lists_rowptr = cands->rowptr;
-    s->lists_dst = cands->dst;
-    s->lists_n = cands->n_cand;
-    s->lists_edits = s->edits;
-    s->lists_hash = h;
-  }
+  s->lists_checked = true;
+  s->lists_kind = cands->ptr_kind;
+  s->lists_rowptr = cands->rowptr;
+  s->lists_dst = cands->dst;
+  s->lists_dev_rowptr = *rowptr;
+  s->lists_dev_dst = *dst;
+  s->lists_n = cands->n_cand;
+  s->lists_edits = s->edits;
+  s->lists_hash = h;
 }
 
 static EvalCtx make_ctx(mm_system *s, const mm_criteria &crit) {
@@ -2256,7 +2257,7 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
   const int32_t *dst;
   int64_t n_cand;
   uint64_t chash = 0;
-  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, s->stage_ws, &chash);
+  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, &chash);
   s->kept_valid = false;
   if (n_cand == 0 || s->M == 0) {
     if (digest) {
@@ -2374,7 +2375,7 @@ void suggest_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *c
   const int32_t *dst;
   int64_t n_cand;
   uint64_t chash = 0;
-  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, s->stage_ws, &chash);
+  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, &chash);
   int64_t K = 0, nm = 0;
   mm_move *kept = nullptr;
   // Host outputs of up to KEYED_MAX kept moves need one round trip: the sort
@@ -2464,8 +2465,7 @@ void eval_kept_into(mm_system *s, const mm_criteria &crit, const mm_candidates *
   const int64_t *rowptr;
   const int32_t *dst;
   int64_t n_cand;
-  Scratch unused;  // only host lists would use it, and they are rejected above
-  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, unused, nullptr, false);
+  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, nullptr, false);  // device lists only: nothing allocated
   if (n_cand == 0 || s->M == 0) return;
   EvalCtx cx = make_ctx(s, crit);
   OutCtx oc{};

@@ -36,7 +36,8 @@ EXPORTED = ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluat
             "mm_export_system", "mm_server_create", "mm_server_add_system", "mm_server_run", "mm_server_stats_get",
             "mm_server_snapshot", "mm_server_free", "mm_selftest_bounded_wait", "mm_last_eval_ms",
             "mm_export_metrics", "mm_similarity", "mm_suggest_r1", "mm_apply_sequence",
-            "mm_suggest_r3", "mm_selftest_stall_scans", "mm_metric_variants", "mm_rank_classes")
+            "mm_suggest_r3", "mm_selftest_stall_scans", "mm_metric_variants", "mm_rank_classes",
+            "mm_batch_config_get")
 
 CLASS_METRICS_DTYPE = np.dtype([("n_methods", "<i4"), ("n_attrs", "<i4"), ("P", "<i8"), ("Q", "<i8"),
                                 ("S", "<i8"), ("lcom_ck", "<i8"), ("hs_num", "<i8"), ("hs_den", "<i8"),
@@ -107,6 +108,8 @@ _lib.mm_batch_autotune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
 _lib.mm_batch_run.argtypes = [_vp, _vp, _vp]
 _lib.mm_batch_suggestions.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_int64)]
+_lib.mm_batch_config_get.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+_lib.mm_batch_config_get.restype = ctypes.c_int
 _lib.mm_batch_free.argtypes = [_vp]
 _lib.mm_batch_free.restype = None
 for _n in ("mm_batch_create", "mm_batch_set_tile", "mm_batch_autotune", "mm_batch_run", "mm_batch_suggestions"):
@@ -439,6 +442,12 @@ class Batch:
         c = ctypes.c_int32()
         _check(_lib.mm_batch_autotune(self._h, ctypes.byref(c)))
         return int(c.value)
+
+    def config(self) -> tuple[int, int]:
+        """mm_batch_config_get: (methods per tile, persistent blocks)."""
+        t, g = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.mm_batch_config_get(self._h, ctypes.byref(t), ctypes.byref(g)))
+        return int(t.value), int(g.value)
 
     def run(self, digest: bool = True):
         """One replay of the batch graph; returns (digests or None, kept counts)."""

@@ -67,6 +67,9 @@ def test_batch_autotune_and_capacity(batch_systems):
     b = mmref.Batch(loaded, mask=1, min_improved=1, kept_cap=64)
     chosen = b.autotune()
     assert chosen in (32, 64, 128, 256, 512, 1024)
+    tile, blocks = b.config()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert tile == chosen and blocks % sms == 0 and 1 <= blocks // sms <= 8
     dig, nk = b.run()
     for i, s in enumerate(systems):
         ref = oracle.Oracle(s, cbo_attrs=(i % 3 != 2)).evaluate(mask=1, min_improved=1)

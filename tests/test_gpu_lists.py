@@ -80,3 +80,24 @@ def test_unknown_list_flags_rejected():
     assert st == mmref.MM_EINVAL
     del keep
     g.free()
+
+
+def test_unchanged_host_lists_reuse_the_device_copy():
+    """Host lists: the suggestion under the flag reuses the evaluation's device
+    copy and check; a different host array is copied and checked again."""
+    s = synth.named("tiny")
+    rp, dst = synth.candidates(s, 12, 5)
+    ref = oracle.Oracle(s).evaluate(mask=7, min_improved=1, cand_rowptr=rp, cand_dst=dst)
+    g = mmref.load_synth(s)
+    mmref.compute_metrics(g, None, None)
+    dig = np.zeros(1, dtype=np.uint64)
+    mmref.evaluate_moves(g, 7, 1, rp, dst, digest=dig)
+    assert int(dig[0]) == ref.digest
+    top, nk, nm = mmref.suggest_moves(g, 50, 7, 1, rp, dst, lists_unchanged=True)
+    assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept) and _kept(top) == _kept(ref.kept[:50], OKEPT)
+    bad = dst.copy()
+    bad[0] = int(s.method_class[0])
+    with pytest.raises(mmref.MMError) as e:
+        mmref.suggest_moves(g, 10, 7, 1, rp, bad, lists_unchanged=True)
+    assert e.value.status == mmref.MM_EINVAL
+    g.free()
