@@ -65,6 +65,8 @@ void release_system(mm_system *s) {
   for (cudaEvent_t e : {s->fork_ev, s->join_ev[0], s->join_ev[1], s->join_ev[2], s->mid_ev[0], s->mid_ev[1],
                         s->eval_ev[0], s->eval_ev[1]})
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : s->chunk_ev)
+    if (e) cudaEventDestroy(e);
   delete s;
 }
 

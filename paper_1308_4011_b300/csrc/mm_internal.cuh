@@ -209,6 +209,7 @@ struct mm_system {
   int64_t lists_n = 0, lists_edits = -1;
   uint64_t lists_hash = 0;
   Scratch lists_ws;
+  cudaEvent_t chunk_ev[8] = {};  // copies of host-list chunks (created on first use)
 
   // similarity values (Sec. II.A) of the last mm_similarity / mm_suggest_r1
   Scratch sim_ws, sim_keys_ws, sim_val_ws, r1_ws;

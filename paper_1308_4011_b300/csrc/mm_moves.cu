@@ -1329,9 +1329,10 @@ struct CsrSys {
   const int64_t *cls_P, *cls_Q, *cls_S;
   uint32_t sw;                        // records per row
   uint32_t c;
-  int32_t M;
+  int32_t M;                          // methods [m0, M) are evaluated (m0 a multiple of CG_M)
   int32_t staged;                     // 0: every method takes the general path
-  unsigned long long *next_group;     // counter handing out groups (zero at launch)
+  unsigned long long *next_group;     // counter handing out groups (m0 / CG_M at launch)
+  const uint32_t *gate;               // nullable: a nonzero word (failed list check) skips the launch
 };
 
 // Asynchronous global -> shared copies (completion awaited by cp_async_wait).
@@ -1462,6 +1463,7 @@ __global__ void __launch_bounds__(CG_WARPS * 32, 4) eval_csr_grouped(CsrSys sy, 
                                                                      const int64_t *cand_rowptr,
                                                                      const int32_t *cand_dst) {
   pdl_wait();
+  if (sy.gate && *sy.gate) return;  // the lists of this launch failed their check
   extern __shared__ __align__(16) unsigned char cg_smem[];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   CsrGroup &w = *reinterpret_cast<CsrGroup *>(cg_smem + (size_t)wid * CG_WARP_BYTES);
@@ -1672,14 +1674,14 @@ __device__ __forceinline__ int32_t owner_of(const int64_t *rowptr, int32_t M, in
 // walk does not change it.
 __global__ void __launch_bounds__(256) validate_cand_dst(const int64_t *rowptr, const int32_t *dst,
                                                          const int32_t *method_class, int32_t M, int32_t c,
-                                                         int64_t n_cand, int64_t per_warp, uint32_t *err,
-                                                         unsigned long long *hash) {
+                                                         int64_t i_lo, int64_t n_cand, int64_t per_warp,
+                                                         uint32_t *err, unsigned long long *hash) {
   pdl_wait();
   __shared__ int32_t s_cnt[8][128];
   __shared__ int32_t s_cls[8][32];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t i_begin = w * per_warp, i_end = min(n_cand, i_begin + per_warp);
+  const int64_t i_begin = i_lo + w * per_warp, i_end = min(n_cand, i_begin + per_warp);
   uint32_t e = 0;
   uint64_t h = 0;
   if (i_begin < i_end) {
@@ -1755,6 +1757,48 @@ __global__ void __launch_bounds__(256) validate_cand_dst(const int64_t *rowptr, 
   }
 }
 
+__global__ void set_counter(unsigned long long *p, unsigned long long v) {
+  pdl_wait();
+  *p = v;
+}
+
+// The restricted kernel over the methods [m0, m1) of candidate lists (m0 a
+// multiple of CG_M); gate (nullable) is read at entry: nonzero skips the launch.
+template <bool REC, bool DIG, bool KEEP>
+void launch_csr_range(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_t *rowptr, const int32_t *dst,
+                      int32_t m0, int32_t m1, const uint32_t *gate) {
+  cudaStream_t st = s->stream;
+  CsrSys sy;
+  sy.cx = cx;
+  sy.cx.packed = 1;  // every probe reads the compressed rows
+  sy.csum = s->csum;
+  sy.cpk = s->cpk;
+  sy.dest_rec = s->dest_rec;
+  sy.cls_n = s->cls_n;
+  sy.cls_a = s->cls_a;
+  sy.cls_P = s->cls_P;
+  sy.cls_Q = s->cls_Q;
+  sy.cls_S = s->cls_S;
+  sy.sw = (uint32_t)s->sum_words;
+  sy.c = (uint32_t)s->c;
+  // record offsets are 32-bit: larger systems evaluate every method on the general path
+  sy.staged = s->sum_words * (2 * (int64_t)s->c + 1) < (int64_t)UINT32_MAX ? 1 : 0;
+  sy.M = m1;
+  sy.gate = gate;
+  const int64_t groups = ceil_div((int64_t)(m1 - m0), CG_M);
+  const int64_t full = grouped_resident_grid<REC, DIG, KEEP>();
+  unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(groups, CG_WARPS), full));
+  sy.next_group = s->d_u64 + 5;
+  if (m0 == 0) {
+    MM_CUDA_TRY(cudaMemsetAsync(sy.next_group, 0, sizeof(unsigned long long), st));
+  } else {
+    pdl_launch(set_counter, 1, 1, 0, st, sy.next_group, (unsigned long long)(m0 / CG_M));
+    MM_LAUNCH_CHECK();
+  }
+  pdl_launch(eval_csr_grouped<REC, DIG, KEEP>, g, CG_WARPS * 32, CG_WARPS * CG_WARP_BYTES, st, sy, oc, rowptr, dst);
+  MM_LAUNCH_CHECK();
+}
+
 template <bool REC, bool DIG, bool KEEP>
 void launch_eval(mm_system *s, const EvalCtx &cx_in, const OutCtx &oc, const int64_t *rowptr, const int32_t *dst) {
   cudaStream_t st = s->stream;
@@ -1778,27 +1822,8 @@ void launch_eval(mm_system *s, const EvalCtx &cx_in, const OutCtx &oc, const int
     DenseSys sy{cx, s->dest_rec, c, M};
     pdl_launch(eval_dense<REC, DIG, KEEP>, dim3(gx, gy), DB_THREADS, 0, st, sy, oc, mchunk);
   } else {
-    CsrSys sy;
-    sy.cx = cx;
-    sy.csum = s->csum;
-    sy.cpk = s->cpk;
-    sy.dest_rec = s->dest_rec;
-    sy.cls_n = s->cls_n;
-    sy.cls_a = s->cls_a;
-    sy.cls_P = s->cls_P;
-    sy.cls_Q = s->cls_Q;
-    sy.cls_S = s->cls_S;
-    sy.sw = (uint32_t)s->sum_words;
-    sy.c = (uint32_t)s->c;
-    // record offsets are 32-bit: larger systems evaluate every method on the general path
-    sy.staged = s->sum_words * (2 * (int64_t)s->c + 1) < (int64_t)UINT32_MAX ? 1 : 0;
-    sy.M = s->M;
-    const int64_t groups = ceil_div((int64_t)s->M, CG_M);
-    const int64_t full = grouped_resident_grid<REC, DIG, KEEP>();
-    unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(groups, CG_WARPS), full));
-    sy.next_group = s->d_u64 + 5;
-    MM_CUDA_TRY(cudaMemsetAsync(sy.next_group, 0, sizeof(unsigned long long), st));
-    pdl_launch(eval_csr_grouped<REC, DIG, KEEP>, g, CG_WARPS * 32, CG_WARPS * CG_WARP_BYTES, st, sy, oc, rowptr, dst);
+    launch_csr_range<REC, DIG, KEEP>(s, cx, oc, rowptr, dst, 0, s->M, nullptr);
+    return;
   }
   MM_LAUNCH_CHECK();
 }
@@ -1823,6 +1848,22 @@ void dispatch_eval(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int6
     case 5: launch_eval<true, false, true>(s, cx, oc, rowptr, dst); break;
     case 6: launch_eval<true, true, false>(s, cx, oc, rowptr, dst); break;
     default: launch_eval<true, true, true>(s, cx, oc, rowptr, dst); break;
+  }
+}
+
+// The restricted kernel over methods [m0, m1) with the output selection of oc.
+void dispatch_csr_range(mm_system *s, const EvalCtx &cx, const OutCtx &oc, const int64_t *rowptr, const int32_t *dst,
+                        int32_t m0, int32_t m1, const uint32_t *gate) {
+  const int sel = (oc.records ? 4 : 0) | (oc.digest ? 2 : 0) | (oc.kept_count ? 1 : 0);
+  switch (sel) {
+    case 0: launch_csr_range<false, false, false>(s, cx, oc, rowptr, dst, m0, m1, gate); break;
+    case 1: launch_csr_range<false, false, true>(s, cx, oc, rowptr, dst, m0, m1, gate); break;
+    case 2: launch_csr_range<false, true, false>(s, cx, oc, rowptr, dst, m0, m1, gate); break;
+    case 3: launch_csr_range<false, true, true>(s, cx, oc, rowptr, dst, m0, m1, gate); break;
+    case 4: launch_csr_range<true, false, false>(s, cx, oc, rowptr, dst, m0, m1, gate); break;
+    case 5: launch_csr_range<true, false, true>(s, cx, oc, rowptr, dst, m0, m1, gate); break;
+    case 6: launch_csr_range<true, true, false>(s, cx, oc, rowptr, dst, m0, m1, gate); break;
+    default: launch_csr_range<true, true, true>(s, cx, oc, rowptr, dst, m0, m1, gate); break;
   }
 }
 
@@ -2176,8 +2217,8 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
       const int64_t warps = std::min<int64_t>(ceil_div(*n_cand, 128), (int64_t)B300_SMS * 16 * (TPB / 32));
       const int64_t per_warp = ceil_div(ceil_div(*n_cand, warps), 128) * 128;
       const unsigned g = (unsigned)ceil_div(ceil_div(*n_cand, per_warp) * 32, TPB);
-      pdl_launch(validate_cand_dst, g, TPB, 0, st, *rowptr, *dst, s->method_class, s->M, s->c, *n_cand, per_warp,
-                                          s->d_err, s->d_u64 + 3);
+      pdl_launch(validate_cand_dst, g, TPB, 0, st, *rowptr, *dst, s->method_class, s->M, s->c, (int64_t)0, *n_cand,
+                 per_warp, s->d_err, s->d_u64 + 3);
       MM_LAUNCH_CHECK();
     }
   }
@@ -2248,6 +2289,87 @@ static int64_t kept_capacity(mm_system *s) {
   return std::max<int64_t>(65536, s->kept_cap);
 }
 
+// Host candidate lists of at least this many entries are copied in chunks of
+// methods, each chunk checked and evaluated while the next one is copied.
+constexpr int64_t HOST_LISTS_CHUNKED = (int64_t)1 << 24;
+constexpr int HOST_LIST_CHUNKS = 8;
+
+// evaluate_moves for large host lists (copy of each chunk overlapped with the
+// check and evaluation of the previous ones).  Returns the content hash.
+static uint64_t evaluate_host_lists(mm_system *s, const mm_candidates *cands, const EvalCtx &cx, const OutCtx &oc) {
+  cudaStream_t st = s->stream;
+  const int32_t M = s->M;
+  const int64_t n = cands->n_cand;
+  const size_t rb = sizeof(int64_t) * ((size_t)M + 1), rb_pad = (rb + 255) & ~size_t(255);
+  char *b = static_cast<char *>(s->lists_ws.need(rb_pad + sizeof(int32_t) * (size_t)n + 256, st));
+  int64_t *rowptr = reinterpret_cast<int64_t *>(b);
+  int32_t *dst = reinterpret_cast<int32_t *>(b + rb_pad);
+  s->lists_checked = false;
+  // chunk bounds at multiples of the kernel's method group, from the host row pointers
+  int32_t mb[HOST_LIST_CHUNKS + 1];
+  int64_t lo[HOST_LIST_CHUNKS + 1];
+  for (int k = 0; k <= HOST_LIST_CHUNKS; ++k) {
+    mb[k] = k == HOST_LIST_CHUNKS ? M : (int32_t)((int64_t)M * k / HOST_LIST_CHUNKS / CG_M * CG_M);
+    lo[k] = k == HOST_LIST_CHUNKS ? n : std::min<int64_t>(std::max<int64_t>(cands->rowptr[mb[k]], 0), n);
+    if (k > 0) lo[k] = std::max(lo[k], lo[k - 1]);  // a malformed rowptr is reported by the check below
+  }
+  MM_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(uint32_t), st));
+  MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 3, 0, sizeof(unsigned long long), st));
+  MM_CUDA_TRY(cudaMemcpyAsync(rowptr, cands->rowptr, rb, cudaMemcpyHostToDevice, st));
+  pdl_launch(validate_cand_rows, grid_for(M), TPB, 0, st, static_cast<const int64_t *>(rowptr), M, n, s->d_err,
+             s->d_u64 + 3);
+  MM_LAUNCH_CHECK();
+  // the destination chunks on a copy stream, ordered after the buffer's allocation
+  static_assert(HOST_LIST_CHUNKS <= (int)(sizeof(s->chunk_ev) / sizeof(s->chunk_ev[0])), "one event per chunk");
+  for (int k = 0; k < HOST_LIST_CHUNKS; ++k)
+    if (!s->chunk_ev[k]) MM_CUDA_TRY(cudaEventCreateWithFlags(&s->chunk_ev[k], cudaEventDisableTiming));
+  cudaStream_t cp = fork_side(s, 1);
+  for (int k = 0; k < HOST_LIST_CHUNKS; ++k) {
+    const int64_t a = lo[k], e = lo[k + 1];
+    if (e > a)
+      MM_CUDA_TRY(cudaMemcpyAsync(dst + a, cands->dst + a, sizeof(int32_t) * (size_t)(e - a), cudaMemcpyHostToDevice,
+                                  cp));
+    MM_CUDA_TRY(cudaEventRecord(s->chunk_ev[k], cp));
+  }
+  if (s->eval_ev[0]) MM_CUDA_TRY(cudaEventRecord(s->eval_ev[0], st));  // mm_last_eval_ms: the pipelined span
+  for (int k = 0; k < HOST_LIST_CHUNKS; ++k) {
+    const int64_t a = lo[k], e = lo[k + 1];
+    MM_CUDA_TRY(cudaStreamWaitEvent(st, s->chunk_ev[k], 0));
+    if (e > a) {
+      const int64_t warps = std::min<int64_t>(ceil_div(e - a, 128), (int64_t)B300_SMS * 16 * (TPB / 32));
+      const int64_t per_warp = ceil_div(ceil_div(e - a, warps), 128) * 128;
+      const unsigned g = (unsigned)ceil_div(ceil_div(e - a, per_warp) * 32, TPB);
+      pdl_launch(validate_cand_dst, g, TPB, 0, st, static_cast<const int64_t *>(rowptr),
+                 static_cast<const int32_t *>(dst), s->method_class, M, s->c, a, e, per_warp, s->d_err,
+                 s->d_u64 + 3);
+      MM_LAUNCH_CHECK();
+    }
+    if (mb[k + 1] > mb[k])
+      dispatch_csr_range(s, cx, oc, rowptr, dst, mb[k], mb[k + 1], s->d_err);  // skipped if a check failed
+  }
+  if (s->eval_ev[1] && cudaEventRecord(s->eval_ev[1], st) == cudaSuccess) s->eval_timed = true;
+  // the check's verdict and the content hash, read back once
+  unsigned long long local[4] = {0, 0, 0, 0};
+  MM_CUDA_TRY(cudaMemcpyAsync(local, s->d_u64 + 3, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  MM_CUDA_TRY(cudaStreamSynchronize(st));
+  uint32_t err = 0;
+  std::memcpy(&err, reinterpret_cast<unsigned char *>(local) + 24, sizeof(uint32_t));
+  const uint64_t h = local[0];
+  if (err & VE_CAND_ROWPTR) throw MmError{MM_EINVAL, "candidates: rowptr must start at 0, be non-decreasing and end at n_cand"};
+  if (err & VE_CAND_RANGE) throw MmError{MM_EINVAL, "candidates: destination class out of range"};
+  if (err & VE_CAND_SELF) throw MmError{MM_EINVAL, "candidates: destination equals the method's own class"};
+  s->lists_checked = true;
+  s->lists_kind = MM_PTR_HOST;
+  s->lists_rowptr = cands->rowptr;
+  s->lists_dst = cands->dst;
+  s->lists_dev_rowptr = rowptr;
+  s->lists_dev_dst = dst;
+  s->lists_n = n;
+  s->lists_edits = s->edits;
+  s->lists_hash = h;
+  return h;
+}
+
 void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *cands, mm_move_eval *records,
                     uint64_t *digest, int32_t kind) {
   check_criteria(crit);
@@ -2257,7 +2379,18 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
   const int32_t *dst;
   int64_t n_cand;
   uint64_t chash = 0;
-  prepare_candidates(s, cands, &rowptr, &dst, &n_cand, &chash);
+  const bool chunked = cands && cands->rowptr && cands->ptr_kind == MM_PTR_HOST && cands->dst &&
+                       cands->n_cand >= HOST_LISTS_CHUNKED && s->M > 0 && !(cands->flags & ~(int32_t)MM_CANDS_UNCHANGED) &&
+                       !((cands->flags & MM_CANDS_UNCHANGED) && s->lists_checked && s->lists_kind == MM_PTR_HOST &&
+                         s->lists_rowptr == cands->rowptr && s->lists_dst == cands->dst &&
+                         s->lists_n == cands->n_cand && s->lists_edits == s->edits);
+  if (chunked) {  // pointers filled in below, after the pipelined copy
+    rowptr = nullptr;
+    dst = nullptr;
+    n_cand = cands->n_cand;
+  } else {
+    prepare_candidates(s, cands, &rowptr, &dst, &n_cand, &chash);
+  }
   s->kept_valid = false;
   if (n_cand == 0 || s->M == 0) {
     if (digest) {
@@ -2283,7 +2416,12 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
   // needs no second pass.
   const int64_t cap = kept_capacity(s);
   attach_kept(s, oc, cap);
-  dispatch_eval(s, cx, oc, rowptr, dst);
+  if (chunked) {
+    chash = evaluate_host_lists(s, cands, cx, oc);
+    rowptr = s->lists_dev_rowptr;
+  } else {
+    dispatch_eval(s, cx, oc, rowptr, dst);
+  }
   s->kept_valid = true;
   s->kept_mask = crit.metric_mask;
   s->kept_min = crit.min_improved;

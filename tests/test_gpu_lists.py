@@ -101,3 +101,35 @@ def test_unchanged_host_lists_reuse_the_device_copy():
         mmref.suggest_moves(g, 10, 7, 1, rp, bad, lists_unchanged=True)
     assert e.value.status == mmref.MM_EINVAL
     g.free()
+
+
+def test_large_host_lists_take_the_pipelined_copy():
+    """Host lists of 2^24 entries or more are copied in chunks overlapped with
+    their check and evaluation: records, digest and kept moves equal the
+    device-list path, and a bad destination in the last chunk is reported."""
+    s = synth.named("medium")
+    rp, dst = synth.candidates(s, 300, 9)   # about 2e7 candidates
+    assert len(dst) >= 1 << 24
+    g = mmref.load_synth(s, device=True)
+    mmref.compute_metrics(g, None, None)
+    n = len(dst)
+    rec_h = torch.empty(n * 16, dtype=torch.uint8, device="cuda")
+    dig_h = torch.zeros(1, dtype=torch.int64, device="cuda")
+    mmref.evaluate_moves(g, 7, 1, rp, dst, records=rec_h, digest=dig_h)   # host lists
+    top_h, nk_h, nm_h = mmref.suggest_moves(g, 100, 7, 1, rp, dst, lists_unchanged=True)
+    rec_d = torch.empty(n * 16, dtype=torch.uint8, device="cuda")
+    dig_d = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rpd, dd = torch.from_numpy(rp).cuda(), torch.from_numpy(dst).cuda()
+    mmref.evaluate_moves(g, 7, 1, rpd, dd, records=rec_d, digest=dig_d)  # device lists
+    top_d, nk_d, nm_d = mmref.suggest_moves(g, 100, 7, 1, rpd, dd)
+    torch.cuda.synchronize()
+    assert torch.equal(rec_h, rec_d) and int(dig_h.item()) == int(dig_d.item())
+    assert (nk_h, nm_h) == (nk_d, nm_d) and _kept(top_h) == _kept(top_d)
+    ref = oracle.Oracle(s).evaluate(mask=7, min_improved=1, cand_rowptr=rp, cand_dst=dst)
+    assert int(dig_d.cpu().numpy().view(np.uint64)[0]) == ref.digest
+    bad = dst.copy()
+    bad[-1] = s.n_classes  # out of range, in the last chunk
+    with pytest.raises(mmref.MMError) as e:
+        mmref.evaluate_moves(g, 7, 1, rp, bad, digest=np.zeros(1, dtype=np.uint64))
+    assert e.value.status == mmref.MM_EINVAL
+    g.free()
