@@ -412,9 +412,9 @@ def run_large(args, rank, world, local_rank, verifier, dist):
 
 def run_large_e2e(args, system, rp, dst, dev, stream):
     """The same step through the C ABI from pinned host buffers: CSR and
-    candidate lists copied in (the suggestion reuses the evaluation's copy of
-    the unchanged lists), class and method metrics and the top-100 copied out;
-    records stay in HBM."""
+    candidate lists copied in (the lists staged while the metrics are computed,
+    then used by the evaluation and the suggestion), class and method metrics
+    and the top-100 copied out; records stay in HBM."""
     import torch
     from paper_1308_4011_b300 import mmref
 
@@ -432,8 +432,10 @@ def run_large_e2e(args, system, rp, dst, dev, stream):
 
     def step():
         s = mmref.load_system(c, *pinned, stream=stream)
+        mmref.stage_candidates(s, rp_h.numpy(), dst_h.numpy())  # copied while the metrics are computed
         mmref.compute_metrics(s, cls_h, meth_h)
-        mmref.evaluate_moves(s, MASK_ALL, MIN_IMPROVED, rp_h.numpy(), dst_h.numpy(), records=records)
+        mmref.evaluate_moves(s, MASK_ALL, MIN_IMPROVED, rp_h.numpy(), dst_h.numpy(), records=records,
+                             lists_unchanged=True)
         mmref.suggest_moves(s, TOPK, MASK_ALL, MIN_IMPROVED, rp_h.numpy(), dst_h.numpy(), out=top_h,
                             lists_unchanged=True)
         s.free()

@@ -218,6 +218,19 @@ typedef struct {
   int32_t flags;
 } mm_candidates;
 
+/* Start copying host candidate lists (ptr_kind MM_PTR_HOST) to the device and
+ * checking them, on a copy stream of the calling thread that first waits for
+ * the work already queued on the system's stream; the system's stream does
+ * not wait for the copy, so later calls (mm_compute_metrics) overlap it.  A
+ * later list call on this handle that passes the same lists with
+ * MM_CANDS_UNCHANGED, with no edit between, waits for the copy and check and
+ * uses them (it reports their errors); any other list call, or freeing the
+ * handle, first waits for the staged copy.  The host arrays must stay
+ * unchanged until then; pinned memory lets the copy run asynchronously.
+ * Errors: MM_EINVAL (NULL system or lists, device lists, bad n_cand or flags),
+ * MM_ENOMEM, MM_ECUDA.  Does not synchronise. */
+MMREF_API mm_status mm_stage_candidates(mm_system *sys, const mm_candidates *cands);
+
 typedef struct {
   int32_t n_classes, n_methods, n_attrs, cbo_attrs;
   int64_t n_acc, n_call;

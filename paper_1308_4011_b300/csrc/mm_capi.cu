@@ -56,6 +56,7 @@ struct SystemScope {
 // Free everything a system holds: device memory in stream order on its stream,
 // then its events (released by the runtime once their last use completes).
 void release_system(mm_system *s) {
+  if (s->lists_staged) cudaStreamWaitEvent(s->stream, s->stage_ev, 0);  // a staged copy may still write lists_ws
   s->arena.release();
   for (Scratch *w : {&s->sort_ws, &s->eval_ws, &s->stage_ws, &s->kept_ws, &s->keyed_ws, &s->edit_ws, &s->sim_ws,
                      &s->sim_keys_ws, &s->sim_val_ws, &s->r1_ws, &s->var_ws, &s->var_keys_ws, &s->adj_ws, &s->lists_ws,
@@ -67,6 +68,7 @@ void release_system(mm_system *s) {
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : s->chunk_ev)
     if (e) cudaEventDestroy(e);
+  if (s->stage_ev) cudaEventDestroy(s->stage_ev);
   delete s;
 }
 
@@ -566,6 +568,14 @@ mm_status mm_rank_classes(mm_system *s, int32_t metric, int32_t k, int32_t *out_
     SystemScope scope(s);
     rank_classes(s, metric, k, out_ids, out_values, out_kind);
     if (out_kind == MM_PTR_HOST) check_wait_fault(s->d_fault, s->stream, "rank_classes");
+  });
+}
+
+mm_status mm_stage_candidates(mm_system *s, const mm_candidates *cands) {
+  return guarded([&] {
+    if (!s) throw MmError{MM_EINVAL, "stage_candidates: NULL system"};
+    SystemScope scope(s);
+    stage_candidates(s, cands);
   });
 }
 

@@ -210,6 +210,14 @@ struct mm_system {
   uint64_t lists_hash = 0;
   Scratch lists_ws;
   cudaEvent_t chunk_ev[8] = {};  // copies of host-list chunks (created on first use)
+  // lists staged by mm_stage_candidates: copied and checked on the copy stream,
+  // done when stage_ev completes; their check's words follow the lists in lists_ws
+  bool lists_staged = false;
+  cudaEvent_t stage_ev = nullptr;
+  uint32_t *stage_err = nullptr;
+  unsigned long long *stage_hash = nullptr;
+  int32_t stage_chunks = 0;                  // method chunks, each copied and checked before chunk_ev[k]
+  int32_t stage_mb[9] = {};                  // first method of each chunk (and the end)
 
   // similarity values (Sec. II.A) of the last mm_similarity / mm_suggest_r1
   Scratch sim_ws, sim_keys_ws, sim_val_ws, r1_ws;
@@ -424,6 +432,11 @@ void rank_classes(mm_system *s, int32_t metric, int32_t k, int32_t *out_ids, int
 // multigraph rows when the coupling was sorted); switch a system to building
 // them with its coupling (mm_metrics.cu).
 void ensure_adjacency(mm_system *s);
+// Host candidate lists copied and checked on a copy stream ahead of their use
+// (mm_stage_candidates); settle_staged orders the system's stream after a
+// pending staged copy (before lists_ws is reused or freed).
+void stage_candidates(mm_system *s, const mm_candidates *cands);
+void settle_staged(mm_system *s);
 void use_bitset_coupling(mm_system *s);
 void build_metrics(mm_system *s);                   // mm_metrics.cu
 void build_move_precompute(mm_system *s);           // mm_moves.cu

@@ -509,7 +509,7 @@ namespace {
 // (errors ignored: at process exit the runtime may already be gone).
 struct SideStreams {
   int device = -1;
-  cudaStream_t s[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t s[4] = {nullptr, nullptr, nullptr, nullptr};  // [0..2] metric branches, [3] list copies
   ~SideStreams() {
     for (cudaStream_t &x : s)
       if (x) {

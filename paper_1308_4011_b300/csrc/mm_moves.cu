@@ -2185,14 +2185,30 @@ static void prepare_candidates(mm_system *s, const mm_candidates *cands, const i
   if (cands->flags & ~(int32_t)MM_CANDS_UNCHANGED) throw MmError{MM_EINVAL, "candidates: unknown flags"};
   *n_cand = cands->n_cand;
   cudaStream_t st = s->stream;
-  if ((cands->flags & MM_CANDS_UNCHANGED) && s->lists_checked && s->lists_kind == cands->ptr_kind &&
-      s->lists_rowptr == cands->rowptr && s->lists_dst == cands->dst && s->lists_n == cands->n_cand &&
-      s->lists_edits == s->edits) {  // checked and hashed by the last list call (host lists: already copied)
+  const bool same = s->lists_kind == cands->ptr_kind && s->lists_rowptr == cands->rowptr &&
+                    s->lists_dst == cands->dst && s->lists_n == cands->n_cand && s->lists_edits == s->edits;
+  if ((cands->flags & MM_CANDS_UNCHANGED) && same && s->lists_staged) {  // staged: wait for its copy and check
+    MM_CUDA_TRY(cudaStreamWaitEvent(st, s->stage_ev, 0));
+    unsigned long long words[2] = {0, 0};  // {hash, error word}
+    MM_CUDA_TRY(cudaMemcpyAsync(&words[0], s->stage_hash, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    MM_CUDA_TRY(cudaMemcpyAsync(&words[1], s->stage_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    MM_CUDA_TRY(cudaStreamSynchronize(st));
+    s->lists_staged = false;
+    const uint32_t err = (uint32_t)words[1];
+    if (err & VE_CAND_ROWPTR) throw MmError{MM_EINVAL, "candidates: rowptr must start at 0, be non-decreasing and end at n_cand"};
+    if (err & VE_CAND_RANGE) throw MmError{MM_EINVAL, "candidates: destination class out of range"};
+    if (err & VE_CAND_SELF) throw MmError{MM_EINVAL, "candidates: destination equals the method's own class"};
+    s->lists_checked = true;
+    s->lists_hash = words[0];
+  }
+  if ((cands->flags & MM_CANDS_UNCHANGED) && same && s->lists_checked) {
+    // checked and hashed by the last list call (host lists: already copied)
     *rowptr = s->lists_dev_rowptr;
     *dst = s->lists_dev_dst;
     if (hash) *hash = s->lists_hash;
     return;
   }
+  settle_staged(s);
   s->lists_checked = false;
   if (cands->ptr_kind == MM_PTR_HOST) {  // copied into the handle's list buffer (kept for MM_CANDS_UNCHANGED)
     size_t rb = sizeof(int64_t) * ((size_t)s->M + 1), db = sizeof(int32_t) * (size_t)cands->n_cand;
@@ -2294,6 +2310,91 @@ static int64_t kept_capacity(mm_system *s) {
 constexpr int64_t HOST_LISTS_CHUNKED = (int64_t)1 << 24;
 constexpr int HOST_LIST_CHUNKS = 8;
 
+// Chunk bounds at multiples of the restricted kernel's method group, from the
+// host row pointers (a malformed rowptr is reported by the device check).
+static int chunk_bounds(const mm_system *s, const mm_candidates *cands, int32_t *mb, int64_t *lo) {
+  const int32_t M = s->M;
+  const int64_t n = cands->n_cand;
+  const int K = n >= HOST_LISTS_CHUNKED ? HOST_LIST_CHUNKS : 1;
+  for (int k = 0; k <= K; ++k) {
+    mb[k] = k == K ? M : (int32_t)((int64_t)M * k / K / CG_M * CG_M);
+    lo[k] = k == K ? n : std::min<int64_t>(std::max<int64_t>(cands->rowptr[mb[k]], 0), n);
+    if (k > 0) lo[k] = std::max(lo[k], lo[k - 1]);
+  }
+  return K;
+}
+
+// Launch the check of destinations [a, e) on stream st.
+static void check_dst_range(mm_system *s, const int64_t *rowptr, const int32_t *dst, int64_t a, int64_t e,
+                            uint32_t *err, unsigned long long *hash, cudaStream_t st) {
+  if (e <= a) return;
+  const int64_t warps = std::min<int64_t>(ceil_div(e - a, 128), (int64_t)B300_SMS * 16 * (TPB / 32));
+  const int64_t per_warp = ceil_div(ceil_div(e - a, warps), 128) * 128;
+  const unsigned g = (unsigned)ceil_div(ceil_div(e - a, per_warp) * 32, TPB);
+  pdl_launch(validate_cand_dst, g, TPB, 0, st, rowptr, dst, s->method_class, s->M, s->c, a, e, per_warp, err, hash);
+  MM_LAUNCH_CHECK();
+}
+
+void settle_staged(mm_system *s) {
+  if (s->lists_staged) {
+    MM_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->stage_ev, 0));
+    s->lists_staged = false;
+  }
+}
+
+// Copy host lists to the device and check them on the copy stream; the
+// system's stream does not wait (see mm_stage_candidates).
+void stage_candidates(mm_system *s, const mm_candidates *cands) {
+  if (!cands || !cands->rowptr) throw MmError{MM_EINVAL, "stage_candidates: no candidate lists"};
+  if (cands->ptr_kind != MM_PTR_HOST) throw MmError{MM_EINVAL, "stage_candidates: the lists must be in host memory"};
+  if (cands->n_cand < 0) throw MmError{MM_EINVAL, "candidates: n_cand < 0"};
+  if (cands->n_cand > 0 && !cands->dst) throw MmError{MM_EINVAL, "candidates: dst is NULL"};
+  if (cands->flags & ~(int32_t)MM_CANDS_UNCHANGED) throw MmError{MM_EINVAL, "candidates: unknown flags"};
+  cudaStream_t st = s->stream;
+  const int32_t M = s->M;
+  const int64_t n = cands->n_cand;
+  settle_staged(s);
+  s->lists_checked = false;
+  if (!s->stage_ev) MM_CUDA_TRY(cudaEventCreateWithFlags(&s->stage_ev, cudaEventDisableTiming));
+  const size_t rb = sizeof(int64_t) * ((size_t)M + 1), rb_pad = (rb + 255) & ~size_t(255);
+  const size_t db_pad = (sizeof(int32_t) * (size_t)n + 255) & ~size_t(255);
+  char *b = static_cast<char *>(s->lists_ws.need(rb_pad + db_pad + 512, st));
+  int64_t *rowptr = reinterpret_cast<int64_t *>(b);
+  int32_t *dst = reinterpret_cast<int32_t *>(b + rb_pad);
+  s->stage_hash = reinterpret_cast<unsigned long long *>(b + rb_pad + db_pad);
+  s->stage_err = reinterpret_cast<uint32_t *>(b + rb_pad + db_pad + 256);
+  MM_CUDA_TRY(cudaMemsetAsync(b + rb_pad + db_pad, 0, 512, st));
+  for (int k = 0; k < HOST_LIST_CHUNKS; ++k)
+    if (!s->chunk_ev[k]) MM_CUDA_TRY(cudaEventCreateWithFlags(&s->chunk_ev[k], cudaEventDisableTiming));
+  int64_t lo[HOST_LIST_CHUNKS + 1];
+  const int K = M > 0 ? chunk_bounds(s, cands, s->stage_mb, lo) : 0;
+  s->stage_chunks = K;
+  cudaStream_t cp = fork_side(s, 3);  // after the buffer's allocation and the cleared words
+  MM_CUDA_TRY(cudaMemcpyAsync(rowptr, cands->rowptr, rb, cudaMemcpyHostToDevice, cp));
+  if (M > 0) {
+    pdl_launch(validate_cand_rows, grid_for(M), TPB, 0, cp, static_cast<const int64_t *>(rowptr), M, n, s->stage_err,
+               s->stage_hash);
+    MM_LAUNCH_CHECK();
+  }
+  for (int k = 0; k < K; ++k) {  // chunk k copied and checked, then its event
+    if (lo[k + 1] > lo[k])
+      MM_CUDA_TRY(cudaMemcpyAsync(dst + lo[k], cands->dst + lo[k], sizeof(int32_t) * (size_t)(lo[k + 1] - lo[k]),
+                                  cudaMemcpyHostToDevice, cp));
+    check_dst_range(s, rowptr, dst, lo[k], lo[k + 1], s->stage_err, s->stage_hash, cp);
+    MM_CUDA_TRY(cudaEventRecord(s->chunk_ev[k], cp));
+  }
+  MM_CUDA_TRY(cudaEventRecord(s->stage_ev, cp));
+  s->lists_staged = true;
+  s->lists_kind = MM_PTR_HOST;
+  s->lists_rowptr = cands->rowptr;
+  s->lists_dst = cands->dst;
+  s->lists_dev_rowptr = rowptr;
+  s->lists_dev_dst = dst;
+  s->lists_n = n;
+  s->lists_edits = s->edits;
+}
+
+
 // evaluate_moves for large host lists (copy of each chunk overlapped with the
 // check and evaluation of the previous ones).  Returns the content hash.
 static uint64_t evaluate_host_lists(mm_system *s, const mm_candidates *cands, const EvalCtx &cx, const OutCtx &oc) {
@@ -2301,18 +2402,14 @@ static uint64_t evaluate_host_lists(mm_system *s, const mm_candidates *cands, co
   const int32_t M = s->M;
   const int64_t n = cands->n_cand;
   const size_t rb = sizeof(int64_t) * ((size_t)M + 1), rb_pad = (rb + 255) & ~size_t(255);
+  settle_staged(s);
   char *b = static_cast<char *>(s->lists_ws.need(rb_pad + sizeof(int32_t) * (size_t)n + 256, st));
   int64_t *rowptr = reinterpret_cast<int64_t *>(b);
   int32_t *dst = reinterpret_cast<int32_t *>(b + rb_pad);
   s->lists_checked = false;
-  // chunk bounds at multiples of the kernel's method group, from the host row pointers
   int32_t mb[HOST_LIST_CHUNKS + 1];
   int64_t lo[HOST_LIST_CHUNKS + 1];
-  for (int k = 0; k <= HOST_LIST_CHUNKS; ++k) {
-    mb[k] = k == HOST_LIST_CHUNKS ? M : (int32_t)((int64_t)M * k / HOST_LIST_CHUNKS / CG_M * CG_M);
-    lo[k] = k == HOST_LIST_CHUNKS ? n : std::min<int64_t>(std::max<int64_t>(cands->rowptr[mb[k]], 0), n);
-    if (k > 0) lo[k] = std::max(lo[k], lo[k - 1]);  // a malformed rowptr is reported by the check below
-  }
+  const int K = chunk_bounds(s, cands, mb, lo);
   MM_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(uint32_t), st));
   MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 3, 0, sizeof(unsigned long long), st));
   MM_CUDA_TRY(cudaMemcpyAsync(rowptr, cands->rowptr, rb, cudaMemcpyHostToDevice, st));
@@ -2324,7 +2421,7 @@ static uint64_t evaluate_host_lists(mm_system *s, const mm_candidates *cands, co
   for (int k = 0; k < HOST_LIST_CHUNKS; ++k)
     if (!s->chunk_ev[k]) MM_CUDA_TRY(cudaEventCreateWithFlags(&s->chunk_ev[k], cudaEventDisableTiming));
   cudaStream_t cp = fork_side(s, 1);
-  for (int k = 0; k < HOST_LIST_CHUNKS; ++k) {
+  for (int k = 0; k < K; ++k) {
     const int64_t a = lo[k], e = lo[k + 1];
     if (e > a)
       MM_CUDA_TRY(cudaMemcpyAsync(dst + a, cands->dst + a, sizeof(int32_t) * (size_t)(e - a), cudaMemcpyHostToDevice,
@@ -2332,18 +2429,10 @@ static uint64_t evaluate_host_lists(mm_system *s, const mm_candidates *cands, co
     MM_CUDA_TRY(cudaEventRecord(s->chunk_ev[k], cp));
   }
   if (s->eval_ev[0]) MM_CUDA_TRY(cudaEventRecord(s->eval_ev[0], st));  // mm_last_eval_ms: the pipelined span
-  for (int k = 0; k < HOST_LIST_CHUNKS; ++k) {
+  for (int k = 0; k < K; ++k) {
     const int64_t a = lo[k], e = lo[k + 1];
     MM_CUDA_TRY(cudaStreamWaitEvent(st, s->chunk_ev[k], 0));
-    if (e > a) {
-      const int64_t warps = std::min<int64_t>(ceil_div(e - a, 128), (int64_t)B300_SMS * 16 * (TPB / 32));
-      const int64_t per_warp = ceil_div(ceil_div(e - a, warps), 128) * 128;
-      const unsigned g = (unsigned)ceil_div(ceil_div(e - a, per_warp) * 32, TPB);
-      pdl_launch(validate_cand_dst, g, TPB, 0, st, static_cast<const int64_t *>(rowptr),
-                 static_cast<const int32_t *>(dst), s->method_class, M, s->c, a, e, per_warp, s->d_err,
-                 s->d_u64 + 3);
-      MM_LAUNCH_CHECK();
-    }
+    check_dst_range(s, rowptr, dst, a, e, s->d_err, s->d_u64 + 3, st);
     if (mb[k + 1] > mb[k])
       dispatch_csr_range(s, cx, oc, rowptr, dst, mb[k], mb[k + 1], s->d_err);  // skipped if a check failed
   }
@@ -2370,6 +2459,35 @@ static uint64_t evaluate_host_lists(mm_system *s, const mm_candidates *cands, co
   return h;
 }
 
+// evaluate_moves for lists staged by mm_stage_candidates: chunk k is evaluated
+// once its copy and check are done (a failed check skips every later launch),
+// the verdict and the content hash read back once.  Returns the hash.
+static uint64_t evaluate_staged_lists(mm_system *s, const EvalCtx &cx, const OutCtx &oc) {
+  cudaStream_t st = s->stream;
+  const int64_t *rowptr = s->lists_dev_rowptr;
+  const int32_t *dst = s->lists_dev_dst;
+  if (s->eval_ev[0]) MM_CUDA_TRY(cudaEventRecord(s->eval_ev[0], st));
+  for (int k = 0; k < s->stage_chunks; ++k) {
+    MM_CUDA_TRY(cudaStreamWaitEvent(st, s->chunk_ev[k], 0));
+    if (s->stage_mb[k + 1] > s->stage_mb[k])
+      dispatch_csr_range(s, cx, oc, rowptr, dst, s->stage_mb[k], s->stage_mb[k + 1], s->stage_err);
+  }
+  if (s->eval_ev[1] && cudaEventRecord(s->eval_ev[1], st) == cudaSuccess) s->eval_timed = true;
+  MM_CUDA_TRY(cudaStreamWaitEvent(st, s->stage_ev, 0));
+  unsigned long long words[2] = {0, 0};  // {hash, error word}
+  MM_CUDA_TRY(cudaMemcpyAsync(&words[0], s->stage_hash, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  MM_CUDA_TRY(cudaMemcpyAsync(&words[1], s->stage_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  MM_CUDA_TRY(cudaStreamSynchronize(st));
+  s->lists_staged = false;
+  const uint32_t err = (uint32_t)words[1];
+  if (err & VE_CAND_ROWPTR) throw MmError{MM_EINVAL, "candidates: rowptr must start at 0, be non-decreasing and end at n_cand"};
+  if (err & VE_CAND_RANGE) throw MmError{MM_EINVAL, "candidates: destination class out of range"};
+  if (err & VE_CAND_SELF) throw MmError{MM_EINVAL, "candidates: destination equals the method's own class"};
+  s->lists_checked = true;
+  s->lists_hash = words[0];
+  return words[0];
+}
+
 void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *cands, mm_move_eval *records,
                     uint64_t *digest, int32_t kind) {
   check_criteria(crit);
@@ -2381,10 +2499,15 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
   uint64_t chash = 0;
   const bool chunked = cands && cands->rowptr && cands->ptr_kind == MM_PTR_HOST && cands->dst &&
                        cands->n_cand >= HOST_LISTS_CHUNKED && s->M > 0 && !(cands->flags & ~(int32_t)MM_CANDS_UNCHANGED) &&
-                       !((cands->flags & MM_CANDS_UNCHANGED) && s->lists_checked && s->lists_kind == MM_PTR_HOST &&
-                         s->lists_rowptr == cands->rowptr && s->lists_dst == cands->dst &&
-                         s->lists_n == cands->n_cand && s->lists_edits == s->edits);
-  if (chunked) {  // pointers filled in below, after the pipelined copy
+                       !((cands->flags & MM_CANDS_UNCHANGED) && (s->lists_checked || s->lists_staged) &&
+                         s->lists_kind == MM_PTR_HOST && s->lists_rowptr == cands->rowptr &&
+                         s->lists_dst == cands->dst && s->lists_n == cands->n_cand && s->lists_edits == s->edits);
+  // lists staged by mm_stage_candidates: each chunk is evaluated as it lands
+  const bool staged = cands && cands->rowptr && (cands->flags & MM_CANDS_UNCHANGED) && s->lists_staged &&
+                      s->lists_kind == cands->ptr_kind && s->lists_rowptr == cands->rowptr &&
+                      s->lists_dst == cands->dst && s->lists_n == cands->n_cand && s->lists_edits == s->edits &&
+                      s->stage_chunks > 0 && cands->n_cand > 0;
+  if (chunked || staged) {  // pointers filled in below, after the pipelined copy
     rowptr = nullptr;
     dst = nullptr;
     n_cand = cands->n_cand;
@@ -2418,6 +2541,9 @@ void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *
   attach_kept(s, oc, cap);
   if (chunked) {
     chash = evaluate_host_lists(s, cands, cx, oc);
+    rowptr = s->lists_dev_rowptr;
+  } else if (staged) {
+    chash = evaluate_staged_lists(s, cx, oc);
     rowptr = s->lists_dev_rowptr;
   } else {
     dispatch_eval(s, cx, oc, rowptr, dst);

@@ -37,7 +37,7 @@ EXPORTED = ("mm_load_system", "mm_set_stream", "mm_compute_metrics", "mm_evaluat
             "mm_server_snapshot", "mm_server_free", "mm_selftest_bounded_wait", "mm_last_eval_ms",
             "mm_export_metrics", "mm_similarity", "mm_suggest_r1", "mm_apply_sequence",
             "mm_suggest_r3", "mm_selftest_stall_scans", "mm_metric_variants", "mm_rank_classes",
-            "mm_batch_config_get")
+            "mm_batch_config_get", "mm_stage_candidates")
 
 CLASS_METRICS_DTYPE = np.dtype([("n_methods", "<i4"), ("n_attrs", "<i4"), ("P", "<i8"), ("Q", "<i8"),
                                 ("S", "<i8"), ("lcom_ck", "<i8"), ("hs_num", "<i8"), ("hs_den", "<i8"),
@@ -108,6 +108,8 @@ _lib.mm_batch_autotune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
 _lib.mm_batch_run.argtypes = [_vp, _vp, _vp]
 _lib.mm_batch_suggestions.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_int64)]
+_lib.mm_stage_candidates.argtypes = [_vp, ctypes.POINTER(_Cands)]
+_lib.mm_stage_candidates.restype = ctypes.c_int
 _lib.mm_batch_config_get.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
 _lib.mm_batch_config_get.restype = ctypes.c_int
 _lib.mm_batch_free.argtypes = [_vp]
@@ -365,6 +367,18 @@ def _cands(cand_rowptr, cand_dst, flags=0):
     n = int(cand_dst.shape[0])
     c = _Cands(_ptr(cand_rowptr), _ptr(cand_dst), n, kind, int(flags))
     return c, (cand_rowptr, cand_dst)
+
+
+def stage_candidates(sys: System, cand_rowptr, cand_dst):
+    """mm_stage_candidates: start copying host lists (numpy; pinned memory for
+    an asynchronous copy) to the device and checking them; a later call with
+    the same arrays and lists_unchanged=True uses them.  The arrays must stay
+    alive and unchanged until then."""
+    cd, keep = _cands(cand_rowptr, cand_dst)
+    if cd is None or cd.ptr_kind != PTR_HOST:
+        raise ValueError("stage_candidates: host (numpy) lists")
+    sys._staged = keep  # the arrays stay referenced while the copy may run
+    _check(_lib.mm_stage_candidates(sys.handle, ctypes.byref(cd)))
 
 
 def evaluate_moves(sys: System, mask: int = DEFAULT_MASK, min_improved: int = DEFAULT_MIN_IMPROVED,

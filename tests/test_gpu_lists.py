@@ -133,3 +133,45 @@ def test_large_host_lists_take_the_pipelined_copy():
         mmref.evaluate_moves(g, 7, 1, rp, bad, digest=np.zeros(1, dtype=np.uint64))
     assert e.value.status == mmref.MM_EINVAL
     g.free()
+
+
+def test_staged_host_lists():
+    """Lists staged before the metrics are computed are used by the evaluation
+    and the suggestion that pass them unchanged; a bad staged list is reported
+    by the call that uses it; an edit between makes the lists be copied and
+    checked again; freeing a handle with a staged copy is safe."""
+    s = synth.named("tiny")
+    rp, dst = synth.candidates(s, 12, 5)
+    ref = oracle.Oracle(s).evaluate(mask=7, min_improved=1, cand_rowptr=rp, cand_dst=dst)
+    rp_p = torch.from_numpy(rp).pin_memory().numpy()
+    dst_p = torch.from_numpy(dst).pin_memory().numpy()
+    g = mmref.load_synth(s, device=True)
+    mmref.stage_candidates(g, rp_p, dst_p)
+    mmref.compute_metrics(g, None, None)
+    dig = np.zeros(1, dtype=np.uint64)
+    mmref.evaluate_moves(g, 7, 1, rp_p, dst_p, digest=dig, lists_unchanged=True)
+    assert int(dig[0]) == ref.digest
+    top, nk, nm = mmref.suggest_moves(g, 50, 7, 1, rp_p, dst_p, lists_unchanged=True)
+    assert (nk, nm) == (ref.n_kept, ref.n_methods_with_kept) and _kept(top) == _kept(ref.kept[:50], OKEPT)
+    # a bad list, staged: the error comes from the call that uses it
+    bad = dst_p.copy()
+    bad[3] = s.n_classes + 7
+    mmref.stage_candidates(g, rp_p, bad)
+    with pytest.raises(mmref.MMError) as e:
+        mmref.evaluate_moves(g, 7, 1, rp_p, bad, digest=dig, lists_unchanged=True)
+    assert e.value.status == mmref.MM_EINVAL
+    # staged, then an edit: copied and checked again (moving method 0 into its
+    # first listed class makes that entry its own class)
+    mmref.stage_candidates(g, rp_p, dst_p)
+    mmref.apply_edit(g, mmref.EDIT_MOVE, 0, int(dst[0]))
+    with pytest.raises(mmref.MMError) as e:
+        mmref.suggest_moves(g, 10, 7, 1, rp_p, dst_p, lists_unchanged=True)
+    assert e.value.status == mmref.MM_EINVAL
+    mmref.stage_candidates(g, rp_p, dst_p)
+    g.free()  # waits for the staged copy
+    with pytest.raises(ValueError):
+        g2 = mmref.load_synth(s, device=True)
+        try:
+            mmref.stage_candidates(g2, torch.from_numpy(rp).cuda(), torch.from_numpy(dst).cuda())
+        finally:
+            g2.free()
