@@ -70,7 +70,7 @@ L2_FLUSH_BYTES = 512 << 20
 # kernel of each workload, from a one-pass ncu capture (None once the kernel
 # changes, until it is captured again)
 EVAL_CSR_TRAFFIC_MASK7 = 986456064   # large restricted, eval_csr_grouped<records, kept>, all three metrics
-EVAL_DENSE_TRAFFIC = 4771699968      # medium, eval_dense<records, kept>
+EVAL_DENSE_TRAFFIC = 4771880448      # medium, eval_dense<records, kept>
 
 
 def _env_int(k, d):
@@ -470,12 +470,19 @@ def cpu_baseline_large(system, rp, dst, mask):
 
 # ---------------------------------------------------------------- nested: medium dense
 
-def run_medium(args, local_rank, verifier):
+# the dense profiling case: 2,000 classes, 24,000 methods (768 MB of records, above L2)
+DENSE_SMALL = dict(n_classes=2000, n_methods=24000, n_attrs=12000, max_class=80, seed=5, zipf_s=1.2, lambda_acc=3.0,
+                   lambda_call=4.0, p_loc=0.70)
+
+
+def run_medium(args, local_rank, verifier, params=None, workload=MEDIUM_WORKLOAD):
+    """The full cross product of one system (the medium one by default), dense
+    evaluation with records, timed step by step."""
     import torch
     from paper_1308_4011_b300 import mmref, synth
 
     dev = torch.device("cuda", local_rank)
-    params = dict(synth.MEDIUM)
+    params = dict(synth.MEDIUM) if params is None else dict(params)
     system = synth.generate(**params, name="medium")
     c, M = system.n_classes, system.n_methods
     n_cand = M * (c - 1)
@@ -519,7 +526,7 @@ def run_medium(args, local_rank, verifier):
     peak, peak_kind = _peaks()
     alg = 16 * n_cand
     k = statistics.median(kern) / 1e3
-    out = {"workload": MEDIUM_WORKLOAD, "criteria": {"metric_mask": MASK_LCOM, "min_improved": MIN_IMPROVED},
+    out = {"workload": workload, "criteria": {"metric_mask": MASK_LCOM, "min_improved": MIN_IMPROVED},
            "candidates_per_step": n_cand, "value": n_cand * args.steps / (sum(step_ms) / 1e3), "unit": UNIT,
            "ms_per_step": sum(step_ms) / args.steps,
            "roofline": {"bound": "hbm", "kernel": "eval_dense<records, kept>", "achieved": round(alg / k / 1e9, 1),
@@ -986,6 +993,9 @@ def main():
     ap.add_argument("--stress-requests", type=int, default=5000)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--batch-systems", type=int, default=256)
+    ap.add_argument("--case", choices=["large", "medium", "dense-small"], default="large",
+                    help="large: the bench line and its sections; medium / dense-small: only the dense step of "
+                         "that system (profiling runs; the JSON line is that step's)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1003,6 +1013,17 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    if args.case != "large":  # one dense step, for profiling
+        params = None if args.case == "medium" else DENSE_SMALL
+        label = MEDIUM_WORKLOAD if args.case == "medium" else (
+            "dense profiling case: 2,000 classes, 24,000 methods, 12,000 attributes, seed 5; full cross product")
+        out, check = run_medium(args, local_rank, verifier, params=params, workload=label)
+        if verifier:
+            out["verified_vs_oracle"] = _check_result("dense", check)
+            verifier.close()
+        out["case"] = args.case
+        print(json.dumps(out), flush=True)
+        return
     # the nested sections run on one GPU only (rank 0 of a single-rank job)
     sections = [x for x in args.sections.split(",") if x] if world == 1 else []
     t_start = time.perf_counter()
