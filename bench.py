@@ -991,7 +991,9 @@ def main():
                     help="nested sections measured beside the bench line (comma list; '' for none)")
     ap.add_argument("--requests", type=int, default=100000)
     ap.add_argument("--stress-requests", type=int, default=5000)
-    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--slots", type=int, default=4,
+                    help="serving worker slots (4 measured best: 1 slot 2,003, 2: 3,226, 3: 4,056, 4: 4,435, "
+                         "5: 4,163, 6: 3,625, 8: 2,049 requests/s)")
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--case", choices=["large", "medium", "dense-small"], default="large",
                     help="large: the bench line and its sections; medium / dense-small: only the dense step of "
