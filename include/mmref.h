@@ -585,7 +585,7 @@ MMREF_API mm_status mm_export_system(mm_system *sys, int32_t *method_class, int3
 typedef struct mm_server mm_server;
 typedef struct {
   int64_t budget_bytes;  /* device memory for resident systems */
-  int32_t n_slots;       /* concurrent requests (1..64) */
+  int32_t n_slots;       /* concurrent requests (1..64); about 4 serves most on one B300 */
   int32_t topk;          /* suggestions returned per request */
   mm_criteria crit;
 } mm_server_config;

@@ -593,7 +593,7 @@ for _n in ("mm_server_create", "mm_server_add_system", "mm_server_run", "mm_serv
 class Server:
     """mm_server_*: resident evolving systems answering edit requests."""
 
-    def __init__(self, budget_bytes: int, n_slots: int = 8, topk: int = 10, mask: int = DEFAULT_MASK,
+    def __init__(self, budget_bytes: int, n_slots: int = 4, topk: int = 10, mask: int = DEFAULT_MASK,
                  min_improved: int = DEFAULT_MIN_IMPROVED):
         cfg = _ServerConfig(int(budget_bytes), int(n_slots), int(topk), _Crit(mask, min_improved))
         h = _vp()
