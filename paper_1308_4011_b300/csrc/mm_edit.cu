@@ -322,7 +322,7 @@ void apply_edit(mm_system *s, const mm_edit &e) {
   s->kept_valid = false;
   const uint32_t kmask = s->kept_mask;
   const int32_t kmin = s->kept_min;
-  build_structures(s);
+  patch_structures(s, e.kind, m, e.target, C);  // class lists, ranks and fan-in: only what the edit changed
   build_metrics(s);
   build_move_precompute(s);
   if (!had_cache) return;

@@ -432,6 +432,8 @@ void rank_classes(mm_system *s, int32_t metric, int32_t k, int32_t *out_ids, int
 // multigraph rows when the coupling was sorted); switch a system to building
 // them with its coupling (mm_metrics.cu).
 void ensure_adjacency(mm_system *s);
+// Class structures after one edit without their full rebuild (mm_system.cu).
+void patch_structures(mm_system *s, int32_t kind, int32_t m, int32_t target, int32_t C);
 // Host candidate lists copied and checked on a copy stream ahead of their use
 // (mm_stage_candidates); settle_staged orders the system's stream after a
 // pending staged copy (before lists_ws is reused or freed).

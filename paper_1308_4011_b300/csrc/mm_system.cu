@@ -317,3 +317,68 @@ void build_structures(mm_system *s) {
     MM_LAUNCH_CHECK();
   }
 }
+
+namespace {
+
+// The class -> methods lists after method m moved from class C to class D,
+// from the lists before (ascending ids within each class): every member keeps
+// its order; m leaves C's segment and enters D's at its rank by id.
+__global__ void move_patch_members(const int32_t *old_list, const int64_t *old_ptr, const int64_t *new_ptr,
+                                   const int32_t *method_class, int32_t M, int32_t m, int32_t C, int32_t D,
+                                   int32_t *cm_list, int32_t *method_local) {
+  pdl_wait();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = old_list[i];
+    int64_t r;
+    int32_t Y;
+    if (x == m) {  // D's members with a smaller id come first
+      int64_t lo = old_ptr[D], hi = old_ptr[D + 1];
+      const int64_t base = lo;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (old_list[mid] < m) lo = mid + 1; else hi = mid;
+      }
+      r = lo - base;
+      Y = D;
+    } else {
+      Y = method_class[x];
+      r = i - old_ptr[Y];
+      if (Y == C && x > m) r -= 1;
+      if (Y == D && x > m) r += 1;
+    }
+    cm_list[new_ptr[Y] + r] = x;
+    method_local[x] = (int32_t)r;
+  }
+}
+
+__global__ void add_to(int32_t *p, int32_t v) {
+  pdl_wait();
+  *p += v;
+}
+
+}  // namespace
+
+// Class structures after an edit, without the full rebuild: a move patches
+// the class -> methods lists and ranks (cls_n and method_class already
+// updated); a call added or removed changes one fan-in; an access changes none.
+void patch_structures(mm_system *s, int32_t kind, int32_t m, int32_t target, int32_t C) {
+  cudaStream_t st = s->stream;
+  if (kind == MM_EDIT_ADD_CALL || kind == MM_EDIT_REMOVE_CALL) {
+    pdl_launch(add_to, 1, 1, 0, st, s->fan_in + target, kind == MM_EDIT_ADD_CALL ? 1 : -1);
+    MM_LAUNCH_CHECK();
+    return;
+  }
+  if (kind != MM_EDIT_MOVE) return;
+  const int64_t c = s->c, M = s->M;
+  char *b = static_cast<char *>(s->eval_ws.need(sizeof(int64_t) * ((size_t)c + 1) + sizeof(int32_t) * (size_t)M + 512,
+                                                st));
+  int64_t *old_ptr = reinterpret_cast<int64_t *>(b);
+  int32_t *old_list = reinterpret_cast<int32_t *>(b + ((sizeof(int64_t) * ((size_t)c + 1) + 255) & ~size_t(255)));
+  MM_CUDA_TRY(cudaMemcpyAsync(old_ptr, s->cm_rowptr, sizeof(int64_t) * ((size_t)c + 1), cudaMemcpyDeviceToDevice, st));
+  MM_CUDA_TRY(cudaMemcpyAsync(old_list, s->cm_list, sizeof(int32_t) * (size_t)M, cudaMemcpyDeviceToDevice, st));
+  scan_exclusive_i32to64(s->cls_n, s->cm_rowptr, c, s->sort_ws, st, s->cm_rowptr + c);
+  pdl_launch(move_patch_members, grid_for(M), TPB, 0, st, static_cast<const int32_t *>(old_list),
+             static_cast<const int64_t *>(old_ptr), static_cast<const int64_t *>(s->cm_rowptr),
+             static_cast<const int32_t *>(s->method_class), (int32_t)M, m, C, target, s->cm_list, s->method_local);
+  MM_LAUNCH_CHECK();
+}
