@@ -14,7 +14,6 @@
 #include "mm_internal.cuh"
 
 void build_structures(mm_system *s);
-void build_metrics(mm_system *s);
 void build_move_precompute(mm_system *s);
 
 struct mm_batch {

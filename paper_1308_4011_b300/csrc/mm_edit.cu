@@ -25,7 +25,6 @@
 #include "mm_internal.cuh"
 
 void build_structures(mm_system *s);
-void build_metrics(mm_system *s);
 void build_move_precompute(mm_system *s);
 void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, Scratch &ws,
                         cudaStream_t st);
@@ -175,21 +174,27 @@ T *regrow(mm_system *s, T *old, int64_t keep, int64_t new_count) {
   return p;
 }
 
-void ensure_capacity(mm_system *s, int64_t n_acc, int64_t n_call) {
+// Returns whether a buffer was regrown (its old content is then gone and the
+// structures built in it must be rebuilt).
+bool ensure_capacity(mm_system *s, int64_t n_acc, int64_t n_call) {
   EditMirror &mr = s->mirror;
+  bool regrown = false;
   if (n_acc > mr.acc_cap) {
+    regrown = true;
     int64_t cap = n_acc + n_acc / 4 + 1024;
     s->acc_idx = regrow(s, s->acc_idx, s->n_acc, cap);
     s->own_list = regrow(s, s->own_list, (int64_t)0, cap);
     mr.acc_cap = cap;
   }
   if (n_call > mr.call_cap) {
+    regrown = true;
     int64_t cap = n_call + n_call / 4 + 1024;
     s->call_idx = regrow(s, s->call_idx, s->n_call, cap);
     s->r_list = regrow(s, s->r_list, (int64_t)0, cap);
     mr.call_cap = cap;
   }
   if (n_acc + n_call > mr.nu_cap) {
+    regrown = true;
     int64_t cap = (n_acc + n_call) + (n_acc + n_call) / 4 + 2048;
     s->mg_dst = regrow(s, s->mg_dst, (int64_t)0, cap);
     s->mg_cnt = regrow(s, s->mg_cnt, (int64_t)0, cap);
@@ -199,6 +204,7 @@ void ensure_capacity(mm_system *s, int64_t n_acc, int64_t n_call) {
     s->cpk = regrow(s, s->cpk, (int64_t)0, 2 * cap);
     mr.nu_cap = cap;
   }
+  return regrown;
 }
 
 // Recompute the load-time summary (largest class) from the per-class sizes of the mirror.
@@ -242,6 +248,9 @@ void apply_edit(mm_system *s, const mm_edit &e) {
   std::set<int32_t> affected;
   affected.insert(C);
   int64_t n_acc = s->n_acc, n_call = s->n_call;
+  // which metric branches the edit can change: LCOM (accesses to own
+  // attributes, membership) and the coupling (uses across classes)
+  bool lcom_changes = false, coupling_changes = false, regrown = false;
   // ---- validate on the mirror, then patch the device CSR
   switch (e.kind) {
     case MM_EDIT_ADD_ACCESS:
@@ -253,7 +262,7 @@ void apply_edit(mm_system *s, const mm_edit &e) {
       const int32_t rank = (int32_t)(it - row.begin());
       if (e.kind == MM_EDIT_ADD_ACCESS) {
         if (present) throw MmError{MM_EEXIST, "apply_edit: the method already accesses this attribute"};
-        ensure_capacity(s, n_acc + 1, n_call);
+        regrown = ensure_capacity(s, n_acc + 1, n_call);
         patch_row(s, s->acc_idx, s->acc_rowptr, n_acc, m, rank, true, e.target);
         row.insert(it, e.target);
         ++n_acc;
@@ -264,6 +273,8 @@ void apply_edit(mm_system *s, const mm_edit &e) {
         --n_acc;
       }
       affected.insert(mr.attr_class[e.target]);
+      lcom_changes = mr.attr_class[e.target] == C;                   // sharing counts own attributes only
+      coupling_changes = mr.attr_class[e.target] != C && s->cbo_attrs;  // a foreign access is a use
       break;
     }
     case MM_EDIT_ADD_CALL:
@@ -277,7 +288,7 @@ void apply_edit(mm_system *s, const mm_edit &e) {
       auto &cr = mr.callers[e.target];
       if (e.kind == MM_EDIT_ADD_CALL) {
         if (present) throw MmError{MM_EEXIST, "apply_edit: the call already exists"};
-        ensure_capacity(s, n_acc, n_call + 1);
+        regrown = ensure_capacity(s, n_acc, n_call + 1);
         patch_row(s, s->call_idx, s->call_rowptr, n_call, m, rank, true, e.target);
         row.insert(it, e.target);
         cr.insert(std::lower_bound(cr.begin(), cr.end(), m), m);
@@ -290,6 +301,7 @@ void apply_edit(mm_system *s, const mm_edit &e) {
         --n_call;
       }
       affected.insert(mr.method_class[e.target]);
+      coupling_changes = mr.method_class[e.target] != C;  // calls never change LCOM
       break;
     }
     case MM_EDIT_MOVE: {
@@ -306,6 +318,7 @@ void apply_edit(mm_system *s, const mm_edit &e) {
       MM_LAUNCH_CHECK();
       mr.method_class[m] = D;
       s->methods_by_class = false;  // the move breaks the grouping by class
+      lcom_changes = coupling_changes = true;
       mr.cls_n[C]--;
       mr.cls_n[D]++;
       break;
@@ -323,7 +336,7 @@ void apply_edit(mm_system *s, const mm_edit &e) {
   const uint32_t kmask = s->kept_mask;
   const int32_t kmin = s->kept_min;
   patch_structures(s, e.kind, m, e.target, C);  // class lists, ranks and fan-in: only what the edit changed
-  build_metrics(s);
+  build_metrics(s, lcom_changes || regrown, coupling_changes || regrown);
   build_move_precompute(s);
   if (!had_cache) return;
   // ---- incremental update of the cached kept moves

@@ -440,7 +440,9 @@ void patch_structures(mm_system *s, int32_t kind, int32_t m, int32_t target, int
 void stage_candidates(mm_system *s, const mm_candidates *cands);
 void settle_staged(mm_system *s);
 void use_bitset_coupling(mm_system *s);
-void build_metrics(mm_system *s);                   // mm_metrics.cu
+// Metrics of every class; an edit may skip the LCOM branch or the coupling
+// branch when it cannot change them (mm_metrics.cu).
+void build_metrics(mm_system *s, bool lcom = true, bool coupling = true);
 void build_move_precompute(mm_system *s);           // mm_moves.cu
 void export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *out_m, int32_t kind);
 void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *cands,

@@ -549,7 +549,7 @@ void wait_point(mm_system *s, int k, cudaStream_t from, cudaStream_t to) {
   if (from != to && s->mid_ev[k]) MM_CUDA_TRY(cudaStreamWaitEvent(to, s->mid_ev[k], 0));
 }
 
-void build_metrics(mm_system *s) {
+void build_metrics(mm_system *s, bool lcom, bool coupling) {
   cudaStream_t st = s->stream;
   const int32_t c = s->c, M = s->M;
 
@@ -557,7 +557,11 @@ void build_metrics(mm_system *s) {
   // counts, P and Q, destination records; lists L and R (side streams 1 and 2,
   // finished by build_move_precompute); branch B (below, on the system's
   // stream): coupling and the adjacency structures.  They share no buffer.
-  {
+  // An edit that leaves LCOM (or the coupling) unchanged skips its branch: the
+  // structures it built stay as they are, and the points the lists wait for
+  // were passed long ago.
+  if (!lcom) s->side_pending[0] = st;
+  if (lcom) {
     cudaStream_t sa = fork_side(s, 0);
     Scratch &ev = s->side_eval[0];  // own scratch whether or not the branch runs concurrently
     Scratch &sw_ = s->side_sort[0];
@@ -606,6 +610,10 @@ void build_metrics(mm_system *s) {
   const int64_t ns = sw * (2 * (int64_t)c + 1);  // summary records: out-rows, in-rows, the zero row
   int32_t *row_count = s->cls_cbo;
   const int64_t nk = s->n_call + (s->cbo_attrs ? s->n_acc : 0);
+  if (!coupling) {
+    join_side(s, 0, s->side_pending[0]);
+    return;
+  }
   if (s->sorted_coupling) {
     // coupling from the use edges through the compressed rows; the full
     // bitsets wait for a dense evaluation
