@@ -336,7 +336,12 @@ void apply_edit(mm_system *s, const mm_edit &e) {
   const uint32_t kmask = s->kept_mask;
   const int32_t kmin = s->kept_min;
   patch_structures(s, e.kind, m, e.target, C);  // class lists, ranks and fan-in: only what the edit changed
-  build_metrics(s, lcom_changes || regrown, coupling_changes || regrown);
+  // the LCOM pair counts of the classes whose membership or own accesses changed
+  LcomClasses only;
+  only.cls[only.n++] = mr.method_class[m];  // m's class now (D after a move)
+  if (e.kind == MM_EDIT_MOVE) only.cls[only.n++] = C;
+  for (int k = 0; k < only.n; ++k) only.members[k] = mr.cls_n[only.cls[k]];
+  build_metrics(s, lcom_changes || regrown, coupling_changes || regrown, regrown ? nullptr : &only);
   build_move_precompute(s);
   if (!had_cache) return;
   // ---- incremental update of the cached kept moves

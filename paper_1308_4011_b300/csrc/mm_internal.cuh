@@ -441,8 +441,15 @@ void stage_candidates(mm_system *s, const mm_candidates *cands);
 void settle_staged(mm_system *s);
 void use_bitset_coupling(mm_system *s);
 // Metrics of every class; an edit may skip the LCOM branch or the coupling
-// branch when it cannot change them (mm_metrics.cu).
-void build_metrics(mm_system *s, bool lcom = true, bool coupling = true);
+// branch when it cannot change them, and recompute the LCOM pair counts of
+// only the (at most two) classes whose membership or own accesses it changed
+// (mm_metrics.cu).
+struct LcomClasses {
+  int n = 0;
+  int32_t cls[2] = {0, 0};
+  int64_t members[2] = {0, 0};  // current method counts of those classes
+};
+void build_metrics(mm_system *s, bool lcom = true, bool coupling = true, const LcomClasses *only = nullptr);
 void build_move_precompute(mm_system *s);           // mm_moves.cu
 void export_metrics(mm_system *s, mm_class_metrics *out_c, mm_method_metrics *out_m, int32_t kind);
 void evaluate_moves(mm_system *s, const mm_criteria &crit, const mm_candidates *cands,

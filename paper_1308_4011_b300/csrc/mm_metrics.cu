@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
                                                   const int64_t *own_ptr, const int32_t *own_list,
                                                   const int32_t *own, int32_t M, int32_t words,
                                                   uint32_t *gbm, int32_t *q, int64_t *cls_Q, int32_t g,
-                                                  unsigned long long *next) {
+                                                  unsigned long long *next, const int32_t *mlist) {
   pdl_wait();
   extern __shared__ uint32_t lu_smem[];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
@@ -96,9 +96,11 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
   __syncwarp();
   // warps take groups from a counter (unions differ widely in length)
   auto take = [&]() { return __shfl_sync(0xffffffffu, lane == 0 ? (int64_t)atomicAdd(next, 1ull) : (int64_t)0, 0); };
+  // with mlist the methods are mlist[0 .. M) (members of the classes an edit changed)
   for (int64_t wg = take(); wg * g < M; wg = take()) {
-    const int64_t base = wg * g, x = base + lane;
-    const bool mine = lane < (uint32_t)g && x < M;
+    const int64_t base = wg * g, pos = base + lane;
+    const bool mine = lane < (uint32_t)g && pos < M;
+    const int64_t x = mine && mlist ? (int64_t)mlist[pos] : pos;
     const int32_t ox = mine ? own[x] : 0;
     const int32_t C = mine ? method_class[x] : 0;
     int32_t u = 0;
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
     while (multi) {
       const int src = __ffs(multi) - 1;
       multi &= multi - 1u;
-      const int64_t xs = base + src;  // method of lane src
+      const int64_t xs = __shfl_sync(0xffffffffu, x, src);  // method of lane src
       const int32_t Cs = __shfl_sync(0xffffffffu, C, src);
       const int64_t a0 = acc_rowptr[xs];
       const int32_t v = accessor_union(acc_idx + a0, acc_rowptr[xs + 1] - a0, Cs, attr_class, own_ptr, own_list,
@@ -128,6 +130,26 @@ __global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, c
       if (qx) atomicAdd(reinterpret_cast<unsigned long long *>(&cls_Q[C]), (unsigned long long)qx);
     }
   }
+}
+
+// the members of up to two classes (counts n0, n1 known to the caller), one list
+__global__ void class_members_list(const int32_t *cm_list, const int64_t *cm_rowptr, int32_t C0, int64_t n0,
+                                   int32_t C1, int64_t n1, int32_t *out) {
+  pdl_wait();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n0 + n1; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = i < n0 ? cm_list[cm_rowptr[C0] + i] : cm_list[cm_rowptr[C1] + (i - n0)];
+}
+
+// P and Q of up to two classes whose pair counts were recomputed
+__global__ void finalize_listed(const int32_t *cls_n, int64_t *cls_Q, int64_t *cls_P, int32_t C0, int32_t C1, int ncls) {
+  pdl_wait();
+  const int k = (int)threadIdx.x;
+  if (k >= ncls) return;
+  const int32_t C = k == 0 ? C0 : C1;
+  const int64_t n = cls_n[C];
+  const int64_t Q = cls_Q[C] / 2;
+  cls_Q[C] = Q;
+  cls_P[C] = n * (n - 1) / 2 - Q;
 }
 
 __global__ void finalize_classes(const int32_t *cls_n, int64_t *cls_Q, int32_t c, int64_t *cls_P) {
@@ -549,7 +571,7 @@ void wait_point(mm_system *s, int k, cudaStream_t from, cudaStream_t to) {
   if (from != to && s->mid_ev[k]) MM_CUDA_TRY(cudaStreamWaitEvent(to, s->mid_ev[k], 0));
 }
 
-void build_metrics(mm_system *s, bool lcom, bool coupling) {
+void build_metrics(mm_system *s, bool lcom, bool coupling, const LcomClasses *only) {
   cudaStream_t st = s->stream;
   const int32_t c = s->c, M = s->M;
 
@@ -567,11 +589,20 @@ void build_metrics(mm_system *s, bool lcom, bool coupling) {
     Scratch &sw_ = s->side_sort[0];
     Scratch &uw = s->side_union[0];
     const int64_t A = s->A;
-    int64_t *acnt = static_cast<int64_t *>(ev.need(sizeof(int64_t) * ((size_t)A + 1), sa));
+    const int64_t nl = only ? only->members[0] + (only->n > 1 ? only->members[1] : 0) : M;
+    const size_t acnt_bytes = (sizeof(int64_t) * ((size_t)A + 1) + 255) & ~size_t(255);
+    // per-attribute counts, then (edits) the listed classes' members
+    char *evb = static_cast<char *>(ev.need(acnt_bytes + (only ? sizeof(int32_t) * (size_t)nl + 256 : 0), sa));
+    int64_t *acnt = reinterpret_cast<int64_t *>(evb);
     MM_CUDA_TRY(cudaMemsetAsync(acnt, 0, sizeof(int64_t) * ((size_t)A + 1), sa));
     MM_CUDA_TRY(cudaMemsetAsync(s->cls_S, 0, sizeof(int64_t) * (size_t)c, sa));
-    MM_CUDA_TRY(cudaMemsetAsync(s->cls_Q, 0, sizeof(int64_t) * (size_t)c, sa));
-    MM_CUDA_TRY(cudaMemsetAsync(s->q, 0, sizeof(int32_t) * (size_t)std::max(M, 1), sa));
+    if (only) {  // the pair counts of the listed classes only; the others stay
+      for (int k = 0; k < only->n; ++k)
+        MM_CUDA_TRY(cudaMemsetAsync(s->cls_Q + only->cls[k], 0, sizeof(int64_t), sa));
+    } else {
+      MM_CUDA_TRY(cudaMemsetAsync(s->cls_Q, 0, sizeof(int64_t) * (size_t)c, sa));
+      MM_CUDA_TRY(cudaMemsetAsync(s->q, 0, sizeof(int32_t) * (size_t)std::max(M, 1), sa));
+    }
     if (M > 0) {
       pdl_launch(own_access_count, grid_for(M), TPB, 0, sa, s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class, M,
                                                      acnt, s->own, s->cls_S);
@@ -586,17 +617,31 @@ void build_metrics(mm_system *s, bool lcom, bool coupling) {
       MM_LAUNCH_CHECK();
     }
     mark_point(s, 1, sa);  // own-access lists built (the s of list L entries needs them)
-    if (M > 0 && A > 0) {
-      // LCOM pair counts from accessor unions
-      const int g = lcom_group(M);
-      const UnionBitmap ub = union_bitmap(s, ceil_div(M, g), uw, sa);
+    if (nl > 0 && A > 0) {
+      // LCOM pair counts from accessor unions (all methods, or the listed classes' members)
+      const int32_t *mlist = nullptr;
+      if (only) {
+        int32_t *ml = reinterpret_cast<int32_t *>(evb + acnt_bytes);
+        pdl_launch(class_members_list, grid_for(nl), TPB, 0, sa, static_cast<const int32_t *>(s->cm_list),
+                   static_cast<const int64_t *>(s->cm_rowptr), only->cls[0], only->members[0],
+                   only->n > 1 ? only->cls[1] : only->cls[0], only->n > 1 ? only->members[1] : (int64_t)0, ml);
+        MM_LAUNCH_CHECK();
+        mlist = ml;
+      }
+      const int g = lcom_group(nl);
+      const UnionBitmap ub = union_bitmap(s, ceil_div(nl, g), uw, sa);
       MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 8, 0, sizeof(unsigned long long), sa));
       pdl_launch(lcom_union, ub.grid, 256, ub.smem, sa, s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class,
-                                                 s->own_ptr, s->own_list, s->own, M, ub.words, ub.gbm, s->q,
-                                                 s->cls_Q, g, s->d_u64 + 8);
+                 s->own_ptr, s->own_list, s->own, (int32_t)nl, ub.words, ub.gbm, s->q, s->cls_Q, g, s->d_u64 + 8,
+                 mlist);
       MM_LAUNCH_CHECK();
     }
-    pdl_launch(finalize_classes, grid_for(c), TPB, 0, sa, s->cls_n, s->cls_Q, c, s->cls_P);
+    if (only) {
+      pdl_launch(finalize_listed, 1, 32, 0, sa, static_cast<const int32_t *>(s->cls_n), s->cls_Q, s->cls_P, only->cls[0],
+                 only->n > 1 ? only->cls[1] : only->cls[0], only->n);
+    } else {
+      pdl_launch(finalize_classes, grid_for(c), TPB, 0, sa, s->cls_n, s->cls_Q, c, s->cls_P);
+    }
     MM_LAUNCH_CHECK();
     pdl_launch(destination_records, grid_for(c), TPB, 0, sa, s->cls_n, s->cls_a, s->cls_P, s->cls_Q, s->cls_S, c,
                                                      s->dest_rec);
