@@ -105,18 +105,19 @@ typedef struct mm_system mm_system; /* opaque; owns all device memory it allocat
  *                             calls itself
  *   cbo_attrs                 1: an access to another class's attribute is a
  *                             use for CBO (default); 0: only calls count
- *   flags                     0, or one of MM_LOAD_SORTED_COUPLING (build the
- *                             class coupling by sorting the use edges; the
+ *   flags                     0, or one of MM_LOAD_PACKED_COUPLING (build the
+ *                             class coupling from the use edges into the
+ *                             compressed rows directly; the
  *                             full c x c adjacency bitsets are then built only
  *                             when a full cross-product evaluation needs
  *                             them), MM_LOAD_BITSET_COUPLING (always build the
- *                             bitsets with the coupling).  With 0 the sorted
+ *                             bitsets with the coupling).  With 0 the packed
  *                             form is chosen when the two bitsets would take
- *                             more than MM_SORTED_COUPLING_BYTES.  Results
+ *                             more than MM_PACKED_COUPLING_BYTES.  Results
  *                             are the same either way.
  */
-enum { MM_LOAD_SORTED_COUPLING = 1, MM_LOAD_BITSET_COUPLING = 2 };
-#define MM_SORTED_COUPLING_BYTES (512.0 * 1024.0 * 1024.0)
+enum { MM_LOAD_PACKED_COUPLING = 1, MM_LOAD_BITSET_COUPLING = 2 };
+#define MM_PACKED_COUPLING_BYTES (512.0 * 1024.0 * 1024.0)
 typedef struct {
   int32_t n_classes, n_methods, n_attrs;
   int32_t ptr_kind; /* MM_PTR_HOST or MM_PTR_DEVICE, for all six arrays */
@@ -327,7 +328,7 @@ MMREF_API mm_status mm_suggest_moves(mm_system *sys, const mm_criteria *crit, co
  * criteria keep at most MM_NOALLOC_MAX_KEPT moves; beyond either the call
  * returns MM_EBUDGET with a message naming the limit, and mm_suggest_moves
  * must be used instead.  The same holds for the full cross product of a
- * system with sorted coupling (MM_LOAD_SORTED_COUPLING) whose adjacency
+ * system with packed coupling (MM_LOAD_PACKED_COUPLING) whose adjacency
  * bitsets no full cross-product call has built yet.  Candidate lists must be
  * NULL (full cross product) or
  * in device memory.  out_topk is in out_kind memory.

@@ -161,7 +161,7 @@ void allocate_compute_buffers(mm_system *s) {
   s->mg_cnt = a.get<int32_t>(nu);
   s->mg_count = a.get<int64_t>(2);
   s->adj_words = ((c + 127) / 128) * 4;  // rows padded to 16 bytes for vector loads
-  if (s->sorted_coupling) {  // built on demand from the multigraph rows
+  if (s->packed_coupling) {  // built on demand from the multigraph rows
     s->out_adj = nullptr;
     s->in_adj = nullptr;
   } else {
@@ -293,12 +293,12 @@ mm_status mm_load_system(const mm_system_desc *desc, void *cuda_stream, mm_syste
     s->n_acc = desc->n_acc;
     s->n_call = desc->n_call;
     s->cbo_attrs = desc->cbo_attrs ? 1 : 0;
-    if (desc->flags & ~(int32_t)(MM_LOAD_SORTED_COUPLING | MM_LOAD_BITSET_COUPLING))
+    if (desc->flags & ~(int32_t)(MM_LOAD_PACKED_COUPLING | MM_LOAD_BITSET_COUPLING))
       throw MmError{MM_EINVAL, "load_system: unknown flags"};
     {
       const double bitset_bytes = 8.0 * (double)((s->c + 127) / 128 * 4) * (double)s->c;
-      s->sorted_coupling = (desc->flags & MM_LOAD_SORTED_COUPLING) ||
-                           (!(desc->flags & MM_LOAD_BITSET_COUPLING) && bitset_bytes > MM_SORTED_COUPLING_BYTES);
+      s->packed_coupling = (desc->flags & MM_LOAD_PACKED_COUPLING) ||
+                           (!(desc->flags & MM_LOAD_BITSET_COUPLING) && bitset_bytes > MM_PACKED_COUPLING_BYTES);
     }
     const int64_t M = s->M, A = s->A;
     // size every load-time buffer, reserve one slab, then carve them out of it

@@ -259,10 +259,11 @@ struct mm_system {
   int64_t *mg_count;               // device scalar: number of distinct (Y, E)
   uint32_t *out_adj, *in_adj;
   int64_t adj_words;
-  // coupling built by sorting the use edges (large systems): the full bitsets
+  // coupling built from the use edges into the compressed rows (large
+  // systems): the full bitsets
   // above are then built from the multigraph rows only when a dense
   // evaluation needs them (adj_ws), and adj_built says whether they are current
-  bool sorted_coupling = false;
+  bool packed_coupling = false;
   bool adj_built = false;
   Scratch adj_ws;
   // compressed two-level adjacency for the restricted evaluation (L2-resident).

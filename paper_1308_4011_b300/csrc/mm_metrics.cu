@@ -659,7 +659,7 @@ void build_metrics(mm_system *s, bool lcom, bool coupling, const LcomClasses *on
     join_side(s, 0, s->side_pending[0]);
     return;
   }
-  if (s->sorted_coupling) {
+  if (s->packed_coupling) {
     // coupling from the use edges through the compressed rows; the full
     // bitsets wait for a dense evaluation
     s->adj_built = false;
@@ -751,7 +751,7 @@ void build_metrics(mm_system *s, bool lcom, bool coupling, const LcomClasses *on
 }
 
 // The full adjacency bitsets, from the multigraph rows, for a system whose
-// coupling was built by sorting (allocated on first use).
+// coupling was built in the packed form (allocated on first use).
 void ensure_adjacency(mm_system *s) {
   if (s->adj_built) return;
   cudaStream_t st = s->stream;
@@ -771,11 +771,11 @@ void ensure_adjacency(mm_system *s) {
 // Build the coupling with the full bitsets from now on (for callers that read
 // them inside captured work, such as a batch's graph).
 void use_bitset_coupling(mm_system *s) {
-  if (!s->sorted_coupling) return;
+  if (!s->packed_coupling) return;
   const int64_t words = s->adj_words * (int64_t)s->c;
   uint32_t *p = static_cast<uint32_t *>(s->adj_ws.need(2 * sizeof(uint32_t) * (size_t)words, s->stream));
   s->out_adj = p;
   s->in_adj = p + words;
-  s->sorted_coupling = false;
+  s->packed_coupling = false;
   s->adj_built = false;
 }

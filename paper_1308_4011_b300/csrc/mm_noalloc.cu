@@ -111,7 +111,7 @@ extern "C" MMREF_API mm_status mm_suggest_moves_noalloc(mm_system *s, const mm_c
     }
     if ((!cands || !cands->rowptr) && !s->adj_built)
       throw MmError{MM_EBUDGET, "suggest_moves_noalloc: the full cross product needs the system's adjacency "
-                                "bitsets, which are built on demand for systems with sorted coupling; use "
+                                "bitsets, which are built on demand for systems with packed coupling; use "
                                 "mm_suggest_moves"};
     WaitScope wait(s->d_fault, &s->test_stall_scans);
     unsigned char *base = scratch_for_device(s->device);

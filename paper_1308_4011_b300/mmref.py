@@ -59,7 +59,7 @@ class _Desc(ctypes.Structure):
                 ("cbo_attrs", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
-LOAD_SORTED_COUPLING, LOAD_BITSET_COUPLING = 1, 2
+LOAD_PACKED_COUPLING, LOAD_BITSET_COUPLING = 1, 2
 class _Crit(ctypes.Structure):
     _fields_ = [("metric_mask", ctypes.c_uint32), ("min_improved", ctypes.c_int32)]
 
@@ -259,7 +259,7 @@ class System:
 def load_system(n_classes, method_class, attr_class, acc_rowptr, acc_idx, call_rowptr, call_idx, *,
                 cbo_attrs: bool = True, stream=None, flags: int = 0) -> System:
     """mm_load_system.  Arrays are either all numpy (host) or all CUDA tensors;
-    flags: 0 or LOAD_SORTED_COUPLING / LOAD_BITSET_COUPLING."""
+    flags: 0 or LOAD_PACKED_COUPLING / LOAD_BITSET_COUPLING."""
     arrs = (method_class, attr_class, acc_rowptr, acc_idx, call_rowptr, call_idx)
     kinds = {_kind(a) for a in arrs}
     if len(kinds) != 1:

@@ -1,4 +1,4 @@
-"""The class coupling built by sorting the use edges (MM_LOAD_SORTED_COUPLING:
+"""The class coupling built from the use edges into the compressed rows (MM_LOAD_PACKED_COUPLING:
 no full adjacency bitsets until a full cross-product evaluation builds them
 from the multigraph rows) gives the same metrics, records, suggestions, edits,
 rules and batches as the bitset construction, and both equal the oracle."""
@@ -20,7 +20,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from paper_1308_4011_b300 import mmref  # noqa: E402
 
-SORTED, BITSET = mmref.LOAD_SORTED_COUPLING, mmref.LOAD_BITSET_COUPLING
+PACKED, BITSET = mmref.LOAD_PACKED_COUPLING, mmref.LOAD_BITSET_COUPLING
 CLASS_MAP = {"n_methods": "n", "n_attrs": "a", "P": "P", "Q": "Q", "S": "S", "lcom_ck": "ck",
              "hs_num": "hs_num", "hs_den": "hs_den", "cbo": "cbo"}
 KEPT = ("m", "d", "n_improved", "d_lcom_ck_sum", "d_cbo_sum")
@@ -49,13 +49,13 @@ def _check_metrics(o, cm, mm_):
 
 
 @pytest.mark.parametrize("cbo_attrs", [True, False])
-def test_sorted_coupling_every_record_on_tiny(cbo_attrs):
+def test_packed_coupling_every_record_on_tiny(cbo_attrs):
     """Metrics and multigraph size; the restricted lists first (compressed rows
     only), then the full cross product (which builds the bitsets from the
     rows), record by record against the oracle."""
     s = synth.named("tiny")
     o = oracle.Oracle(s, cbo_attrs=cbo_attrs)
-    g = mmref.load_synth(s, cbo_attrs=cbo_attrs, device=True, flags=SORTED)
+    g = mmref.load_synth(s, cbo_attrs=cbo_attrs, device=True, flags=PACKED)
     cm, mm_ = mmref.compute_metrics(g, "host", "host")
     _check_metrics(o, cm, mm_)
     assert g.info()["n_class_edges"] == len(o.multigraph()[1])
@@ -75,10 +75,10 @@ def test_sorted_coupling_every_record_on_tiny(cbo_attrs):
 
 
 @pytest.mark.parametrize("seed", range(4))
-def test_sorted_and_bitset_forms_agree_on_random_systems(seed):
+def test_packed_and_bitset_forms_agree_on_random_systems(seed):
     s = tiny_random(seed + 40)
     outs = []
-    for flags in (SORTED, BITSET):
+    for flags in (PACKED, BITSET):
         g = mmref.load_synth(s, device=True, flags=flags)
         cm, mm_ = mmref.compute_metrics(g, "host", "host")
         rec, dig = _records(g, 7, 1)
@@ -87,7 +87,7 @@ def test_sorted_and_bitset_forms_agree_on_random_systems(seed):
     assert outs[0] == outs[1]
 
 
-def test_sorted_coupling_long_rows_general_path():
+def test_packed_coupling_long_rows_general_path():
     """Methods with more list entries than the restricted kernel stages take
     its general path, whose probes read the compressed rows."""
     rng = np.random.default_rng(11)
@@ -108,7 +108,7 @@ def test_sorted_coupling_long_rows_general_path():
     rp[1:] = np.cumsum([len(r) for r in rows])
     dst = np.asarray([D for r in rows for D in r], dtype=np.int32)
     o = oracle.Oracle(s, threads=1)
-    g = mmref.load_synth(s, device=True, flags=SORTED)
+    g = mmref.load_synth(s, device=True, flags=PACKED)
     mmref.compute_metrics(g, None, None)
     for mask, mi in ((7, 1), (3, 1)):
         ref = o.evaluate(mask=mask, min_improved=mi, cand_rowptr=rp, cand_dst=dst, method=1, records=True)
@@ -117,10 +117,10 @@ def test_sorted_coupling_long_rows_general_path():
     g.free()
 
 
-def test_sorted_coupling_medium_digest():
+def test_packed_coupling_medium_digest():
     s = synth.named("medium")
     o = oracle.Oracle(s)
-    g = mmref.load_synth(s, device=True, flags=SORTED)
+    g = mmref.load_synth(s, device=True, flags=PACKED)
     cm, mm_ = mmref.compute_metrics(g, "host", "host")
     _check_metrics(o, cm, mm_)
     dig = np.zeros(1, dtype=np.uint64)
@@ -129,8 +129,8 @@ def test_sorted_coupling_medium_digest():
     g.free()
 
 
-def test_large_system_takes_the_sorted_form_by_size():
-    """50,000 classes: the bitsets would take 626 MB, so the sorted form is
+def test_large_system_takes_the_packed_form_by_size():
+    """50,000 classes: the bitsets would take 626 MB, so the packed form is
     chosen without a flag; the restricted lists evaluate without building them."""
     s = synth.named("large")
     rp, dst = synth.candidates(s, synth.LARGE_EXTRA_CANDIDATES, seed=2)
@@ -144,11 +144,11 @@ def test_large_system_takes_the_sorted_form_by_size():
     g.free()
 
 
-def test_edits_on_sorted_coupling():
-    """Edits rebuild the coupling by sorting; the kept list kept up to date
+def test_edits_on_packed_coupling():
+    """Edits rebuild the coupling in the packed form; the kept list kept up to date
     through the dense tiles (bitsets built on demand) equals a fresh oracle."""
     s = synth.generate(60, 500, 250, max_class=30, seed=3, lambda_acc=3, lambda_call=4, p_loc=0.7)
-    g = mmref.load_synth(s, device=True, flags=SORTED)
+    g = mmref.load_synth(s, device=True, flags=PACKED)
     mmref.compute_metrics(g, None, None)
     mmref.suggest_moves(g, 10, 3, 2)
     rng = np.random.default_rng(2)
@@ -168,11 +168,11 @@ def test_edits_on_sorted_coupling():
 
 
 def test_noalloc_full_cross_product_needs_the_bitsets():
-    """Before any full cross-product call has built the bitsets of a sorted
+    """Before any full cross-product call has built the bitsets of a packed
     system, the allocation-free suggestion refuses (MM_EBUDGET); after one, it
     answers like mm_suggest_moves."""
     s = synth.named("tiny")
-    g = mmref.load_synth(s, device=True, flags=SORTED)
+    g = mmref.load_synth(s, device=True, flags=PACKED)
     mmref.compute_metrics(g, None, None)
     with pytest.raises(mmref.MMError) as e:
         mmref.suggest_moves_noalloc(g, 10, 3, 2)
@@ -183,10 +183,10 @@ def test_noalloc_full_cross_product_needs_the_bitsets():
     g.free()
 
 
-def test_batch_of_sorted_systems():
+def test_batch_of_packed_systems():
     """A batch switches its systems to the bitset form (its graph reads them)."""
     systems = [synth.generate(**synth.batched_params(100 + i)) for i in range(3)]
-    gs = [mmref.load_synth(x, device=True, flags=SORTED) for x in systems]
+    gs = [mmref.load_synth(x, device=True, flags=PACKED) for x in systems]
     b = mmref.Batch(gs, mask=3, min_improved=2)
     digests, n_kept = b.run()
     for i, x in enumerate(systems):
