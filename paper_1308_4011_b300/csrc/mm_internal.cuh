@@ -332,6 +332,9 @@ void zero_buffers(void *a, size_t na, void *b, size_t nb, void *c, size_t nc, cu
 uint32_t stalled_scan_probe();
 void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch &ws, cudaStream_t st,
                             int64_t *total_dev = nullptr);
+// Summary records: record k's first packed word = the number of marked words
+// in records 0 .. k-1 (an exclusive scan of their popcounts, written into .y).
+void scan_summary_first(uint2 *csum, int64_t n, Scratch &ws, cudaStream_t st);
 
 // Stable LSD radix sort of n keys (and optional uint32 values) on bits [0, nbits).
 // The result is left in keys/vals; alt buffers are scratch of the same size.
@@ -340,6 +343,52 @@ void radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t
 void radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
                     int nbits, Scratch &ws, cudaStream_t st);
 // ---------------------------------------------------------------- pipeline stages
+
+// Use edges of a warp's group of nm <= 32 consecutive methods x0 .. x0+nm-1:
+// each method's calls, then (with_acc) its accesses, are the contiguous range
+// [seg(x), seg(x + 1)) with seg(x) = call_rowptr[x] + acc_rowptr[x] (calls
+// only: call_rowptr[x]), so the group's edges are [s0, s1) and the warp can
+// walk them 32 at a time with coalesced loads and stores.  Lane l holds the
+// bounds of method x0 + l.
+struct UseGroup {
+  int64_t seg, cr, ar;
+  int32_t nc;
+  int64_t s0, s1;
+};
+__device__ __forceinline__ UseGroup use_group(const int64_t *call_rowptr, const int64_t *acc_rowptr, bool with_acc,
+                                              int64_t x0, int32_t nm, uint32_t lane) {
+  UseGroup u;
+  const int64_t x = x0 + min((int32_t)lane, nm);  // lanes from nm on hold the group's end
+  u.cr = call_rowptr[x];
+  u.ar = with_acc ? acc_rowptr[x] : 0;
+  u.seg = u.cr + u.ar;
+  u.nc = (int32_t)lane < nm ? (int32_t)(call_rowptr[x + 1] - u.cr) : 0;
+  u.s0 = __shfl_sync(0xffffffffu, u.seg, 0);
+  if (nm < 32) {
+    u.s1 = __shfl_sync(0xffffffffu, u.seg, nm);
+  } else {
+    u.s1 = call_rowptr[x0 + 32] + (with_acc ? acc_rowptr[x0 + 32] : 0);
+  }
+  return u;
+}
+// Edge p of the group (every lane calls it, p need not be in range): the
+// method's slot, whether it is a call, and its index in call_idx or acc_idx.
+__device__ __forceinline__ void use_edge_at(const UseGroup &u, int64_t p, int32_t nm, int32_t &slot, bool &is_call,
+                                            int64_t &idx) {
+  int32_t lo = 0;  // the last slot whose range starts at or before p
+#pragma unroll
+  for (int b = 16; b > 0; b >>= 1) {
+    const int32_t mid = lo + b;
+    const int64_t sv = __shfl_sync(0xffffffffu, u.seg, mid & 31);
+    if (mid < nm && sv <= p) lo = mid;
+  }
+  slot = lo;
+  const int64_t o = p - __shfl_sync(0xffffffffu, u.seg, lo);
+  const int32_t nc = __shfl_sync(0xffffffffu, u.nc, lo);
+  const int64_t cr = __shfl_sync(0xffffffffu, u.cr, lo), ar = __shfl_sync(0xffffffffu, u.ar, lo);
+  is_call = o < nc;
+  idx = is_call ? cr + o : ar + (o - nc);
+}
 
 void load_validate_and_summarise(mm_system *s);     // mm_system.cu
 void load_finish(mm_system *s);                     // mm_system.cu
@@ -354,7 +403,9 @@ struct UnionBitmap {
   uint32_t *gbm;
   unsigned grid;
 };
-UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted, Scratch &ws, cudaStream_t st);
+// reserve: further shared bytes per block of 8 warps that the kernel needs
+// beside the bitmaps (the bitmaps go to global memory when both do not fit)
+UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted, Scratch &ws, cudaStream_t st, size_t reserve = 0);
 // Side streams of the calling thread on the current device (created on first
 // use).  fork_side() returns the stream a branch runs on: side stream i, made
 // to wait for the work so far on s->stream, or s->stream itself when the

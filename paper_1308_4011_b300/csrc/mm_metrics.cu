@@ -67,53 +67,156 @@ __global__ void own_access_fill(const int32_t *method_class, const int32_t *meth
 
 // LCOM pair counts: q_x = methods of x's class sharing an own attribute with x
 // = |union of the accessor lists of x's own attributes| - 1 (x itself), and
-// sum_x q_x = 2 Q_C.  One thread per method: with one own attribute the union
-// is its accessor list; methods with two or more are taken by the whole warp
-// in turn, with bitmap words per warp in shared memory, or in a zeroed global
-// slice when the largest class is too big.
-// A warp owns g consecutive methods (one per lane, g = 8, 16 or 32); each
-// method with two or more own attributes takes the whole warp for its accessor
-// union, one after the other, so g sets the length of a warp's chain of
-// dependent loads: small groups when the methods do not fill the GPU's warps,
-// 32 when they do.
+// sum_x q_x = 2 Q_C.  A warp owns g consecutive methods (one slot each) and
+// walks their accesses, which are contiguous, 32 at a time: an own access of
+// a method with one own attribute gives q directly (its list length - 1);
+// those of methods with two or more have their accessor lists expanded
+// across the lanes, and every accessor other than x goes into x's hash table
+// of LU_TAB class-local ranks in shared memory (an insert that finds the rank
+// already there adds nothing).  The distinct ranks per table are q_x.  A
+// method whose table fills up, and every method of a listed subset (edits),
+// takes the whole warp for a bitmap union over its class's method ranks
+// (bitmap words per warp in shared memory, or in a zeroed global slice when
+// the largest class is too big).
+constexpr int LU_TAB = 32;
+constexpr uint32_t LU_EMPTY = 0xffffffffu;
+struct LcomWarp {
+  uint32_t tab[32 * LU_TAB];  // per slot: open addressing, linear probing
+  int64_t arp[33];            // access row bounds of the group's methods
+  int32_t res[32];            // q + 1 of slots with one own attribute
+  int32_t full[32];           // slot whose table filled up
+};
+constexpr size_t LU_WARP_BYTES = (sizeof(LcomWarp) + 15) / 16 * 16;
+constexpr size_t LU_RESERVE = LU_WARP_BYTES * 8;  // per block of 8 warps
+
 inline int lcom_group(int64_t M) {
   const int64_t per_warp = M / (B300_SMS * 64);
   return per_warp >= 32 ? 32 : (per_warp >= 16 ? 16 : 8);
 }
 
-__global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, const int64_t *acc_rowptr,
-                                                  const int32_t *acc_idx, const int32_t *attr_class,
-                                                  const int64_t *own_ptr, const int32_t *own_list,
-                                                  const int32_t *own, int32_t M, int32_t words,
-                                                  uint32_t *gbm, int32_t *q, int64_t *cls_Q, int32_t g,
-                                                  unsigned long long *next, const int32_t *mlist) {
+__device__ __forceinline__ void lu_insert(uint32_t *tab, int32_t *full, int32_t slot, uint32_t j) {
+  uint32_t h = (j * 2654435761u) >> 27;  // LU_TAB = 32 buckets
+  for (int t = 0; t < LU_TAB; ++t) {
+    const uint32_t old = atomicCAS(&tab[slot * LU_TAB + h], LU_EMPTY, j);
+    if (old == LU_EMPTY || old == j) return;
+    h = (h + 1u) & (LU_TAB - 1);
+  }
+  full[slot] = 1;
+}
+
+__global__ void __launch_bounds__(256) lcom_union(const int32_t *method_class, const int32_t *method_local,
+                                                  const int64_t *acc_rowptr, const int32_t *acc_idx,
+                                                  const int32_t *attr_class, const int64_t *own_ptr,
+                                                  const int32_t *own_list, const int32_t *own, int32_t M,
+                                                  int32_t words, uint32_t *gbm, int32_t *q, int64_t *cls_Q,
+                                                  int32_t g, unsigned long long *next, const int32_t *mlist) {
   pdl_wait();
-  extern __shared__ uint32_t lu_smem[];
-  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-  uint32_t *bm = gbm ? gbm + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wid) * words : lu_smem + wid * words;
+  extern __shared__ __align__(16) uint32_t lu_smem[];
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  LcomWarp &lw = *reinterpret_cast<LcomWarp *>(reinterpret_cast<unsigned char *>(lu_smem) + wid * LU_WARP_BYTES);
+  uint32_t *bm = gbm ? gbm + ((int64_t)blockIdx.x * nw + wid) * words
+                     : reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(lu_smem) + nw * LU_WARP_BYTES) +
+                           wid * words;
   if (!gbm)
     for (int32_t i = (int32_t)lane; i < words; i += 32) bm[i] = 0u;
+  for (int32_t i = (int32_t)lane; i < 32 * LU_TAB; i += 32) lw.tab[i] = LU_EMPTY;
+  lw.full[lane] = 0;
   __syncwarp();
   // warps take groups from a counter (unions differ widely in length)
   auto take = [&]() { return __shfl_sync(0xffffffffu, lane == 0 ? (int64_t)atomicAdd(next, 1ull) : (int64_t)0, 0); };
-  // with mlist the methods are mlist[0 .. M) (members of the classes an edit changed)
   for (int64_t wg = take(); wg * g < M; wg = take()) {
     const int64_t base = wg * g, pos = base + lane;
-    const bool mine = lane < (uint32_t)g && pos < M;
+    const int32_t nm = (int32_t)min((int64_t)g, (int64_t)M - base);
+    const bool mine = (int32_t)lane < nm;
+    // with mlist the methods are mlist[0 .. M) (members of the classes an edit changed)
     const int64_t x = mine && mlist ? (int64_t)mlist[pos] : pos;
     const int32_t ox = mine ? own[x] : 0;
-    const int32_t C = mine ? method_class[x] : 0;
+    const int32_t C = mine ? method_class[x] : -1;
     int32_t u = 0;
-    if (ox == 1) {
-      for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
-        const int32_t al = acc_idx[e];
-        if (attr_class[al] == C) {
-          u = (int32_t)(own_ptr[al + 1] - own_ptr[al]);
-          break;
+    bool over = false;
+    if (mlist) {
+      if (ox == 1) {
+        for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e) {
+          const int32_t al = acc_idx[e];
+          if (attr_class[al] == C) {
+            u = (int32_t)(own_ptr[al + 1] - own_ptr[al]);
+            break;
+          }
         }
       }
+      over = ox >= 2;
+    } else {
+      const int32_t r = mine ? method_local[x] : -1;
+      if ((int32_t)lane <= nm) lw.arp[lane] = acc_rowptr[base + lane];
+      if (lane == 0 && nm == 32) lw.arp[32] = acc_rowptr[base + 32];
+      __syncwarp();
+      const int64_t a_hi = lw.arp[nm];
+      for (int64_t e0 = lw.arp[0]; e0 < a_hi; e0 += 32) {
+        const int64_t e = e0 + lane;
+        const bool v = e < a_hi;
+        int32_t sl = 0;  // slot of access e: the last with arp[sl] <= e
+        if (v) {
+          int32_t lo = 0, hi = nm - 1;
+          while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (lw.arp[mid] <= e) lo = mid; else hi = mid - 1;
+          }
+          sl = lo;
+        }
+        const int32_t Cs = __shfl_sync(0xffffffffu, C, sl), oxs = __shfl_sync(0xffffffffu, ox, sl);
+        const int32_t rs = __shfl_sync(0xffffffffu, r, sl);
+        const int32_t al = v && oxs > 0 ? acc_idx[e] : 0;
+        const bool ow = v && oxs > 0 && attr_class[al] == Cs;
+        int64_t p0 = 0;
+        int32_t n = 0;
+        if (ow) {
+          p0 = own_ptr[al];
+          n = (int32_t)(own_ptr[al + 1] - p0);
+          if (oxs == 1) lw.res[sl] = n;
+        }
+        if (oxs < 2) n = 0;
+        // the n accessors of each lane's attribute, 32 at a time across the warp
+        int32_t incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+          if ((int)lane >= o) incl += t;
+        }
+        const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int32_t k0 = 0; k0 < total; k0 += 32) {
+          const int32_t k = k0 + (int32_t)lane;
+          int32_t lo = 0, hi = 31;  // lane holding element k: the first whose inclusive count exceeds k
+#pragma unroll
+          for (int step = 0; step < 5; ++step) {
+            const int32_t mid = (lo + hi) >> 1;
+            const int32_t pm = __shfl_sync(0xffffffffu, incl, mid);
+            if (pm > k) hi = mid; else lo = mid + 1;
+          }
+          const int32_t excl = __shfl_sync(0xffffffffu, incl, lo) - __shfl_sync(0xffffffffu, n, lo);
+          const int64_t pb = __shfl_sync(0xffffffffu, p0, lo);
+          const int32_t ss = __shfl_sync(0xffffffffu, sl, lo), rr = __shfl_sync(0xffffffffu, rs, lo);
+          if (k < total) {
+            const int32_t j = own_list[pb + (k - excl)];
+            if (j != rr) lu_insert(lw.tab, lw.full, ss, (uint32_t)j);
+          }
+        }
+      }
+      __syncwarp();
+      if (ox == 1) u = lw.res[lane];
+      if (ox >= 2) {
+        int32_t cnt = 0;
+#pragma unroll 8
+        for (int t = 0; t < LU_TAB; ++t)  // skewed: lane l reads bank (t + l) mod 32
+          cnt += lw.tab[lane * LU_TAB + ((t + (int)lane) & (LU_TAB - 1))] != LU_EMPTY;
+        u = cnt + 1;
+        over = lw.full[lane] != 0;
+      }
+      __syncwarp();
+      for (int32_t i = (int32_t)lane; i < 32 * LU_TAB; i += 32) lw.tab[i] = LU_EMPTY;
+      lw.full[lane] = 0;
+      __syncwarp();
     }
-    uint32_t multi = __ballot_sync(0xffffffffu, ox >= 2);
+    uint32_t multi = __ballot_sync(0xffffffffu, over);
     while (multi) {
       const int src = __ffs(multi) - 1;
       multi &= multi - 1u;
@@ -323,6 +426,25 @@ __global__ void coupling_count(const uint64_t *edges, int64_t n, const int64_t *
   }
 }
 
+// the same from the packed rows: E's position in out-row Y is the row position
+// of its packed word plus the bits below E in that word
+__global__ void coupling_count_packed(const uint64_t *__restrict__ edges, int64_t n,
+                                      const int64_t *__restrict__ mg_rowptr, const uint2 *__restrict__ csum,
+                                      const uint32_t *__restrict__ cpk, const int32_t *__restrict__ wrank, int64_t sw,
+                                      int32_t *__restrict__ mg_cnt) {
+  pdl_wait();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = edges[i];
+    if (k == ~0ull) continue;
+    const int32_t Y = (int32_t)(k >> 32), E = (int32_t)(uint32_t)k;
+    const int64_t row0 = mg_rowptr[Y];
+    const uint2 rec = csum[(int64_t)Y * sw + (E >> 10)];
+    const uint32_t widx = rec.y + __popc(rec.x & ((1u << ((E >> 5) & 31)) - 1u));
+    const int32_t rank = wrank[widx] + __popc(cpk[widx] & ((1u << (E & 31)) - 1u));
+    atomicAdd(&mg_cnt[row0 + rank], 1);
+  }
+}
+
 __global__ void summary_popc(const uint2 *sum, int64_t n, int32_t *cnt) {
   pdl_wait();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -371,32 +493,40 @@ __device__ __forceinline__ void mark_summary(uint2 *csum, int64_t sw, int64_t ro
 
 // edge keys (Y << 32 | E, or ~0 inside the class) at the method's calls, then
 // its accesses, and the summary bits of both rows of every coupling edge
-__global__ void coupling_keys(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
-                              const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
-                              int32_t M, int32_t c, int32_t cbo_attrs, uint2 *csum, int64_t sw, uint64_t *edges) {
+__global__ void coupling_keys(const int32_t *__restrict__ method_class, const int64_t *__restrict__ call_rowptr,
+                              const int32_t *__restrict__ call_idx, const int64_t *__restrict__ acc_rowptr,
+                              const int32_t *__restrict__ acc_idx, const int32_t *__restrict__ attr_class, int32_t M,
+                              int32_t c, int32_t cbo_attrs, uint2 *__restrict__ csum, int64_t sw,
+                              uint64_t *__restrict__ edges) {
   pdl_wait();
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < M; x += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t Y = method_class[x];
-    int64_t pos = call_rowptr[x] + (cbo_attrs ? acc_rowptr[x] : 0);
-    const int64_t ne = call_rowptr[x + 1] - call_rowptr[x];
-    const int64_t na = cbo_attrs ? acc_rowptr[x + 1] - acc_rowptr[x] : 0;
-    for (int64_t k = 0; k < ne + na; ++k) {
-      const int32_t E = k < ne ? method_class[call_idx[call_rowptr[x] + k]] : attr_class[acc_idx[acc_rowptr[x] + k - ne]];
-      if (E != Y) {
-        mark_summary(csum, sw, Y, E);
-        mark_summary(csum, sw, (int64_t)c + E, Y);
-        edges[pos++] = ((uint64_t)(uint32_t)Y << 32) | (uint32_t)E;
-      } else {
-        edges[pos++] = ~0ull;
+  // a warp per 32 methods: their edges are one contiguous range (coalesced
+  // index loads and key stores)
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < M; w += nwarps) {
+    const int64_t x0 = w * 32;
+    const int32_t nm = (int32_t)min((int64_t)32, (int64_t)M - x0);
+    const UseGroup u = use_group(call_rowptr, acc_rowptr, cbo_attrs != 0, x0, nm, lane);
+    const int32_t Yl = (int32_t)lane < nm ? method_class[x0 + lane] : 0;
+    for (int64_t p0 = u.s0; p0 < u.s1; p0 += 32) {
+      const int64_t p = p0 + lane;
+      int32_t slot;
+      bool is_call;
+      int64_t idx;
+      use_edge_at(u, p, nm, slot, is_call, idx);
+      const int32_t Y = __shfl_sync(0xffffffffu, Yl, slot);
+      if (p < u.s1) {
+        const int32_t E = is_call ? method_class[call_idx[idx]] : attr_class[acc_idx[idx]];
+        if (E != Y) {
+          mark_summary(csum, sw, Y, E);
+          mark_summary(csum, sw, (int64_t)c + E, Y);
+          edges[p] = ((uint64_t)(uint32_t)Y << 32) | (uint32_t)E;
+        } else {
+          edges[p] = ~0ull;
+        }
       }
     }
   }
-}
-
-__global__ void summary_first(uint2 *sum, const int64_t *first, int64_t n) {
-  pdl_wait();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    sum[i].y = (uint32_t)first[i];
 }
 
 __device__ __forceinline__ void pack_bit(const uint2 *csum, int64_t sw, int64_t row, int32_t col, uint32_t *cpk) {
@@ -436,12 +566,13 @@ __global__ void packed_row_counts(const uint2 *csum, const uint32_t *cpk, int32_
 // the classes of out-row Y in ascending order at mg_rowptr[Y], counts zeroed
 // (warp per row, lane per summary record; records ascend with the lane)
 __global__ void packed_row_enumerate(const uint2 *csum, const uint32_t *cpk, int32_t c, int64_t sw,
-                                     const int64_t *mg_rowptr, int32_t *mg_dst, int32_t *mg_cnt) {
+                                     const int64_t *mg_rowptr, int32_t *mg_dst, int32_t *mg_cnt, int32_t *wrank) {
   pdl_wait();
   const uint32_t lane = threadIdx.x & 31u;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t Y = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; Y < c; Y += nwarps) {
-    int64_t pos = mg_rowptr[Y];
+    const int64_t row0 = mg_rowptr[Y];
+    int64_t pos = row0;
     for (int64_t k0 = 0; k0 < sw; k0 += 32) {
       const int64_t k = k0 + lane;
       uint2 rec = make_uint2(0u, 0u);
@@ -463,6 +594,7 @@ __global__ void packed_row_enumerate(const uint2 *csum, const uint32_t *cpk, int
         const int j = __ffs(bits) - 1;
         bits &= bits - 1u;
         uint32_t word = cpk[idx];
+        wrank[idx] = (int32_t)(p - row0);  // position of the word's first class in the row
         while (word) {
           const int b = __ffs(word) - 1;
           word &= word - 1u;
@@ -508,17 +640,17 @@ __global__ void destination_records(const int32_t *cls_n, const int32_t *cls_a, 
 
 }  // namespace
 
-UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted, Scratch &ws, cudaStream_t st) {
+UnionBitmap union_bitmap(mm_system *s, int64_t warps_wanted, Scratch &ws, cudaStream_t st, size_t reserve) {
   UnionBitmap ub;
   ub.words = (int32_t)std::max<int64_t>(1, ceil_div(std::max(s->summary.max_class_methods, 1), 32));
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps_wanted, 8), B300_SMS * 8));
   ub.grid = (unsigned)blocks;
   const size_t per_block = (size_t)ub.words * 8 * sizeof(uint32_t);
-  if (per_block <= 48 * 1024) {
-    ub.smem = per_block;
+  if (per_block + reserve <= 48 * 1024) {
+    ub.smem = per_block + reserve;
     ub.gbm = nullptr;
   } else {
-    ub.smem = 0;
+    ub.smem = reserve;
     const size_t bytes = per_block * (size_t)blocks;
     ub.gbm = static_cast<uint32_t *>(ws.need(bytes, st));
     MM_CUDA_TRY(cudaMemsetAsync(ub.gbm, 0, bytes, st));
@@ -629,11 +761,11 @@ void build_metrics(mm_system *s, bool lcom, bool coupling, const LcomClasses *on
         mlist = ml;
       }
       const int g = lcom_group(nl);
-      const UnionBitmap ub = union_bitmap(s, ceil_div(nl, g), uw, sa);
+      const UnionBitmap ub = union_bitmap(s, ceil_div(nl, g), uw, sa, LU_RESERVE);
       MM_CUDA_TRY(cudaMemsetAsync(s->d_u64 + 8, 0, sizeof(unsigned long long), sa));
-      pdl_launch(lcom_union, ub.grid, 256, ub.smem, sa, s->method_class, s->acc_rowptr, s->acc_idx, s->attr_class,
-                 s->own_ptr, s->own_list, s->own, (int32_t)nl, ub.words, ub.gbm, s->q, s->cls_Q, g, s->d_u64 + 8,
-                 mlist);
+      pdl_launch(lcom_union, ub.grid, 256, ub.smem, sa, s->method_class, s->method_local, s->acc_rowptr, s->acc_idx,
+                 s->attr_class, s->own_ptr, s->own_list, s->own, (int32_t)nl, ub.words, ub.gbm, s->q, s->cls_Q, g,
+                 s->d_u64 + 8, mlist);
       MM_LAUNCH_CHECK();
     }
     if (only) {
@@ -664,23 +796,17 @@ void build_metrics(mm_system *s, bool lcom, bool coupling, const LcomClasses *on
     // bitsets wait for a dense evaluation
     s->adj_built = false;
     Carve cv{static_cast<char *>(s->eval_ws.need(
-        256 * 4 + sizeof(uint64_t) * (size_t)std::max<int64_t>(nk, 1) + (sizeof(int64_t) + sizeof(int32_t)) * (size_t)ns,
-        st))};
+        256 * 2 + (sizeof(uint64_t) + sizeof(int32_t)) * (size_t)std::max<int64_t>(nk, 1), st))};
     uint64_t *edges = cv.take<uint64_t>(nk);
-    int64_t *first = cv.take<int64_t>(ns);
-    int32_t *cnt = cv.take<int32_t>(ns);
+    int32_t *wrank = cv.take<int32_t>(std::max<int64_t>(nk, 1));  // out-rows hold at most nk packed words
     zero_buffers(s->csum, sizeof(uint2) * (size_t)ns, s->cpk, sizeof(uint32_t) * 2 * (size_t)nk, nullptr, 0, st);
     if (M > 0) {
-      pdl_launch(coupling_keys, grid_for(M), TPB, 0, st, s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
+      pdl_launch(coupling_keys, (unsigned)std::min<int64_t>(ceil_div(M, 256), B300_SMS * 16), TPB, 0, st,
+                 s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
                  s->acc_idx, s->attr_class, M, c, s->cbo_attrs, s->csum, sw, edges);
       MM_LAUNCH_CHECK();
     }
-    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(ns, TPB), B300_SMS * 16);
-    pdl_launch(summary_popc, g, TPB, 0, st, static_cast<const uint2 *>(s->csum), ns, cnt);
-    MM_LAUNCH_CHECK();
-    scan_exclusive_i32to64(cnt, first, ns, s->sort_ws, st);
-    pdl_launch(summary_first, g, TPB, 0, st, s->csum, static_cast<const int64_t *>(first), ns);
-    MM_LAUNCH_CHECK();
+    scan_summary_first(s->csum, ns, s->sort_ws, st);
     const unsigned grow = (unsigned)std::min<int64_t>(ceil_div((int64_t)c * 32, TPB), B300_SMS * 16);
     if (nk > 0) {
       const unsigned gk = (unsigned)std::min<int64_t>(ceil_div(nk, TPB), B300_SMS * 16);
@@ -694,12 +820,13 @@ void build_metrics(mm_system *s, bool lcom, bool coupling, const LcomClasses *on
     scan_exclusive_i32to64(row_count, s->mg_rowptr, c, s->sort_ws, st, s->mg_rowptr + c);
     pdl_launch(packed_row_enumerate, grow, TPB, 0, st, static_cast<const uint2 *>(s->csum),
                static_cast<const uint32_t *>(s->cpk), c, sw, static_cast<const int64_t *>(s->mg_rowptr), s->mg_dst,
-               s->mg_cnt);
+               s->mg_cnt, wrank);
     MM_LAUNCH_CHECK();
     if (nk > 0) {
-      pdl_launch(coupling_count, (unsigned)std::min<int64_t>(ceil_div(nk, TPB), B300_SMS * 16), TPB, 0, st,
+      pdl_launch(coupling_count_packed, (unsigned)std::min<int64_t>(ceil_div(nk, TPB), B300_SMS * 16), TPB, 0, st,
                  static_cast<const uint64_t *>(edges), nk, static_cast<const int64_t *>(s->mg_rowptr),
-                 static_cast<const int32_t *>(s->mg_dst), s->mg_cnt);
+                 static_cast<const uint2 *>(s->csum), static_cast<const uint32_t *>(s->cpk),
+                 static_cast<const int32_t *>(wrank), sw, s->mg_cnt);
       MM_LAUNCH_CHECK();
     }
     MM_CUDA_TRY(cudaMemcpyAsync(s->mg_count, s->mg_rowptr + c, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));

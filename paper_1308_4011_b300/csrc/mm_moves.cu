@@ -111,30 +111,45 @@ __global__ void __launch_bounds__(256) l_entries_s(const int4 *l_list, const int
 // count the list entries (and the own-class run), once, after a scan of the
 // counts, to write them in method order.
 
-__global__ void method_use_keys32(const int32_t *method_class, const int64_t *call_rowptr, const int32_t *call_idx,
-                                  const int64_t *acc_rowptr, const int32_t *acc_idx, const int32_t *attr_class,
-                                  int32_t M, uint32_t *keys) {
+__global__ void method_use_keys32(const int32_t *__restrict__ method_class, const int64_t *__restrict__ call_rowptr,
+                                  const int32_t *__restrict__ call_idx, const int64_t *__restrict__ acc_rowptr,
+                                  const int32_t *__restrict__ acc_idx, const int32_t *__restrict__ attr_class,
+                                  int32_t M, uint32_t *__restrict__ keys) {
   pdl_wait();
   int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= M) return;
-  int64_t pos = call_rowptr[x] + acc_rowptr[x];
-  for (int64_t e = call_rowptr[x]; e < call_rowptr[x + 1]; ++e)
-    keys[pos++] = (uint32_t)method_class[call_idx[e]] << 1;
-  for (int64_t e = acc_rowptr[x]; e < acc_rowptr[x + 1]; ++e)
-    keys[pos++] = ((uint32_t)attr_class[acc_idx[e]] << 1) | 1u;
+  const int64_t c0 = call_rowptr[x], c1 = call_rowptr[x + 1], a0 = acc_rowptr[x], a1 = acc_rowptr[x + 1];
+  uint32_t *out = keys + c0 + a0;
+#pragma unroll 4
+  for (int64_t e = c0; e < c1; ++e) *out++ = (uint32_t)method_class[call_idx[e]] << 1;
+#pragma unroll 4
+  for (int64_t e = a0; e < a1; ++e) *out++ = ((uint32_t)attr_class[acc_idx[e]] << 1) | 1u;
 }
 
 // class of every caller y of x, bucketed by callee x (order inside a bucket is arbitrary)
-__global__ void caller_classes_scatter(const int32_t *method_class, const int64_t *call_rowptr,
-                                       const int32_t *call_idx, int32_t M, const int64_t *rin_off,
-                                       int32_t *cursor, uint32_t *keys) {
+__global__ void caller_classes_scatter(const int32_t *__restrict__ method_class,
+                                       const int64_t *__restrict__ call_rowptr, const int32_t *__restrict__ call_idx,
+                                       int32_t M, const int64_t *__restrict__ rin_off, int32_t *__restrict__ cursor,
+                                       uint32_t *__restrict__ keys) {
   pdl_wait();
   int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (y >= M) return;
   const uint32_t cy = (uint32_t)method_class[y];
-  for (int64_t e = call_rowptr[y]; e < call_rowptr[y + 1]; ++e) {
-    const int32_t x = call_idx[e];
-    keys[rin_off[x] + atomicAdd(&cursor[x], 1)] = cy;
+  const int64_t e1 = call_rowptr[y + 1];
+  for (int64_t e0 = call_rowptr[y]; e0 < e1; e0 += 4) {
+    int32_t xs[4];
+    int64_t off[4];
+    int32_t slot[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xs[u] = e0 + u < e1 ? call_idx[e0 + u] : -1;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      off[u] = xs[u] >= 0 ? rin_off[xs[u]] : 0;
+      slot[u] = xs[u] >= 0 ? atomicAdd(&cursor[xs[u]], 1) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (xs[u] >= 0) keys[off[u] + slot[u]] = cy;
   }
 }
 
@@ -496,8 +511,8 @@ void begin_move_lists(mm_system *s) {
   const ListBufs b = list_bufs(s, sl, sr);
   // list L: per-method sort of the use keys, runs counted, scanned, written
   if (nu > 0) {
-    pdl_launch(method_use_keys32, grid_for(M), TPB, 0, sl, s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr,
-                                                   s->acc_idx, s->attr_class, M, b.lkeys);
+    pdl_launch(method_use_keys32, grid_for(M), TPB, 0, sl,
+               s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr, s->acc_idx, s->attr_class, M, b.lkeys);
     MM_LAUNCH_CHECK();
   }
   pdl_launch(segment_sort_count_block, grid_for(M), 256, 0, sl, s->call_rowptr, s->acc_rowptr, M, b.lkeys, b.lsorted, 1,

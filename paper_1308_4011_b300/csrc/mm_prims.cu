@@ -82,9 +82,30 @@ constexpr int SCAN1_THREADS = 1024;
 constexpr int SCAN1_ROWS = 16;
 constexpr int64_t SCAN1_MAX = (int64_t)SCAN1_THREADS * SCAN1_ROWS;  // larger inputs: the one-pass scan
 
+// Element access of the scans: ld(k) is element k of the input as the sum
+// type, st(k, v) writes output k (plain arrays, or fields of records).
 template <class Tin, class Tout>
-__global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(const Tin *in, Tout *out, int64_t n,
-                                                                   Tout *total_out) {
+struct ArrLoad {
+  const Tin *p;
+  __device__ __forceinline__ Tout operator()(int64_t k) const { return (Tout)p[k]; }
+};
+template <class Tout>
+struct ArrStore {
+  Tout *p;
+  __device__ __forceinline__ void operator()(int64_t k, Tout v) const { p[k] = v; }
+};
+// summary records: the marked words of record k, and its first packed word
+struct SummaryLoad {
+  const uint2 *p;
+  __device__ __forceinline__ int64_t operator()(int64_t k) const { return (int64_t)__popc(p[k].x); }
+};
+struct SummaryStore {
+  uint2 *p;
+  __device__ __forceinline__ void operator()(int64_t k, int64_t v) const { p[k].y = (uint32_t)v; }
+};
+
+template <class Tout, class Ld, class St>
+__global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(Ld ld, St st, int64_t n, Tout *total_out) {
   pdl_wait();
   __shared__ Tout wsum[SCAN1_THREADS / 32];
   __shared__ Tout block_total;
@@ -96,7 +117,7 @@ __global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(const Tin *in
 #pragma unroll
   for (int i = 0; i < SCAN1_ROWS; ++i) {
     const int64_t k = b0 + i;
-    v[i] = (i < ipt && k < n) ? (Tout)in[k] : Tout(0);
+    v[i] = (i < ipt && k < n) ? ld(k) : Tout(0);
     sum += v[i];
   }
   Tout incl = sum;
@@ -123,7 +144,7 @@ __global__ void __launch_bounds__(SCAN1_THREADS) scan_single_block(const Tin *in
 #pragma unroll
   for (int i = 0; i < SCAN1_ROWS; ++i) {
     const int64_t k = b0 + i;
-    if (i < ipt && k < n) out[k] = run;
+    if (i < ipt && k < n) st(k, run);
     run += v[i];
   }
   if (threadIdx.x == 0 && total_out) *total_out = block_total;
@@ -146,8 +167,8 @@ constexpr int SP_STALL_LIMIT = 1 << 12;  // the test hook's short limit
 // stall != 0 (test hook): tile 0 holds back its state until another tile's
 // look-back has run out (or four limits have passed), so the tiles after it
 // take the fallback below.
-template <class Tin, class Tout>
-__global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(const Tin *in, Tout *out, int64_t n, Tout *total_out,
+template <class Tout, class Ld, class St>
+__global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(Ld ld, St st, int64_t n, Tout *total_out,
                                                               unsigned long long *status, unsigned int *tile_ctr,
                                                               unsigned int *fault, int wait_limit, int stall) {
   pdl_wait();
@@ -170,41 +191,61 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(const Tin *in, Tout
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
     const int64_t k = base + i;
-    v[i] = k < n ? (Tout)in[k] : Tout(0);
+    v[i] = k < n ? ld(k) : Tout(0);
     sum += v[i];
   }
   Tout ex = block_exclusive_sum<Tout>(sum, &tot);
   volatile unsigned long long *vs = status;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // warp 0 looks back over 32 predecessor states at a time: lane k reads
+    // tile j - k; the nearest inclusive state ends the walk, aggregates before
+    // it are summed, a state not yet published holds the walk at that tile
+    const uint32_t lane = threadIdx.x;
     const Tout agg = tot;
-    s_agg = agg;
     Tout prefix = 0;
-    if (tile == 0 && stall) {
-      volatile unsigned int *vf = fault;
-      for (int spins = 0; *vf == 0u && spins < 4 * wait_limit; ++spins) __nanosleep(32);
-    }
-    if (tile > 0) {
-      atomicExch(&status[tile], ((unsigned long long)agg << 2) | SP_AGG);
-      __threadfence();  // the state is visible before any output of this tile
-      int spins = 0;
-      for (int64_t j = tile - 1; j >= 0;) {
-        const unsigned long long w = vs[j];
-        const unsigned long long f = w & 3ull;
-        if (f == 0ull) {
-          if (++spins > wait_limit) {
-            atomicOr(fault, 1u);
-            s_j = j;
-            break;
-          }
-          __nanosleep(32);
-          continue;
-        }
-        prefix += (Tout)(w >> 2);
-        if (f == SP_INCL) break;
-        --j;
+    if (lane == 0) {
+      s_agg = agg;
+      if (tile == 0 && stall) {
+        volatile unsigned int *vf = fault;
+        for (int spins = 0; *vf == 0u && spins < 4 * wait_limit; ++spins) __nanosleep(32);
+      }
+      if (tile > 0) {
+        atomicExch(&status[tile], ((unsigned long long)agg << 2) | SP_AGG);
+        __threadfence();  // the state is visible before any output of this tile
       }
     }
-    s_prefix = prefix;
+    __syncwarp();
+    int spins = 0;
+    for (int64_t j = tile - 1; j >= 0;) {
+      const int64_t t = j - (int64_t)lane;
+      const unsigned long long w = t >= 0 ? (unsigned long long)vs[t] : (unsigned long long)SP_INCL;  // before tile 0: an inclusive 0
+      const unsigned long long f = w & 3ull;
+      const uint32_t incl = __ballot_sync(0xffffffffu, f == SP_INCL);
+      const uint32_t wait = __ballot_sync(0xffffffffu, f == 0ull);
+      const int32_t lim = incl ? __ffs(incl) - 1 : 31;  // lanes 0 .. lim matter
+      const uint32_t upto = lim == 31 ? 0xffffffffu : (2u << lim) - 1u;
+      const uint32_t held = wait & upto;
+      const int32_t take = held ? __ffs(held) - 1 : lim + 1;  // lanes 0 .. take-1 are summed
+      Tout part = (int32_t)lane < take ? (Tout)(w >> 2) : Tout(0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      prefix += part;
+      if (!held) {
+        if (incl) break;
+        j -= 32;
+        continue;
+      }
+      j -= take;  // the walk resumes at the tile not yet published
+      if (++spins > wait_limit) {
+        if (lane == 0) {
+          atomicOr(fault, 1u);
+          s_j = j;
+        }
+        break;
+      }
+      if (take == 0) __nanosleep(32);
+    }
+    if (lane == 0) s_prefix = prefix;
   }
   __syncthreads();
   // Fallback after a wait that ran out: the block walks on from tile s_j,
@@ -225,7 +266,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(const Tin *in, Tout
     } else {
       Tout part = 0;
       const int64_t lo = j * (int64_t)SCAN_TILE, hi = min(lo + (int64_t)SCAN_TILE, n);
-      for (int64_t k = lo + threadIdx.x; k < hi; k += SCAN_THREADS) part += (Tout)in[k];
+      for (int64_t k = lo + threadIdx.x; k < hi; k += SCAN_THREADS) part += ld(k);
       block_exclusive_sum<Tout>(part, &tot);
       if (threadIdx.x == 0) {
         __threadfence();
@@ -248,19 +289,19 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(const Tin *in, Tout
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
     const int64_t k = base + i;
-    if (k < n) out[k] = ex;
+    if (k < n) st(k, ex);
     ex += v[i];
   }
 }
 
-template <class Tin, class Tout>
-void scan_exclusive(const Tin *in, Tout *out, int64_t n, Tout *total_dev, Scratch &ws, cudaStream_t st) {
+template <class Tout, class Ld, class St>
+void scan_exclusive_with(Ld ld, St sto, int64_t n, Tout *total_dev, Scratch &ws, cudaStream_t st) {
   if (n <= 0) {
     if (total_dev) MM_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(Tout), st));
     return;
   }
   if (n <= SCAN1_MAX) {
-    pdl_launch(scan_single_block<Tin, Tout>, 1, SCAN1_THREADS, 0, st, in, out, n, total_dev);
+    pdl_launch(scan_single_block<Tout, Ld, St>, 1, SCAN1_THREADS, 0, st, ld, sto, n, total_dev);
     MM_LAUNCH_CHECK();
     return;
   }
@@ -273,10 +314,15 @@ void scan_exclusive(const Tin *in, Tout *out, int64_t n, Tout *total_dev, Scratc
     --*t_stall;
     stall = 1;
   }
-  pdl_launch(scan_onepass<Tin, Tout>, (unsigned)nb, SCAN_THREADS, 0, st, in, out, n, total_dev, status,
+  pdl_launch(scan_onepass<Tout, Ld, St>, (unsigned)nb, SCAN_THREADS, 0, st, ld, sto, n, total_dev, status,
              reinterpret_cast<unsigned int *>(status + nb), current_fault_word(),
              stall ? SP_STALL_LIMIT : SP_WAIT_LIMIT, stall);
   MM_LAUNCH_CHECK();
+}
+
+template <class Tin, class Tout>
+void scan_exclusive(const Tin *in, Tout *out, int64_t n, Tout *total_dev, Scratch &ws, cudaStream_t st) {
+  scan_exclusive_with<Tout>(ArrLoad<Tin, Tout>{in}, ArrStore<Tout>{out}, n, total_dev, ws, st);
 }
 
 // ---------------------------------------------------------------- radix sort
@@ -464,7 +510,8 @@ uint32_t stalled_scan_probe() {
   const unsigned int first = 1;
   MM_CUDA_TRY(cudaMemcpy(status + 2, &first, sizeof(first), cudaMemcpyHostToDevice));
   uint32_t *fault = reinterpret_cast<uint32_t *>(status + 3);
-  pdl_launch(scan_onepass<int32_t, int64_t>, 1, SCAN_THREADS, 0, 0, in, out, n, (int64_t *)nullptr, status,
+  pdl_launch(scan_onepass<int64_t, ArrLoad<int32_t, int64_t>, ArrStore<int64_t>>, 1, SCAN_THREADS, 0, 0,
+             ArrLoad<int32_t, int64_t>{in}, ArrStore<int64_t>{out}, n, (int64_t *)nullptr, status,
              reinterpret_cast<unsigned int *>(status + 2), fault, SP_WAIT_LIMIT, 0);
   MM_LAUNCH_CHECK();
   MM_CUDA_TRY(cudaDeviceSynchronize());
@@ -491,6 +538,10 @@ void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tot
 void scan_exclusive_i32to64(const int32_t *in, int64_t *out, int64_t n, Scratch &ws, cudaStream_t st,
                             int64_t *total_dev) {
   scan_exclusive<int32_t, int64_t>(in, out, n, total_dev, ws, st);
+}
+
+void scan_summary_first(uint2 *csum, int64_t n, Scratch &ws, cudaStream_t st) {
+  scan_exclusive_with<int64_t>(SummaryLoad{csum}, SummaryStore{csum}, n, (int64_t *)nullptr, ws, st);
 }
 
 void radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int nbits,
