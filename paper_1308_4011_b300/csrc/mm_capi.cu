@@ -171,6 +171,7 @@ void allocate_compute_buffers(mm_system *s) {
   s->sum_words = (s->adj_words + 31) / 32;
   s->csum = a.get<uint2>(s->sum_words * (2 * c + 1));
   s->cpk = a.get<uint32_t>(2 * nu);
+  s->wrank = s->packed_coupling ? a.get<int32_t>(nu) : nullptr;
   s->dest_rec = a.get<int4>(2 * c);
   s->hdr = a.get<MoveHdr>(M);
   s->l_list = a.get<int4>(nu);

@@ -272,6 +272,7 @@ struct mm_system {
   // row is non-zero; `first` = index in cpk of the first non-zero word it marks.
   uint2 *csum;
   uint32_t *cpk;                   // non-zero words, row by row (at most one per distinct pair and side)
+  int32_t *wrank;                  // packed form: per out-row word, the row position of its first class
   int64_t sum_words;               // records per row = ceil(adj_words / 32)
   // destination record per class: {P - Q, S, n, a} (32 bytes, one load per candidate)
   int4 *dest_rec;
@@ -343,6 +344,20 @@ void radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t
 void radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
                     int nbits, Scratch &ws, cudaStream_t st);
 // ---------------------------------------------------------------- pipeline stages
+
+// cnt[Y][E] of the multigraph in the packed form: bit E of out-row Y, and its
+// position in the row from the word's row position plus the bits below it
+__device__ __forceinline__ int32_t mg_lookup_packed(const uint2 *csum, const uint32_t *cpk, const int32_t *wrank,
+                                                    int64_t sw, const int64_t *rowptr, const int32_t *cnt, int32_t Y,
+                                                    int32_t E) {
+  const uint2 rec = csum[(int64_t)Y * sw + (E >> 10)];
+  const uint32_t b = ((uint32_t)E >> 5) & 31u;
+  if (!((rec.x >> b) & 1u)) return 0;
+  const uint32_t widx = rec.y + __popc(rec.x & ((1u << b) - 1u));
+  const uint32_t word = cpk[widx], below = (1u << ((uint32_t)E & 31u)) - 1u;
+  if (!((word >> ((uint32_t)E & 31u)) & 1u)) return 0;
+  return cnt[rowptr[Y] + wrank[widx] + __popc(word & below)];
+}
 
 // Use edges of a warp's group of nm <= 32 consecutive methods x0 .. x0+nm-1:
 // each method's calls, then (with_acc) its accesses, are the contiguous range

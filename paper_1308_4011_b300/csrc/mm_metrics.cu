@@ -796,9 +796,9 @@ void build_metrics(mm_system *s, bool lcom, bool coupling, const LcomClasses *on
     // bitsets wait for a dense evaluation
     s->adj_built = false;
     Carve cv{static_cast<char *>(s->eval_ws.need(
-        256 * 2 + (sizeof(uint64_t) + sizeof(int32_t)) * (size_t)std::max<int64_t>(nk, 1), st))};
+        256 + sizeof(uint64_t) * (size_t)std::max<int64_t>(nk, 1), st))};
     uint64_t *edges = cv.take<uint64_t>(nk);
-    int32_t *wrank = cv.take<int32_t>(std::max<int64_t>(nk, 1));  // out-rows hold at most nk packed words
+    int32_t *wrank = s->wrank;  // out-rows hold at most nk <= n_call + n_acc packed words
     zero_buffers(s->csum, sizeof(uint2) * (size_t)ns, s->cpk, sizeof(uint32_t) * 2 * (size_t)nk, nullptr, 0, st);
     if (M > 0) {
       pdl_launch(coupling_keys, (unsigned)std::min<int64_t>(ceil_div(M, 256), B300_SMS * 16), TPB, 0, st,

@@ -365,14 +365,27 @@ __global__ void __launch_bounds__(256) lists_fill_l(const int64_t *call_rowptr, 
 }
 
 // cnt(C, E) of every L entry with a use edge (C = class of its method)
-__global__ void lists_lookup_l(const int64_t *n_l, const int32_t *l_x, const int32_t *method_class,
-                               const int64_t *mg_rowptr, const int32_t *mg_dst, const int32_t *mg_cnt,
+// Multigraph look-ups of the list entries: a binary search in the row, or
+// (packed coupling form) the row position read off the packed words.
+struct MgLookup {
+  const int64_t *rowptr;
+  const int32_t *dst, *cnt;
+  const uint2 *csum;       // packed form (else nullptr)
+  const uint32_t *cpk;
+  const int32_t *wrank;
+  int64_t sw;
+  __device__ __forceinline__ int32_t operator()(int32_t Y, int32_t E) const {
+    return csum ? mg_lookup_packed(csum, cpk, wrank, sw, rowptr, cnt, Y, E) : mg_lookup(rowptr, dst, cnt, Y, E);
+  }
+};
+
+__global__ void lists_lookup_l(const int64_t *n_l, const int32_t *l_x, const int32_t *method_class, MgLookup mg,
                                int4 *l_list) {
   pdl_wait();
   const int64_t nl = *n_l;
   for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += (int64_t)gridDim.x * blockDim.x) {
     const int4 v = l_list[l];
-    if (v.y > 0) l_list[l].z = mg_lookup(mg_rowptr, mg_dst, mg_cnt, method_class[l_x[l]], v.x);
+    if (v.y > 0) l_list[l].z = mg(method_class[l_x[l]], v.x);
   }
 }
 
@@ -406,13 +419,12 @@ __global__ void __launch_bounds__(256) lists_fill_r(const int64_t *rin_off, int3
 }
 
 // cnt(X, C) of every R entry: {X, in, cnt(X, C), 0}
-__global__ void lists_lookup_r(const int64_t *n_r, const int64_t *mg_rowptr, const int32_t *mg_dst,
-                               const int32_t *mg_cnt, int4 *r_list) {
+__global__ void lists_lookup_r(const int64_t *n_r, MgLookup mg, int4 *r_list) {
   pdl_wait();
   const int64_t nr = *n_r;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
     const int4 v = r_list[r];
-    r_list[r] = make_int4(v.x, v.y, mg_lookup(mg_rowptr, mg_dst, mg_cnt, v.x, v.w), 0);
+    r_list[r] = make_int4(v.x, v.y, mg(v.x, v.w), 0);
   }
 }
 
@@ -546,6 +558,19 @@ void begin_move_lists(mm_system *s) {
   }
 }
 
+static MgLookup mg_lookups(const mm_system *s) {
+  MgLookup m;
+  m.rowptr = s->mg_rowptr;
+  m.dst = s->mg_dst;
+  m.cnt = s->mg_cnt;
+  const bool packed = s->packed_coupling && s->wrank;
+  m.csum = packed ? s->csum : nullptr;
+  m.cpk = s->cpk;
+  m.wrank = s->wrank;
+  m.sw = s->sum_words;
+  return m;
+}
+
 // Second half: multigraph counts of every entry (after the coupling branch),
 // s per L entry (after the own-access lists), then the per-method headers.
 void build_move_precompute(mm_system *s) {
@@ -557,8 +582,9 @@ void build_move_precompute(mm_system *s) {
   const ListBufs b = list_bufs(s, sl, sr);
   wait_point(s, 0, st, sl);
   if (nu > 0) {
-    pdl_launch(lists_lookup_l, (unsigned)std::min<int64_t>(ceil_div(nu, TPB), B300_SMS * 16), TPB, 0, sl, 
-        b.l_off + M, s->l_x, s->method_class, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->l_list);
+    pdl_launch(lists_lookup_l, (unsigned)std::min<int64_t>(ceil_div(nu, TPB), B300_SMS * 16), TPB, 0, sl,
+               static_cast<const int64_t *>(b.l_off + M), static_cast<const int32_t *>(s->l_x),
+               static_cast<const int32_t *>(s->method_class), mg_lookups(s), s->l_list);
     MM_LAUNCH_CHECK();
     wait_point(s, 1, s->side_pending[0], sl);
     const UnionBitmap ub = union_bitmap(s, ceil_div(nu, 32), s->side_union[1], sl);
@@ -568,8 +594,8 @@ void build_move_precompute(mm_system *s) {
   }
   wait_point(s, 0, st, sr);
   if (nc > 0) {
-    pdl_launch(lists_lookup_r, (unsigned)std::min<int64_t>(ceil_div(nc, TPB), B300_SMS * 16), TPB, 0, sr, 
-        b.r_off + M, s->mg_rowptr, s->mg_dst, s->mg_cnt, s->r_list);
+    pdl_launch(lists_lookup_r, (unsigned)std::min<int64_t>(ceil_div(nc, TPB), B300_SMS * 16), TPB, 0, sr,
+               static_cast<const int64_t *>(b.r_off + M), mg_lookups(s), s->r_list);
     MM_LAUNCH_CHECK();
   }
   join_side(s, 1, sl);

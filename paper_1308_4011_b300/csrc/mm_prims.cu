@@ -185,13 +185,23 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(Ld ld, St st, int64
   }
   __syncthreads();
   const int64_t tile = s_tile;
-  const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  const int64_t tile0 = tile * SCAN_TILE;
+  // the tile goes through shared memory: loaded and stored in warp-contiguous
+  // order (coalesced), scanned as SCAN_ITEMS consecutive elements per thread
+  // (one padding element per 32 keeps both orders free of bank conflicts)
+  __shared__ Tout s_x[SCAN_TILE + SCAN_TILE / 32];
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const int k = i * SCAN_THREADS + (int)threadIdx.x;
+    s_x[k + (k >> 5)] = tile0 + k < n ? ld(tile0 + k) : Tout(0);
+  }
+  __syncthreads();
   Tout v[SCAN_ITEMS];
   Tout sum = 0;
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
-    const int64_t k = base + i;
-    v[i] = k < n ? ld(k) : Tout(0);
+    const int k = (int)threadIdx.x * SCAN_ITEMS + i;
+    v[i] = s_x[k + (k >> 5)];
     sum += v[i];
   }
   Tout ex = block_exclusive_sum<Tout>(sum, &tot);
@@ -282,15 +292,21 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_onepass(Ld ld, St st, int64
     const Tout prefix = s_prefix, agg = s_agg;
     atomicExch(&status[tile], ((unsigned long long)(prefix + agg) << 2) | SP_INCL);
     __threadfence();
-    if (total_out && base + SCAN_TILE >= n) *total_out = prefix + agg;  // the last tile
+    if (total_out && tile0 + SCAN_TILE >= n) *total_out = prefix + agg;  // the last tile
   }
   if (tile == 0) __syncthreads();  // tile 0's first state comes here: publish before writing (in-place scans)
   ex += s_prefix;
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
-    const int64_t k = base + i;
-    if (k < n) st(k, ex);
+    const int k = (int)threadIdx.x * SCAN_ITEMS + i;
+    s_x[k + (k >> 5)] = ex;
     ex += v[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const int k = i * SCAN_THREADS + (int)threadIdx.x;
+    if (tile0 + k < n) st(tile0 + k, s_x[k + (k >> 5)]);
   }
 }
 
