@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(256) segment_sort_count_block(const int64_t *a
                                                                 const uint32_t *in, uint32_t *out, int shift,
                                                                 const int32_t *method_class, int32_t cbo_attrs,
                                                                 int32_t *len_out, int32_t *self_out,
-                                                                uint8_t *long_seg) {
+                                                                int32_t *work) {
   pdl_wait();
   __shared__ uint32_t sk[SB_KEYS];
   const int64_t x0 = (int64_t)blockIdx.x * blockDim.x;
@@ -228,13 +228,13 @@ __global__ void __launch_bounds__(256) segment_sort_count_block(const int64_t *a
     for (int64_t k = threadIdx.x; k < nk; k += blockDim.x) sk[k] = in[K0 + k];
   __syncthreads();
   const int64_t x = x0 + threadIdx.x;
+  bool warp_sort = false;
   if (x < M) {
     int64_t p0, len;
     segment(a, b, x, &p0, &len);
     if (!fits || len > SB_SEG) {
-      long_seg[x] = 1;
+      warp_sort = true;
     } else {
-      long_seg[x] = 0;
       uint32_t *v = sk + (p0 - K0);
       for (int32_t i = 1; i < (int32_t)len; ++i) {  // insertion sort (stable)
         const uint32_t key = v[i];
@@ -258,6 +258,15 @@ __global__ void __launch_bounds__(256) segment_sort_count_block(const int64_t *a
       self_out[x] = self;
     }
   }
+  // segments left to the warp version go on its list (one atomic per warp)
+  const uint32_t wm = __ballot_sync(0xffffffffu, warp_sort);
+  if (wm) {
+    const uint32_t lane = threadIdx.x & 31u;
+    int32_t base = 0;
+    if (lane == (uint32_t)(__ffs(wm) - 1)) base = atomicAdd(work, __popc(wm));
+    base = __shfl_sync(0xffffffffu, base, __ffs(wm) - 1);
+    if (warp_sort) work[1 + base + __popc(wm & ((1u << lane) - 1u))] = (int32_t)x;
+  }
   __syncthreads();
   if (fits)
     for (int64_t k = threadIdx.x; k < nk; k += blockDim.x) out[K0 + k] = sk[k];
@@ -272,13 +281,14 @@ __global__ void __launch_bounds__(256) segment_sort_count(const int64_t *a, cons
                                                           const uint32_t *in, uint32_t *out, int shift,
                                                           const int32_t *method_class, int32_t cbo_attrs,
                                                           int32_t *len_out, int32_t *self_out,
-                                                          const uint8_t *only) {
+                                                          const int32_t *work) {
   pdl_wait();
   __shared__ uint32_t sk[8][32];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < M; x += nwarps) {
-    if (only && !only[x]) continue;  // done by the block version
+  const int64_t nwork = work[0];  // the methods the block version left
+  for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < nwork; wi += nwarps) {
+    const int64_t x = work[1 + wi];
     int64_t p0, len;
     segment(a, b, x, &p0, &len);
     const uint32_t *runs_keys;
@@ -475,7 +485,7 @@ struct ListBufs {
   uint32_t *lkeys, *lsorted, *rkeys, *rsorted;
   int64_t *l_off, *rin_off, *r_off;
   int32_t *l_len, *out_self, *r_len, *in_self, *cursor;
-  uint8_t *llong, *rlong;
+  int32_t *lwork, *rwork;
 };
 
 ListBufs list_bufs(mm_system *s, cudaStream_t sl, cudaStream_t sr) {
@@ -487,7 +497,8 @@ ListBufs list_bufs(mm_system *s, cudaStream_t sl, cudaStream_t sr) {
     return (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nkeys, 1) + 15) / 16 * 16 +
            sizeof(int64_t) * (size_t)n64 * ((size_t)M + 1) + sizeof(int32_t) * (size_t)n32 * (size_t)M + 64;
   };
-  const size_t lb = part_bytes(nu, 1, 2) + (size_t)M, rbytes = part_bytes(nc, 2, 3) + (size_t)M;
+  const size_t work = sizeof(int32_t) * ((size_t)M + 1);
+  const size_t lb = part_bytes(nu, 1, 2) + work, rbytes = part_bytes(nc, 2, 3) + work;
   char *lbase = static_cast<char *>(s->side_eval[1].need(lb, sl));
   char *rbase = static_cast<char *>(s->side_eval[2].need(rbytes, sr));
   ListBufs b;
@@ -496,7 +507,7 @@ ListBufs list_bufs(mm_system *s, cudaStream_t sl, cudaStream_t sr) {
   b.l_off = reinterpret_cast<int64_t *>(lbase + (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nu, 1) + 15) / 16 * 16);
   b.l_len = reinterpret_cast<int32_t *>(b.l_off + (M + 1));
   b.out_self = b.l_len + M;
-  b.llong = reinterpret_cast<uint8_t *>(b.out_self + M);  // segments left to the warp version
+  b.lwork = b.out_self + M;  // [0]: count, then the methods whose segments the warp version sorts
   b.rkeys = reinterpret_cast<uint32_t *>(rbase);
   b.rsorted = b.rkeys + std::max<int64_t>(nc, 1);
   b.rin_off = reinterpret_cast<int64_t *>(rbase + (sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(nc, 1) + 15) / 16 * 16);
@@ -504,7 +515,7 @@ ListBufs list_bufs(mm_system *s, cudaStream_t sl, cudaStream_t sr) {
   b.r_len = reinterpret_cast<int32_t *>(b.r_off + (M + 1));
   b.in_self = b.r_len + M;
   b.cursor = b.in_self + M;
-  b.rlong = reinterpret_cast<uint8_t *>(b.cursor + M);
+  b.rwork = b.cursor + M;
   return b;
 }
 }  // namespace
@@ -516,7 +527,8 @@ void begin_move_lists(mm_system *s) {
   s->side_pending[1] = s->side_pending[2] = s->stream;
   if (M == 0) return;
   const int64_t nu = s->n_call + s->n_acc, nc = s->n_call;
-  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * 32, TPB), B300_SMS * 16);
+  // the warp sorts take only the segments the block sorts left: a few per system
+  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * 32, TPB), B300_SMS * 2);
   cudaStream_t sl = fork_side(s, 1), sr = fork_side(s, 2);
   s->side_pending[1] = sl;
   s->side_pending[2] = sr;
@@ -527,11 +539,12 @@ void begin_move_lists(mm_system *s) {
                s->method_class, s->call_rowptr, s->call_idx, s->acc_rowptr, s->acc_idx, s->attr_class, M, b.lkeys);
     MM_LAUNCH_CHECK();
   }
+  MM_CUDA_TRY(cudaMemsetAsync(b.lwork, 0, sizeof(int32_t), sl));
   pdl_launch(segment_sort_count_block, grid_for(M), 256, 0, sl, s->call_rowptr, s->acc_rowptr, M, b.lkeys, b.lsorted, 1,
-                                                        s->method_class, s->cbo_attrs, b.l_len, b.out_self, b.llong);
+                                                        s->method_class, s->cbo_attrs, b.l_len, b.out_self, b.lwork);
   MM_LAUNCH_CHECK();
   pdl_launch(segment_sort_count, gw, TPB, 0, sl, s->call_rowptr, s->acc_rowptr, M, b.lkeys, b.lsorted, 1, s->method_class,
-                                         s->cbo_attrs, b.l_len, b.out_self, b.llong);
+                                         s->cbo_attrs, b.l_len, b.out_self, static_cast<const int32_t *>(b.lwork));
   MM_LAUNCH_CHECK();
   scan_exclusive_i32to64(b.l_len, b.l_off, M, s->side_sort[1], sl, b.l_off + M);
   pdl_launch(lists_fill_l, grid_for(M), 256, 0, sl, s->call_rowptr, s->acc_rowptr, M, b.lsorted, s->method_class,
@@ -545,11 +558,12 @@ void begin_move_lists(mm_system *s) {
                                                         b.cursor, b.rkeys);
     MM_LAUNCH_CHECK();
   }
+  MM_CUDA_TRY(cudaMemsetAsync(b.rwork, 0, sizeof(int32_t), sr));
   pdl_launch(segment_sort_count_block, grid_for(M), 256, 0, sr, b.rin_off, nullptr, M, b.rkeys, b.rsorted, 0,
-                                                        s->method_class, s->cbo_attrs, b.r_len, b.in_self, b.rlong);
+                                                        s->method_class, s->cbo_attrs, b.r_len, b.in_self, b.rwork);
   MM_LAUNCH_CHECK();
   pdl_launch(segment_sort_count, gw, TPB, 0, sr, b.rin_off, nullptr, M, b.rkeys, b.rsorted, 0, s->method_class,
-                                         s->cbo_attrs, b.r_len, b.in_self, b.rlong);
+                                         s->cbo_attrs, b.r_len, b.in_self, static_cast<const int32_t *>(b.rwork));
   MM_LAUNCH_CHECK();
   scan_exclusive_i32to64(b.r_len, b.r_off, M, s->side_sort[2], sr, b.r_off + M);
   if (nc > 0) {
