@@ -273,18 +273,45 @@ def job_oracle_snapshot(c, arrays, mask, mi, topk):
             "top": [(int(k["m"]), int(k["d"])) for k in r.kept[:topk]], "n_cand": r.n_cand}
 
 
+class _Deferred:
+    """A job held until Verifier.start(); get() waits for its result."""
+
+    def __init__(self, verifier, fn, args):
+        self.verifier, self.fn, self.args, self.res = verifier, fn, args, None
+
+    def get(self):
+        self.verifier.start()
+        return self.res.get()
+
+
 class Verifier:
     """One spawned worker process (the oracle threads over all host cores),
-    started before the first GPU call."""
+    started before the first GPU call.  Jobs are held until start() (or the
+    first get()), so that the host-driven timed sections do not share the
+    host cores with them; after it they run as they are submitted."""
 
     def __init__(self):
         import multiprocessing as mp
         self.pool = mp.get_context("spawn").Pool(1, initializer=_verifier_init)
+        self.held = []
+        self.running = False
 
     def submit(self, fn, *args):
-        return self.pool.apply_async(fn, args)
+        job = _Deferred(self, fn, args)
+        if self.running:
+            job.res = self.pool.apply_async(fn, args)
+        else:
+            self.held.append(job)
+        return job
+
+    def start(self):
+        self.running = True
+        for job in self.held:
+            job.res = self.pool.apply_async(job.fn, job.args)
+        self.held = []
 
     def close(self):
+        self.start()
         self.pool.close()
         self.pool.join()
 
@@ -1053,6 +1080,10 @@ def main():
     line, large_checks, system = run_large(args, rank, world, local_rank, verifier, dist)
     if "serving" in sections:
         nested["serving"], serving_snaps = run_serving(args, local_rank, verifier)
+    if verifier:
+        # the host-driven sections (the bench line, serving) are done: the
+        # oracle's jobs run from here on, beside the graph- and kernel-bound ones
+        verifier.start()
     if "batched" in sections:
         nested["batched"], batched_check = run_batched(args, local_rank, verifier)
     if "medium" in sections:
