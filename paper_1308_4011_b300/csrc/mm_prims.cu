@@ -364,55 +364,90 @@ __global__ void radix_upsweep(const K *keys, int64_t n, int shift, uint32_t *his
   for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) hist[(int64_t)d * ntiles + blockIdx.x] = cnt[d];
 }
 
+// Scatter pass: every key's rank among the tile's keys of its digit (warps in
+// order, then rows, then lanes: the input order, so the pass is stable).  The
+// tile is first staged in shared memory in digit order, then written out
+// position by position, so that keys of one digit leave as a contiguous run
+// (coalesced stores instead of one scattered store per key).
 template <class K, bool VALS>
 __global__ void __launch_bounds__(RS_THREADS) radix_downsweep(const K *keys_in, const uint32_t *vals_in,
                                                                K *keys_out, uint32_t *vals_out, int64_t n,
                                                                int shift, const uint32_t *offsets,
                                                                int64_t ntiles) {
+  static_assert(RS_THREADS == RS_RADIX, "one digit per thread in the per-digit passes");
   pdl_wait();
   __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
+  __shared__ uint32_t tstart[RS_RADIX];  // first tile-local position of each digit
+  __shared__ uint32_t goff[RS_RADIX];    // first output position of each digit for this tile
+  __shared__ K skey[RS_TILE];
+  __shared__ uint8_t sdig[RS_TILE];
+  __shared__ uint32_t ttotal;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < RS_WARPS * RS_RADIX; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
   __syncthreads();
-  const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (RS_ITEMS * 32);
+  const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t wbase = tbase + (int64_t)warp * (RS_ITEMS * 32);
   const uint32_t lt = (1u << lane) - 1u;
-  K key[RS_ITEMS];
-  uint32_t val[RS_ITEMS];
-  uint32_t rank[RS_ITEMS];
-  uint32_t dig[RS_ITEMS];
+  // per key: its rank among the warp's keys of its digit (< 512) << 8 | digit,
+  // or ~0 past the end; the keys themselves are read again when staged
+  uint32_t rd[RS_ITEMS];
 #pragma unroll
   for (int r = 0; r < RS_ITEMS; ++r) {
     int64_t idx = wbase + r * 32 + lane;
     bool valid = idx < n;
-    key[r] = valid ? keys_in[idx] : K(0);
-    if (VALS) val[r] = valid ? vals_in[idx] : 0u;
-    uint32_t d = (uint32_t)(key[r] >> shift) & 0xffu;
-    dig[r] = valid ? d : 0xffffffffu;
+    const K k = valid ? keys_in[idx] : K(0);
+    uint32_t d = (uint32_t)(k >> shift) & 0xffu;
     uint32_t tag = valid ? d : (0x1000u + lane);  // invalid lanes never match
     uint32_t peers = __match_any_sync(0xffffffffu, tag);
     uint32_t before = 0;
     if (valid) before = wcnt[warp][d];
-    rank[r] = before + __popc(peers & lt);
+    rd[r] = valid ? ((before + __popc(peers & lt)) << 8) | d : 0xffffffffu;
     __syncwarp();
     if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) {
-    uint32_t run = offsets[(int64_t)d * ntiles + blockIdx.x];
-    for (int w = 0; w < RS_WARPS; ++w) {
-      uint32_t t = wcnt[w][d];
-      wcnt[w][d] = run;
-      run += t;
-    }
+  // per digit (thread d): the warps' prefixes, the tile's count and its output offset
+  const int d0 = threadIdx.x;
+  uint32_t run = 0;
+  for (int w = 0; w < RS_WARPS; ++w) {
+    const uint32_t t = wcnt[w][d0];
+    wcnt[w][d0] = run;
+    run += t;
   }
+  goff[d0] = offsets[(int64_t)d0 * ntiles + blockIdx.x];
+  const uint32_t ts = block_exclusive_sum<uint32_t>(run, &ttotal);  // synchronises the block
+  tstart[d0] = ts;
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < RS_ITEMS; ++r) {
-    if (dig[r] != 0xffffffffu) {
-      uint32_t pos = wcnt[warp][dig[r]] + rank[r];
-      keys_out[pos] = key[r];
-      if (VALS) vals_out[pos] = val[r];
+    if (rd[r] != 0xffffffffu) {
+      const uint32_t d = rd[r] & 0xffu;
+      const uint32_t lp = tstart[d] + wcnt[warp][d] + (rd[r] >> 8);
+      skey[lp] = keys_in[wbase + r * 32 + lane];
+      sdig[lp] = (uint8_t)d;
+    }
+  }
+  __syncthreads();
+  const int cnt = (int)min((int64_t)RS_TILE, n - tbase);
+  for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
+    const uint32_t d = sdig[i];
+    keys_out[goff[d] + (uint32_t)i - tstart[d]] = skey[i];
+  }
+  if (VALS) {
+    __syncthreads();  // the keys are out: their stage takes the values
+    uint32_t *sval = reinterpret_cast<uint32_t *>(skey);
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+      if (rd[r] != 0xffffffffu) {
+        const uint32_t d = rd[r] & 0xffu;
+        sval[tstart[d] + wcnt[warp][d] + (rd[r] >> 8)] = vals_in[wbase + r * 32 + lane];
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
+      const uint32_t d = sdig[i];
+      vals_out[goff[d] + (uint32_t)i - tstart[d]] = sval[i];
     }
   }
 }

@@ -117,11 +117,21 @@ __global__ void run_heads(const uint64_t *keys, int64_t n, int32_t *flag) {
     flag[k] = (k == 0 || keys[k - 1] != keys[k]) ? 1 : 0;
 }
 
-// every run becomes one value (x, y, i, u); the sum of i per u for the average
+// every run becomes one value (x, y, i, u); the sum of i per u for the average.
+// u takes few distinct values, so the sums are gathered per block in shared
+// memory (when u's range fits) and added to the global ones once per block.
+constexpr int SV_HIST_MAX = 4096;  // u in [0, SV_HIST_MAX): shared-memory sums
+
 __global__ void similarity_values(const uint64_t *keys, int64_t n, const int32_t *flag, const int64_t *pos,
                                   const int32_t *np, int32_t M, int32_t *px, int32_t *py, int32_t *pi, int32_t *pu,
-                                  unsigned long long *sum_i) {
+                                  unsigned long long *sum_i, int32_t umax) {
   pdl_wait();
+  extern __shared__ unsigned long long sv_sum[];
+  const bool local = umax < SV_HIST_MAX;
+  if (local) {
+    for (int32_t t = threadIdx.x; t <= umax; t += blockDim.x) sv_sum[t] = 0ull;
+    __syncthreads();
+  }
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     if (!flag[k]) continue;
     const uint64_t key = keys[k];
@@ -134,7 +144,12 @@ __global__ void similarity_values(const uint64_t *keys, int64_t n, const int32_t
     py[o] = y;
     pi[o] = i;
     pu[o] = u;
-    atomicAdd(&sum_i[u], (unsigned long long)i);
+    atomicAdd(local ? &sv_sum[u] : &sum_i[u], (unsigned long long)i);
+  }
+  if (local) {
+    __syncthreads();
+    for (int32_t t = threadIdx.x; t <= umax; t += blockDim.x)
+      if (sv_sum[t]) atomicAdd(&sum_i[t], sv_sum[t]);
   }
 }
 
@@ -299,9 +314,11 @@ void compute_similarity(mm_system *s) {
   s->sim_i = vv.take<int32_t>(n_val);
   s->sim_u = vv.take<int32_t>(n_val);
   MM_CUDA_TRY(cudaMemsetAsync(sum_i, 0, sizeof(unsigned long long) * (size_t)(s->sim_umax + 1), st));
-  pdl_launch(similarity_values, grid_for(n_co), TPB, 0, st, static_cast<const uint64_t *>(keys), n_co,
-             static_cast<const int32_t *>(flag), static_cast<const int64_t *>(pos), static_cast<const int32_t *>(np),
-             M, s->sim_x, s->sim_y, s->sim_i, s->sim_u, sum_i);
+  const size_t sv_smem = s->sim_umax < SV_HIST_MAX ? sizeof(unsigned long long) * ((size_t)s->sim_umax + 1) : 0;
+  pdl_launch(similarity_values, (unsigned)std::min<int64_t>(ceil_div(n_co, TPB), B300_SMS * 8), TPB, sv_smem, st,
+             static_cast<const uint64_t *>(keys), n_co, static_cast<const int32_t *>(flag),
+             static_cast<const int64_t *>(pos), static_cast<const int32_t *>(np), M, s->sim_x, s->sim_y, s->sim_i,
+             s->sim_u, sum_i, s->sim_umax);
   MM_LAUNCH_CHECK();
   // the average over the values, in one fixed order (u ascending), on the host
   std::vector<unsigned long long> hs((size_t)s->sim_umax + 1);
