@@ -28,9 +28,9 @@ Measured in the same run and reported as nested keys:
            the medium system, rule R3 on the large system, four rounds of
            non-conflicting moves on the medium system.
 The oracle checks run in a separate low-priority process started before the
-first GPU call; the bench line is timed first, before any oracle job is queued,
-and the nested sections run beside the checks; the CPU baseline is timed after
-them.
+first GPU call; its jobs are held until the bench line and the serving section
+(both driven by host threads) are timed, and run beside the other nested
+sections; the CPU baseline is timed after them.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
